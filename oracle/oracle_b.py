@@ -1,0 +1,241 @@
+"""The Lagrange FMM by its algorithm, in plain NumPy, for tiny inputs.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+``lagrange_fmm`` follows Algorithm 2 of arXiv:1712.07739 step by step on a
+uniform octree with levels 0 .. L-1:
+
+  (1.a) P2M  W_m  = sum_{y_j in I} L_p(ybar_m, y_j) q_j              (leaves)
+  (1.b) M2M  W_m' = sum_{J in C(I)} sum_m L_p(ybar_m', ybar_m) W_m   (up)
+  (2)   M2L  s(xbar_l) = sum_{J in I(I)} sum_m K(xbar_l - ybar_m) W_m
+  (3.a) L2L  s(xbar_l') += sum_l L_p(xbar_l', xbar_l) s(xbar_l)       (down)
+  (3.b) L2P  s(x_i) = sum_l L_p(xbar_l, x_i) s(xbar_l) + near sum over N(I)
+
+``pairwise_far_field`` is Algorithm 1 applied to every interaction-list pair
+at every level (no M2M / L2L); the two agree to rounding because same-degree
+Lagrange interpolation reproduces the parent basis exactly, which is a pin.
+
+Conventions (readings of the paper where it is silent):
+* root cube: edge H = s (1 + 2^-10), s the largest extent of the source
+  points (1 if they coincide), centred on their bounding box; a point goes to
+  cell floor((y - origin) * (2^l / H)), clamped to [0, 2^l - 1];
+* nodes: p equispaced nodes per dimension including the cell faces,
+  t_a = a / (p - 1), a = 0..p-1 (Section 4.1);
+* basis: "owner cell's basis at node l, evaluated at the point" for all of
+  P2M, M2M, L2L and L2P (the argument order of L_p is inconsistent between
+  Algorithms 1 and 2);
+* C(.), I(.), P(.), N(.) are the standard uniform-octree sets; M2L runs at
+  levels >= 2; the near sum skips source points of the target's own segment.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+from . import direct_stress, kernel
+
+
+def root_box(y):
+    lo = y.min(axis=0)
+    hi = y.max(axis=0)
+    s = float(np.max(hi - lo))
+    if s == 0.0:
+        s = 1.0
+    H = s * (1.0 + 2.0 ** -10)
+    origin = 0.5 * (lo + hi) - 0.5 * H
+    return origin, H
+
+
+def cell_of(y, origin, H, level):
+    n = 1 << level
+    idx = np.floor((y - origin) * (n / H)).astype(np.int64)
+    return np.clip(idx, 0, n - 1)
+
+
+def basis_1d(t, p):
+    """ell_a(t) = prod_{b != a} (t - t_b) / (t_a - t_b), t_a = a/(p-1)."""
+    nodes = np.arange(p) / (p - 1)
+    t = np.asarray(t, dtype=np.float64)
+    out = np.ones(t.shape + (p,))
+    for a in range(p):
+        for b in range(p):
+            if b != a:
+                out[..., a] *= (t - nodes[b]) / (nodes[a] - nodes[b])
+    return out
+
+
+def basis_3d(t, p):
+    """L_p(xbar_l, x) for local coordinates t [n, 3] -> [n, p^3], l = (a, b, c)
+    flattened with a (x) slowest."""
+    bx, by, bz = basis_1d(t[:, 0], p), basis_1d(t[:, 1], p), basis_1d(t[:, 2], p)
+    return np.einsum("na,nb,nc->nabc", bx, by, bz).reshape(len(t), p ** 3)
+
+
+def child_transfer(p):
+    """M[c][a', a] = ell_a'((c + t_a) / 2): parent basis a' at child node a."""
+    nodes = np.arange(p) / (p - 1)
+    return [basis_1d((c + nodes) / 2.0, p).T for c in (0, 1)]
+
+
+def interaction_offsets(cell):
+    """Offsets o = B - A of the interaction list I(B) for a cell B at
+    integer coordinates ``cell``: children of the parent's neighbours that
+    are not neighbours of B."""
+    par = np.asarray(cell) // 2
+    out = []
+    for dp in itertools.product((-1, 0, 1), repeat=3):
+        for c in itertools.product((0, 1), repeat=3):
+            a = 2 * (par + np.asarray(dp)) + np.asarray(c)
+            o = np.asarray(cell) - a
+            if np.max(np.abs(o)) >= 2:
+                out.append(tuple(o))
+    return out
+
+
+def _node_kernels(mat, p, h, o, rows=None):
+    """T_o[l, :, m, :] = K(xbar_l - ybar_m) for one offset o, with the node
+    difference (o + (t_l - t_m)) h; returns [len(rows), 6, p^3, 9] for the
+    requested target-node rows l (all rows by default)."""
+    t = np.arange(p) / (p - 1)
+    g = np.array(list(itertools.product(t, t, t)))  # [p^3, 3], x slowest
+    if rows is None:
+        rows = np.arange(len(g))
+    diff = g[rows][:, None, :] - g[None, :, :]       # [l, m, 3]
+    d = (np.asarray(o, dtype=np.float64)[None, None, :] + diff) * h
+    K = kernel(mat, d.reshape(-1, 3)).reshape(len(rows), len(g), 6, 9)
+    return np.ascontiguousarray(K.transpose(0, 2, 1, 3))
+
+
+def _apply_offset(mat, p, h, o, Wstack, chunk=64):
+    """sum_m K(xbar_l - ybar_m) W_m for a stack of source weights [n, p^3, 9]
+    -> [n, p^3, 6], building the node kernel a block of rows at a time."""
+    P3 = p ** 3
+    out = np.zeros((Wstack.shape[0], P3, 6))
+    for r0 in range(0, P3, chunk):
+        rows = np.arange(r0, min(P3, r0 + chunk))
+        T = _node_kernels(mat, p, h, o, rows)
+        out[:, rows, :] = np.einsum("lamw,nmw->nla", T, Wstack)
+    return out
+
+
+def _near(mat, xt, tseg, tleaf, ys, qs, sseg, sleaf, n):
+    out = np.zeros((len(xt), 6))
+    skey = sleaf[:, 0] * n * n + sleaf[:, 1] * n + sleaf[:, 2]
+    order = np.argsort(skey, kind="stable")
+    for key in np.unique(tleaf[:, 0] * n * n + tleaf[:, 1] * n + tleaf[:, 2]):
+        B = np.array([key // (n * n), (key // n) % n, key % n])
+        ti = np.nonzero((tleaf == B).all(axis=1))[0]
+        lo = np.maximum(B - 1, 0)
+        hi = np.minimum(B + 1, n - 1)
+        m = ((sleaf >= lo) & (sleaf <= hi)).all(axis=1)
+        sj = np.nonzero(m)[0]
+        if len(sj) == 0:
+            continue
+        out[ti] = direct_stress(mat, xt[ti], tseg[ti], ys[sj], qs[sj], sseg[sj])
+    del order
+    return out
+
+
+def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
+    """Stress [n_t, 6] at targets by Algorithm 2 (targets default to sources)."""
+    ys = np.asarray(ys, dtype=np.float64)
+    qs = np.asarray(qs, dtype=np.float64).reshape(-1, 9)
+    if xt is None:
+        xt, tseg = ys, sseg
+    origin, H = root_box(ys)
+    lf = L - 1
+    nL = 1 << lf
+    P3 = p ** 3
+    # (1.a) P2M at the leaves
+    W = {lf: np.zeros((nL, nL, nL, P3, 9))}
+    sl = cell_of(ys, origin, H, lf)
+    hL = H / nL
+    t = (ys - (origin + sl * hL)) / hL
+    Lb = basis_3d(t, p)
+    np.add.at(W[lf], (sl[:, 0], sl[:, 1], sl[:, 2]), Lb[:, :, None] * qs[:, None, :])
+    # (1.b) M2M up the tree
+    M = child_transfer(p)
+    for lev in range(lf - 1, 1, -1):
+        n = 1 << lev
+        Wp = np.zeros((n, n, n, P3, 9))
+        Wc = W[lev + 1]
+        for c in itertools.product((0, 1), repeat=3):
+            ch = Wc[c[0]::2, c[1]::2, c[2]::2].reshape(n, n, n, p, p, p, 9)
+            Wp += np.einsum("Aa,Bb,Cc,xyzabcw->xyzABCw", M[c[0]], M[c[1]], M[c[2]], ch).reshape(
+                n, n, n, P3, 9)
+        W[lev] = Wp
+    # (2) M2L at every level >= 2, pairs grouped by offset
+    S = {}
+    for lev in range(2, lf + 1):
+        n = 1 << lev
+        h = H / n
+        S[lev] = np.zeros((n, n, n, P3, 6))
+        occ = np.zeros((n, n, n), dtype=bool)
+        c = cell_of(ys, origin, H, lev)
+        occ[c[:, 0], c[:, 1], c[:, 2]] = True
+        tocc = np.zeros((n, n, n), dtype=bool)
+        c = cell_of(xt, origin, H, lev)
+        tocc[c[:, 0], c[:, 1], c[:, 2]] = True
+        groups = {}
+        for B in itertools.product(range(n), repeat=3):
+            if not tocc[B]:
+                continue  # no target below B: its local values are never used
+            for o in interaction_offsets(B):
+                A = tuple(B[d] - o[d] for d in range(3))
+                if all(0 <= A[d] < n for d in range(3)) and occ[A]:
+                    groups.setdefault(o, []).append((B, A))
+        for o, pairs in groups.items():
+            Ws = np.stack([W[lev][A] for _, A in pairs])
+            res = _apply_offset(mat, p, h, o, Ws)
+            for (B, _), r in zip(pairs, res):
+                S[lev][B] += r
+    # (3.a) L2L down the tree
+    for lev in range(3, lf + 1):
+        n = 1 << (lev - 1)
+        Sp = S[lev - 1].reshape(n, n, n, p, p, p, 6)
+        for c in itertools.product((0, 1), repeat=3):
+            add = np.einsum("Aa,Bb,Cc,xyzABCs->xyzabcs", M[c[0]], M[c[1]], M[c[2]], Sp)
+            S[lev][c[0]::2, c[1]::2, c[2]::2] += add.reshape(n, n, n, P3, 6)
+    # (3.b) L2P + near field
+    tl = cell_of(xt, origin, H, lf)
+    out = np.zeros((len(xt), 6))
+    if lf >= 2:
+        tt = (xt - (origin + tl * hL)) / hL
+        out += np.einsum("nl,nls->ns", basis_3d(tt, p), S[lf][tl[:, 0], tl[:, 1], tl[:, 2]])
+    out += _near(mat, xt, np.asarray(tseg), tl, ys, qs, np.asarray(sseg), sl, nL)
+    return out
+
+
+def pairwise_far_field(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
+    """Far field of the same tree by Algorithm 1 applied to each (B, A) pair
+    with A in I(B), at each level >= 2 (anterpolate from A's points, node
+    kernel, interpolate to B's points).  Near sum included."""
+    ys = np.asarray(ys, dtype=np.float64)
+    qs = np.asarray(qs, dtype=np.float64).reshape(-1, 9)
+    if xt is None:
+        xt, tseg = ys, sseg
+    origin, H = root_box(ys)
+    lf = L - 1
+    out = np.zeros((len(xt), 6))
+    for lev in range(2, lf + 1):
+        n = 1 << lev
+        h = H / n
+        sc = cell_of(ys, origin, H, lev)
+        tc = cell_of(xt, origin, H, lev)
+        for B in {tuple(r) for r in tc}:
+            ti = np.nonzero((tc == B).all(axis=1))[0]
+            LB = basis_3d((xt[ti] - (origin + np.asarray(B) * h)) / h, p)
+            for o in interaction_offsets(B):
+                A = tuple(B[d] - o[d] for d in range(3))
+                sj = np.nonzero((sc == A).all(axis=1))[0]
+                if len(sj) == 0:
+                    continue
+                LA = basis_3d((ys[sj] - (origin + np.asarray(A) * h)) / h, p)
+                Wm = LA.T @ qs[sj]                                   # step 1
+                sl = _apply_offset(mat, p, h, o, Wm[None])[0]        # step 2
+                out[ti] += LB @ sl                                    # step 3
+    nL = 1 << lf
+    out += _near(mat, xt, np.asarray(tseg), cell_of(xt, origin, H, lf), ys, qs,
+                 np.asarray(sseg), cell_of(ys, origin, H, lf), nL)
+    return out
