@@ -1,0 +1,298 @@
+"""Benchmark: Lagrange-FMM segment nodal forces per second on one GB300.
+
+A step is one pass of the whole hot path over one synthetic network:
+Gauss points + tree build (fmm_build_tree) and the FMM evaluation of
+Peach-Koehler nodal forces (fmm_eval_nodal_forces: P2M, M2M, M2L, L2L,
+L2P + near field, forces).  The M2L operators (per medium and order) are
+built once before timing, as the method prescribes (they do not depend on
+the configuration).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...     # the FP64 CPU oracle, sampled
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1712_07739_gb300 import synth  # noqa: E402
+
+METRIC = "FMM segment nodal forces/sec at 1e-4 rel err: mixed+learned vs plain FP64, 1 GB300"
+UNIT = "segments/s"
+
+# per-pair arithmetic of the near field (counted from the kernel source):
+# separation 3, |d|^2 5, rsqrt 1, direction 3, h (18 components) ~100,
+# contraction with the 6x18 source tensor 216, 1/R^2 scaling and accumulate 13
+FLOP_PER_NEAR_PAIR = {"iso": 341}
+FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 (nominal, profiling recipe table)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+WORKLOADS = {
+    "c1": dict(
+        desc="2,000 segments (50 hexagonal glide loops x 40), isotropic mu=1 nu=0.3, order p=4, 3-level octree, "
+             "4 Gauss points/segment, FP64 plain",
+        gen=lambda seed: synth.hexagon_loops(seed=seed), C=lambda: synth.isotropic_voigt(1.0, 0.3),
+        h_mode="iso", p=4, levels=3, precision="fp64"),
+}
+DEFAULT_WORKLOAD = "c1"
+
+
+def _rank_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def oracle_sample_rate(wl, nodes, segs, b, budget_s, nthreads=0):
+    """FP64 oracle direct sum on a bounded sample of segments; segments/s."""
+    import oracle
+
+    C6 = wl["C"]()
+    mat = oracle.Material.iso(1.0, 0.3) if wl["h_mode"] == "iso" else oracle.Material.aniso(C6, Q=64)
+    y, q, sid = oracle.quadrature(nodes, segs, b, 4)
+    rng = np.random.default_rng(123)
+    n = 1
+    used = 1
+    while True:
+        pick = rng.choice(len(segs), size=min(n, len(segs)), replace=False)
+        tgt = (pick[:, None] * 4 + np.arange(4)[None, :]).reshape(-1)
+        t0 = time.perf_counter()
+        sig, used = oracle.direct_stress(mat, y[tgt], sid[tgt], y, q, sid, nthreads, return_threads=True)
+        oracle.segment_forces(nodes, segs[pick], b[pick], sig, 4)
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or n >= len(segs):
+            return len(pick) / dt, used, len(pick), dt
+        n = min(len(segs), max(n * 2, int(n * budget_s / max(dt, 1e-3) * 0.9)))
+
+
+def run_reference(args, wl):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return
+    nodes, segs, b = wl["gen"](0)
+    per_step = max(2.0, 150.0 / (args.steps + args.warmup))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, used, nseg, dt = oracle_sample_rate(wl, nodes, segs, b, per_step)
+        if i >= args.warmup:
+            rates.append((r, used, nseg, dt))
+    segs_done = sum(x[2] for x in rates)
+    t_tot = sum(x[3] for x in rates)
+    value = segs_done / t_tot
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / len(rates),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": rates[0][1], "kind": "oracle",
+                         "sample": f"{rates[0][2]} randomly drawn segments per step (their Gauss points against "
+                                   f"all {len(segs) * 4} source points), FP64 direct Mura sum"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def run_ours(args, wl):
+    import torch
+
+    import paper_1712_07739_gb300 as gb
+
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    nodes, segs, b = wl["gen"](rank)  # weak scaling: each rank its own configuration
+    n_segs = len(segs)
+    d_nodes = torch.tensor(nodes, device=dev)
+    d_segs = torch.tensor(segs, device=dev)
+    d_b = torch.tensor(b, device=dev)
+    f = gb.FMM(p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"])
+    f.set_material(wl["C"]())
+    out = torch.empty((len(nodes), 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        f.build(d_nodes, d_segs, d_b)
+        f.nodal_forces(out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = f.tree_info()
+    work = f.work_counts()
+    f.set_timing(True)
+    launches0 = f.launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+        stage.append(f.stage_times())
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = f.launch_count() - launches0
+    step_ms = [a.elapsed_time(b_) for a, b_ in evs]
+    t_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * n_segs * args.steps / (t_ms / 1e3)
+
+    # end to end through the public API: pinned host inputs in, forces out
+    h_nodes = torch.tensor(nodes).pin_memory()
+    h_segs = torch.tensor(segs).pin_memory()
+    h_b = torch.tensor(b).pin_memory()
+    h_out = torch.empty((len(nodes), 3), dtype=torch.float64).pin_memory()
+    f.set_timing(False)
+    e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_nodes.copy_(h_nodes, non_blocking=True)
+        d_segs.copy_(h_segs, non_blocking=True)
+        d_b.copy_(h_b, non_blocking=True)
+        step()
+        h_out.copy_(out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e_ms.append(e0.elapsed_time(e1))
+    e2e = world * n_segs * len(e_ms) / (sum(e_ms) / 1e3)
+    h2d = h_nodes.numel() * 8 + h_segs.numel() * 8 + h_b.numel() * 8
+    d2h = h_out.numel() * 8
+
+    # roofline of the dominant kernel (stage times are CUDA events around it)
+    st = np.array(stage)            # [steps, 8]: precontract, P2M+M2M, M2L, L2L, L2P+P2P, forces
+    m2l_ms, leaf_ms = st[:, 2].mean(), st[:, 4].mean()
+    p = wl["p"]
+    fp64 = wl["precision"] == "fp64"
+    peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+    if leaf_ms >= m2l_ms:
+        flops = work["near_pairs"] * FLOP_PER_NEAR_PAIR[wl["h_mode"]] + work["points"] * (12 * p ** 3 + 30 * p)
+        achieved = flops / (leaf_ms / 1e3) / 1e12
+        dom = "k_leaf_eval_f64 (L2P + near-field P2P)"
+    else:
+        flops = work["m2l_pairs"] * 2 * 54 * p ** 6
+        achieved = flops / (m2l_ms / 1e3) / 1e12
+        dom = "k_m2l_f64 (M2L)"
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "FP64 1.25 TFLOP/s nominal (recipe)" if fp64 else "152 SM x 128 lanes x 2 x 2.07 GHz"}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            r, used, nseg, dt = oracle_sample_rate(wl, nodes, segs, b, 15.0)
+            cpu = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle",
+                   "sample": f"{nseg} randomly drawn segments (their Gauss points against all {len(segs) * 4} "
+                             f"source points), FP64 direct Mura sum, {dt:.1f} s"}
+        res = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32/bf16",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "n_segs": n_segs, "levels": info["levels"],
+                       "p": p, "precision": wl["precision"], "h_mode": wl["h_mode"],
+                       "l2": "flushed: 256 MiB write between steps, outside the step events",
+                       "step": "fmm_build_tree + fmm_eval_nodal_forces"},
+            "stage_ms": {"precontract": st[:, 0].mean(), "p2m_m2m": st[:, 1].mean(), "m2l": m2l_ms,
+                         "l2l": st[:, 3].mean(), "l2p_p2p": leaf_ms, "forces": st[:, 5].mean()},
+            "work": work, "wall_s": wall,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk, "roofline": roofline, "cpu_baseline": cpu,
+        }
+        print(json.dumps(res, default=float))
+    f.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

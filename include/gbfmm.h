@@ -1,0 +1,169 @@
+/*
+ * gbfmm -- Lagrange fast multipole method for the stress field and
+ * Peach-Koehler forces of straight dislocation segments, on one GPU.
+ *
+ * Method: Chen, Aubry, Oppelstrup, Arsenlis, Darve, "Fast algorithms for
+ * evaluating the stress field of dislocation lines in anisotropic elastic
+ * media" (arXiv:1712.07739).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every pointer argument marked "device" is a CUDA device pointer owned by
+ *   the caller; the library never frees it and never copies it to the host.
+ *   Pointers marked "host" are read during the call only.
+ * - All device work is issued, in order, on the CUDA stream given to
+ *   fmm_create (the legacy default stream if NULL).  Entry points return as
+ *   soon as the work is queued, except where a comment says they
+ *   synchronise.  Results are valid once that stream reaches the call.
+ * - Return value: GBFMM_OK (0) or a negative GBFMM_ERR_* code; the context
+ *   keeps a message for the last error (fmm_last_error).  On an error the
+ *   outputs of that call are undefined and the context stays usable.
+ * - Stress is stored in Voigt order xx, yy, zz, yz, xz, xy (6 doubles per
+ *   point); vectors are xyz triples; all arrays are row-major and densely
+ *   packed.
+ * - The library owns its workspaces (tree, multipole and local values, the
+ *   M2L operator tables), allocated by fmm_set_material and fmm_build_tree
+ *   and released by fmm_destroy.  fmm_eval_nodal_forces allocates nothing;
+ *   fmm_eval_stress grows a target buffer when n_t exceeds every earlier
+ *   call's.
+ */
+#ifndef GBFMM_H
+#define GBFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define GBFMM_OK 0
+#define GBFMM_ERR_INVALID_ARG -1   /* a size, pointer or option is out of range */
+#define GBFMM_ERR_NOT_BUILT -2     /* fmm_eval_* before fmm_build_tree */
+#define GBFMM_ERR_NO_MATERIAL -3   /* fmm_build_tree / fmm_eval_* before fmm_set_material */
+#define GBFMM_ERR_CUDA -4          /* a CUDA runtime call failed (message has the name) */
+#define GBFMM_ERR_TIMEOUT -5       /* a bounded device wait gave up */
+#define GBFMM_ERR_DEGENERATE -6    /* zero-length segment or non-positive-definite medium */
+
+/* precision of the pass */
+#define GBFMM_FP64 0   /* every stage in FP64 */
+#define GBFMM_MIXED 1  /* FP32 P2M/M2M/L2L/L2P and near field (FP64 for close pairs),
+                          M2L on tcgen05 tensor cores (BF16 with split correction) */
+
+/* how the Green's-function factor h_vpq(T) = R^2 dG_vp/dx_q is evaluated */
+#define GBFMM_H_ISO 0     /* closed form of the isotropic Green's function (Sec. 2, Eq. "k_iso") */
+#define GBFMM_H_CIRCLE 1  /* trapezoid rule of the unit-circle integral (any medium) */
+#define GBFMM_H_MLP 2     /* trained network (fmm_train_h), plain evaluator where flagged */
+
+typedef struct {
+    int p;                 /* Lagrange nodes per dimension, 2..8 (Sec. 4.1) */
+    int n_gauss;           /* Gauss points per segment, 1..16 (Sec. 2, Eq. "stress_discrete") */
+    int levels;            /* octree levels L >= 3, leaves at level L-1; 0 = choose from N_s */
+    int precision;         /* GBFMM_FP64 or GBFMM_MIXED */
+    int h_mode;            /* GBFMM_H_ISO, GBFMM_H_CIRCLE or GBFMM_H_MLP */
+    int circle_q;          /* trapezoid points on the half circle for GBFMM_H_CIRCLE; 0 = 64 */
+    int leaf_segments;     /* with levels == 0: target mean segments per occupied leaf; 0 = 32 */
+    double near_fp64;      /* MIXED: near pairs closer than near_fp64 x (source segment length)
+                              are evaluated in FP64; 0 = 2.0 */
+} gbfmm_options;
+
+typedef struct gbfmm_ctx gbfmm_ctx;
+
+/* Fill *opt with defaults (p=4, n_gauss=4, levels=0, FP64, H_ISO). */
+void fmm_default_options(gbfmm_options *opt);
+
+/* Create a context.  opt: host, copied.  cuda_stream: a cudaStream_t or NULL.
+ * The current CUDA device at this call is the one the context uses. */
+int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *cuda_stream);
+
+/* Destroy a context and free its device memory (synchronises its stream). */
+void fmm_destroy(gbfmm_ctx *ctx);
+
+/* Message of the last error on this context ("" if none). */
+const char *fmm_last_error(const gbfmm_ctx *ctx);
+
+/* Set the elastic medium and precompute the M2L operators.
+ *
+ * C_voigt: host, 36 doubles, the 6x6 stiffness in Voigt order
+ * (11, 22, 33, 23, 13, 12), row-major; must be symmetric positive definite.
+ * With GBFMM_H_ISO the medium must be isotropic (C11 - C12 = 2 C44, cubic
+ * form); mu = C44 and nu = C12 / (2 (C12 + C44)) are taken from it.
+ *
+ * Builds, on the device, the kernel K_abwr = A_{ab,wr,vpq} h_vpq / R^2 of
+ * Sec. 2, Eq. "kernel" at every node difference of every M2L offset (the
+ * operators T_{A->B} of Sec. 4.1, Eq. "m2l"; they depend only on the medium
+ * and p, Sec. 4.1) for cells of unit size; level l scales them by
+ * (2^l / H)^2 (homogeneity of degree -2, Sec. 4.1 footnote).
+ * Synchronises the stream.  Errors: INVALID_ARG, DEGENERATE, CUDA. */
+int fmm_set_material(gbfmm_ctx *ctx, const double *C_voigt);
+
+/* Build the octree of a segment network.
+ *
+ * node_xyz:  device, [n_nodes][3] double, node positions.
+ * seg_nodes: device, [n_segs][2] int64, node indices (line sense n0 -> n1).
+ * burgers:   device, [n_segs][3] double, Burgers vector per segment.
+ *
+ * Computes the Gauss points y and strengths q_wr = 1/2 b_w omega S_r of
+ * Sec. 2, Eq. "stress_discrete", the root cube (edge H = s (1 + 2^-10), s the
+ * largest extent of the Gauss points, centred on their bounding box), bins
+ * every point into its leaf and sorts points by leaf.  The context keeps
+ * the three pointers: fmm_eval_nodal_forces reads them again, so they must
+ * stay valid and unchanged until the next fmm_build_tree or fmm_destroy.
+ * Synchronises the stream (reads back the bounding box).
+ * Errors: INVALID_ARG (n_segs < 1, n_nodes < 2, null pointer), CUDA. */
+int fmm_build_tree(gbfmm_ctx *ctx, int64_t n_nodes, const double *node_xyz,
+                   int64_t n_segs, const int64_t *seg_nodes, const double *burgers);
+
+/* Stress at arbitrary points (Sec. 2, Eq. "stress3" by Algorithm 2).
+ *
+ * x:     device, [n_t][3] double target positions.  Targets outside the root
+ *        cube are assigned to the nearest boundary leaf.
+ * sigma: device, [n_t][6] double, output (Voigt).
+ * Every source point contributes (no self exclusion: targets are free
+ * points).  Errors: NOT_BUILT, NO_MATERIAL, INVALID_ARG, CUDA. */
+int fmm_eval_stress(gbfmm_ctx *ctx, int64_t n_t, const double *x, double *sigma);
+
+/* Peach-Koehler nodal forces of the built network (Sec. 2 and Sec. 1).
+ *
+ * The stress is evaluated at every Gauss point, leaving out the point's own
+ * segment; the force per unit length (sigma . b) x xi is integrated against
+ * the linear shape functions of the segment ends with the same Gauss rule:
+ *   f1 = sum_k (omega_k/2) (1 - xi_k)/2 (sigma_k b) x S,
+ *   f2 = sum_k (omega_k/2) (1 + xi_k)/2 (sigma_k b) x S.
+ * f_nodes: device, [n_nodes][3] double, output: sum of the end forces of
+ *          the segments incident to each node (overwritten).
+ * f_seg:   device, [n_segs][2][3] double (f1, f2 per segment) or NULL.
+ * sigma_pts: device, [n_segs * n_gauss][6] double (stress at each Gauss point,
+ *          segment-major) or NULL.
+ * Errors: NOT_BUILT, NO_MATERIAL, CUDA. */
+int fmm_eval_nodal_forces(gbfmm_ctx *ctx, double *f_nodes, double *f_seg, double *sigma_pts);
+
+/* Level count, leaf count and number of Gauss points of the built tree
+ * (host outputs; any may be NULL). */
+int fmm_tree_info(const gbfmm_ctx *ctx, int *levels, int64_t *n_leaves, int64_t *n_points);
+
+/* Device time in milliseconds of each stage of the last fmm_eval_* call,
+ * measured with CUDA events on the context stream: [0] precompute
+ * source tensors, [1] P2M+M2M, [2] M2L, [3] L2L, [4] L2P+P2P, [5] forces.
+ * Only filled when timing was enabled with fmm_set_timing(ctx, 1); the
+ * call then synchronises the stream.  times: host, 8 doubles. */
+int fmm_set_timing(gbfmm_ctx *ctx, int enable);
+int fmm_stage_times(const gbfmm_ctx *ctx, double *times);
+
+/* Number of CUDA kernels this context has launched since fmm_create
+ * (host output). */
+int fmm_launch_count(const gbfmm_ctx *ctx, int64_t *count);
+
+/* Work of one pass over the built tree, for roofline accounting
+ * (host output, 4 int64): [0] near-field point pairs evaluated by the
+ * self-evaluation of fmm_eval_nodal_forces (target x source point pairs in
+ * neighbouring leaves, own-segment pairs excluded), [1] M2L cell pairs
+ * (target cell, interaction-list cell) with both non-empty, [2] occupied
+ * leaves, [3] Gauss points.  Launches two small kernels and synchronises.
+ * Errors: NOT_BUILT, CUDA. */
+int fmm_work_counts(gbfmm_ctx *ctx, int64_t *counts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,195 @@
+"""gbfmm: Lagrange FMM for dislocation stresses and Peach-Koehler forces on GB300.
+
+Thin ctypes binding over the C ABI declared in ``include/gbfmm.h``.  Every
+step of the pass runs in the library's CUDA kernels; this module only
+marshals torch CUDA tensors (for device memory) and the current torch CUDA
+stream.  Importing it does not need a GPU; constructing ``FMM`` loads the
+compiled library and raises if it is missing -- there is no CPU fallback.
+
+Method: Chen, Aubry, Oppelstrup, Arsenlis, Darve, arXiv:1712.07739
+(Sec. 2 for the stress formula and kernel, Sec. 4 / Algorithm 2 for the pass).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgbfmm.so")
+
+FP64, MIXED = 0, 1
+H_ISO, H_CIRCLE, H_MLP = 0, 1, 2
+_PREC = {"fp64": FP64, "mixed": MIXED}
+_HMODE = {"iso": H_ISO, "circle": H_CIRCLE, "mlp": H_MLP}
+
+# exported names the header declares (checked by the CPU test suite)
+EXPORTS = [
+    "fmm_default_options", "fmm_create", "fmm_destroy", "fmm_last_error",
+    "fmm_set_material", "fmm_build_tree", "fmm_eval_stress", "fmm_eval_nodal_forces",
+    "fmm_tree_info", "fmm_set_timing", "fmm_stage_times", "fmm_launch_count", "fmm_work_counts",
+]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("p", ctypes.c_int), ("n_gauss", ctypes.c_int), ("levels", ctypes.c_int),
+        ("precision", ctypes.c_int), ("h_mode", ctypes.c_int), ("circle_q", ctypes.c_int),
+        ("leaf_segments", ctypes.c_int), ("near_fp64", ctypes.c_double),
+    ]
+
+
+class GbfmmError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgbfmm.so (built by ``build.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise GbfmmError(f"CUDA library not built: {path} (run paper_1712_07739_gb300.build.build())")
+    L = ctypes.CDLL(path)
+    vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p
+    L.fmm_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.fmm_default_options.restype = None
+    L.fmm_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Options), vp]
+    L.fmm_destroy.argtypes = [vp]
+    L.fmm_destroy.restype = None
+    L.fmm_last_error.argtypes = [vp]
+    L.fmm_last_error.restype = ctypes.c_char_p
+    L.fmm_set_material.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.fmm_build_tree.argtypes = [vp, i64, dp, i64, dp, dp]
+    L.fmm_eval_stress.argtypes = [vp, i64, dp, dp]
+    L.fmm_eval_nodal_forces.argtypes = [vp, dp, dp, dp]
+    L.fmm_tree_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.fmm_set_timing.argtypes = [vp, ctypes.c_int]
+    L.fmm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.fmm_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+    L.fmm_work_counts.argtypes = [vp, ctypes.POINTER(i64)]
+    for name in ("fmm_launch_count", "fmm_work_counts", "fmm_create", "fmm_set_material", "fmm_build_tree", "fmm_eval_stress",
+                 "fmm_eval_nodal_forces", "fmm_tree_info", "fmm_set_timing", "fmm_stage_times"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class FMM:
+    """One Lagrange-FMM context on the current CUDA device and stream.
+
+    ``FMM(p=4).set_material(C).build(nodes, segs, b).nodal_forces()``; inputs
+    are torch CUDA tensors: nodes float64 [n, 3], segs int64 [m, 2],
+    burgers float64 [m, 3].  The context keeps references to them.
+    """
+
+    def __init__(self, p=4, n_gauss=4, levels=0, precision="fp64", h_mode="iso", circle_q=0,
+                 leaf_segments=0, near_fp64=0.0, stream=None):
+        import torch
+
+        self._torch = torch
+        self._lib = load_library()
+        o = Options()
+        self._lib.fmm_default_options(ctypes.byref(o))
+        o.p, o.n_gauss, o.levels = p, n_gauss, levels
+        o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        o.h_mode = _HMODE[h_mode] if isinstance(h_mode, str) else int(h_mode)
+        o.circle_q, o.leaf_segments, o.near_fp64 = circle_q, leaf_segments, near_fp64
+        self.options = o
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self._lib.fmm_create(ctypes.byref(h), ctypes.byref(o), ctypes.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise GbfmmError(f"fmm_create failed ({rc})")
+        self._h = h
+        self._keep = ()
+        self.n_nodes = self.n_segs = 0
+
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = self._lib.fmm_last_error(self._h).decode()
+            raise GbfmmError(f"{what} failed ({rc}): {msg}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_material(self, C_voigt):
+        C = np.ascontiguousarray(np.asarray(C_voigt, dtype=np.float64).reshape(36))
+        self._check(self._lib.fmm_set_material(self._h, C.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                    "fmm_set_material")
+        return self
+
+    def build(self, nodes, segs, burgers):
+        t = self._torch
+        nodes = nodes.to(dtype=t.float64).contiguous()
+        segs = segs.to(dtype=t.int64).contiguous()
+        burgers = burgers.to(dtype=t.float64).contiguous()
+        for x in (nodes, segs, burgers):
+            if not x.is_cuda:
+                raise GbfmmError("build: inputs must be CUDA tensors")
+        self._keep = (nodes, segs, burgers)
+        self.n_nodes, self.n_segs = nodes.shape[0], segs.shape[0]
+        self._check(self._lib.fmm_build_tree(self._h, nodes.shape[0], _ptr(nodes), segs.shape[0], _ptr(segs),
+                                             _ptr(burgers)), "fmm_build_tree")
+        return self
+
+    def nodal_forces(self, out=None, f_seg=None, sigma_pts=None):
+        t = self._torch
+        if out is None:
+            dev = self._keep[0].device if self._keep else t.device("cuda", t.cuda.current_device())
+            out = t.empty((max(self.n_nodes, 0), 3), dtype=t.float64, device=dev)
+        self._check(self._lib.fmm_eval_nodal_forces(self._h, _ptr(out), _ptr(f_seg), _ptr(sigma_pts)),
+                    "fmm_eval_nodal_forces")
+        return out
+
+    def stress(self, x, out=None):
+        t = self._torch
+        x = x.to(dtype=t.float64).contiguous()
+        if out is None:
+            out = t.empty((x.shape[0], 6), dtype=t.float64, device=x.device)
+        self._check(self._lib.fmm_eval_stress(self._h, x.shape[0], _ptr(x), _ptr(out)), "fmm_eval_stress")
+        return out
+
+    def tree_info(self):
+        lv, nl, npt = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.fmm_tree_info(self._h, ctypes.byref(lv), ctypes.byref(nl), ctypes.byref(npt)),
+                    "fmm_tree_info")
+        return {"levels": lv.value, "n_leaves": nl.value, "n_points": npt.value}
+
+    def launch_count(self):
+        c = ctypes.c_int64()
+        self._check(self._lib.fmm_launch_count(self._h, ctypes.byref(c)), "fmm_launch_count")
+        return c.value
+
+    def work_counts(self):
+        """near point pairs, M2L cell pairs, occupied leaves, points (synchronises)."""
+        a = (ctypes.c_int64 * 4)()
+        self._check(self._lib.fmm_work_counts(self._h, a), "fmm_work_counts")
+        return {"near_pairs": a[0], "m2l_pairs": a[1], "occupied_leaves": a[2], "points": a[3]}
+
+    def set_timing(self, on=True):
+        self._check(self._lib.fmm_set_timing(self._h, int(bool(on))), "fmm_set_timing")
+        return self
+
+    def stage_times(self):
+        a = (ctypes.c_double * 8)()
+        self._check(self._lib.fmm_stage_times(self._h, a), "fmm_stage_times")
+        return list(a)

@@ -1,0 +1,297 @@
+// C ABI of the library: context life cycle, tree build and evaluation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.cuh"
+
+int fmm_kernel_attrs(gbfmm_ctx *ctx);  // fmm.cu
+int mixed_alloc(gbfmm_ctx *ctx);       // mixed.cu
+int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t);
+
+int set_err(gbfmm_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+template <typename T>
+static void release(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+static void free_tree(gbfmm_ctx *ctx) {
+    release(ctx->d_y);
+    release(ctx->d_q);
+    release(ctx->d_sid);
+    release(ctx->d_slen);
+    release(ctx->d_pos);
+    release(ctx->d_pleaf);
+    release(ctx->d_sig);
+    release(ctx->d_P);
+    release(ctx->d_Pf);
+    release(ctx->d_y0);
+    release(ctx->d_q0);
+    release(ctx->d_leaf_of);
+    release(ctx->d_perm);
+    release(ctx->d_len0);
+    release(ctx->d_W);
+    release(ctx->d_S);
+    release(ctx->d_Wf);
+    release(ctx->d_Sf);
+    release(ctx->d_tmp_i);
+    release(ctx->d_leaf_start);
+    release(ctx->d_t_start);
+    release(ctx->d_cnt);
+    release(ctx->d_cursor);
+    release(ctx->d_tmp_d);
+    release(ctx->d_part);
+    release(ctx->d_bad);
+    release(ctx->d_yrel);
+    ctx->mx_cap_N = ctx->mx_cap_cells = 0;
+    ctx->cap_N = ctx->cap_segs = ctx->cap_cells = ctx->cap_leaves = 0;
+    ctx->built = false;
+}
+
+// (Re)allocate the tree buffers only when a size exceeds its capacity, so a
+// repeated build of a same-size network allocates nothing.
+static int ensure_tree_buffers(gbfmm_ctx *ctx) {
+    const int64_t N = ctx->N, ns = ctx->n_segs, nc = ctx->n_cells, nl = ctx->n_leaves;
+    const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p;
+    const bool fp64 = ctx->opt.precision == GBFMM_FP64;
+    if (N > ctx->cap_N) {
+        release(ctx->d_y); release(ctx->d_q); release(ctx->d_sid); release(ctx->d_slen); release(ctx->d_pos);
+        release(ctx->d_pleaf); release(ctx->d_sig); release(ctx->d_y0); release(ctx->d_q0);
+        if (fp64) release(ctx->d_P);
+        release(ctx->d_leaf_of); release(ctx->d_perm);
+        CK(cudaMalloc(&ctx->d_y, N * 3 * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_q, N * 9 * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_sid, N * sizeof(int64_t)));
+        CK(cudaMalloc(&ctx->d_slen, N * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_pos, N * sizeof(int)));
+        CK(cudaMalloc(&ctx->d_pleaf, N * sizeof(int)));
+        CK(cudaMalloc(&ctx->d_sig, N * 6 * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_y0, N * 3 * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_q0, N * 9 * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_leaf_of, N * sizeof(int)));
+        CK(cudaMalloc(&ctx->d_perm, N * sizeof(int)));
+        if (fp64) CK(cudaMalloc(&ctx->d_P, N * 108 * sizeof(double)));
+        ctx->cap_N = N;
+    }
+    if (ns > ctx->cap_segs) {
+        release(ctx->d_len0);
+        CK(cudaMalloc(&ctx->d_len0, ns * sizeof(double)));
+        ctx->cap_segs = ns;
+    }
+    if (nc > ctx->cap_cells) {
+        release(ctx->d_W); release(ctx->d_S); release(ctx->d_tmp_i);
+        CK(cudaMalloc(&ctx->d_tmp_i, 2 * nc * sizeof(int)));
+        if (fp64) {
+            CK(cudaMalloc(&ctx->d_W, nc * P3 * 9 * sizeof(double)));
+            CK(cudaMalloc(&ctx->d_S, nc * P3 * 6 * sizeof(double)));
+        }
+        ctx->cap_cells = nc;
+    }
+    if (nl > ctx->cap_leaves) {
+        release(ctx->d_leaf_start); release(ctx->d_t_start); release(ctx->d_cnt); release(ctx->d_cursor);
+        CK(cudaMalloc(&ctx->d_leaf_start, (nl + 1) * sizeof(int)));
+        CK(cudaMalloc(&ctx->d_t_start, (nl + 1) * sizeof(int)));
+        CK(cudaMalloc(&ctx->d_cnt, nl * sizeof(int)));
+        CK(cudaMalloc(&ctx->d_cursor, nl * sizeof(int)));
+        ctx->cap_leaves = nl;
+    }
+    if (!ctx->d_part) CK(cudaMalloc(&ctx->d_part, 512 * 6 * sizeof(double)));
+    if (!ctx->d_bad) CK(cudaMalloc(&ctx->d_bad, sizeof(int)));
+    return GBFMM_OK;
+}
+
+extern "C" void fmm_default_options(gbfmm_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->p = 4;
+    o->n_gauss = 4;
+    o->levels = 0;
+    o->precision = GBFMM_FP64;
+    o->h_mode = GBFMM_H_ISO;
+    o->circle_q = 0;
+    o->leaf_segments = 0;
+    o->near_fp64 = 0.0;
+}
+
+extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *stream) {
+    if (!out || !opt) return GBFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (opt->p < 2 || opt->p > GB_MAXP || opt->n_gauss < 1 || opt->n_gauss > GB_MAXG ||
+        (opt->levels != 0 && (opt->levels < 3 || opt->levels > 9)) ||
+        (opt->precision != GBFMM_FP64 && opt->precision != GBFMM_MIXED) || opt->h_mode < 0 || opt->h_mode > 2 ||
+        opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0))
+        return GBFMM_ERR_INVALID_ARG;
+    gbfmm_ctx *ctx = new gbfmm_ctx();
+    ctx->opt = *opt;
+    if (ctx->opt.near_fp64 == 0.0) ctx->opt.near_fp64 = 2.0;
+    if (ctx->opt.leaf_segments == 0) ctx->opt.leaf_segments = 32;
+    ctx->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        delete ctx;
+        return GBFMM_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (cudaMalloc(&ctx->d_box, sizeof(TreeBox)) != cudaSuccess) {
+        delete ctx;
+        return GBFMM_ERR_CUDA;
+    }
+    if (fmm_kernel_attrs(ctx) != GBFMM_OK) {
+        cudaFree(ctx->d_box);
+        delete ctx;
+        return GBFMM_ERR_CUDA;
+    }
+    *out = ctx;
+    return GBFMM_OK;
+}
+
+extern "C" void fmm_destroy(gbfmm_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free_tree(ctx);
+    void *ps[] = {ctx->d_box, ctx->d_mat, ctx->d_Asym, ctx->d_Asym_f, ctx->d_Klat,
+                  ctx->d_t_pos, ctx->d_t_x, ctx->d_t_sig, ctx->d_t_tmp};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    m2l_tc_free(ctx);
+    if (ctx->timer.on)
+        for (auto &e : ctx->timer.ev) cudaEventDestroy(e);
+    delete ctx;
+}
+
+extern "C" const char *fmm_last_error(const gbfmm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static int choose_levels(const gbfmm_ctx *ctx, int64_t n_segs) {
+    if (ctx->opt.levels) return ctx->opt.levels;
+    double leaves = double(n_segs) / double(ctx->opt.leaf_segments);
+    int lf = int(std::lround(std::log(std::max(leaves, 1.0)) / std::log(8.0)));
+    lf = std::max(2, std::min(7, lf));
+    return lf + 1;
+}
+
+extern "C" int fmm_build_tree(gbfmm_ctx *ctx, int64_t n_nodes, const double *node_xyz, int64_t n_segs,
+                              const int64_t *seg_nodes, const double *burgers) {
+    if (!ctx) return GBFMM_ERR_INVALID_ARG;
+    if (n_segs < 1 || n_nodes < 2 || !node_xyz || !seg_nodes || !burgers)
+        return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_build_tree: empty network or null pointer");
+    const int64_t N = n_segs * ctx->opt.n_gauss;
+    if (N >= (int64_t(1) << 31)) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_build_tree: too many points");
+    ctx->built = false;
+    ctx->n_nodes = n_nodes;
+    ctx->n_segs = n_segs;
+    ctx->N = N;
+    ctx->node_xyz = node_xyz;
+    ctx->seg_nodes = seg_nodes;
+    ctx->burgers = burgers;
+    ctx->L = choose_levels(ctx, n_segs);
+    const int L = ctx->L;
+    ctx->n_leaves = int64_t(1) << (3 * (L - 1));
+    ctx->n_cells = cell_base(L);
+    int rc = ensure_tree_buffers(ctx);
+    if (rc) return rc;
+    rc = tree_build(ctx);
+    if (rc) return rc;
+    if (ctx->opt.precision == GBFMM_MIXED) {
+        rc = mixed_alloc(ctx);
+        if (rc) return rc;
+    }
+    ctx->built = true;
+    return GBFMM_OK;
+}
+
+static int begin_eval(gbfmm_ctx *ctx) {
+    if (!ctx->have_material) return set_err(ctx, GBFMM_ERR_NO_MATERIAL, "fmm_eval: call fmm_set_material first");
+    if (!ctx->built) return set_err(ctx, GBFMM_ERR_NOT_BUILT, "fmm_eval: call fmm_build_tree first");
+    ctx->timer.n = 0;
+    return GBFMM_OK;
+}
+
+static int end_eval(gbfmm_ctx *ctx) {
+    if (!ctx->timer.on) return GBFMM_OK;
+    CK(cudaEventSynchronize(ctx->timer.ev[ctx->timer.n - 1]));
+    for (int i = 0; i < 8; ++i) ctx->stage_ms[i] = 0.0;
+    for (int i = 0; i + 1 < ctx->timer.n && i < 8; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->timer.ev[i], ctx->timer.ev[i + 1]);
+        ctx->stage_ms[i] = ms;
+    }
+    return GBFMM_OK;
+}
+
+static int run_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
+    if (ctx->opt.precision == GBFMM_MIXED) return mixed_pass(ctx, free_targets, n_t);
+    return fmm_pass(ctx, free_targets, n_t);
+}
+
+extern "C" int fmm_eval_stress(gbfmm_ctx *ctx, int64_t n_t, const double *x, double *sigma) {
+    if (!ctx) return GBFMM_ERR_INVALID_ARG;
+    int rc = begin_eval(ctx);
+    if (rc) return rc;
+    if (n_t < 0 || (n_t > 0 && (!x || !sigma)) || n_t >= (int64_t(1) << 31))
+        return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_eval_stress: bad target array");
+    if (n_t == 0) return GBFMM_OK;
+    rc = targets_sort(ctx, n_t, x);
+    if (rc) return rc;
+    rc = run_pass(ctx, true, n_t);
+    if (rc) return rc;
+    rc = targets_scatter(ctx, n_t, sigma);
+    if (rc) return rc;
+    return end_eval(ctx);
+}
+
+extern "C" int fmm_eval_nodal_forces(gbfmm_ctx *ctx, double *f_nodes, double *f_seg, double *sigma_pts) {
+    if (!ctx) return GBFMM_ERR_INVALID_ARG;
+    int rc = begin_eval(ctx);
+    if (rc) return rc;
+    if (!f_nodes) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_eval_nodal_forces: null output");
+    rc = run_pass(ctx, false, ctx->N);
+    if (rc) return rc;
+    rc = forces_from_stress(ctx, f_nodes, f_seg, sigma_pts);
+    if (rc) return rc;
+    return end_eval(ctx);
+}
+
+extern "C" int fmm_tree_info(const gbfmm_ctx *ctx, int *levels, int64_t *n_leaves, int64_t *n_points) {
+    if (!ctx) return GBFMM_ERR_INVALID_ARG;
+    if (levels) *levels = ctx->L;
+    if (n_leaves) *n_leaves = ctx->n_leaves;
+    if (n_points) *n_points = ctx->N;
+    return GBFMM_OK;
+}
+
+extern "C" int fmm_set_timing(gbfmm_ctx *ctx, int enable) {
+    if (!ctx) return GBFMM_ERR_INVALID_ARG;
+    if (enable && !ctx->timer.on) {
+        for (auto &e : ctx->timer.ev) CK(cudaEventCreate(&e));
+        ctx->timer.on = true;
+    } else if (!enable && ctx->timer.on) {
+        for (auto &e : ctx->timer.ev) cudaEventDestroy(e);
+        ctx->timer.on = false;
+    }
+    return GBFMM_OK;
+}
+
+extern "C" int fmm_stage_times(const gbfmm_ctx *ctx, double *t) {
+    if (!ctx || !t) return GBFMM_ERR_INVALID_ARG;
+    for (int i = 0; i < 8; ++i) t[i] = ctx->stage_ms[i];
+    return GBFMM_OK;
+}
+
+extern "C" int fmm_launch_count(const gbfmm_ctx *ctx, int64_t *count) {
+    if (!ctx || !count) return GBFMM_ERR_INVALID_ARG;
+    *count = ctx->launches;
+    return GBFMM_OK;
+}
+
+int work_counts(gbfmm_ctx *ctx, int64_t *out);  // fmm.cu
+
+extern "C" int fmm_work_counts(gbfmm_ctx *ctx, int64_t *out) {
+    if (!ctx || !out) return GBFMM_ERR_INVALID_ARG;
+    if (!ctx->built) return set_err(ctx, GBFMM_ERR_NOT_BUILT, "fmm_work_counts: call fmm_build_tree first");
+    return work_counts(ctx, out);
+}

@@ -1,0 +1,137 @@
+// Internal declarations of the gbfmm CUDA library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gbfmm.h"
+#include "m2l_tc.cuh"
+
+#define GB_MAXP 8
+#define GB_MAXG 16
+
+// Stress components in Voigt order: (a, b) index pairs.
+// h_vpq is symmetric in (v, p); the 6 pairs below use the same order, so a
+// symmetric-pair index k = 3 * pair + q covers the 18 distinct components.
+__host__ __device__ inline int voigt_a(int i) { return i < 3 ? i : (i == 3 ? 1 : 0); }
+__host__ __device__ inline int voigt_b(int i) { return i < 3 ? i : (i == 5 ? 1 : 2); }
+
+// Material as the device kernels see it (copied by value into kernel args
+// through a device buffer).
+struct DevMaterial {
+    int mode;     // GBFMM_H_ISO / GBFMM_H_CIRCLE / GBFMM_H_MLP
+    int Q;        // half-circle trapezoid points
+    double hc;    // iso: 1 / (16 pi mu (1 - nu))
+    double ha;    // iso: 3 - 4 nu
+    double C[81]; // C_ijkl
+};
+
+// Geometry of the tree as kernels see it; the root box lives on the device
+// (written by the bounding-box kernel), everything else is host-known.
+struct TreeBox {
+    double origin[3];
+    double H;      // root cube edge
+    double lo[3], hi[3];
+};
+
+struct Timer {
+    cudaEvent_t ev[16];
+    bool on = false;
+    int n = 0;
+};
+
+struct gbfmm_ctx {
+    gbfmm_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    int sm_count = 0;
+
+    // material
+    bool have_material = false;
+    DevMaterial mat{};
+    DevMaterial *d_mat = nullptr;
+    double Asym[6 * 9 * 18];   // A contracted over the (v,p) symmetry: [ab][wr][k]
+    double *d_Asym = nullptr;
+    float *d_Asym_f = nullptr;
+    int lat_n = 0;             // lattice points per dimension, 8 (p-1) + 1
+    double *d_Klat = nullptr;  // [lat_n^3][54] kernel at unit-cell lattice differences
+
+    // mixed-precision M2L on tensor cores
+    TcPlan tc;
+
+    // tree
+    bool built = false;
+    int L = 0;                 // levels; leaves at level L-1
+    int64_t n_nodes = 0, n_segs = 0, N = 0;
+    int64_t n_cells = 0;       // all levels
+    int64_t n_leaves = 0;
+    TreeBox *d_box = nullptr;
+    double gauss_xi[GB_MAXG], gauss_w[GB_MAXG];
+    double *d_y = nullptr;     // [N][3] sorted by leaf
+    double *d_q = nullptr;     // [N][9]
+    int64_t *d_sid = nullptr;  // [N] segment of each sorted point
+    double *d_slen = nullptr;  // [N] length of that segment
+    int *d_pos = nullptr;      // [N] original point index -> sorted position
+    int *d_pleaf = nullptr;    // [N] leaf of each sorted point
+    int *d_leaf_start = nullptr;  // [n_leaves + 1]
+    int *d_tmp_i = nullptr;       // scratch ints, N + n_leaves + 1
+    double *d_tmp_d = nullptr;    // scratch doubles
+    // build scratch
+    double *d_y0 = nullptr, *d_q0 = nullptr, *d_len0 = nullptr, *d_part = nullptr;
+    int *d_leaf_of = nullptr, *d_cnt = nullptr, *d_cursor = nullptr, *d_perm = nullptr, *d_bad = nullptr;
+    // capacities (elements) of the buffers sized by N, segments, cells, leaves
+    int64_t cap_N = 0, cap_segs = 0, cap_cells = 0, cap_leaves = 0;
+    const int64_t *seg_nodes = nullptr;  // caller's arrays (kept for forces)
+    const double *burgers = nullptr;
+    const double *node_xyz = nullptr;
+
+    // per-eval buffers
+    double *d_P = nullptr;     // [N][108] precontracted source tensors (FP64)
+    float *d_Pf = nullptr;     // [N][108] FP32 copy for the mixed path
+    double *d_W = nullptr;     // [n_cells][p^3][9] multipole weights
+    double *d_S = nullptr;     // [n_cells][p^3][6] local values
+    float *d_Wf = nullptr;
+    float *d_Sf = nullptr;
+    double *d_sig = nullptr;   // [N][6] stress at sorted points
+    float4 *d_yrel = nullptr;  // [N] mixed: leaf-relative FP32 position, segment length
+    int64_t mx_cap_N = 0, mx_cap_cells = 0;
+
+    // free-target evaluation
+    int64_t t_cap = 0;
+    int *d_t_pos = nullptr;     // target -> sorted slot
+    int *d_t_start = nullptr;   // [n_leaves + 1]
+    double *d_t_x = nullptr;    // sorted targets
+    double *d_t_sig = nullptr;  // sorted results
+    int *d_t_tmp = nullptr;
+
+    int64_t launches = 0;      // kernels launched by this context so far
+    Timer timer;
+    double stage_ms[8] = {0};
+};
+
+// error helpers
+int set_err(gbfmm_ctx *c, int code, const std::string &msg);
+#define CK(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return set_err(ctx, GBFMM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// cell indexing: level l occupies [cell_base(l), cell_base(l) + 8^l),
+// linear index (z * n + y) * n + x with n = 2^l.
+inline int64_t cell_base(int l) { return ((int64_t(1) << (3 * l)) - 1) / 7; }
+__host__ __device__ inline int64_t cell_base_d(int l) { return ((int64_t(1) << (3 * l)) - 1) / 7; }
+
+// stages (implemented in the .cu files)
+int material_setup(gbfmm_ctx *ctx);                 // material.cu
+int tree_build(gbfmm_ctx *ctx);                     // tree.cu
+int fmm_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t);  // fmm.cu
+int forces_from_stress(gbfmm_ctx *ctx, double *f_nodes, double *f_seg, double *sigma_pts);
+int targets_sort(gbfmm_ctx *ctx, int64_t n_t, const double *x);
+int targets_scatter(gbfmm_ctx *ctx, int64_t n_t, double *sigma);
+void timer_mark(gbfmm_ctx *ctx);
+void compute_occ(gbfmm_ctx *ctx, const int *start, int *occ);

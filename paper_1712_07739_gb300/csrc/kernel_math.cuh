@@ -1,0 +1,124 @@
+// Device arithmetic of the dislocation kernel, shared by the setup and the
+// near-field kernels of this library.
+//
+// The kernel of Sec. 2, Eq. "kernel" is K_abwr = A_{ab,wr,vpq} dG_vp/dx_q
+// with dG_vp/dx_q = h_vpq(T) / R^2.  h is symmetric in (v, p), so only 18
+// components are kept, in the order k = 3 * pair + q with pairs
+// (0,0) (1,1) (2,2) (1,2) (0,2) (0,1).
+#pragma once
+#include "internal.cuh"
+
+// Isotropic medium: derivative of the Kelvin Green's function
+// G_vp = [(3 - 4 nu) delta_vp + T_v T_p] / (16 pi mu (1 - nu) R), which is
+// Sec. 2, Eq. "k_iso" with R,ii = 2/R and R,vp = (delta_vp - T_v T_p)/R:
+// h_vpq = hc [ -ha delta_vp T_q + delta_vq T_p + delta_pq T_v - 3 T_v T_p T_q ].
+template <typename R>
+__device__ __forceinline__ void h_iso_sym(R hc, R ha, const R T[3], R hs[18]) {
+    constexpr int PV[6] = {0, 1, 2, 1, 0, 0};
+    constexpr int PP[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+    for (int pr = 0; pr < 6; ++pr) {
+        const int v = PV[pr], p = PP[pr];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            R s = R(-3) * T[v] * T[p] * T[q];
+            if (v == p) s -= ha * T[q];
+            if (v == q) s += T[p];
+            if (p == q) s += T[v];
+            hs[3 * pr + q] = hc * s;
+        }
+    }
+}
+
+// (a b)_jk = a_i C_ijkl b_l
+template <typename R, typename CT>
+__device__ __forceinline__ void cmat(const CT *C, const R a[3], const R b[3], R M[9]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R s = 0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int l = 0; l < 3; ++l) s += a[i] * R(C[((i * 3 + j) * 3 + k) * 3 + l]) * b[l];
+            M[j * 3 + k] = s;
+        }
+}
+
+// Any medium: h_vpq(T) = 1/(8 pi^2) oint [ -T_q (zz)^-1_vp + z_q F_vp ] dphi
+// over the unit circle z . T = 0, F = (zz)^-1 [(zT) + (Tz)] (zz)^-1.
+// The integrand has period pi, so the loop is the Q-point trapezoid rule on
+// [0, pi) doubled.  C is read through the generic 81-entry tensor.
+template <typename R, typename CT>
+__device__ __forceinline__ void h_circle_sym(const CT *C, int Q, const R Tin[3], R hs[18]) {
+    R T[3] = {Tin[0], Tin[1], Tin[2]};
+    // e1: T with its smallest component replaced, orthogonalised; e2 = T x e1
+    int k0 = 0;
+    if (fabs(double(T[1])) < fabs(double(T[k0]))) k0 = 1;
+    if (fabs(double(T[2])) < fabs(double(T[k0]))) k0 = 2;
+    R e1[3] = {R(0), R(0), R(0)};
+    e1[k0] = R(1);
+    R d = e1[0] * T[0] + e1[1] * T[1] + e1[2] * T[2];
+    for (int i = 0; i < 3; ++i) e1[i] -= d * T[i];
+    R n = R(1) / sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int i = 0; i < 3; ++i) e1[i] *= n;
+    R e2[3] = {T[1] * e1[2] - T[2] * e1[1], T[2] * e1[0] - T[0] * e1[2], T[0] * e1[1] - T[1] * e1[0]};
+    R acc[18];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) acc[i] = 0;
+    for (int k = 0; k < Q; ++k) {
+        double s, c;
+        sincospi(double(k) / double(Q), &s, &c);
+        R z[3];
+        for (int i = 0; i < 3; ++i) z[i] = R(c) * e1[i] + R(s) * e2[i];
+        R M[9], ZT[9];
+        cmat<R, CT>(C, z, z, M);
+        cmat<R, CT>(C, z, T, ZT);
+        // inverse of the symmetric positive-definite M (adjugate / determinant)
+        R i00 = M[4] * M[8] - M[5] * M[7];
+        R i01 = M[2] * M[7] - M[1] * M[8];
+        R i02 = M[1] * M[5] - M[2] * M[4];
+        R i11 = M[0] * M[8] - M[2] * M[6];
+        R i12 = M[2] * M[3] - M[0] * M[5];
+        R i22 = M[0] * M[4] - M[1] * M[3];
+        R idet = R(1) / (M[0] * i00 + M[1] * (M[5] * M[6] - M[3] * M[8]) + M[2] * (M[3] * M[7] - M[4] * M[6]));
+        R Mi[9] = {i00 * idet, i01 * idet, i02 * idet, i01 * idet, i11 * idet,
+                   i12 * idet, i02 * idet, i12 * idet, i22 * idet};
+        R S[9];
+        for (int j = 0; j < 3; ++j)
+            for (int l = 0; l < 3; ++l) S[j * 3 + l] = ZT[j * 3 + l] + ZT[l * 3 + j];
+        R tmp[9], F[9];
+        for (int j = 0; j < 3; ++j)
+            for (int l = 0; l < 3; ++l)
+                tmp[j * 3 + l] = Mi[j * 3] * S[l] + Mi[j * 3 + 1] * S[3 + l] + Mi[j * 3 + 2] * S[6 + l];
+        for (int j = 0; j < 3; ++j)
+            for (int l = 0; l < 3; ++l)
+                F[j * 3 + l] = tmp[j * 3] * Mi[l] + tmp[j * 3 + 1] * Mi[3 + l] + tmp[j * 3 + 2] * Mi[6 + l];
+        constexpr int PV[6] = {0, 1, 2, 1, 0, 0};
+        constexpr int PP[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+        for (int pr = 0; pr < 6; ++pr) {
+            const int v = PV[pr], p = PP[pr];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc[3 * pr + q] += -T[q] * Mi[v * 3 + p] + z[q] * F[v * 3 + p];
+        }
+    }
+    // 2 (pi / Q) / (8 pi^2) = 1 / (4 pi Q)
+    const R f = R(1.0 / (4.0 * 3.14159265358979323846 * double(Q)));
+#pragma unroll
+    for (int i = 0; i < 18; ++i) hs[i] = acc[i] * f;
+}
+
+// Lagrange basis on the p equispaced nodes t_a = a / (p - 1) of [0, 1]
+// (Sec. 4.1 footnote): ell_a(t) = prod_{b != a} (t - t_b) / (t_a - t_b).
+template <typename R>
+__device__ __forceinline__ void lagrange_1d(int p, R t, R *out) {
+    const R inv = R(1) / R(p - 1);
+    for (int a = 0; a < p; ++a) {
+        R v = R(1);
+        for (int b = 0; b < p; ++b)
+            if (b != a) v *= (t - R(b) * inv) / (R(a - b) * inv);
+        out[a] = v;
+    }
+}

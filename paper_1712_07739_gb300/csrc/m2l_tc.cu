@@ -1,0 +1,577 @@
+// M2L on the tcgen05 tensor cores: offset-grouped dense GEMMs (Sec. 4.1,
+// Eq. "m2l"; Algorithm 2 step 2) in BF16 with FP32 accumulation in TMEM.
+//
+// Formulation.  At level l the cells form a 2^l grid.  Split it into the 8
+// parity classes c = (x & 1, y & 1, z & 1); each class is an m^3 sub-grid,
+// m = 2^(l-1).  For a target cell B = 2P + c and an offset o in its
+// interaction list, the source A = B - o lies in class c' = (c - o) mod 2 at
+// sub-grid position P + s, s = floor((c - o) / 2) in [-1, 1]^3.  The 189
+// offsets of class c are therefore, each, a constant shift between two
+// sub-grids, and the M2L of a brick of 128 target cells (8 x 4 x 4 in the
+// sub-grid) is
+//     S[brick, n] = (2^l / H)^2  sum_o  sum_k  W_c'[brick + s_o, k] T_o[n, k]
+// with k = (node m, component wr) and n = (node l, stress component ab):
+// one GEMM of M = 128 cells, N = 6 p^3 and K = 189 x 9 p^3, accumulated in
+// tensor memory.  The A tile (shifted brick of multipole weights) and the
+// B tile (rows of the operator T_o) are both plain TMA box loads; boxes that
+// stick out of the sub-grid are zero-filled by the TMA unit.
+//
+// Precision: W and T_o are rounded to BF16 (hi).  For the offsets nearest
+// to the target (max |o_i| = 2, the largest far-field terms) the residuals
+// W_lo = W - hi(W) and T_lo = T - hi(T) add two more passes,
+// hi*hi + lo*hi + hi*lo, which restores ~FP32 accuracy where it matters.
+//
+// Warp roles (192 threads): warp 0 issues TMA loads, warp 1 owns TMEM and
+// issues the MMAs, warps 2-5 read the accumulator out (warp w reads TMEM
+// lanes 32 (w % 4) .. 32 (w % 4) + 31).  Every mbarrier wait is bounded;
+// on time-out a device status word gets GBFMM_ERR_TIMEOUT and the block
+// winds down, freeing its tensor memory.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "m2l_tc.cuh"
+
+namespace {
+
+struct OffsetEntry {
+    short top;      // operator index 0..315
+    short lo;       // index in the residual table, -1 when the offset has no split pass
+    signed char cls;  // source parity class
+    signed char sx, sy, sz;
+};
+
+__constant__ OffsetEntry c_offs[8][189];
+
+struct M2LParams {
+    CUtensorMap tmW[GB_TC_MAXLEV];    // W hi per level: (Kp, m, m, m, 8) bf16
+    CUtensorMap tmWlo[GB_TC_MAXLEV];  // W residual per level
+    CUtensorMap tmT;                  // T hi: (Kp, Np, 316)
+    CUtensorMap tmTlo;                // T residual: (Kp, Np, n_lo)
+    int kb;         // K blocks of 64
+    int nsub;       // N per MMA (multiple of 16, <= 256)
+    int ncta;       // 3 * nsub
+    int nvalid;     // 6 p^3
+    int tmem_cols;  // power of two >= ncta
+    int split;      // residual passes on the near offsets
+};
+
+constexpr int kStageA = 128 * 64 * 2;  // 16 KB
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: gives up after ~4 s of device time
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *status) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (globaltimer() - t0 > 4000000000ull) {
+            atomicExch(status, GBFMM_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c2,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// UMMA shared-memory descriptor, K-major, 128-byte swizzle: start address,
+// leading offset 16 B (unused inside one swizzle atom), stride offset 1024 B
+// between 8-row groups, descriptor version 1, layout SWIZZLE_128B (2).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= uint64_t((addr >> 4) & 0x3FFF);
+    d |= uint64_t(1) << 16;
+    d |= uint64_t(1024 >> 4) << 32;
+    d |= uint64_t(1) << 46;
+    d |= uint64_t(2) << 61;
+    return d;
+}
+
+// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// number of K-block iterations of one work item (same count on every warp)
+__device__ __forceinline__ int passes_of(const OffsetEntry &e, int split) { return (split && e.lo >= 0) ? 3 : 1; }
+
+__global__ void __launch_bounds__(192, 1)
+    k_m2l_tc(const __grid_constant__ M2LParams P, const int4 *__restrict__ work, const int *__restrict__ tocc,
+             const TreeBox *__restrict__ box, float *__restrict__ S, int *__restrict__ status, int stages) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int stageB = P.ncta * 128;
+    const int stage_bytes = kStageA + stageB;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + stages * stage_bytes);
+    // bars[0..stages): full, [stages..2 stages): empty, [2 stages]: accumulator ready
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 1);
+
+    const int4 w = work[blockIdx.x];
+    const int level = w.x, cls = w.y, brick = w.z, group = w.w;
+    const int m = 1 << (level - 1), n = 1 << level;
+    const int nbx = (m + 7) / 8, nby = (m + 3) / 4;
+    const int bx0 = (brick % nbx) * 8, by0 = ((brick / nbx) % nby) * 4, bz0 = (brick / (nbx * nby)) * 4;
+    const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
+
+    // skip bricks without targets (uniform over the block)
+    {
+        __shared__ int any;
+        if (threadIdx.x == 0) any = 0;
+        __syncthreads();
+        if (threadIdx.x < 128) {
+            const int rx = threadIdx.x % 8, ry = (threadIdx.x / 8) % 4, rz = threadIdx.x / 32;
+            const int px = bx0 + rx, py = by0 + ry, pz = bz0 + rz;
+            if (px < m && py < m && pz < m) {
+                const int64_t g = cell_base_d(level) + (int64_t(2 * pz + cz) * n + (2 * py + cy)) * n + (2 * px + cx);
+                if (tocc[g] > 0) any = 1;
+            }
+        }
+        __syncthreads();
+        if (!any) return;
+    }
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2 * stages + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(P.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[stages]), accb = smem_u32(&bars[2 * stages]);
+    const uint32_t smem0 = smem_u32(smem);
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        int it = 0;
+        bool ok = true;
+        for (int oi = 0; oi < 189 && ok; ++oi) {
+            const OffsetEntry e = c_offs[cls][oi];
+            const int np = passes_of(e, P.split);
+            for (int pass = 0; pass < np && ok; ++pass) {
+                const CUtensorMap *ta = (pass == 1) ? &P.tmWlo[level] : &P.tmW[level];
+                const CUtensorMap *tb = (pass == 2) ? &P.tmTlo : &P.tmT;
+                const int tidx = (pass == 2) ? e.lo : e.top;
+                for (int kb = 0; kb < P.kb; ++kb, ++it) {
+                    const int s = it % stages;
+                    const uint32_t ph = (it / stages) & 1;
+                    if (!mbar_wait(empty0 + 8 * s, ph ^ 1, status)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = full0 + 8 * s;
+                    mbar_expect_tx(fb, kStageA + stageB);
+                    const uint32_t a = smem0 + s * stage_bytes;
+                    tma_load_5d(a, ta, kb * 64, bx0 + e.sx, by0 + e.sy, bz0 + e.sz, e.cls, fb);
+                    for (int j = 0; j < 3; ++j)
+                        tma_load_3d(a + kStageA + j * P.nsub * 128, tb, kb * 64, group * P.ncta + j * P.nsub, tidx,
+                                    fb);
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        const uint32_t idesc = idesc_bf16(128, P.nsub);
+        int it = 0;
+        bool ok = true;
+        for (int oi = 0; oi < 189 && ok; ++oi) {
+            const OffsetEntry e = c_offs[cls][oi];
+            const int np = passes_of(e, P.split);
+            for (int pass = 0; pass < np && ok; ++pass) {
+                for (int kb = 0; kb < P.kb; ++kb, ++it) {
+                    const int s = it % stages;
+                    const uint32_t ph = (it / stages) & 1;
+                    if (!mbar_wait(full0 + 8 * s, ph, status)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t a = smem0 + s * stage_bytes;
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = sw128_desc(a + kk * 32);
+                        for (int j = 0; j < 3; ++j) {
+                            const uint64_t bd = sw128_desc(a + kStageA + j * P.nsub * 128 + kk * 32);
+                            mma_bf16(tmem + j * P.nsub, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(empty0 + 8 * s);
+                }
+            }
+        }
+        mma_commit(accb);  // fires when every MMA issued above has completed
+    } else if (warp >= 2) {
+        // ---------------- epilogue: TMEM -> scaled FP32 local values
+        const bool ok = mbar_wait(accb, 0, status);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int q = warp % 4;
+        const int row = q * 32 + lane;
+        const int rx = row % 8, ry = (row / 8) % 4, rz = row / 32;
+        const int px = bx0 + rx, py = by0 + ry, pz = bz0 + rz;
+        const bool valid = ok && px < m && py < m && pz < m;
+        const int64_t g = cell_base_d(level) + (int64_t(2 * pz + cz) * n + (2 * py + cy)) * n + (2 * px + cx);
+        const float sc = float(double(n) / box->H) * float(double(n) / box->H);
+        float *dst = S + g * int64_t(P.nvalid);
+        if (ok) {
+            for (int j = 0; j < 3; ++j)
+                for (int c0 = 0; c0 < P.nsub; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t(j * P.nsub + c0), v);
+                    const int col = group * P.ncta + j * P.nsub + c0;
+                    if (valid)
+                        for (int i = 0; i < 16; ++i)
+                            if (col + i < P.nvalid) dst[col + i] = v[i] * sc;
+                }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols));
+    }
+}
+
+// ---------------------------------------------------------------- operators
+// T_o[n = l*6 + ab][k = m*9 + wr] = Klat[o (p-1) + l - m][ab][wr] (unit cell);
+// hi = bf16(T), lo = bf16(T - hi) (residual table only for split offsets).
+__global__ void k_build_ops(int p, int lat_n, int Np, int Kp, const double *__restrict__ Klat,
+                            const int *__restrict__ off_xyz, const int *__restrict__ lo_of, int n_off,
+                            __nv_bfloat16 *__restrict__ Thi, __nv_bfloat16 *__restrict__ Tlo) {
+    const int64_t total = int64_t(n_off) * Np * Kp;
+    const int P3 = p * p * p;
+    const int R0 = (lat_n - 1) / 2;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int k = int(idx % Kp);
+        const int nn = int((idx / Kp) % Np);
+        const int o = int(idx / (int64_t(Kp) * Np));
+        double v = 0.0;
+        if (nn < 6 * P3 && k < 9 * P3) {
+            const int l = nn / 6, ab = nn % 6, mm = k / 9, wr = k % 9;
+            const int ox = off_xyz[3 * o], oy = off_xyz[3 * o + 1], oz = off_xyz[3 * o + 2];
+            const int Dx = ox * (p - 1) + (l % p) - (mm % p) + R0;
+            const int Dy = oy * (p - 1) + ((l / p) % p) - ((mm / p) % p) + R0;
+            const int Dz = oz * (p - 1) + (l / (p * p)) - (mm / (p * p)) + R0;
+            v = Klat[((int64_t(Dz) * lat_n + Dy) * lat_n + Dx) * 54 + ab * 9 + wr];
+        }
+        const __nv_bfloat16 hi = __double2bfloat16(v);
+        Thi[idx] = hi;
+        const int li = lo_of[o];
+        if (li >= 0) Tlo[(int64_t(li) * Np + nn) * Kp + k] = __double2bfloat16(v - double(__bfloat162float(hi)));
+    }
+}
+
+// W (FP32, [cell][p^3 * 9]) -> parity-split BF16 hi / lo, [class][mz][my][mx][Kp] per level
+__global__ void k_pack_w(int level, int P3, int Kp, const float *__restrict__ W, const int *__restrict__ occ,
+                         __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+    const int n = 1 << level, m = n / 2;
+    const int64_t cells = int64_t(n) * n * n;
+    const int64_t total = cells * Kp;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int k = int(idx % Kp);
+        const int64_t lin = idx / Kp;
+        const int x = int(lin % n), y = int((lin / n) % n), z = int(lin / (int64_t(n) * n));
+        const int cls = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+        const int64_t dst = ((((int64_t(cls) * m + z / 2) * m + y / 2) * m + x / 2) * Kp) + k;
+        const int64_t g = cell_base_d(level) + lin;
+        float v = 0.f;
+        if (k < 9 * P3 && occ[g] > 0) v = W[g * 9 * P3 + k];
+        const __nv_bfloat16 h = __float2bfloat16(v);
+        hi[dst] = h;
+        lo[dst] = __float2bfloat16(v - __bfloat162float(h));
+    }
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled get_encoder() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+inline unsigned nblk(int64_t n, int b) { return unsigned(std::min<int64_t>((n + b - 1) / b, 1 << 20)); }
+
+}  // namespace
+
+// Offsets, their parity-class lists and the operator tables.
+int m2l_tc_setup(gbfmm_ctx *ctx) {
+    const int p = ctx->opt.p, P3 = p * p * p;
+    TcPlan &T = ctx->tc;
+    T.Kp = ((9 * P3 + 63) / 64) * 64;
+    // N per MMA: multiple of 16, three of them per block, 3 nsub <= 512 TMEM columns
+    const int nv = 6 * P3;
+    int best = 0, best_waste = 1 << 30;
+    for (int ns = 16; ns <= 160; ns += 16) {
+        const int g = (nv + 3 * ns - 1) / (3 * ns);
+        const int waste = g * 3 * ns - nv + g * 64;  // padding plus a per-group cost
+        if (waste < best_waste) {
+            best_waste = waste;
+            best = ns;
+        }
+    }
+    T.nsub = best;
+    T.ncta = 3 * best;
+    T.groups = (nv + T.ncta - 1) / T.ncta;
+    T.Np = T.groups * T.ncta;
+    T.tmem_cols = 32;
+    while (T.tmem_cols < T.ncta) T.tmem_cols *= 2;
+    // the 316 offsets, and which of them get the residual passes
+    std::vector<int> off;
+    std::vector<int> lo_of;
+    int n_lo = 0;
+    for (int oz = -3; oz <= 3; ++oz)
+        for (int oy = -3; oy <= 3; ++oy)
+            for (int ox = -3; ox <= 3; ++ox) {
+                const int mx = std::max(std::abs(ox), std::max(std::abs(oy), std::abs(oz)));
+                if (mx < 2) continue;
+                off.push_back(ox);
+                off.push_back(oy);
+                off.push_back(oz);
+                lo_of.push_back(mx == 2 ? n_lo++ : -1);
+            }
+    T.n_off = int(off.size() / 3);
+    T.n_lo = n_lo;
+    OffsetEntry ent[8][189];
+    for (int c = 0; c < 8; ++c) {
+        const int cc[3] = {c & 1, (c >> 1) & 1, c >> 2};
+        int cnt = 0;
+        for (int i = 0; i < T.n_off; ++i) {
+            const int o[3] = {off[3 * i], off[3 * i + 1], off[3 * i + 2]};
+            bool in = true;
+            for (int d = 0; d < 3; ++d)
+                if (o[d] < -3 + cc[d] || o[d] > 2 + cc[d]) in = false;
+            if (!in) continue;
+            OffsetEntry &e = ent[c][cnt++];
+            e.top = short(i);
+            e.lo = short(lo_of[i]);
+            int sc = 0;
+            signed char sh[3];
+            for (int d = 0; d < 3; ++d) {
+                const int t = cc[d] - o[d];  // in [-2, 3]
+                const int fl = (t >= 0) ? t / 2 : -((-t + 1) / 2);
+                sh[d] = (signed char)fl;
+                sc |= (t - 2 * fl) << d;
+            }
+            e.cls = (signed char)sc;
+            e.sx = sh[0];
+            e.sy = sh[1];
+            e.sz = sh[2];
+        }
+        if (cnt != 189) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "m2l setup: class offset count != 189");
+    }
+    CK(cudaMemcpyToSymbol(c_offs, ent, sizeof(ent)));
+    int *d_off = nullptr, *d_lo = nullptr;
+    CK(cudaMalloc(&d_off, off.size() * sizeof(int)));
+    CK(cudaMalloc(&d_lo, lo_of.size() * sizeof(int)));
+    CK(cudaMemcpy(d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_lo, lo_of.data(), lo_of.size() * sizeof(int), cudaMemcpyHostToDevice));
+    const size_t hi_elems = size_t(T.n_off) * T.Np * T.Kp, lo_elems = size_t(T.n_lo) * T.Np * T.Kp;
+    if (T.Thi) cudaFree(T.Thi);
+    if (T.Tlo) cudaFree(T.Tlo);
+    T.Thi = T.Tlo = nullptr;
+    CK(cudaMalloc(&T.Thi, hi_elems * 2));
+    CK(cudaMalloc(&T.Tlo, lo_elems * 2));
+    ++ctx->launches;
+    k_build_ops<<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off,
+                                                                         d_lo, T.n_off, T.Thi, T.Tlo);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(d_off);
+    cudaFree(d_lo);
+    if (!T.d_status) CK(cudaMalloc(&T.d_status, sizeof(int)));
+    CK(cudaMemset(T.d_status, 0, sizeof(int)));
+    T.ready_ops = true;
+    return GBFMM_OK;
+}
+
+static int encode(gbfmm_ctx *ctx, CUtensorMap *tm, void *base, int rank, const cuuint64_t *dims,
+                  const cuuint64_t *strides, const cuuint32_t *boxd) {
+    EncodeTiled enc = get_encoder();
+    if (!enc) return set_err(ctx, GBFMM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, cuuint32_t(rank), base, dims, strides, boxd, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_err(ctx, GBFMM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
+    return GBFMM_OK;
+}
+
+// Per-tree buffers: packed W (hi / lo), tensor maps, work list.
+int m2l_tc_prepare(gbfmm_ctx *ctx) {
+    TcPlan &T = ctx->tc;
+    const int L = ctx->L;
+    if (L - 1 >= GB_TC_MAXLEV) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "tensor-core M2L: too many levels");
+    int64_t tot = 0;
+    for (int l = 2; l < L; ++l) {
+        T.wofs[l] = tot;
+        tot += (int64_t(1) << (3 * l)) * T.Kp;
+    }
+    if (tot > T.w_cap) {
+        if (T.Whi) cudaFree(T.Whi);
+        if (T.Wlo) cudaFree(T.Wlo);
+        T.Whi = T.Wlo = nullptr;
+        CK(cudaMalloc(&T.Whi, tot * 2));
+        CK(cudaMalloc(&T.Wlo, tot * 2));
+        T.w_cap = tot;
+    }
+    std::vector<int4> wl;
+    for (int l = 2; l < L; ++l) {
+        const int m = 1 << (l - 1);
+        const int nb = ((m + 7) / 8) * ((m + 3) / 4) * ((m + 3) / 4);
+        for (int c = 0; c < 8; ++c)
+            for (int b = 0; b < nb; ++b)
+                for (int g = 0; g < T.groups; ++g) wl.push_back(make_int4(l, c, b, g));
+    }
+    T.n_work = int(wl.size());
+    if (T.n_work > T.work_cap) {
+        if (T.d_work) cudaFree(T.d_work);
+        T.d_work = nullptr;
+        CK(cudaMalloc(&T.d_work, wl.size() * sizeof(int4)));
+        T.work_cap = T.n_work;
+    }
+    CK(cudaMemcpy(T.d_work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    return GBFMM_OK;
+}
+
+int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc, float *Sf) {
+    TcPlan &T = ctx->tc;
+    const int L = ctx->L, p = ctx->opt.p, P3 = p * p * p;
+    static M2LParams prm;  // large: build on the heap-like static, copied by value at launch
+    std::memset(&prm, 0, sizeof(prm));
+    for (int l = 2; l < L; ++l) {
+        const int m = 1 << (l - 1);
+        ++ctx->launches;
+        const int64_t el = (int64_t(1) << (3 * l)) * T.Kp;
+        k_pack_w<<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, T.Whi + T.wofs[l], T.Wlo + T.wofs[l]);
+        const cuuint64_t dims[5] = {cuuint64_t(T.Kp), cuuint64_t(m), cuuint64_t(m), cuuint64_t(m), 8};
+        const cuuint64_t row = cuuint64_t(T.Kp) * 2;
+        const cuuint64_t strides[4] = {row, row * m, row * m * m, row * m * m * m};
+        const cuuint32_t boxd[5] = {64, 8, 4, 4, 1};
+        int rc = encode(ctx, &prm.tmW[l], T.Whi + T.wofs[l], 5, dims, strides, boxd);
+        if (rc) return rc;
+        rc = encode(ctx, &prm.tmWlo[l], T.Wlo + T.wofs[l], 5, dims, strides, boxd);
+        if (rc) return rc;
+    }
+    {
+        const cuuint64_t dims[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(T.n_off)};
+        const cuuint64_t strides[2] = {cuuint64_t(T.Kp) * 2, cuuint64_t(T.Kp) * 2 * T.Np};
+        const cuuint32_t boxd[3] = {64, cuuint32_t(T.nsub), 1};
+        int rc = encode(ctx, &prm.tmT, T.Thi, 3, dims, strides, boxd);
+        if (rc) return rc;
+        const cuuint64_t dl[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(std::max(T.n_lo, 1))};
+        rc = encode(ctx, &prm.tmTlo, T.Tlo, 3, dl, strides, boxd);
+        if (rc) return rc;
+    }
+    prm.kb = T.Kp / 64;
+    prm.nsub = T.nsub;
+    prm.ncta = T.ncta;
+    prm.nvalid = 6 * P3;
+    prm.tmem_cols = T.tmem_cols;
+    prm.split = T.split;
+    const int stage_bytes = 128 * 64 * 2 + T.ncta * 128;
+    int stages = std::max(2, std::min(6, (200 * 1024) / stage_bytes));
+    const size_t smem = size_t(stages) * stage_bytes + 1024 + (2 * stages + 2) * 8 + 64;
+    CK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    ++ctx->launches;
+    k_m2l_tc<<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_work, tocc, ctx->d_box, Sf, T.d_status, stages);
+    CK(cudaGetLastError());
+    return GBFMM_OK;
+}
+
+void m2l_tc_free(gbfmm_ctx *ctx) {
+    TcPlan &T = ctx->tc;
+    void *ps[] = {T.Thi, T.Tlo, T.Whi, T.Wlo, T.d_work, T.d_status};
+    for (void *q : ps)
+        if (q) cudaFree(q);
+    T = TcPlan{};
+}

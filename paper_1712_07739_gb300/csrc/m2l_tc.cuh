@@ -1,0 +1,28 @@
+// Tensor-core M2L plan (see m2l_tc.cu).
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#define GB_TC_MAXLEV 8
+
+struct gbfmm_ctx;
+
+struct TcPlan {
+    bool ready_ops = false;
+    int Kp = 0, Np = 0;        // padded K (9 p^3 -> multiple of 64) and N (6 p^3 -> groups x 3 nsub)
+    int nsub = 0, ncta = 0, groups = 0, tmem_cols = 0;
+    int n_off = 0, n_lo = 0;   // operators and residual operators
+    int split = 1;             // residual passes on offsets with max |o_i| = 2
+    __nv_bfloat16 *Thi = nullptr, *Tlo = nullptr;
+    __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr;
+    int64_t wofs[GB_TC_MAXLEV] = {0};
+    int64_t w_cap = 0;
+    int4 *d_work = nullptr;
+    int n_work = 0, work_cap = 0;
+    int *d_status = nullptr;
+};
+
+int m2l_tc_setup(gbfmm_ctx *ctx);    // operators (per medium and p)
+int m2l_tc_prepare(gbfmm_ctx *ctx);  // per tree
+int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc, float *Sf);
+void m2l_tc_free(gbfmm_ctx *ctx);

@@ -1,0 +1,182 @@
+// Elastic medium, the contraction A of Sec. 2 Eq. "kernel", and the
+// precomputed M2L node kernels of Sec. 4.1 Eq. "m2l".
+//
+// Theorem 1 says the node kernel of an offset o depends only on l - m; with
+// the cell size factored out (homogeneity of degree -2, Sec. 4.1 footnote)
+// every entry of every one of the 316 operators is K at one point of the
+// integer lattice D = o (p-1) + (l - m), |D_i| <= 4 (p-1), scaled by
+// 1/(p-1).  The table d_Klat holds K at all of those points for a unit
+// cell; the FP64 M2L reads it directly and the tensor-core M2L expands it
+// into dense per-offset operators.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "internal.cuh"
+#include "kernel_math.cuh"
+
+namespace {
+
+int levi(int i, int j, int k) { return ((i - j) * (j - k) * (k - i)) / 2; }
+
+// C_ijkl from the 6x6 Voigt matrix (11, 22, 33, 23, 13, 12)
+void voigt_to_full(const double *V, double *C) {
+    auto vi = [](int i, int j) {
+        if (i == j) return i;
+        if ((i == 1 && j == 2) || (i == 2 && j == 1)) return 3;
+        if ((i == 0 && j == 2) || (i == 2 && j == 0)) return 4;
+        return 5;
+    };
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) C[((i * 3 + j) * 3 + k) * 3 + l] = V[vi(i, j) * 6 + vi(k, l)];
+}
+
+// Positive definiteness of the strain-energy form: Cholesky of the Mandel
+// matrix (Voigt with shear rows/columns scaled by sqrt 2).
+bool positive_definite(const double *V) {
+    double M[36];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j)
+            M[i * 6 + j] = V[i * 6 + j] * (i >= 3 ? std::sqrt(2.0) : 1.0) * (j >= 3 ? std::sqrt(2.0) : 1.0);
+    for (int j = 0; j < 6; ++j) {
+        double d = M[j * 6 + j];
+        for (int k = 0; k < j; ++k) d -= M[j * 6 + k] * M[j * 6 + k];
+        if (!(d > 0.0)) return false;
+        d = std::sqrt(d);
+        M[j * 6 + j] = d;
+        for (int i = j + 1; i < 6; ++i) {
+            double s = M[i * 6 + j];
+            for (int k = 0; k < j; ++k) s -= M[i * 6 + k] * M[j * 6 + k];
+            M[i * 6 + j] = s / d;
+        }
+    }
+    return true;
+}
+
+// K at every lattice point D (unit cell, node spacing 1/(p-1)):
+// K[ab][wr] = sum_k Asym[ab][wr][k] h_k(D/|D|) / |D/(p-1)|^2
+__global__ void k_lattice(const DevMaterial *mat, const double *Asym, int p, int lat_n, double *Klat) {
+    int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    int64_t total = int64_t(lat_n) * lat_n * lat_n;
+    if (idx >= total) return;
+    int R0 = (lat_n - 1) / 2;
+    int dx = int(idx % lat_n) - R0;
+    int dy = int((idx / lat_n) % lat_n) - R0;
+    int dz = int(idx / (int64_t(lat_n) * lat_n)) - R0;
+    double *out = Klat + idx * 54;
+    if (dx == 0 && dy == 0 && dz == 0) {
+        for (int i = 0; i < 54; ++i) out[i] = 0.0;
+        return;
+    }
+    double s = 1.0 / double(p - 1);
+    double d[3] = {dx * s, dy * s, dz * s};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double ir = 1.0 / sqrt(r2);
+    double T[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
+    double hs[18];
+    if (mat->mode == GBFMM_H_ISO)
+        h_iso_sym<double>(mat->hc, mat->ha, T, hs);
+    else
+        h_circle_sym<double, double>(mat->C, mat->Q, T, hs);
+    double ir2 = 1.0 / r2;
+    for (int i = 0; i < 54; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < 18; ++k) acc += Asym[i * 18 + k] * hs[k];
+        out[i] = acc * ir2;
+    }
+}
+
+}  // namespace
+
+int material_setup(gbfmm_ctx *ctx) {
+    const int p = ctx->opt.p;
+    // A_{ab,wr,vpq} = sum_{n,g} eps_ngr C_abvg C_pqwn, folded over (v,p) <-> (p,v)
+    const double *C = ctx->mat.C;
+    static const int PV[6] = {0, 1, 2, 1, 0, 0}, PP[6] = {0, 1, 2, 2, 2, 1};
+    for (int ab = 0; ab < 6; ++ab) {
+        int a = voigt_a(ab), b = voigt_b(ab);
+        for (int w = 0; w < 3; ++w)
+            for (int r = 0; r < 3; ++r)
+                for (int pr = 0; pr < 6; ++pr)
+                    for (int q = 0; q < 3; ++q) {
+                        double tot = 0.0;
+                        for (int sym = 0; sym < 2; ++sym) {
+                            int v = sym ? PP[pr] : PV[pr];
+                            int pp = sym ? PV[pr] : PP[pr];
+                            if (sym && v == pp) break;
+                            double s = 0.0;
+                            for (int n = 0; n < 3; ++n)
+                                for (int g = 0; g < 3; ++g) {
+                                    int e = levi(n, g, r);
+                                    if (!e) continue;
+                                    s += e * C[((a * 3 + b) * 3 + v) * 3 + g] * C[((pp * 3 + q) * 3 + w) * 3 + n];
+                                }
+                            tot += s;
+                        }
+                        ctx->Asym[(ab * 9 + w * 3 + r) * 18 + pr * 3 + q] = tot;
+                    }
+    }
+    float Af[6 * 9 * 18];
+    for (int i = 0; i < 6 * 9 * 18; ++i) Af[i] = float(ctx->Asym[i]);
+    if (!ctx->d_mat) CK(cudaMalloc(&ctx->d_mat, sizeof(DevMaterial)));
+    if (!ctx->d_Asym) CK(cudaMalloc(&ctx->d_Asym, sizeof(ctx->Asym)));
+    if (!ctx->d_Asym_f) CK(cudaMalloc(&ctx->d_Asym_f, sizeof(Af)));
+    CK(cudaMemcpyAsync(ctx->d_mat, &ctx->mat, sizeof(DevMaterial), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_Asym, ctx->Asym, sizeof(ctx->Asym), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_Asym_f, Af, sizeof(Af), cudaMemcpyHostToDevice, ctx->stream));
+
+    int lat_n = 8 * (p - 1) + 1;
+    int64_t total = int64_t(lat_n) * lat_n * lat_n;
+    if (ctx->lat_n != lat_n) {
+        if (ctx->d_Klat) cudaFree(ctx->d_Klat);
+        ctx->d_Klat = nullptr;
+        CK(cudaMalloc(&ctx->d_Klat, total * 54 * sizeof(double)));
+        ctx->lat_n = lat_n;
+    }
+    ++ctx->launches;
+    k_lattice<<<unsigned((total + 127) / 128), 128, 0, ctx->stream>>>(ctx->d_mat, ctx->d_Asym, p, lat_n, ctx->d_Klat);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GBFMM_OK;
+}
+
+extern "C" int fmm_set_material(gbfmm_ctx *ctx, const double *V) {
+    if (!ctx) return GBFMM_ERR_INVALID_ARG;
+    if (!V) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_set_material: null stiffness");
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j)
+            if (!std::isfinite(V[i * 6 + j]) || std::fabs(V[i * 6 + j] - V[j * 6 + i]) > 1e-12 * std::fabs(V[i * 6 + j]) + 1e-300)
+                return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_set_material: stiffness not symmetric/finite");
+    if (!positive_definite(V)) return set_err(ctx, GBFMM_ERR_DEGENERATE, "fmm_set_material: stiffness not positive definite");
+    DevMaterial m{};
+    voigt_to_full(V, m.C);
+    m.mode = ctx->opt.h_mode;
+    m.Q = ctx->opt.circle_q > 0 ? ctx->opt.circle_q : 64;
+    if (m.mode == GBFMM_H_ISO) {
+        double c11 = V[0], c12 = V[1], c44 = V[21];
+        double scale = std::fabs(c11) + std::fabs(c12) + std::fabs(c44);
+        bool cubic = true;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 6; ++j) {
+                double want = (j < 3) ? (i == j ? c11 : c12) : 0.0;
+                if (std::fabs(V[i * 6 + j] - want) > 1e-12 * scale) cubic = false;
+            }
+        for (int i = 3; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                double want = (i == j) ? c44 : 0.0;
+                if (std::fabs(V[i * 6 + j] - want) > 1e-12 * scale) cubic = false;
+            }
+        if (!cubic || std::fabs(c11 - c12 - 2.0 * c44) > 1e-12 * scale)
+            return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_set_material: GBFMM_H_ISO needs an isotropic stiffness");
+        double mu = c44, nu = c12 / (2.0 * (c12 + c44));
+        m.hc = 1.0 / (16.0 * M_PI * mu * (1.0 - nu));
+        m.ha = 3.0 - 4.0 * nu;
+    }
+    ctx->mat = m;
+    int rc = material_setup(ctx);
+    if (rc) return rc;
+    ctx->have_material = true;
+    return GBFMM_OK;
+}
