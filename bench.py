@@ -33,10 +33,22 @@ from paper_1712_07739_gb300 import synth  # noqa: E402
 METRIC = "FMM segment nodal forces/sec at 1e-4 rel err: mixed+learned vs plain FP64, 1 GB300"
 UNIT = "segments/s"
 
-# per-pair arithmetic of the near field (counted from the kernel source):
-# separation 3, |d|^2 5, rsqrt 1, direction 3, h (18 components) ~100,
-# contraction with the 6x18 source tensor 216, 1/R^2 scaling and accumulate 13
-FLOP_PER_NEAR_PAIR = {"iso": 341}
+# per-pair arithmetic of the near field (counted from the kernel source, FMA = 2):
+# FP64 path, isotropic: separation 3, |d|^2 5, rsqrt 1, direction 3, h (18
+#   components) ~100, contraction with the 6x18 source tensor 216, scale and
+#   accumulate 13 -> 341
+# mixed path, isotropic polynomial form: separation 3, |d|^2 5, rsqrt 1,
+#   1/R^3 and 1/R^5 3, cubic monomials 16, per stress component 3 linear +
+#   10 cubic FMAs and 2 scaled adds (29) x 6 -> 202
+# mixed path, unit-circle h: Q x (zz and zT 2 x 81 FMA, inverse 30, F 54,
+#   accumulate 36, direction 6) ~ Q x 450, plus the 6x18 contraction 216
+FLOP_PER_NEAR_PAIR = {("fp64", "iso"): 341, ("mixed", "iso"): 202}
+
+
+def near_pair_flops(precision, h_mode, q):
+    if (precision, h_mode) in FLOP_PER_NEAR_PAIR:
+        return FLOP_PER_NEAR_PAIR[(precision, h_mode)]
+    return 450 * q + 216 + 20
 FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 (nominal, profiling recipe table)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
@@ -47,6 +59,16 @@ WORKLOADS = {
         gen=lambda seed: synth.hexagon_loops(seed=seed), C=lambda: synth.isotropic_voigt(1.0, 0.3),
         h_mode="iso", p=4, levels=3, precision="fp64"),
 }
+WORKLOADS["c3"] = dict(
+    desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs, sigma 0.02), cubic C11=1.684 C12=1.214 "
+         "C44=0.754, order p=6, mixed precision (BF16 tensor-core M2L with split passes, FP32 near field with FP64 "
+         "close pairs), unit-circle h (Q=24 FP32 / 64 FP64)",
+    gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
+    h_mode="circle", circle_q=24, p=6, levels=0, precision="mixed")
+WORKLOADS["c3_iso"] = dict(
+    desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs), isotropic mu=1 nu=0.3, p=6, mixed precision",
+    gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.isotropic_voigt(1.0, 0.3),
+    h_mode="iso", p=6, levels=0, precision="mixed")
 DEFAULT_WORKLOAD = "c1"
 
 
@@ -94,6 +116,15 @@ class ClockSampler:
         reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_bf16_peak():
+    """Dense BF16 peak from MEASURED_PEAKS.json (burst: the kernel is timed on its own)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "MEASURED_PEAKS.json bf16_tflops (burst), of measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s bf16 burst (profiling recipe), of fallback"
 
 
 def oracle_sample_rate(wl, nodes, segs, b, budget_s, nthreads=0):
@@ -163,7 +194,8 @@ def run_ours(args, wl):
     d_nodes = torch.tensor(nodes, device=dev)
     d_segs = torch.tensor(segs, device=dev)
     d_b = torch.tensor(b, device=dev)
-    f = gb.FMM(p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"])
+    f = gb.FMM(p=wl["p"], levels=args.levels or wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
+               circle_q=wl.get("circle_q", 0))
     f.set_material(wl["C"]())
     out = torch.empty((len(nodes), 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -239,16 +271,22 @@ def run_ours(args, wl):
     fp64 = wl["precision"] == "fp64"
     peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
     if leaf_ms >= m2l_ms:
-        flops = work["near_pairs"] * FLOP_PER_NEAR_PAIR[wl["h_mode"]] + work["points"] * (12 * p ** 3 + 30 * p)
+        flops = (work["near_pairs"] * near_pair_flops(wl["precision"], wl["h_mode"], wl.get("circle_q", 64))
+                 + work["points"] * (12 * p ** 3 + 30 * p))
         achieved = flops / (leaf_ms / 1e3) / 1e12
-        dom = "k_leaf_eval_f64 (L2P + near-field P2P)"
+        dom = ("k_leaf_eval_f64" if fp64 else "k_near_mixed") + " (L2P + near-field P2P)"
+        bound, src = "alu", ("FP64 1.25 TFLOP/s nominal (recipe)" if fp64 else "152 SM x 128 lanes x 2 x 2.07 GHz")
     else:
         flops = work["m2l_pairs"] * 2 * 54 * p ** 6
         achieved = flops / (m2l_ms / 1e3) / 1e12
-        dom = "k_m2l_f64 (M2L)"
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "FP64 1.25 TFLOP/s nominal (recipe)" if fp64 else "152 SM x 128 lanes x 2 x 2.07 GHz"}
+        if fp64:
+            dom, bound, src = "k_m2l_f64 (M2L)", "alu", "FP64 1.25 TFLOP/s nominal (recipe)"
+        else:
+            dom, bound = "k_m2l_tc (M2L, tcgen05 BF16)", "tensor"
+            peak, src = measured_bf16_peak()
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "work": "algorithmic: near pairs x FLOP/pair (+ L2P), or M2L cell pairs x 2*54*p^6"}
 
     if rank == 0:
         cpu = None
@@ -286,6 +324,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--levels", type=int, default=0, help="override the workload's tree depth")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

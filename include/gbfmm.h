@@ -65,6 +65,9 @@ typedef struct {
     int leaf_segments;     /* with levels == 0: target mean segments per occupied leaf; 0 = 32 */
     double near_fp64;      /* MIXED: near pairs closer than near_fp64 x (source segment length)
                               are evaluated in FP64; 0 = 2.0 */
+    int m2l_split;         /* MIXED: BF16 residual (split) passes of the tensor-core M2L:
+                              0 = on the offsets with max |o_i| = 2 (default), 1 = none,
+                              2 = on all 316 offsets */
 } gbfmm_options;
 
 typedef struct gbfmm_ctx gbfmm_ctx;
@@ -162,6 +165,19 @@ int fmm_launch_count(const gbfmm_ctx *ctx, int64_t *count);
  * leaves, [3] Gauss points.  Launches two small kernels and synchronises.
  * Errors: NOT_BUILT, CUDA. */
 int fmm_work_counts(gbfmm_ctx *ctx, int64_t *counts);
+
+/* Status word of the device kernels that wait on barriers (the tensor-core
+ * M2L): GBFMM_OK, or GBFMM_ERR_TIMEOUT when a bounded wait gave up during an
+ * earlier pass (that pass's outputs are then invalid).  Synchronises the
+ * stream, reads the word into *status (host) and clears it. */
+int fmm_device_status(gbfmm_ctx *ctx, int *status);
+
+/* Failure-detection test hook.  kind = 1: the next tensor-core M2L
+ * (GBFMM_MIXED) arms its first pipeline stage without loading it, so the
+ * consumer's bounded wait runs out (about 1 s); the pass then reports
+ * GBFMM_ERR_TIMEOUT through fmm_device_status and its outputs are invalid.
+ * Nothing faults and the context stays usable.  Errors: INVALID_ARG. */
+int fmm_inject_fault(gbfmm_ctx *ctx, int kind);
 
 #ifdef __cplusplus
 }

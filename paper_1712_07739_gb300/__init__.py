@@ -29,6 +29,7 @@ EXPORTS = [
     "fmm_default_options", "fmm_create", "fmm_destroy", "fmm_last_error",
     "fmm_set_material", "fmm_build_tree", "fmm_eval_stress", "fmm_eval_nodal_forces",
     "fmm_tree_info", "fmm_set_timing", "fmm_stage_times", "fmm_launch_count", "fmm_work_counts",
+    "fmm_device_status", "fmm_inject_fault",
 ]
 
 
@@ -36,7 +37,7 @@ class Options(ctypes.Structure):
     _fields_ = [
         ("p", ctypes.c_int), ("n_gauss", ctypes.c_int), ("levels", ctypes.c_int),
         ("precision", ctypes.c_int), ("h_mode", ctypes.c_int), ("circle_q", ctypes.c_int),
-        ("leaf_segments", ctypes.c_int), ("near_fp64", ctypes.c_double),
+        ("leaf_segments", ctypes.c_int), ("near_fp64", ctypes.c_double), ("m2l_split", ctypes.c_int),
     ]
 
 
@@ -72,7 +73,9 @@ def load_library(path: str = LIB_PATH):
     L.fmm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.fmm_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
     L.fmm_work_counts.argtypes = [vp, ctypes.POINTER(i64)]
-    for name in ("fmm_launch_count", "fmm_work_counts", "fmm_create", "fmm_set_material", "fmm_build_tree", "fmm_eval_stress",
+    L.fmm_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.fmm_inject_fault.argtypes = [vp, ctypes.c_int]
+    for name in ("fmm_inject_fault", "fmm_device_status", "fmm_launch_count", "fmm_work_counts", "fmm_create", "fmm_set_material", "fmm_build_tree", "fmm_eval_stress",
                  "fmm_eval_nodal_forces", "fmm_tree_info", "fmm_set_timing", "fmm_stage_times"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -92,7 +95,7 @@ class FMM:
     """
 
     def __init__(self, p=4, n_gauss=4, levels=0, precision="fp64", h_mode="iso", circle_q=0,
-                 leaf_segments=0, near_fp64=0.0, stream=None):
+                 leaf_segments=0, near_fp64=0.0, m2l_split=0, stream=None):
         import torch
 
         self._torch = torch
@@ -103,6 +106,7 @@ class FMM:
         o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
         o.h_mode = _HMODE[h_mode] if isinstance(h_mode, str) else int(h_mode)
         o.circle_q, o.leaf_segments, o.near_fp64 = circle_q, leaf_segments, near_fp64
+        o.m2l_split = m2l_split
         self.options = o
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -184,6 +188,17 @@ class FMM:
         a = (ctypes.c_int64 * 4)()
         self._check(self._lib.fmm_work_counts(self._h, a), "fmm_work_counts")
         return {"near_pairs": a[0], "m2l_pairs": a[1], "occupied_leaves": a[2], "points": a[3]}
+
+    def device_status(self):
+        """0, or GBFMM_ERR_TIMEOUT (-5) if a bounded device wait gave up (synchronises, clears)."""
+        v = ctypes.c_int()
+        self._check(self._lib.fmm_device_status(self._h, ctypes.byref(v)), "fmm_device_status")
+        return v.value
+
+    def inject_fault(self, kind=1):
+        """Test hook: make the next tensor-core M2L's bounded wait run out."""
+        self._check(self._lib.fmm_inject_fault(self._h, int(kind)), "fmm_inject_fault")
+        return self
 
     def set_timing(self, on=True):
         self._check(self._lib.fmm_set_timing(self._h, int(bool(on))), "fmm_set_timing")

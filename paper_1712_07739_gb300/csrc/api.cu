@@ -125,7 +125,8 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
     if (opt->p < 2 || opt->p > GB_MAXP || opt->n_gauss < 1 || opt->n_gauss > GB_MAXG ||
         (opt->levels != 0 && (opt->levels < 3 || opt->levels > 9)) ||
         (opt->precision != GBFMM_FP64 && opt->precision != GBFMM_MIXED) || opt->h_mode < 0 || opt->h_mode > 2 ||
-        opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0))
+        opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0) || opt->m2l_split < 0 ||
+        opt->m2l_split > 2)
         return GBFMM_ERR_INVALID_ARG;
     gbfmm_ctx *ctx = new gbfmm_ctx();
     ctx->opt = *opt;
@@ -294,4 +295,15 @@ extern "C" int fmm_work_counts(gbfmm_ctx *ctx, int64_t *out) {
     if (!ctx || !out) return GBFMM_ERR_INVALID_ARG;
     if (!ctx->built) return set_err(ctx, GBFMM_ERR_NOT_BUILT, "fmm_work_counts: call fmm_build_tree first");
     return work_counts(ctx, out);
+}
+
+extern "C" int fmm_device_status(gbfmm_ctx *ctx, int *status) {
+    if (!ctx || !status) return GBFMM_ERR_INVALID_ARG;
+    return m2l_tc_status(ctx, status);
+}
+
+extern "C" int fmm_inject_fault(gbfmm_ctx *ctx, int kind) {
+    if (!ctx || kind != 1) return GBFMM_ERR_INVALID_ARG;
+    ctx->tc.inject_drop = 1;
+    return GBFMM_OK;
 }

@@ -393,148 +393,6 @@ __global__ void k_prep_mixed(int64_t N, int L, const TreeBox *__restrict__ box, 
                           float(y[3 * i + 2] - (box->origin[2] + (cz + 0.5) * h)), float(slen[i]));
 }
 
-// One block per leaf holding targets.  Far part: FP32 interpolation of the
-// leaf's local values.  Near part: FP32 pair sum on leaf-relative
-// coordinates (the separation is exact to FP32 rounding of leaf-sized
-// numbers, not of the box size); pairs closer than near_fp64 source-segment
-// lengths are summed in FP64 from the FP64 positions and source tensors.
-template <int MODE>
-__global__ void __launch_bounds__(128) k_leaf_eval_mixed(
-    int p, int L, float near2, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat,
-    const int *__restrict__ tstart, const double *__restrict__ xt, const int64_t *__restrict__ tsid,
-    const int *__restrict__ sstart, const float4 *__restrict__ yrel, const double *__restrict__ ys,
-    const float *__restrict__ Pf, const double *__restrict__ P64, const int64_t *__restrict__ ssid,
-    const float *__restrict__ S, double *__restrict__ sig) {
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    constexpr int CH = 64;
-    const int P3 = p * p * p;
-    float *sS = reinterpret_cast<float *>(sm_raw);  // [P3][6]
-    float4 *sy = reinterpret_cast<float4 *>(sS + ((P3 * 6 + 3) & ~3));  // [CH]
-    float *sP = reinterpret_cast<float *>(sy + CH);                     // [CH][108]
-    int *ssd = reinterpret_cast<int *>(sP + CH * 108);                  // [CH]
-    float *sC = reinterpret_cast<float *>(ssd + CH);                    // [81]
-    const int64_t leaf = blockIdx.x;
-    const int t0 = tstart[leaf], t1 = tstart[leaf + 1];
-    if (t0 == t1) return;
-    const int nl = 1 << (L - 1);
-    int cx, cy, cz;
-    cell_xyz(leaf, nl, cx, cy, cz);
-    const bool far = L >= 3;
-    if (far) {
-        const float *Sl = S + (cell_base_d(L - 1) + leaf) * int64_t(P3) * 6;
-        for (int i = threadIdx.x; i < P3 * 6; i += blockDim.x) sS[i] = Sl[i];
-    }
-    if (MODE == GBFMM_H_CIRCLE)
-        for (int i = threadIdx.x; i < 81; i += blockDim.x) sC[i] = float(mat->C[i]);
-    const double h = box->H / nl, ih = double(nl) / box->H;
-    const double c0[3] = {box->origin[0] + cx * h, box->origin[1] + cy * h, box->origin[2] + cz * h};
-    const float hc = float(mat->hc), ha = float(mat->ha);
-    const int Q = mat->Q;
-    const double hc64 = mat->hc, ha64 = mat->ha;
-    for (int r0 = t0; r0 < t1; r0 += blockDim.x) {
-        const int t = r0 + threadIdx.x;
-        const bool valid = t < t1;
-        double x[3] = {0, 0, 0};
-        float xr[3] = {0.f, 0.f, 0.f};
-        float acc[6] = {0, 0, 0, 0, 0, 0};
-        double acc64[6] = {0, 0, 0, 0, 0, 0};
-        int myseg = -1;
-        __syncthreads();
-        if (valid) {
-            for (int d = 0; d < 3; ++d) {
-                x[d] = xt[3 * int64_t(t) + d];
-                xr[d] = float(x[d] - (c0[d] + 0.5 * h));
-            }
-            myseg = tsid ? int(tsid[t]) : -1;
-            if (far) {
-                float bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
-                lagrange_1d<float>(p, float((x[0] - c0[0]) * ih), bx);
-                lagrange_1d<float>(p, float((x[1] - c0[1]) * ih), by);
-                lagrange_1d<float>(p, float((x[2] - c0[2]) * ih), bz);
-                for (int l = 0; l < P3; ++l) {
-                    const float w = bx[l % p] * by[(l / p) % p] * bz[l / (p * p)];
-                    for (int ab = 0; ab < 6; ++ab) acc[ab] += w * sS[l * 6 + ab];
-                }
-            }
-        }
-        for (int nb = 0; nb < 27; ++nb) {
-            const int dxn = nb % 3 - 1, dyn = (nb / 3) % 3 - 1, dzn = nb / 9 - 1;
-            const int ax = cx + dxn, ay = cy + dyn, az = cz + dzn;
-            if (ax < 0 || ay < 0 || az < 0 || ax >= nl || ay >= nl || az >= nl) continue;
-            const int64_t A = (int64_t(az) * nl + ay) * nl + ax;
-            const int s0 = sstart[A], s1 = sstart[A + 1];
-            // target relative to the source leaf's centre
-            const float xs0 = xr[0] - float(dxn * h), xs1 = xr[1] - float(dyn * h), xs2 = xr[2] - float(dzn * h);
-            for (int j0 = s0; j0 < s1; j0 += CH) {
-                const int nj = min(CH, s1 - j0);
-                __syncthreads();
-                for (int i = threadIdx.x; i < nj; i += blockDim.x) {
-                    sy[i] = yrel[j0 + i];
-                    ssd[i] = int(ssid[j0 + i]);
-                }
-                {
-                    const float4 *src = reinterpret_cast<const float4 *>(Pf + 108 * int64_t(j0));
-                    float4 *dst = reinterpret_cast<float4 *>(sP);
-                    for (int i = threadIdx.x; i < nj * 27; i += blockDim.x) dst[i] = src[i];
-                }
-                __syncthreads();
-                if (!valid) continue;
-                for (int j = 0; j < nj; ++j) {
-                    if (ssd[j] == myseg) continue;
-                    const float4 yj = sy[j];
-                    const float d0 = xs0 - yj.x, d1 = xs1 - yj.y, d2 = xs2 - yj.z;
-                    const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
-                    if (r2 < near2 * yj.w * yj.w) {
-                        // close pair: FP64 throughout
-                        const int64_t jj = j0 + j;
-                        double d[3] = {x[0] - ys[3 * jj], x[1] - ys[3 * jj + 1], x[2] - ys[3 * jj + 2]};
-                        const double rr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                        if (rr == 0.0) continue;
-                        const double ir = rsqrt(rr);
-                        double T[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
-                        double hs[18];
-                        if (MODE == GBFMM_H_ISO)
-                            h_iso_sym<double>(hc64, ha64, T, hs);
-                        else
-                            h_circle_sym<double, double>(mat->C, Q, T, hs);
-                        const double *Pj = P64 + 108 * jj;
-                        const double ir2 = ir * ir;
-                        for (int ab = 0; ab < 6; ++ab) {
-                            double sacc = 0.0;
-                            for (int k = 0; k < 18; ++k) sacc += Pj[ab * 18 + k] * hs[k];
-                            acc64[ab] += sacc * ir2;
-                        }
-                        continue;
-                    }
-                    const float ir = rsqrtf(r2);
-                    float T[3] = {d0 * ir, d1 * ir, d2 * ir};
-                    float hs[18];
-                    if (MODE == GBFMM_H_ISO)
-                        h_iso_sym<float>(hc, ha, T, hs);
-                    else
-                        h_circle_sym<float, float>(sC, Q, T, hs);
-                    const float ir2 = ir * ir;
-                    const float *Pj = sP + 108 * j;
-#pragma unroll
-                    for (int ab = 0; ab < 6; ++ab) {
-                        float sacc = 0.f;
-#pragma unroll
-                        for (int k = 0; k < 18; ++k) sacc += Pj[ab * 18 + k] * hs[k];
-                        acc[ab] += sacc * ir2;
-                    }
-                }
-            }
-        }
-        if (valid)
-            for (int ab = 0; ab < 6; ++ab) sig[6 * int64_t(t) + ab] = double(acc[ab]) + acc64[ab];
-    }
-}
-
-__global__ void k_f64_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
-    int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (i < n) b[i] = float(a[i]);
-}
-
 // ---------------------------------------------------------------- forces
 struct ForceParams {
     double xi[GB_MAXG], w[GB_MAXG];
@@ -810,9 +668,8 @@ int fmm_kernel_attrs(gbfmm_ctx *ctx) {
     return GBFMM_OK;
 }
 
-static size_t mixed_leaf_smem(int P3) {
-    return size_t((P3 * 6 + 3) & ~3) * 4 + 64 * 16 + 64 * 108 * 4 + 64 * 4 + 81 * 4 + 16;
-}
+int near_prepare(gbfmm_ctx *ctx);  // near.cu
+int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t *tsid, double *sig);
 
 int mixed_alloc(gbfmm_ctx *ctx) {
     const int64_t N = ctx->N, nc = ctx->n_cells;
@@ -853,10 +710,7 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     const int *tstart = free_targets ? ctx->d_t_start : ctx->d_leaf_start;
     Transfer tr = make_transfer(p);
     timer_mark(ctx);
-    ++ctx->launches;
-    k_precontract<double><<<nblk(N, 128), 128, 0, st>>>(N, ctx->d_q, ctx->d_Asym, ctx->d_P);
-    ++ctx->launches;
-    k_f64_to_f32<<<nblk(N * 108, 256), 256, 0, st>>>(N * 108, ctx->d_P, ctx->d_Pf);
+    if (int rc = near_prepare(ctx)) return rc;
     ++ctx->launches;
     k_prep_mixed<<<nblk(N, 256), 256, 0, st>>>(N, L, ctx->d_box, ctx->d_y, ctx->d_pleaf, ctx->d_slen, ctx->d_yrel);
     compute_occ(ctx, ctx->d_leaf_start, occ);
@@ -889,21 +743,10 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     }
     timer_mark(ctx);
     {
-        const size_t smem = mixed_leaf_smem(P3);
         const double *xt = free_targets ? ctx->d_t_x : ctx->d_y;
         const int64_t *tsid = free_targets ? nullptr : ctx->d_sid;
         double *sig = free_targets ? ctx->d_t_sig : ctx->d_sig;
-        const float near2 = float(ctx->opt.near_fp64 * ctx->opt.near_fp64);
-        ++ctx->launches;
-        if (ctx->mat.mode == GBFMM_H_ISO)
-            k_leaf_eval_mixed<GBFMM_H_ISO><<<unsigned(nl), 128, smem, st>>>(
-                p, L, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, ctx->d_y,
-                ctx->d_Pf, ctx->d_P, ctx->d_sid, ctx->d_Sf, sig);
-        else
-            k_leaf_eval_mixed<GBFMM_H_CIRCLE><<<unsigned(nl), 128, smem, st>>>(
-                p, L, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, ctx->d_y,
-                ctx->d_Pf, ctx->d_P, ctx->d_sid, ctx->d_Sf, sig);
-        CK(cudaGetLastError());
+        if (int rc = near_run(ctx, tstart, xt, tsid, sig)) return rc;
     }
     timer_mark(ctx);
     (void)n_t;

@@ -61,6 +61,7 @@ struct M2LParams {
     int nvalid;     // 6 p^3
     int tmem_cols;  // power of two >= ncta
     int split;      // residual passes on the near offsets
+    int drop_first; // failure-detection test: arm the first stage but issue no load into it
 };
 
 constexpr int kStageA = 128 * 64 * 2;  // 16 KB
@@ -93,13 +94,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait: gives up after ~4 s of device time
+// bounded wait: gives up after ~1 s of device time
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *status) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
         if (mbar_try(bar, parity)) return true;
-        if (globaltimer() - t0 > 4000000000ull) {
+        if (globaltimer() - t0 > 1000000000ull) {
             atomicExch(status, GBFMM_ERR_TIMEOUT);
             return false;
         }
@@ -186,10 +187,14 @@ __global__ void __launch_bounds__(192, 1)
     const int bx0 = (brick % nbx) * 8, by0 = ((brick / nbx) % nby) * 4, bz0 = (brick / (nbx * nby)) * 4;
     const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
 
-    // skip bricks without targets (uniform over the block)
+    // skip bricks without targets, and do no work once an earlier block's
+    // time-out is flagged (both decided once for the whole block)
     {
-        __shared__ int any;
-        if (threadIdx.x == 0) any = 0;
+        __shared__ int any, stop;
+        if (threadIdx.x == 0) {
+            any = 0;
+            stop = *reinterpret_cast<volatile int *>(status) != 0;
+        }
         __syncthreads();
         if (threadIdx.x < 128) {
             const int rx = threadIdx.x % 8, ry = (threadIdx.x / 8) % 4, rz = threadIdx.x / 32;
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(192, 1)
             }
         }
         __syncthreads();
-        if (!any) return;
+        if (!any || stop) return;
     }
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -241,6 +246,7 @@ __global__ void __launch_bounds__(192, 1)
                     }
                     const uint32_t fb = full0 + 8 * s;
                     mbar_expect_tx(fb, kStageA + stageB);
+                    if (P.drop_first && it == 0) continue;  // the MMA warp's wait on this stage runs out
                     const uint32_t a = smem0 + s * stage_bytes;
                     tma_load_5d(a, ta, kb * 64, bx0 + e.sx, by0 + e.sy, bz0 + e.sz, e.cls, fb);
                     for (int j = 0; j < 3; ++j)
@@ -417,7 +423,8 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
                 off.push_back(ox);
                 off.push_back(oy);
                 off.push_back(oz);
-                lo_of.push_back(mx == 2 ? n_lo++ : -1);
+                const bool split = ctx->opt.m2l_split == 2 || (ctx->opt.m2l_split == 0 && mx == 2);
+                lo_of.push_back(split ? n_lo++ : -1);
             }
     T.n_off = int(off.size() / 3);
     T.n_lo = n_lo;
@@ -460,7 +467,8 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     if (T.Tlo) cudaFree(T.Tlo);
     T.Thi = T.Tlo = nullptr;
     CK(cudaMalloc(&T.Thi, hi_elems * 2));
-    CK(cudaMalloc(&T.Tlo, lo_elems * 2));
+    CK(cudaMalloc(&T.Tlo, std::max<size_t>(lo_elems, 1) * 2));
+    T.split = n_lo > 0 ? 1 : 0;
     ++ctx->launches;
     k_build_ops<<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off,
                                                                          d_lo, T.n_off, T.Thi, T.Tlo);
@@ -558,6 +566,8 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     prm.nvalid = 6 * P3;
     prm.tmem_cols = T.tmem_cols;
     prm.split = T.split;
+    prm.drop_first = T.inject_drop;
+    T.inject_drop = 0;
     const int stage_bytes = 128 * 64 * 2 + T.ncta * 128;
     int stages = std::max(2, std::min(6, (200 * 1024) / stage_bytes));
     const size_t smem = size_t(stages) * stage_bytes + 1024 + (2 * stages + 2) * 8 + 64;
@@ -565,6 +575,16 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     ++ctx->launches;
     k_m2l_tc<<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_work, tocc, ctx->d_box, Sf, T.d_status, stages);
     CK(cudaGetLastError());
+    return GBFMM_OK;
+}
+
+// read and clear the device status word of the tensor-core M2L
+int m2l_tc_status(gbfmm_ctx *ctx, int *out) {
+    *out = 0;
+    if (!ctx->tc.d_status) return GBFMM_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(out, ctx->tc.d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(ctx->tc.d_status, 0, sizeof(int)));
     return GBFMM_OK;
 }
 

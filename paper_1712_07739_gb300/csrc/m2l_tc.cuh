@@ -20,9 +20,11 @@ struct TcPlan {
     int4 *d_work = nullptr;
     int n_work = 0, work_cap = 0;
     int *d_status = nullptr;
+    int inject_drop = 0;       // set by fmm_inject_fault: the next run leaves one stage unfilled
 };
 
 int m2l_tc_setup(gbfmm_ctx *ctx);    // operators (per medium and p)
 int m2l_tc_prepare(gbfmm_ctx *ctx);  // per tree
 int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc, float *Sf);
 void m2l_tc_free(gbfmm_ctx *ctx);
+int m2l_tc_status(gbfmm_ctx *ctx, int *out);

@@ -1,0 +1,299 @@
+// Near field (Algorithm 2 step 3.b, second sum) and L2P of the mixed-
+// precision pass: one warp per target leaf.
+//
+// For a source point j the kernel contraction of Sec. 2 Eq. "stress3",
+// s_ab += sum_wr K_abwr(x - y_j) q_j,wr, is folded once per source into
+// P_j[ab][k] = sum_wr Asym[ab][wr][k] q_j,wr, so a pair costs
+// s_ab += sum_k P_j[ab][k] h_k(T) / R^2 (k over the 18 distinct h
+// components).  Since q_j = (omega_g / 2) b (x S), P_j is the segment's
+// tensor scaled by the point's Gauss weight.
+//
+// Isotropic medium: h is the odd cubic polynomial of Sec. 2 Eq. "k_iso"
+// differentiated, h_vpq = c [-a d_vp T_q + d_vq T_p + d_pq T_v - 3 T_v T_p T_q],
+// so sum_k P[ab][k] h_k(T) / R^2 = (lin_ab . d) / R^3 + (cub_ab . d^(3)) / R^5
+// with d = x - y, 3 linear and 10 cubic-monomial coefficients per ab
+// (78 per source, an exact rewrite).  Other media keep the 108 entries of P
+// and evaluate h by the unit-circle rule in FP32.
+//
+// Precision: positions enter as FP32 offsets from their own leaf centre, so
+// a separation carries the rounding of leaf-sized numbers, not of the box
+// size; pairs closer than near_fp64 x (source segment length) are summed in
+// FP64 from FP64 positions and FP64 source coefficients.
+#include <cmath>
+
+#include "internal.cuh"
+#include "kernel_math.cuh"
+
+namespace {
+
+inline unsigned nblk(int64_t n, int b) { return unsigned((n + b - 1) / b); }
+
+__device__ __forceinline__ void cell_xyz3(int64_t lin, int n, int &x, int &y, int &z) {
+    x = int(lin % n);
+    y = int((lin / n) % n);
+    z = int(lin / (int64_t(n) * n));
+}
+
+// cubic monomials d_i d_j d_k, i <= j <= k
+__host__ __device__ constexpr int mono_index(int i, int j, int k) {
+    // sorted triple -> 0..9 in the order 000 001 002 011 012 022 111 112 122 222
+    return (i == 0) ? ((j == 0) ? k : (j == 1 ? 2 + k : 5)) : ((i == 1) ? (j == 1 ? 5 + k : 8) : 9);
+}
+
+template <typename R>
+__device__ __forceinline__ void monomials(const R d[3], R m[10]) {
+    const R a00 = d[0] * d[0], a01 = d[0] * d[1], a02 = d[0] * d[2];
+    const R a11 = d[1] * d[1], a12 = d[1] * d[2], a22 = d[2] * d[2];
+    m[0] = a00 * d[0];
+    m[1] = a00 * d[1];
+    m[2] = a00 * d[2];
+    m[3] = a11 * d[0];
+    m[4] = a01 * d[2];
+    m[5] = a22 * d[0];
+    m[6] = a11 * d[1];
+    m[7] = a11 * d[2];
+    m[8] = a22 * d[1];
+    m[9] = a22 * d[2];
+    (void)a02;
+    (void)a12;
+}
+
+// Per-source coefficient tensors, stride NCS per point: 78 used of 80
+// (isotropic polynomial form, padded for 16-byte rows) or 108 (P itself).
+// Computed in FP64 from q, stored in FP64 and FP32.
+template <int NCS>
+__global__ void k_src_coef(int64_t N, const double *__restrict__ q, const double *__restrict__ Asym, double hc,
+                           double ha, double *__restrict__ c64, float *__restrict__ c32) {
+    __shared__ double As[6 * 9 * 18];
+    for (int i = threadIdx.x; i < 6 * 9 * 18; i += blockDim.x) As[i] = Asym[i];
+    __syncthreads();
+    const int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (j >= N) return;
+    double qq[9];
+    for (int i = 0; i < 9; ++i) qq[i] = q[9 * j + i];
+    constexpr int PV[6] = {0, 1, 2, 1, 0, 0}, PP[6] = {0, 1, 2, 2, 2, 1};
+    for (int ab = 0; ab < 6; ++ab) {
+        double P[18];
+        for (int k = 0; k < 18; ++k) {
+            double s = 0.0;
+            for (int wr = 0; wr < 9; ++wr) s += As[(ab * 9 + wr) * 18 + k] * qq[wr];
+            P[k] = s;
+        }
+        if (NCS == 108) {
+            for (int k = 0; k < 18; ++k) {
+                c64[j * 108 + ab * 18 + k] = P[k];
+                c32[j * 108 + ab * 18 + k] = float(P[k]);
+            }
+        } else {
+            double lin[3] = {0, 0, 0}, cub[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            for (int pr = 0; pr < 6; ++pr) {
+                const int v = PV[pr], p = PP[pr];
+                for (int qd = 0; qd < 3; ++qd) {
+                    const double w = P[3 * pr + qd];
+                    if (v == p) lin[qd] += -ha * hc * w;
+                    if (v == qd) lin[p] += hc * w;
+                    if (p == qd) lin[v] += hc * w;
+                    int a = v, b = p, c = qd, t;
+                    if (a > b) { t = a; a = b; b = t; }
+                    if (b > c) { t = b; b = c; c = t; }
+                    if (a > b) { t = a; a = b; b = t; }
+                    cub[mono_index(a, b, c)] += -3.0 * hc * w;
+                }
+            }
+            for (int i = 0; i < 3; ++i) {
+                c64[j * NCS + ab * 13 + i] = lin[i];
+                c32[j * NCS + ab * 13 + i] = float(lin[i]);
+            }
+            for (int i = 0; i < 10; ++i) {
+                c64[j * NCS + ab * 13 + 3 + i] = cub[i];
+                c32[j * NCS + ab * 13 + 3 + i] = float(cub[i]);
+            }
+        }
+    }
+    if (NCS == 80)
+        for (int i = 78; i < 80; ++i) {
+            c64[j * 80 + i] = 0.0;
+            c32[j * 80 + i] = 0.f;
+        }
+}
+
+template <typename R>
+__device__ __forceinline__ void pair_iso(const R d[3], R ir, const R *c, R acc[6]) {
+    const R ir2 = ir * ir, ir3 = ir * ir2, ir5 = ir3 * ir2;
+    R m[10];
+    monomials<R>(d, m);
+#pragma unroll
+    for (int ab = 0; ab < 6; ++ab) {
+        const R *cc = c + ab * 13;
+        const R l = cc[0] * d[0] + cc[1] * d[1] + cc[2] * d[2];
+        R u = R(0);
+#pragma unroll
+        for (int i = 0; i < 10; ++i) u += cc[3 + i] * m[i];
+        acc[ab] += ir3 * l + ir5 * u;
+    }
+}
+
+template <typename R, typename CT>
+__device__ __forceinline__ void pair_generic(const R d[3], R ir, const R *c, const CT *C, int Q, R acc[6]) {
+    R T[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
+    R hs[18];
+    h_circle_sym<R, CT>(C, Q, T, hs);
+    const R ir2 = ir * ir;
+#pragma unroll
+    for (int ab = 0; ab < 6; ++ab) {
+        R s = R(0);
+#pragma unroll
+        for (int k = 0; k < 18; ++k) s += c[ab * 18 + k] * hs[k];
+        acc[ab] += s * ir2;
+    }
+}
+
+constexpr int WARPS = 4;
+
+// NCS: per-source coefficient stride (80 isotropic, 108 generic); SCH
+// sources are staged per warp chunk (static shared memory stays < 48 KB)
+template <int NCS, int SCH>
+__global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
+    int p, int L, int64_t nl, float near2, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat,
+    const int *__restrict__ tstart, const double *__restrict__ xt, const int64_t *__restrict__ tsid,
+    const int *__restrict__ sstart, const float4 *__restrict__ yrel, const double *__restrict__ ys,
+    const float *__restrict__ c32, const double *__restrict__ c64, const int64_t *__restrict__ ssid,
+    const float *__restrict__ S, double *__restrict__ sig) {
+    __shared__ __align__(16) float sP[WARPS][SCH * NCS];
+    __shared__ float4 sy[WARPS][SCH];
+    __shared__ int ssd[WARPS][SCH];
+    __shared__ float sC[81];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (NCS == 108)
+        for (int i = threadIdx.x; i < 81; i += blockDim.x) sC[i] = float(mat->C[i]);
+    __syncthreads();
+    const int64_t leaf = blockIdx.x * int64_t(WARPS) + warp;
+    if (leaf >= nl) return;
+    const int t0 = tstart[leaf], t1 = tstart[leaf + 1];
+    if (t0 == t1) return;
+    const int P3 = p * p * p;
+    const int nlv = 1 << (L - 1);
+    int cx, cy, cz;
+    cell_xyz3(leaf, nlv, cx, cy, cz);
+    const bool far = L >= 3;
+    const double h = box->H / nlv, ih = double(nlv) / box->H;
+    const double c0[3] = {box->origin[0] + cx * h, box->origin[1] + cy * h, box->origin[2] + cz * h};
+    const int Q = mat->Q;
+    const float *Sl = S + (cell_base_d(L - 1) + leaf) * int64_t(P3) * 6;
+    float *wP = sP[warp];
+    float4 *wy = sy[warp];
+    int *wsd = ssd[warp];
+    for (int r0 = t0; r0 < t1; r0 += 32) {
+        const int t = r0 + lane;
+        const bool valid = t < t1;
+        double x[3] = {0, 0, 0};
+        float xr[3] = {0.f, 0.f, 0.f};
+        float acc[6] = {0, 0, 0, 0, 0, 0};
+        double acc64[6] = {0, 0, 0, 0, 0, 0};
+        int myseg = -1;
+        if (valid) {
+            for (int d = 0; d < 3; ++d) {
+                x[d] = xt[3 * int64_t(t) + d];
+                xr[d] = float(x[d] - (c0[d] + 0.5 * h));
+            }
+            myseg = tsid ? int(tsid[t]) : -1;
+        }
+        if (far) {
+            float bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
+            lagrange_1d<float>(p, float((x[0] - c0[0]) * ih), bx);
+            lagrange_1d<float>(p, float((x[1] - c0[1]) * ih), by);
+            lagrange_1d<float>(p, float((x[2] - c0[2]) * ih), bz);
+            for (int lz = 0; lz < p; ++lz)
+                for (int ly = 0; ly < p; ++ly) {
+                    const float wyz = by[ly] * bz[lz];
+                    for (int lx = 0; lx < p; ++lx) {
+                        const float w = bx[lx] * wyz;
+                        const float *s6 = Sl + ((lz * p + ly) * p + lx) * 6;
+                        for (int ab = 0; ab < 6; ++ab) acc[ab] += w * __ldg(s6 + ab);
+                    }
+                }
+        }
+        for (int nb = 0; nb < 27; ++nb) {
+            const int dxn = nb % 3 - 1, dyn = (nb / 3) % 3 - 1, dzn = nb / 9 - 1;
+            const int ax = cx + dxn, ay = cy + dyn, az = cz + dzn;
+            if (ax < 0 || ay < 0 || az < 0 || ax >= nlv || ay >= nlv || az >= nlv) continue;
+            const int64_t A = (int64_t(az) * nlv + ay) * nlv + ax;
+            const int s0 = sstart[A], s1 = sstart[A + 1];
+            const float xs[3] = {xr[0] - float(dxn * h), xr[1] - float(dyn * h), xr[2] - float(dzn * h)};
+            for (int j0 = s0; j0 < s1; j0 += SCH) {
+                const int nj = min(SCH, s1 - j0);
+                __syncwarp();
+                if (lane < nj) {
+                    wy[lane] = yrel[j0 + lane];
+                    wsd[lane] = int(ssid[j0 + lane]);
+                }
+                {
+                    const float4 *src = reinterpret_cast<const float4 *>(c32 + int64_t(NCS) * j0);
+                    float4 *dst = reinterpret_cast<float4 *>(wP);
+                    const int nv = nj * NCS / 4;
+                    for (int i = lane; i < nv; i += 32) dst[i] = __ldg(src + i);
+                }
+                __syncwarp();
+                if (!valid) continue;
+                for (int j = 0; j < nj; ++j) {
+                    if (wsd[j] == myseg) continue;
+                    const float4 yj = wy[j];
+                    float d[3] = {xs[0] - yj.x, xs[1] - yj.y, xs[2] - yj.z};
+                    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 < near2 * yj.w * yj.w) {
+                        const int64_t jj = j0 + j;
+                        double dd[3] = {x[0] - ys[3 * jj], x[1] - ys[3 * jj + 1], x[2] - ys[3 * jj + 2]};
+                        const double rr = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+                        if (rr == 0.0) continue;
+                        const double ir = rsqrt(rr);
+                        if (NCS == 80)
+                            pair_iso<double>(dd, ir, c64 + 80 * jj, acc64);
+                        else
+                            pair_generic<double, double>(dd, ir, c64 + 108 * jj, mat->C, mat->Q, acc64);
+                        continue;
+                    }
+                    const float ir = rsqrtf(r2);
+                    if (NCS == 80)
+                        pair_iso<float>(d, ir, wP + 80 * j, acc);
+                    else
+                        pair_generic<float, float>(d, ir, wP + 108 * j, sC, Q, acc);
+                }
+            }
+        }
+        if (valid)
+            for (int ab = 0; ab < 6; ++ab) sig[6 * int64_t(t) + ab] = double(acc[ab]) + acc64[ab];
+    }
+}
+
+}  // namespace
+
+int near_coef_count(const gbfmm_ctx *ctx) { return ctx->mat.mode == GBFMM_H_ISO ? 80 : 108; }
+
+int near_prepare(gbfmm_ctx *ctx) {
+    const int64_t N = ctx->N;
+    ++ctx->launches;
+    if (near_coef_count(ctx) == 80)
+        k_src_coef<80><<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, ctx->mat.hc, ctx->mat.ha,
+                                                                ctx->d_P, ctx->d_Pf);
+    else
+        k_src_coef<108><<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, ctx->mat.hc, ctx->mat.ha,
+                                                                 ctx->d_P, ctx->d_Pf);
+    CK(cudaGetLastError());
+    return GBFMM_OK;
+}
+
+int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t *tsid, double *sig) {
+    const int64_t nl = ctx->n_leaves;
+    const float near2 = float(ctx->opt.near_fp64 * ctx->opt.near_fp64);
+    ++ctx->launches;
+    if (near_coef_count(ctx) == 80)
+        k_near_mixed<80, 32><<<nblk(nl, WARPS), WARPS * 32, 0, ctx->stream>>>(
+            ctx->opt.p, ctx->L, nl, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel,
+            ctx->d_y, ctx->d_Pf, ctx->d_P, ctx->d_sid, ctx->d_Sf, sig);
+    else
+        k_near_mixed<108, 24><<<nblk(nl, WARPS), WARPS * 32, 0, ctx->stream>>>(
+            ctx->opt.p, ctx->L, nl, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel,
+            ctx->d_y, ctx->d_Pf, ctx->d_P, ctx->d_sid, ctx->d_Sf, sig);
+    CK(cudaGetLastError());
+    return GBFMM_OK;
+}

@@ -148,20 +148,47 @@ __global__ void k_scatter(int64_t n, const int *__restrict__ leaf_of, const int 
     perm[slot] = int(i);
 }
 
-// restore original order inside each leaf (insertion sort; leaves are small)
+// restore original order inside each leaf: one block per leaf, bitonic
+// sort in shared memory (leaves above 8192 points: one-thread insertion sort)
 __global__ void k_leaf_sort(int64_t n_leaves, const int *__restrict__ start, int *__restrict__ perm) {
-    int64_t l = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (l >= n_leaves) return;
-    int b = start[l], e = start[l + 1];
-    for (int i = b + 1; i < e; ++i) {
-        int v = perm[i];
-        int j = i - 1;
-        while (j >= b && perm[j] > v) {
-            perm[j + 1] = perm[j];
-            --j;
-        }
-        perm[j + 1] = v;
+    constexpr int CAP = 8192;
+    __shared__ int v[CAP];
+    const int64_t l = blockIdx.x;
+    const int b = start[l], e = start[l + 1], n = e - b;
+    if (n <= 1) return;
+    if (n > CAP) {
+        if (threadIdx.x == 0)
+            for (int i = b + 1; i < e; ++i) {
+                const int x = perm[i];
+                int j = i - 1;
+                while (j >= b && perm[j] > x) {
+                    perm[j + 1] = perm[j];
+                    --j;
+                }
+                perm[j + 1] = x;
+            }
+        return;
     }
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = i < n ? perm[b + i] : 0x7fffffff;
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const int a = v[i], c = v[ixj];
+                    if ((a > c) == up) {
+                        v[i] = c;
+                        v[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) perm[b + i] = v[i];
 }
 
 __global__ void k_gather_points(int64_t n, int n_g, const int *__restrict__ perm, const double *__restrict__ y0,
@@ -258,7 +285,7 @@ int tree_build(gbfmm_ctx *ctx) {
     ++ctx->launches;
     k_scatter<<<nblk(N, 256), 256, 0, st>>>(N, leaf_of, ctx->d_leaf_start, cursor, perm);
     ++ctx->launches;
-    k_leaf_sort<<<nblk(nl, 128), 128, 0, st>>>(nl, ctx->d_leaf_start, perm);
+    k_leaf_sort<<<unsigned(nl), 128, 0, st>>>(nl, ctx->d_leaf_start, perm);
     ++ctx->launches;
     k_gather_points<<<nblk(N, 256), 256, 0, st>>>(N, ng, perm, y0, q0, len0, leaf_of, ctx->d_y, ctx->d_q,
                                                   ctx->d_sid, ctx->d_slen, ctx->d_pos, ctx->d_pleaf);
@@ -302,7 +329,7 @@ int targets_sort(gbfmm_ctx *ctx, int64_t n_t, const double *x) {
     ++ctx->launches;
     k_scatter<<<nblk(n_t, 256), 256, 0, st>>>(n_t, leaf_of, ctx->d_t_start, cursor, perm);
     ++ctx->launches;
-    k_leaf_sort<<<nblk(nl, 128), 128, 0, st>>>(nl, ctx->d_t_start, perm);
+    k_leaf_sort<<<unsigned(nl), 128, 0, st>>>(nl, ctx->d_t_start, perm);
     ++ctx->launches;
     k_gather_targets<<<nblk(n_t, 256), 256, 0, st>>>(n_t, perm, x, ctx->d_t_x, ctx->d_t_pos);
     CK(cudaGetLastError());
