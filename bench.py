@@ -62,13 +62,13 @@ WORKLOADS = {
 WORKLOADS["c3"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs, sigma 0.02), cubic C11=1.684 C12=1.214 "
          "C44=0.754, order p=6, mixed precision (BF16 tensor-core M2L with split passes, FP32 near field with FP64 "
-         "close pairs), unit-circle h (Q=24 FP32 / 64 FP64)",
+         "close pairs), unit-circle h (cubic form, Q=20 points on the half circle), 7-level octree",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
-    h_mode="circle", circle_q=24, p=6, levels=0, precision="mixed")
+    h_mode="circle", circle_q=20, p=6, levels=7, precision="mixed")
 WORKLOADS["c3_iso"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs), isotropic mu=1 nu=0.3, p=6, mixed precision",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.isotropic_voigt(1.0, 0.3),
-    h_mode="iso", p=6, levels=0, precision="mixed")
+    h_mode="iso", p=6, levels=7, precision="mixed")
 DEFAULT_WORKLOAD = "c1"
 
 

@@ -179,6 +179,44 @@ int fmm_device_status(gbfmm_ctx *ctx, int *status);
  * Nothing faults and the context stays usable.  Errors: INVALID_ARG. */
 int fmm_inject_fault(gbfmm_ctx *ctx, int kind);
 
+/* ------------------------------------------------------------------------
+ * Learned angular factor (a stand-in for the plain evaluator of h).
+ *
+ * A network 3 -> 128 -> 128 -> 128 -> 27 (SiLU; BF16 weight matrices, FP32
+ * biases and accumulation) maps a unit direction T to h_vpq(T) (27
+ * components, index (v*3 + p)*3 + q); h is odd, so the network sees T folded
+ * into the upper half-space and the sign is restored.  Parameters: 37,664
+ * floats, order W1 [128x3], b1 [128], W2 [128x128], b2, W3 [128x128], b3,
+ * W4 [32x128] (rows 27..31 zero), b4 [32]; plus 27 output scales.
+ * Directions are device float [n][3] (unit length not required).
+ * ------------------------------------------------------------------------ */
+
+/* h by the plain evaluator of the context's medium (FP64 unit-circle rule,
+ * or the isotropic closed form), as float y [n][27] (device).
+ * Errors: NO_MATERIAL, INVALID_ARG, CUDA. */
+int fmm_mlp_labels(gbfmm_ctx *ctx, int64_t n, const float *dirs, float *y);
+
+/* Train the network on the plain evaluator's h at the given directions
+ * (device, [n][3]; the caller draws them): Adam, mini-batches of `batch`,
+ * `epochs` passes, cosine-decayed learning rate from `lr`, initial weights
+ * and shuffling from `seed`.  final_loss (host, may be NULL): last batch's
+ * mean squared error in scaled units.  Synchronises the stream.
+ * Errors: NO_MATERIAL, INVALID_ARG, CUDA. */
+int fmm_mlp_train(gbfmm_ctx *ctx, int64_t n, const float *dirs, int epochs, int batch, double lr,
+                  uint64_t seed, float *final_loss);
+
+/* Copy the parameters (host, 37,664 floats) and output scales (host, 27). */
+int fmm_mlp_get(gbfmm_ctx *ctx, float *theta, float *scale);
+int fmm_mlp_set(gbfmm_ctx *ctx, const float *theta, const float *scale);
+
+/* Network h at n directions: h (device, float [n][27]). */
+int fmm_mlp_eval(gbfmm_ctx *ctx, int64_t n, const float *dirs, float *h);
+
+/* Loss and gradient of one batch for the current parameters: y (device,
+ * [n][27] target h), grad (device, 37,664 floats), loss (host, may be NULL;
+ * synchronises when given). */
+int fmm_mlp_grad(gbfmm_ctx *ctx, int n, const float *dirs, const float *y, float *grad, float *loss);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,9 @@ EXPORTS = [
     "fmm_set_material", "fmm_build_tree", "fmm_eval_stress", "fmm_eval_nodal_forces",
     "fmm_tree_info", "fmm_set_timing", "fmm_stage_times", "fmm_launch_count", "fmm_work_counts",
     "fmm_device_status", "fmm_inject_fault",
+    "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
 ]
+MLP_PARAMS = 37664
 
 
 class Options(ctypes.Structure):
@@ -75,7 +77,15 @@ def load_library(path: str = LIB_PATH):
     L.fmm_work_counts.argtypes = [vp, ctypes.POINTER(i64)]
     L.fmm_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.fmm_inject_fault.argtypes = [vp, ctypes.c_int]
-    for name in ("fmm_inject_fault", "fmm_device_status", "fmm_launch_count", "fmm_work_counts", "fmm_create", "fmm_set_material", "fmm_build_tree", "fmm_eval_stress",
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.fmm_mlp_train.argtypes = [vp, i64, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, fp]
+    L.fmm_mlp_get.argtypes = [vp, fp, fp]
+    L.fmm_mlp_set.argtypes = [vp, fp, fp]
+    L.fmm_mlp_eval.argtypes = [vp, i64, dp, dp]
+    L.fmm_mlp_grad.argtypes = [vp, ctypes.c_int, dp, dp, dp, fp]
+    L.fmm_mlp_labels.argtypes = [vp, i64, dp, dp]
+    for name in ("fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
+                 "fmm_inject_fault", "fmm_device_status", "fmm_launch_count", "fmm_work_counts", "fmm_create", "fmm_set_material", "fmm_build_tree", "fmm_eval_stress",
                  "fmm_eval_nodal_forces", "fmm_tree_info", "fmm_set_timing", "fmm_stage_times"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -199,6 +209,53 @@ class FMM:
         """Test hook: make the next tensor-core M2L's bounded wait run out."""
         self._check(self._lib.fmm_inject_fault(self._h, int(kind)), "fmm_inject_fault")
         return self
+
+    # ---------------------------------------------------------- learned h
+    def _f32(self, x):
+        return x.to(dtype=self._torch.float32).contiguous()
+
+    def mlp_labels(self, dirs):
+        """Plain-evaluator h (27 components) at unit directions [n, 3] (device)."""
+        dirs = self._f32(dirs)
+        y = self._torch.empty((dirs.shape[0], 27), dtype=self._torch.float32, device=dirs.device)
+        self._check(self._lib.fmm_mlp_labels(self._h, dirs.shape[0], _ptr(dirs), _ptr(y)), "fmm_mlp_labels")
+        return y
+
+    def mlp_train(self, dirs, epochs=10, batch=4096, lr=2e-3, seed=0):
+        """Train the network on the plain evaluator's values at dirs; returns the last batch loss."""
+        dirs = self._f32(dirs)
+        loss = ctypes.c_float()
+        self._check(self._lib.fmm_mlp_train(self._h, dirs.shape[0], _ptr(dirs), int(epochs), int(batch), float(lr),
+                                            int(seed), ctypes.byref(loss)), "fmm_mlp_train")
+        return loss.value
+
+    def mlp_get(self):
+        th = np.zeros(MLP_PARAMS, np.float32)
+        sc = np.zeros(27, np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        self._check(self._lib.fmm_mlp_get(self._h, th.ctypes.data_as(fp), sc.ctypes.data_as(fp)), "fmm_mlp_get")
+        return th, sc
+
+    def mlp_set(self, theta, scale):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        sc = np.ascontiguousarray(scale, dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        self._check(self._lib.fmm_mlp_set(self._h, th.ctypes.data_as(fp), sc.ctypes.data_as(fp)), "fmm_mlp_set")
+        return self
+
+    def mlp_eval(self, dirs):
+        dirs = self._f32(dirs)
+        h = self._torch.empty((dirs.shape[0], 27), dtype=self._torch.float32, device=dirs.device)
+        self._check(self._lib.fmm_mlp_eval(self._h, dirs.shape[0], _ptr(dirs), _ptr(h)), "fmm_mlp_eval")
+        return h
+
+    def mlp_grad(self, dirs, y):
+        dirs, y = self._f32(dirs), self._f32(y)
+        g = self._torch.empty(MLP_PARAMS, dtype=self._torch.float32, device=dirs.device)
+        loss = ctypes.c_float()
+        self._check(self._lib.fmm_mlp_grad(self._h, dirs.shape[0], _ptr(dirs), _ptr(y), _ptr(g),
+                                           ctypes.byref(loss)), "fmm_mlp_grad")
+        return g, loss.value
 
     def set_timing(self, on=True):
         self._check(self._lib.fmm_set_timing(self._h, int(bool(on))), "fmm_set_timing")

@@ -7,6 +7,7 @@
 #include "internal.cuh"
 
 int fmm_kernel_attrs(gbfmm_ctx *ctx);  // fmm.cu
+void mlp_free(gbfmm_ctx *ctx);         // mlp.cu
 int mixed_alloc(gbfmm_ctx *ctx);       // mixed.cu
 int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t);
 
@@ -160,6 +161,7 @@ extern "C" void fmm_destroy(gbfmm_ctx *ctx) {
     for (void *p : ps)
         if (p) cudaFree(p);
     m2l_tc_free(ctx);
+    mlp_free(ctx);
     if (ctx->timer.on)
         for (auto &e : ctx->timer.ev) cudaEventDestroy(e);
     delete ctx;

@@ -359,6 +359,8 @@ __global__ void k_leaf_eval_f64(int p, int L, const TreeBox *__restrict__ box, c
                     double hs[18];
                     if (MODE == GBFMM_H_ISO)
                         h_iso_sym<double>(m.hc, m.ha, T, hs);
+                    else if (m.cubic)
+                        h_circle_cubic<double>(m.c12, m.c44, m.cd, m.Q, T, hs);
                     else
                         h_circle_sym<double, double>(mat->C, m.Q, T, hs);
                     const double ir2 = ir * ir;

@@ -26,6 +26,8 @@ struct DevMaterial {
     double hc;    // iso: 1 / (16 pi mu (1 - nu))
     double ha;    // iso: 3 - 4 nu
     double C[81]; // C_ijkl
+    int cubic;    // 1: cubic with axes along x, y, z (c12, c44, cd below are set)
+    double c12, c44, cd;  // C12, C44, C11 - C12 - 2 C44
 };
 
 // Geometry of the tree as kernels see it; the root box lives on the device
@@ -34,6 +36,17 @@ struct TreeBox {
     double origin[3];
     double H;      // root cube edge
     double lo[3], hi[3];
+};
+
+// learned angular factor (mlp.cu)
+struct MlpState {
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;  // FP32 masters, gradient, Adam moments
+    __nv_bfloat16 *theta_h = nullptr;  // BF16 copy used by the kernels
+    float *scale = nullptr;            // per-output scale [32]
+    float *loss = nullptr;
+    void *bufs = nullptr;              // batch activations
+    bool trained = false;
+    int64_t step = 0;
 };
 
 struct Timer {
@@ -61,6 +74,8 @@ struct gbfmm_ctx {
 
     // mixed-precision M2L on tensor cores
     TcPlan tc;
+    // learned h
+    MlpState mlp;
 
     // tree
     bool built = false;

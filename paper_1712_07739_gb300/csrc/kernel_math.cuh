@@ -30,6 +30,18 @@ __device__ __forceinline__ void h_iso_sym(R hc, R ha, const R T[3], R hs[18]) {
     }
 }
 
+// sin and cos of pi k / Q in the precision of the caller (no FP64 on the FP32 path)
+template <typename R>
+__device__ __forceinline__ void circle_point(int k, int Q, R *s, R *c);
+template <>
+__device__ __forceinline__ void circle_point<double>(int k, int Q, double *s, double *c) {
+    sincospi(double(k) / double(Q), s, c);
+}
+template <>
+__device__ __forceinline__ void circle_point<float>(int k, int Q, float *s, float *c) {
+    sincospif(float(k) / float(Q), s, c);
+}
+
 // (a b)_jk = a_i C_ijkl b_l
 template <typename R, typename CT>
 __device__ __forceinline__ void cmat(const CT *C, const R a[3], const R b[3], R M[9]) {
@@ -55,8 +67,8 @@ __device__ __forceinline__ void h_circle_sym(const CT *C, int Q, const R Tin[3],
     R T[3] = {Tin[0], Tin[1], Tin[2]};
     // e1: T with its smallest component replaced, orthogonalised; e2 = T x e1
     int k0 = 0;
-    if (fabs(double(T[1])) < fabs(double(T[k0]))) k0 = 1;
-    if (fabs(double(T[2])) < fabs(double(T[k0]))) k0 = 2;
+    if (fabs(T[1]) < fabs(T[k0])) k0 = 1;
+    if (fabs(T[2]) < fabs(T[k0])) k0 = 2;
     R e1[3] = {R(0), R(0), R(0)};
     e1[k0] = R(1);
     R d = e1[0] * T[0] + e1[1] * T[1] + e1[2] * T[2];
@@ -68,10 +80,10 @@ __device__ __forceinline__ void h_circle_sym(const CT *C, int Q, const R Tin[3],
 #pragma unroll
     for (int i = 0; i < 18; ++i) acc[i] = 0;
     for (int k = 0; k < Q; ++k) {
-        double s, c;
-        sincospi(double(k) / double(Q), &s, &c);
+        R s, c;
+        circle_point<R>(k, Q, &s, &c);
         R z[3];
-        for (int i = 0; i < 3; ++i) z[i] = R(c) * e1[i] + R(s) * e2[i];
+        for (int i = 0; i < 3; ++i) z[i] = c * e1[i] + s * e2[i];
         R M[9], ZT[9];
         cmat<R, CT>(C, z, z, M);
         cmat<R, CT>(C, z, T, ZT);
@@ -105,6 +117,71 @@ __device__ __forceinline__ void h_circle_sym(const CT *C, int Q, const R Tin[3],
         }
     }
     // 2 (pi / Q) / (8 pi^2) = 1 / (4 pi Q)
+    const R f = R(1.0 / (4.0 * 3.14159265358979323846 * double(Q)));
+#pragma unroll
+    for (int i = 0; i < 18; ++i) hs[i] = acc[i] * f;
+}
+
+// Cubic medium with crystal axes along x, y, z:
+// C_ijkl = C12 d_ij d_kl + C44 (d_ik d_jl + d_il d_jk) + D d_ijkl, D = C11 - C12 - 2 C44,
+// so (zz)_jk = (C12 + C44) z_j z_k + (C44 |z|^2 + D z_j^2) d_jk and, for z . T = 0,
+// (zT) + (Tz) = (C12 + C44) (z_j T_k + z_k T_j) + 2 D z_j T_j d_jk.
+// Same integral as h_circle_sym, about a third of the arithmetic.
+template <typename R>
+__device__ __forceinline__ void h_circle_cubic(R c12, R c44, R D, int Q, const R Tin[3], R hs[18]) {
+    R T[3] = {Tin[0], Tin[1], Tin[2]};
+    int k0 = 0;
+    if (fabs(T[1]) < fabs(T[k0])) k0 = 1;
+    if (fabs(T[2]) < fabs(T[k0])) k0 = 2;
+    R e1[3] = {R(0), R(0), R(0)};
+    e1[k0] = R(1);
+    R dd = e1[0] * T[0] + e1[1] * T[1] + e1[2] * T[2];
+    for (int i = 0; i < 3; ++i) e1[i] -= dd * T[i];
+    R nrm = R(1) / sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int i = 0; i < 3; ++i) e1[i] *= nrm;
+    R e2[3] = {T[1] * e1[2] - T[2] * e1[1], T[2] * e1[0] - T[0] * e1[2], T[0] * e1[1] - T[1] * e1[0]};
+    const R cp = c12 + c44;
+    R acc[18];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) acc[i] = 0;
+    for (int k = 0; k < Q; ++k) {
+        R sn, cs;
+        circle_point<R>(k, Q, &sn, &cs);
+        R z[3];
+        for (int i = 0; i < 3; ++i) z[i] = cs * e1[i] + sn * e2[i];
+        // M = (zz) (symmetric; |z| = 1)
+        const R m00 = cp * z[0] * z[0] + c44 + D * z[0] * z[0];
+        const R m11 = cp * z[1] * z[1] + c44 + D * z[1] * z[1];
+        const R m22 = cp * z[2] * z[2] + c44 + D * z[2] * z[2];
+        const R m01 = cp * z[0] * z[1], m02 = cp * z[0] * z[2], m12 = cp * z[1] * z[2];
+        // inverse by cofactors
+        const R i00 = m11 * m22 - m12 * m12, i01 = m02 * m12 - m01 * m22, i02 = m01 * m12 - m02 * m11;
+        const R i11 = m00 * m22 - m02 * m02, i12 = m01 * m02 - m00 * m12, i22 = m00 * m11 - m01 * m01;
+        const R idet = R(1) / (m00 * i00 + m01 * i01 + m02 * i02);
+        const R Mi[9] = {i00 * idet, i01 * idet, i02 * idet, i01 * idet, i11 * idet,
+                         i12 * idet, i02 * idet, i12 * idet, i22 * idet};
+        // S = (zT) + (Tz)
+        R S[9];
+        for (int j = 0; j < 3; ++j)
+            for (int l = 0; l < 3; ++l) S[j * 3 + l] = cp * (z[j] * T[l] + z[l] * T[j]);
+        for (int j = 0; j < 3; ++j) S[j * 3 + j] += R(2) * D * z[j] * T[j];
+        R tmp[9], F[9];
+        for (int j = 0; j < 3; ++j)
+            for (int l = 0; l < 3; ++l)
+                tmp[j * 3 + l] = Mi[j * 3] * S[l] + Mi[j * 3 + 1] * S[3 + l] + Mi[j * 3 + 2] * S[6 + l];
+        for (int j = 0; j < 3; ++j)
+            for (int l = j; l < 3; ++l)
+                F[j * 3 + l] = tmp[j * 3] * Mi[l] + tmp[j * 3 + 1] * Mi[3 + l] + tmp[j * 3 + 2] * Mi[6 + l];
+        constexpr int PV[6] = {0, 1, 2, 1, 0, 0};
+        constexpr int PP[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+        for (int pr = 0; pr < 6; ++pr) {
+            const int v = PV[pr], p = PP[pr];
+            const int vl = v < p ? v : p, ph = v < p ? p : v;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc[3 * pr + q] += -T[q] * Mi[v * 3 + p] + z[q] * F[vl * 3 + ph];
+        }
+    }
     const R f = R(1.0 / (4.0 * 3.14159265358979323846 * double(Q)));
 #pragma unroll
     for (int i = 0; i < 18; ++i) hs[i] = acc[i] * f;

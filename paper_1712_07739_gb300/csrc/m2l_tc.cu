@@ -166,11 +166,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Is any cell of the shifted source box occupied?  Brick flags are per level,
+// class and aligned 8 x 4 x 4 brick of the sub-grid; the box of a shift in
+// [-1, 1]^3 overlaps at most 2 x 2 x 2 aligned bricks.
+__device__ __forceinline__ bool source_occupied(const unsigned char *__restrict__ bocc, int m, int bx0, int by0,
+                                                int bz0, const OffsetEntry &e) {
+    const int nbx = (m + 7) / 8, nby = (m + 3) / 4, nbz = (m + 3) / 4;
+    const int x0 = bx0 + e.sx, y0 = by0 + e.sy, z0 = bz0 + e.sz;
+    const int ax0 = max(x0, 0) / 8, ax1 = min(x0 + 7, m - 1) / 8;
+    const int ay0 = max(y0, 0) / 4, ay1 = min(y0 + 3, m - 1) / 4;
+    const int az0 = max(z0, 0) / 4, az1 = min(z0 + 3, m - 1) / 4;
+    if (x0 + 7 < 0 || y0 + 3 < 0 || z0 + 3 < 0 || x0 >= m || y0 >= m || z0 >= m) return false;
+    for (int bz = az0; bz <= az1; ++bz)
+        for (int by = ay0; by <= ay1; ++by)
+            for (int bx = ax0; bx <= ax1; ++bx)
+                if (bocc[((int64_t(e.cls) * nbz + bz) * nby + by) * nbx + bx]) return true;
+    return false;
+}
+
 // number of K-block iterations of one work item (same count on every warp)
 __device__ __forceinline__ int passes_of(const OffsetEntry &e, int split) { return (split && e.lo >= 0) ? 3 : 1; }
 
 __global__ void __launch_bounds__(192, 1)
     k_m2l_tc(const __grid_constant__ M2LParams P, const int4 *__restrict__ work, const int *__restrict__ tocc,
+             const unsigned char *__restrict__ bocc_all, const int64_t *__restrict__ bocc_ofs,
              const TreeBox *__restrict__ box, float *__restrict__ S, int *__restrict__ status, int stages) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -186,6 +205,7 @@ __global__ void __launch_bounds__(192, 1)
     const int nbx = (m + 7) / 8, nby = (m + 3) / 4;
     const int bx0 = (brick % nbx) * 8, by0 = ((brick / nbx) % nby) * 4, bz0 = (brick / (nbx * nby)) * 4;
     const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
+    const unsigned char *bocc = bocc_all + bocc_ofs[level];
 
     // skip bricks without targets, and do no work once an earlier block's
     // time-out is flagged (both decided once for the whole block)
@@ -232,6 +252,7 @@ __global__ void __launch_bounds__(192, 1)
         bool ok = true;
         for (int oi = 0; oi < 189 && ok; ++oi) {
             const OffsetEntry e = c_offs[cls][oi];
+            if (!source_occupied(bocc, m, bx0, by0, bz0, e)) continue;
             const int np = passes_of(e, P.split);
             for (int pass = 0; pass < np && ok; ++pass) {
                 const CUtensorMap *ta = (pass == 1) ? &P.tmWlo[level] : &P.tmW[level];
@@ -262,6 +283,7 @@ __global__ void __launch_bounds__(192, 1)
         bool ok = true;
         for (int oi = 0; oi < 189 && ok; ++oi) {
             const OffsetEntry e = c_offs[cls][oi];
+            if (!source_occupied(bocc, m, bx0, by0, bz0, e)) continue;
             const int np = passes_of(e, P.split);
             for (int pass = 0; pass < np && ok; ++pass) {
                 for (int kb = 0; kb < P.kb; ++kb, ++it) {
@@ -287,6 +309,8 @@ __global__ void __launch_bounds__(192, 1)
         mma_commit(accb);  // fires when every MMA issued above has completed
     } else if (warp >= 2) {
         // ---------------- epilogue: TMEM -> scaled FP32 local values
+        bool any_src = false;
+        for (int oi = 0; oi < 189 && !any_src; ++oi) any_src = source_occupied(bocc, m, bx0, by0, bz0, c_offs[cls][oi]);
         const bool ok = mbar_wait(accb, 0, status);
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int q = warp % 4;
@@ -297,7 +321,11 @@ __global__ void __launch_bounds__(192, 1)
         const int64_t g = cell_base_d(level) + (int64_t(2 * pz + cz) * n + (2 * py + cy)) * n + (2 * px + cx);
         const float sc = float(double(n) / box->H) * float(double(n) / box->H);
         float *dst = S + g * int64_t(P.nvalid);
-        if (ok) {
+        if (ok && !any_src) {
+            // no occupied source anywhere in the interaction list: zero local values
+            if (valid)
+                for (int col = group * P.ncta; col < min(P.nvalid, (group + 1) * P.ncta); ++col) dst[col] = 0.f;
+        } else if (ok) {
             for (int j = 0; j < 3; ++j)
                 for (int c0 = 0; c0 < P.nsub; c0 += 16) {
                     float v[16];
@@ -366,6 +394,20 @@ __global__ void k_pack_w(int level, int P3, int Kp, const float *__restrict__ W,
         const __nv_bfloat16 h = __float2bfloat16(v);
         hi[dst] = h;
         lo[dst] = __float2bfloat16(v - __bfloat162float(h));
+    }
+}
+
+// brick flags: one byte per (class, aligned 8 x 4 x 4 brick) of a level
+__global__ void k_brick_occ(int level, const int *__restrict__ occ, unsigned char *__restrict__ bocc) {
+    const int n = 1 << level, m = n / 2;
+    const int nbx = (m + 7) / 8, nby = (m + 3) / 4, nbz = (m + 3) / 4;
+    const int64_t cells = int64_t(n) * n * n;
+    for (int64_t lin = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; lin < cells;
+         lin += int64_t(gridDim.x) * blockDim.x) {
+        if (occ[cell_base_d(level) + lin] == 0) continue;
+        const int x = int(lin % n), y = int((lin / n) % n), z = int(lin / (int64_t(n) * n));
+        const int cls = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+        bocc[((int64_t(cls) * nbz + (z / 2) / 4) * nby + (y / 2) / 4) * nbx + (x / 2) / 8] = 1;
     }
 }
 
@@ -512,6 +554,23 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
         CK(cudaMalloc(&T.Wlo, tot * 2));
         T.w_cap = tot;
     }
+    int64_t bocc_tot = 0;
+    std::vector<int64_t> bofs(GB_TC_MAXLEV, 0);
+    for (int l = 2; l < L; ++l) {
+        const int m = 1 << (l - 1);
+        bofs[l] = bocc_tot;
+        bocc_tot += int64_t(8) * ((m + 7) / 8) * ((m + 3) / 4) * ((m + 3) / 4);
+    }
+    if (bocc_tot > T.bocc_cap) {
+        if (T.d_bocc) cudaFree(T.d_bocc);
+        T.d_bocc = nullptr;
+        CK(cudaMalloc(&T.d_bocc, bocc_tot));
+        T.bocc_cap = bocc_tot;
+    }
+    T.bocc_tot = bocc_tot;
+    for (int l = 0; l < GB_TC_MAXLEV; ++l) T.bocc_h[l] = bofs[l];
+    if (!T.d_bocc_ofs) CK(cudaMalloc(&T.d_bocc_ofs, GB_TC_MAXLEV * sizeof(int64_t)));
+    CK(cudaMemcpy(T.d_bocc_ofs, bofs.data(), GB_TC_MAXLEV * sizeof(int64_t), cudaMemcpyHostToDevice));
     std::vector<int4> wl;
     for (int l = 2; l < L; ++l) {
         const int m = 1 << (l - 1);
@@ -550,6 +609,11 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
         rc = encode(ctx, &prm.tmWlo[l], T.Wlo + T.wofs[l], 5, dims, strides, boxd);
         if (rc) return rc;
     }
+    CK(cudaMemsetAsync(T.d_bocc, 0, T.bocc_tot, ctx->stream));
+    for (int l = 2; l < L; ++l) {
+        ++ctx->launches;
+        k_brick_occ<<<nblk(int64_t(1) << (3 * l), 256), 256, 0, ctx->stream>>>(l, occ, T.d_bocc + T.bocc_h[l]);
+    }
     {
         const cuuint64_t dims[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(T.n_off)};
         const cuuint64_t strides[2] = {cuuint64_t(T.Kp) * 2, cuuint64_t(T.Kp) * 2 * T.Np};
@@ -573,7 +637,8 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     const size_t smem = size_t(stages) * stage_bytes + 1024 + (2 * stages + 2) * 8 + 64;
     CK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     ++ctx->launches;
-    k_m2l_tc<<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_work, tocc, ctx->d_box, Sf, T.d_status, stages);
+    k_m2l_tc<<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_work, tocc, T.d_bocc, T.d_bocc_ofs, ctx->d_box, Sf,
+                                                   T.d_status, stages);
     CK(cudaGetLastError());
     return GBFMM_OK;
 }
@@ -590,7 +655,7 @@ int m2l_tc_status(gbfmm_ctx *ctx, int *out) {
 
 void m2l_tc_free(gbfmm_ctx *ctx) {
     TcPlan &T = ctx->tc;
-    void *ps[] = {T.Thi, T.Tlo, T.Whi, T.Wlo, T.d_work, T.d_status};
+    void *ps[] = {T.Thi, T.Tlo, T.Whi, T.Wlo, T.d_work, T.d_status, T.d_bocc, T.d_bocc_ofs};
     for (void *q : ps)
         if (q) cudaFree(q);
     T = TcPlan{};

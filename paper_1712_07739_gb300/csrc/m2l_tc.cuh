@@ -20,7 +20,11 @@ struct TcPlan {
     int4 *d_work = nullptr;
     int n_work = 0, work_cap = 0;
     int *d_status = nullptr;
-    int inject_drop = 0;       // set by fmm_inject_fault: the next run leaves one stage unfilled
+    int inject_drop = 0;
+    unsigned char *d_bocc = nullptr;  // occupied-brick flags, all levels
+    int64_t *d_bocc_ofs = nullptr;    // per-level offset into d_bocc
+    int64_t bocc_cap = 0, bocc_tot = 0;
+    int64_t bocc_h[GB_TC_MAXLEV] = {0};       // set by fmm_inject_fault: the next run leaves one stage unfilled
 };
 
 int m2l_tc_setup(gbfmm_ctx *ctx);    // operators (per medium and p)

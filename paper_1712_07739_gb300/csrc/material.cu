@@ -78,6 +78,8 @@ __global__ void k_lattice(const DevMaterial *mat, const double *Asym, int p, int
     double hs[18];
     if (mat->mode == GBFMM_H_ISO)
         h_iso_sym<double>(mat->hc, mat->ha, T, hs);
+    else if (mat->cubic)
+        h_circle_cubic<double>(mat->c12, mat->c44, mat->cd, mat->Q, T, hs);
     else
         h_circle_sym<double, double>(mat->C, mat->Q, T, hs);
     double ir2 = 1.0 / r2;
@@ -152,6 +154,23 @@ extern "C" int fmm_set_material(gbfmm_ctx *ctx, const double *V) {
     if (!positive_definite(V)) return set_err(ctx, GBFMM_ERR_DEGENERATE, "fmm_set_material: stiffness not positive definite");
     DevMaterial m{};
     voigt_to_full(V, m.C);
+    {
+        // cubic with axes along x, y, z: C11 = C22 = C33, C12 = C13 = C23, C44 = C55 = C66, rest 0
+        const double c11 = V[0], c12 = V[1], c44 = V[21];
+        const double sc = std::fabs(c11) + std::fabs(c12) + std::fabs(c44);
+        bool cub = true;
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                double want = 0.0;
+                if (i < 3 && j < 3) want = (i == j) ? c11 : c12;
+                if (i >= 3 && i == j) want = c44;
+                if (std::fabs(V[i * 6 + j] - want) > 1e-14 * sc) cub = false;
+            }
+        m.cubic = cub ? 1 : 0;
+        m.c12 = c12;
+        m.c44 = c44;
+        m.cd = c11 - c12 - 2.0 * c44;
+    }
     m.mode = ctx->opt.h_mode;
     m.Q = ctx->opt.circle_q > 0 ? ctx->opt.circle_q : 64;
     if (m.mode == GBFMM_H_ISO) {

@@ -133,11 +133,18 @@ __device__ __forceinline__ void pair_iso(const R d[3], R ir, const R *c, R acc[6
     }
 }
 
-template <typename R, typename CT>
-__device__ __forceinline__ void pair_generic(const R d[3], R ir, const R *c, const CT *C, int Q, R acc[6]) {
+// h models of the near kernel
+constexpr int HM_ISO = 0, HM_CUBIC = 1, HM_GENERIC = 2;
+
+template <int HM, typename R, typename CT>
+__device__ __forceinline__ void pair_generic(const R d[3], R ir, const R *c, const CT *C, int Q, R c12, R c44, R cd,
+                                             R acc[6]) {
     R T[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
     R hs[18];
-    h_circle_sym<R, CT>(C, Q, T, hs);
+    if (HM == HM_CUBIC)
+        h_circle_cubic<R>(c12, c44, cd, Q, T, hs);
+    else
+        h_circle_sym<R, CT>(C, Q, T, hs);
     const R ir2 = ir * ir;
 #pragma unroll
     for (int ab = 0; ab < 6; ++ab) {
@@ -150,9 +157,23 @@ __device__ __forceinline__ void pair_generic(const R d[3], R ir, const R *c, con
 
 constexpr int WARPS = 4;
 
-// NCS: per-source coefficient stride (80 isotropic, 108 generic); SCH
+// one close pair in FP64 (kept out of line so the FP32 pair loop keeps its registers)
+template <int HM>
+__device__ __noinline__ void close_pair_f64(const double *x, const double *y, const double *c, const DevMaterial *mat,
+                                            double *acc64) {
+    double dd[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+    const double rr = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+    if (rr == 0.0) return;
+    const double ir = rsqrt(rr);
+    if (HM == HM_ISO)
+        pair_iso<double>(dd, ir, c, acc64);
+    else
+        pair_generic<HM, double, double>(dd, ir, c, mat->C, mat->Q, mat->c12, mat->c44, mat->cd, acc64);
+}
+
+// NCS: per-source coefficient stride (80 isotropic, 108 otherwise); SCH
 // sources are staged per warp chunk (static shared memory stays < 48 KB)
-template <int NCS, int SCH>
+template <int HM, int NCS, int SCH>
 __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
     int p, int L, int64_t nl, float near2, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat,
     const int *__restrict__ tstart, const double *__restrict__ xt, const int64_t *__restrict__ tsid,
@@ -164,7 +185,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
     __shared__ int ssd[WARPS][SCH];
     __shared__ float sC[81];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (NCS == 108)
+    if (HM == HM_GENERIC)
         for (int i = threadIdx.x; i < 81; i += blockDim.x) sC[i] = float(mat->C[i]);
     __syncthreads();
     const int64_t leaf = blockIdx.x * int64_t(WARPS) + warp;
@@ -179,6 +200,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
     const double h = box->H / nlv, ih = double(nlv) / box->H;
     const double c0[3] = {box->origin[0] + cx * h, box->origin[1] + cy * h, box->origin[2] + cz * h};
     const int Q = mat->Q;
+    const float c12f = float(mat->c12), c44f = float(mat->c44), cdf = float(mat->cd);
     const float *Sl = S + (cell_base_d(L - 1) + leaf) * int64_t(P3) * 6;
     float *wP = sP[warp];
     float4 *wy = sy[warp];
@@ -242,21 +264,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
                     const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
                     if (r2 < near2 * yj.w * yj.w) {
                         const int64_t jj = j0 + j;
-                        double dd[3] = {x[0] - ys[3 * jj], x[1] - ys[3 * jj + 1], x[2] - ys[3 * jj + 2]};
-                        const double rr = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
-                        if (rr == 0.0) continue;
-                        const double ir = rsqrt(rr);
-                        if (NCS == 80)
-                            pair_iso<double>(dd, ir, c64 + 80 * jj, acc64);
-                        else
-                            pair_generic<double, double>(dd, ir, c64 + 108 * jj, mat->C, mat->Q, acc64);
+                        close_pair_f64<HM>(x, ys + 3 * jj, c64 + NCS * jj, mat, acc64);
                         continue;
                     }
                     const float ir = rsqrtf(r2);
-                    if (NCS == 80)
+                    if (HM == HM_ISO)
                         pair_iso<float>(d, ir, wP + 80 * j, acc);
                     else
-                        pair_generic<float, float>(d, ir, wP + 108 * j, sC, Q, acc);
+                        pair_generic<HM, float, float>(d, ir, wP + 108 * j, sC, Q, c12f, c44f, cdf, acc);
                 }
             }
         }
@@ -286,14 +301,17 @@ int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t 
     const int64_t nl = ctx->n_leaves;
     const float near2 = float(ctx->opt.near_fp64 * ctx->opt.near_fp64);
     ++ctx->launches;
+#define GB_NEAR_ARGS                                                                                           \
+    ctx->opt.p, ctx->L, nl, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, ctx->d_y, \
+        ctx->d_Pf, ctx->d_P, ctx->d_sid, ctx->d_Sf, sig
+    const unsigned grid = nblk(nl, WARPS);
     if (near_coef_count(ctx) == 80)
-        k_near_mixed<80, 32><<<nblk(nl, WARPS), WARPS * 32, 0, ctx->stream>>>(
-            ctx->opt.p, ctx->L, nl, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel,
-            ctx->d_y, ctx->d_Pf, ctx->d_P, ctx->d_sid, ctx->d_Sf, sig);
+        k_near_mixed<HM_ISO, 80, 32><<<grid, WARPS * 32, 0, ctx->stream>>>(GB_NEAR_ARGS);
+    else if (ctx->mat.cubic)
+        k_near_mixed<HM_CUBIC, 108, 24><<<grid, WARPS * 32, 0, ctx->stream>>>(GB_NEAR_ARGS);
     else
-        k_near_mixed<108, 24><<<nblk(nl, WARPS), WARPS * 32, 0, ctx->stream>>>(
-            ctx->opt.p, ctx->L, nl, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel,
-            ctx->d_y, ctx->d_Pf, ctx->d_P, ctx->d_sid, ctx->d_Sf, sig);
+        k_near_mixed<HM_GENERIC, 108, 24><<<grid, WARPS * 32, 0, ctx->stream>>>(GB_NEAR_ARGS);
+#undef GB_NEAR_ARGS
     CK(cudaGetLastError());
     return GBFMM_OK;
 }

@@ -177,6 +177,22 @@ def ensemble(n_configs=64, ns_range=(10_000, 200_000), density_range=(0.2, 5.0),
     return out
 
 
+def directions(n=2_000_000, near_frac=0.2, spread_deg=5.0, seed=3):
+    """Unit directions for training the angular network: a fraction uniform on
+    the sphere, the rest scattered (angular Gaussian, spread_deg) about the
+    6 <100> and 8 <111> axes of the cubic crystal.  float32 [n, 3]."""
+    rng = np.random.default_rng(seed)
+    n_near = int(round(n * near_frac))
+    u = rng.normal(size=(n - n_near, 3))
+    axes = np.concatenate([np.eye(3), -np.eye(3),
+                           np.array([[a, b, c] for a in (-1, 1) for b in (-1, 1) for c in (-1, 1)]) / np.sqrt(3.0)])
+    pick = axes[rng.integers(len(axes), size=n_near)]
+    v = pick + rng.normal(scale=np.deg2rad(spread_deg), size=(n_near, 3))
+    d = np.concatenate([u, v])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return d[rng.permutation(n)].astype(np.float32)
+
+
 def config(name: str):
     """Named workloads: c1 (2,000 iso), c2 (50,000 cubic), c3 (1M slabs)."""
     if name == "c1":

@@ -1,0 +1,105 @@
+"""The learned angular factor: GPU BF16 training and inference kernels vs the
+FP64 CPU reference network, and the trained network vs the plain evaluator.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp_ref
+from paper_1712_07739_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CUB = synth.cubic_voigt()
+
+
+def _bf16(a):
+    t = torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64)
+    return t.numpy()
+
+
+def _ctx():
+    import paper_1712_07739_gb300 as gb
+
+    return gb.FMM(p=3, levels=3, precision="mixed", h_mode="circle", circle_q=64).set_material(CUB)
+
+
+def _params(seed=0):
+    rng = np.random.default_rng(seed)
+    th = np.zeros(mlp_ref.N_PARAMS)
+    o = 0
+    for name, shp in mlp_ref.SIZES:
+        n = int(np.prod(shp))
+        fan = shp[1] if len(shp) == 2 else 128
+        th[o:o + n] = rng.normal(scale=np.sqrt(2.0 / fan), size=n) if len(shp) == 2 else rng.normal(scale=0.1, size=n)
+        o += n
+    d = mlp_ref.unpack(th)
+    d["W4"][27:] = 0.0
+    d["b4"][27:] = 0.0
+    return mlp_ref.pack(d).astype(np.float32), rng.uniform(0.02, 0.08, 27).astype(np.float32)
+
+
+def _rounded(theta):
+    """CPU view of the GPU's parameters: BF16 weight matrices, FP32 biases."""
+    d = mlp_ref.unpack(theta.astype(np.float64))
+    for k in ("W1", "W2", "W3", "W4"):
+        d[k] = _bf16(d[k])
+    return mlp_ref.pack(d)
+
+
+def test_labels_match_oracle():
+    f = _ctx()
+    dirs = synth.directions(500, seed=5)
+    y = f.mlp_labels(torch.tensor(dirs, device="cuda")).cpu().numpy()
+    C = oracle.voigt_to_cijkl(CUB)
+    ref = np.array([oracle.h_circle(C, t.astype(np.float64), 64).reshape(27) for t in dirs])
+    assert np.max(np.abs(y - ref)) <= 1e-6 * np.abs(ref).max()
+
+
+def test_forward_matches_cpu_reference():
+    f = _ctx()
+    theta, scale = _params(1)
+    f.mlp_set(theta, scale)
+    dirs = synth.directions(2000, seed=6)
+    h = f.mlp_eval(torch.tensor(dirs, device="cuda")).cpu().numpy()
+    ref, _ = mlp_ref.forward(_rounded(theta), dirs.astype(np.float64), scale)
+    err = np.linalg.norm(h - ref) / np.linalg.norm(ref)
+    print("forward GPU vs CPU:", err)
+    assert err < 2e-2  # BF16 activations between layers
+
+
+def test_gradients_match_cpu_reference():
+    f = _ctx()
+    theta, scale = _params(2)
+    f.mlp_set(theta, scale)
+    dirs = synth.directions(1024, seed=7)
+    rng = np.random.default_rng(8)
+    y = rng.normal(scale=0.05, size=(1024, 27)).astype(np.float32)
+    g, loss = f.mlp_grad(torch.tensor(dirs, device="cuda"), torch.tensor(y, device="cuda"))
+    g = g.cpu().numpy().astype(np.float64)
+    l_ref, g_ref = mlp_ref.loss_and_grad(_rounded(theta), dirs.astype(np.float64), y.astype(np.float64), scale)
+    assert abs(loss - l_ref) <= 2e-2 * l_ref
+    o = 0
+    for name, shp in mlp_ref.SIZES:
+        n = int(np.prod(shp))
+        a, b = g[o:o + n], g_ref[o:o + n]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        print(f"grad {name}: {rel:.3e}")
+        assert rel < 5e-2, name
+        o += n
+
+
+def test_training_reduces_error():
+    f = _ctx()
+    dirs = torch.tensor(synth.directions(400_000, seed=9), device="cuda")
+    loss = f.mlp_train(dirs, epochs=25, batch=4096, lr=3e-3, seed=1)
+    test = torch.tensor(synth.directions(20_000, seed=10), device="cuda")
+    h = f.mlp_eval(test).cpu().numpy()
+    y = f.mlp_labels(test).cpu().numpy()
+    err = np.sqrt(np.mean((h - y) ** 2)) / np.sqrt(np.mean(y ** 2))
+    print("trained network relative RMS error:", err, "loss", loss)
+    assert err < 5e-2
+    # odd by construction
+    h2 = f.mlp_eval(-test).cpu().numpy()
+    assert np.array_equal(h2, -h)
