@@ -217,6 +217,28 @@ int fmm_mlp_eval(gbfmm_ctx *ctx, int64_t n, const float *dirs, float *h);
  * synchronises when given). */
 int fmm_mlp_grad(gbfmm_ctx *ctx, int n, const float *dirs, const float *y, float *grad, float *loss);
 
+/* Network h at n directions without allocating device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * must not allocate during the call -- a dislocation-dynamics code that
+ * evaluates h from inside its own fixed memory pool or a time step it
+ * replays, or one that runs under a device-memory budget it manages itself.
+ * Results equal those of fmm_mlp_eval.  Instead of per-context buffers it
+ * uses one statically allocated device array of 4.5 MiB (activations of
+ * 4,096 directions; larger n is processed 4,096 at a time), which every
+ * GPU that loads this library holds until the process exits.
+ *
+ * dirs: device, float [n][3]; h: device, float [n][27]; n <= 2^24, larger
+ * n returns GBFMM_ERR_INVALID_ARG with a message.  Call it with the
+ * context's device current.  The first call on a device looks up the
+ * array's device address (no allocation); make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams, other
+ * contexts on the same device, other host threads) race and must be
+ * serialised by the caller.  Errors: INVALID_ARG (sizes, pointers, network
+ * not set), CUDA. */
+int fmm_mlp_eval_noalloc(gbfmm_ctx *ctx, int64_t n, const float *dirs, float *h);
+
 #ifdef __cplusplus
 }
 #endif

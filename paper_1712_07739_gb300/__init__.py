@@ -31,6 +31,7 @@ EXPORTS = [
     "fmm_tree_info", "fmm_set_timing", "fmm_stage_times", "fmm_launch_count", "fmm_work_counts",
     "fmm_device_status", "fmm_inject_fault",
     "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
+    "fmm_mlp_eval_noalloc",
 ]
 MLP_PARAMS = 37664
 
@@ -84,7 +85,8 @@ def load_library(path: str = LIB_PATH):
     L.fmm_mlp_eval.argtypes = [vp, i64, dp, dp]
     L.fmm_mlp_grad.argtypes = [vp, ctypes.c_int, dp, dp, dp, fp]
     L.fmm_mlp_labels.argtypes = [vp, i64, dp, dp]
-    for name in ("fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
+    L.fmm_mlp_eval_noalloc.argtypes = [vp, i64, dp, dp]
+    for name in ("fmm_mlp_eval_noalloc", "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
                  "fmm_inject_fault", "fmm_device_status", "fmm_launch_count", "fmm_work_counts", "fmm_create", "fmm_set_material", "fmm_build_tree", "fmm_eval_stress",
                  "fmm_eval_nodal_forces", "fmm_tree_info", "fmm_set_timing", "fmm_stage_times"):
         getattr(L, name).restype = ctypes.c_int
@@ -248,6 +250,14 @@ class FMM:
         h = self._torch.empty((dirs.shape[0], 27), dtype=self._torch.float32, device=dirs.device)
         self._check(self._lib.fmm_mlp_eval(self._h, dirs.shape[0], _ptr(dirs), _ptr(h)), "fmm_mlp_eval")
         return h
+
+    def mlp_eval_noalloc(self, dirs, out):
+        """Network h into a caller-provided tensor, with no device allocation
+        in the library (scratch is a static device array)."""
+        dirs = self._f32(dirs)
+        self._check(self._lib.fmm_mlp_eval_noalloc(self._h, dirs.shape[0], _ptr(dirs), _ptr(out)),
+                    "fmm_mlp_eval_noalloc")
+        return out
 
     def mlp_grad(self, dirs, y):
         dirs, y = self._f32(dirs), self._f32(y)

@@ -540,3 +540,70 @@ void mlp_free(gbfmm_ctx *ctx) {
     }
     M = MlpState{};
 }
+
+// ---------------------------------------------------------------- no-allocation evaluation
+// fmm_mlp_eval_noalloc: the network evaluation of fmm_mlp_eval for callers
+// that must not allocate device memory during the call (see gbfmm.h).  The
+// activations live in one file-scope device array; its device address is
+// looked up once per device.
+#define GB_NOALLOC_CHUNK 4096                      // directions per pass over the scratch
+#define GB_NOALLOC_MAX (int64_t(1) << 24)          // largest n accepted per call
+static constexpr size_t kNoallocZ = size_t(GB_NOALLOC_CHUNK) * 128 * sizeof(float);   // pre-activations
+static constexpr size_t kNoallocA = size_t(GB_NOALLOC_CHUNK) * 128 * sizeof(bf16);    // one activation buffer
+static constexpr size_t kNoallocO = size_t(GB_NOALLOC_CHUNK) * 32 * sizeof(float);    // outputs
+static constexpr size_t kNoallocBytes = kNoallocZ + 2 * kNoallocA + kNoallocO;         // 4.5 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+static unsigned char *noalloc_base(gbfmm_ctx *ctx) {
+    // one lookup per device, made with that device current (the context's)
+    static unsigned char *base[64] = {nullptr};
+    const int dev = ctx->device;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != dev || dev < 0 || dev >= 64) return nullptr;
+    if (!base[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+        base[dev] = static_cast<unsigned char *>(p);
+    }
+    return base[dev];
+}
+
+extern "C" int fmm_mlp_eval_noalloc(gbfmm_ctx *ctx, int64_t n, const float *dirs, float *h) {
+    if (!ctx) return GBFMM_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!dirs || !h)))
+        return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_mlp_eval_noalloc: bad arguments");
+    if (n > GB_NOALLOC_MAX)
+        return set_err(ctx, GBFMM_ERR_INVALID_ARG,
+                       "fmm_mlp_eval_noalloc: n = " + std::to_string(n) + " exceeds the maximum of " +
+                           std::to_string(GB_NOALLOC_MAX) + " directions per call");
+    if (!ctx->mlp.trained) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_mlp_eval_noalloc: network not set");
+    if (n == 0) return GBFMM_OK;
+    unsigned char *base = noalloc_base(ctx);
+    if (!base)
+        return set_err(ctx, GBFMM_ERR_CUDA,
+                       "fmm_mlp_eval_noalloc: scratch address lookup failed (is the context's device current?)");
+    float *z = reinterpret_cast<float *>(base);
+    bf16 *a = reinterpret_cast<bf16 *>(base + kNoallocZ);
+    bf16 *b = reinterpret_cast<bf16 *>(base + kNoallocZ + kNoallocA);
+    float *o = reinterpret_cast<float *>(base + kNoallocZ + 2 * kNoallocA);
+    cudaStream_t st = ctx->stream;
+    const MlpState &M = ctx->mlp;
+    const bf16 *th = M.theta_h;
+    const float *bias = M.theta;
+    for (int64_t b0 = 0; b0 < n; b0 += GB_NOALLOC_CHUNK) {
+        const int nb = int(std::min<int64_t>(GB_NOALLOC_CHUNK, n - b0));
+        const int64_t e = int64_t(nb) * 128;
+        const float *d = dirs + 3 * b0;
+        ctx->launches += 7;
+        k_layer1<<<nblk(e, 256), 256, 0, st>>>(nb, d, th, bias, nullptr, nullptr, a);
+        gemm(st, nb, 128, 128, a, 128, 1, th + OFF_W2, 1, 128, bias + OFF_B2, z, 128);
+        k_silu<<<nblk(e, 256), 256, 0, st>>>(e, z, b);
+        gemm(st, nb, 128, 128, b, 128, 1, th + OFF_W3, 1, 128, bias + OFF_B3, z, 128);
+        k_silu<<<nblk(e, 256), 256, 0, st>>>(e, z, a);
+        gemm(st, nb, 32, 128, a, 128, 1, th + OFF_W4, 1, 128, bias + OFF_B4, o, 32);
+        k_output<<<nblk(int64_t(nb) * 27, 256), 256, 0, st>>>(nb, d, o, M.scale, h + 27 * b0);
+    }
+    CK(cudaGetLastError());
+    return GBFMM_OK;
+}
