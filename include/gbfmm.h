@@ -65,9 +65,12 @@ typedef struct {
     int leaf_segments;     /* with levels == 0: target mean segments per occupied leaf; 0 = 32 */
     double near_fp64;      /* MIXED: near pairs closer than near_fp64 x (source segment length)
                               are evaluated in FP64; 0 = 2.0 */
-    int m2l_split;         /* MIXED: BF16 residual (split) passes of the tensor-core M2L:
-                              0 = on the offsets with max |o_i| = 2 (default), 1 = none,
-                              2 = on all 316 offsets */
+    int m2l_split;         /* MIXED: operand precision of the tensor-core M2L:
+                              0 = BF16 with residual (split) passes on the offsets with
+                              max |o_i| = 2 (default), 1 = BF16 only, 2 = BF16 with residual
+                              passes on all 316 offsets, 3 = TF32 (FP32 operands) */
+    double mlp_min_dist;   /* GBFMM_H_MLP: near pairs closer than this many source segment
+                              lengths use the plain evaluator; 0 = 8 */
 } gbfmm_options;
 
 typedef struct gbfmm_ctx gbfmm_ctx;
@@ -204,6 +207,15 @@ int fmm_mlp_labels(gbfmm_ctx *ctx, int64_t n, const float *dirs, float *y);
  * Errors: NO_MATERIAL, INVALID_ARG, CUDA. */
 int fmm_mlp_train(gbfmm_ctx *ctx, int64_t n, const float *dirs, int epochs, int batch, double lr,
                   uint64_t seed, float *final_loss);
+
+/* Judge the network against the plain evaluator per angular bin (5 x 256
+ * bins of direction, 64 sample directions each) and record which bins the
+ * near field of GBFMM_H_MLP must evaluate with the plain rule: those whose
+ * largest component error exceeds bin_tol x (RMS of h).  fallback_frac
+ * (host, may be NULL): fraction of bins flagged.  Required before a
+ * GBFMM_H_MLP evaluation.  Synchronises the stream.
+ * Errors: INVALID_ARG (network not set), NO_MATERIAL, CUDA. */
+int fmm_mlp_calibrate(gbfmm_ctx *ctx, double bin_tol, double *fallback_frac);
 
 /* Copy the parameters (host, 37,664 floats) and output scales (host, 27). */
 int fmm_mlp_get(gbfmm_ctx *ctx, float *theta, float *scale);

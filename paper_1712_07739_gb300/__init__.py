@@ -31,7 +31,7 @@ EXPORTS = [
     "fmm_tree_info", "fmm_set_timing", "fmm_stage_times", "fmm_launch_count", "fmm_work_counts",
     "fmm_device_status", "fmm_inject_fault",
     "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
-    "fmm_mlp_eval_noalloc",
+    "fmm_mlp_eval_noalloc", "fmm_mlp_calibrate",
 ]
 MLP_PARAMS = 37664
 
@@ -41,6 +41,7 @@ class Options(ctypes.Structure):
         ("p", ctypes.c_int), ("n_gauss", ctypes.c_int), ("levels", ctypes.c_int),
         ("precision", ctypes.c_int), ("h_mode", ctypes.c_int), ("circle_q", ctypes.c_int),
         ("leaf_segments", ctypes.c_int), ("near_fp64", ctypes.c_double), ("m2l_split", ctypes.c_int),
+        ("mlp_min_dist", ctypes.c_double),
     ]
 
 
@@ -86,7 +87,8 @@ def load_library(path: str = LIB_PATH):
     L.fmm_mlp_grad.argtypes = [vp, ctypes.c_int, dp, dp, dp, fp]
     L.fmm_mlp_labels.argtypes = [vp, i64, dp, dp]
     L.fmm_mlp_eval_noalloc.argtypes = [vp, i64, dp, dp]
-    for name in ("fmm_mlp_eval_noalloc", "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
+    L.fmm_mlp_calibrate.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    for name in ("fmm_mlp_calibrate", "fmm_mlp_eval_noalloc", "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
                  "fmm_inject_fault", "fmm_device_status", "fmm_launch_count", "fmm_work_counts", "fmm_create", "fmm_set_material", "fmm_build_tree", "fmm_eval_stress",
                  "fmm_eval_nodal_forces", "fmm_tree_info", "fmm_set_timing", "fmm_stage_times"):
         getattr(L, name).restype = ctypes.c_int
@@ -107,7 +109,7 @@ class FMM:
     """
 
     def __init__(self, p=4, n_gauss=4, levels=0, precision="fp64", h_mode="iso", circle_q=0,
-                 leaf_segments=0, near_fp64=0.0, m2l_split=0, stream=None):
+                 leaf_segments=0, near_fp64=0.0, m2l_split=0, mlp_min_dist=0.0, stream=None):
         import torch
 
         self._torch = torch
@@ -119,6 +121,7 @@ class FMM:
         o.h_mode = _HMODE[h_mode] if isinstance(h_mode, str) else int(h_mode)
         o.circle_q, o.leaf_segments, o.near_fp64 = circle_q, leaf_segments, near_fp64
         o.m2l_split = m2l_split
+        o.mlp_min_dist = mlp_min_dist
         self.options = o
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -230,6 +233,13 @@ class FMM:
         self._check(self._lib.fmm_mlp_train(self._h, dirs.shape[0], _ptr(dirs), int(epochs), int(batch), float(lr),
                                             int(seed), ctypes.byref(loss)), "fmm_mlp_train")
         return loss.value
+
+    def mlp_calibrate(self, bin_tol=2e-2):
+        """Flag the angular bins where the network's error exceeds bin_tol x RMS(h);
+        returns the flagged fraction."""
+        fr = ctypes.c_double()
+        self._check(self._lib.fmm_mlp_calibrate(self._h, float(bin_tol), ctypes.byref(fr)), "fmm_mlp_calibrate")
+        return fr.value
 
     def mlp_get(self):
         th = np.zeros(MLP_PARAMS, np.float32)

@@ -127,7 +127,7 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
         (opt->levels != 0 && (opt->levels < 3 || opt->levels > 9)) ||
         (opt->precision != GBFMM_FP64 && opt->precision != GBFMM_MIXED) || opt->h_mode < 0 || opt->h_mode > 2 ||
         opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0) || opt->m2l_split < 0 ||
-        opt->m2l_split > 2)
+        opt->m2l_split > 3)
         return GBFMM_ERR_INVALID_ARG;
     gbfmm_ctx *ctx = new gbfmm_ctx();
     ctx->opt = *opt;

@@ -45,6 +45,8 @@ struct MlpState {
     float *scale = nullptr;            // per-output scale [32]
     float *loss = nullptr;
     void *bufs = nullptr;              // batch activations
+    uint32_t *d_binmask = nullptr;     // [48] angular bins where the plain evaluator is used
+    double fallback_frac = 1.0;        // fraction of bins flagged by the last calibration
     bool trained = false;
     int64_t step = 0;
 };

@@ -187,6 +187,63 @@ __device__ __forceinline__ void h_circle_cubic(R c12, R c44, R D, int Q, const R
     for (int i = 0; i < 18; ++i) hs[i] = acc[i] * f;
 }
 
+// FP32 form of h_circle_cubic for the near-field loop: scalar registers only,
+// the points (cos, sin)(pi k / Q) of the half circle from a table.
+__device__ __forceinline__ void h_cubic_f32(float cp, float c44, float D, int Q, const float2 *__restrict__ tab,
+                                            const float T[3], float hs[18]) {
+    const float T0 = T[0], T1 = T[1], T2 = T[2];
+    int k0 = 0;
+    if (fabsf(T1) < fabsf(T0)) k0 = 1;
+    if (fabsf(T2) < fabsf(k0 == 0 ? T0 : T1)) k0 = 2;
+    float a0 = k0 == 0 ? 1.f : 0.f, a1 = k0 == 1 ? 1.f : 0.f, a2 = k0 == 2 ? 1.f : 0.f;
+    const float dd = a0 * T0 + a1 * T1 + a2 * T2;
+    a0 -= dd * T0;
+    a1 -= dd * T1;
+    a2 -= dd * T2;
+    const float nr = rsqrtf(a0 * a0 + a1 * a1 + a2 * a2);
+    const float e10 = a0 * nr, e11 = a1 * nr, e12 = a2 * nr;
+    const float e20 = T1 * e12 - T2 * e11, e21 = T2 * e10 - T0 * e12, e22 = T0 * e11 - T1 * e10;
+    const float cpD = cp + D, cpD2 = 2.f * (cp + D);
+    float acc[18];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) acc[i] = 0.f;
+    for (int k = 0; k < Q; ++k) {
+        const float2 t = tab[k];
+        const float z0 = t.x * e10 + t.y * e20, z1 = t.x * e11 + t.y * e21, z2 = t.x * e12 + t.y * e22;
+        const float m00 = fmaf(cpD, z0 * z0, c44), m11 = fmaf(cpD, z1 * z1, c44), m22 = fmaf(cpD, z2 * z2, c44);
+        const float m01 = cp * z0 * z1, m02 = cp * z0 * z2, m12 = cp * z1 * z2;
+        float i00 = m11 * m22 - m12 * m12, i01 = m02 * m12 - m01 * m22, i02 = m01 * m12 - m02 * m11;
+        float i11 = m00 * m22 - m02 * m02, i12 = m01 * m02 - m00 * m12, i22 = m00 * m11 - m01 * m01;
+        const float idet = __frcp_rn(m00 * i00 + m01 * i01 + m02 * i02);
+        i00 *= idet; i01 *= idet; i02 *= idet; i11 *= idet; i12 *= idet; i22 *= idet;
+        const float s00 = cpD2 * z0 * T0, s11 = cpD2 * z1 * T1, s22 = cpD2 * z2 * T2;
+        const float s01 = cp * (z0 * T1 + z1 * T0), s02 = cp * (z0 * T2 + z2 * T0), s12 = cp * (z1 * T2 + z2 * T1);
+        // U = Mi S, F = U Mi (symmetric)
+        const float u00 = i00 * s00 + i01 * s01 + i02 * s02, u01 = i00 * s01 + i01 * s11 + i02 * s12,
+                    u02 = i00 * s02 + i01 * s12 + i02 * s22;
+        const float u10 = i01 * s00 + i11 * s01 + i12 * s02, u11 = i01 * s01 + i11 * s11 + i12 * s12,
+                    u12 = i01 * s02 + i11 * s12 + i12 * s22;
+        const float u20 = i02 * s00 + i12 * s01 + i22 * s02, u21 = i02 * s01 + i12 * s11 + i22 * s12,
+                    u22 = i02 * s02 + i12 * s12 + i22 * s22;
+        const float F00 = u00 * i00 + u01 * i01 + u02 * i02, F01 = u00 * i01 + u01 * i11 + u02 * i12,
+                    F02 = u00 * i02 + u01 * i12 + u02 * i22;
+        const float F11 = u10 * i01 + u11 * i11 + u12 * i12, F12 = u10 * i02 + u11 * i12 + u12 * i22,
+                    F22 = u20 * i02 + u21 * i12 + u22 * i22;
+        // pairs (00) (11) (22) (12) (02) (01), each with q = 0, 1, 2
+        const float Mp[6] = {i00, i11, i22, i12, i02, i01};
+        const float Fp[6] = {F00, F11, F22, F12, F02, F01};
+#pragma unroll
+        for (int pr = 0; pr < 6; ++pr) {
+            acc[3 * pr + 0] += z0 * Fp[pr] - T0 * Mp[pr];
+            acc[3 * pr + 1] += z1 * Fp[pr] - T1 * Mp[pr];
+            acc[3 * pr + 2] += z2 * Fp[pr] - T2 * Mp[pr];
+        }
+    }
+    const float f = 1.f / (4.f * 3.14159265358979f * float(Q));
+#pragma unroll
+    for (int i = 0; i < 18; ++i) hs[i] = acc[i] * f;
+}
+
 // Lagrange basis on the p equispaced nodes t_a = a / (p - 1) of [0, 1]
 // (Sec. 4.1 footnote): ell_a(t) = prod_{b != a} (t - t_b) / (t_a - t_b).
 template <typename R>

@@ -62,6 +62,8 @@ struct M2LParams {
     int tmem_cols;  // power of two >= ncta
     int split;      // residual passes on the near offsets
     int drop_first; // failure-detection test: arm the first stage but issue no load into it
+    int kstep;      // operand elements per 128-byte row: 64 (bf16) or 32 (tf32)
+    uint32_t idesc; // tcgen05 instruction descriptor
 };
 
 constexpr int kStageA = 128 * 64 * 2;  // 16 KB
@@ -138,16 +140,26 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
     return d;
 }
 
-// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+// instruction descriptor: D f32 (bits 4-5 = 1), A and B format (bits 7-9,
+// 10-12: 1 = bf16 for kind::f16, 2 = tf32 for kind::tf32), both K-major,
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28
+inline uint32_t idesc_of(int M, int N, bool tf32) {
+    const uint32_t f = tf32 ? 2u : 1u;
+    return (1u << 4) | (f << 7) | (f << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+template <bool TF32>
+__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (TF32)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -187,6 +199,7 @@ __device__ __forceinline__ bool source_occupied(const unsigned char *__restrict_
 // number of K-block iterations of one work item (same count on every warp)
 __device__ __forceinline__ int passes_of(const OffsetEntry &e, int split) { return (split && e.lo >= 0) ? 3 : 1; }
 
+template <bool TF32>
 __global__ void __launch_bounds__(192, 1)
     k_m2l_tc(const __grid_constant__ M2LParams P, const int4 *__restrict__ work, const int *__restrict__ tocc,
              const unsigned char *__restrict__ bocc_all, const int64_t *__restrict__ bocc_ofs,
@@ -269,16 +282,16 @@ __global__ void __launch_bounds__(192, 1)
                     mbar_expect_tx(fb, kStageA + stageB);
                     if (P.drop_first && it == 0) continue;  // the MMA warp's wait on this stage runs out
                     const uint32_t a = smem0 + s * stage_bytes;
-                    tma_load_5d(a, ta, kb * 64, bx0 + e.sx, by0 + e.sy, bz0 + e.sz, e.cls, fb);
+                    tma_load_5d(a, ta, kb * P.kstep, bx0 + e.sx, by0 + e.sy, bz0 + e.sz, e.cls, fb);
                     for (int j = 0; j < 3; ++j)
-                        tma_load_3d(a + kStageA + j * P.nsub * 128, tb, kb * 64, group * P.ncta + j * P.nsub, tidx,
-                                    fb);
+                        tma_load_3d(a + kStageA + j * P.nsub * 128, tb, kb * P.kstep, group * P.ncta + j * P.nsub,
+                                    tidx, fb);
                 }
             }
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
-        const uint32_t idesc = idesc_bf16(128, P.nsub);
+        const uint32_t idesc = P.idesc;
         int it = 0;
         bool ok = true;
         for (int oi = 0; oi < 189 && ok; ++oi) {
@@ -299,7 +312,7 @@ __global__ void __launch_bounds__(192, 1)
                         const uint64_t ad = sw128_desc(a + kk * 32);
                         for (int j = 0; j < 3; ++j) {
                             const uint64_t bd = sw128_desc(a + kStageA + j * P.nsub * 128 + kk * 32);
-                            mma_bf16(tmem + j * P.nsub, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                            mma_issue<TF32>(tmem + j * P.nsub, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
                         }
                     }
                     mma_commit(empty0 + 8 * s);
@@ -348,9 +361,23 @@ __global__ void __launch_bounds__(192, 1)
 // ---------------------------------------------------------------- operators
 // T_o[n = l*6 + ab][k = m*9 + wr] = Klat[o (p-1) + l - m][ab][wr] (unit cell);
 // hi = bf16(T), lo = bf16(T - hi) (residual table only for split offsets).
+template <typename E>
+__device__ __forceinline__ E to_elem(double v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_elem<__nv_bfloat16>(double v) {
+    return __double2bfloat16(v);
+}
+template <>
+__device__ __forceinline__ float to_elem<float>(double v) {
+    return float(v);
+}
+__device__ __forceinline__ double elem_value(__nv_bfloat16 x) { return double(__bfloat162float(x)); }
+__device__ __forceinline__ double elem_value(float x) { return double(x); }
+
+template <typename E>
 __global__ void k_build_ops(int p, int lat_n, int Np, int Kp, const double *__restrict__ Klat,
                             const int *__restrict__ off_xyz, const int *__restrict__ lo_of, int n_off,
-                            __nv_bfloat16 *__restrict__ Thi, __nv_bfloat16 *__restrict__ Tlo) {
+                            E *__restrict__ Thi, E *__restrict__ Tlo) {
     const int64_t total = int64_t(n_off) * Np * Kp;
     const int P3 = p * p * p;
     const int R0 = (lat_n - 1) / 2;
@@ -368,16 +395,17 @@ __global__ void k_build_ops(int p, int lat_n, int Np, int Kp, const double *__re
             const int Dz = oz * (p - 1) + (l / (p * p)) - (mm / (p * p)) + R0;
             v = Klat[((int64_t(Dz) * lat_n + Dy) * lat_n + Dx) * 54 + ab * 9 + wr];
         }
-        const __nv_bfloat16 hi = __double2bfloat16(v);
+        const E hi = to_elem<E>(v);
         Thi[idx] = hi;
         const int li = lo_of[o];
-        if (li >= 0) Tlo[(int64_t(li) * Np + nn) * Kp + k] = __double2bfloat16(v - double(__bfloat162float(hi)));
+        if (li >= 0 && Tlo) Tlo[(int64_t(li) * Np + nn) * Kp + k] = to_elem<E>(v - elem_value(hi));
     }
 }
 
 // W (FP32, [cell][p^3 * 9]) -> parity-split BF16 hi / lo, [class][mz][my][mx][Kp] per level
+template <typename E>
 __global__ void k_pack_w(int level, int P3, int Kp, const float *__restrict__ W, const int *__restrict__ occ,
-                         __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+                         E *__restrict__ hi, E *__restrict__ lo) {
     const int n = 1 << level, m = n / 2;
     const int64_t cells = int64_t(n) * n * n;
     const int64_t total = cells * Kp;
@@ -391,9 +419,9 @@ __global__ void k_pack_w(int level, int P3, int Kp, const float *__restrict__ W,
         const int64_t g = cell_base_d(level) + lin;
         float v = 0.f;
         if (k < 9 * P3 && occ[g] > 0) v = W[g * 9 * P3 + k];
-        const __nv_bfloat16 h = __float2bfloat16(v);
+        const E h = to_elem<E>(double(v));
         hi[dst] = h;
-        lo[dst] = __float2bfloat16(v - __bfloat162float(h));
+        if (lo) lo[dst] = to_elem<E>(double(v) - elem_value(h));
     }
 }
 
@@ -435,6 +463,8 @@ inline unsigned nblk(int64_t n, int b) { return unsigned(std::min<int64_t>((n + 
 int m2l_tc_setup(gbfmm_ctx *ctx) {
     const int p = ctx->opt.p, P3 = p * p * p;
     TcPlan &T = ctx->tc;
+    T.tf32 = ctx->opt.m2l_split == 3 ? 1 : 0;
+    T.esz = T.tf32 ? 4 : 2;
     T.Kp = ((9 * P3 + 63) / 64) * 64;
     // N per MMA: multiple of 16, three of them per block, 3 nsub <= 512 TMEM columns
     const int nv = 6 * P3;
@@ -465,7 +495,7 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
                 off.push_back(ox);
                 off.push_back(oy);
                 off.push_back(oz);
-                const bool split = ctx->opt.m2l_split == 2 || (ctx->opt.m2l_split == 0 && mx == 2);
+                const bool split = !T.tf32 && (ctx->opt.m2l_split == 2 || (ctx->opt.m2l_split == 0 && mx == 2));
                 lo_of.push_back(split ? n_lo++ : -1);
             }
     T.n_off = int(off.size() / 3);
@@ -508,12 +538,17 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     if (T.Thi) cudaFree(T.Thi);
     if (T.Tlo) cudaFree(T.Tlo);
     T.Thi = T.Tlo = nullptr;
-    CK(cudaMalloc(&T.Thi, hi_elems * 2));
-    CK(cudaMalloc(&T.Tlo, std::max<size_t>(lo_elems, 1) * 2));
+    CK(cudaMalloc(&T.Thi, hi_elems * T.esz));
+    CK(cudaMalloc(&T.Tlo, std::max<size_t>(lo_elems, 1) * T.esz));
     T.split = n_lo > 0 ? 1 : 0;
     ++ctx->launches;
-    k_build_ops<<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off,
-                                                                         d_lo, T.n_off, T.Thi, T.Tlo);
+    if (T.tf32)
+        k_build_ops<float><<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(
+            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, T.n_off, (float *)T.Thi, (float *)nullptr);
+    else
+        k_build_ops<__nv_bfloat16><<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(
+            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, T.n_off, (__nv_bfloat16 *)T.Thi,
+            (__nv_bfloat16 *)T.Tlo);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
     cudaFree(d_off);
@@ -525,11 +560,12 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
 }
 
 static int encode(gbfmm_ctx *ctx, CUtensorMap *tm, void *base, int rank, const cuuint64_t *dims,
-                  const cuuint64_t *strides, const cuuint32_t *boxd) {
+                  const cuuint64_t *strides, const cuuint32_t *boxd, bool f32) {
     EncodeTiled enc = get_encoder();
     if (!enc) return set_err(ctx, GBFMM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, cuuint32_t(rank), base, dims, strides, boxd, es,
+    CUresult r = enc(tm, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, cuuint32_t(rank),
+                     base, dims, strides, boxd, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_err(ctx, GBFMM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
@@ -550,8 +586,8 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
         if (T.Whi) cudaFree(T.Whi);
         if (T.Wlo) cudaFree(T.Wlo);
         T.Whi = T.Wlo = nullptr;
-        CK(cudaMalloc(&T.Whi, tot * 2));
-        CK(cudaMalloc(&T.Wlo, tot * 2));
+        CK(cudaMalloc(&T.Whi, tot * T.esz));
+        CK(cudaMalloc(&T.Wlo, tot * T.esz));
         T.w_cap = tot;
     }
     int64_t bocc_tot = 0;
@@ -599,14 +635,19 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
         const int m = 1 << (l - 1);
         ++ctx->launches;
         const int64_t el = (int64_t(1) << (3 * l)) * T.Kp;
-        k_pack_w<<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, T.Whi + T.wofs[l], T.Wlo + T.wofs[l]);
+        void *whi = (char *)T.Whi + T.wofs[l] * T.esz, *wlo = (char *)T.Wlo + T.wofs[l] * T.esz;
+        if (T.tf32)
+            k_pack_w<float><<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, (float *)whi, (float *)nullptr);
+        else
+            k_pack_w<__nv_bfloat16><<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, (__nv_bfloat16 *)whi,
+                                                                             (__nv_bfloat16 *)wlo);
         const cuuint64_t dims[5] = {cuuint64_t(T.Kp), cuuint64_t(m), cuuint64_t(m), cuuint64_t(m), 8};
-        const cuuint64_t row = cuuint64_t(T.Kp) * 2;
+        const cuuint64_t row = cuuint64_t(T.Kp) * T.esz;
         const cuuint64_t strides[4] = {row, row * m, row * m * m, row * m * m * m};
-        const cuuint32_t boxd[5] = {64, 8, 4, 4, 1};
-        int rc = encode(ctx, &prm.tmW[l], T.Whi + T.wofs[l], 5, dims, strides, boxd);
+        const cuuint32_t boxd[5] = {cuuint32_t(128 / T.esz), 8, 4, 4, 1};
+        int rc = encode(ctx, &prm.tmW[l], whi, 5, dims, strides, boxd, T.tf32);
         if (rc) return rc;
-        rc = encode(ctx, &prm.tmWlo[l], T.Wlo + T.wofs[l], 5, dims, strides, boxd);
+        rc = encode(ctx, &prm.tmWlo[l], wlo, 5, dims, strides, boxd, T.tf32);
         if (rc) return rc;
     }
     CK(cudaMemsetAsync(T.d_bocc, 0, T.bocc_tot, ctx->stream));
@@ -616,15 +657,17 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     }
     {
         const cuuint64_t dims[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(T.n_off)};
-        const cuuint64_t strides[2] = {cuuint64_t(T.Kp) * 2, cuuint64_t(T.Kp) * 2 * T.Np};
-        const cuuint32_t boxd[3] = {64, cuuint32_t(T.nsub), 1};
-        int rc = encode(ctx, &prm.tmT, T.Thi, 3, dims, strides, boxd);
+        const cuuint64_t strides[2] = {cuuint64_t(T.Kp) * T.esz, cuuint64_t(T.Kp) * T.esz * T.Np};
+        const cuuint32_t boxd[3] = {cuuint32_t(128 / T.esz), cuuint32_t(T.nsub), 1};
+        int rc = encode(ctx, &prm.tmT, T.Thi, 3, dims, strides, boxd, T.tf32);
         if (rc) return rc;
         const cuuint64_t dl[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(std::max(T.n_lo, 1))};
-        rc = encode(ctx, &prm.tmTlo, T.Tlo, 3, dl, strides, boxd);
+        rc = encode(ctx, &prm.tmTlo, T.Tlo, 3, dl, strides, boxd, T.tf32);
         if (rc) return rc;
     }
-    prm.kb = T.Kp / 64;
+    prm.kstep = 128 / T.esz;
+    prm.kb = T.Kp / prm.kstep;
+    prm.idesc = idesc_of(128, T.nsub, T.tf32);
     prm.nsub = T.nsub;
     prm.ncta = T.ncta;
     prm.nvalid = 6 * P3;
@@ -635,10 +678,16 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     const int stage_bytes = 128 * 64 * 2 + T.ncta * 128;
     int stages = std::max(2, std::min(6, (200 * 1024) / stage_bytes));
     const size_t smem = size_t(stages) * stage_bytes + 1024 + (2 * stages + 2) * 8 + 64;
-    CK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     ++ctx->launches;
-    k_m2l_tc<<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_work, tocc, T.d_bocc, T.d_bocc_ofs, ctx->d_box, Sf,
-                                                   T.d_status, stages);
+    if (T.tf32) {
+        CK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_m2l_tc<true><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_work, tocc, T.d_bocc, T.d_bocc_ofs, ctx->d_box,
+                                                             Sf, T.d_status, stages);
+    } else {
+        CK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_m2l_tc<false><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_work, tocc, T.d_bocc, T.d_bocc_ofs, ctx->d_box,
+                                                              Sf, T.d_status, stages);
+    }
     CK(cudaGetLastError());
     return GBFMM_OK;
 }

@@ -13,8 +13,10 @@ struct TcPlan {
     int nsub = 0, ncta = 0, groups = 0, tmem_cols = 0;
     int n_off = 0, n_lo = 0;   // operators and residual operators
     int split = 1;             // residual passes on offsets with max |o_i| = 2
-    __nv_bfloat16 *Thi = nullptr, *Tlo = nullptr;
-    __nv_bfloat16 *Whi = nullptr, *Wlo = nullptr;
+    int tf32 = 0;              // operands in FP32 storage, MMA kind::tf32 (no residual passes)
+    int esz = 2;               // operand element size in bytes
+    void *Thi = nullptr, *Tlo = nullptr;  // operators [n_off][Np][Kp] (bf16, or fp32 when tf32)
+    void *Whi = nullptr, *Wlo = nullptr;  // packed multipole weights
     int64_t wofs[GB_TC_MAXLEV] = {0};
     int64_t w_cap = 0;
     int4 *d_work = nullptr;

@@ -34,9 +34,16 @@ constexpr int OFF_W1 = 0, OFF_B1 = 384, OFF_W2 = 512, OFF_B2 = 16896, OFF_W3 = 1
 
 inline unsigned nblk(int64_t n, int b) { return unsigned(std::min<int64_t>((n + b - 1) / b, 1 << 22)); }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+// SiLU through the hardware tanh (the same form the near-field kernel uses):
+// sigmoid(z) = (1 + tanh(z/2)) / 2, silu = z sigmoid(z), silu' = s (1 + z (1 - s))
+__device__ __forceinline__ float tanh_hw(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float silu(float z) { return 0.5f * z * (1.f + tanh_hw(0.5f * z)); }
 __device__ __forceinline__ float dsilu(float z) {
-    const float s = 1.f / (1.f + __expf(-z));
+    const float s = 0.5f * (1.f + tanh_hw(0.5f * z));
     return s * (1.f + z * (1.f - s));
 }
 
@@ -526,9 +533,72 @@ extern "C" int fmm_mlp_train(gbfmm_ctx *ctx, int64_t n, const float *dirs, int e
     return GBFMM_OK;
 }
 
+// Judge the network per angular bin against the plain evaluator: 64 directions
+// per bin of the near-field kernel's binning (dominant axis face +z, +x, -x,
+// +y, -y and a 16 x 16 grid of the other two components); a bin whose largest
+// component error exceeds bin_tol x (RMS of h over all samples) is flagged
+// and its pairs take the plain evaluator.
+extern "C" int fmm_mlp_calibrate(gbfmm_ctx *ctx, double bin_tol, double *fallback_frac) {
+    if (!ctx || !(bin_tol > 0.0)) return GBFMM_ERR_INVALID_ARG;
+    if (!ctx->mlp.trained) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_mlp_calibrate: train or set the network first");
+    const int nb = 5 * 256, per = 64;
+    std::vector<float> dirs(size_t(nb) * per * 3);
+    for (int b = 0; b < nb; ++b) {
+        const int f = b / 256, bu = (b / 16) % 16, bv = b % 16;
+        for (int i = 0; i < per; ++i) {
+            const float u = -1.f + 2.f * (bu + (i % 8 + 0.5f) / 8.f) / 16.f;
+            const float v = -1.f + 2.f * (bv + (i / 8 + 0.5f) / 8.f) / 16.f;
+            float d[3];
+            if (f == 0) { d[0] = u; d[1] = v; d[2] = 1.f; }
+            else if (f <= 2) { d[0] = f == 1 ? 1.f : -1.f; d[1] = u; d[2] = v; }
+            else { d[0] = u; d[1] = f == 3 ? 1.f : -1.f; d[2] = v; }
+            const float n = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            for (int c = 0; c < 3; ++c) dirs[(size_t(b) * per + i) * 3 + c] = d[c] / n;
+        }
+    }
+    const int64_t n = int64_t(nb) * per;
+    float *dd = nullptr, *y = nullptr, *hm = nullptr;
+    CK(cudaMalloc(&dd, n * 3 * sizeof(float)));
+    CK(cudaMalloc(&y, n * 27 * sizeof(float)));
+    CK(cudaMalloc(&hm, n * 27 * sizeof(float)));
+    CK(cudaMemcpy(dd, dirs.data(), n * 3 * sizeof(float), cudaMemcpyHostToDevice));
+    int rc = fmm_mlp_labels(ctx, n, dd, y);
+    if (rc) return rc;
+    rc = mlp_eval_device(ctx, n, dd, hm);
+    if (rc) return rc;
+    std::vector<float> hy(n * 27), hh(n * 27);
+    CK(cudaMemcpyAsync(hy.data(), y, n * 27 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hh.data(), hm, n * 27 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(dd);
+    cudaFree(y);
+    cudaFree(hm);
+    double ss = 0.0;
+    for (float v : hy) ss += double(v) * v;
+    const double rms = std::sqrt(ss / double(hy.size()));
+    uint32_t mask[48] = {0};
+    int flagged = 0;
+    for (int b = 0; b < nb; ++b) {
+        double e = 0.0;
+        for (int i = 0; i < per * 27; ++i) {
+            const size_t k = size_t(b) * per * 27 + i;
+            e = std::max(e, std::fabs(double(hh[k]) - double(hy[k])));
+        }
+        if (e > bin_tol * rms) {
+            mask[b >> 5] |= 1u << (b & 31);
+            ++flagged;
+        }
+    }
+    if (!ctx->mlp.d_binmask) CK(cudaMalloc(&ctx->mlp.d_binmask, sizeof(mask)));
+    CK(cudaMemcpy(ctx->mlp.d_binmask, mask, sizeof(mask), cudaMemcpyHostToDevice));
+    ctx->mlp.fallback_frac = double(flagged) / double(nb);
+    if (fallback_frac) *fallback_frac = ctx->mlp.fallback_frac;
+    return GBFMM_OK;
+}
+
 void mlp_free(gbfmm_ctx *ctx) {
     MlpState &M = ctx->mlp;
-    void *ps[] = {M.theta, M.grad, M.m, M.v, M.theta_h, M.scale, M.loss};
+    void *ps[] = {M.theta, M.grad, M.m, M.v, M.theta_h, M.scale, M.loss, M.d_binmask};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (M.bufs) {

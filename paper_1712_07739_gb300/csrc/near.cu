@@ -23,6 +23,7 @@
 
 #include "internal.cuh"
 #include "kernel_math.cuh"
+#include "mlp_warp.cuh"
 
 namespace {
 
@@ -138,13 +139,17 @@ constexpr int HM_ISO = 0, HM_CUBIC = 1, HM_GENERIC = 2;
 
 template <int HM, typename R, typename CT>
 __device__ __forceinline__ void pair_generic(const R d[3], R ir, const R *c, const CT *C, int Q, R c12, R c44, R cd,
-                                             R acc[6]) {
+                                             R acc[6], const float2 *tab = nullptr) {
     R T[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
     R hs[18];
-    if (HM == HM_CUBIC)
-        h_circle_cubic<R>(c12, c44, cd, Q, T, hs);
-    else
+    if (HM == HM_CUBIC) {
+        if constexpr (sizeof(R) == 4)
+            h_cubic_f32(c12 + c44, c44, cd, Q, tab, T, hs);
+        else
+            h_circle_cubic<R>(c12, c44, cd, Q, T, hs);
+    } else {
         h_circle_sym<R, CT>(C, Q, T, hs);
+    }
     const R ir2 = ir * ir;
 #pragma unroll
     for (int ab = 0; ab < 6; ++ab) {
@@ -156,20 +161,6 @@ __device__ __forceinline__ void pair_generic(const R d[3], R ir, const R *c, con
 }
 
 constexpr int WARPS = 4;
-
-// one close pair in FP64 (kept out of line so the FP32 pair loop keeps its registers)
-template <int HM>
-__device__ __noinline__ void close_pair_f64(const double *x, const double *y, const double *c, const DevMaterial *mat,
-                                            double *acc64) {
-    double dd[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
-    const double rr = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
-    if (rr == 0.0) return;
-    const double ir = rsqrt(rr);
-    if (HM == HM_ISO)
-        pair_iso<double>(dd, ir, c, acc64);
-    else
-        pair_generic<HM, double, double>(dd, ir, c, mat->C, mat->Q, mat->c12, mat->c44, mat->cd, acc64);
-}
 
 // NCS: per-source coefficient stride (80 isotropic, 108 otherwise); SCH
 // sources are staged per warp chunk (static shared memory stays < 48 KB)
@@ -184,9 +175,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
     __shared__ float4 sy[WARPS][SCH];
     __shared__ int ssd[WARPS][SCH];
     __shared__ float sC[81];
+    __shared__ float2 sTab[128];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (HM == HM_GENERIC)
         for (int i = threadIdx.x; i < 81; i += blockDim.x) sC[i] = float(mat->C[i]);
+    if (HM == HM_CUBIC)
+        for (int i = threadIdx.x; i < mat->Q && i < 128; i += blockDim.x) {
+            float sn, cs;
+            sincospif(float(i) / float(mat->Q), &sn, &cs);
+            sTab[i] = make_float2(cs, sn);
+        }
     __syncthreads();
     const int64_t leaf = blockIdx.x * int64_t(WARPS) + warp;
     if (leaf >= nl) return;
@@ -206,8 +204,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
     float4 *wy = sy[warp];
     int *wsd = ssd[warp];
     for (int r0 = t0; r0 < t1; r0 += 32) {
-        const int t = r0 + lane;
-        const bool valid = t < t1;
+        // tg targets this round, 32 / tg lanes per target splitting the sources
+        const int nrem = min(32, t1 - r0);
+        int tg = 1;
+        while (tg < nrem) tg <<= 1;
+        const int ls = 32 / tg, tl = lane % tg, ph = lane / tg;
+        const int t = r0 + tl;
+        const bool valid = tl < nrem;
         double x[3] = {0, 0, 0};
         float xr[3] = {0.f, 0.f, 0.f};
         float acc[6] = {0, 0, 0, 0, 0, 0};
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
             }
             myseg = tsid ? int(tsid[t]) : -1;
         }
-        if (far) {
+        if (far && ph == 0) {
             float bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
             lagrange_1d<float>(p, float((x[0] - c0[0]) * ih), bx);
             lagrange_1d<float>(p, float((x[1] - c0[1]) * ih), by);
@@ -257,25 +260,317 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
                 }
                 __syncwarp();
                 if (!valid) continue;
-                for (int j = 0; j < nj; ++j) {
+                for (int j = ph; j < nj; j += ls) {
                     if (wsd[j] == myseg) continue;
                     const float4 yj = wy[j];
                     float d[3] = {xs[0] - yj.x, xs[1] - yj.y, xs[2] - yj.z};
                     const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    if (r2 < near2 * yj.w * yj.w) {
+                    // A close pair takes its separation from the FP64 positions (the
+                    // FP32 difference would cancel) and goes to its own FP64
+                    // accumulator; the kernel itself is evaluated in FP32 on that
+                    // separation, whose relative error is then ~1e-7.
+                    const bool close = r2 < near2 * yj.w * yj.w;
+                    float ir;
+                    if (close) {
                         const int64_t jj = j0 + j;
-                        close_pair_f64<HM>(x, ys + 3 * jj, c64 + NCS * jj, mat, acc64);
-                        continue;
+                        const double dd0 = x[0] - ys[3 * jj], dd1 = x[1] - ys[3 * jj + 1], dd2 = x[2] - ys[3 * jj + 2];
+                        const double rr = dd0 * dd0 + dd1 * dd1 + dd2 * dd2;
+                        if (rr == 0.0) continue;
+                        d[0] = float(dd0);
+                        d[1] = float(dd1);
+                        d[2] = float(dd2);
+                        ir = float(rsqrt(rr));
+                    } else {
+                        ir = rsqrtf(r2);
                     }
-                    const float ir = rsqrtf(r2);
+                    float part[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     if (HM == HM_ISO)
-                        pair_iso<float>(d, ir, wP + 80 * j, acc);
+                        pair_iso<float>(d, ir, wP + 80 * j, part);
                     else
-                        pair_generic<HM, float, float>(d, ir, wP + 108 * j, sC, Q, c12f, c44f, cdf, acc);
+                        pair_generic<HM, float, float>(d, ir, wP + 108 * j, sC, Q, c12f, c44f, cdf, part, sTab);
+                    if (close) {
+#pragma unroll
+                        for (int ab = 0; ab < 6; ++ab) acc64[ab] += double(part[ab]);
+                    } else {
+#pragma unroll
+                        for (int ab = 0; ab < 6; ++ab) acc[ab] += part[ab];
+                    }
                 }
             }
         }
-        if (valid)
+        // fold the lanes that shared a target (fixed order: deterministic)
+        for (int off = tg; off < 32; off <<= 1)
+            for (int ab = 0; ab < 6; ++ab) {
+                acc[ab] += __shfl_xor_sync(0xffffffffu, acc[ab], off);
+                acc64[ab] += __shfl_xor_sync(0xffffffffu, acc64[ab], off);
+            }
+        if (valid && ph == 0)
+            for (int ab = 0; ab < 6; ++ab) sig[6 * int64_t(t) + ab] = double(acc[ab]) + acc64[ab];
+    }
+}
+
+// ---------------------------------------------------------------- near field with the learned h
+// Angular bin of a folded direction (upper half-space): dominant axis face
+// (+z, +x, -x, +y, -y) and a 16 x 16 grid of the two other components.
+__device__ __forceinline__ int dir_bin(float x, float y, float z) {
+    const float ax = fabsf(x), ay = fabsf(y), az = fabsf(z);
+    int f;
+    float u, v, m;
+    if (az >= ax && az >= ay) {
+        f = 0, u = x, v = y, m = az;
+    } else if (ax >= ay) {
+        f = x > 0.f ? 1 : 2, u = y, v = z, m = ax;
+    } else {
+        f = y > 0.f ? 3 : 4, u = x, v = z, m = ay;
+    }
+    const int bu = min(15, max(0, int((u / m + 1.f) * 8.f)));
+    const int bv = min(15, max(0, int((v / m + 1.f) * 8.f)));
+    return f * 256 + bu * 16 + bv;
+}
+
+constexpr int MSCH = 16;  // sources staged per warp chunk in the network kernel
+
+// Pairs at distance >= rmin x (source segment length) whose direction lies in
+// an angular bin the plain evaluator accepted use the network; the rest take
+// the plain path of k_near_mixed (FP32 cubic or generic rule, FP64
+// separation for close pairs).  Network pairs are queued per warp and
+// evaluated sixteen at a time by warp MMAs; every queued contribution is
+// added by the lane that queued it, in queue order (deterministic).
+template <bool CUBIC>
+__global__ void __launch_bounds__(WARPS * 32) k_near_mlp(
+    int p, int L, int64_t nl, float near2, float rmin2, const TreeBox *__restrict__ box,
+    const DevMaterial *__restrict__ mat, const int *__restrict__ tstart, const double *__restrict__ xt,
+    const int64_t *__restrict__ tsid, const int *__restrict__ sstart, const float4 *__restrict__ yrel,
+    const double *__restrict__ ys, const float *__restrict__ c32, const int64_t *__restrict__ ssid,
+    const float *__restrict__ S, double *__restrict__ sig, const __nv_bfloat16 *__restrict__ th,
+    const float *__restrict__ th32, const float *__restrict__ hscale, const uint32_t *__restrict__ binmask) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    mlpw::Weights &Wt = *reinterpret_cast<mlpw::Weights *>(dsm);
+    __shared__ __align__(16) float sP[WARPS][MSCH * 108];
+    __shared__ float4 sy[WARPS][MSCH];
+    __shared__ int ssd[WARPS][MSCH];
+    __shared__ float4 qd[WARPS][48];
+    __shared__ int qj[WARPS][48], ql[WARPS][48];
+    __shared__ float qc[WARPS][16][6];
+    __shared__ float sC[81];
+    __shared__ float2 sTab[128];
+    __shared__ uint32_t sBin[48];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int g = lane >> 2, tq = lane & 3;
+    mlpw::load(Wt, th, th32, hscale);
+    for (int i = threadIdx.x; i < 81; i += blockDim.x) sC[i] = float(mat->C[i]);
+    for (int i = threadIdx.x; i < mat->Q && i < 128; i += blockDim.x) {
+        float sn, cs;
+        sincospif(float(i) / float(mat->Q), &sn, &cs);
+        sTab[i] = make_float2(cs, sn);
+    }
+    for (int i = threadIdx.x; i < 48; i += blockDim.x) sBin[i] = binmask[i];
+    __syncthreads();
+    const int64_t leaf = blockIdx.x * int64_t(WARPS) + warp;
+    if (leaf >= nl) return;
+    const int t0 = tstart[leaf], t1 = tstart[leaf + 1];
+    if (t0 == t1) return;
+    const int P3 = p * p * p;
+    const int nlv = 1 << (L - 1);
+    int cx, cy, cz;
+    cell_xyz3(leaf, nlv, cx, cy, cz);
+    const bool far = L >= 3;
+    const double h = box->H / nlv, ih = double(nlv) / box->H;
+    const double c0[3] = {box->origin[0] + cx * h, box->origin[1] + cy * h, box->origin[2] + cz * h};
+    const int Q = mat->Q;
+    const float c12f = float(mat->c12), c44f = float(mat->c44), cdf = float(mat->cd);
+    const float *Sl = S + (cell_base_d(L - 1) + leaf) * int64_t(P3) * 6;
+    float *wP = sP[warp];
+    float4 *wy = sy[warp];
+    int *wsd = ssd[warp];
+    float4 *wq = qd[warp];
+    int *wj = qj[warp], *wl = ql[warp];
+    float(*wc)[6] = qc[warp];
+    for (int r0 = t0; r0 < t1; r0 += 32) {
+        const int nrem = min(32, t1 - r0);
+        int tg = 1;
+        while (tg < nrem) tg <<= 1;
+        const int ls = 32 / tg, tl = lane % tg, ph = lane / tg;
+        const int t = r0 + tl;
+        const bool valid = tl < nrem;
+        double x[3] = {0, 0, 0};
+        float xr[3] = {0.f, 0.f, 0.f};
+        float acc[6] = {0, 0, 0, 0, 0, 0};
+        double acc64[6] = {0, 0, 0, 0, 0, 0};
+        int myseg = -1;
+        if (valid) {
+            for (int d = 0; d < 3; ++d) {
+                x[d] = xt[3 * int64_t(t) + d];
+                xr[d] = float(x[d] - (c0[d] + 0.5 * h));
+            }
+            myseg = tsid ? int(tsid[t]) : -1;
+        }
+        if (far && ph == 0) {
+            float bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
+            lagrange_1d<float>(p, float((x[0] - c0[0]) * ih), bx);
+            lagrange_1d<float>(p, float((x[1] - c0[1]) * ih), by);
+            lagrange_1d<float>(p, float((x[2] - c0[2]) * ih), bz);
+            for (int lz = 0; lz < p; ++lz)
+                for (int ly = 0; ly < p; ++ly) {
+                    const float wyz = by[ly] * bz[lz];
+                    for (int lx = 0; lx < p; ++lx) {
+                        const float w = bx[lx] * wyz;
+                        const float *s6 = Sl + ((lz * p + ly) * p + lx) * 6;
+                        for (int ab = 0; ab < 6; ++ab) acc[ab] += w * __ldg(s6 + ab);
+                    }
+                }
+        }
+        int qn = 0;  // queued network pairs (warp-uniform)
+        for (int nb = 0; nb < 27; ++nb) {
+            const int dxn = nb % 3 - 1, dyn = (nb / 3) % 3 - 1, dzn = nb / 9 - 1;
+            const int ax = cx + dxn, ay = cy + dyn, az = cz + dzn;
+            if (ax < 0 || ay < 0 || az < 0 || ax >= nlv || ay >= nlv || az >= nlv) continue;
+            const int64_t A = (int64_t(az) * nlv + ay) * nlv + ax;
+            const int s0 = sstart[A], s1 = sstart[A + 1];
+            const float xs[3] = {xr[0] - float(dxn * h), xr[1] - float(dyn * h), xr[2] - float(dzn * h)};
+            for (int j0 = s0; j0 < s1; j0 += MSCH) {
+                const int nj = min(MSCH, s1 - j0);
+                __syncwarp();
+                if (lane < nj) {
+                    wy[lane] = yrel[j0 + lane];
+                    wsd[lane] = int(ssid[j0 + lane]);
+                }
+                {
+                    const float4 *src = reinterpret_cast<const float4 *>(c32 + int64_t(108) * j0);
+                    float4 *dst = reinterpret_cast<float4 *>(wP);
+                    for (int i = lane; i < nj * 27; i += 32) dst[i] = __ldg(src + i);
+                }
+                __syncwarp();
+                const int nit = (nj + ls - 1) / ls;
+                for (int it = 0; it < nit; ++it) {
+                    const int j = ph + it * ls;
+                    bool eligible = false;
+                    float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (valid && j < nj && wsd[j] != myseg) {
+                        const float4 yj = wy[j];
+                        float d[3] = {xs[0] - yj.x, xs[1] - yj.y, xs[2] - yj.z};
+                        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        const bool close = r2 < near2 * yj.w * yj.w;
+                        bool ok = true;
+                        float ir;
+                        if (close) {
+                            const int64_t jj = j0 + j;
+                            const double dd0 = x[0] - ys[3 * jj], dd1 = x[1] - ys[3 * jj + 1], dd2 = x[2] - ys[3 * jj + 2];
+                            const double rr = dd0 * dd0 + dd1 * dd1 + dd2 * dd2;
+                            ok = rr != 0.0;
+                            d[0] = float(dd0);
+                            d[1] = float(dd1);
+                            d[2] = float(dd2);
+                            ir = ok ? float(rsqrt(rr)) : 0.f;
+                        } else {
+                            ir = rsqrtf(r2);
+                        }
+                        if (ok) {
+                            const float T0 = d[0] * ir, T1 = d[1] * ir, T2 = d[2] * ir;
+                            const float sg = mlpw::fold_sign(T0, T1, T2);
+                            const int bin = dir_bin(sg * T0, sg * T1, sg * T2);
+                            const bool net = !close && r2 >= rmin2 * yj.w * yj.w && !((sBin[bin >> 5] >> (bin & 31)) & 1u);
+                            if (net) {
+                                eligible = true;
+                                qv = make_float4(T0, T1, T2, ir * ir);
+                            } else {
+                                float part[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                                if (CUBIC)
+                                    pair_generic<HM_CUBIC, float, float>(d, ir, wP + 108 * j, sC, Q, c12f, c44f, cdf,
+                                                                         part, sTab);
+                                else
+                                    pair_generic<HM_GENERIC, float, float>(d, ir, wP + 108 * j, sC, Q, c12f, c44f,
+                                                                           cdf, part, sTab);
+                                if (close) {
+                                    for (int ab = 0; ab < 6; ++ab) acc64[ab] += double(part[ab]);
+                                } else {
+                                    for (int ab = 0; ab < 6; ++ab) acc[ab] += part[ab];
+                                }
+                            }
+                        }
+                    }
+                    // enqueue this iteration's network pairs in lane order
+                    const unsigned m = __ballot_sync(0xffffffffu, eligible);
+                    if (eligible) {
+                        const int pos = qn + __popc(m & ((1u << lane) - 1u));
+                        wq[pos] = qv;
+                        wj[pos] = j;
+                        wl[pos] = lane;
+                    }
+                    qn += __popc(m);
+                    __syncwarp();
+                    // evaluate full tiles of 16 (and the remainder at the chunk's end)
+                    while (qn >= 16 || (qn > 0 && it == nit - 1)) {
+                        const int nrow = min(16, qn);
+                        const bool vlo = g < nrow, vhi = g + 8 < nrow;
+                        const float4 ql4 = vlo ? wq[g] : make_float4(0.f, 0.f, 1.f, 0.f);
+                        const float4 qh4 = vhi ? wq[g + 8] : make_float4(0.f, 0.f, 1.f, 0.f);
+                        const float slo = mlpw::fold_sign(ql4.x, ql4.y, ql4.z);
+                        const float shi = mlpw::fold_sign(qh4.x, qh4.y, qh4.z);
+                        const float dlo[3] = {slo * ql4.x, slo * ql4.y, slo * ql4.z};
+                        const float dhi[3] = {shi * qh4.x, shi * qh4.y, shi * qh4.z};
+                        float olo[8], ohi[8];
+                        mlpw::eval16(Wt, dlo, dhi, g, tq, olo, ohi);
+                        float plo[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, phi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                        const float *Plo = wP + 108 * (vlo ? wj[g] : 0), *Phi = wP + 108 * (vhi ? wj[g + 8] : 0);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int col = 8 * (e >> 1) + 2 * tq + (e & 1);
+                            if (col >= 27) continue;
+                            const int v = col / 9, pp = (col / 3) % 3, q = col % 3;
+                            constexpr int PIX[9] = {0, 5, 4, 5, 1, 3, 4, 3, 2};
+                            const int k = 3 * PIX[v * 3 + pp] + q;
+                            const float wgt = (v == pp ? 1.f : 0.5f) * Wt.scale[col];
+                            const float hl = olo[e] * wgt * slo, hh = ohi[e] * wgt * shi;
+#pragma unroll
+                            for (int ab = 0; ab < 6; ++ab) {
+                                plo[ab] += Plo[ab * 18 + k] * hl;
+                                phi[ab] += Phi[ab * 18 + k] * hh;
+                            }
+                        }
+#pragma unroll
+                        for (int ab = 0; ab < 6; ++ab) {
+                            plo[ab] += __shfl_xor_sync(0xffffffffu, plo[ab], 1);
+                            plo[ab] += __shfl_xor_sync(0xffffffffu, plo[ab], 2);
+                            phi[ab] += __shfl_xor_sync(0xffffffffu, phi[ab], 1);
+                            phi[ab] += __shfl_xor_sync(0xffffffffu, phi[ab], 2);
+                        }
+                        if (tq == 0 && vlo)
+                            for (int ab = 0; ab < 6; ++ab) wc[g][ab] = plo[ab] * ql4.w;
+                        if (tq == 1 && vhi)
+                            for (int ab = 0; ab < 6; ++ab) wc[g + 8][ab] = phi[ab] * qh4.w;
+                        __syncwarp();
+                        for (int r = 0; r < nrow; ++r)
+                            if (wl[r] == lane)
+                                for (int ab = 0; ab < 6; ++ab) acc[ab] += wc[r][ab];
+                        __syncwarp();
+                        // drop the evaluated rows
+                        const int rest = qn - nrow;
+                        float4 mv = make_float4(0.f, 0.f, 0.f, 0.f);
+                        int mj = 0, ml = 0;
+                        if (lane < rest) {
+                            mv = wq[nrow + lane];
+                            mj = wj[nrow + lane];
+                            ml = wl[nrow + lane];
+                        }
+                        __syncwarp();
+                        if (lane < rest) {
+                            wq[lane] = mv;
+                            wj[lane] = mj;
+                            wl[lane] = ml;
+                        }
+                        qn = rest;
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+        for (int off = tg; off < 32; off <<= 1)
+            for (int ab = 0; ab < 6; ++ab) {
+                acc[ab] += __shfl_xor_sync(0xffffffffu, acc[ab], off);
+                acc64[ab] += __shfl_xor_sync(0xffffffffu, acc64[ab], off);
+            }
+        if (valid && ph == 0)
             for (int ab = 0; ab < 6; ++ab) sig[6 * int64_t(t) + ab] = double(acc[ab]) + acc64[ab];
     }
 }
@@ -301,6 +596,27 @@ int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t 
     const int64_t nl = ctx->n_leaves;
     const float near2 = float(ctx->opt.near_fp64 * ctx->opt.near_fp64);
     ++ctx->launches;
+    if (ctx->mat.mode == GBFMM_H_MLP) {
+        if (!ctx->mlp.trained || !ctx->mlp.d_binmask)
+            return set_err(ctx, GBFMM_ERR_INVALID_ARG, "GBFMM_H_MLP: train (or set) and calibrate the network first");
+        const float rmin = float(ctx->opt.mlp_min_dist > 0.0 ? ctx->opt.mlp_min_dist : 8.0);
+        const size_t smem = sizeof(mlpw::Weights);
+        const unsigned grid = nblk(nl, WARPS);
+#define GB_MLP_ARGS                                                                                                  \
+    ctx->opt.p, ctx->L, nl, near2, rmin *rmin, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, \
+        ctx->d_y, ctx->d_Pf, ctx->d_sid, ctx->d_Sf, sig, ctx->mlp.theta_h, ctx->mlp.theta, ctx->mlp.scale,        \
+        ctx->mlp.d_binmask
+        if (ctx->mat.cubic) {
+            CK(cudaFuncSetAttribute(k_near_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            k_near_mlp<true><<<grid, WARPS * 32, smem, ctx->stream>>>(GB_MLP_ARGS);
+        } else {
+            CK(cudaFuncSetAttribute(k_near_mlp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            k_near_mlp<false><<<grid, WARPS * 32, smem, ctx->stream>>>(GB_MLP_ARGS);
+        }
+#undef GB_MLP_ARGS
+        CK(cudaGetLastError());
+        return GBFMM_OK;
+    }
 #define GB_NEAR_ARGS                                                                                           \
     ctx->opt.p, ctx->L, nl, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, ctx->d_y, \
         ctx->d_Pf, ctx->d_P, ctx->d_sid, ctx->d_Sf, sig

@@ -50,5 +50,5 @@ def test_options_layout_matches_header():
 
     import paper_1712_07739_gb300 as gb
 
-    # 7 ints + padding + 1 double + 1 int + padding = 48 bytes on LP64
-    assert ctypes.sizeof(gb.Options) == 48
+    # 7 ints + pad + double + int + pad + double = 56 bytes on LP64
+    assert ctypes.sizeof(gb.Options) == 56

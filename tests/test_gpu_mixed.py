@@ -59,7 +59,7 @@ def test_mixed_orders_depths(p, L):
     assert err <= TOL_MIXED
 
 
-@pytest.mark.parametrize("split", [0, 1, 2])
+@pytest.mark.parametrize("split", [0, 1, 2, 3])
 def test_mixed_equals_fp64_gpu_pass_closely(split):
     """Slab-clustered network (the dense-wall structure of the 1M-segment
     workload, scaled down) at p = 6: every split setting meets 1e-4 on forces."""
