@@ -69,6 +69,15 @@ WORKLOADS["c3_iso"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs), isotropic mu=1 nu=0.3, p=6, mixed precision",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.isotropic_voigt(1.0, 0.3),
     h_mode="iso", p=6, levels=7, precision="mixed")
+WORKLOADS["c3q"] = dict(
+    desc="profiling case: 250,000 segments (5,000 loops x 50 in 32 Gaussian slabs), cubic, p=6, mixed, 6-level octree",
+    gen=lambda seed: synth.slab_loops(n_loops=5000, seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
+    h_mode="circle", circle_q=20, p=6, levels=6, precision="mixed")
+WORKLOADS["c3_mlp"] = dict(
+    desc="c3 network with the learned angular factor in the near field (pairs beyond 8 segment lengths in bins "
+         "the plain evaluator accepted at 2e-2 x RMS(h)), plain cubic rule elsewhere",
+    gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="mlp", circle_q=20, p=6, levels=7,
+    precision="mixed", mlp=dict(n_dirs=2_000_000, epochs=12, batch=8192, lr=3e-3, bin_tol=2e-2))
 DEFAULT_WORKLOAD = "c1"
 
 
@@ -197,6 +206,14 @@ def run_ours(args, wl):
     f = gb.FMM(p=wl["p"], levels=args.levels or wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
                circle_q=wl.get("circle_q", 0))
     f.set_material(wl["C"]())
+    mlp_info = None
+    if wl["h_mode"] == "mlp":
+        m = wl["mlp"]
+        t_tr = time.perf_counter()
+        loss = f.mlp_train(torch.tensor(synth.directions(m["n_dirs"], seed=3), device=dev), epochs=m["epochs"],
+                           batch=m["batch"], lr=m["lr"], seed=0)
+        frac = f.mlp_calibrate(m["bin_tol"])
+        mlp_info = {"train_s": time.perf_counter() - t_tr, "final_loss": loss, "bins_on_plain_rule": frac}
     out = torch.empty((len(nodes), 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
@@ -310,6 +327,8 @@ def run_ours(args, wl):
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "roofline": roofline, "cpu_baseline": cpu,
         }
+        if mlp_info is not None:
+            res["learned"] = mlp_info
         print(json.dumps(res, default=float))
     f.close()
     if world > 1:

@@ -103,3 +103,30 @@ def test_training_reduces_error():
     # odd by construction
     h2 = f.mlp_eval(-test).cpu().numpy()
     assert np.array_equal(h2, -h)
+
+
+def test_network_in_near_field_vs_plain():
+    """Mixed pass with the learned h in the near field (pairs beyond
+    mlp_min_dist segment lengths, bins the plain evaluator accepted) against
+    the same pass with the plain evaluator everywhere."""
+    import paper_1712_07739_gb300 as gb
+
+    nodes, segs, b = synth.slab_loops(n_loops=200, segs_per_loop=20, n_slabs=4, seed=33)
+    dn, ds, db = (torch.tensor(a, device="cuda") for a in (nodes, segs, b))
+    plain = gb.FMM(p=4, levels=5, precision="mixed", h_mode="circle", circle_q=32).set_material(CUB)
+    plain.build(dn, ds, db)
+    Fp = plain.nodal_forces().cpu().numpy()
+    f = gb.FMM(p=4, levels=5, precision="mixed", h_mode="mlp", circle_q=32, mlp_min_dist=8.0).set_material(CUB)
+    f.mlp_train(torch.tensor(synth.directions(400_000, seed=34), device="cuda"), epochs=20, batch=4096, lr=3e-3,
+                seed=2)
+    frac = f.mlp_calibrate(2e-2)
+    f.build(dn, ds, db)
+    Fm = f.nodal_forces().cpu().numpy()
+    err = np.linalg.norm(Fm - Fp) / np.linalg.norm(Fp)
+    print(f"network near field vs plain: rel L2 {err:.3e}, bins on the plain rule {frac:.3f}")
+    assert np.isfinite(Fm).all()
+    assert err < 1e-2
+    # with every bin on the plain rule the two passes agree to rounding
+    f.mlp_calibrate(1e-12)
+    Fa = f.nodal_forces().cpu().numpy()
+    assert np.linalg.norm(Fa - Fp) / np.linalg.norm(Fp) < 1e-6
