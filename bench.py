@@ -78,6 +78,12 @@ WORKLOADS["c3_mlp"] = dict(
          "the plain evaluator accepted at 2e-2 x RMS(h)), plain cubic rule elsewhere",
     gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="mlp", circle_q=20, p=6, levels=7,
     precision="mixed", mlp=dict(n_dirs=2_000_000, epochs=12, batch=8192, lr=3e-3, bin_tol=2e-2))
+WORKLOADS["c5"] = dict(
+    desc="64 independent cubic networks, N_s log-uniform in [1e4, 2e5] (4,639,301 segments in all), loop "
+         "densities 0.2-5x, mixed precision p=6, unit-circle Q=20, depth per network by the autotuner, evaluation "
+         "of all 64 recorded in one CUDA graph",
+    batch=True, gen_batch=lambda seed: synth.ensemble(seed=4 + 1000 * seed), C=lambda: synth.cubic_voigt(),
+    h_mode="circle", circle_q=20, p=6, levels=0, precision="mixed")
 DEFAULT_WORKLOAD = "c1"
 
 
@@ -183,6 +189,121 @@ def run_reference(args, wl):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
+
+
+def run_batch(args, wl):
+    """Batched ensemble: a step builds every network and evaluates all of them."""
+    import torch
+
+    import paper_1712_07739_gb300 as gb
+
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    nets = wl["gen_batch"](rank)
+    n_segs = sum(len(s) for _, s, _ in nets)
+    dn = [(torch.tensor(n, device=dev), torch.tensor(s, device=dev), torch.tensor(b, device=dev)) for n, s, b in nets]
+    bt = gb.Batch(len(nets), p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
+                  circle_q=wl.get("circle_q", 0)).set_material(wl["C"]())
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        for k, (n, s, b) in enumerate(dn):
+            bt.build(k, n, s, b)
+        return bt.nodal_forces()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    depths = [bt.info(k)["levels"] for k in range(len(nets))]
+    l0 = bt.info(0)["launches"]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = bt.info(0)["launches"] - l0
+    t_ms = sum(a.elapsed_time(b_) for a, b_ in evs)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * n_segs * args.steps / (t_ms / 1e3)
+    # end to end with host inputs and outputs
+    hn = [(torch.tensor(n).pin_memory(), torch.tensor(s).pin_memory(), torch.tensor(b).pin_memory()) for n, s, b in nets]
+    e_ms = []
+    h2d = sum(x.numel() * 8 for t3 in hn for x in t3)
+    d2h = sum(len(n) * 3 * 8 for n, _, _ in nets)
+    outs_h = [torch.empty((len(n), 3), dtype=torch.float64).pin_memory() for n, _, _ in nets]
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for (a, b_, c), (x, y, z) in zip(dn, hn):
+            a.copy_(x, non_blocking=True)
+            b_.copy_(y, non_blocking=True)
+            c.copy_(z, non_blocking=True)
+        F = step()
+        for o, f_ in zip(outs_h, F):
+            o.copy_(f_, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e_ms.append(e0.elapsed_time(e1))
+    e2e = world * n_segs * len(e_ms) / (sum(e_ms) / 1e3)
+    # roofline of the dominant kernel on the largest network, measured alone
+    big = int(np.argmax([len(s) for _, s, _ in nets]))
+    f = gb.FMM(p=wl["p"], levels=depths[big], precision=wl["precision"], h_mode=wl["h_mode"],
+               circle_q=wl.get("circle_q", 0)).set_material(wl["C"]())
+    f.build(*dn[big])
+    out = torch.empty((len(nets[big][0]), 3), dtype=torch.float64, device=dev)
+    f.nodal_forces(out=out)
+    f.set_timing(True)
+    f.nodal_forces(out=out)
+    st = f.stage_times()
+    work = f.work_counts()
+    p = wl["p"]
+    if st[4] >= st[2]:
+        flops = work["near_pairs"] * near_pair_flops("mixed", wl["h_mode"], wl.get("circle_q", 64))
+        roof = {"bound": "alu", "kernel": "k_near_mixed (largest network alone)", "achieved": flops / (st[4] / 1e3) / 1e12,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "peak_source": "152 SM x 128 lanes x 2 x 2.07 GHz"}
+    else:
+        pk, src = measured_bf16_peak()
+        flops = work["m2l_pairs"] * 2 * 54 * p ** 6
+        roof = {"bound": "tensor", "kernel": "k_m2l_tc (largest network alone)",
+                "achieved": flops / (st[2] / 1e3) / 1e12, "peak": pk, "unit": "TFLOP/s", "peak_source": src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    if rank == 0:
+        res = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/bf16", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "n_configs": len(nets), "n_segs": n_segs,
+                       "depths": depths, "l2": "flushed: 256 MiB write between steps, outside the step events",
+                       "step": "fmm_batch_build x 64 + fmm_batch_eval_nodal_forces (one graph)"},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": None,
+        }
+        print(json.dumps(res, default=float))
+    f.close()
+    bt.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_ours(args, wl):
@@ -348,6 +469,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
+    elif wl.get("batch"):
+        run_batch(args, wl)
     else:
         run_ours(args, wl)
 

@@ -183,6 +183,45 @@ int fmm_device_status(gbfmm_ctx *ctx, int *status);
 int fmm_inject_fault(gbfmm_ctx *ctx, int kind);
 
 /* ------------------------------------------------------------------------
+ * Batches of independent segment networks.
+ *
+ * A batch holds one network per slot; all slots share the medium's tables
+ * (kernel lattice and M2L operators, which do not depend on the network).
+ * With opt.levels == 0 each slot's tree depth is chosen by an autotuner: a
+ * pass is modelled as c_near x (near point pairs) + c_far x (cells of levels
+ * >= 2) (the near/far cost balance of App. B), the two constants are
+ * measured once by timing a pass of the first network built, and the depth
+ * with the smallest predicted time among L0-1..L0+1 (L0 from N_s /
+ * leaf_segments) is kept; the slot keeps it for later builds while its N_s
+ * stays within 10 %.  fmm_batch_eval_nodal_forces records the passes of
+ * all slots into one CUDA graph (spread over up to 8 internal streams and
+ * joined back onto the batch's stream) on its first call after a build, and
+ * replays it afterwards.
+ * ------------------------------------------------------------------------ */
+typedef struct gbfmm_batch gbfmm_batch;
+
+/* n_configs >= 1 slots, options as for fmm_create; cuda_stream: the
+ * stream the batch's evaluation is ordered on. */
+int fmm_batch_create(gbfmm_batch **out, const gbfmm_options *opt, int n_configs, void *cuda_stream);
+void fmm_batch_destroy(gbfmm_batch *batch);
+const char *fmm_batch_last_error(const gbfmm_batch *batch);
+/* Medium for every slot (host, 36 doubles, as fmm_set_material).  Synchronises. */
+int fmm_batch_set_material(gbfmm_batch *batch, const double *C_voigt);
+/* Build slot k's tree (arguments as fmm_build_tree; the same lifetime rule
+ * for the three arrays).  Runs the autotuner when the batch's options have
+ * levels == 0.  Synchronises.  Errors: INVALID_ARG, NO_MATERIAL, CUDA. */
+int fmm_batch_build(gbfmm_batch *batch, int k, int64_t n_nodes, const double *node_xyz, int64_t n_segs,
+                    const int64_t *seg_nodes, const double *burgers);
+/* Nodal forces of every slot: f_nodes is a host array of n_configs device
+ * pointers ([n_nodes_k][3] double each, overwritten).  Asynchronous on the
+ * batch's stream.  Errors: NOT_BUILT, CUDA. */
+int fmm_batch_eval_nodal_forces(gbfmm_batch *batch, double *const *f_nodes);
+/* Slot k's tree depth, the total kernel launches of all slots, and the
+ * autotuner's cost constants (seconds per near pair, per cell); any output
+ * may be NULL. */
+int fmm_batch_info(const gbfmm_batch *batch, int k, int *levels, int64_t *launches, double *c_near, double *c_far);
+
+/* ------------------------------------------------------------------------
  * Learned angular factor (a stand-in for the plain evaluator of h).
  *
  * A network 3 -> 128 -> 128 -> 128 -> 27 (SiLU; BF16 weight matrices, FP32

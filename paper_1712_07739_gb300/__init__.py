@@ -32,6 +32,8 @@ EXPORTS = [
     "fmm_device_status", "fmm_inject_fault",
     "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
     "fmm_mlp_eval_noalloc", "fmm_mlp_calibrate",
+    "fmm_batch_create", "fmm_batch_destroy", "fmm_batch_last_error", "fmm_batch_set_material", "fmm_batch_build",
+    "fmm_batch_eval_nodal_forces", "fmm_batch_info",
 ]
 MLP_PARAMS = 37664
 
@@ -88,6 +90,19 @@ def load_library(path: str = LIB_PATH):
     L.fmm_mlp_labels.argtypes = [vp, i64, dp, dp]
     L.fmm_mlp_eval_noalloc.argtypes = [vp, i64, dp, dp]
     L.fmm_mlp_calibrate.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    L.fmm_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Options), ctypes.c_int, vp]
+    L.fmm_batch_destroy.argtypes = [vp]
+    L.fmm_batch_destroy.restype = None
+    L.fmm_batch_last_error.argtypes = [vp]
+    L.fmm_batch_last_error.restype = ctypes.c_char_p
+    L.fmm_batch_set_material.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.fmm_batch_build.argtypes = [vp, ctypes.c_int, i64, dp, i64, dp, dp]
+    L.fmm_batch_eval_nodal_forces.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
+    L.fmm_batch_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    for name in ("fmm_batch_create", "fmm_batch_set_material", "fmm_batch_build", "fmm_batch_eval_nodal_forces",
+                 "fmm_batch_info"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("fmm_mlp_calibrate", "fmm_mlp_eval_noalloc", "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
                  "fmm_inject_fault", "fmm_device_status", "fmm_launch_count", "fmm_work_counts", "fmm_create", "fmm_set_material", "fmm_build_tree", "fmm_eval_stress",
                  "fmm_eval_nodal_forces", "fmm_tree_info", "fmm_set_timing", "fmm_stage_times"):
@@ -285,3 +300,79 @@ class FMM:
         a = (ctypes.c_double * 8)()
         self._check(self._lib.fmm_stage_times(self._h, a), "fmm_stage_times")
         return list(a)
+
+
+class Batch:
+    """Independent segment networks evaluated together (shared medium tables,
+    autotuned depth per network with levels=0, graph-recorded evaluation)."""
+
+    def __init__(self, n_configs, p=6, n_gauss=4, levels=0, precision="mixed", h_mode="circle", circle_q=0,
+                 leaf_segments=0, near_fp64=0.0, m2l_split=0, stream=None):
+        import torch
+
+        self._torch = torch
+        self._lib = load_library()
+        o = Options()
+        self._lib.fmm_default_options(ctypes.byref(o))
+        o.p, o.n_gauss, o.levels = p, n_gauss, levels
+        o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        o.h_mode = _HMODE[h_mode] if isinstance(h_mode, str) else int(h_mode)
+        o.circle_q, o.leaf_segments, o.near_fp64, o.m2l_split = circle_q, leaf_segments, near_fp64, m2l_split
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self._lib.fmm_batch_create(ctypes.byref(h), ctypes.byref(o), int(n_configs),
+                                        ctypes.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise GbfmmError(f"fmm_batch_create failed ({rc})")
+        self._h = h
+        self.n = int(n_configs)
+        self._keep = [None] * self.n
+        self._out = [None] * self.n
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise GbfmmError(f"{what} failed ({rc}): {self._lib.fmm_batch_last_error(self._h).decode()}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fmm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_material(self, C_voigt):
+        C = np.ascontiguousarray(np.asarray(C_voigt, dtype=np.float64).reshape(36))
+        self._check(self._lib.fmm_batch_set_material(self._h, C.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                    "fmm_batch_set_material")
+        return self
+
+    def build(self, k, nodes, segs, burgers):
+        t = self._torch
+        nodes = nodes.to(dtype=t.float64).contiguous()
+        segs = segs.to(dtype=t.int64).contiguous()
+        burgers = burgers.to(dtype=t.float64).contiguous()
+        self._keep[k] = (nodes, segs, burgers)
+        if self._out[k] is None or self._out[k].shape[0] != nodes.shape[0]:
+            self._out[k] = t.empty((nodes.shape[0], 3), dtype=t.float64, device=nodes.device)
+        self._check(self._lib.fmm_batch_build(self._h, int(k), nodes.shape[0], _ptr(nodes), segs.shape[0],
+                                              _ptr(segs), _ptr(burgers)), "fmm_batch_build")
+        return self
+
+    def nodal_forces(self):
+        """Evaluate every network; returns the list of [n_nodes_k, 3] tensors (reused between calls)."""
+        arr = (ctypes.c_void_p * self.n)(*[o.data_ptr() for o in self._out])
+        self._check(self._lib.fmm_batch_eval_nodal_forces(self._h, arr), "fmm_batch_eval_nodal_forces")
+        return self._out
+
+    def info(self, k):
+        lv, la = ctypes.c_int(), ctypes.c_int64()
+        cn, cf = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.fmm_batch_info(self._h, int(k), ctypes.byref(lv), ctypes.byref(la), ctypes.byref(cn),
+                                             ctypes.byref(cf)), "fmm_batch_info")
+        return {"levels": lv.value, "launches": la.value, "c_near": cn.value, "c_far": cf.value}

@@ -156,6 +156,13 @@ extern "C" void fmm_destroy(gbfmm_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     free_tree(ctx);
+    if (ctx->borrowed_material) {
+        ctx->d_mat = nullptr;
+        ctx->d_Asym = nullptr;
+        ctx->d_Asym_f = nullptr;
+        ctx->d_Klat = nullptr;
+        ctx->tc.Thi = ctx->tc.Tlo = nullptr;
+    }
     void *ps[] = {ctx->d_box, ctx->d_mat, ctx->d_Asym, ctx->d_Asym_f, ctx->d_Klat,
                   ctx->d_t_pos, ctx->d_t_x, ctx->d_t_sig, ctx->d_t_tmp};
     for (void *p : ps)

@@ -78,6 +78,7 @@ struct gbfmm_ctx {
     TcPlan tc;
     // learned h
     MlpState mlp;
+    bool borrowed_material = false;  // medium tables belong to another context (a batch)
 
     // tree
     bool built = false;
@@ -152,3 +153,4 @@ int targets_sort(gbfmm_ctx *ctx, int64_t n_t, const double *x);
 int targets_scatter(gbfmm_ctx *ctx, int64_t n_t, double *sigma);
 void timer_mark(gbfmm_ctx *ctx);
 void compute_occ(gbfmm_ctx *ctx, const int *start, int *occ);
+int share_material(gbfmm_ctx *dst, const gbfmm_ctx *src);  // material.cu

@@ -144,8 +144,58 @@ int material_setup(gbfmm_ctx *ctx) {
     return GBFMM_OK;
 }
 
+// Use src's medium tables (kernel lattice, M2L operators) without copying:
+// contexts of one batch share them.  dst must not outlive src.
+int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
+    if (!src->have_material) return set_err(ctx, GBFMM_ERR_NO_MATERIAL, "share_material: source has no material");
+    if (ctx->opt.p != src->opt.p || ctx->opt.precision != src->opt.precision || ctx->opt.h_mode != src->opt.h_mode ||
+        ctx->opt.m2l_split != src->opt.m2l_split)
+        return set_err(ctx, GBFMM_ERR_INVALID_ARG, "share_material: options differ");
+    ctx->mat = src->mat;
+    std::memcpy(ctx->Asym, src->Asym, sizeof(ctx->Asym));
+    ctx->d_mat = src->d_mat;
+    ctx->d_Asym = src->d_Asym;
+    ctx->d_Asym_f = src->d_Asym_f;
+    ctx->d_Klat = src->d_Klat;
+    ctx->lat_n = src->lat_n;
+    TcPlan &T = ctx->tc;
+    const TcPlan &S = src->tc;
+    T.ready_ops = S.ready_ops;
+    T.Kp = S.Kp;
+    T.Np = S.Np;
+    T.nsub = S.nsub;
+    T.ncta = S.ncta;
+    T.groups = S.groups;
+    T.tmem_cols = S.tmem_cols;
+    T.n_off = S.n_off;
+    T.n_lo = S.n_lo;
+    T.split = S.split;
+    T.tf32 = S.tf32;
+    T.esz = S.esz;
+    T.Thi = S.Thi;
+    T.Tlo = S.Tlo;
+    if (!T.d_status) {
+        CK(cudaMalloc(&T.d_status, sizeof(int)));
+        CK(cudaMemset(T.d_status, 0, sizeof(int)));
+    }
+    ctx->borrowed_material = true;
+    ctx->have_material = true;
+    return GBFMM_OK;
+}
+
 extern "C" int fmm_set_material(gbfmm_ctx *ctx, const double *V) {
     if (!ctx) return GBFMM_ERR_INVALID_ARG;
+    if (ctx->borrowed_material) {
+        // stop sharing: this context builds its own tables from here on
+        ctx->d_mat = nullptr;
+        ctx->d_Asym = nullptr;
+        ctx->d_Asym_f = nullptr;
+        ctx->d_Klat = nullptr;
+        ctx->lat_n = 0;
+        ctx->tc.Thi = ctx->tc.Tlo = nullptr;
+        ctx->tc.ready_ops = false;
+        ctx->borrowed_material = false;
+    }
     if (!V) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_set_material: null stiffness");
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 6; ++j)
