@@ -87,6 +87,28 @@ WORKLOADS["c5"] = dict(
 DEFAULT_WORKLOAD = "c1"
 
 
+def rank_configs(n_configs, world, rank):
+    """Configurations of an ensemble handled by one rank (round robin): the
+    networks are independent, so ranks exchange nothing but timings."""
+    return list(range(rank, n_configs, world))
+
+
+def global_rate(local_segs, local_ms, group=None):
+    """Whole-job throughput: segments of all ranks over the slowest rank's time
+    (sum of segments, max of milliseconds across the process group)."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized():
+        return local_segs / (local_ms / 1e3), local_segs, local_ms
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    segs = torch.tensor([float(local_segs)], dtype=torch.float64, device=dev)
+    ms = torch.tensor([float(local_ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(segs, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(ms, op=dist.ReduceOp.MAX, group=group)
+    return float(segs.item()) / (float(ms.item()) / 1e3), float(segs.item()), float(ms.item())
+
+
 def _rank_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -205,7 +227,8 @@ def run_batch(args, wl):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
-    nets = wl["gen_batch"](rank)
+    nets_all = wl["gen_batch"](0)  # every rank draws the same ensemble and takes its share
+    nets = [nets_all[k] for k in rank_configs(len(nets_all), world, rank)]
     n_segs = sum(len(s) for _, s, _ in nets)
     dn = [(torch.tensor(n, device=dev), torch.tensor(s, device=dev), torch.tensor(b, device=dev)) for n, s, b in nets]
     bt = gb.Batch(len(nets), p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
@@ -238,11 +261,7 @@ def run_batch(args, wl):
     clk = clocks.stop()
     launches = bt.info(0)["launches"] - l0
     t_ms = sum(a.elapsed_time(b_) for a, b_ in evs)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * n_segs * args.steps / (t_ms / 1e3)
+    value, _, t_ms = global_rate(n_segs * args.steps, t_ms)
     # end to end with host inputs and outputs
     hn = [(torch.tensor(n).pin_memory(), torch.tensor(s).pin_memory(), torch.tensor(b).pin_memory()) for n, s, b in nets]
     e_ms = []
@@ -264,7 +283,7 @@ def run_batch(args, wl):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e_ms.append(e0.elapsed_time(e1))
-    e2e = world * n_segs * len(e_ms) / (sum(e_ms) / 1e3)
+    e2e, _, _ = global_rate(n_segs * len(e_ms), sum(e_ms))
     # roofline of the dominant kernel on the largest network, measured alone
     big = int(np.argmax([len(s) for _, s, _ in nets]))
     f = gb.FMM(p=wl["p"], levels=depths[big], precision=wl["precision"], h_mode=wl["h_mode"],
@@ -291,9 +310,10 @@ def run_batch(args, wl):
     if rank == 0:
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f32/bf16", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "n_configs": len(nets), "n_segs": n_segs,
+            "config": {"workload": args.workload, "desc": wl["desc"], "n_configs": len(nets_all),
+                       "n_segs_rank0": n_segs,
                        "depths": depths, "l2": "flushed: 256 MiB write between steps, outside the step events",
                        "step": "fmm_batch_build x 64 + fmm_batch_eval_nodal_forces (one graph)"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -370,13 +390,12 @@ def run_ours(args, wl):
         torch.distributed.barrier()
     clk = clocks.stop()
     launches = f.launch_count() - launches0
+    dev_status = f.device_status()  # non-zero: a bounded wait ran out, the pass is invalid
+    if dev_status != 0:
+        raise RuntimeError(f"device status {dev_status} after the timed steps")
     step_ms = [a.elapsed_time(b_) for a, b_ in evs]
     t_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * n_segs * args.steps / (t_ms / 1e3)
+    value, _, t_ms = global_rate(n_segs * args.steps, t_ms)
 
     # end to end through the public API: pinned host inputs in, forces out
     h_nodes = torch.tensor(nodes).pin_memory()
@@ -398,7 +417,7 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e_ms.append(e0.elapsed_time(e1))
-    e2e = world * n_segs * len(e_ms) / (sum(e_ms) / 1e3)
+    e2e, _, _ = global_rate(n_segs * len(e_ms), sum(e_ms))
     h2d = h_nodes.numel() * 8 + h_segs.numel() * 8 + h_b.numel() * 8
     d2h = h_out.numel() * 8
 
@@ -446,7 +465,8 @@ def run_ours(args, wl):
                          "l2l": st[:, 3].mean(), "l2p_p2p": leaf_ms, "forces": st[:, 5].mean()},
             "work": work, "wall_s": wall,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "clocks": clk, "roofline": roofline, "cpu_baseline": cpu,
+            "gpu_launches": launches, "device_status": dev_status, "clocks": clk, "roofline": roofline,
+            "cpu_baseline": cpu,
         }
         if mlp_info is not None:
             res["learned"] = mlp_info

@@ -177,7 +177,7 @@ int fmm_device_status(gbfmm_ctx *ctx, int *status);
 
 /* Failure-detection test hook.  kind = 1: the next tensor-core M2L
  * (GBFMM_MIXED) arms its first pipeline stage without loading it, so the
- * consumer's bounded wait runs out (about 1 s); the pass then reports
+ * consumer's bounded wait runs out (about 10 s); the pass then reports
  * GBFMM_ERR_TIMEOUT through fmm_device_status and its outputs are invalid.
  * Nothing faults and the context stays usable.  Errors: INVALID_ARG. */
 int fmm_inject_fault(gbfmm_ctx *ctx, int kind);

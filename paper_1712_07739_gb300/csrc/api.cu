@@ -169,6 +169,12 @@ extern "C" void fmm_destroy(gbfmm_ctx *ctx) {
         if (p) cudaFree(p);
     m2l_tc_free(ctx);
     mlp_free(ctx);
+    {
+        NearWork &W = ctx->nw;
+        void *ps2[] = {W.items, W.sorted, W.keys, W.cnt, W.key_of, W.off, W.misc};
+        for (void *q : ps2)
+            if (q) cudaFree(q);
+    }
     if (ctx->timer.on)
         for (auto &e : ctx->timer.ev) cudaEventDestroy(e);
     delete ctx;

@@ -21,7 +21,9 @@ int work_counts(gbfmm_ctx *ctx, int64_t *out);  // fmm.cu
 
 struct gbfmm_batch {
     gbfmm_options opt{};
-    cudaStream_t stream = nullptr;  // caller's
+    cudaStream_t stream = nullptr;  // caller's (may be the legacy default stream)
+    cudaStream_t cap = nullptr;     // stream the graph is recorded on and launched on
+    cudaEvent_t in = nullptr, done = nullptr;  // caller -> cap and cap -> caller ordering
     std::vector<gbfmm_ctx *> ctx;
     std::vector<cudaStream_t> side;  // fan-out streams
     std::vector<cudaEvent_t> ev;     // fork + one join per side stream
@@ -66,6 +68,12 @@ extern "C" int fmm_batch_create(gbfmm_batch **out, const gbfmm_options *opt, int
             delete b;
             return GBFMM_ERR_CUDA;
         }
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+        delete b;
+        return GBFMM_ERR_CUDA;
+    }
     for (int k = 0; k < n; ++k) {
         gbfmm_ctx *c = nullptr;
         int rc = fmm_create(&c, opt, b->side[k % ns]);
@@ -90,6 +98,9 @@ extern "C" void fmm_batch_destroy(gbfmm_batch *b) {
     for (size_t k = b->ctx.size(); k-- > 0;) fmm_destroy(b->ctx[k]);
     for (auto s : b->side) cudaStreamDestroy(s);
     for (auto e : b->ev) cudaEventDestroy(e);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->in) cudaEventDestroy(b->in);
+    if (b->done) cudaEventDestroy(b->done);
     delete b;
 }
 
@@ -192,20 +203,24 @@ extern "C" int fmm_batch_eval_nodal_forces(gbfmm_batch *b, double *const *f_node
     for (int k = 0; k < n && same; ++k) same = b->out[k] == f_nodes[k];
     if (!same) {
         drop_graph(b);
-        // record: fork from the caller's stream onto the side streams, every
+        // record on the batch's own stream: fork onto the side streams, every
         // network's pass on its side stream, join back
-        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-            return berr(b, GBFMM_ERR_CUDA, "fmm_batch_eval: cudaStreamBeginCapture");
-        cudaEventRecord(b->ev[ns], b->stream);
+        const cudaError_t pre = cudaGetLastError();
+        if (pre != cudaSuccess)
+            return berr(b, GBFMM_ERR_CUDA, std::string("fmm_batch_eval: pending error ") + cudaGetErrorString(pre));
+        const cudaError_t eb = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (eb != cudaSuccess)
+            return berr(b, GBFMM_ERR_CUDA, std::string("fmm_batch_eval: cudaStreamBeginCapture: ") + cudaGetErrorString(eb));
+        cudaEventRecord(b->ev[ns], b->cap);
         for (int i = 0; i < ns; ++i) cudaStreamWaitEvent(b->side[i], b->ev[ns], 0);
         int rc = GBFMM_OK;
         for (int k = 0; k < n && !rc; ++k) rc = fmm_eval_nodal_forces(b->ctx[k], f_nodes[k], nullptr, nullptr);
         for (int i = 0; i < ns; ++i) {
             cudaEventRecord(b->ev[i], b->side[i]);
-            cudaStreamWaitEvent(b->stream, b->ev[i], 0);
+            cudaStreamWaitEvent(b->cap, b->ev[i], 0);
         }
         cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        cudaError_t e = cudaStreamEndCapture(b->cap, &g);
         if (rc) {
             if (g) cudaGraphDestroy(g);
             return berr(b, rc, "fmm_batch_eval: " + std::string(fmm_last_error(b->ctx[0])));
@@ -216,8 +231,11 @@ extern "C" int fmm_batch_eval_nodal_forces(gbfmm_batch *b, double *const *f_node
             return berr(b, GBFMM_ERR_CUDA, "fmm_batch_eval: cudaGraphInstantiate");
         for (int k = 0; k < n; ++k) b->out[k] = f_nodes[k];
     }
-    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess)
-        return berr(b, GBFMM_ERR_CUDA, "fmm_batch_eval: cudaGraphLaunch");
+    // order the replay after the caller's prior work and the caller's later work after it
+    if (cudaEventRecord(b->in, b->stream) != cudaSuccess || cudaStreamWaitEvent(b->cap, b->in, 0) != cudaSuccess ||
+        cudaGraphLaunch(b->exec, b->cap) != cudaSuccess || cudaEventRecord(b->done, b->cap) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->done, 0) != cudaSuccess)
+        return berr(b, GBFMM_ERR_CUDA, "fmm_batch_eval: graph launch");
     return GBFMM_OK;
 }
 

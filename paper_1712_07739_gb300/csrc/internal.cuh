@@ -51,6 +51,13 @@ struct MlpState {
     int64_t step = 0;
 };
 
+// work list of the near kernels (near.cu)
+struct NearWork {
+    int2 *items = nullptr, *sorted = nullptr;
+    int *keys = nullptr, *cnt = nullptr, *key_of = nullptr, *off = nullptr, *misc = nullptr;
+    int64_t cap = 0, cap_leaves = 0;
+};
+
 struct Timer {
     cudaEvent_t ev[16];
     bool on = false;
@@ -78,6 +85,7 @@ struct gbfmm_ctx {
     TcPlan tc;
     // learned h
     MlpState mlp;
+    NearWork nw;
     bool borrowed_material = false;  // medium tables belong to another context (a batch)
 
     // tree

@@ -96,13 +96,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait: gives up after ~1 s of device time
+// bounded wait: gives up after ~10 s of device time (a healthy wait lasts microseconds)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *status) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
         if (mbar_try(bar, parity)) return true;
-        if (globaltimer() - t0 > 1000000000ull) {
+        if (globaltimer() - t0 > 10000000000ull) {
             atomicExch(status, GBFMM_ERR_TIMEOUT);
             return false;
         }

@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
     const int *__restrict__ tstart, const double *__restrict__ xt, const int64_t *__restrict__ tsid,
     const int *__restrict__ sstart, const float4 *__restrict__ yrel, const double *__restrict__ ys,
     const float *__restrict__ c32, const double *__restrict__ c64, const int64_t *__restrict__ ssid,
-    const float *__restrict__ S, double *__restrict__ sig) {
+    const float *__restrict__ S, double *__restrict__ sig, const int2 *__restrict__ items,
+    const int *__restrict__ n_items) {
     __shared__ __align__(16) float sP[WARPS][SCH * NCS];
     __shared__ float4 sy[WARPS][SCH];
     __shared__ int ssd[WARPS][SCH];
@@ -186,10 +187,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
             sTab[i] = make_float2(cs, sn);
         }
     __syncthreads();
-    const int64_t leaf = blockIdx.x * int64_t(WARPS) + warp;
-    if (leaf >= nl) return;
-    const int t0 = tstart[leaf], t1 = tstart[leaf + 1];
-    if (t0 == t1) return;
+    // one work item per warp: up to 32 targets of one leaf, heaviest first
+    const int64_t item = blockIdx.x * int64_t(WARPS) + warp;
+    if (item >= *n_items) return;
+    const int2 wi = items[item];
+    const int64_t leaf = wi.x;
+    const int t0 = wi.y, t1 = min(wi.y + 32, tstart[leaf + 1]);
     const int P3 = p * p * p;
     const int nlv = 1 << (L - 1);
     int cx, cy, cz;
@@ -343,7 +346,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mlp(
     const int64_t *__restrict__ tsid, const int *__restrict__ sstart, const float4 *__restrict__ yrel,
     const double *__restrict__ ys, const float *__restrict__ c32, const int64_t *__restrict__ ssid,
     const float *__restrict__ S, double *__restrict__ sig, const __nv_bfloat16 *__restrict__ th,
-    const float *__restrict__ th32, const float *__restrict__ hscale, const uint32_t *__restrict__ binmask) {
+    const float *__restrict__ th32, const float *__restrict__ hscale, const uint32_t *__restrict__ binmask,
+    const int2 *__restrict__ items, const int *__restrict__ n_items) {
     extern __shared__ __align__(16) unsigned char dsm[];
     mlpw::Weights &Wt = *reinterpret_cast<mlpw::Weights *>(dsm);
     __shared__ __align__(16) float sP[WARPS][MSCH * 108];
@@ -366,10 +370,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mlp(
     }
     for (int i = threadIdx.x; i < 48; i += blockDim.x) sBin[i] = binmask[i];
     __syncthreads();
-    const int64_t leaf = blockIdx.x * int64_t(WARPS) + warp;
-    if (leaf >= nl) return;
-    const int t0 = tstart[leaf], t1 = tstart[leaf + 1];
-    if (t0 == t1) return;
+    // one work item per warp: up to 32 targets of one leaf, heaviest first
+    const int64_t item = blockIdx.x * int64_t(WARPS) + warp;
+    if (item >= *n_items) return;
+    const int2 wi = items[item];
+    const int64_t leaf = wi.x;
+    const int t0 = wi.y, t1 = min(wi.y + 32, tstart[leaf + 1]);
     const int P3 = p * p * p;
     const int nlv = 1 << (L - 1);
     int cx, cy, cz;
@@ -575,6 +581,95 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mlp(
     }
 }
 
+// ---------------------------------------------------------------- work list
+// Items are (leaf, first target) for every 32 targets of a leaf; the cost of
+// an item is ~ (its targets) x (sources in the 27 neighbour leaves).  Items
+// are ordered by decreasing cost class (floor log2) so that the heaviest
+// start first and the uneven leaf populations of clustered networks do not
+// leave a long tail.
+__global__ void k_items_count(int64_t nl, int L, const int *__restrict__ tstart, const int *__restrict__ sstart,
+                              int *__restrict__ cnt, int *__restrict__ key_cnt) {
+    const int64_t l = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (l >= nl) return;
+    const int nt = tstart[l + 1] - tstart[l];
+    cnt[l] = (nt + 31) / 32;
+    if (nt == 0) return;
+    const int nlv = 1 << (L - 1);
+    int cx, cy, cz;
+    cell_xyz3(l, nlv, cx, cy, cz);
+    int64_t ns = 0;
+    for (int nb = 0; nb < 27; ++nb) {
+        const int ax = cx + nb % 3 - 1, ay = cy + (nb / 3) % 3 - 1, az = cz + nb / 9 - 1;
+        if (ax < 0 || ay < 0 || az < 0 || ax >= nlv || ay >= nlv || az >= nlv) continue;
+        const int64_t A = (int64_t(az) * nlv + ay) * nlv + ax;
+        ns += sstart[A + 1] - sstart[A];
+    }
+    const int64_t cost = int64_t(min(nt, 32)) * ns;
+    const int key = cost > 0 ? 63 - __clzll(cost) : 0;  // floor log2
+    key_cnt[l] = key;
+}
+
+__global__ void k_items_fill(int64_t nl, const int *__restrict__ tstart, const int *__restrict__ off,
+                             const int *__restrict__ key_of, int2 *__restrict__ items, int *__restrict__ keys,
+                             int *__restrict__ hist) {
+    const int64_t l = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (l >= nl) return;
+    const int t0 = tstart[l], t1 = tstart[l + 1];
+    const int key = 63 - key_of[l];
+    int o = off[l];
+    for (int r0 = t0; r0 < t1; r0 += 32, ++o) {
+        items[o] = make_int2(int(l), r0);
+        keys[o] = key;
+        atomicAdd(&hist[key], 1);
+    }
+}
+
+__global__ void k_items_order(int n_total_cap, const int *__restrict__ total, const int2 *__restrict__ items,
+                              const int *__restrict__ keys, const int *__restrict__ hist, int *__restrict__ cursor,
+                              int2 *__restrict__ sorted, int *__restrict__ n_items) {
+    __shared__ int base[64];
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < 64; ++k) {
+            base[k] = run;
+            run += hist[k];
+        }
+    }
+    __syncthreads();
+    const int n = *total;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_items = n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n && i < n_total_cap; i += gridDim.x * blockDim.x) {
+        const int k = keys[i];
+        sorted[base[k] + atomicAdd(&cursor[k], 1)] = items[i];
+    }
+}
+
+__global__ void k_scan_small(int64_t n, const int *__restrict__ cnt, int *__restrict__ start) {
+    // exclusive scan, one block of 1024 threads (cnt -> start[0..n])
+    __shared__ int part[1024];
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t b = threadIdx.x * per, e = min(n, b + per);
+    int s = 0;
+    for (int64_t i = b; i < e; ++i) s += cnt[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int t = 0; t < int(blockDim.x); ++t) {
+            const int v = part[t];
+            part[t] = run;
+            run += v;
+        }
+        start[n] = run;
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int64_t i = b; i < e; ++i) {
+        start[i] = run;
+        run += cnt[i];
+    }
+}
+
 }  // namespace
 
 int near_coef_count(const gbfmm_ctx *ctx) { return ctx->mat.mode == GBFMM_H_ISO ? 80 : 108; }
@@ -592,20 +687,62 @@ int near_prepare(gbfmm_ctx *ctx) {
     return GBFMM_OK;
 }
 
+// work list for the near kernels (no host synchronisation: the item count
+// stays on the device and surplus warps return)
+static int build_items(gbfmm_ctx *ctx, const int *tstart, int64_t n_targets, int *&n_items, int2 *&items,
+                       int64_t &cap) {
+    const int64_t nl = ctx->n_leaves;
+    cap = nl + n_targets / 32 + 1;
+    NearWork &W = ctx->nw;
+    if (cap > W.cap || nl > W.cap_leaves) {
+        void *ps[] = {W.items, W.sorted, W.keys, W.cnt, W.key_of, W.off, W.misc};
+        for (void *q : ps)
+            if (q) cudaFree(q);
+        W = NearWork{};
+        CK(cudaMalloc(&W.items, cap * sizeof(int2)));
+        CK(cudaMalloc(&W.sorted, cap * sizeof(int2)));
+        CK(cudaMalloc(&W.keys, cap * sizeof(int)));
+        CK(cudaMalloc(&W.cnt, nl * sizeof(int)));
+        CK(cudaMalloc(&W.key_of, nl * sizeof(int)));
+        CK(cudaMalloc(&W.off, (nl + 1) * sizeof(int)));
+        CK(cudaMalloc(&W.misc, 192 * sizeof(int)));  // hist[64], cursor[64], n_items, total
+        W.cap = cap;
+        W.cap_leaves = nl;
+    }
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemsetAsync(W.misc, 0, 192 * sizeof(int), st));
+    CK(cudaMemsetAsync(W.key_of, 0, nl * sizeof(int), st));
+    ctx->launches += 4;
+    k_items_count<<<nblk(nl, 256), 256, 0, st>>>(nl, ctx->L, tstart, ctx->d_leaf_start, W.cnt, W.key_of);
+    k_scan_small<<<1, 1024, 0, st>>>(nl, W.cnt, W.off);
+    k_items_fill<<<nblk(nl, 256), 256, 0, st>>>(nl, tstart, W.off, W.key_of, W.items, W.keys, W.misc);
+    k_items_order<<<nblk(cap, 256) < 1024 ? nblk(cap, 256) : 1024, 256, 0, st>>>(
+        int(cap), W.off + nl, W.items, W.keys, W.misc, W.misc + 64, W.sorted, W.misc + 128);
+    CK(cudaGetLastError());
+    n_items = W.misc + 128;
+    items = W.sorted;
+    return GBFMM_OK;
+}
+
 int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t *tsid, double *sig) {
     const int64_t nl = ctx->n_leaves;
     const float near2 = float(ctx->opt.near_fp64 * ctx->opt.near_fp64);
+    int *n_items = nullptr;
+    int2 *items = nullptr;
+    int64_t cap = 0;
+    const int64_t n_targets = tsid ? ctx->N : ctx->t_cap;
+    if (int rc = build_items(ctx, tstart, n_targets, n_items, items, cap)) return rc;
+    const unsigned grid = nblk(cap, WARPS);
     ++ctx->launches;
     if (ctx->mat.mode == GBFMM_H_MLP) {
         if (!ctx->mlp.trained || !ctx->mlp.d_binmask)
             return set_err(ctx, GBFMM_ERR_INVALID_ARG, "GBFMM_H_MLP: train (or set) and calibrate the network first");
         const float rmin = float(ctx->opt.mlp_min_dist > 0.0 ? ctx->opt.mlp_min_dist : 8.0);
         const size_t smem = sizeof(mlpw::Weights);
-        const unsigned grid = nblk(nl, WARPS);
 #define GB_MLP_ARGS                                                                                                  \
     ctx->opt.p, ctx->L, nl, near2, rmin *rmin, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, \
         ctx->d_y, ctx->d_Pf, ctx->d_sid, ctx->d_Sf, sig, ctx->mlp.theta_h, ctx->mlp.theta, ctx->mlp.scale,        \
-        ctx->mlp.d_binmask
+        ctx->mlp.d_binmask, items, n_items
         if (ctx->mat.cubic) {
             CK(cudaFuncSetAttribute(k_near_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
             k_near_mlp<true><<<grid, WARPS * 32, smem, ctx->stream>>>(GB_MLP_ARGS);
@@ -619,8 +756,7 @@ int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t 
     }
 #define GB_NEAR_ARGS                                                                                           \
     ctx->opt.p, ctx->L, nl, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, ctx->d_y, \
-        ctx->d_Pf, ctx->d_P, ctx->d_sid, ctx->d_Sf, sig
-    const unsigned grid = nblk(nl, WARPS);
+        ctx->d_Pf, ctx->d_P, ctx->d_sid, ctx->d_Sf, sig, items, n_items
     if (near_coef_count(ctx) == 80)
         k_near_mixed<HM_ISO, 80, 32><<<grid, WARPS * 32, 0, ctx->stream>>>(GB_NEAR_ARGS);
     else if (ctx->mat.cubic)

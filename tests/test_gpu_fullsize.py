@@ -26,28 +26,36 @@ def _bench_workload(name):
 
 
 @pytest.fixture(scope="module")
-def c3_forces():
-    import paper_1712_07739_gb300 as gb
-
+def c3_case():
     wl = _bench_workload("c3")
     nodes, segs, b = wl["gen"](0)
-    f = gb.FMM(p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
-               circle_q=wl["circle_q"]).set_material(wl["C"]())
-    f.build(torch.tensor(nodes, device="cuda"), torch.tensor(segs, device="cuda"), torch.tensor(b, device="cuda"))
-    F = f.nodal_forces().cpu().numpy()
-    assert f.device_status() == 0
-    return nodes, segs, b, F, wl
-
-
-def test_full_size_sampled_nodes_match_direct_sum(c3_forces):
-    nodes, segs, b, F, wl = c3_forces
-    assert np.isfinite(F).all()
     rng = np.random.default_rng(2024)
     ids = rng.choice(len(nodes), 4, replace=False)
     mat = oracle.Material.aniso(wl["C"](), Q=32)
     Fo, used = oracle.sampled_node_forces(mat, nodes, segs, b, ids)
+    return nodes, segs, b, wl, ids, Fo, used
+
+
+def _forces(nodes, segs, b, wl, **over):
+    import paper_1712_07739_gb300 as gb
+
+    kw = dict(p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"], circle_q=wl["circle_q"])
+    kw.update(over)
+    f = gb.FMM(**kw).set_material(wl["C"]())
+    f.build(torch.tensor(nodes, device="cuda"), torch.tensor(segs, device="cuda"), torch.tensor(b, device="cuda"))
+    F = f.nodal_forces().cpu().numpy()
+    assert f.device_status() == 0
+    return F
+
+
+@pytest.mark.parametrize("label,over", [("bench configuration", {}),
+                                        ("BF16 split on all offsets, Q=32", {"m2l_split": 2, "circle_q": 32})])
+def test_full_size_sampled_nodes_match_direct_sum(c3_case, label, over):
+    nodes, segs, b, wl, ids, Fo, used = c3_case
+    F = _forces(nodes, segs, b, wl, **over)
+    assert np.isfinite(F).all()
     err = np.linalg.norm(F[ids] - Fo) / np.linalg.norm(Fo)
-    print(f"1M segments, {len(ids)} sampled nodes vs direct sum ({used} threads): rel L2 {err:.3e}")
+    print(f"1M segments, {label}: {len(ids)} sampled nodes vs direct sum ({used} threads): rel L2 {err:.3e}")
     assert err < 1e-3
 
 
