@@ -40,15 +40,35 @@ UNIT = "segments/s"
 # mixed path, isotropic polynomial form: separation 3, |d|^2 5, rsqrt 1,
 #   1/R^3 and 1/R^5 3, cubic monomials 16, per stress component 3 linear +
 #   10 cubic FMAs and 2 scaled adds (29) x 6 -> 202
-# mixed path, unit-circle h: Q x (zz and zT 2 x 81 FMA, inverse 30, F 54,
-#   accumulate 36, direction 6) ~ Q x 450, plus the 6x18 contraction 216
+# unit-circle h in a cubic medium with axes along x, y, z (the specialised
+#   form both paths use): separation, |d|^2, rsqrt, direction and circle basis
+#   41; per circle point 219 (point 9, zz 15, cofactors 18, determinant and
+#   scaling 12, zT 18, U = (zz)^-1 zT 45, F = U (zz)^-1 30, accumulate 18 x 4);
+#   final scale 19; contraction with the 6x18 source tensor and 1/R^2 229;
+#   accumulate 6 -> 219 Q + 295
+# unit-circle h, general medium: Q x (zz and zT from the 81-entry C 2 x 81
+#   FMA, inverse 30, F 54, accumulate 36, point 6) ~ Q x 450, plus 236
 FLOP_PER_NEAR_PAIR = {("fp64", "iso"): 341, ("mixed", "iso"): 202}
 
 
-def near_pair_flops(precision, h_mode, q):
-    if (precision, h_mode) in FLOP_PER_NEAR_PAIR:
+def is_cubic_aligned(C6):
+    """Cubic symmetry with the crystal axes along x, y, z (Voigt 6x6)."""
+    C = np.asarray(C6, dtype=np.float64).reshape(6, 6)
+    off = C.copy()
+    for i in range(3):
+        off[i, :3] = 0.0
+        off[3 + i, 3 + i] = 0.0
+    return (np.allclose(np.diag(C)[:3], C[0, 0]) and np.allclose(np.diag(C)[3:], C[3, 3])
+            and np.allclose([C[0, 1], C[0, 2], C[1, 2]], C[0, 1]) and np.allclose(C[:3, :3], C[:3, :3].T)
+            and not np.any(off))
+
+
+def near_pair_flops(precision, h_mode, q, cubic=False):
+    if h_mode == "iso":
         return FLOP_PER_NEAR_PAIR[(precision, h_mode)]
-    return 450 * q + 216 + 20
+    return 219 * q + 295 if cubic else 450 * q + 236
+
+
 FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 (nominal, profiling recipe table)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
@@ -78,13 +98,18 @@ WORKLOADS["c3_mlp"] = dict(
          "the plain evaluator accepted at 2e-2 x RMS(h)), plain cubic rule elsewhere",
     gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="mlp", circle_q=20, p=6, levels=7,
     precision="mixed", mlp=dict(n_dirs=2_000_000, epochs=12, batch=8192, lr=3e-3, bin_tol=2e-2))
+WORKLOADS["c3_fp64"] = dict(
+    desc="the 1,000,000-segment cubic slab network of c3 through the plain FP64 path: FP64 M2L, FP64 near field, "
+         "unit-circle h (cubic form, Q=32), p=6, 7-level octree",
+    gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=32, p=6, levels=7,
+    precision="fp64")
 WORKLOADS["c5"] = dict(
     desc="64 independent cubic networks, N_s log-uniform in [1e4, 2e5] (4,639,301 segments in all), loop "
          "densities 0.2-5x, mixed precision p=6, unit-circle Q=20, depth per network by the autotuner, evaluation "
          "of all 64 recorded in one CUDA graph",
     batch=True, gen_batch=lambda seed: synth.ensemble(seed=4 + 1000 * seed), C=lambda: synth.cubic_voigt(),
     h_mode="circle", circle_q=20, p=6, levels=0, precision="mixed")
-DEFAULT_WORKLOAD = "c1"
+DEFAULT_WORKLOAD = "c3"
 
 
 def rank_configs(n_configs, world, rank):
@@ -164,26 +189,47 @@ def measured_bf16_peak():
         return 1900.0, "fallback 1.9 PFLOP/s bf16 burst (profiling recipe), of fallback"
 
 
-def oracle_sample_rate(wl, nodes, segs, b, budget_s, nthreads=0):
-    """FP64 oracle direct sum on a bounded sample of segments; segments/s."""
+def oracle_sample_rate(wl, nodes, segs, b, budget_s, nthreads=0, seed=123):
+    """FP64 oracle direct sum (Eq. "stress3") timed on a bounded sample.
+
+    Targets are the Gauss points of randomly drawn segments (at least four
+    per host thread: the oracle runs one target per thread), sources a random
+    subset of all source points; the work of the direct sum is the same for
+    every (target, source) pair, so the full workload's rate is
+    pairs/s / (n_g x all source points) segments/s.  The sample grows (sources
+    first, then segments) until one evaluation takes about budget_s / 2.
+    Returns (segments/s, threads, description, seconds)."""
     import oracle
 
     C6 = wl["C"]()
     mat = oracle.Material.iso(1.0, 0.3) if wl["h_mode"] == "iso" else oracle.Material.aniso(C6, Q=64)
     y, q, sid = oracle.quadrature(nodes, segs, b, 4)
-    rng = np.random.default_rng(123)
-    n = 1
-    used = 1
+    n_all = len(y)
+    rng = np.random.default_rng(seed)
+    threads = nthreads or os.cpu_count() or 1
+    n_seg = min(len(segs), threads)
+    n_src = min(n_all, 4096)
     while True:
-        pick = rng.choice(len(segs), size=min(n, len(segs)), replace=False)
+        pick = rng.choice(len(segs), size=n_seg, replace=False)
         tgt = (pick[:, None] * 4 + np.arange(4)[None, :]).reshape(-1)
+        src = np.sort(rng.choice(n_all, size=n_src, replace=False)) if n_src < n_all else np.arange(n_all)
         t0 = time.perf_counter()
-        sig, used = oracle.direct_stress(mat, y[tgt], sid[tgt], y, q, sid, nthreads, return_threads=True)
+        sig, used = oracle.direct_stress(mat, y[tgt], sid[tgt], y[src], q[src], sid[src], nthreads,
+                                         return_threads=True)
         oracle.segment_forces(nodes, segs[pick], b[pick], sig, 4)
         dt = time.perf_counter() - t0
-        if dt >= budget_s or n >= len(segs):
-            return len(pick) / dt, used, len(pick), dt
-        n = min(len(segs), max(n * 2, int(n * budget_s / max(dt, 1e-3) * 0.9)))
+        done = n_src == n_all and n_seg == len(segs)
+        if dt >= 0.5 * budget_s or done:
+            rate = len(tgt) * n_src / dt / (4.0 * n_all)
+            desc = (f"{n_seg} randomly drawn segments ({len(tgt)} Gauss-point targets) against {n_src} of the "
+                    f"{n_all} source points, FP64 direct Mura sum ({'isotropic closed form' if wl['h_mode'] == 'iso' else 'unit circle, Q=64'}), "
+                    f"{dt:.1f} s; segments/s = pairs/s / (4 x {n_all})")
+            return rate, used, desc, dt
+        grow = max(2.0, 0.6 * budget_s / max(dt, 1e-3))
+        if n_src < n_all:
+            n_src = int(min(n_all, n_src * grow))
+        else:
+            n_seg = int(min(len(segs), n_seg * grow))
 
 
 def run_reference(args, wl):
@@ -194,20 +240,19 @@ def run_reference(args, wl):
     per_step = max(2.0, 150.0 / (args.steps + args.warmup))
     rates = []
     for i in range(args.warmup + args.steps):
-        r, used, nseg, dt = oracle_sample_rate(wl, nodes, segs, b, per_step)
+        r, used, desc, dt = oracle_sample_rate(wl, nodes, segs, b, per_step, seed=123 + i)
         if i >= args.warmup:
-            rates.append((r, used, nseg, dt))
-    segs_done = sum(x[2] for x in rates)
+            rates.append((r, used, desc, dt))
+    seg_equiv = sum(r * dt for r, _, _, dt in rates)   # segments of the full workload the samples amount to
     t_tot = sum(x[3] for x in rates)
-    value = segs_done / t_tot
+    value = seg_equiv / t_tot
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / len(rates),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": rates[0][1], "kind": "oracle",
-                         "sample": f"{rates[0][2]} randomly drawn segments per step (their Gauss points against "
-                                   f"all {len(segs) * 4} source points), FP64 direct Mura sum"},
+                         "sample": "per step: " + rates[0][2]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -345,7 +390,7 @@ def run_ours(args, wl):
     d_segs = torch.tensor(segs, device=dev)
     d_b = torch.tensor(b, device=dev)
     f = gb.FMM(p=wl["p"], levels=args.levels or wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
-               circle_q=wl.get("circle_q", 0))
+               circle_q=wl.get("circle_q", 0), m2l_split=wl.get("m2l_split", 0))
     f.set_material(wl["C"]())
     mlp_info = None
     if wl["h_mode"] == "mlp":
@@ -428,7 +473,8 @@ def run_ours(args, wl):
     fp64 = wl["precision"] == "fp64"
     peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
     if leaf_ms >= m2l_ms:
-        flops = (work["near_pairs"] * near_pair_flops(wl["precision"], wl["h_mode"], wl.get("circle_q", 64))
+        flops = (work["near_pairs"] * near_pair_flops(wl["precision"], wl["h_mode"], wl.get("circle_q", 64),
+                                                      is_cubic_aligned(wl["C"]()))
                  + work["points"] * (12 * p ** 3 + 30 * p))
         achieved = flops / (leaf_ms / 1e3) / 1e12
         dom = ("k_leaf_eval_f64" if fp64 else "k_near_mixed") + " (L2P + near-field P2P)"
@@ -448,10 +494,8 @@ def run_ours(args, wl):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            r, used, nseg, dt = oracle_sample_rate(wl, nodes, segs, b, 15.0)
-            cpu = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle",
-                   "sample": f"{nseg} randomly drawn segments (their Gauss points against all {len(segs) * 4} "
-                             f"source points), FP64 direct Mura sum, {dt:.1f} s"}
+            r, used, desc, dt = oracle_sample_rate(wl, nodes, segs, b, 20.0)
+            cpu = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc}
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -459,6 +503,7 @@ def run_ours(args, wl):
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "n_segs": n_segs, "levels": info["levels"],
                        "p": p, "precision": wl["precision"], "h_mode": wl["h_mode"],
+                       "circle_q": wl.get("circle_q", 0), "m2l_split": wl.get("m2l_split", 0),
                        "l2": "flushed: 256 MiB write between steps, outside the step events",
                        "step": "fmm_build_tree + fmm_eval_nodal_forces"},
             "stage_ms": {"precontract": st[:, 0].mean(), "p2m_m2m": st[:, 1].mean(), "m2l": m2l_ms,
@@ -485,8 +530,17 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--levels", type=int, default=0, help="override the workload's tree depth")
+    ap.add_argument("--p", type=int, default=0, help="override the workload's interpolation order")
+    ap.add_argument("--m2l-split", type=int, default=-1, help="override the M2L operand mode (fmm options)")
+    ap.add_argument("--circle-q", type=int, default=0, help="override the unit-circle points")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.p:
+        wl["p"] = args.p
+    if args.m2l_split >= 0:
+        wl["m2l_split"] = args.m2l_split
+    if args.circle_q:
+        wl["circle_q"] = args.circle_q
     if args.impl == "reference":
         run_reference(args, wl)
     elif wl.get("batch"):

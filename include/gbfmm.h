@@ -68,7 +68,11 @@ typedef struct {
     int m2l_split;         /* MIXED: operand precision of the tensor-core M2L:
                               0 = BF16 with residual (split) passes on the offsets with
                               max |o_i| = 2 (default), 1 = BF16 only, 2 = BF16 with residual
-                              passes on all 316 offsets, 3 = TF32 (FP32 operands) */
+                              passes on all 316 offsets, 3 = TF32 (FP32 operands),
+                              4 = FP16 with per-level scaling of the multipole values (a power
+                              of two from each level's largest |W|) and one power-of-two scale
+                              for the operators, 5 = as 4 plus residual passes on the offsets
+                              with max |o_i| = 2 */
     double mlp_min_dist;   /* GBFMM_H_MLP: near pairs closer than this many source segment
                               lengths use the plain evaluator; 0 = 8 */
 } gbfmm_options;

@@ -127,7 +127,7 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
         (opt->levels != 0 && (opt->levels < 3 || opt->levels > 9)) ||
         (opt->precision != GBFMM_FP64 && opt->precision != GBFMM_MIXED) || opt->h_mode < 0 || opt->h_mode > 2 ||
         opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0) || opt->m2l_split < 0 ||
-        opt->m2l_split > 3)
+        opt->m2l_split > 5)
         return GBFMM_ERR_INVALID_ARG;
     gbfmm_ctx *ctx = new gbfmm_ctx();
     ctx->opt = *opt;
@@ -218,6 +218,31 @@ extern "C" int fmm_build_tree(gbfmm_ctx *ctx, int64_t n_nodes, const double *nod
     }
     ctx->built = true;
     return GBFMM_OK;
+}
+
+uint64_t layout_hash(const gbfmm_ctx *c) {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a, 64 bit
+    auto mix = [&h](const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    };
+    auto v = [&mix](auto x) { mix(&x, sizeof(x)); };
+    mix(&c->opt, sizeof(c->opt));
+    v(c->L), v(c->N), v(c->n_segs), v(c->n_nodes), v(c->n_cells), v(c->n_leaves), v(c->t_cap);
+    v(c->node_xyz), v(c->seg_nodes), v(c->burgers), v(c->stream);
+    const void *ptrs[] = {c->d_mat, c->d_Asym, c->d_Asym_f, c->d_Klat, c->d_box, c->d_y, c->d_q, c->d_sid,
+                          c->d_slen, c->d_pos, c->d_pleaf, c->d_leaf_start, c->d_tmp_i, c->d_tmp_d, c->d_P,
+                          c->d_Pf, c->d_W, c->d_S, c->d_Wf, c->d_Sf, c->d_sig, c->d_yrel, c->d_t_pos, c->d_t_start,
+                          c->d_t_x, c->d_t_sig, c->tc.Thi, c->tc.Tlo, c->tc.Whi, c->tc.Wlo, c->tc.d_work,
+                          c->tc.d_status, c->tc.d_bocc, c->tc.d_bocc_ofs, c->mlp.theta, c->mlp.theta_h,
+                          c->mlp.scale, c->mlp.d_binmask, c->nw.items, c->nw.sorted, c->nw.keys, c->nw.cnt,
+                          c->nw.key_of, c->nw.off, c->nw.misc};
+    mix(ptrs, sizeof(ptrs));
+    v(c->mat.mode), v(c->mat.Q), v(c->mat.cubic), v(c->tc.n_work), v(c->tc.split), v(c->tc.tf32);
+    mix(c->tc.wofs, sizeof(c->tc.wofs));
+    mix(c->tc.bocc_h, sizeof(c->tc.bocc_h));
+    v(c->tc.bocc_tot), v(c->nw.cap), v(c->nw.cap_leaves), v(c->mlp.trained);
+    return h;
 }
 
 static int begin_eval(gbfmm_ctx *ctx) {

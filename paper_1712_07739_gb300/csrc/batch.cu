@@ -28,6 +28,7 @@ struct gbfmm_batch {
     std::vector<cudaStream_t> side;  // fan-out streams
     std::vector<cudaEvent_t> ev;     // fork + one join per side stream
     std::vector<double *> out;       // force outputs recorded in the graph
+    std::vector<uint64_t> layout;    // layout_hash of each context when the graph was recorded
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     double c_near = 0.0, c_far = 0.0;  // seconds per near pair / per cell (autotuner)
@@ -85,6 +86,7 @@ extern "C" int fmm_batch_create(gbfmm_batch **out, const gbfmm_options *opt, int
         b->ctx.push_back(c);
     }
     b->out.assign(n, nullptr);
+    b->layout.assign(n, 0);
     b->tuned_L.assign(n, 0);
     b->tuned_ns.assign(n, 0);
     *out = b;
@@ -199,8 +201,10 @@ extern "C" int fmm_batch_eval_nodal_forces(gbfmm_batch *b, double *const *f_node
     const int n = int(b->ctx.size()), ns = int(b->side.size());
     for (int k = 0; k < n; ++k)
         if (!b->ctx[k]->built) return berr(b, GBFMM_ERR_NOT_BUILT, "fmm_batch_eval: config " + std::to_string(k) + " not built");
+    // the recorded graph is reused while every output pointer and every
+    // context's layout (sizes, depth, buffers) is what it was when recorded
     bool same = b->exec != nullptr;
-    for (int k = 0; k < n && same; ++k) same = b->out[k] == f_nodes[k];
+    for (int k = 0; k < n && same; ++k) same = b->out[k] == f_nodes[k] && b->layout[k] == layout_hash(b->ctx[k]);
     if (!same) {
         drop_graph(b);
         // record on the batch's own stream: fork onto the side streams, every
@@ -229,7 +233,10 @@ extern "C" int fmm_batch_eval_nodal_forces(gbfmm_batch *b, double *const *f_node
         b->graph = g;
         if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess)
             return berr(b, GBFMM_ERR_CUDA, "fmm_batch_eval: cudaGraphInstantiate");
-        for (int k = 0; k < n; ++k) b->out[k] = f_nodes[k];
+        for (int k = 0; k < n; ++k) {
+            b->out[k] = f_nodes[k];
+            b->layout[k] = layout_hash(b->ctx[k]);
+        }
     }
     // order the replay after the caller's prior work and the caller's later work after it
     if (cudaEventRecord(b->in, b->stream) != cudaSuccess || cudaStreamWaitEvent(b->cap, b->in, 0) != cudaSuccess ||

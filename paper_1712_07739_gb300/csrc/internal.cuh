@@ -140,6 +140,11 @@ struct gbfmm_ctx {
 
 // error helpers
 int set_err(gbfmm_ctx *c, int code, const std::string &msg);
+
+// Hash of everything an evaluation's launches depend on besides the contents
+// of device memory: sizes, depth, options and every device pointer.  A graph
+// recorded from an evaluation stays valid while this value is unchanged.
+uint64_t layout_hash(const gbfmm_ctx *ctx);  // api.cu
 #define CK(call)                                                                   \
     do {                                                                           \
         cudaError_t e_ = (call);                                                   \

@@ -28,6 +28,7 @@
 // winds down, freeing its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,9 +63,22 @@ struct M2LParams {
     int tmem_cols;  // power of two >= ncta
     int split;      // residual passes on the near offsets
     int drop_first; // failure-detection test: arm the first stage but issue no load into it
-    int kstep;      // operand elements per 128-byte row: 64 (bf16) or 32 (tf32)
+    int kstep;      // operand elements per 128-byte row: 64 (bf16, fp16) or 32 (tf32)
     uint32_t idesc; // tcgen05 instruction descriptor
+    const unsigned *wmax;  // FP16 mode: per-level max |W| bits (the W scale), else null
+    float inv_op_scale;    // FP16 mode: 1 / operator scale, else 1
 };
+
+// FP16 mode: power of two that brings a level's largest |W| into [2^12, 2^13)
+// (FP16 is normal from 2^-14 to 65504, so 26 binades below the largest value
+// keep full relative precision); 1 for a level without values
+__device__ __forceinline__ float wscale_of(unsigned bits) {
+    const float mx = __uint_as_float(bits);
+    if (!(mx > 0.f)) return 1.f;
+    int e;
+    frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+    return ldexpf(1.f, 13 - e);
+}
 
 constexpr int kStageA = 128 * 64 * 2;  // 16 KB
 
@@ -143,8 +157,9 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
 // instruction descriptor: D f32 (bits 4-5 = 1), A and B format (bits 7-9,
 // 10-12: 1 = bf16 for kind::f16, 2 = tf32 for kind::tf32), both K-major,
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28
-inline uint32_t idesc_of(int M, int N, bool tf32) {
-    const uint32_t f = tf32 ? 2u : 1u;
+inline uint32_t idesc_of(int M, int N, bool tf32, bool fp16) {
+    // operand formats: kind::tf32 -> 2 (TF32); kind::f16 -> 0 (F16) or 1 (BF16); D in F32
+    const uint32_t f = tf32 ? 2u : (fp16 ? 0u : 1u);
     return (1u << 4) | (f << 7) | (f << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
@@ -332,7 +347,8 @@ __global__ void __launch_bounds__(192, 1)
         const int px = bx0 + rx, py = by0 + ry, pz = bz0 + rz;
         const bool valid = ok && px < m && py < m && pz < m;
         const int64_t g = cell_base_d(level) + (int64_t(2 * pz + cz) * n + (2 * py + cy)) * n + (2 * px + cx);
-        const float sc = float(double(n) / box->H) * float(double(n) / box->H);
+        float sc = float(double(n) / box->H) * float(double(n) / box->H);
+        if (P.wmax) sc *= P.inv_op_scale / wscale_of(P.wmax[level]);
         float *dst = S + g * int64_t(P.nvalid);
         if (ok && !any_src) {
             // no occupied source anywhere in the interaction list: zero local values
@@ -371,13 +387,18 @@ template <>
 __device__ __forceinline__ float to_elem<float>(double v) {
     return float(v);
 }
+template <>
+__device__ __forceinline__ __half to_elem<__half>(double v) {
+    return __double2half(v);
+}
+__device__ __forceinline__ double elem_value(__half x) { return double(__half2float(x)); }
 __device__ __forceinline__ double elem_value(__nv_bfloat16 x) { return double(__bfloat162float(x)); }
 __device__ __forceinline__ double elem_value(float x) { return double(x); }
 
 template <typename E>
 __global__ void k_build_ops(int p, int lat_n, int Np, int Kp, const double *__restrict__ Klat,
                             const int *__restrict__ off_xyz, const int *__restrict__ lo_of, int n_off,
-                            E *__restrict__ Thi, E *__restrict__ Tlo) {
+                            double scale, E *__restrict__ Thi, E *__restrict__ Tlo) {
     const int64_t total = int64_t(n_off) * Np * Kp;
     const int P3 = p * p * p;
     const int R0 = (lat_n - 1) / 2;
@@ -393,7 +414,7 @@ __global__ void k_build_ops(int p, int lat_n, int Np, int Kp, const double *__re
             const int Dx = ox * (p - 1) + (l % p) - (mm % p) + R0;
             const int Dy = oy * (p - 1) + ((l / p) % p) - ((mm / p) % p) + R0;
             const int Dz = oz * (p - 1) + (l / (p * p)) - (mm / (p * p)) + R0;
-            v = Klat[((int64_t(Dz) * lat_n + Dy) * lat_n + Dx) * 54 + ab * 9 + wr];
+            v = scale * Klat[((int64_t(Dz) * lat_n + Dy) * lat_n + Dx) * 54 + ab * 9 + wr];
         }
         const E hi = to_elem<E>(v);
         Thi[idx] = hi;
@@ -405,8 +426,9 @@ __global__ void k_build_ops(int p, int lat_n, int Np, int Kp, const double *__re
 // W (FP32, [cell][p^3 * 9]) -> parity-split BF16 hi / lo, [class][mz][my][mx][Kp] per level
 template <typename E>
 __global__ void k_pack_w(int level, int P3, int Kp, const float *__restrict__ W, const int *__restrict__ occ,
-                         E *__restrict__ hi, E *__restrict__ lo) {
+                         const unsigned *__restrict__ wmax, E *__restrict__ hi, E *__restrict__ lo) {
     const int n = 1 << level, m = n / 2;
+    const double s = wmax ? double(wscale_of(wmax[level])) : 1.0;
     const int64_t cells = int64_t(n) * n * n;
     const int64_t total = cells * Kp;
     for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
@@ -419,10 +441,38 @@ __global__ void k_pack_w(int level, int P3, int Kp, const float *__restrict__ W,
         const int64_t g = cell_base_d(level) + lin;
         float v = 0.f;
         if (k < 9 * P3 && occ[g] > 0) v = W[g * 9 * P3 + k];
-        const E h = to_elem<E>(double(v));
+        const double vs = s * double(v);
+        const E h = to_elem<E>(vs);
         hi[dst] = h;
-        if (lo) lo[dst] = to_elem<E>(double(v) - elem_value(h));
+        if (lo) lo[dst] = to_elem<E>(vs - elem_value(h));
     }
+}
+
+// largest |W| over the occupied cells of one level (non-negative floats order
+// like their bit patterns)
+__global__ void k_wmax(int level, int P3, const float *__restrict__ W, const int *__restrict__ occ,
+                       unsigned *__restrict__ wmax) {
+    const int64_t cells = int64_t(1) << (3 * level), base = cell_base_d(level);
+    const int64_t total = cells * 9 * P3;
+    float mx = 0.f;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t g = base + idx / (9 * P3);
+        if (occ[g] > 0) mx = fmaxf(mx, fabsf(W[base * 9 * P3 + idx]));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(wmax + level, __float_as_uint(mx));
+}
+
+// largest |K| over the kernel lattice, skipping the singular origin
+__global__ void k_lattice_absmax(int64_t n_pts, int64_t origin, const double *__restrict__ Klat,
+                                 unsigned long long *__restrict__ out) {
+    double mx = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n_pts * 54;
+         i += int64_t(gridDim.x) * blockDim.x)
+        if (i / 54 != origin && isfinite(Klat[i])) mx = fmax(mx, fabs(Klat[i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
 }
 
 // brick flags: one byte per (class, aligned 8 x 4 x 4 brick) of a level
@@ -464,6 +514,7 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     const int p = ctx->opt.p, P3 = p * p * p;
     TcPlan &T = ctx->tc;
     T.tf32 = ctx->opt.m2l_split == 3 ? 1 : 0;
+    T.fp16 = (ctx->opt.m2l_split == 4 || ctx->opt.m2l_split == 5) ? 1 : 0;
     T.esz = T.tf32 ? 4 : 2;
     T.Kp = ((9 * P3 + 63) / 64) * 64;
     // N per MMA: multiple of 16, three of them per block, 3 nsub <= 512 TMEM columns
@@ -495,7 +546,8 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
                 off.push_back(ox);
                 off.push_back(oy);
                 off.push_back(oz);
-                const bool split = !T.tf32 && (ctx->opt.m2l_split == 2 || (ctx->opt.m2l_split == 0 && mx == 2));
+                const int sm = ctx->opt.m2l_split;
+                const bool split = !T.tf32 && (sm == 2 || ((sm == 0 || sm == 5) && mx == 2));
                 lo_of.push_back(split ? n_lo++ : -1);
             }
     T.n_off = int(off.size() / 3);
@@ -541,13 +593,40 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     CK(cudaMalloc(&T.Thi, hi_elems * T.esz));
     CK(cudaMalloc(&T.Tlo, std::max<size_t>(lo_elems, 1) * T.esz));
     T.split = n_lo > 0 ? 1 : 0;
+    T.op_scale = 1.0;
+    if (T.fp16) {
+        // one power of two for all operators: the largest lattice value maps below 2^14
+        unsigned long long *d_mx = nullptr, mx_bits = 0;
+        CK(cudaMalloc(&d_mx, sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(d_mx, 0, sizeof(unsigned long long), ctx->stream));
+        const int64_t n_pts = int64_t(ctx->lat_n) * ctx->lat_n * ctx->lat_n;
+        const int64_t origin = n_pts / 2;  // lattice centre, D = 0
+        ++ctx->launches;
+        k_lattice_absmax<<<1024, 256, 0, ctx->stream>>>(n_pts, origin, ctx->d_Klat, d_mx);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&mx_bits, d_mx, sizeof(mx_bits), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        cudaFree(d_mx);
+        double mx = 0.0;
+        std::memcpy(&mx, &mx_bits, sizeof(mx));
+        if (mx > 0.0) {
+            int e = 0;
+            std::frexp(mx, &e);
+            T.op_scale = std::ldexp(1.0, 14 - e);
+        }
+        if (!T.d_wmax) CK(cudaMalloc(&T.d_wmax, GB_TC_MAXLEV * sizeof(unsigned)));
+    }
     ++ctx->launches;
     if (T.tf32)
         k_build_ops<float><<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(
-            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, T.n_off, (float *)T.Thi, (float *)nullptr);
+            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, T.n_off, 1.0, (float *)T.Thi, (float *)nullptr);
+    else if (T.fp16)
+        k_build_ops<__half><<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(
+            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, T.n_off, T.op_scale, (__half *)T.Thi,
+            (__half *)T.Tlo);
     else
         k_build_ops<__nv_bfloat16><<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(
-            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, T.n_off, (__nv_bfloat16 *)T.Thi,
+            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, T.n_off, 1.0, (__nv_bfloat16 *)T.Thi,
             (__nv_bfloat16 *)T.Tlo);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
@@ -560,11 +639,14 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
 }
 
 static int encode(gbfmm_ctx *ctx, CUtensorMap *tm, void *base, int rank, const cuuint64_t *dims,
-                  const cuuint64_t *strides, const cuuint32_t *boxd, bool f32) {
+                  const cuuint64_t *strides, const cuuint32_t *boxd, const TcPlan &T) {
     EncodeTiled enc = get_encoder();
     if (!enc) return set_err(ctx, GBFMM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = enc(tm, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, cuuint32_t(rank),
+    const CUtensorMapDataType dt = T.tf32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : T.fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = enc(tm, dt, cuuint32_t(rank),
                      base, dims, strides, boxd, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -631,23 +713,34 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     const int L = ctx->L, p = ctx->opt.p, P3 = p * p * p;
     static M2LParams prm;  // large: build on the heap-like static, copied by value at launch
     std::memset(&prm, 0, sizeof(prm));
+    if (T.fp16) CK(cudaMemsetAsync(T.d_wmax, 0, GB_TC_MAXLEV * sizeof(unsigned), ctx->stream));
     for (int l = 2; l < L; ++l) {
         const int m = 1 << (l - 1);
-        ++ctx->launches;
         const int64_t el = (int64_t(1) << (3 * l)) * T.Kp;
         void *whi = (char *)T.Whi + T.wofs[l] * T.esz, *wlo = (char *)T.Wlo + T.wofs[l] * T.esz;
-        if (T.tf32)
-            k_pack_w<float><<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, (float *)whi, (float *)nullptr);
-        else
-            k_pack_w<__nv_bfloat16><<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, (__nv_bfloat16 *)whi,
-                                                                             (__nv_bfloat16 *)wlo);
+        if (T.tf32) {
+            ++ctx->launches;
+            k_pack_w<float><<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, nullptr, (float *)whi,
+                                                                    (float *)nullptr);
+        } else if (T.fp16) {
+            const int64_t vals = (int64_t(1) << (3 * l)) * 9 * P3;
+            ctx->launches += 2;
+            k_wmax<<<unsigned(std::min<int64_t>(nblk(vals, 256), 4 * 152)), 256, 0, ctx->stream>>>(l, P3, Wf, occ,
+                                                                                                   T.d_wmax);
+            k_pack_w<__half><<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, T.d_wmax, (__half *)whi,
+                                                                     (__half *)wlo);
+        } else {
+            ++ctx->launches;
+            k_pack_w<__nv_bfloat16><<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, nullptr,
+                                                                             (__nv_bfloat16 *)whi, (__nv_bfloat16 *)wlo);
+        }
         const cuuint64_t dims[5] = {cuuint64_t(T.Kp), cuuint64_t(m), cuuint64_t(m), cuuint64_t(m), 8};
         const cuuint64_t row = cuuint64_t(T.Kp) * T.esz;
         const cuuint64_t strides[4] = {row, row * m, row * m * m, row * m * m * m};
         const cuuint32_t boxd[5] = {cuuint32_t(128 / T.esz), 8, 4, 4, 1};
-        int rc = encode(ctx, &prm.tmW[l], whi, 5, dims, strides, boxd, T.tf32);
+        int rc = encode(ctx, &prm.tmW[l], whi, 5, dims, strides, boxd, T);
         if (rc) return rc;
-        rc = encode(ctx, &prm.tmWlo[l], wlo, 5, dims, strides, boxd, T.tf32);
+        rc = encode(ctx, &prm.tmWlo[l], wlo, 5, dims, strides, boxd, T);
         if (rc) return rc;
     }
     CK(cudaMemsetAsync(T.d_bocc, 0, T.bocc_tot, ctx->stream));
@@ -659,15 +752,17 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
         const cuuint64_t dims[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(T.n_off)};
         const cuuint64_t strides[2] = {cuuint64_t(T.Kp) * T.esz, cuuint64_t(T.Kp) * T.esz * T.Np};
         const cuuint32_t boxd[3] = {cuuint32_t(128 / T.esz), cuuint32_t(T.nsub), 1};
-        int rc = encode(ctx, &prm.tmT, T.Thi, 3, dims, strides, boxd, T.tf32);
+        int rc = encode(ctx, &prm.tmT, T.Thi, 3, dims, strides, boxd, T);
         if (rc) return rc;
         const cuuint64_t dl[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(std::max(T.n_lo, 1))};
-        rc = encode(ctx, &prm.tmTlo, T.Tlo, 3, dl, strides, boxd, T.tf32);
+        rc = encode(ctx, &prm.tmTlo, T.Tlo, 3, dl, strides, boxd, T);
         if (rc) return rc;
     }
     prm.kstep = 128 / T.esz;
     prm.kb = T.Kp / prm.kstep;
-    prm.idesc = idesc_of(128, T.nsub, T.tf32);
+    prm.idesc = idesc_of(128, T.nsub, T.tf32, T.fp16);
+    prm.wmax = T.fp16 ? T.d_wmax : nullptr;
+    prm.inv_op_scale = float(1.0 / T.op_scale);
     prm.nsub = T.nsub;
     prm.ncta = T.ncta;
     prm.nvalid = 6 * P3;
@@ -704,7 +799,7 @@ int m2l_tc_status(gbfmm_ctx *ctx, int *out) {
 
 void m2l_tc_free(gbfmm_ctx *ctx) {
     TcPlan &T = ctx->tc;
-    void *ps[] = {T.Thi, T.Tlo, T.Whi, T.Wlo, T.d_work, T.d_status, T.d_bocc, T.d_bocc_ofs};
+    void *ps[] = {T.Thi, T.Tlo, T.Whi, T.Wlo, T.d_work, T.d_status, T.d_bocc, T.d_bocc_ofs, T.d_wmax};
     for (void *q : ps)
         if (q) cudaFree(q);
     T = TcPlan{};

@@ -14,6 +14,10 @@ struct TcPlan {
     int n_off = 0, n_lo = 0;   // operators and residual operators
     int split = 1;             // residual passes on offsets with max |o_i| = 2
     int tf32 = 0;              // operands in FP32 storage, MMA kind::tf32 (no residual passes)
+    int fp16 = 0;              // FP16 operands: operators x op_scale, multipole values x a power of
+                               // two per level chosen from the level's largest |W|
+    double op_scale = 1.0;     // power of two applied to the FP16 operators
+    unsigned *d_wmax = nullptr;  // per level: bits of max |W| over occupied cells (FP16 mode)
     int esz = 2;               // operand element size in bytes
     void *Thi = nullptr, *Tlo = nullptr;  // operators [n_off][Np][Kp] (bf16, or fp32 when tf32)
     void *Whi = nullptr, *Wlo = nullptr;  // packed multipole weights

@@ -171,6 +171,8 @@ int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
     T.n_lo = S.n_lo;
     T.split = S.split;
     T.tf32 = S.tf32;
+    T.fp16 = S.fp16;
+    T.op_scale = S.op_scale;
     T.esz = S.esz;
     T.Thi = S.Thi;
     T.Tlo = S.Tlo;
@@ -178,6 +180,7 @@ int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
         CK(cudaMalloc(&T.d_status, sizeof(int)));
         CK(cudaMemset(T.d_status, 0, sizeof(int)));
     }
+    if (T.fp16 && !T.d_wmax) CK(cudaMalloc(&T.d_wmax, GB_TC_MAXLEV * sizeof(unsigned)));
     ctx->borrowed_material = true;
     ctx->have_material = true;
     return GBFMM_OK;

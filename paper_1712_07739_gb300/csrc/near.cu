@@ -687,12 +687,12 @@ int near_prepare(gbfmm_ctx *ctx) {
     return GBFMM_OK;
 }
 
-// work list for the near kernels (no host synchronisation: the item count
-// stays on the device and surplus warps return)
-static int build_items(gbfmm_ctx *ctx, const int *tstart, int64_t n_targets, int *&n_items, int2 *&items,
-                       int64_t &cap) {
+// capacity of the near-field work list for n_targets targets: called when
+// the tree is built, so that an evaluation recorded into a CUDA graph
+// allocates nothing
+int near_alloc(gbfmm_ctx *ctx, int64_t n_targets) {
     const int64_t nl = ctx->n_leaves;
-    cap = nl + n_targets / 32 + 1;
+    const int64_t cap = nl + n_targets / 32 + 1;
     NearWork &W = ctx->nw;
     if (cap > W.cap || nl > W.cap_leaves) {
         void *ps[] = {W.items, W.sorted, W.keys, W.cnt, W.key_of, W.off, W.misc};
@@ -709,6 +709,17 @@ static int build_items(gbfmm_ctx *ctx, const int *tstart, int64_t n_targets, int
         W.cap = cap;
         W.cap_leaves = nl;
     }
+    return GBFMM_OK;
+}
+
+// work list for the near kernels (no host synchronisation: the item count
+// stays on the device and surplus warps return)
+static int build_items(gbfmm_ctx *ctx, const int *tstart, int64_t n_targets, int *&n_items, int2 *&items,
+                       int64_t &cap) {
+    const int64_t nl = ctx->n_leaves;
+    cap = nl + n_targets / 32 + 1;
+    if (int rc = near_alloc(ctx, n_targets)) return rc;
+    NearWork &W = ctx->nw;
     cudaStream_t st = ctx->stream;
     CK(cudaMemsetAsync(W.misc, 0, 192 * sizeof(int), st));
     CK(cudaMemsetAsync(W.key_of, 0, nl * sizeof(int), st));

@@ -58,3 +58,24 @@ def test_batch_autotuned_depths():
         f = gb.FMM(p=4, levels=info[k]["levels"], precision="mixed", h_mode="circle", circle_q=24).set_material(CUB)
         f.build(_gpu(n), _gpu(s), _gpu(b))
         assert np.array_equal(F[k].cpu().numpy(), f.nodal_forces().cpu().numpy())
+
+
+def test_batch_rebuild_with_another_network_rerecords():
+    """Replacing one network (other size, other buffers) invalidates the
+    recorded graph: the next evaluation records a new one and matches a
+    separate context; rebuilding the same network keeps results identical."""
+    import paper_1712_07739_gb300 as gb
+
+    nets = _nets()
+    bt = gb.Batch(len(nets), p=4, levels=4, precision="mixed", h_mode="circle", circle_q=24).set_material(CUB)
+    for k, (n, s, b) in enumerate(nets):
+        bt.build(k, _gpu(n), _gpu(s), _gpu(b))
+    F0 = [f.cpu().numpy().copy() for f in bt.nodal_forces()]
+    other = synth.polygon_loops(n_segs=14000, n_loops=300, seed=99, box=0.8)
+    bt.build(1, _gpu(other[0]), _gpu(other[1]), _gpu(other[2]))
+    F1 = [f.cpu().numpy().copy() for f in bt.nodal_forces()]
+    f = gb.FMM(p=4, levels=4, precision="mixed", h_mode="circle", circle_q=24).set_material(CUB)
+    f.build(_gpu(other[0]), _gpu(other[1]), _gpu(other[2]))
+    assert np.array_equal(F1[1], f.nodal_forces().cpu().numpy())
+    for k in (0, 2, 3):
+        assert np.array_equal(F1[k], F0[k]), k

@@ -49,7 +49,9 @@ def _forces(nodes, segs, b, wl, **over):
 
 
 @pytest.mark.parametrize("label,over", [("bench configuration", {}),
-                                        ("BF16 split on all offsets, Q=32", {"m2l_split": 2, "circle_q": 32})])
+                                        ("BF16 split on all offsets, Q=32", {"m2l_split": 2, "circle_q": 32}),
+                                        ("FP16 scaled operands", {"m2l_split": 4}),
+                                        ("p=7, FP16 scaled operands", {"p": 7, "m2l_split": 4})])
 def test_full_size_sampled_nodes_match_direct_sum(c3_case, label, over):
     nodes, segs, b, wl, ids, Fo, used = c3_case
     F = _forces(nodes, segs, b, wl, **over)

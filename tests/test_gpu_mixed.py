@@ -59,7 +59,7 @@ def test_mixed_orders_depths(p, L):
     assert err <= TOL_MIXED
 
 
-@pytest.mark.parametrize("split", [0, 1, 2, 3])
+@pytest.mark.parametrize("split", [0, 1, 2, 3, 4, 5])
 def test_mixed_equals_fp64_gpu_pass_closely(split):
     """Slab-clustered network (the dense-wall structure of the 1M-segment
     workload, scaled down) at p = 6: every split setting meets 1e-4 on forces."""
@@ -81,7 +81,7 @@ def test_mixed_cubic_circle():
     assert err <= TOL_MIXED
 
 
-@pytest.mark.parametrize("split,tol", [(2, TOL_MIXED), (0, 1e-3)])
+@pytest.mark.parametrize("split,tol", [(2, TOL_MIXED), (0, 1e-3), (4, 1e-3)])
 def test_mixed_free_targets(split, tol):
     """Free points see mostly far field, so the BF16 rounding of the
     offsets without residual passes shows; splitting all offsets meets 1e-4."""

@@ -15,6 +15,7 @@
   target (Section 5.2, single-loop configuration).
 """
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -77,10 +78,56 @@ def test_theorem1_toeplitz(p):
     assert len(seen) == (2 * p - 1) ** 3
 
 
-def test_memory_formula():
-    # Eq. "mem_unif": 54 * 316 * (2p-1)^3 * f bytes; the paper quotes ~300 MB at p=7
-    mem = 54 * 316 * (2 * 7 - 1) ** 3 * 8
-    assert abs(mem / 1e9 - 0.30) < 0.01
+def _printed_values():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_printed_values.txt")
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                q, arg, val, unit, tol, where = [x.strip() for x in line.split("|")]
+                rows.append((q, arg, float(val), unit, float(tol), where))
+    return rows
+
+
+def _oracle_counts():
+    """Operator count and kernel components from the oracle's own structures:
+    the distinct offsets over the 8 child positions, and the width of one
+    node-kernel block."""
+    offs = set()
+    for c in itertools.product((0, 1), repeat=3):
+        offs.update(ob.interaction_offsets((4 + c[0], 4 + c[1], 4 + c[2])))
+    T = ob._node_kernels(ISO, 2, 0.25, (2, 0, 0))  # [l, 6, m, 9]
+    return len(offs), T.shape[1] * T.shape[3]
+
+
+def _unique_blocks(p):
+    T = ob._node_kernels(ISO, p, 0.25, (3, 1, -2))
+    idx = list(itertools.product(range(p), repeat=3))
+    keys = {tuple(np.round(T[li, :, mi, :].ravel() / np.abs(T).max(), 11))
+            for li in range(len(idx)) for mi in range(len(idx))}
+    return len(keys)
+
+
+def test_printed_values_reproduced():
+    """Every value in tests/golden/paper_printed_values.txt follows from the
+    oracle: operator counts from its interaction lists, unique blocks counted
+    on its node-kernel matrices, memory from Eq. "mem_unif" with those."""
+    n_ops, n_comp = _oracle_counts()
+    rows = _printed_values()
+    assert len(rows) == 6
+    for q, arg, val, unit, tol, where in rows:
+        if q == "lagrange_m2l_memory_fp64":
+            p = int(arg.split("=")[1])
+            got = n_comp * n_ops * (2 * p - 1) ** 3 * 8 / 1e9
+        elif q == "kernel_components":
+            got = n_comp
+        elif q == "precomputed_operators":
+            got = n_ops
+        elif q == "toeplitz_unique_blocks":
+            got = _unique_blocks(int(arg.split("=")[1]))
+        else:
+            raise AssertionError(q)
+        assert abs(got - val) <= tol, (q, arg, got, val, where)
 
 
 def _tiny(seed=0, n_loops=6, per=10):
