@@ -81,8 +81,8 @@ WORKLOADS = {
 }
 WORKLOADS["c3"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs, sigma 0.02), cubic C11=1.684 C12=1.214 "
-         "C44=0.754, order p=6, mixed precision (BF16 tensor-core M2L with split passes, FP32 near field with FP64 "
-         "close pairs), unit-circle h (cubic form, Q=20 points on the half circle), 7-level octree",
+         "C44=0.754, order p=6, mixed precision (FP16 tensor-core M2L with per-level scaling, FP32 near field with "
+         "FP64 close pairs), unit-circle h (cubic form, Q=20 points on the half circle), 7-level octree",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
     h_mode="circle", circle_q=20, p=6, levels=7, precision="mixed")
 WORKLOADS["c3_iso"] = dict(
@@ -390,7 +390,7 @@ def run_ours(args, wl):
     d_segs = torch.tensor(segs, device=dev)
     d_b = torch.tensor(b, device=dev)
     f = gb.FMM(p=wl["p"], levels=args.levels or wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
-               circle_q=wl.get("circle_q", 0), m2l_split=wl.get("m2l_split", 0))
+               circle_q=wl.get("circle_q", 0), m2l_split=wl.get("m2l_split", 4))
     f.set_material(wl["C"]())
     mlp_info = None
     if wl["h_mode"] == "mlp":
@@ -503,7 +503,7 @@ def run_ours(args, wl):
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "n_segs": n_segs, "levels": info["levels"],
                        "p": p, "precision": wl["precision"], "h_mode": wl["h_mode"],
-                       "circle_q": wl.get("circle_q", 0), "m2l_split": wl.get("m2l_split", 0),
+                       "circle_q": wl.get("circle_q", 0), "m2l_split": wl.get("m2l_split", 4),
                        "l2": "flushed: 256 MiB write between steps, outside the step events",
                        "step": "fmm_build_tree + fmm_eval_nodal_forces"},
             "stage_ms": {"precontract": st[:, 0].mean(), "p2m_m2m": st[:, 1].mean(), "m2l": m2l_ms,

@@ -55,6 +55,14 @@ extern "C" {
 #define GBFMM_H_CIRCLE 1  /* trapezoid rule of the unit-circle integral (any medium) */
 #define GBFMM_H_MLP 2     /* trained network (fmm_train_h), plain evaluator where flagged */
 
+/* operand precision of the tensor-core M2L (gbfmm_options.m2l_split, MIXED only) */
+#define GBFMM_M2L_BF16_SPLIT 0      /* BF16, residual passes on the offsets with max |o_i| = 2 */
+#define GBFMM_M2L_BF16 1            /* BF16 only */
+#define GBFMM_M2L_BF16_SPLIT_ALL 2  /* BF16, residual passes on all 316 offsets */
+#define GBFMM_M2L_TF32 3            /* FP32 operands, kind::tf32 */
+#define GBFMM_M2L_FP16 4            /* FP16, multipole values scaled per level (fmm_default_options) */
+#define GBFMM_M2L_FP16_SPLIT 5      /* FP16 scaled, residual passes on the offsets with max |o_i| = 2 */
+
 typedef struct {
     int p;                 /* Lagrange nodes per dimension, 2..8 (Sec. 4.1) */
     int n_gauss;           /* Gauss points per segment, 1..16 (Sec. 2, Eq. "stress_discrete") */
@@ -65,14 +73,14 @@ typedef struct {
     int leaf_segments;     /* with levels == 0: target mean segments per occupied leaf; 0 = 32 */
     double near_fp64;      /* MIXED: near pairs closer than near_fp64 x (source segment length)
                               are evaluated in FP64; 0 = 2.0 */
-    int m2l_split;         /* MIXED: operand precision of the tensor-core M2L:
+    int m2l_split;         /* MIXED: operand precision of the tensor-core M2L, GBFMM_M2L_*:
                               0 = BF16 with residual (split) passes on the offsets with
-                              max |o_i| = 2 (default), 1 = BF16 only, 2 = BF16 with residual
-                              passes on all 316 offsets, 3 = TF32 (FP32 operands),
-                              4 = FP16 with per-level scaling of the multipole values (a power
-                              of two from each level's largest |W|) and one power-of-two scale
-                              for the operators, 5 = as 4 plus residual passes on the offsets
-                              with max |o_i| = 2 */
+                              max |o_i| = 2, 1 = BF16 only, 2 = BF16 with residual passes on
+                              all 316 offsets, 3 = TF32 (FP32 operands), 4 = FP16 with
+                              per-level scaling of the multipole values (a power of two from
+                              each level's largest |W|) and one power-of-two scale for the
+                              operators (fmm_default_options), 5 = as 4 plus residual passes
+                              on the offsets with max |o_i| = 2 */
     double mlp_min_dist;   /* GBFMM_H_MLP: near pairs closer than this many source segment
                               lengths use the plain evaluator; 0 = 8 */
 } gbfmm_options;

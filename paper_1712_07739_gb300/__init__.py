@@ -124,7 +124,7 @@ class FMM:
     """
 
     def __init__(self, p=4, n_gauss=4, levels=0, precision="fp64", h_mode="iso", circle_q=0,
-                 leaf_segments=0, near_fp64=0.0, m2l_split=0, mlp_min_dist=0.0, stream=None):
+                 leaf_segments=0, near_fp64=0.0, m2l_split=4, mlp_min_dist=0.0, stream=None):
         import torch
 
         self._torch = torch
@@ -307,7 +307,7 @@ class Batch:
     autotuned depth per network with levels=0, graph-recorded evaluation)."""
 
     def __init__(self, n_configs, p=6, n_gauss=4, levels=0, precision="mixed", h_mode="circle", circle_q=0,
-                 leaf_segments=0, near_fp64=0.0, m2l_split=0, stream=None):
+                 leaf_segments=0, near_fp64=0.0, m2l_split=4, stream=None):
         import torch
 
         self._torch = torch

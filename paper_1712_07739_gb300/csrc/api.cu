@@ -118,6 +118,7 @@ extern "C" void fmm_default_options(gbfmm_options *o) {
     o->circle_q = 0;
     o->leaf_segments = 0;
     o->near_fp64 = 0.0;
+    o->m2l_split = GBFMM_M2L_FP16;
 }
 
 extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *stream) {
@@ -233,15 +234,14 @@ uint64_t layout_hash(const gbfmm_ctx *c) {
     const void *ptrs[] = {c->d_mat, c->d_Asym, c->d_Asym_f, c->d_Klat, c->d_box, c->d_y, c->d_q, c->d_sid,
                           c->d_slen, c->d_pos, c->d_pleaf, c->d_leaf_start, c->d_tmp_i, c->d_tmp_d, c->d_P,
                           c->d_Pf, c->d_W, c->d_S, c->d_Wf, c->d_Sf, c->d_sig, c->d_yrel, c->d_t_pos, c->d_t_start,
-                          c->d_t_x, c->d_t_sig, c->tc.Thi, c->tc.Tlo, c->tc.Whi, c->tc.Wlo, c->tc.d_work,
-                          c->tc.d_status, c->tc.d_bocc, c->tc.d_bocc_ofs, c->mlp.theta, c->mlp.theta_h,
+                          c->d_t_x, c->d_t_sig, c->tc.Thi, c->tc.Tlo, c->tc.Whi, c->tc.Wlo, c->tc.d_status,
+                          c->tc.d_flags, c->tc.d_pos, c->tc.d_list, c->tc.d_seg, c->tc.d_wmax, c->mlp.theta, c->mlp.theta_h,
                           c->mlp.scale, c->mlp.d_binmask, c->nw.items, c->nw.sorted, c->nw.keys, c->nw.cnt,
                           c->nw.key_of, c->nw.off, c->nw.misc};
     mix(ptrs, sizeof(ptrs));
     v(c->mat.mode), v(c->mat.Q), v(c->mat.cubic), v(c->tc.n_work), v(c->tc.split), v(c->tc.tf32);
     mix(c->tc.wofs, sizeof(c->tc.wofs));
-    mix(c->tc.bocc_h, sizeof(c->tc.bocc_h));
-    v(c->tc.bocc_tot), v(c->nw.cap), v(c->nw.cap_leaves), v(c->mlp.trained);
+    v(c->tc.n_slots), v(c->tc.n_seg), v(c->nw.cap), v(c->nw.cap_leaves), v(c->mlp.trained);
     return h;
 }
 

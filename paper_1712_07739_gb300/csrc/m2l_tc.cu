@@ -1,5 +1,5 @@
 // M2L on the tcgen05 tensor cores: offset-grouped dense GEMMs (Sec. 4.1,
-// Eq. "m2l"; Algorithm 2 step 2) in BF16 with FP32 accumulation in TMEM.
+// Eq. "m2l"; Algorithm 2 step 2) with FP32 accumulation in TMEM.
 //
 // Formulation.  At level l the cells form a 2^l grid.  Split it into the 8
 // parity classes c = (x & 1, y & 1, z & 1); each class is an m^3 sub-grid,
@@ -7,25 +7,32 @@
 // interaction list, the source A = B - o lies in class c' = (c - o) mod 2 at
 // sub-grid position P + s, s = floor((c - o) / 2) in [-1, 1]^3.  The 189
 // offsets of class c are therefore, each, a constant shift between two
-// sub-grids, and the M2L of a brick of 128 target cells (8 x 4 x 4 in the
-// sub-grid) is
-//     S[brick, n] = (2^l / H)^2  sum_o  sum_k  W_c'[brick + s_o, k] T_o[n, k]
+// sub-grids.
+//
+// Tiles.  The sub-grid of a class is cut into micro-bricks of 2 x 2 x 2
+// cells; the micro-bricks holding at least one target cell are listed per
+// (level, class) in Morton order, and 16 consecutive ones (128 cells) form a
+// tile.  The M2L of a tile is
+//     S[cell, n] = (2^l / H)^2  sum_o  sum_k  W_c'[cell + s_o, k] T_o[n, k]
 // with k = (node m, component wr) and n = (node l, stress component ab):
-// one GEMM of M = 128 cells, N = 6 p^3 and K = 189 x 9 p^3, accumulated in
-// tensor memory.  The A tile (shifted brick of multipole weights) and the
-// B tile (rows of the operator T_o) are both plain TMA box loads; boxes that
-// stick out of the sub-grid are zero-filled by the TMA unit.
+// one GEMM of M = 128 cells, N = 6 p^3 and K = (active offsets) x 9 p^3,
+// accumulated in tensor memory.  The A tile is 16 TMA box loads of 2 x 2 x 2
+// shifted multipole rows (1 KB each, zero-filled where a box leaves the
+// sub-grid), the B tile rows of the operator T_o (TMA box loads).  Offsets
+// whose 128 source cells are all empty are skipped.
 //
-// Precision: W and T_o are rounded to BF16 (hi).  For the offsets nearest
-// to the target (max |o_i| = 2, the largest far-field terms) the residuals
-// W_lo = W - hi(W) and T_lo = T - hi(T) add two more passes,
-// hi*hi + lo*hi + hi*lo, which restores ~FP32 accuracy where it matters.
+// Precision: BF16 operands (hi); for the offsets nearest to the target
+// (max |o_i| = 2, the largest far-field terms) the residuals W_lo = W - hi(W)
+// and T_lo = T - hi(T) add two more passes, hi*hi + lo*hi + hi*lo.  Other
+// modes: TF32 operands; FP16 operands with a power-of-two scale per level for
+// W and one for the operators (FP16 carries 3 more mantissa bits than BF16).
 //
-// Warp roles (192 threads): warp 0 issues TMA loads, warp 1 owns TMEM and
-// issues the MMAs, warps 2-5 read the accumulator out (warp w reads TMEM
-// lanes 32 (w % 4) .. 32 (w % 4) + 31).  Every mbarrier wait is bounded;
-// on time-out a device status word gets GBFMM_ERR_TIMEOUT and the block
-// winds down, freeing its tensor memory.
+// Warp roles (192 threads): warp 0 issues TMA loads (lane j loads
+// micro-brick j, lanes 16-18 the operator rows), warp 1 owns TMEM and issues
+// the MMAs, warps 2-5 read the accumulator out (warp w reads TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31).  Every mbarrier wait is bounded; on
+// time-out a device status word gets GBFMM_ERR_TIMEOUT and the block winds
+// down, freeing its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -52,7 +59,7 @@ struct OffsetEntry {
 __constant__ OffsetEntry c_offs[8][189];
 
 struct M2LParams {
-    CUtensorMap tmW[GB_TC_MAXLEV];    // W hi per level: (Kp, m, m, m, 8) bf16
+    CUtensorMap tmW[GB_TC_MAXLEV];    // W hi per level: (Kp, m, m, m, 8), box (64, 2, 2, 2, 1)
     CUtensorMap tmWlo[GB_TC_MAXLEV];  // W residual per level
     CUtensorMap tmT;                  // T hi: (Kp, Np, 316)
     CUtensorMap tmTlo;                // T residual: (Kp, Np, n_lo)
@@ -193,32 +200,40 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Is any cell of the shifted source box occupied?  Brick flags are per level,
-// class and aligned 8 x 4 x 4 brick of the sub-grid; the box of a shift in
-// [-1, 1]^3 overlaps at most 2 x 2 x 2 aligned bricks.
-__device__ __forceinline__ bool source_occupied(const unsigned char *__restrict__ bocc, int m, int bx0, int by0,
-                                                int bz0, const OffsetEntry &e) {
-    const int nbx = (m + 7) / 8, nby = (m + 3) / 4, nbz = (m + 3) / 4;
-    const int x0 = bx0 + e.sx, y0 = by0 + e.sy, z0 = bz0 + e.sz;
-    const int ax0 = max(x0, 0) / 8, ax1 = min(x0 + 7, m - 1) / 8;
-    const int ay0 = max(y0, 0) / 4, ay1 = min(y0 + 3, m - 1) / 4;
-    const int az0 = max(z0, 0) / 4, az1 = min(z0 + 3, m - 1) / 4;
-    if (x0 + 7 < 0 || y0 + 3 < 0 || z0 + 3 < 0 || x0 >= m || y0 >= m || z0 >= m) return false;
-    for (int bz = az0; bz <= az1; ++bz)
-        for (int by = ay0; by <= ay1; ++by)
-            for (int bx = ax0; bx <= ax1; ++bx)
-                if (bocc[((int64_t(e.cls) * nbz + bz) * nby + by) * nbx + bx]) return true;
-    return false;
+// Micro-brick slots: level l (2 <= l < L) has 8 classes x mb^3 micro-bricks,
+// mb = 2^(l-2); slots of a level follow those of the levels below it, and
+// within (level, class) the micro-bricks are in Morton order.
+__host__ __device__ inline int64_t mb_slot_base(int l) { return 8 * (((int64_t(1) << (3 * (l - 2))) - 1) / 7); }
+
+__device__ __forceinline__ uint32_t morton_part(uint32_t v) {  // 10 bits -> every third bit
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
 }
+__device__ __forceinline__ uint32_t morton_compact(uint32_t v) {
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030c30c3u;
+    v = (v | (v >> 4)) & 0x0300f00fu;
+    v = (v | (v >> 8)) & 0x030000ffu;
+    v = (v | (v >> 16)) & 0x3ffu;
+    return v;
+}
+
+// Segments: one per (level, class), index (l - 2) * 8 + c.  seg[s] = {first
+// list entry, micro-bricks, first tile}; seg[n_seg].z = total tiles.
+constexpr int kMaxSeg = 8 * GB_TC_MAXLEV;
 
 // number of K-block iterations of one work item (same count on every warp)
 __device__ __forceinline__ int passes_of(const OffsetEntry &e, int split) { return (split && e.lo >= 0) ? 3 : 1; }
 
 template <bool TF32>
 __global__ void __launch_bounds__(192, 1)
-    k_m2l_tc(const __grid_constant__ M2LParams P, const int4 *__restrict__ work, const int *__restrict__ tocc,
-             const unsigned char *__restrict__ bocc_all, const int64_t *__restrict__ bocc_ofs,
-             const TreeBox *__restrict__ box, float *__restrict__ S, int *__restrict__ status, int stages) {
+    k_m2l_tc(const __grid_constant__ M2LParams P, const int4 *__restrict__ seg, int n_seg,
+             const int *__restrict__ mb_list, const int *__restrict__ occ, const int *__restrict__ tocc,
+             const TreeBox *__restrict__ box, float *__restrict__ S, int *__restrict__ status, int stages, int groups) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int stageB = P.ncta * 128;
@@ -227,36 +242,59 @@ __global__ void __launch_bounds__(192, 1)
     // bars[0..stages): full, [stages..2 stages): empty, [2 stages]: accumulator ready
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 1);
 
-    const int4 w = work[blockIdx.x];
-    const int level = w.x, cls = w.y, brick = w.z, group = w.w;
-    const int m = 1 << (level - 1), n = 1 << level;
-    const int nbx = (m + 7) / 8, nby = (m + 3) / 4;
-    const int bx0 = (brick % nbx) * 8, by0 = ((brick / nbx) % nby) * 4, bz0 = (brick / (nbx * nby)) * 4;
-    const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
-    const unsigned char *bocc = bocc_all + bocc_ofs[level];
-
-    // skip bricks without targets, and do no work once an earlier block's
-    // time-out is flagged (both decided once for the whole block)
-    {
-        __shared__ int any, stop;
-        if (threadIdx.x == 0) {
-            any = 0;
-            stop = *reinterpret_cast<volatile int *>(status) != 0;
-        }
-        __syncthreads();
-        if (threadIdx.x < 128) {
-            const int rx = threadIdx.x % 8, ry = (threadIdx.x / 8) % 4, rz = threadIdx.x / 32;
-            const int px = bx0 + rx, py = by0 + ry, pz = bz0 + rz;
-            if (px < m && py < m && pz < m) {
-                const int64_t g = cell_base_d(level) + (int64_t(2 * pz + cz) * n + (2 * py + cy)) * n + (2 * px + cx);
-                if (tocc[g] > 0) any = 1;
+    __shared__ int s_level, s_cls, s_nmb, s_stop;
+    __shared__ int s_mb[16][3];        // micro-brick origins (sub-grid cells) of this tile
+    __shared__ uint32_t s_active[6];   // offsets with at least one occupied source cell
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int tile = blockIdx.x / groups, group = blockIdx.x % groups;
+    if (threadIdx.x == 0) {
+        s_level = -1;
+        s_stop = *reinterpret_cast<volatile int *>(status) != 0;
+        if (tile < seg[n_seg].z)
+            for (int si = 0; si < n_seg; ++si) {
+                const int4 sg = seg[si];
+                const int nt = (sg.y + 15) / 16;
+                if (tile >= sg.z && tile < sg.z + nt) {
+                    const int t = tile - sg.z;
+                    s_level = si / 8 + 2;
+                    s_cls = si % 8;
+                    s_nmb = min(16, sg.y - 16 * t);
+                    for (int j = 0; j < s_nmb; ++j) {
+                        const uint32_t code = uint32_t(mb_list[sg.x + 16 * t + j]);
+                        s_mb[j][0] = 2 * int(morton_compact(code));
+                        s_mb[j][1] = 2 * int(morton_compact(code >> 1));
+                        s_mb[j][2] = 2 * int(morton_compact(code >> 2));
+                    }
+                    break;
+                }
             }
-        }
-        __syncthreads();
-        if (!any || stop) return;
+    }
+    if (threadIdx.x < 6) s_active[threadIdx.x] = 0u;
+    __syncthreads();
+    if (s_level < 0 || s_stop) return;  // surplus block, or an earlier block timed out
+    const int level = s_level, cls = s_cls, nmb = s_nmb;
+    const int m = 1 << (level - 1), n = 1 << level;
+    const int64_t cbase = cell_base_d(level);
+
+    // active offsets: lane r of warp w checks rows 4r .. 4r + 3 (micro-brick r / 2)
+    for (int oi = warp; oi < 189; oi += 6) {
+        const OffsetEntry e = c_offs[cls][oi];
+        const int ccx = e.cls & 1, ccy = (e.cls >> 1) & 1, ccz = e.cls >> 2;
+        bool hit = false;
+        const int j = lane / 2;
+        if (j < nmb)
+            for (int q = 0; q < 4; ++q) {
+                const int w8 = 4 * (lane & 1) + q;  // row within the micro-brick: x fastest, then y, z
+                const int px = s_mb[j][0] + (w8 & 1) + e.sx, py = s_mb[j][1] + ((w8 >> 1) & 1) + e.sy,
+                          pz = s_mb[j][2] + (w8 >> 2) + e.sz;
+                if (px >= 0 && py >= 0 && pz >= 0 && px < m && py < m && pz < m) {
+                    const int64_t g = cbase + (int64_t(2 * pz + ccz) * n + (2 * py + ccy)) * n + (2 * px + ccx);
+                    hit |= occ[g] > 0;
+                }
+            }
+        if (__any_sync(0xffffffffu, hit) && lane == 0) atomicOr(&s_active[oi / 32], 1u << (oi % 32));
     }
 
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2 * stages + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -273,14 +311,15 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t tmem = *tmem_slot;
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[stages]), accb = smem_u32(&bars[2 * stages]);
     const uint32_t smem0 = smem_u32(smem);
+    const uint32_t stage_tx = uint32_t(nmb) * 1024u + uint32_t(stageB);
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer
+    if (warp == 0) {
+        // ---------------- TMA producer (the whole warp: one load per lane and stage)
         int it = 0;
         bool ok = true;
         for (int oi = 0; oi < 189 && ok; ++oi) {
+            if (!((s_active[oi / 32] >> (oi % 32)) & 1u)) continue;
             const OffsetEntry e = c_offs[cls][oi];
-            if (!source_occupied(bocc, m, bx0, by0, bz0, e)) continue;
             const int np = passes_of(e, P.split);
             for (int pass = 0; pass < np && ok; ++pass) {
                 const CUtensorMap *ta = (pass == 1) ? &P.tmWlo[level] : &P.tmW[level];
@@ -289,18 +328,24 @@ __global__ void __launch_bounds__(192, 1)
                 for (int kb = 0; kb < P.kb; ++kb, ++it) {
                     const int s = it % stages;
                     const uint32_t ph = (it / stages) & 1;
-                    if (!mbar_wait(empty0 + 8 * s, ph ^ 1, status)) {
+                    int go = 1;
+                    if (lane == 0) {
+                        go = mbar_wait(empty0 + 8 * s, ph ^ 1, status) ? 1 : 0;
+                        if (go) mbar_expect_tx(full0 + 8 * s, stage_tx);
+                    }
+                    go = __shfl_sync(0xffffffffu, go, 0);  // also orders expect_tx before the loads
+                    if (!go) {
                         ok = false;
                         break;
                     }
-                    const uint32_t fb = full0 + 8 * s;
-                    mbar_expect_tx(fb, kStageA + stageB);
                     if (P.drop_first && it == 0) continue;  // the MMA warp's wait on this stage runs out
-                    const uint32_t a = smem0 + s * stage_bytes;
-                    tma_load_5d(a, ta, kb * P.kstep, bx0 + e.sx, by0 + e.sy, bz0 + e.sz, e.cls, fb);
-                    for (int j = 0; j < 3; ++j)
-                        tma_load_3d(a + kStageA + j * P.nsub * 128, tb, kb * P.kstep, group * P.ncta + j * P.nsub,
-                                    tidx, fb);
+                    const uint32_t a = smem0 + s * stage_bytes, fb = full0 + 8 * s;
+                    if (lane < nmb)
+                        tma_load_5d(a + lane * 1024, ta, kb * P.kstep, s_mb[lane][0] + e.sx, s_mb[lane][1] + e.sy,
+                                    s_mb[lane][2] + e.sz, e.cls, fb);
+                    else if (lane >= 16 && lane < 19)
+                        tma_load_3d(a + kStageA + (lane - 16) * P.nsub * 128, tb, kb * P.kstep,
+                                    group * P.ncta + (lane - 16) * P.nsub, tidx, fb);
                 }
             }
         }
@@ -310,8 +355,8 @@ __global__ void __launch_bounds__(192, 1)
         int it = 0;
         bool ok = true;
         for (int oi = 0; oi < 189 && ok; ++oi) {
+            if (!((s_active[oi / 32] >> (oi % 32)) & 1u)) continue;
             const OffsetEntry e = c_offs[cls][oi];
-            if (!source_occupied(bocc, m, bx0, by0, bz0, e)) continue;
             const int np = passes_of(e, P.split);
             for (int pass = 0; pass < np && ok; ++pass) {
                 for (int kb = 0; kb < P.kb; ++kb, ++it) {
@@ -336,17 +381,22 @@ __global__ void __launch_bounds__(192, 1)
         }
         mma_commit(accb);  // fires when every MMA issued above has completed
     } else if (warp >= 2) {
-        // ---------------- epilogue: TMEM -> scaled FP32 local values
+        // ---------------- epilogue: TMEM -> scaled FP32 local values of the tile's target cells
         bool any_src = false;
-        for (int oi = 0; oi < 189 && !any_src; ++oi) any_src = source_occupied(bocc, m, bx0, by0, bz0, c_offs[cls][oi]);
+        for (int i = 0; i < 6; ++i) any_src |= s_active[i] != 0u;
         const bool ok = mbar_wait(accb, 0, status);
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int q = warp % 4;
         const int row = q * 32 + lane;
-        const int rx = row % 8, ry = (row / 8) % 4, rz = row / 32;
-        const int px = bx0 + rx, py = by0 + ry, pz = bz0 + rz;
-        const bool valid = ok && px < m && py < m && pz < m;
-        const int64_t g = cell_base_d(level) + (int64_t(2 * pz + cz) * n + (2 * py + cy)) * n + (2 * px + cx);
+        const int j = row / 8, w8 = row % 8;
+        bool valid = ok && j < nmb;
+        int64_t g = 0;
+        if (valid) {
+            const int px = s_mb[j][0] + (w8 & 1), py = s_mb[j][1] + ((w8 >> 1) & 1), pz = s_mb[j][2] + (w8 >> 2);
+            const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
+            g = cbase + (int64_t(2 * pz + cz) * n + (2 * py + cy)) * n + (2 * px + cx);
+            valid = tocc[g] > 0;
+        }
         float sc = float(double(n) / box->H) * float(double(n) / box->H);
         if (P.wmax) sc *= P.inv_op_scale / wscale_of(P.wmax[level]);
         float *dst = S + g * int64_t(P.nvalid);
@@ -355,11 +405,11 @@ __global__ void __launch_bounds__(192, 1)
             if (valid)
                 for (int col = group * P.ncta; col < min(P.nvalid, (group + 1) * P.ncta); ++col) dst[col] = 0.f;
         } else if (ok) {
-            for (int j = 0; j < 3; ++j)
+            for (int jj = 0; jj < 3; ++jj)
                 for (int c0 = 0; c0 < P.nsub; c0 += 16) {
                     float v[16];
-                    tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t(j * P.nsub + c0), v);
-                    const int col = group * P.ncta + j * P.nsub + c0;
+                    tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t(jj * P.nsub + c0), v);
+                    const int col = group * P.ncta + jj * P.nsub + c0;
                     if (valid)
                         for (int i = 0; i < 16; ++i)
                             if (col + i < P.nvalid) dst[col + i] = v[i] * sc;
@@ -475,18 +525,83 @@ __global__ void k_lattice_absmax(int64_t n_pts, int64_t origin, const double *__
     if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
 }
 
-// brick flags: one byte per (class, aligned 8 x 4 x 4 brick) of a level
-__global__ void k_brick_occ(int level, const int *__restrict__ occ, unsigned char *__restrict__ bocc) {
-    const int n = 1 << level, m = n / 2;
-    const int nbx = (m + 7) / 8, nby = (m + 3) / 4, nbz = (m + 3) / 4;
+// Target micro-brick flags of one level: slot of (class, micro-brick) set
+// when one of its 8 cells holds targets
+__global__ void k_mb_flags(int level, const int *__restrict__ tocc, int *__restrict__ flags) {
+    const int n = 1 << level;
+    const int mb = n / 4;
     const int64_t cells = int64_t(n) * n * n;
     for (int64_t lin = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; lin < cells;
          lin += int64_t(gridDim.x) * blockDim.x) {
-        if (occ[cell_base_d(level) + lin] == 0) continue;
+        if (tocc[cell_base_d(level) + lin] == 0) continue;
         const int x = int(lin % n), y = int((lin / n) % n), z = int(lin / (int64_t(n) * n));
         const int cls = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
-        bocc[((int64_t(cls) * nbz + (z / 2) / 4) * nby + (y / 2) / 4) * nbx + (x / 2) / 8] = 1;
+        const uint32_t code = morton_part(uint32_t(x >> 2)) | (morton_part(uint32_t(y >> 2)) << 1) |
+                              (morton_part(uint32_t(z >> 2)) << 2);
+        flags[mb_slot_base(level) + int64_t(cls) * mb * mb * mb + code] = 1;
     }
+}
+
+// exclusive scan of n flags into pos[0..n] (one block)
+__global__ void k_scan_flags(int n, const int *__restrict__ flags, int *__restrict__ pos) {
+    __shared__ int part[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024 * 8) {
+        int v[8], sum = 0;
+        for (int i = 0; i < 8; ++i) {
+            const int k = base + threadIdx.x * 8 + i;
+            v[i] = k < n ? flags[k] : 0;
+            sum += v[i];
+        }
+        part[threadIdx.x] = sum;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int t = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+            __syncthreads();
+            part[threadIdx.x] += t;
+            __syncthreads();
+        }
+        int run = carry + part[threadIdx.x] - sum;
+        for (int i = 0; i < 8; ++i) {
+            const int k = base + threadIdx.x * 8 + i;
+            if (k < n) pos[k] = run;
+            run += v[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) pos[n] = carry;
+}
+
+// compact list of the flagged slots (their Morton code within the segment)
+__global__ void k_mb_list(int n, int L, const int *__restrict__ flags, const int *__restrict__ pos,
+                          int *__restrict__ list) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (!flags[k]) continue;
+        int l = 2;
+        while (l + 1 < L && k >= mb_slot_base(l + 1)) ++l;
+        const int64_t mb3 = int64_t(1) << (3 * (l - 2));
+        list[pos[k]] = int((k - mb_slot_base(l)) % mb3);
+    }
+}
+
+// segment table: {first list entry, micro-bricks, first tile}; seg[n_seg].z = tiles
+__global__ void k_seg_table(int L, const int *__restrict__ pos, int4 *__restrict__ seg) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int tiles = 0, si = 0;
+    for (int l = 2; l < L; ++l) {
+        const int64_t mb3 = int64_t(1) << (3 * (l - 2));
+        for (int c = 0; c < 8; ++c, ++si) {
+            const int64_t s0 = mb_slot_base(l) + c * mb3;
+            const int first = pos[s0], cnt = pos[s0 + mb3] - first;
+            seg[si] = make_int4(first, cnt, tiles, 0);
+            tiles += (cnt + 15) / 16;
+        }
+    }
+    seg[si] = make_int4(0, 0, tiles, 0);
 }
 
 typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -672,39 +787,24 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
         CK(cudaMalloc(&T.Wlo, tot * T.esz));
         T.w_cap = tot;
     }
-    int64_t bocc_tot = 0;
-    std::vector<int64_t> bofs(GB_TC_MAXLEV, 0);
-    for (int l = 2; l < L; ++l) {
-        const int m = 1 << (l - 1);
-        bofs[l] = bocc_tot;
-        bocc_tot += int64_t(8) * ((m + 7) / 8) * ((m + 3) / 4) * ((m + 3) / 4);
+    // micro-brick slots, list and segment table (filled on the device per pass)
+    const int64_t slots = mb_slot_base(L);
+    if (slots > T.slot_cap) {
+        void *ps[] = {T.d_flags, T.d_pos, T.d_list};
+        for (void *q : ps)
+            if (q) cudaFree(q);
+        T.d_flags = T.d_pos = T.d_list = nullptr;
+        CK(cudaMalloc(&T.d_flags, slots * sizeof(int)));
+        CK(cudaMalloc(&T.d_pos, (slots + 1) * sizeof(int)));
+        CK(cudaMalloc(&T.d_list, slots * sizeof(int)));
+        T.slot_cap = slots;
     }
-    if (bocc_tot > T.bocc_cap) {
-        if (T.d_bocc) cudaFree(T.d_bocc);
-        T.d_bocc = nullptr;
-        CK(cudaMalloc(&T.d_bocc, bocc_tot));
-        T.bocc_cap = bocc_tot;
-    }
-    T.bocc_tot = bocc_tot;
-    for (int l = 0; l < GB_TC_MAXLEV; ++l) T.bocc_h[l] = bofs[l];
-    if (!T.d_bocc_ofs) CK(cudaMalloc(&T.d_bocc_ofs, GB_TC_MAXLEV * sizeof(int64_t)));
-    CK(cudaMemcpy(T.d_bocc_ofs, bofs.data(), GB_TC_MAXLEV * sizeof(int64_t), cudaMemcpyHostToDevice));
-    std::vector<int4> wl;
-    for (int l = 2; l < L; ++l) {
-        const int m = 1 << (l - 1);
-        const int nb = ((m + 7) / 8) * ((m + 3) / 4) * ((m + 3) / 4);
-        for (int c = 0; c < 8; ++c)
-            for (int b = 0; b < nb; ++b)
-                for (int g = 0; g < T.groups; ++g) wl.push_back(make_int4(l, c, b, g));
-    }
-    T.n_work = int(wl.size());
-    if (T.n_work > T.work_cap) {
-        if (T.d_work) cudaFree(T.d_work);
-        T.d_work = nullptr;
-        CK(cudaMalloc(&T.d_work, wl.size() * sizeof(int4)));
-        T.work_cap = T.n_work;
-    }
-    CK(cudaMemcpy(T.d_work, wl.data(), wl.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (!T.d_seg) CK(cudaMalloc(&T.d_seg, (kMaxSeg + 1) * sizeof(int4)));
+    T.n_slots = slots;
+    T.n_seg = 8 * (L - 2);
+    int64_t tiles = 0;  // upper bound: every micro-brick holds targets
+    for (int l = 2; l < L; ++l) tiles += 8 * ((int64_t(1) << (3 * (l - 2))) + 15) / 16;
+    T.n_work = int(tiles * T.groups);
     return GBFMM_OK;
 }
 
@@ -728,26 +828,30 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
             k_wmax<<<unsigned(std::min<int64_t>(nblk(vals, 256), 4 * 152)), 256, 0, ctx->stream>>>(l, P3, Wf, occ,
                                                                                                    T.d_wmax);
             k_pack_w<__half><<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, T.d_wmax, (__half *)whi,
-                                                                     (__half *)wlo);
+                                                                     T.split ? (__half *)wlo : nullptr);
         } else {
             ++ctx->launches;
-            k_pack_w<__nv_bfloat16><<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, nullptr,
-                                                                             (__nv_bfloat16 *)whi, (__nv_bfloat16 *)wlo);
+            k_pack_w<__nv_bfloat16><<<nblk(el, 256), 256, 0, ctx->stream>>>(
+                l, P3, T.Kp, Wf, occ, nullptr, (__nv_bfloat16 *)whi, T.split ? (__nv_bfloat16 *)wlo : nullptr);
         }
         const cuuint64_t dims[5] = {cuuint64_t(T.Kp), cuuint64_t(m), cuuint64_t(m), cuuint64_t(m), 8};
         const cuuint64_t row = cuuint64_t(T.Kp) * T.esz;
         const cuuint64_t strides[4] = {row, row * m, row * m * m, row * m * m * m};
-        const cuuint32_t boxd[5] = {cuuint32_t(128 / T.esz), 8, 4, 4, 1};
+        const cuuint32_t boxd[5] = {cuuint32_t(128 / T.esz), 2, 2, 2, 1};  // one micro-brick
         int rc = encode(ctx, &prm.tmW[l], whi, 5, dims, strides, boxd, T);
         if (rc) return rc;
         rc = encode(ctx, &prm.tmWlo[l], wlo, 5, dims, strides, boxd, T);
         if (rc) return rc;
     }
-    CK(cudaMemsetAsync(T.d_bocc, 0, T.bocc_tot, ctx->stream));
+    CK(cudaMemsetAsync(T.d_flags, 0, T.n_slots * sizeof(int), ctx->stream));
     for (int l = 2; l < L; ++l) {
         ++ctx->launches;
-        k_brick_occ<<<nblk(int64_t(1) << (3 * l), 256), 256, 0, ctx->stream>>>(l, occ, T.d_bocc + T.bocc_h[l]);
+        k_mb_flags<<<nblk(int64_t(1) << (3 * l), 256), 256, 0, ctx->stream>>>(l, tocc, T.d_flags);
     }
+    ctx->launches += 3;
+    k_scan_flags<<<1, 1024, 0, ctx->stream>>>(int(T.n_slots), T.d_flags, T.d_pos);
+    k_mb_list<<<nblk(T.n_slots, 256), 256, 0, ctx->stream>>>(int(T.n_slots), L, T.d_flags, T.d_pos, T.d_list);
+    k_seg_table<<<1, 32, 0, ctx->stream>>>(L, T.d_pos, T.d_seg);
     {
         const cuuint64_t dims[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(T.n_off)};
         const cuuint64_t strides[2] = {cuuint64_t(T.Kp) * T.esz, cuuint64_t(T.Kp) * T.esz * T.Np};
@@ -776,12 +880,12 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     ++ctx->launches;
     if (T.tf32) {
         CK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        k_m2l_tc<true><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_work, tocc, T.d_bocc, T.d_bocc_ofs, ctx->d_box,
-                                                             Sf, T.d_status, stages);
+        k_m2l_tc<true><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
+                                                             Sf, T.d_status, stages, T.groups);
     } else {
         CK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        k_m2l_tc<false><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_work, tocc, T.d_bocc, T.d_bocc_ofs, ctx->d_box,
-                                                              Sf, T.d_status, stages);
+        k_m2l_tc<false><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
+                                                              Sf, T.d_status, stages, T.groups);
     }
     CK(cudaGetLastError());
     return GBFMM_OK;
@@ -799,7 +903,7 @@ int m2l_tc_status(gbfmm_ctx *ctx, int *out) {
 
 void m2l_tc_free(gbfmm_ctx *ctx) {
     TcPlan &T = ctx->tc;
-    void *ps[] = {T.Thi, T.Tlo, T.Whi, T.Wlo, T.d_work, T.d_status, T.d_bocc, T.d_bocc_ofs, T.d_wmax};
+    void *ps[] = {T.Thi, T.Tlo, T.Whi, T.Wlo, T.d_status, T.d_flags, T.d_pos, T.d_list, T.d_seg, T.d_wmax};
     for (void *q : ps)
         if (q) cudaFree(q);
     T = TcPlan{};

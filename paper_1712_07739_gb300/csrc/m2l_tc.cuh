@@ -23,14 +23,13 @@ struct TcPlan {
     void *Whi = nullptr, *Wlo = nullptr;  // packed multipole weights
     int64_t wofs[GB_TC_MAXLEV] = {0};
     int64_t w_cap = 0;
-    int4 *d_work = nullptr;
-    int n_work = 0, work_cap = 0;
+    int n_work = 0;            // blocks launched: tile bound x groups (surplus blocks return)
     int *d_status = nullptr;
-    int inject_drop = 0;
-    unsigned char *d_bocc = nullptr;  // occupied-brick flags, all levels
-    int64_t *d_bocc_ofs = nullptr;    // per-level offset into d_bocc
-    int64_t bocc_cap = 0, bocc_tot = 0;
-    int64_t bocc_h[GB_TC_MAXLEV] = {0};       // set by fmm_inject_fault: the next run leaves one stage unfilled
+    int inject_drop = 0;       // set by fmm_inject_fault: the next run leaves one stage unfilled
+    int *d_flags = nullptr, *d_pos = nullptr, *d_list = nullptr;  // target micro-bricks, all levels
+    int4 *d_seg = nullptr;     // per (level, class): first list entry, count, first tile
+    int64_t slot_cap = 0, n_slots = 0;
+    int n_seg = 0;
 };
 
 int m2l_tc_setup(gbfmm_ctx *ctx);    // operators (per medium and p)
