@@ -172,7 +172,8 @@ extern "C" void fmm_destroy(gbfmm_ctx *ctx) {
     mlp_free(ctx);
     {
         NearWork &W = ctx->nw;
-        void *ps2[] = {W.items, W.sorted, W.keys, W.cnt, W.key_of, W.off, W.misc};
+        void *ps2[] = {W.items, W.sorted, W.keys, W.cnt, W.key_of, W.off, W.misc, W.pitems, W.psorted, W.pkeys,
+                       W.pmisc, W.part};
         for (void *q : ps2)
             if (q) cudaFree(q);
     }
@@ -237,7 +238,8 @@ uint64_t layout_hash(const gbfmm_ctx *c) {
                           c->d_t_x, c->d_t_sig, c->tc.Thi, c->tc.Tlo, c->tc.Whi, c->tc.Wlo, c->tc.d_status,
                           c->tc.d_flags, c->tc.d_pos, c->tc.d_list, c->tc.d_seg, c->tc.d_wmax, c->mlp.theta, c->mlp.theta_h,
                           c->mlp.scale, c->mlp.d_binmask, c->nw.items, c->nw.sorted, c->nw.keys, c->nw.cnt,
-                          c->nw.key_of, c->nw.off, c->nw.misc};
+                          c->nw.key_of, c->nw.off, c->nw.misc, c->nw.pitems, c->nw.psorted,
+                          c->nw.pkeys, c->nw.pmisc, c->nw.part};
     mix(ptrs, sizeof(ptrs));
     v(c->mat.mode), v(c->mat.Q), v(c->mat.cubic), v(c->tc.n_work), v(c->tc.split), v(c->tc.tf32);
     mix(c->tc.wofs, sizeof(c->tc.wofs));

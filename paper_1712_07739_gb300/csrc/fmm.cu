@@ -672,6 +672,7 @@ int fmm_kernel_attrs(gbfmm_ctx *ctx) {
 
 int near_prepare(gbfmm_ctx *ctx);  // near.cu
 int near_alloc(gbfmm_ctx *ctx, int64_t n_targets);  // near.cu
+int near_sym_alloc(gbfmm_ctx *ctx);                 // near.cu
 int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t *tsid, double *sig);
 
 int mixed_alloc(gbfmm_ctx *ctx) {
@@ -698,6 +699,7 @@ int mixed_alloc(gbfmm_ctx *ctx) {
         ctx->mx_cap_cells = nc;
     }
     if (int rc = near_alloc(ctx, N)) return rc;
+    if (int rc = near_sym_alloc(ctx)) return rc;
     if (!ctx->tc.ready_ops) {
         int rc = m2l_tc_setup(ctx);
         if (rc) return rc;

@@ -56,6 +56,12 @@ struct NearWork {
     int2 *items = nullptr, *sorted = nullptr;
     int *keys = nullptr, *cnt = nullptr, *key_of = nullptr, *off = nullptr, *misc = nullptr;
     int64_t cap = 0, cap_leaves = 0;
+    // symmetric near field (nodal forces, unit-circle h): leaf-pair items and
+    // per-direction partial stresses [28][N][6]
+    int2 *pitems = nullptr, *psorted = nullptr;
+    int *pkeys = nullptr, *pmisc = nullptr;
+    double *part = nullptr;
+    int64_t pcap = 0, part_cap = 0;
 };
 
 struct Timer {

@@ -312,6 +312,308 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
     }
 }
 
+// ---------------------------------------------------------------- symmetric near field
+// Nodal forces (targets = sources): h is odd, h(-T) = -h(T), so one
+// evaluation of h for the point pair (i, j) serves both directions,
+//     s_i += P_j h(T_ij) / R^2   and   s_j -= P_i h(T_ij) / R^2.
+// Work items are leaf pairs (A, B) with B = A + o over the 14 offsets o of
+// the upper half of the 3 x 3 x 3 neighbourhood (o = 0 included: pairs j > i
+// of one leaf).  Contributions are written to partial slots, one per point
+// and neighbour direction (27 directions + the reverse half of the own
+// leaf), each written by exactly one warp in a fixed order; the combine kernel
+// adds the far field (L2P) and the slots in a fixed order.  Close pairs
+// (closer than near_fp64 x the longer of the two segments) take FP64
+// separations and FP64 sums, as in the one-sided kernel.
+constexpr int SYM_WARPS = 4, SYM_SCH = 8;
+constexpr int kSlots = 28;
+
+template <int HM>
+__global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
+    int L, float near2, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat,
+    const int *__restrict__ sstart, const float4 *__restrict__ yrel, const double *__restrict__ ys,
+    const float *__restrict__ c32, const int64_t *__restrict__ ssid, double *__restrict__ part, int64_t N,
+    const int2 *__restrict__ items, const int *__restrict__ n_items) {
+    extern __shared__ __align__(16) float sm_sym[];
+    float *wPA = sm_sym + (threadIdx.x / 32) * (32 * 108 + SYM_SCH * 108);  // [108][32]: lanes' own tensors
+    float *wPB = wPA + 32 * 108;                                            // [SCH][108] staged sources
+    __shared__ float4 syB[SYM_WARPS][SYM_SCH];
+    __shared__ int sdB[SYM_WARPS][SYM_SCH];
+    __shared__ float saccB[SYM_WARPS][SYM_SCH][6];
+    __shared__ double sacc64B[SYM_WARPS][SYM_SCH][6];
+    __shared__ float sC[81];
+    __shared__ float2 sTab[128];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (HM == HM_GENERIC)
+        for (int i = threadIdx.x; i < 81; i += blockDim.x) sC[i] = float(mat->C[i]);
+    if (HM == HM_CUBIC)
+        for (int i = threadIdx.x; i < mat->Q && i < 128; i += blockDim.x) {
+            float sn, cs;
+            sincospif(float(i) / float(mat->Q), &sn, &cs);
+            sTab[i] = make_float2(cs, sn);
+        }
+    __syncthreads();
+    const int64_t item = blockIdx.x * int64_t(SYM_WARPS) + warp;
+    if (item >= *n_items) return;
+    const int2 wi = items[item];
+    const int64_t Aleaf = wi.x;
+    const int d = wi.y;  // 0..13: neighbour index 13 + d
+    const int nlv = 1 << (L - 1);
+    int ax, ay, az;
+    cell_xyz3(Aleaf, nlv, ax, ay, az);
+    const int nb = 13 + d;
+    const int ox = nb % 3 - 1, oy = (nb / 3) % 3 - 1, oz = nb / 9 - 1;
+    const int64_t Bleaf = (int64_t(az + oz) * nlv + (ay + oy)) * nlv + (ax + ox);
+    const bool self = d == 0;
+    const int sA0 = sstart[Aleaf], sA1 = sstart[Aleaf + 1];
+    const int sB0 = sstart[Bleaf], sB1 = sstart[Bleaf + 1];
+    const int slot_f = nb, slot_r = self ? 27 : 26 - nb;
+    const double h = box->H / nlv;
+    // B's leaf-relative positions, seen from A's leaf centre
+    const float bsh[3] = {float(ox * h), float(oy * h), float(oz * h)};
+    const int Q = mat->Q;
+    const float c12f = float(mat->c12), c44f = float(mat->c44), cdf = float(mat->cd);
+    const int nA = sA1 - sA0;
+    const int tg = nA >= 32 ? 32 : (nA > 16 ? 32 : (nA > 8 ? 16 : (nA > 4 ? 8 : (nA > 2 ? 4 : (nA > 1 ? 2 : 1)))));
+    const int ls = 32 / tg, ti = lane % tg, tj = lane / tg;
+    bool first_chunk = true;
+    for (int r0 = sA0; r0 < sA1; r0 += tg) {
+        const int i = r0 + ti;
+        const bool vi = i < sA1;
+        // stage the lanes' own source tensors, transposed (column ti): lanes read
+        // consecutive words
+        __syncwarp();
+        if (vi && tj == 0) {
+            const float4 *src = reinterpret_cast<const float4 *>(c32 + int64_t(108) * i);
+            for (int c4 = 0; c4 < 27; ++c4) {
+                const float4 v = __ldg(src + c4);
+                wPA[(4 * c4) * 32 + ti] = v.x;
+                wPA[(4 * c4 + 1) * 32 + ti] = v.y;
+                wPA[(4 * c4 + 2) * 32 + ti] = v.z;
+                wPA[(4 * c4 + 3) * 32 + ti] = v.w;
+            }
+        }
+        __syncwarp();
+        float4 yi = make_float4(0.f, 0.f, 0.f, 0.f);
+        double xi[3] = {0.0, 0.0, 0.0};
+        int segi = -2;
+        if (vi) {
+            yi = yrel[i];
+            xi[0] = ys[3 * int64_t(i)], xi[1] = ys[3 * int64_t(i) + 1], xi[2] = ys[3 * int64_t(i) + 2];
+            segi = int(ssid[i]);
+        }
+        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        double acc64[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        const float *Pi = wPA + ti;  // element c at Pi[32 c]
+        const int jb0 = self ? r0 : sB0;  // own leaf: pairs j > i only
+        for (int j0 = jb0; j0 < sB1; j0 += SYM_SCH) {
+            const int nj = min(SYM_SCH, sB1 - j0);
+            __syncwarp();
+            if (lane < nj) {
+                syB[warp][lane] = yrel[j0 + lane];
+                sdB[warp][lane] = int(ssid[j0 + lane]);
+            }
+            for (int k = lane; k < SYM_SCH * 6; k += 32) {
+                (&saccB[warp][0][0])[k] = 0.f;
+                (&sacc64B[warp][0][0])[k] = 0.0;
+            }
+            {
+                const float4 *src = reinterpret_cast<const float4 *>(c32 + int64_t(108) * j0);
+                float4 *dst = reinterpret_cast<float4 *>(wPB);
+                for (int k = lane; k < nj * 27; k += 32) dst[k] = __ldg(src + k);
+            }
+            __syncwarp();
+            for (int jj = 0; jj < nj; jj += ls) {
+                const int jl = jj + tj;  // this lane's source within the chunk
+                const int j = j0 + jl;
+                bool on = vi && jl < nj && (!self || j > i);
+                float4 yj = make_float4(0.f, 0.f, 0.f, 1.f);
+                if (on) {
+                    yj = syB[warp][jl];
+                    on = sdB[warp][jl] != segi;
+                }
+                float d3[3] = {yi.x - (yj.x + bsh[0]), yi.y - (yj.y + bsh[1]), yi.z - (yj.z + bsh[2])};
+                const float r2 = d3[0] * d3[0] + d3[1] * d3[1] + d3[2] * d3[2];
+                const float lmax = fmaxf(yi.w, yj.w);
+                const bool close = on && r2 < near2 * lmax * lmax;
+                float ir = 1.f;
+                if (close) {
+                    const double e0 = xi[0] - ys[3 * int64_t(j)], e1 = xi[1] - ys[3 * int64_t(j) + 1],
+                                 e2 = xi[2] - ys[3 * int64_t(j) + 2];
+                    const double rr = e0 * e0 + e1 * e1 + e2 * e2;
+                    if (rr == 0.0) on = false;
+                    d3[0] = float(e0), d3[1] = float(e1), d3[2] = float(e2);
+                    ir = rr > 0.0 ? float(rsqrt(rr)) : 1.f;
+                } else if (on) {
+                    ir = rsqrtf(r2);
+                }
+                float fw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, rv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (on) {
+                    float T[3] = {d3[0] * ir, d3[1] * ir, d3[2] * ir};
+                    float hs[18];
+                    if (HM == HM_CUBIC)
+                        h_cubic_f32(c12f + c44f, c44f, cdf, Q, sTab, T, hs);
+                    else
+                        h_circle_sym<float, float>(sC, Q, T, hs);
+                    const float ir2 = ir * ir;
+                    const float *Pj = wPB + 108 * jl;
+#pragma unroll
+                    for (int ab = 0; ab < 6; ++ab) {
+                        float sf = 0.f, sr = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 18; ++k) {
+                            sf = fmaf(Pj[ab * 18 + k], hs[k], sf);
+                            sr = fmaf(Pi[32 * (ab * 18 + k)], hs[k], sr);
+                        }
+                        fw[ab] = sf * ir2;
+                        rv[ab] = -sr * ir2;
+                    }
+                    if (close) {
+#pragma unroll
+                        for (int ab = 0; ab < 6; ++ab) acc64[ab] += double(fw[ab]);
+                    } else {
+#pragma unroll
+                        for (int ab = 0; ab < 6; ++ab) acc[ab] += fw[ab];
+                    }
+                }
+                // reverse: sum over the tg lanes that share source jl (fixed order)
+                const bool anyclose = __any_sync(0xffffffffu, close);
+                double rv64[6];
+#pragma unroll
+                for (int ab = 0; ab < 6; ++ab) {
+                    rv64[ab] = close ? double(rv[ab]) : 0.0;
+                    if (close) rv[ab] = 0.f;
+                }
+                for (int off = 1; off < tg; off <<= 1)
+#pragma unroll
+                    for (int ab = 0; ab < 6; ++ab) rv[ab] += __shfl_xor_sync(0xffffffffu, rv[ab], off);
+                if (anyclose)
+                    for (int off = 1; off < tg; off <<= 1)
+#pragma unroll
+                        for (int ab = 0; ab < 6; ++ab) rv64[ab] += __shfl_xor_sync(0xffffffffu, rv64[ab], off);
+                if (ti == 0 && jl < nj) {
+#pragma unroll
+                    for (int ab = 0; ab < 6; ++ab) {
+                        saccB[warp][jl][ab] += rv[ab];
+                        if (anyclose) sacc64B[warp][jl][ab] += rv64[ab];
+                    }
+                }
+            }
+            __syncwarp();
+            // reverse partials of this chunk's sources: this warp is their only writer; the
+            // first target chunk stores, later ones add (in the own leaf the first chunk
+            // visits every source, later chunks only j >= r0)
+            for (int k = lane; k < nj * 6; k += 32) {
+                const int jl = k / 6, ab = k % 6;
+                double *dst = part + (int64_t(slot_r) * N + (j0 + jl)) * 6 + ab;
+                const double v = double(saccB[warp][jl][ab]) + sacc64B[warp][jl][ab];
+                *dst = first_chunk ? v : *dst + v;
+            }
+        }
+        first_chunk = false;
+        // forward: sum over the lanes that share target i (fixed order)
+        for (int off = tg; off < 32; off <<= 1)
+#pragma unroll
+            for (int ab = 0; ab < 6; ++ab) {
+                acc[ab] += __shfl_xor_sync(0xffffffffu, acc[ab], off);
+                acc64[ab] += __shfl_xor_sync(0xffffffffu, acc64[ab], off);
+            }
+        if (vi && tj == 0)
+#pragma unroll
+            for (int ab = 0; ab < 6; ++ab) part[(int64_t(slot_f) * N + i) * 6 + ab] = double(acc[ab]) + acc64[ab];
+    }
+}
+
+// far field (L2P) plus the partial slots, in a fixed order
+__global__ void k_near_combine(int p, int L, int64_t N, const TreeBox *__restrict__ box,
+                               const int *__restrict__ sstart, const int *__restrict__ pleaf,
+                               const double *__restrict__ xt, const float *__restrict__ S,
+                               const double *__restrict__ part, double *__restrict__ sig) {
+    const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (t >= N) return;
+    const int nlv = 1 << (L - 1);
+    const int64_t leaf = pleaf[t];
+    int cx, cy, cz;
+    cell_xyz3(leaf, nlv, cx, cy, cz);
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (L >= 3) {
+        const int P3 = p * p * p;
+        const double h = box->H / nlv, ih = double(nlv) / box->H;
+        float bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
+        lagrange_1d<float>(p, float((xt[3 * t] - (box->origin[0] + cx * h)) * ih), bx);
+        lagrange_1d<float>(p, float((xt[3 * t + 1] - (box->origin[1] + cy * h)) * ih), by);
+        lagrange_1d<float>(p, float((xt[3 * t + 2] - (box->origin[2] + cz * h)) * ih), bz);
+        const float *Sl = S + (cell_base_d(L - 1) + leaf) * int64_t(P3) * 6;
+        for (int lz = 0; lz < p; ++lz)
+            for (int ly = 0; ly < p; ++ly) {
+                const float wyz = by[ly] * bz[lz];
+                for (int lx = 0; lx < p; ++lx) {
+                    const float w = bx[lx] * wyz;
+                    const float *s6 = Sl + ((lz * p + ly) * p + lx) * 6;
+                    for (int ab = 0; ab < 6; ++ab) acc[ab] += w * __ldg(s6 + ab);
+                }
+            }
+    }
+    double out[6];
+    for (int ab = 0; ab < 6; ++ab) out[ab] = double(acc[ab]);
+    for (int s = 0; s < kSlots; ++s) {
+        const int nb = s == 27 ? 13 : s;
+        const int bx = cx + nb % 3 - 1, by = cy + (nb / 3) % 3 - 1, bz = cz + nb / 9 - 1;
+        if (bx < 0 || by < 0 || bz < 0 || bx >= nlv || by >= nlv || bz >= nlv) continue;
+        const int64_t B = (int64_t(bz) * nlv + by) * nlv + bx;
+        if (sstart[B + 1] == sstart[B]) continue;
+        const double *ps = part + (int64_t(s) * N + t) * 6;
+        for (int ab = 0; ab < 6; ++ab) out[ab] += ps[ab];
+    }
+    for (int ab = 0; ab < 6; ++ab) sig[6 * t + ab] = out[ab];
+}
+
+// leaf-pair work items (A, d), heaviest first (log2 of |A| |B| buckets)
+__global__ void k_pairs_count(int64_t nl, int L, const int *__restrict__ sstart, int *__restrict__ cnt) {
+    const int64_t l = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (l >= nl) return;
+    const int nA = sstart[l + 1] - sstart[l];
+    int c = 0;
+    if (nA > 0) {
+        const int nlv = 1 << (L - 1);
+        int x, y, z;
+        cell_xyz3(l, nlv, x, y, z);
+        for (int d = 0; d < 14; ++d) {
+            const int nb = 13 + d;
+            const int bx = x + nb % 3 - 1, by = y + (nb / 3) % 3 - 1, bz = z + nb / 9 - 1;
+            if (bx < 0 || by < 0 || bz < 0 || bx >= nlv || by >= nlv || bz >= nlv) continue;
+            const int64_t B = (int64_t(bz) * nlv + by) * nlv + bx;
+            if (sstart[B + 1] > sstart[B]) ++c;
+        }
+    }
+    cnt[l] = c;
+}
+
+__global__ void k_pairs_fill(int64_t nl, int L, const int *__restrict__ sstart, const int *__restrict__ off,
+                             int2 *__restrict__ items, int *__restrict__ keys, int *__restrict__ hist) {
+    const int64_t l = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (l >= nl) return;
+    const int nA = sstart[l + 1] - sstart[l];
+    if (nA == 0) return;
+    const int nlv = 1 << (L - 1);
+    int x, y, z;
+    cell_xyz3(l, nlv, x, y, z);
+    int o = off[l];
+    for (int d = 0; d < 14; ++d) {
+        const int nb = 13 + d;
+        const int bx = x + nb % 3 - 1, by = y + (nb / 3) % 3 - 1, bz = z + nb / 9 - 1;
+        if (bx < 0 || by < 0 || bz < 0 || bx >= nlv || by >= nlv || bz >= nlv) continue;
+        const int64_t B = (int64_t(bz) * nlv + by) * nlv + bx;
+        const int nB = sstart[B + 1] - sstart[B];
+        if (nB == 0) continue;
+        const int64_t cost = d == 0 ? int64_t(nA) * nA / 2 + 1 : int64_t(nA) * nB;
+        const int key = 63 - (63 - __clzll(cost));
+        items[o] = make_int2(int(l), d);
+        keys[o] = key;
+        atomicAdd(&hist[key], 1);
+        ++o;
+    }
+}
+
 // ---------------------------------------------------------------- near field with the learned h
 // Angular bin of a folded direction (upper half-space): dominant axis face
 // (+z, +x, -x, +y, -y) and a 16 x 16 grid of the two other components.
@@ -698,7 +1000,9 @@ int near_alloc(gbfmm_ctx *ctx, int64_t n_targets) {
         void *ps[] = {W.items, W.sorted, W.keys, W.cnt, W.key_of, W.off, W.misc};
         for (void *q : ps)
             if (q) cudaFree(q);
-        W = NearWork{};
+        W.items = W.sorted = nullptr;
+        W.keys = W.cnt = W.key_of = W.off = W.misc = nullptr;
+        W.cap = W.cap_leaves = 0;
         CK(cudaMalloc(&W.items, cap * sizeof(int2)));
         CK(cudaMalloc(&W.sorted, cap * sizeof(int2)));
         CK(cudaMalloc(&W.keys, cap * sizeof(int)));
@@ -735,7 +1039,70 @@ static int build_items(gbfmm_ctx *ctx, const int *tstart, int64_t n_targets, int
     return GBFMM_OK;
 }
 
+// the symmetric kernel applies to nodal forces with the unit-circle h
+static bool near_symmetric(const gbfmm_ctx *ctx) { return ctx->mat.mode == GBFMM_H_CIRCLE; }
+
+int near_sym_alloc(gbfmm_ctx *ctx) {
+    if (!near_symmetric(ctx)) return GBFMM_OK;
+    NearWork &W = ctx->nw;
+    const int64_t pcap = 14 * ctx->n_leaves;
+    if (pcap > W.pcap) {
+        void *ps[] = {W.pitems, W.psorted, W.pkeys, W.pmisc};
+        for (void *q : ps)
+            if (q) cudaFree(q);
+        W.pitems = W.psorted = nullptr;
+        W.pkeys = W.pmisc = nullptr;
+        CK(cudaMalloc(&W.pitems, pcap * sizeof(int2)));
+        CK(cudaMalloc(&W.psorted, pcap * sizeof(int2)));
+        CK(cudaMalloc(&W.pkeys, pcap * sizeof(int)));
+        CK(cudaMalloc(&W.pmisc, 192 * sizeof(int)));
+        W.pcap = pcap;
+    }
+    if (ctx->N > W.part_cap) {
+        if (W.part) cudaFree(W.part);
+        W.part = nullptr;
+        CK(cudaMalloc(&W.part, size_t(kSlots) * ctx->N * 6 * sizeof(double)));
+        W.part_cap = ctx->N;
+    }
+    return GBFMM_OK;
+}
+
+static int near_run_sym(gbfmm_ctx *ctx, double *sig) {
+    const int64_t nl = ctx->n_leaves, N = ctx->N;
+    if (int rc = near_alloc(ctx, N)) return rc;
+    if (int rc = near_sym_alloc(ctx)) return rc;
+    NearWork &W = ctx->nw;
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemsetAsync(W.pmisc, 0, 192 * sizeof(int), st));
+    ctx->launches += 6;
+    k_pairs_count<<<nblk(nl, 256), 256, 0, st>>>(nl, ctx->L, ctx->d_leaf_start, W.cnt);
+    k_scan_small<<<1, 1024, 0, st>>>(nl, W.cnt, W.off);
+    k_pairs_fill<<<nblk(nl, 256), 256, 0, st>>>(nl, ctx->L, ctx->d_leaf_start, W.off, W.pitems, W.pkeys, W.pmisc);
+    k_items_order<<<nblk(W.pcap, 256) < 1024 ? nblk(W.pcap, 256) : 1024, 256, 0, st>>>(
+        int(W.pcap), W.off + nl, W.pitems, W.pkeys, W.pmisc, W.pmisc + 64, W.psorted, W.pmisc + 128);
+    const float near2 = float(ctx->opt.near_fp64 * ctx->opt.near_fp64);
+    const size_t smem = size_t(SYM_WARPS) * (32 + SYM_SCH) * 108 * sizeof(float);
+    const unsigned grid = nblk(W.pcap, SYM_WARPS);
+    if (ctx->mat.cubic) {
+        CK(cudaFuncSetAttribute(k_near_sym<HM_CUBIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_near_sym<HM_CUBIC><<<grid, SYM_WARPS * 32, smem, st>>>(ctx->L, near2, ctx->d_box, ctx->d_mat,
+                                                                 ctx->d_leaf_start, ctx->d_yrel, ctx->d_y, ctx->d_Pf,
+                                                                 ctx->d_sid, W.part, N, W.psorted, W.pmisc + 128);
+    } else {
+        CK(cudaFuncSetAttribute(k_near_sym<HM_GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_near_sym<HM_GENERIC><<<grid, SYM_WARPS * 32, smem, st>>>(ctx->L, near2, ctx->d_box, ctx->d_mat,
+                                                                   ctx->d_leaf_start, ctx->d_yrel, ctx->d_y,
+                                                                   ctx->d_Pf, ctx->d_sid, W.part, N, W.psorted,
+                                                                   W.pmisc + 128);
+    }
+    k_near_combine<<<nblk(N, 256), 256, 0, st>>>(ctx->opt.p, ctx->L, N, ctx->d_box, ctx->d_leaf_start, ctx->d_pleaf,
+                                                 ctx->d_y, ctx->d_Sf, W.part, sig);
+    CK(cudaGetLastError());
+    return GBFMM_OK;
+}
+
 int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t *tsid, double *sig) {
+    if (tsid && near_symmetric(ctx)) return near_run_sym(ctx, sig);
     const int64_t nl = ctx->n_leaves;
     const float near2 = float(ctx->opt.near_fp64 * ctx->opt.near_fp64);
     int *n_items = nullptr;

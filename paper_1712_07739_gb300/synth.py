@@ -218,3 +218,30 @@ def isotropic_voigt(mu=1.0, nu=0.3):
     """6x6 Voigt stiffness of an isotropic medium (Lame lambda, mu)."""
     lam = 2.0 * mu * nu / (1.0 - 2.0 * nu)
     return cubic_voigt(lam + 2.0 * mu, lam, mu)
+
+
+def rotation(axis=(1.0, 2.0, 3.0), angle=0.7):
+    """Proper rotation matrix about a unit axis (Rodrigues)."""
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    K = np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+    return np.eye(3) + np.sin(angle) * K + (1.0 - np.cos(angle)) * (K @ K)
+
+
+def rotated_voigt(C6, R):
+    """Voigt stiffness of the medium C6 turned by the rotation R
+    (C'_ijkl = R_ia R_jb R_kc R_ld C_abcd): a crystal whose axes are not
+    along x, y, z."""
+    pairs = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    C = np.zeros((3, 3, 3, 3))
+    for I, (i, j) in enumerate(pairs):
+        for J, (k, l) in enumerate(pairs):
+            for a, b in ((i, j), (j, i)):
+                for c, d in ((k, l), (l, k)):
+                    C[a, b, c, d] = C6[I][J]
+    Cr = np.einsum("ia,jb,kc,ld,abcd->ijkl", R, R, R, R, C)
+    out = np.zeros((6, 6))
+    for I, (i, j) in enumerate(pairs):
+        for J, (k, l) in enumerate(pairs):
+            out[I, J] = Cr[i, j, k, l]
+    return out

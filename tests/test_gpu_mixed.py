@@ -1,5 +1,6 @@
-"""Mixed-precision pass (FP32 stages, BF16 tensor-core M2L with split
-correction, FP32 near field with FP64 close pairs) vs the FP64 oracle.
+"""Mixed-precision pass (FP32 stages, tensor-core M2L in FP16 with per-level
+scaling or BF16 with split correction, FP32 near field with FP64 close
+pairs) vs the FP64 oracle.
 
 Tolerance: relative L2 nodal-force error <= 1e-4 against the oracle's
 Algorithm 2 at the same order and tree (the mixed-precision bar of the
@@ -68,6 +69,19 @@ def test_mixed_equals_fp64_gpu_pass_closely(split):
     _, Fd = _run(nodes, segs, b, ISO_C, p=6, levels=5, precision="fp64")
     err = oracle.rel_l2(Fm, Fd)
     print(f"mixed split={split} vs fp64 GPU:", err)
+    assert err <= TOL_MIXED
+
+
+def test_mixed_rotated_crystal_general_rule():
+    """A cubic crystal turned off the x, y, z axes: the near field takes the
+    general unit-circle rule (all 81 stiffness entries), evaluated once per
+    point pair for both directions."""
+    nodes, segs, b = synth.polygon_loops(n_segs=600, n_loops=16, seed=27)
+    C6 = synth.rotated_voigt(synth.cubic_voigt(), synth.rotation())
+    _, F = _run(nodes, segs, b, C6, p=4, levels=4, precision="mixed", h_mode="circle", circle_q=48)
+    Fo = _oracle_forces(oracle.Material.aniso(C6, Q=48), nodes, segs, b, 4, 4)
+    err = oracle.rel_l2(F, Fo)
+    print("mixed rotated crystal vs Algorithm 2:", err)
     assert err <= TOL_MIXED
 
 

@@ -130,3 +130,43 @@ def test_network_in_near_field_vs_plain():
     f.mlp_calibrate(1e-12)
     Fa = f.nodal_forces().cpu().numpy()
     assert np.linalg.norm(Fa - Fp) / np.linalg.norm(Fp) < 1e-6
+
+
+def _near_ms(f, dn, ds, db, reps=3):
+    f.build(dn, ds, db)
+    f.set_timing(True)
+    f.nodal_forces()  # warm-up
+    t = []
+    for _ in range(reps):
+        F = f.nodal_forces()
+        t.append(f.stage_times()[4])
+    f.set_timing(False)
+    return min(t), F.cpu().numpy()
+
+
+def test_network_gain_rotated_crystal():
+    """What the trained network gains: in a cubic crystal whose axes are not
+    along x, y, z the plain evaluator is the general unit-circle rule (zz and
+    zT from all 81 stiffness entries at Q = 32 points per pair); the network
+    costs the same whatever the medium.  Same network, same pass: near-field
+    time with the network (pairs beyond mlp_min_dist segment lengths, bins the
+    plain evaluator accepted) against the plain evaluator everywhere, and the
+    force difference it costs."""
+    import paper_1712_07739_gb300 as gb
+
+    C = synth.rotated_voigt(CUB, synth.rotation())
+    nodes, segs, b = synth.slab_loops(n_loops=2000, segs_per_loop=50, n_slabs=8, seed=35)
+    dn, ds, db = (torch.tensor(a, device="cuda") for a in (nodes, segs, b))
+    kw = dict(p=5, levels=5, precision="mixed", circle_q=32)
+    plain = gb.FMM(h_mode="circle", **kw).set_material(C)
+    t_plain, Fp = _near_ms(plain, dn, ds, db)
+    f = gb.FMM(h_mode="mlp", mlp_min_dist=4.0, **kw).set_material(C)
+    f.mlp_train(torch.tensor(synth.directions(1_000_000, seed=36), device="cuda"), epochs=15, batch=8192, lr=3e-3,
+                seed=3)
+    frac = f.mlp_calibrate(5e-2)
+    t_mlp, Fm = _near_ms(f, dn, ds, db)
+    err = np.linalg.norm(Fm - Fp) / np.linalg.norm(Fp)
+    print(f"rotated cubic crystal, 100k segments: near field plain {t_plain:.1f} ms, network {t_mlp:.1f} ms "
+          f"(gain {t_plain / t_mlp:.2f}x), bins on the plain rule {frac:.3f}, force difference {err:.2e}")
+    assert np.isfinite(Fm).all()
+    assert err < 2e-2
