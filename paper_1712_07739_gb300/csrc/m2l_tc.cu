@@ -9,17 +9,16 @@
 // offsets of class c are therefore, each, a constant shift between two
 // sub-grids.
 //
-// Tiles.  The sub-grid of a class is cut into micro-bricks of 2 x 2 x 2
-// cells; the micro-bricks holding at least one target cell are listed per
-// (level, class) in Morton order, and 16 consecutive ones (128 cells) form a
-// tile.  The M2L of a tile is
+// Tiles.  The sub-grid of a class is cut into bricks of 8 x 4 x 4 cells (128
+// rows); the bricks holding at least one target cell are listed per (level,
+// class) and each is one tile.  The M2L of a tile is
 //     S[cell, n] = (2^l / H)^2  sum_o  sum_k  W_c'[cell + s_o, k] T_o[n, k]
 // with k = (node m, component wr) and n = (node l, stress component ab):
 // one GEMM of M = 128 cells, N = 6 p^3 and K = (active offsets) x 9 p^3,
-// accumulated in tensor memory.  The A tile is 16 TMA box loads of 2 x 2 x 2
-// shifted multipole rows (1 KB each, zero-filled where a box leaves the
-// sub-grid), the B tile rows of the operator T_o (TMA box loads).  Offsets
-// whose 128 source cells are all empty are skipped.
+// accumulated in tensor memory.  The A tile is one TMA box of shifted
+// multipole rows (zero-filled where the box leaves the sub-grid), the B tile
+// rows of the operator T_o.  Offsets whose 128 source cells are all empty
+// are skipped (checked per cell when the tile starts).
 //
 // Precision: BF16 operands (hi); for the offsets nearest to the target
 // (max |o_i| = 2, the largest far-field terms) the residuals W_lo = W - hi(W)
@@ -27,8 +26,8 @@
 // modes: TF32 operands; FP16 operands with a power-of-two scale per level for
 // W and one for the operators (FP16 carries 3 more mantissa bits than BF16).
 //
-// Warp roles (192 threads): warp 0 issues TMA loads (lane j loads
-// micro-brick j, lanes 16-18 the operator rows), warp 1 owns TMEM and issues
+// Warp roles (192 threads): warp 0 issues TMA loads (lane j loads brick j
+// of the tile, lanes 16-18 the operator rows), warp 1 owns TMEM and issues
 // the MMAs, warps 2-5 read the accumulator out (warp w reads TMEM lanes
 // 32 (w % 4) .. 32 (w % 4) + 31).  Every mbarrier wait is bounded; on
 // time-out a device status word gets GBFMM_ERR_TIMEOUT and the block winds
@@ -200,30 +199,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Micro-brick slots: level l (2 <= l < L) has 8 classes x mb^3 micro-bricks,
-// mb = 2^(l-2); slots of a level follow those of the levels below it, and
-// within (level, class) the micro-bricks are in Morton order.
-__host__ __device__ inline int64_t mb_slot_base(int l) { return 8 * (((int64_t(1) << (3 * (l - 2))) - 1) / 7); }
+// Bricks: BX x BY x BZ cells of one class sub-grid, RB = 128 / NBT cells;
+// NBT bricks of one (level, class) make a 128-row tile.  Slots: level l
+// (2 <= l < L) has 8 classes x nbx x nby x nbz bricks (x fastest) starting at
+// base[l]; the bricks that hold targets are listed in slot order.
+constexpr int BX = 8, BY = 4, BZ = 4, RB = BX * BY * BZ, NBT = 128 / RB;
+static_assert(NBT * RB == 128, "a tile holds 128 cells");
 
-__device__ __forceinline__ uint32_t morton_part(uint32_t v) {  // 10 bits -> every third bit
-    v &= 0x3ffu;
-    v = (v | (v << 16)) & 0x030000ffu;
-    v = (v | (v << 8)) & 0x0300f00fu;
-    v = (v | (v << 4)) & 0x030c30c3u;
-    v = (v | (v << 2)) & 0x09249249u;
-    return v;
-}
-__device__ __forceinline__ uint32_t morton_compact(uint32_t v) {
-    v &= 0x09249249u;
-    v = (v | (v >> 2)) & 0x030c30c3u;
-    v = (v | (v >> 4)) & 0x0300f00fu;
-    v = (v | (v >> 8)) & 0x030000ffu;
-    v = (v | (v >> 16)) & 0x3ffu;
-    return v;
-}
+using BrickGrid = TcPlanGrid;
 
 // Segments: one per (level, class), index (l - 2) * 8 + c.  seg[s] = {first
-// list entry, micro-bricks, first tile}; seg[n_seg].z = total tiles.
+// list entry, bricks, first tile}; seg[n_seg].z = total tiles.
 constexpr int kMaxSeg = 8 * GB_TC_MAXLEV;
 
 // number of K-block iterations of one work item (same count on every warp)
@@ -231,7 +217,7 @@ __device__ __forceinline__ int passes_of(const OffsetEntry &e, int split) { retu
 
 template <bool TF32>
 __global__ void __launch_bounds__(192, 1)
-    k_m2l_tc(const __grid_constant__ M2LParams P, const int4 *__restrict__ seg, int n_seg,
+    k_m2l_tc(const __grid_constant__ M2LParams P, const BrickGrid G, const int4 *__restrict__ seg, int n_seg,
              const int *__restrict__ mb_list, const int *__restrict__ occ, const int *__restrict__ tocc,
              const TreeBox *__restrict__ box, float *__restrict__ S, int *__restrict__ status, int stages, int groups) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -243,7 +229,7 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 1);
 
     __shared__ int s_level, s_cls, s_nmb, s_stop;
-    __shared__ int s_mb[16][3];        // micro-brick origins (sub-grid cells) of this tile
+    __shared__ int s_mb[NBT][3];       // brick origins (sub-grid cells) of this tile
     __shared__ uint32_t s_active[6];   // offsets with at least one occupied source cell
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int tile = blockIdx.x / groups, group = blockIdx.x % groups;
@@ -253,17 +239,18 @@ __global__ void __launch_bounds__(192, 1)
         if (tile < seg[n_seg].z)
             for (int si = 0; si < n_seg; ++si) {
                 const int4 sg = seg[si];
-                const int nt = (sg.y + 15) / 16;
+                const int nt = (sg.y + NBT - 1) / NBT;
                 if (tile >= sg.z && tile < sg.z + nt) {
                     const int t = tile - sg.z;
-                    s_level = si / 8 + 2;
+                    const int l = si / 8 + 2;
+                    s_level = l;
                     s_cls = si % 8;
-                    s_nmb = min(16, sg.y - 16 * t);
+                    s_nmb = min(NBT, sg.y - NBT * t);
                     for (int j = 0; j < s_nmb; ++j) {
-                        const uint32_t code = uint32_t(mb_list[sg.x + 16 * t + j]);
-                        s_mb[j][0] = 2 * int(morton_compact(code));
-                        s_mb[j][1] = 2 * int(morton_compact(code >> 1));
-                        s_mb[j][2] = 2 * int(morton_compact(code >> 2));
+                        const int bi = mb_list[sg.x + NBT * t + j];
+                        s_mb[j][0] = BX * (bi % G.nbx[l]);
+                        s_mb[j][1] = BY * ((bi / G.nbx[l]) % G.nby[l]);
+                        s_mb[j][2] = BZ * (bi / (G.nbx[l] * G.nby[l]));
                     }
                     break;
                 }
@@ -276,22 +263,21 @@ __global__ void __launch_bounds__(192, 1)
     const int m = 1 << (level - 1), n = 1 << level;
     const int64_t cbase = cell_base_d(level);
 
-    // active offsets: lane r of warp w checks rows 4r .. 4r + 3 (micro-brick r / 2)
+    // active offsets: lane r of warp w checks tile rows 4r .. 4r + 3
     for (int oi = warp; oi < 189; oi += 6) {
         const OffsetEntry e = c_offs[cls][oi];
         const int ccx = e.cls & 1, ccy = (e.cls >> 1) & 1, ccz = e.cls >> 2;
         bool hit = false;
-        const int j = lane / 2;
-        if (j < nmb)
-            for (int q = 0; q < 4; ++q) {
-                const int w8 = 4 * (lane & 1) + q;  // row within the micro-brick: x fastest, then y, z
-                const int px = s_mb[j][0] + (w8 & 1) + e.sx, py = s_mb[j][1] + ((w8 >> 1) & 1) + e.sy,
-                          pz = s_mb[j][2] + (w8 >> 2) + e.sz;
-                if (px >= 0 && py >= 0 && pz >= 0 && px < m && py < m && pz < m) {
-                    const int64_t g = cbase + (int64_t(2 * pz + ccz) * n + (2 * py + ccy)) * n + (2 * px + ccx);
-                    hit |= occ[g] > 0;
-                }
+        for (int q = 0; q < 4; ++q) {
+            const int row = 4 * lane + q, j = row / RB, w = row % RB;  // in a brick: x fastest, then y, z
+            if (j >= nmb) continue;
+            const int px = s_mb[j][0] + w % BX + e.sx, py = s_mb[j][1] + (w / BX) % BY + e.sy,
+                      pz = s_mb[j][2] + w / (BX * BY) + e.sz;
+            if (px >= 0 && py >= 0 && pz >= 0 && px < m && py < m && pz < m) {
+                const int64_t g = cbase + (int64_t(2 * pz + ccz) * n + (2 * py + ccy)) * n + (2 * px + ccx);
+                hit |= occ[g] > 0;
             }
+        }
         if (__any_sync(0xffffffffu, hit) && lane == 0) atomicOr(&s_active[oi / 32], 1u << (oi % 32));
     }
 
@@ -311,7 +297,7 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t tmem = *tmem_slot;
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[stages]), accb = smem_u32(&bars[2 * stages]);
     const uint32_t smem0 = smem_u32(smem);
-    const uint32_t stage_tx = uint32_t(nmb) * 1024u + uint32_t(stageB);
+    const uint32_t stage_tx = uint32_t(nmb) * uint32_t(RB * 128) + uint32_t(stageB);
 
     if (warp == 0) {
         // ---------------- TMA producer (the whole warp: one load per lane and stage)
@@ -341,8 +327,8 @@ __global__ void __launch_bounds__(192, 1)
                     if (P.drop_first && it == 0) continue;  // the MMA warp's wait on this stage runs out
                     const uint32_t a = smem0 + s * stage_bytes, fb = full0 + 8 * s;
                     if (lane < nmb)
-                        tma_load_5d(a + lane * 1024, ta, kb * P.kstep, s_mb[lane][0] + e.sx, s_mb[lane][1] + e.sy,
-                                    s_mb[lane][2] + e.sz, e.cls, fb);
+                        tma_load_5d(a + lane * (RB * 128), ta, kb * P.kstep, s_mb[lane][0] + e.sx,
+                                    s_mb[lane][1] + e.sy, s_mb[lane][2] + e.sz, e.cls, fb);
                     else if (lane >= 16 && lane < 19)
                         tma_load_3d(a + kStageA + (lane - 16) * P.nsub * 128, tb, kb * P.kstep,
                                     group * P.ncta + (lane - 16) * P.nsub, tidx, fb);
@@ -388,14 +374,17 @@ __global__ void __launch_bounds__(192, 1)
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int q = warp % 4;
         const int row = q * 32 + lane;
-        const int j = row / 8, w8 = row % 8;
+        const int j = row / RB, w = row % RB;
         bool valid = ok && j < nmb;
         int64_t g = 0;
         if (valid) {
-            const int px = s_mb[j][0] + (w8 & 1), py = s_mb[j][1] + ((w8 >> 1) & 1), pz = s_mb[j][2] + (w8 >> 2);
-            const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
-            g = cbase + (int64_t(2 * pz + cz) * n + (2 * py + cy)) * n + (2 * px + cx);
-            valid = tocc[g] > 0;
+            const int px = s_mb[j][0] + w % BX, py = s_mb[j][1] + (w / BX) % BY, pz = s_mb[j][2] + w / (BX * BY);
+            valid = px < m && py < m && pz < m;  // bricks of small levels stick out of the sub-grid
+            if (valid) {
+                const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
+                g = cbase + (int64_t(2 * pz + cz) * n + (2 * py + cy)) * n + (2 * px + cx);
+                valid = tocc[g] > 0;
+            }
         }
         float sc = float(double(n) / box->H) * float(double(n) / box->H);
         if (P.wmax) sc *= P.inv_op_scale / wscale_of(P.wmax[level]);
@@ -525,20 +514,20 @@ __global__ void k_lattice_absmax(int64_t n_pts, int64_t origin, const double *__
     if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
 }
 
-// Target micro-brick flags of one level: slot of (class, micro-brick) set
-// when one of its 8 cells holds targets
-__global__ void k_mb_flags(int level, const int *__restrict__ tocc, int *__restrict__ flags) {
+// Target brick flags of one level: slot of (class, brick) set when one of its
+// cells holds targets
+__global__ void k_mb_flags(int level, BrickGrid G, const int *__restrict__ tocc, int *__restrict__ flags) {
     const int n = 1 << level;
-    const int mb = n / 4;
     const int64_t cells = int64_t(n) * n * n;
+    const int nbx = G.nbx[level], nby = G.nby[level];
+    const int64_t nb3 = int64_t(nbx) * nby * G.nbz[level];
     for (int64_t lin = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; lin < cells;
          lin += int64_t(gridDim.x) * blockDim.x) {
         if (tocc[cell_base_d(level) + lin] == 0) continue;
         const int x = int(lin % n), y = int((lin / n) % n), z = int(lin / (int64_t(n) * n));
         const int cls = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
-        const uint32_t code = morton_part(uint32_t(x >> 2)) | (morton_part(uint32_t(y >> 2)) << 1) |
-                              (morton_part(uint32_t(z >> 2)) << 2);
-        flags[mb_slot_base(level) + int64_t(cls) * mb * mb * mb + code] = 1;
+        const int bx = (x >> 1) / BX, by = (y >> 1) / BY, bz = (z >> 1) / BZ;
+        flags[G.base[level] + cls * nb3 + (int64_t(bz) * nby + by) * nbx + bx] = 1;
     }
 }
 
@@ -576,29 +565,29 @@ __global__ void k_scan_flags(int n, const int *__restrict__ flags, int *__restri
     if (threadIdx.x == 0) pos[n] = carry;
 }
 
-// compact list of the flagged slots (their Morton code within the segment)
-__global__ void k_mb_list(int n, int L, const int *__restrict__ flags, const int *__restrict__ pos,
+// compact list of the flagged slots (brick index within its segment)
+__global__ void k_mb_list(int n, int L, BrickGrid G, const int *__restrict__ flags, const int *__restrict__ pos,
                           int *__restrict__ list) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         if (!flags[k]) continue;
         int l = 2;
-        while (l + 1 < L && k >= mb_slot_base(l + 1)) ++l;
-        const int64_t mb3 = int64_t(1) << (3 * (l - 2));
-        list[pos[k]] = int((k - mb_slot_base(l)) % mb3);
+        while (l + 1 < L && k >= G.base[l + 1]) ++l;
+        const int64_t nb3 = int64_t(G.nbx[l]) * G.nby[l] * G.nbz[l];
+        list[pos[k]] = int((k - G.base[l]) % nb3);
     }
 }
 
-// segment table: {first list entry, micro-bricks, first tile}; seg[n_seg].z = tiles
-__global__ void k_seg_table(int L, const int *__restrict__ pos, int4 *__restrict__ seg) {
+// segment table: {first list entry, bricks, first tile}; seg[n_seg].z = tiles
+__global__ void k_seg_table(int L, BrickGrid G, const int *__restrict__ pos, int4 *__restrict__ seg) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int tiles = 0, si = 0;
     for (int l = 2; l < L; ++l) {
-        const int64_t mb3 = int64_t(1) << (3 * (l - 2));
+        const int64_t nb3 = int64_t(G.nbx[l]) * G.nby[l] * G.nbz[l];
         for (int c = 0; c < 8; ++c, ++si) {
-            const int64_t s0 = mb_slot_base(l) + c * mb3;
-            const int first = pos[s0], cnt = pos[s0 + mb3] - first;
+            const int64_t s0 = G.base[l] + c * nb3;
+            const int first = pos[s0], cnt = pos[s0 + nb3] - first;
             seg[si] = make_int4(first, cnt, tiles, 0);
-            tiles += (cnt + 15) / 16;
+            tiles += (cnt + NBT - 1) / NBT;
         }
     }
     seg[si] = make_int4(0, 0, tiles, 0);
@@ -787,8 +776,21 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
         CK(cudaMalloc(&T.Wlo, tot * T.esz));
         T.w_cap = tot;
     }
-    // micro-brick slots, list and segment table (filled on the device per pass)
-    const int64_t slots = mb_slot_base(L);
+    // brick slots, list and segment table (filled on the device per pass)
+    BrickGrid &G = T.grid;
+    int64_t slots = 0, tiles = 0;  // tiles: upper bound, every brick holds targets
+    for (int l = 0; l <= GB_TC_MAXLEV; ++l) G.base[l] = 0;
+    for (int l = 2; l < L; ++l) {
+        const int m = 1 << (l - 1);
+        G.nbx[l] = (m + BX - 1) / BX;
+        G.nby[l] = (m + BY - 1) / BY;
+        G.nbz[l] = (m + BZ - 1) / BZ;
+        const int64_t nb3 = int64_t(G.nbx[l]) * G.nby[l] * G.nbz[l];
+        G.base[l] = slots;
+        slots += 8 * nb3;
+        tiles += 8 * ((nb3 + NBT - 1) / NBT);
+    }
+    G.base[L] = slots;
     if (slots > T.slot_cap) {
         void *ps[] = {T.d_flags, T.d_pos, T.d_list};
         for (void *q : ps)
@@ -802,8 +804,6 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
     if (!T.d_seg) CK(cudaMalloc(&T.d_seg, (kMaxSeg + 1) * sizeof(int4)));
     T.n_slots = slots;
     T.n_seg = 8 * (L - 2);
-    int64_t tiles = 0;  // upper bound: every micro-brick holds targets
-    for (int l = 2; l < L; ++l) tiles += 8 * ((int64_t(1) << (3 * (l - 2))) + 15) / 16;
     T.n_work = int(tiles * T.groups);
     return GBFMM_OK;
 }
@@ -837,7 +837,7 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
         const cuuint64_t dims[5] = {cuuint64_t(T.Kp), cuuint64_t(m), cuuint64_t(m), cuuint64_t(m), 8};
         const cuuint64_t row = cuuint64_t(T.Kp) * T.esz;
         const cuuint64_t strides[4] = {row, row * m, row * m * m, row * m * m * m};
-        const cuuint32_t boxd[5] = {cuuint32_t(128 / T.esz), 2, 2, 2, 1};  // one micro-brick
+        const cuuint32_t boxd[5] = {cuuint32_t(128 / T.esz), BX, BY, BZ, 1};  // one brick
         int rc = encode(ctx, &prm.tmW[l], whi, 5, dims, strides, boxd, T);
         if (rc) return rc;
         rc = encode(ctx, &prm.tmWlo[l], wlo, 5, dims, strides, boxd, T);
@@ -846,12 +846,13 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     CK(cudaMemsetAsync(T.d_flags, 0, T.n_slots * sizeof(int), ctx->stream));
     for (int l = 2; l < L; ++l) {
         ++ctx->launches;
-        k_mb_flags<<<nblk(int64_t(1) << (3 * l), 256), 256, 0, ctx->stream>>>(l, tocc, T.d_flags);
+        k_mb_flags<<<nblk(int64_t(1) << (3 * l), 256), 256, 0, ctx->stream>>>(l, T.grid, tocc, T.d_flags);
     }
     ctx->launches += 3;
     k_scan_flags<<<1, 1024, 0, ctx->stream>>>(int(T.n_slots), T.d_flags, T.d_pos);
-    k_mb_list<<<nblk(T.n_slots, 256), 256, 0, ctx->stream>>>(int(T.n_slots), L, T.d_flags, T.d_pos, T.d_list);
-    k_seg_table<<<1, 32, 0, ctx->stream>>>(L, T.d_pos, T.d_seg);
+    k_mb_list<<<nblk(T.n_slots, 256), 256, 0, ctx->stream>>>(int(T.n_slots), L, T.grid, T.d_flags, T.d_pos,
+                                                             T.d_list);
+    k_seg_table<<<1, 32, 0, ctx->stream>>>(L, T.grid, T.d_pos, T.d_seg);
     {
         const cuuint64_t dims[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(T.n_off)};
         const cuuint64_t strides[2] = {cuuint64_t(T.Kp) * T.esz, cuuint64_t(T.Kp) * T.esz * T.Np};
@@ -880,11 +881,11 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     ++ctx->launches;
     if (T.tf32) {
         CK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        k_m2l_tc<true><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
+        k_m2l_tc<true><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.grid, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
                                                              Sf, T.d_status, stages, T.groups);
     } else {
         CK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        k_m2l_tc<false><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
+        k_m2l_tc<false><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.grid, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
                                                               Sf, T.d_status, stages, T.groups);
     }
     CK(cudaGetLastError());

@@ -109,3 +109,29 @@ def test_full_size_repeatable_and_linear_in_b():
     f.build(dn, ds, torch.tensor(2.0 * b, device="cuda"))
     F4 = f.nodal_forces().cpu().numpy()
     assert np.linalg.norm(F4 - 4.0 * F1) <= 1e-6 * np.linalg.norm(F1)
+
+
+GOLDEN_Q = os.path.join(ROOT, "tests", "golden", "c3q_sampled_forces.json")
+
+
+@pytest.mark.parametrize("p", [6, 8])
+def test_quarter_size_error_budget(p):
+    """250,000-segment slab network, 32 nodes against the direct sum (stored
+    by tests/golden/make_c3q_sampled_forces.py): the FP64 pass measures the
+    interpolation error of order p, the mixed pass adds the precision error."""
+    wl = _bench_workload("c3q")
+    nodes, segs, b = wl["gen"](0)
+    with open(GOLDEN_Q) as fh:
+        gold = json.load(fh)
+    assert gold["n_segs"] == len(segs) and gold["checks"]["sum_segs"] == int(segs.sum())
+    ids = np.array(gold["node_ids"])
+    assert np.allclose(nodes[ids], np.array(gold["node_xyz"]), rtol=0, atol=1e-12)
+    Fo = np.array(gold["forces"])
+    Fd = _forces(nodes, segs, b, wl, p=p, precision="fp64", circle_q=32)
+    Fm = _forces(nodes, segs, b, wl, p=p)
+    e_d = np.linalg.norm(Fd[ids] - Fo) / np.linalg.norm(Fo)
+    e_m = np.linalg.norm(Fm[ids] - Fo) / np.linalg.norm(Fo)
+    e_md = oracle.rel_l2(Fm, Fd)
+    print(f"250k segments, p={p}: FP64 pass vs direct sum {e_d:.3e}, mixed vs direct sum {e_m:.3e}, "
+          f"mixed vs FP64 pass (all nodes) {e_md:.3e}")
+    assert e_d < 1e-3 and e_m < 1e-3
