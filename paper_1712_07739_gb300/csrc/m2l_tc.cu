@@ -876,7 +876,8 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     prm.drop_first = T.inject_drop;
     T.inject_drop = 0;
     const int stage_bytes = 128 * 64 * 2 + T.ncta * 128;
-    int stages = std::max(2, std::min(6, (200 * 1024) / stage_bytes));
+    // as many stages as fit in the 227 KB a block may use (barriers and alignment take ~1.2 KB)
+    int stages = std::max(2, std::min(6, (225 * 1024) / stage_bytes));
     const size_t smem = size_t(stages) * stage_bytes + 1024 + (2 * stages + 2) * 8 + 64;
     ++ctx->launches;
     if (T.tf32) {

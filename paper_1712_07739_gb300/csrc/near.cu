@@ -372,11 +372,13 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
     const float bsh[3] = {float(ox * h), float(oy * h), float(oz * h)};
     const int Q = mat->Q;
     const float c12f = float(mat->c12), c44f = float(mat->c44), cdf = float(mat->cd);
-    const int nA = sA1 - sA0;
-    const int tg = nA >= 32 ? 32 : (nA > 16 ? 32 : (nA > 8 ? 16 : (nA > 4 ? 8 : (nA > 2 ? 4 : (nA > 1 ? 2 : 1)))));
-    const int ls = 32 / tg, ti = lane % tg, tj = lane / tg;
     bool first_chunk = true;
-    for (int r0 = sA0; r0 < sA1; r0 += tg) {
+    for (int r0 = sA0; r0 < sA1; r0 += 32) {
+        // tg targets in this chunk, 32 / tg lanes per target splitting the sources
+        const int nrem = min(32, sA1 - r0);
+        int tg = 1;
+        while (tg < nrem) tg <<= 1;
+        const int ls = 32 / tg, ti = lane % tg, tj = lane / tg;
         const int i = r0 + ti;
         const bool vi = i < sA1;
         // stage the lanes' own source tensors, transposed (column ti): lanes read

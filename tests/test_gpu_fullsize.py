@@ -64,7 +64,8 @@ def _forces(nodes, segs, b, wl, **over):
     ("bench configuration", {}, 3e-4),
     ("BF16, residual passes on the nearest offsets", {"m2l_split": 0}, 3e-4),
     ("p=7", {"p": 7}, 3e-4),
-    ("p=8", {"p": 8}, 3e-4),
+    ("p=7, FP16 with residual passes on the nearest offsets", {"p": 7, "m2l_split": 5}, 3e-4),
+    ("p=8, FP16 with residual passes on the nearest offsets", {"p": 8, "m2l_split": 5}, 3e-4),
 ])
 def test_full_size_sampled_nodes_match_direct_sum(c3_case, label, over, tol):
     nodes, segs, b, wl, ids, Fo = c3_case
