@@ -42,10 +42,11 @@ UNIT = "segments/s"
 #   10 cubic FMAs and 2 scaled adds (29) x 6 -> 202
 # unit-circle h in a cubic medium with axes along x, y, z (the specialised
 #   form both paths use): separation, |d|^2, rsqrt, direction and circle basis
-#   41; per circle point 219 (point 9, zz 15, cofactors 18, determinant and
-#   scaling 12, zT 18, U = (zz)^-1 zT 45, F = U (zz)^-1 30, accumulate 18 x 4);
-#   final scale 19; contraction with the 6x18 source tensor and 1/R^2 229;
-#   accumulate 6 -> 219 Q + 295
+#   41; per circle point 193 (point 9, zz 15, adjugate 18, determinant and
+#   reciprocal 6, zT 18, U = adj zT 45, F = U adj 30, 1/det^2 into z 4,
+#   accumulate z F 36, sum of (zz)^-1 12); final T-term and scale 36;
+#   contraction with the 6x18 source tensor and 1/R^2 223; accumulate 6
+#   -> 193 Q + 306
 # unit-circle h, general medium: Q x (zz and zT from the 81-entry C 2 x 81
 #   FMA, inverse 30, F 54, accumulate 36, point 6) ~ Q x 450, plus 236
 FLOP_PER_NEAR_PAIR = {("fp64", "iso"): 341, ("mixed", "iso"): 202}
@@ -66,7 +67,7 @@ def is_cubic_aligned(C6):
 def near_pair_flops(precision, h_mode, q, cubic=False):
     if h_mode == "iso":
         return FLOP_PER_NEAR_PAIR[(precision, h_mode)]
-    return 219 * q + 295 if cubic else 450 * q + 236
+    return 193 * q + 306 if cubic else 450 * q + 236
 
 
 FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 (nominal, profiling recipe table)

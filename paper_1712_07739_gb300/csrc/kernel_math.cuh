@@ -204,21 +204,27 @@ __device__ __forceinline__ void h_cubic_f32(float cp, float c44, float D, int Q,
     const float e10 = a0 * nr, e11 = a1 * nr, e12 = a2 * nr;
     const float e20 = T1 * e12 - T2 * e11, e21 = T2 * e10 - T0 * e12, e22 = T0 * e11 - T1 * e10;
     const float cpD = cp + D, cpD2 = 2.f * (cp + D);
-    float acc[18];
+    // With C = adj(zz), (zz)^-1 = C / det and F = C S C / det^2, so the point's
+    // factors fold into z (z / det^2) and the (zz)^-1 sum (C / det); the
+    // T-term of the integrand is summed over the points first,
+    // sum_k T_q (zz)^-1_vp = T_q sum_k (zz)^-1_vp.
+    float acc[18], msum[6];
 #pragma unroll
     for (int i = 0; i < 18; ++i) acc[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) msum[i] = 0.f;
     for (int k = 0; k < Q; ++k) {
         const float2 t = tab[k];
         const float z0 = t.x * e10 + t.y * e20, z1 = t.x * e11 + t.y * e21, z2 = t.x * e12 + t.y * e22;
         const float m00 = fmaf(cpD, z0 * z0, c44), m11 = fmaf(cpD, z1 * z1, c44), m22 = fmaf(cpD, z2 * z2, c44);
         const float m01 = cp * z0 * z1, m02 = cp * z0 * z2, m12 = cp * z1 * z2;
-        float i00 = m11 * m22 - m12 * m12, i01 = m02 * m12 - m01 * m22, i02 = m01 * m12 - m02 * m11;
-        float i11 = m00 * m22 - m02 * m02, i12 = m01 * m02 - m00 * m12, i22 = m00 * m11 - m01 * m01;
-        const float idet = __frcp_rn(m00 * i00 + m01 * i01 + m02 * i02);
-        i00 *= idet; i01 *= idet; i02 *= idet; i11 *= idet; i12 *= idet; i22 *= idet;
+        const float i00 = m11 * m22 - m12 * m12, i01 = m02 * m12 - m01 * m22, i02 = m01 * m12 - m02 * m11;
+        const float i11 = m00 * m22 - m02 * m02, i12 = m01 * m02 - m00 * m12, i22 = m00 * m11 - m01 * m01;
+        float idet;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(idet) : "f"(m00 * i00 + m01 * i01 + m02 * i02));
         const float s00 = cpD2 * z0 * T0, s11 = cpD2 * z1 * T1, s22 = cpD2 * z2 * T2;
         const float s01 = cp * (z0 * T1 + z1 * T0), s02 = cp * (z0 * T2 + z2 * T0), s12 = cp * (z1 * T2 + z2 * T1);
-        // U = Mi S, F = U Mi (symmetric)
+        // U = C S, F = U C (symmetric), both without the 1 / det factors
         const float u00 = i00 * s00 + i01 * s01 + i02 * s02, u01 = i00 * s01 + i01 * s11 + i02 * s12,
                     u02 = i00 * s02 + i01 * s12 + i02 * s22;
         const float u10 = i01 * s00 + i11 * s01 + i12 * s02, u11 = i01 * s01 + i11 * s11 + i12 * s12,
@@ -229,19 +235,26 @@ __device__ __forceinline__ void h_cubic_f32(float cp, float c44, float D, int Q,
                     F02 = u00 * i02 + u01 * i12 + u02 * i22;
         const float F11 = u10 * i01 + u11 * i11 + u12 * i12, F12 = u10 * i02 + u11 * i12 + u12 * i22,
                     F22 = u20 * i02 + u21 * i12 + u22 * i22;
+        const float w = idet * idet;
+        const float y0 = z0 * w, y1 = z1 * w, y2 = z2 * w;
         // pairs (00) (11) (22) (12) (02) (01), each with q = 0, 1, 2
         const float Mp[6] = {i00, i11, i22, i12, i02, i01};
         const float Fp[6] = {F00, F11, F22, F12, F02, F01};
 #pragma unroll
         for (int pr = 0; pr < 6; ++pr) {
-            acc[3 * pr + 0] += z0 * Fp[pr] - T0 * Mp[pr];
-            acc[3 * pr + 1] += z1 * Fp[pr] - T1 * Mp[pr];
-            acc[3 * pr + 2] += z2 * Fp[pr] - T2 * Mp[pr];
+            acc[3 * pr + 0] = fmaf(y0, Fp[pr], acc[3 * pr + 0]);
+            acc[3 * pr + 1] = fmaf(y1, Fp[pr], acc[3 * pr + 1]);
+            acc[3 * pr + 2] = fmaf(y2, Fp[pr], acc[3 * pr + 2]);
+            msum[pr] = fmaf(Mp[pr], idet, msum[pr]);
         }
     }
     const float f = 1.f / (4.f * 3.14159265358979f * float(Q));
 #pragma unroll
-    for (int i = 0; i < 18; ++i) hs[i] = acc[i] * f;
+    for (int pr = 0; pr < 6; ++pr) {
+        hs[3 * pr + 0] = (acc[3 * pr + 0] - T0 * msum[pr]) * f;
+        hs[3 * pr + 1] = (acc[3 * pr + 1] - T1 * msum[pr]) * f;
+        hs[3 * pr + 2] = (acc[3 * pr + 2] - T2 * msum[pr]) * f;
+    }
 }
 
 // Lagrange basis on the p equispaced nodes t_a = a / (p - 1) of [0, 1]

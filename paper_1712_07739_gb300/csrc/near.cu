@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
     const float *__restrict__ c32, const int64_t *__restrict__ ssid, double *__restrict__ part, int64_t N,
     const int2 *__restrict__ items, const int *__restrict__ n_items) {
     extern __shared__ __align__(16) float sm_sym[];
-    float *wPA = sm_sym + (threadIdx.x / 32) * (32 * 108 + SYM_SCH * 108);  // [108][32]: lanes' own tensors
+    float *wPA = sm_sym + (threadIdx.x / 32) * (32 * 108 + SYM_SCH * 108);  // [32][108]: lanes' own tensors
     float *wPB = wPA + 32 * 108;                                            // [SCH][108] staged sources
     __shared__ float4 syB[SYM_WARPS][SYM_SCH];
     __shared__ int sdB[SYM_WARPS][SYM_SCH];
@@ -381,18 +381,13 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
         const int ls = 32 / tg, ti = lane % tg, tj = lane / tg;
         const int i = r0 + ti;
         const bool vi = i < sA1;
-        // stage the lanes' own source tensors, transposed (column ti): lanes read
-        // consecutive words
+        // stage the lanes' own source tensors, one 432-byte row per target: the
+        // 16-byte reads of 8 consecutive rows fall in 8 different bank quads
         __syncwarp();
-        if (vi && tj == 0) {
-            const float4 *src = reinterpret_cast<const float4 *>(c32 + int64_t(108) * i);
-            for (int c4 = 0; c4 < 27; ++c4) {
-                const float4 v = __ldg(src + c4);
-                wPA[(4 * c4) * 32 + ti] = v.x;
-                wPA[(4 * c4 + 1) * 32 + ti] = v.y;
-                wPA[(4 * c4 + 2) * 32 + ti] = v.z;
-                wPA[(4 * c4 + 3) * 32 + ti] = v.w;
-            }
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(c32 + int64_t(108) * r0);
+            float4 *dst = reinterpret_cast<float4 *>(wPA);
+            for (int k = lane; k < nrem * 27; k += 32) dst[k] = __ldg(src + k);
         }
         __syncwarp();
         float4 yi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -405,7 +400,7 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
         }
         float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         double acc64[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        const float *Pi = wPA + ti;  // element c at Pi[32 c]
+        const float4 *Pi4 = reinterpret_cast<const float4 *>(wPA + 108 * ti);
         const int jb0 = self ? r0 : sB0;  // own leaf: pairs j > i only
         for (int j0 = jb0; j0 < sB1; j0 += SYM_SCH) {
             const int nj = min(SYM_SCH, sB1 - j0);
@@ -457,17 +452,23 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
                     else
                         h_circle_sym<float, float>(sC, Q, T, hs);
                     const float ir2 = ir * ir;
-                    const float *Pj = wPB + 108 * jl;
+                    const float4 *Pj4 = reinterpret_cast<const float4 *>(wPB + 108 * jl);
+                    // both contractions over the 108 entries in 16-byte pieces (entry c = 18 ab + k)
+#pragma unroll
+                    for (int c4 = 0; c4 < 27; ++c4) {
+                        const float4 pj = Pj4[c4], pi = Pi4[c4];
+                        const float vj[4] = {pj.x, pj.y, pj.z, pj.w}, vi4[4] = {pi.x, pi.y, pi.z, pi.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int c = 4 * c4 + e;
+                            fw[c / 18] = fmaf(vj[e], hs[c % 18], fw[c / 18]);
+                            rv[c / 18] = fmaf(vi4[e], hs[c % 18], rv[c / 18]);
+                        }
+                    }
 #pragma unroll
                     for (int ab = 0; ab < 6; ++ab) {
-                        float sf = 0.f, sr = 0.f;
-#pragma unroll
-                        for (int k = 0; k < 18; ++k) {
-                            sf = fmaf(Pj[ab * 18 + k], hs[k], sf);
-                            sr = fmaf(Pi[32 * (ab * 18 + k)], hs[k], sr);
-                        }
-                        fw[ab] = sf * ir2;
-                        rv[ab] = -sr * ir2;
+                        fw[ab] *= ir2;
+                        rv[ab] *= -ir2;
                     }
                     if (close) {
 #pragma unroll
@@ -477,27 +478,28 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
                         for (int ab = 0; ab < 6; ++ab) acc[ab] += fw[ab];
                     }
                 }
-                // reverse: sum over the tg lanes that share source jl (fixed order)
-                const bool anyclose = __any_sync(0xffffffffu, close);
-                double rv64[6];
+                // reverse: sum over the tg lanes that share source jl (fixed order); close
+                // pairs go through FP64, only when the warp has one
+                if (__any_sync(0xffffffffu, close)) {
+                    double rv64[6];
 #pragma unroll
-                for (int ab = 0; ab < 6; ++ab) {
-                    rv64[ab] = close ? double(rv[ab]) : 0.0;
-                    if (close) rv[ab] = 0.f;
+                    for (int ab = 0; ab < 6; ++ab) {
+                        rv64[ab] = close ? double(rv[ab]) : 0.0;
+                        if (close) rv[ab] = 0.f;
+                    }
+                    for (int off = 1; off < tg; off <<= 1)
+#pragma unroll
+                        for (int ab = 0; ab < 6; ++ab) rv64[ab] += __shfl_xor_sync(0xffffffffu, rv64[ab], off);
+                    if (ti == 0 && jl < nj)
+#pragma unroll
+                        for (int ab = 0; ab < 6; ++ab) sacc64B[warp][jl][ab] += rv64[ab];
                 }
                 for (int off = 1; off < tg; off <<= 1)
 #pragma unroll
                     for (int ab = 0; ab < 6; ++ab) rv[ab] += __shfl_xor_sync(0xffffffffu, rv[ab], off);
-                if (anyclose)
-                    for (int off = 1; off < tg; off <<= 1)
-#pragma unroll
-                        for (int ab = 0; ab < 6; ++ab) rv64[ab] += __shfl_xor_sync(0xffffffffu, rv64[ab], off);
                 if (ti == 0 && jl < nj) {
 #pragma unroll
-                    for (int ab = 0; ab < 6; ++ab) {
-                        saccB[warp][jl][ab] += rv[ab];
-                        if (anyclose) sacc64B[warp][jl][ab] += rv64[ab];
-                    }
+                    for (int ab = 0; ab < 6; ++ab) saccB[warp][jl][ab] += rv[ab];
                 }
             }
             __syncwarp();

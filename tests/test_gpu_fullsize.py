@@ -61,11 +61,13 @@ def _forces(nodes, segs, b, wl, **over):
 
 
 @pytest.mark.parametrize("label,over,tol", [
-    ("bench configuration", {}, 3e-4),
-    ("BF16, residual passes on the nearest offsets", {"m2l_split": 0}, 3e-4),
-    ("p=7", {"p": 7}, 3e-4),
-    ("p=7, FP16 with residual passes on the nearest offsets", {"p": 7, "m2l_split": 5}, 3e-4),
-    ("p=8, FP16 with residual passes on the nearest offsets", {"p": 8, "m2l_split": 5}, 3e-4),
+    pytest.param("bench configuration", {}, 3e-4, id="bench"),
+    pytest.param("BF16, residual passes on the nearest offsets", {"m2l_split": 0}, 3e-4, id="bf16split"),
+    pytest.param("p=7", {"p": 7}, 3e-4, id="p7"),
+    pytest.param("p=7, FP16 with residual passes on the nearest offsets", {"p": 7, "m2l_split": 5}, 3e-4,
+                 id="p7split"),
+    pytest.param("p=8, FP16 with residual passes on the nearest offsets", {"p": 8, "m2l_split": 5}, 3e-4,
+                 id="p8split"),
 ])
 def test_full_size_sampled_nodes_match_direct_sum(c3_case, label, over, tol):
     nodes, segs, b, wl, ids, Fo = c3_case
