@@ -70,6 +70,11 @@ def near_pair_flops(precision, h_mode, q, cubic=False):
     return 193 * q + 306 if cubic else 450 * q + 236
 
 
+# DRAM bytes per target point of one k_near_sym launch (cubic rule, Q = 20), from
+# one ncu capture on the 250,000-segment slab network (dram__bytes_read.sum +
+# dram__bytes_write.sum = 7.55 GB for 1,000,000 points); valid for that kernel
+# version only
+NEAR_SYM_DRAM_BYTES_PER_POINT = 7.554e9 / 1.0e6
 FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 (nominal, profiling recipe table)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
@@ -473,13 +478,19 @@ def run_ours(args, wl):
     p = wl["p"]
     fp64 = wl["precision"] == "fp64"
     peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+    traffic, traffic_src = None, None
     if leaf_ms >= m2l_ms:
         flops = (work["near_pairs"] * near_pair_flops(wl["precision"], wl["h_mode"], wl.get("circle_q", 64),
                                                       is_cubic_aligned(wl["C"]()))
                  + work["points"] * (12 * p ** 3 + 30 * p))
         achieved = flops / (leaf_ms / 1e3) / 1e12
-        dom = ("k_leaf_eval_f64" if fp64 else "k_near_mixed") + " (L2P + near-field P2P)"
+        sym = not fp64 and wl["h_mode"] == "circle"
+        dom = ("k_leaf_eval_f64" if fp64 else ("k_near_sym" if sym else "k_near_mixed")) + " (L2P + near-field P2P)"
         bound, src = "alu", ("FP64 1.25 TFLOP/s nominal (recipe)" if fp64 else "152 SM x 128 lanes x 2 x 2.07 GHz")
+        if sym and wl.get("circle_q") == 20:
+            traffic = NEAR_SYM_DRAM_BYTES_PER_POINT * work["points"]
+            traffic_src = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_near_sym on the "
+                           "250k-segment slab network (7.55 GB for 1,000,000 points), scaled by points")
     else:
         flops = work["m2l_pairs"] * 2 * 54 * p ** 6
         achieved = flops / (m2l_ms / 1e3) / 1e12
@@ -489,7 +500,7 @@ def run_ours(args, wl):
             dom, bound = "k_m2l_tc (M2L, tcgen05 BF16)", "tensor"
             peak, src = measured_bf16_peak()
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": src,
                 "work": "algorithmic: near pairs x FLOP/pair (+ L2P), or M2L cell pairs x 2*54*p^6"}
 
     if rank == 0:
