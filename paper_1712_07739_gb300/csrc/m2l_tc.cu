@@ -9,16 +9,17 @@
 // offsets of class c are therefore, each, a constant shift between two
 // sub-grids.
 //
-// Tiles.  The sub-grid of a class is cut into bricks of 8 x 4 x 4 cells (128
-// rows); the bricks holding at least one target cell are listed per (level,
-// class) and each is one tile.  The M2L of a tile is
+// Tiles.  The cells of a (level, class) that hold targets are listed in
+// Morton order of their sub-grid position; 128 consecutive ones form a tile.
+// The M2L of a tile is
 //     S[cell, n] = (2^l / H)^2  sum_o  sum_k  W_c'[cell + s_o, k] T_o[n, k]
 // with k = (node m, component wr) and n = (node l, stress component ab):
 // one GEMM of M = 128 cells, N = 6 p^3 and K = (active offsets) x 9 p^3,
-// accumulated in tensor memory.  The A tile is one TMA box of shifted
-// multipole rows (zero-filled where the box leaves the sub-grid), the B tile
-// rows of the operator T_o.  Offsets whose 128 source cells are all empty
-// are skipped (checked per cell when the tile starts).
+// accumulated in tensor memory.  The A tile (the 128 shifted multipole rows)
+// is gathered by cp.async, one row per thread, into the swizzled layout the
+// MMA reads (sources outside the sub-grid or without segments read as
+// zeros); the B tile (rows of the operator T_o) comes by TMA.  Offsets whose
+// 128 source cells are all empty are skipped.
 //
 // Precision: BF16 operands (hi); for the offsets nearest to the target
 // (max |o_i| = 2, the largest far-field terms) the residuals W_lo = W - hi(W)
@@ -26,10 +27,11 @@
 // modes: TF32 operands; FP16 operands with a power-of-two scale per level for
 // W and one for the operators (FP16 carries 3 more mantissa bits than BF16).
 //
-// Warp roles (192 threads): warp 0 issues TMA loads (lane j loads brick j
-// of the tile, lanes 16-18 the operator rows), warp 1 owns TMEM and issues
-// the MMAs, warps 2-5 read the accumulator out (warp w reads TMEM lanes
-// 32 (w % 4) .. 32 (w % 4) + 31).  Every mbarrier wait is bounded; on
+// Warp roles (192 threads): warp 0 loads the operator rows by TMA, warp 1
+// owns TMEM and issues the MMAs, warps 2-5 gather the multipole rows (each
+// thread waits for its copies, fences them to the async proxy and arrives on
+// the stage's barrier) and then read the accumulator out (warp w reads TMEM
+// lanes 32 (w % 4) .. 32 (w % 4) + 31).  Every mbarrier wait is bounded; on
 // time-out a device status word gets GBFMM_ERR_TIMEOUT and the block winds
 // down, freeing its tensor memory.
 #include <cuda.h>
@@ -58,8 +60,9 @@ struct OffsetEntry {
 __constant__ OffsetEntry c_offs[8][189];
 
 struct M2LParams {
-    CUtensorMap tmW[GB_TC_MAXLEV];    // W hi per level: (Kp, m, m, m, 8), box (64, 2, 2, 2, 1)
-    CUtensorMap tmWlo[GB_TC_MAXLEV];  // W residual per level
+    const uint8_t *Whi, *Wlo;         // packed W (hi, residual), level l at byte wofs[l]
+    int64_t wofs[GB_TC_MAXLEV];
+    int row_bytes;                    // K_pad x element size
     CUtensorMap tmT;                  // T hi: (Kp, Np, 316)
     CUtensorMap tmTlo;                // T residual: (Kp, Np, n_lo)
     int kb;         // K blocks of 64
@@ -127,6 +130,26 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *st
             return false;
         }
     }
+}
+
+// 16-byte global -> shared copy; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most n groups of this thread are pending (n is 0..5)
+__device__ __forceinline__ void cp_async_wait(int n) {
+    switch (n) {
+        case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+    }
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
@@ -199,17 +222,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Bricks: BX x BY x BZ cells of one class sub-grid, RB = 128 / NBT cells;
-// NBT bricks of one (level, class) make a 128-row tile.  Slots: level l
-// (2 <= l < L) has 8 classes x nbx x nby x nbz bricks (x fastest) starting at
-// base[l]; the bricks that hold targets are listed in slot order.
-constexpr int BX = 8, BY = 4, BZ = 4, RB = BX * BY * BZ, NBT = 128 / RB;
-static_assert(NBT * RB == 128, "a tile holds 128 cells");
+// Target lists.  Every cell of levels 2 .. L-1 has one slot: level l starts
+// at cell_base(l) - cell_base(2), then class c (m^3 slots each), then the
+// Morton code of the cell's sub-grid position.  The cells holding targets are
+// listed in slot order; 128 consecutive ones of a (level, class) make a tile.
+__host__ __device__ inline int64_t slot_base(int l) { return cell_base_d(l) - cell_base_d(2); }
 
-using BrickGrid = TcPlanGrid;
+__device__ __forceinline__ uint32_t morton_part(uint32_t v) {  // 10 bits -> every third bit
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__device__ __forceinline__ uint32_t morton_compact(uint32_t v) {
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030c30c3u;
+    v = (v | (v >> 4)) & 0x0300f00fu;
+    v = (v | (v >> 8)) & 0x030000ffu;
+    v = (v | (v >> 16)) & 0x3ffu;
+    return v;
+}
 
 // Segments: one per (level, class), index (l - 2) * 8 + c.  seg[s] = {first
-// list entry, bricks, first tile}; seg[n_seg].z = total tiles.
+// list entry, cells, first tile}; seg[n_seg].z = total tiles.
 constexpr int kMaxSeg = 8 * GB_TC_MAXLEV;
 
 // number of K-block iterations of one work item (same count on every warp)
@@ -217,8 +254,8 @@ __device__ __forceinline__ int passes_of(const OffsetEntry &e, int split) { retu
 
 template <bool TF32>
 __global__ void __launch_bounds__(192, 1)
-    k_m2l_tc(const __grid_constant__ M2LParams P, const BrickGrid G, const int4 *__restrict__ seg, int n_seg,
-             const int *__restrict__ mb_list, const int *__restrict__ occ, const int *__restrict__ tocc,
+    k_m2l_tc(const __grid_constant__ M2LParams P, const int4 *__restrict__ seg, int n_seg,
+             const int *__restrict__ list, const int *__restrict__ occ, const int *__restrict__ tocc,
              const TreeBox *__restrict__ box, float *__restrict__ S, int *__restrict__ status, int stages, int groups) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -228,8 +265,8 @@ __global__ void __launch_bounds__(192, 1)
     // bars[0..stages): full, [stages..2 stages): empty, [2 stages]: accumulator ready
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 1);
 
-    __shared__ int s_level, s_cls, s_nmb, s_stop;
-    __shared__ int s_mb[NBT][3];       // brick origins (sub-grid cells) of this tile
+    __shared__ int s_level, s_cls, s_rows, s_nrow, s_stop;
+    __shared__ short s_tgt[128][3];    // sub-grid positions of the tile's target cells
     __shared__ uint32_t s_active[6];   // offsets with at least one occupied source cell
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int tile = blockIdx.x / groups, group = blockIdx.x % groups;
@@ -239,19 +276,12 @@ __global__ void __launch_bounds__(192, 1)
         if (tile < seg[n_seg].z)
             for (int si = 0; si < n_seg; ++si) {
                 const int4 sg = seg[si];
-                const int nt = (sg.y + NBT - 1) / NBT;
+                const int nt = (sg.y + 127) / 128;
                 if (tile >= sg.z && tile < sg.z + nt) {
-                    const int t = tile - sg.z;
-                    const int l = si / 8 + 2;
-                    s_level = l;
+                    s_level = si / 8 + 2;
                     s_cls = si % 8;
-                    s_nmb = min(NBT, sg.y - NBT * t);
-                    for (int j = 0; j < s_nmb; ++j) {
-                        const int bi = mb_list[sg.x + NBT * t + j];
-                        s_mb[j][0] = BX * (bi % G.nbx[l]);
-                        s_mb[j][1] = BY * ((bi / G.nbx[l]) % G.nby[l]);
-                        s_mb[j][2] = BZ * (bi / (G.nbx[l] * G.nby[l]));
-                    }
+                    s_rows = sg.x + 128 * (tile - sg.z);  // first list entry of the tile
+                    s_nrow = min(128, sg.y - 128 * (tile - sg.z));
                     break;
                 }
             }
@@ -259,9 +289,18 @@ __global__ void __launch_bounds__(192, 1)
     if (threadIdx.x < 6) s_active[threadIdx.x] = 0u;
     __syncthreads();
     if (s_level < 0 || s_stop) return;  // surplus block, or an earlier block timed out
-    const int level = s_level, cls = s_cls, nmb = s_nmb;
+    const int level = s_level, cls = s_cls, nrow = s_nrow;
     const int m = 1 << (level - 1), n = 1 << level;
     const int64_t cbase = cell_base_d(level);
+    if (threadIdx.x < 128) {
+        int sx = -1024, sy = -1024, sz = -1024;  // rows past the tile's cells: far outside the sub-grid
+        if (threadIdx.x < nrow) {
+            const uint32_t code = uint32_t(list[s_rows + threadIdx.x]);
+            sx = int(morton_compact(code)), sy = int(morton_compact(code >> 1)), sz = int(morton_compact(code >> 2));
+        }
+        s_tgt[threadIdx.x][0] = short(sx), s_tgt[threadIdx.x][1] = short(sy), s_tgt[threadIdx.x][2] = short(sz);
+    }
+    __syncthreads();
 
     // active offsets: lane r of warp w checks tile rows 4r .. 4r + 3
     for (int oi = warp; oi < 189; oi += 6) {
@@ -269,10 +308,8 @@ __global__ void __launch_bounds__(192, 1)
         const int ccx = e.cls & 1, ccy = (e.cls >> 1) & 1, ccz = e.cls >> 2;
         bool hit = false;
         for (int q = 0; q < 4; ++q) {
-            const int row = 4 * lane + q, j = row / RB, w = row % RB;  // in a brick: x fastest, then y, z
-            if (j >= nmb) continue;
-            const int px = s_mb[j][0] + w % BX + e.sx, py = s_mb[j][1] + (w / BX) % BY + e.sy,
-                      pz = s_mb[j][2] + w / (BX * BY) + e.sz;
+            const int row = 4 * lane + q;
+            const int px = s_tgt[row][0] + e.sx, py = s_tgt[row][1] + e.sy, pz = s_tgt[row][2] + e.sz;
             if (px >= 0 && py >= 0 && pz >= 0 && px < m && py < m && pz < m) {
                 const int64_t g = cbase + (int64_t(2 * pz + ccz) * n + (2 * py + ccy)) * n + (2 * px + ccx);
                 hit |= occ[g] > 0;
@@ -282,7 +319,9 @@ __global__ void __launch_bounds__(192, 1)
     }
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2 * stages + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        // full: the operator-load thread (expect_tx) + 128 gathering threads; empty: the MMA commit
+        for (int s = 0; s < stages; ++s) mbar_init(smem_u32(&bars[s]), 129);
+        for (int s = stages; s < 2 * stages + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -297,10 +336,9 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t tmem = *tmem_slot;
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[stages]), accb = smem_u32(&bars[2 * stages]);
     const uint32_t smem0 = smem_u32(smem);
-    const uint32_t stage_tx = uint32_t(nmb) * uint32_t(RB * 128) + uint32_t(stageB);
 
-    if (warp == 0) {
-        // ---------------- TMA producer (the whole warp: one load per lane and stage)
+    if (warp == 0 && lane == 0) {
+        // ---------------- operator rows (B) by TMA
         int it = 0;
         bool ok = true;
         for (int oi = 0; oi < 189 && ok; ++oi) {
@@ -308,30 +346,22 @@ __global__ void __launch_bounds__(192, 1)
             const OffsetEntry e = c_offs[cls][oi];
             const int np = passes_of(e, P.split);
             for (int pass = 0; pass < np && ok; ++pass) {
-                const CUtensorMap *ta = (pass == 1) ? &P.tmWlo[level] : &P.tmW[level];
                 const CUtensorMap *tb = (pass == 2) ? &P.tmTlo : &P.tmT;
                 const int tidx = (pass == 2) ? e.lo : e.top;
                 for (int kb = 0; kb < P.kb; ++kb, ++it) {
                     const int s = it % stages;
                     const uint32_t ph = (it / stages) & 1;
-                    int go = 1;
-                    if (lane == 0) {
-                        go = mbar_wait(empty0 + 8 * s, ph ^ 1, status) ? 1 : 0;
-                        if (go) mbar_expect_tx(full0 + 8 * s, stage_tx);
-                    }
-                    go = __shfl_sync(0xffffffffu, go, 0);  // also orders expect_tx before the loads
-                    if (!go) {
+                    if (!mbar_wait(empty0 + 8 * s, ph ^ 1, status)) {
                         ok = false;
                         break;
                     }
+                    const uint32_t fb = full0 + 8 * s;
+                    mbar_expect_tx(fb, uint32_t(stageB));
                     if (P.drop_first && it == 0) continue;  // the MMA warp's wait on this stage runs out
-                    const uint32_t a = smem0 + s * stage_bytes, fb = full0 + 8 * s;
-                    if (lane < nmb)
-                        tma_load_5d(a + lane * (RB * 128), ta, kb * P.kstep, s_mb[lane][0] + e.sx,
-                                    s_mb[lane][1] + e.sy, s_mb[lane][2] + e.sz, e.cls, fb);
-                    else if (lane >= 16 && lane < 19)
-                        tma_load_3d(a + kStageA + (lane - 16) * P.nsub * 128, tb, kb * P.kstep,
-                                    group * P.ncta + (lane - 16) * P.nsub, tidx, fb);
+                    const uint32_t a = smem0 + s * stage_bytes;
+                    for (int j = 0; j < 3; ++j)
+                        tma_load_3d(a + kStageA + j * P.nsub * 128, tb, kb * P.kstep, group * P.ncta + j * P.nsub,
+                                    tidx, fb);
                 }
             }
         }
@@ -367,24 +397,70 @@ __global__ void __launch_bounds__(192, 1)
         }
         mma_commit(accb);  // fires when every MMA issued above has completed
     } else if (warp >= 2) {
+        const int row = threadIdx.x - 64;  // 0..127: this thread's tile row
+        {
+            // ---------------- multipole rows (A): gathered by cp.async into the 128-byte
+            // swizzled K-major layout (16-byte piece c of row r at (c ^ (r & 7)) * 16);
+            // sources outside the sub-grid, or empty, read as zeros
+            const int lag = stages - 1;
+            int it = 0, done = 0;
+            bool ok = true;
+            const uint32_t rowdst = uint32_t(row) * 128u;
+            for (int oi = 0; oi < 189 && ok; ++oi) {
+                if (!((s_active[oi / 32] >> (oi % 32)) & 1u)) continue;
+                const OffsetEntry e = c_offs[cls][oi];
+                const int px = s_tgt[row][0] + e.sx, py = s_tgt[row][1] + e.sy, pz = s_tgt[row][2] + e.sz;
+                bool have = px >= 0 && py >= 0 && pz >= 0 && px < m && py < m && pz < m;
+                int64_t srow = 0;
+                if (have) {
+                    const int ccx = e.cls & 1, ccy = (e.cls >> 1) & 1, ccz = e.cls >> 2;
+                    have = occ[cbase + (int64_t(2 * pz + ccz) * n + (2 * py + ccy)) * n + (2 * px + ccx)] > 0;
+                    srow = ((int64_t(e.cls) * m + pz) * m + py) * m + px;
+                }
+                const uint32_t nb = have ? 16u : 0u;
+                const int np = passes_of(e, P.split);
+                for (int pass = 0; pass < np && ok; ++pass) {
+                    const uint8_t *src = ((pass == 1) ? P.Wlo : P.Whi) + P.wofs[level] + srow * P.row_bytes;
+                    for (int kb = 0; kb < P.kb; ++kb, ++it) {
+                        const int s = it % stages;
+                        const uint32_t ph = (it / stages) & 1;
+                        if (!mbar_wait(empty0 + 8 * s, ph ^ 1, status)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t dst = smem0 + s * stage_bytes + rowdst;
+                        const uint8_t *sk = src + kb * 128;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) cp_async16(dst + ((c ^ (row & 7)) << 4), sk + 16 * c, nb);
+                        cp_async_commit();
+                        if (it - done >= lag) {
+                            // the copies of stage `done` are complete: make them visible to the
+                            // tensor cores, then count this thread in that stage's full barrier
+                            cp_async_wait(lag);
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                            mbar_arrive(full0 + 8 * (done % stages));
+                            ++done;
+                        }
+                    }
+                }
+            }
+            cp_async_wait(0);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (; done < it; ++done) mbar_arrive(full0 + 8 * (done % stages));
+        }
         // ---------------- epilogue: TMEM -> scaled FP32 local values of the tile's target cells
         bool any_src = false;
         for (int i = 0; i < 6; ++i) any_src |= s_active[i] != 0u;
         const bool ok = mbar_wait(accb, 0, status);
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int q = warp % 4;
-        const int row = q * 32 + lane;
-        const int j = row / RB, w = row % RB;
-        bool valid = ok && j < nmb;
+        const int trow = q * 32 + lane;  // TMEM lane = tile row
+        bool valid = ok && trow < nrow;
         int64_t g = 0;
         if (valid) {
-            const int px = s_mb[j][0] + w % BX, py = s_mb[j][1] + (w / BX) % BY, pz = s_mb[j][2] + w / (BX * BY);
-            valid = px < m && py < m && pz < m;  // bricks of small levels stick out of the sub-grid
-            if (valid) {
-                const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
-                g = cbase + (int64_t(2 * pz + cz) * n + (2 * py + cy)) * n + (2 * px + cx);
-                valid = tocc[g] > 0;
-            }
+            const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
+            g = cbase + (int64_t(2 * s_tgt[trow][2] + cz) * n + (2 * s_tgt[trow][1] + cy)) * n +
+                (2 * s_tgt[trow][0] + cx);
         }
         float sc = float(double(n) / box->H) * float(double(n) / box->H);
         if (P.wmax) sc *= P.inv_op_scale / wscale_of(P.wmax[level]);
@@ -514,20 +590,17 @@ __global__ void k_lattice_absmax(int64_t n_pts, int64_t origin, const double *__
     if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
 }
 
-// Target brick flags of one level: slot of (class, brick) set when one of its
-// cells holds targets
-__global__ void k_mb_flags(int level, BrickGrid G, const int *__restrict__ tocc, int *__restrict__ flags) {
-    const int n = 1 << level;
-    const int64_t cells = int64_t(n) * n * n;
-    const int nbx = G.nbx[level], nby = G.nby[level];
-    const int64_t nb3 = int64_t(nbx) * nby * G.nbz[level];
+// Target flags of one level: the slot of every cell that holds targets
+__global__ void k_mb_flags(int level, const int *__restrict__ tocc, int *__restrict__ flags) {
+    const int n = 1 << level, m = n / 2;
+    const int64_t cells = int64_t(n) * n * n, m3 = int64_t(m) * m * m;
     for (int64_t lin = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; lin < cells;
          lin += int64_t(gridDim.x) * blockDim.x) {
-        if (tocc[cell_base_d(level) + lin] == 0) continue;
         const int x = int(lin % n), y = int((lin / n) % n), z = int(lin / (int64_t(n) * n));
         const int cls = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
-        const int bx = (x >> 1) / BX, by = (y >> 1) / BY, bz = (z >> 1) / BZ;
-        flags[G.base[level] + cls * nb3 + (int64_t(bz) * nby + by) * nbx + bx] = 1;
+        const uint32_t code = morton_part(uint32_t(x >> 1)) | (morton_part(uint32_t(y >> 1)) << 1) |
+                              (morton_part(uint32_t(z >> 1)) << 2);
+        flags[slot_base(level) + cls * m3 + code] = tocc[cell_base_d(level) + lin] > 0 ? 1 : 0;
     }
 }
 
@@ -565,29 +638,29 @@ __global__ void k_scan_flags(int n, const int *__restrict__ flags, int *__restri
     if (threadIdx.x == 0) pos[n] = carry;
 }
 
-// compact list of the flagged slots (brick index within its segment)
-__global__ void k_mb_list(int n, int L, BrickGrid G, const int *__restrict__ flags, const int *__restrict__ pos,
+// compact list of the flagged slots (Morton code of the cell within its class)
+__global__ void k_mb_list(int n, int L, const int *__restrict__ flags, const int *__restrict__ pos,
                           int *__restrict__ list) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         if (!flags[k]) continue;
         int l = 2;
-        while (l + 1 < L && k >= G.base[l + 1]) ++l;
-        const int64_t nb3 = int64_t(G.nbx[l]) * G.nby[l] * G.nbz[l];
-        list[pos[k]] = int((k - G.base[l]) % nb3);
+        while (l + 1 < L && k >= slot_base(l + 1)) ++l;
+        const int64_t m3 = int64_t(1) << (3 * (l - 1));
+        list[pos[k]] = int((k - slot_base(l)) % m3);
     }
 }
 
-// segment table: {first list entry, bricks, first tile}; seg[n_seg].z = tiles
-__global__ void k_seg_table(int L, BrickGrid G, const int *__restrict__ pos, int4 *__restrict__ seg) {
+// segment table: {first list entry, cells, first tile}; seg[n_seg].z = tiles
+__global__ void k_seg_table(int L, const int *__restrict__ pos, int4 *__restrict__ seg) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int tiles = 0, si = 0;
     for (int l = 2; l < L; ++l) {
-        const int64_t nb3 = int64_t(G.nbx[l]) * G.nby[l] * G.nbz[l];
+        const int64_t m3 = int64_t(1) << (3 * (l - 1));
         for (int c = 0; c < 8; ++c, ++si) {
-            const int64_t s0 = G.base[l] + c * nb3;
-            const int first = pos[s0], cnt = pos[s0 + nb3] - first;
+            const int64_t s0 = slot_base(l) + c * m3;
+            const int first = pos[s0], cnt = pos[s0 + m3] - first;
             seg[si] = make_int4(first, cnt, tiles, 0);
-            tiles += (cnt + NBT - 1) / NBT;
+            tiles += (cnt + 127) / 128;
         }
     }
     seg[si] = make_int4(0, 0, tiles, 0);
@@ -776,21 +849,10 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
         CK(cudaMalloc(&T.Wlo, tot * T.esz));
         T.w_cap = tot;
     }
-    // brick slots, list and segment table (filled on the device per pass)
-    BrickGrid &G = T.grid;
-    int64_t slots = 0, tiles = 0;  // tiles: upper bound, every brick holds targets
-    for (int l = 0; l <= GB_TC_MAXLEV; ++l) G.base[l] = 0;
-    for (int l = 2; l < L; ++l) {
-        const int m = 1 << (l - 1);
-        G.nbx[l] = (m + BX - 1) / BX;
-        G.nby[l] = (m + BY - 1) / BY;
-        G.nbz[l] = (m + BZ - 1) / BZ;
-        const int64_t nb3 = int64_t(G.nbx[l]) * G.nby[l] * G.nbz[l];
-        G.base[l] = slots;
-        slots += 8 * nb3;
-        tiles += 8 * ((nb3 + NBT - 1) / NBT);
-    }
-    G.base[L] = slots;
+    // cell slots, target list and segment table (filled on the device per pass)
+    const int64_t slots = slot_base(L);
+    int64_t tiles = 0;  // upper bound: every cell holds targets
+    for (int l = 2; l < L; ++l) tiles += 8 * (((int64_t(1) << (3 * (l - 1))) + 127) / 128);
     if (slots > T.slot_cap) {
         void *ps[] = {T.d_flags, T.d_pos, T.d_list};
         for (void *q : ps)
@@ -815,7 +877,6 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     std::memset(&prm, 0, sizeof(prm));
     if (T.fp16) CK(cudaMemsetAsync(T.d_wmax, 0, GB_TC_MAXLEV * sizeof(unsigned), ctx->stream));
     for (int l = 2; l < L; ++l) {
-        const int m = 1 << (l - 1);
         const int64_t el = (int64_t(1) << (3 * l)) * T.Kp;
         void *whi = (char *)T.Whi + T.wofs[l] * T.esz, *wlo = (char *)T.Wlo + T.wofs[l] * T.esz;
         if (T.tf32) {
@@ -834,25 +895,19 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
             k_pack_w<__nv_bfloat16><<<nblk(el, 256), 256, 0, ctx->stream>>>(
                 l, P3, T.Kp, Wf, occ, nullptr, (__nv_bfloat16 *)whi, T.split ? (__nv_bfloat16 *)wlo : nullptr);
         }
-        const cuuint64_t dims[5] = {cuuint64_t(T.Kp), cuuint64_t(m), cuuint64_t(m), cuuint64_t(m), 8};
-        const cuuint64_t row = cuuint64_t(T.Kp) * T.esz;
-        const cuuint64_t strides[4] = {row, row * m, row * m * m, row * m * m * m};
-        const cuuint32_t boxd[5] = {cuuint32_t(128 / T.esz), BX, BY, BZ, 1};  // one brick
-        int rc = encode(ctx, &prm.tmW[l], whi, 5, dims, strides, boxd, T);
-        if (rc) return rc;
-        rc = encode(ctx, &prm.tmWlo[l], wlo, 5, dims, strides, boxd, T);
-        if (rc) return rc;
+        prm.wofs[l] = T.wofs[l] * T.esz;
     }
-    CK(cudaMemsetAsync(T.d_flags, 0, T.n_slots * sizeof(int), ctx->stream));
+    prm.Whi = static_cast<const uint8_t *>(T.Whi);
+    prm.Wlo = static_cast<const uint8_t *>(T.Wlo);
+    prm.row_bytes = T.Kp * T.esz;
     for (int l = 2; l < L; ++l) {
         ++ctx->launches;
-        k_mb_flags<<<nblk(int64_t(1) << (3 * l), 256), 256, 0, ctx->stream>>>(l, T.grid, tocc, T.d_flags);
+        k_mb_flags<<<nblk(int64_t(1) << (3 * l), 256), 256, 0, ctx->stream>>>(l, tocc, T.d_flags);
     }
     ctx->launches += 3;
     k_scan_flags<<<1, 1024, 0, ctx->stream>>>(int(T.n_slots), T.d_flags, T.d_pos);
-    k_mb_list<<<nblk(T.n_slots, 256), 256, 0, ctx->stream>>>(int(T.n_slots), L, T.grid, T.d_flags, T.d_pos,
-                                                             T.d_list);
-    k_seg_table<<<1, 32, 0, ctx->stream>>>(L, T.grid, T.d_pos, T.d_seg);
+    k_mb_list<<<nblk(T.n_slots, 256), 256, 0, ctx->stream>>>(int(T.n_slots), L, T.d_flags, T.d_pos, T.d_list);
+    k_seg_table<<<1, 32, 0, ctx->stream>>>(L, T.d_pos, T.d_seg);
     {
         const cuuint64_t dims[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(T.n_off)};
         const cuuint64_t strides[2] = {cuuint64_t(T.Kp) * T.esz, cuuint64_t(T.Kp) * T.esz * T.Np};
@@ -882,11 +937,11 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     ++ctx->launches;
     if (T.tf32) {
         CK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        k_m2l_tc<true><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.grid, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
+        k_m2l_tc<true><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
                                                              Sf, T.d_status, stages, T.groups);
     } else {
         CK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        k_m2l_tc<false><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.grid, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
+        k_m2l_tc<false><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
                                                               Sf, T.d_status, stages, T.groups);
     }
     CK(cudaGetLastError());

@@ -7,12 +7,6 @@
 
 struct gbfmm_ctx;
 
-// brick grid of the tensor-core M2L: slot base and bricks per level
-struct TcPlanGrid {
-    int64_t base[GB_TC_MAXLEV + 1] = {0};
-    int nbx[GB_TC_MAXLEV] = {0}, nby[GB_TC_MAXLEV] = {0}, nbz[GB_TC_MAXLEV] = {0};
-};
-
 struct TcPlan {
     bool ready_ops = false;
     int Kp = 0, Np = 0;        // padded K (9 p^3 -> multiple of 64) and N (6 p^3 -> groups x 3 nsub)
@@ -32,9 +26,8 @@ struct TcPlan {
     int n_work = 0;            // blocks launched: tile bound x groups (surplus blocks return)
     int *d_status = nullptr;
     int inject_drop = 0;       // set by fmm_inject_fault: the next run leaves one stage unfilled
-    int *d_flags = nullptr, *d_pos = nullptr, *d_list = nullptr;  // target micro-bricks, all levels
+    int *d_flags = nullptr, *d_pos = nullptr, *d_list = nullptr;  // target cells of levels >= 2
     int4 *d_seg = nullptr;     // per (level, class): first list entry, count, first tile
-    TcPlanGrid grid;           // brick grid per level (slot bases and brick counts)
     int64_t slot_cap = 0, n_slots = 0;
     int n_seg = 0;
 };
