@@ -48,7 +48,10 @@ extern "C" {
 /* precision of the pass */
 #define GBFMM_FP64 0   /* every stage in FP64 */
 #define GBFMM_MIXED 1  /* FP32 P2M/M2M/L2L/L2P and near field (FP64 for close pairs),
-                          M2L on tcgen05 tensor cores (BF16 with split correction) */
+                          M2L on tcgen05 tensor cores (operand precision: m2l_split) */
+#define GBFMM_MIXED_F64T 2  /* as GBFMM_MIXED with P2M, M2M, L2L and L2P in FP64: the rounding of
+                               these interpolations, amplified by the Lebesgue constants of the
+                               equispaced nodes, limits GBFMM_MIXED at orders p >= 7 */
 
 /* how the Green's-function factor h_vpq(T) = R^2 dG_vp/dx_q is evaluated */
 #define GBFMM_H_ISO 0     /* closed form of the isotropic Green's function (Sec. 2, Eq. "k_iso") */
@@ -67,7 +70,7 @@ typedef struct {
     int p;                 /* Lagrange nodes per dimension, 2..8 (Sec. 4.1) */
     int n_gauss;           /* Gauss points per segment, 1..16 (Sec. 2, Eq. "stress_discrete") */
     int levels;            /* octree levels L >= 3, leaves at level L-1; 0 = choose from N_s */
-    int precision;         /* GBFMM_FP64 or GBFMM_MIXED */
+    int precision;         /* GBFMM_FP64, GBFMM_MIXED or GBFMM_MIXED_F64T */
     int h_mode;            /* GBFMM_H_ISO, GBFMM_H_CIRCLE or GBFMM_H_MLP */
     int circle_q;          /* trapezoid points on the half circle for GBFMM_H_CIRCLE; 0 = 64 */
     int leaf_segments;     /* with levels == 0: target mean segments per occupied leaf; 0 = 32 */

@@ -19,9 +19,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libgbfmm.so")
 
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_F64T = 0, 1, 2  # gbfmm_options.precision
 H_ISO, H_CIRCLE, H_MLP = 0, 1, 2
-_PREC = {"fp64": FP64, "mixed": MIXED}
+_PREC = {"fp64": FP64, "mixed": MIXED, "mixed_f64t": MIXED_F64T}
 _HMODE = {"iso": H_ISO, "circle": H_CIRCLE, "mlp": H_MLP}
 
 # exported names the header declares (checked by the CPU test suite)

@@ -61,6 +61,7 @@ static int ensure_tree_buffers(gbfmm_ctx *ctx) {
     const int64_t N = ctx->N, ns = ctx->n_segs, nc = ctx->n_cells, nl = ctx->n_leaves;
     const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p;
     const bool fp64 = ctx->opt.precision == GBFMM_FP64;
+    const bool w64 = ctx->opt.precision != GBFMM_MIXED;  // FP64 multipole and local values
     if (N > ctx->cap_N) {
         release(ctx->d_y); release(ctx->d_q); release(ctx->d_sid); release(ctx->d_slen); release(ctx->d_pos);
         release(ctx->d_pleaf); release(ctx->d_sig); release(ctx->d_y0); release(ctx->d_q0);
@@ -88,7 +89,7 @@ static int ensure_tree_buffers(gbfmm_ctx *ctx) {
     if (nc > ctx->cap_cells) {
         release(ctx->d_W); release(ctx->d_S); release(ctx->d_tmp_i);
         CK(cudaMalloc(&ctx->d_tmp_i, 2 * nc * sizeof(int)));
-        if (fp64) {
+        if (w64) {
             CK(cudaMalloc(&ctx->d_W, nc * P3 * 9 * sizeof(double)));
             CK(cudaMalloc(&ctx->d_S, nc * P3 * 6 * sizeof(double)));
         }
@@ -126,7 +127,7 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
     *out = nullptr;
     if (opt->p < 2 || opt->p > GB_MAXP || opt->n_gauss < 1 || opt->n_gauss > GB_MAXG ||
         (opt->levels != 0 && (opt->levels < 3 || opt->levels > 9)) ||
-        (opt->precision != GBFMM_FP64 && opt->precision != GBFMM_MIXED) || opt->h_mode < 0 || opt->h_mode > 2 ||
+        (opt->precision < GBFMM_FP64 || opt->precision > GBFMM_MIXED_F64T) || opt->h_mode < 0 || opt->h_mode > 2 ||
         opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0) || opt->m2l_split < 0 ||
         opt->m2l_split > 5)
         return GBFMM_ERR_INVALID_ARG;
@@ -214,7 +215,7 @@ extern "C" int fmm_build_tree(gbfmm_ctx *ctx, int64_t n_nodes, const double *nod
     if (rc) return rc;
     rc = tree_build(ctx);
     if (rc) return rc;
-    if (ctx->opt.precision == GBFMM_MIXED) {
+    if (ctx->opt.precision != GBFMM_FP64) {
         rc = mixed_alloc(ctx);
         if (rc) return rc;
     }
@@ -267,7 +268,7 @@ static int end_eval(gbfmm_ctx *ctx) {
 }
 
 static int run_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
-    if (ctx->opt.precision == GBFMM_MIXED) return mixed_pass(ctx, free_targets, n_t);
+    if (ctx->opt.precision != GBFMM_FP64) return mixed_pass(ctx, free_targets, n_t);
     return fmm_pass(ctx, free_targets, n_t);
 }
 

@@ -707,8 +707,15 @@ int mixed_alloc(gbfmm_ctx *ctx) {
     return m2l_tc_prepare(ctx);
 }
 
+// leaf-level local values FP64 -> FP32 (GBFMM_MIXED_F64T, for the near kernels that read FP32)
+__global__ void k_leaf_s_to_f32(int64_t n, const double *__restrict__ S, float *__restrict__ Sf) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        Sf[i] = float(S[i]);
+}
+
 int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     cudaStream_t st = ctx->stream;
+    const bool t64 = ctx->opt.precision == GBFMM_MIXED_F64T;  // FP64 P2M, M2M, L2L, L2P
     const int p = ctx->opt.p, L = ctx->L, P3 = p * p * p;
     const int64_t N = ctx->N, nl = ctx->n_leaves;
     int *occ = ctx->d_tmp_i;
@@ -725,27 +732,45 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     timer_mark(ctx);
     if (L >= 3) {
         ++ctx->launches;
-        k_p2m<float><<<unsigned(nl), 256, 0, st>>>(p, L, ctx->d_box, ctx->d_leaf_start, ctx->d_y, ctx->d_q, ctx->d_Wf);
-        const size_t sm9 = size_t(2) * P3 * 9 * sizeof(float);
+        if (t64)
+            k_p2m<double><<<unsigned(nl), 256, 0, st>>>(p, L, ctx->d_box, ctx->d_leaf_start, ctx->d_y, ctx->d_q,
+                                                        ctx->d_W);
+        else
+            k_p2m<float><<<unsigned(nl), 256, 0, st>>>(p, L, ctx->d_box, ctx->d_leaf_start, ctx->d_y, ctx->d_q,
+                                                       ctx->d_Wf);
         for (int lev = L - 2; lev >= 2; --lev) {
             ++ctx->launches;
-            k_m2m<float><<<unsigned(int64_t(1) << (3 * lev)), 256, sm9, st>>>(p, lev, tr, occ, ctx->d_Wf);
+            const unsigned g = unsigned(int64_t(1) << (3 * lev));
+            if (t64)
+                k_m2m<double><<<g, 256, size_t(2) * P3 * 9 * sizeof(double), st>>>(p, lev, tr, occ, ctx->d_W);
+            else
+                k_m2m<float><<<g, 256, size_t(2) * P3 * 9 * sizeof(float), st>>>(p, lev, tr, occ, ctx->d_Wf);
         }
         CK(cudaGetLastError());
     }
     timer_mark(ctx);
     if (L >= 3) {
-        int rc = m2l_tc_run(ctx, ctx->d_Wf, occ, tocc, ctx->d_Sf);
+        int rc = m2l_tc_run(ctx, ctx->d_Wf, t64 ? ctx->d_W : nullptr, occ, tocc, ctx->d_Sf, t64 ? ctx->d_S : nullptr);
         if (rc) return rc;
     }
     timer_mark(ctx);
     if (L >= 4) {
-        const size_t sm6 = size_t(2) * P3 * 6 * sizeof(float);
         for (int lev = 3; lev <= L - 1; ++lev) {
             ++ctx->launches;
-            k_l2l<float><<<unsigned(int64_t(1) << (3 * lev)), 256, sm6, st>>>(p, lev, tr, tocc, ctx->d_Sf);
+            const unsigned g = unsigned(int64_t(1) << (3 * lev));
+            if (t64)
+                k_l2l<double><<<g, 256, size_t(2) * P3 * 6 * sizeof(double), st>>>(p, lev, tr, tocc, ctx->d_S);
+            else
+                k_l2l<float><<<g, 256, size_t(2) * P3 * 6 * sizeof(float), st>>>(p, lev, tr, tocc, ctx->d_Sf);
         }
         CK(cudaGetLastError());
+    }
+    if (t64 && L >= 3) {
+        // FP32 copy of the leaf level for the near kernels that read FP32 local values
+        const int64_t n = nl * P3 * 6;
+        ++ctx->launches;
+        k_leaf_s_to_f32<<<unsigned(std::min<int64_t>((n + 255) / 256, 4096)), 256, 0, st>>>(
+            n, ctx->d_S + cell_base(L - 1) * P3 * 6, ctx->d_Sf + cell_base(L - 1) * P3 * 6);
     }
     timer_mark(ctx);
     {

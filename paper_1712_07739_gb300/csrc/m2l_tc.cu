@@ -256,7 +256,8 @@ template <bool TF32>
 __global__ void __launch_bounds__(192, 1)
     k_m2l_tc(const __grid_constant__ M2LParams P, const int4 *__restrict__ seg, int n_seg,
              const int *__restrict__ list, const int *__restrict__ occ, const int *__restrict__ tocc,
-             const TreeBox *__restrict__ box, float *__restrict__ S, int *__restrict__ status, int stages, int groups) {
+             const TreeBox *__restrict__ box, float *__restrict__ S, double *__restrict__ S64,
+             int *__restrict__ status, int stages, int groups) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int stageB = P.ncta * 128;
@@ -465,10 +466,14 @@ __global__ void __launch_bounds__(192, 1)
         float sc = float(double(n) / box->H) * float(double(n) / box->H);
         if (P.wmax) sc *= P.inv_op_scale / wscale_of(P.wmax[level]);
         float *dst = S + g * int64_t(P.nvalid);
+        double *dst64 = S64 ? S64 + g * int64_t(P.nvalid) : nullptr;  // FP64 local values, when kept
         if (ok && !any_src) {
             // no occupied source anywhere in the interaction list: zero local values
             if (valid)
-                for (int col = group * P.ncta; col < min(P.nvalid, (group + 1) * P.ncta); ++col) dst[col] = 0.f;
+                for (int col = group * P.ncta; col < min(P.nvalid, (group + 1) * P.ncta); ++col) {
+                    if (dst64) dst64[col] = 0.0;
+                    else dst[col] = 0.f;
+                }
         } else if (ok) {
             for (int jj = 0; jj < 3; ++jj)
                 for (int c0 = 0; c0 < P.nsub; c0 += 16) {
@@ -477,7 +482,10 @@ __global__ void __launch_bounds__(192, 1)
                     const int col = group * P.ncta + jj * P.nsub + c0;
                     if (valid)
                         for (int i = 0; i < 16; ++i)
-                            if (col + i < P.nvalid) dst[col + i] = v[i] * sc;
+                            if (col + i < P.nvalid) {
+                                if (dst64) dst64[col + i] = double(v[i]) * double(sc);
+                                else dst[col + i] = v[i] * sc;
+                            }
                 }
         }
     }
@@ -539,8 +547,8 @@ __global__ void k_build_ops(int p, int lat_n, int Np, int Kp, const double *__re
 }
 
 // W (FP32, [cell][p^3 * 9]) -> parity-split BF16 hi / lo, [class][mz][my][mx][Kp] per level
-template <typename E>
-__global__ void k_pack_w(int level, int P3, int Kp, const float *__restrict__ W, const int *__restrict__ occ,
+template <typename E, typename TW>
+__global__ void k_pack_w(int level, int P3, int Kp, const TW *__restrict__ W, const int *__restrict__ occ,
                          const unsigned *__restrict__ wmax, E *__restrict__ hi, E *__restrict__ lo) {
     const int n = 1 << level, m = n / 2;
     const double s = wmax ? double(wscale_of(wmax[level])) : 1.0;
@@ -554,9 +562,9 @@ __global__ void k_pack_w(int level, int P3, int Kp, const float *__restrict__ W,
         const int cls = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
         const int64_t dst = ((((int64_t(cls) * m + z / 2) * m + y / 2) * m + x / 2) * Kp) + k;
         const int64_t g = cell_base_d(level) + lin;
-        float v = 0.f;
-        if (k < 9 * P3 && occ[g] > 0) v = W[g * 9 * P3 + k];
-        const double vs = s * double(v);
+        double v = 0.0;
+        if (k < 9 * P3 && occ[g] > 0) v = double(W[g * 9 * P3 + k]);
+        const double vs = s * v;
         const E h = to_elem<E>(vs);
         hi[dst] = h;
         if (lo) lo[dst] = to_elem<E>(vs - elem_value(h));
@@ -565,7 +573,8 @@ __global__ void k_pack_w(int level, int P3, int Kp, const float *__restrict__ W,
 
 // largest |W| over the occupied cells of one level (non-negative floats order
 // like their bit patterns)
-__global__ void k_wmax(int level, int P3, const float *__restrict__ W, const int *__restrict__ occ,
+template <typename TW>
+__global__ void k_wmax(int level, int P3, const TW *__restrict__ W, const int *__restrict__ occ,
                        unsigned *__restrict__ wmax) {
     const int64_t cells = int64_t(1) << (3 * level), base = cell_base_d(level);
     const int64_t total = cells * 9 * P3;
@@ -573,7 +582,7 @@ __global__ void k_wmax(int level, int P3, const float *__restrict__ W, const int
     for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
          idx += int64_t(gridDim.x) * blockDim.x) {
         const int64_t g = base + idx / (9 * P3);
-        if (occ[g] > 0) mx = fmaxf(mx, fabsf(W[base * 9 * P3 + idx]));
+        if (occ[g] > 0) mx = fmaxf(mx, fabsf(float(W[base * 9 * P3 + idx])));
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(wmax + level, __float_as_uint(mx));
@@ -870,7 +879,8 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
     return GBFMM_OK;
 }
 
-int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc, float *Sf) {
+int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *occ, const int *tocc, float *Sf,
+               double *S64) {
     TcPlan &T = ctx->tc;
     const int L = ctx->L, p = ctx->opt.p, P3 = p * p * p;
     static M2LParams prm;  // large: build on the heap-like static, copied by value at launch
@@ -879,21 +889,34 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     for (int l = 2; l < L; ++l) {
         const int64_t el = (int64_t(1) << (3 * l)) * T.Kp;
         void *whi = (char *)T.Whi + T.wofs[l] * T.esz, *wlo = (char *)T.Wlo + T.wofs[l] * T.esz;
+        const unsigned gb = nblk(el, 256);
         if (T.tf32) {
             ++ctx->launches;
-            k_pack_w<float><<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, nullptr, (float *)whi,
-                                                                    (float *)nullptr);
+            if (W64)
+                k_pack_w<float><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, W64, occ, nullptr, (float *)whi, (float *)nullptr);
+            else
+                k_pack_w<float><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, nullptr, (float *)whi, (float *)nullptr);
         } else if (T.fp16) {
             const int64_t vals = (int64_t(1) << (3 * l)) * 9 * P3;
+            const unsigned gm = unsigned(std::min<int64_t>(nblk(vals, 256), 4 * 152));
+            __half *lo = T.split ? (__half *)wlo : nullptr;
             ctx->launches += 2;
-            k_wmax<<<unsigned(std::min<int64_t>(nblk(vals, 256), 4 * 152)), 256, 0, ctx->stream>>>(l, P3, Wf, occ,
-                                                                                                   T.d_wmax);
-            k_pack_w<__half><<<nblk(el, 256), 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, T.d_wmax, (__half *)whi,
-                                                                     T.split ? (__half *)wlo : nullptr);
+            if (W64) {
+                k_wmax<<<gm, 256, 0, ctx->stream>>>(l, P3, W64, occ, T.d_wmax);
+                k_pack_w<__half><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, W64, occ, T.d_wmax, (__half *)whi, lo);
+            } else {
+                k_wmax<<<gm, 256, 0, ctx->stream>>>(l, P3, Wf, occ, T.d_wmax);
+                k_pack_w<__half><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, T.d_wmax, (__half *)whi, lo);
+            }
         } else {
+            __nv_bfloat16 *lo = T.split ? (__nv_bfloat16 *)wlo : nullptr;
             ++ctx->launches;
-            k_pack_w<__nv_bfloat16><<<nblk(el, 256), 256, 0, ctx->stream>>>(
-                l, P3, T.Kp, Wf, occ, nullptr, (__nv_bfloat16 *)whi, T.split ? (__nv_bfloat16 *)wlo : nullptr);
+            if (W64)
+                k_pack_w<__nv_bfloat16><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, W64, occ, nullptr,
+                                                                     (__nv_bfloat16 *)whi, lo);
+            else
+                k_pack_w<__nv_bfloat16><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, nullptr,
+                                                                     (__nv_bfloat16 *)whi, lo);
         }
         prm.wofs[l] = T.wofs[l] * T.esz;
     }
@@ -938,11 +961,11 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc,
     if (T.tf32) {
         CK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         k_m2l_tc<true><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
-                                                             Sf, T.d_status, stages, T.groups);
+                                                             Sf, S64, T.d_status, stages, T.groups);
     } else {
         CK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         k_m2l_tc<false><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
-                                                              Sf, T.d_status, stages, T.groups);
+                                                              Sf, S64, T.d_status, stages, T.groups);
     }
     CK(cudaGetLastError());
     return GBFMM_OK;

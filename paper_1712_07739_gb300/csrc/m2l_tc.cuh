@@ -34,6 +34,8 @@ struct TcPlan {
 
 int m2l_tc_setup(gbfmm_ctx *ctx);    // operators (per medium and p)
 int m2l_tc_prepare(gbfmm_ctx *ctx);  // per tree
-int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const int *occ, const int *tocc, float *Sf);
+// W64 / S64 non-null: FP64 multipole values in, FP64 local values out (GBFMM_MIXED_F64T)
+int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *occ, const int *tocc, float *Sf,
+               double *S64);
 void m2l_tc_free(gbfmm_ctx *ctx);
 int m2l_tc_status(gbfmm_ctx *ctx, int *out);

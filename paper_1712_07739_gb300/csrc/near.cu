@@ -531,17 +531,37 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
 __global__ void k_near_combine(int p, int L, int64_t N, const TreeBox *__restrict__ box,
                                const int *__restrict__ sstart, const int *__restrict__ pleaf,
                                const double *__restrict__ xt, const float *__restrict__ S,
-                               const double *__restrict__ part, double *__restrict__ sig) {
+                               const double *__restrict__ S64, const double *__restrict__ part,
+                               double *__restrict__ sig) {
     const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (t >= N) return;
     const int nlv = 1 << (L - 1);
     const int64_t leaf = pleaf[t];
     int cx, cy, cz;
     cell_xyz3(leaf, nlv, cx, cy, cz);
-    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (L >= 3) {
+    double out[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (L >= 3 && S64) {
+        // FP64 local values (GBFMM_MIXED_F64T): interpolate in FP64
         const int P3 = p * p * p;
         const double h = box->H / nlv, ih = double(nlv) / box->H;
+        double bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
+        lagrange_1d<double>(p, (xt[3 * t] - (box->origin[0] + cx * h)) * ih, bx);
+        lagrange_1d<double>(p, (xt[3 * t + 1] - (box->origin[1] + cy * h)) * ih, by);
+        lagrange_1d<double>(p, (xt[3 * t + 2] - (box->origin[2] + cz * h)) * ih, bz);
+        const double *Sl = S64 + (cell_base_d(L - 1) + leaf) * int64_t(P3) * 6;
+        for (int lz = 0; lz < p; ++lz)
+            for (int ly = 0; ly < p; ++ly) {
+                const double wyz = by[ly] * bz[lz];
+                for (int lx = 0; lx < p; ++lx) {
+                    const double w = bx[lx] * wyz;
+                    const double *s6 = Sl + ((lz * p + ly) * p + lx) * 6;
+                    for (int ab = 0; ab < 6; ++ab) out[ab] += w * s6[ab];
+                }
+            }
+    } else if (L >= 3) {
+        const int P3 = p * p * p;
+        const double h = box->H / nlv, ih = double(nlv) / box->H;
+        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
         lagrange_1d<float>(p, float((xt[3 * t] - (box->origin[0] + cx * h)) * ih), bx);
         lagrange_1d<float>(p, float((xt[3 * t + 1] - (box->origin[1] + cy * h)) * ih), by);
@@ -556,9 +576,8 @@ __global__ void k_near_combine(int p, int L, int64_t N, const TreeBox *__restric
                     for (int ab = 0; ab < 6; ++ab) acc[ab] += w * __ldg(s6 + ab);
                 }
             }
+        for (int ab = 0; ab < 6; ++ab) out[ab] = double(acc[ab]);
     }
-    double out[6];
-    for (int ab = 0; ab < 6; ++ab) out[ab] = double(acc[ab]);
     for (int s = 0; s < kSlots; ++s) {
         const int nb = s == 27 ? 13 : s;
         const int bx = cx + nb % 3 - 1, by = cy + (nb / 3) % 3 - 1, bz = cz + nb / 9 - 1;
@@ -1099,8 +1118,9 @@ static int near_run_sym(gbfmm_ctx *ctx, double *sig) {
                                                                    ctx->d_Pf, ctx->d_sid, W.part, N, W.psorted,
                                                                    W.pmisc + 128);
     }
+    const double *S64 = ctx->opt.precision == GBFMM_MIXED_F64T ? ctx->d_S : nullptr;
     k_near_combine<<<nblk(N, 256), 256, 0, st>>>(ctx->opt.p, ctx->L, N, ctx->d_box, ctx->d_leaf_start, ctx->d_pleaf,
-                                                 ctx->d_y, ctx->d_Sf, W.part, sig);
+                                                 ctx->d_y, ctx->d_Sf, S64, W.part, sig);
     CK(cudaGetLastError());
     return GBFMM_OK;
 }

@@ -68,6 +68,9 @@ def _forces(nodes, segs, b, wl, **over):
                  id="p7split"),
     pytest.param("p=8, FP16 with residual passes on the nearest offsets", {"p": 8, "m2l_split": 5}, 3e-4,
                  id="p8split"),
+    pytest.param("p=7, FP64 interpolation stages", {"p": 7, "precision": "mixed_f64t"}, 3e-4, id="p7f64t"),
+    pytest.param("p=8, FP64 interpolation stages, FP16 with residual passes on the nearest offsets",
+                 {"p": 8, "precision": "mixed_f64t", "m2l_split": 5}, 3e-4, id="p8f64t"),
 ])
 def test_full_size_sampled_nodes_match_direct_sum(c3_case, label, over, tol):
     nodes, segs, b, wl, ids, Fo = c3_case
@@ -117,8 +120,8 @@ def test_full_size_repeatable_and_linear_in_b():
 GOLDEN_Q = os.path.join(ROOT, "tests", "golden", "c3q_sampled_forces.json")
 
 
-@pytest.mark.parametrize("p", [6, 8])
-def test_quarter_size_error_budget(p):
+@pytest.mark.parametrize("p,prec", [(6, "mixed"), (8, "mixed"), (8, "mixed_f64t")])
+def test_quarter_size_error_budget(p, prec):
     """250,000-segment slab network, 32 nodes against the direct sum (stored
     by tests/golden/make_c3q_sampled_forces.py): the FP64 pass measures the
     interpolation error of order p, the mixed pass adds the precision error."""
@@ -131,10 +134,10 @@ def test_quarter_size_error_budget(p):
     assert np.allclose(nodes[ids], np.array(gold["node_xyz"]), rtol=0, atol=1e-12)
     Fo = np.array(gold["forces"])
     Fd = _forces(nodes, segs, b, wl, p=p, precision="fp64", circle_q=32)
-    Fm = _forces(nodes, segs, b, wl, p=p)
+    Fm = _forces(nodes, segs, b, wl, p=p, precision=prec)
     e_d = np.linalg.norm(Fd[ids] - Fo) / np.linalg.norm(Fo)
     e_m = np.linalg.norm(Fm[ids] - Fo) / np.linalg.norm(Fo)
     e_md = oracle.rel_l2(Fm, Fd)
-    print(f"250k segments, p={p}: FP64 pass vs direct sum {e_d:.3e}, mixed vs direct sum {e_m:.3e}, "
-          f"mixed vs FP64 pass (all nodes) {e_md:.3e}")
+    print(f"250k segments, p={p}, {prec}: FP64 pass vs direct sum {e_d:.3e}, {prec} vs direct sum {e_m:.3e}, "
+          f"{prec} vs FP64 pass (all nodes) {e_md:.3e}")
     assert e_d < 1e-3 and e_m < 1e-3

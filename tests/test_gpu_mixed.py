@@ -85,6 +85,17 @@ def test_mixed_rotated_crystal_general_rule():
     assert err <= TOL_MIXED
 
 
+def test_mixed_fp64_interpolation_stages():
+    """GBFMM_MIXED_F64T: P2M, M2M, L2L and L2P in FP64 around the tensor-core
+    M2L and the FP32 near field, against Algorithm 2 at p = 6."""
+    nodes, segs, b = synth.polygon_loops(n_segs=800, n_loops=25, seed=21)
+    _, F = _run(nodes, segs, b, ISO_C, p=6, levels=4, precision="mixed_f64t")
+    Fo = _oracle_forces(ISO, nodes, segs, b, 6, 4)
+    err = oracle.rel_l2(F, Fo)
+    print("mixed with FP64 interpolation stages, p=6 L=4 vs Algorithm 2:", err)
+    assert err <= TOL_MIXED
+
+
 def test_mixed_cubic_circle():
     nodes, segs, b = synth.polygon_loops(n_segs=400, n_loops=12, seed=23)
     C6 = synth.cubic_voigt()
