@@ -65,9 +65,28 @@ def is_cubic_aligned(C6):
 
 
 def near_pair_flops(precision, h_mode, q, cubic=False):
+    """FLOP per ordered near pair of the one-sided evaluation."""
     if h_mode == "iso":
         return FLOP_PER_NEAR_PAIR[(precision, h_mode)]
     return 193 * q + 306 if cubic else 450 * q + 236
+
+
+def near_flops(wl, work):
+    """Algorithmic FLOP of the near field (+ L2P) of one pass and the kernel
+    that does it.  With the unit-circle h the mixed pass evaluates h once per
+    unordered pair (h is odd) and contracts it for both directions: per
+    ordered pair half an h evaluation (cubic rule 193 Q + 77, general rule
+    450 Q + 20) plus one contraction (229)."""
+    p, q = wl["p"], wl.get("circle_q", 64)
+    cubic = is_cubic_aligned(wl["C"]())
+    l2p = work["points"] * (12 * p ** 3 + 30 * p)
+    if wl["precision"] == "fp64":
+        return work["near_pairs"] * near_pair_flops("fp64", wl["h_mode"], q, cubic) + l2p, "k_leaf_eval_f64"
+    if wl["h_mode"] == "circle":
+        h = 193 * q + 77 if cubic else 450 * q + 20
+        return work["near_pairs"] * (h / 2.0 + 229) + l2p, "k_near_sym"
+    name = "k_near_mlp" if wl["h_mode"] == "mlp" else "k_near_mixed"
+    return work["near_pairs"] * near_pair_flops("mixed", wl["h_mode"], q, cubic) + l2p, name
 
 
 # DRAM bytes per target point of one k_near_sym launch (cubic rule, Q = 20), from
@@ -348,8 +367,8 @@ def run_batch(args, wl):
     work = f.work_counts()
     p = wl["p"]
     if st[4] >= st[2]:
-        flops = work["near_pairs"] * near_pair_flops("mixed", wl["h_mode"], wl.get("circle_q", 64))
-        roof = {"bound": "alu", "kernel": "k_near_mixed (largest network alone)", "achieved": flops / (st[4] / 1e3) / 1e12,
+        flops, kname = near_flops(wl, work)
+        roof = {"bound": "alu", "kernel": kname + " (largest network alone)", "achieved": flops / (st[4] / 1e3) / 1e12,
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "peak_source": "152 SM x 128 lanes x 2 x 2.07 GHz"}
     else:
         pk, src = measured_bf16_peak()
@@ -480,12 +499,10 @@ def run_ours(args, wl):
     peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
     traffic, traffic_src = None, None
     if leaf_ms >= m2l_ms:
-        flops = (work["near_pairs"] * near_pair_flops(wl["precision"], wl["h_mode"], wl.get("circle_q", 64),
-                                                      is_cubic_aligned(wl["C"]()))
-                 + work["points"] * (12 * p ** 3 + 30 * p))
+        flops, kname = near_flops(wl, work)
         achieved = flops / (leaf_ms / 1e3) / 1e12
-        sym = not fp64 and wl["h_mode"] == "circle"
-        dom = ("k_leaf_eval_f64" if fp64 else ("k_near_sym" if sym else "k_near_mixed")) + " (L2P + near-field P2P)"
+        sym = kname == "k_near_sym"
+        dom = kname + " (L2P + near-field P2P)"
         bound, src = "alu", ("FP64 1.25 TFLOP/s nominal (recipe)" if fp64 else "152 SM x 128 lanes x 2 x 2.07 GHz")
         if sym and wl.get("circle_q") == 20:
             traffic = NEAR_SYM_DRAM_BYTES_PER_POINT * work["points"]
@@ -501,7 +518,8 @@ def run_ours(args, wl):
             peak, src = measured_bf16_peak()
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": src,
-                "work": "algorithmic: near pairs x FLOP/pair (+ L2P), or M2L cell pairs x 2*54*p^6"}
+                "work": "algorithmic: near pairs x FLOP/pair (h once per unordered pair when h is the unit-circle "
+                        "rule) + L2P, or M2L cell pairs x 2*54*p^6"}
 
     if rank == 0:
         cpu = None
