@@ -10,16 +10,20 @@
 // sub-grids.
 //
 // Tiles.  The cells of a (level, class) that hold targets are listed in
-// Morton order of their sub-grid position; 128 consecutive ones form a tile.
-// The M2L of a tile is
+// Morton order of their sub-grid position; 128 consecutive ones form a tile,
+// and a CTA takes TPC = 3 consecutive tiles and one group of nsub operator
+// rows.  The M2L of a tile is
 //     S[cell, n] = (2^l / H)^2  sum_o  sum_k  W_c'[cell + s_o, k] T_o[n, k]
 // with k = (node m, component wr) and n = (node l, stress component ab):
-// one GEMM of M = 128 cells, N = 6 p^3 and K = (active offsets) x 9 p^3,
-// accumulated in tensor memory.  The A tile (the 128 shifted multipole rows)
-// is gathered by cp.async, one row per thread, into the swizzled layout the
-// MMA reads (sources outside the sub-grid or without segments read as
-// zeros); the B tile (rows of the operator T_o) comes by TMA.  Offsets whose
-// 128 source cells are all empty are skipped.
+// per tile one GEMM of M = 128 cells, N = nsub and K = (active offsets) x
+// 9 p^3, accumulated in tensor memory (TPC accumulators of nsub columns).
+// Each pipeline stage holds the three tiles' multipole rows (gathered by
+// cp.async, one row per thread and tile, into the swizzled layout the MMA
+// reads; sources outside the sub-grid or without segments read as zeros)
+// and one block of operator rows (TMA) that all three tiles use: a stage
+// moves 66 KB for 7.1 MFLOP, mostly rows of the level's multipole table,
+// which stay in L2 far better than the 1.6 GB of operators.  Offsets whose
+// sources are all empty are skipped.
 //
 // Precision: BF16 operands (hi); for the offsets nearest to the target
 // (max |o_i| = 2, the largest far-field terms) the residuals W_lo = W - hi(W)
@@ -67,7 +71,7 @@ struct M2LParams {
     CUtensorMap tmTlo;                // T residual: (Kp, Np, n_lo)
     int kb;         // K blocks of 64
     int nsub;       // N per MMA (multiple of 16, <= 256)
-    int ncta;       // 3 * nsub
+    int ncta;       // operator rows per CTA (= nsub)
     int nvalid;     // 6 p^3
     int tmem_cols;  // power of two >= ncta
     int split;      // residual passes on the near offsets
@@ -89,7 +93,9 @@ __device__ __forceinline__ float wscale_of(unsigned bits) {
     return ldexpf(1.f, 13 - e);
 }
 
-constexpr int kStageA = 128 * 64 * 2;  // 16 KB
+constexpr int TPC = 3;                        // tiles of 128 cells per CTA, sharing each operator stage
+constexpr int kTileA = 128 * 128;             // one tile's multipole rows per stage: 16 KB
+constexpr int kStageA = TPC * kTileA;         // 48 KB
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -266,8 +272,8 @@ __global__ void __launch_bounds__(192, 1)
     // bars[0..stages): full, [stages..2 stages): empty, [2 stages]: accumulator ready
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 1);
 
-    __shared__ int s_level, s_cls, s_rows, s_nrow, s_stop;
-    __shared__ short s_tgt[128][3];    // sub-grid positions of the tile's target cells
+    __shared__ int s_level, s_cls, s_rows, s_nrow, s_stop;  // s_rows, s_nrow: first list entry, cells of the CTA
+    __shared__ short s_tgt[TPC][128][3];  // sub-grid positions of the tiles' target cells
     __shared__ uint32_t s_active[6];   // offsets with at least one occupied source cell
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int tile = blockIdx.x / groups, group = blockIdx.x % groups;
@@ -277,12 +283,12 @@ __global__ void __launch_bounds__(192, 1)
         if (tile < seg[n_seg].z)
             for (int si = 0; si < n_seg; ++si) {
                 const int4 sg = seg[si];
-                const int nt = (sg.y + 127) / 128;
+                const int nt = ((sg.y + 127) / 128 + TPC - 1) / TPC;
                 if (tile >= sg.z && tile < sg.z + nt) {
                     s_level = si / 8 + 2;
                     s_cls = si % 8;
-                    s_rows = sg.x + 128 * (tile - sg.z);  // first list entry of the tile
-                    s_nrow = min(128, sg.y - 128 * (tile - sg.z));
+                    s_rows = sg.x + 128 * TPC * (tile - sg.z);  // first list entry of the CTA's tiles
+                    s_nrow = min(128 * TPC, sg.y - 128 * TPC * (tile - sg.z));
                     break;
                 }
             }
@@ -293,24 +299,25 @@ __global__ void __launch_bounds__(192, 1)
     const int level = s_level, cls = s_cls, nrow = s_nrow;
     const int m = 1 << (level - 1), n = 1 << level;
     const int64_t cbase = cell_base_d(level);
-    if (threadIdx.x < 128) {
-        int sx = -1024, sy = -1024, sz = -1024;  // rows past the tile's cells: far outside the sub-grid
-        if (threadIdx.x < nrow) {
-            const uint32_t code = uint32_t(list[s_rows + threadIdx.x]);
+    for (int r = threadIdx.x; r < 128 * TPC; r += blockDim.x) {
+        int sx = -1024, sy = -1024, sz = -1024;  // rows past the CTA's cells: far outside the sub-grid
+        if (r < nrow) {
+            const uint32_t code = uint32_t(list[s_rows + r]);
             sx = int(morton_compact(code)), sy = int(morton_compact(code >> 1)), sz = int(morton_compact(code >> 2));
         }
-        s_tgt[threadIdx.x][0] = short(sx), s_tgt[threadIdx.x][1] = short(sy), s_tgt[threadIdx.x][2] = short(sz);
+        s_tgt[r / 128][r % 128][0] = short(sx), s_tgt[r / 128][r % 128][1] = short(sy);
+        s_tgt[r / 128][r % 128][2] = short(sz);
     }
     __syncthreads();
 
-    // active offsets: lane r of warp w checks tile rows 4r .. 4r + 3
+    // active offsets: lane r of warp w checks rows 4r .. 4r + 3 of every tile
     for (int oi = warp; oi < 189; oi += 6) {
         const OffsetEntry e = c_offs[cls][oi];
         const int ccx = e.cls & 1, ccy = (e.cls >> 1) & 1, ccz = e.cls >> 2;
         bool hit = false;
-        for (int q = 0; q < 4; ++q) {
-            const int row = 4 * lane + q;
-            const int px = s_tgt[row][0] + e.sx, py = s_tgt[row][1] + e.sy, pz = s_tgt[row][2] + e.sz;
+        for (int q = 0; q < 4 * TPC; ++q) {
+            const int t = q / 4, row = 4 * lane + q % 4;
+            const int px = s_tgt[t][row][0] + e.sx, py = s_tgt[t][row][1] + e.sy, pz = s_tgt[t][row][2] + e.sz;
             if (px >= 0 && py >= 0 && pz >= 0 && px < m && py < m && pz < m) {
                 const int64_t g = cbase + (int64_t(2 * pz + ccz) * n + (2 * py + ccy)) * n + (2 * px + ccx);
                 hit |= occ[g] > 0;
@@ -359,10 +366,7 @@ __global__ void __launch_bounds__(192, 1)
                     const uint32_t fb = full0 + 8 * s;
                     mbar_expect_tx(fb, uint32_t(stageB));
                     if (P.drop_first && it == 0) continue;  // the MMA warp's wait on this stage runs out
-                    const uint32_t a = smem0 + s * stage_bytes;
-                    for (int j = 0; j < 3; ++j)
-                        tma_load_3d(a + kStageA + j * P.nsub * 128, tb, kb * P.kstep, group * P.ncta + j * P.nsub,
-                                    tidx, fb);
+                    tma_load_3d(smem0 + s * stage_bytes + kStageA, tb, kb * P.kstep, group * P.ncta, tidx, fb);
                 }
             }
         }
@@ -386,10 +390,10 @@ __global__ void __launch_bounds__(192, 1)
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t a = smem0 + s * stage_bytes;
                     for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ad = sw128_desc(a + kk * 32);
-                        for (int j = 0; j < 3; ++j) {
-                            const uint64_t bd = sw128_desc(a + kStageA + j * P.nsub * 128 + kk * 32);
-                            mma_issue<TF32>(tmem + j * P.nsub, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                        const uint64_t bd = sw128_desc(a + kStageA + kk * 32);
+                        for (int t = 0; t < TPC; ++t) {
+                            const uint64_t ad = sw128_desc(a + t * kTileA + kk * 32);
+                            mma_issue<TF32>(tmem + t * P.nsub, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
                         }
                     }
                     mma_commit(empty0 + 8 * s);
@@ -410,18 +414,24 @@ __global__ void __launch_bounds__(192, 1)
             for (int oi = 0; oi < 189 && ok; ++oi) {
                 if (!((s_active[oi / 32] >> (oi % 32)) & 1u)) continue;
                 const OffsetEntry e = c_offs[cls][oi];
-                const int px = s_tgt[row][0] + e.sx, py = s_tgt[row][1] + e.sy, pz = s_tgt[row][2] + e.sz;
-                bool have = px >= 0 && py >= 0 && pz >= 0 && px < m && py < m && pz < m;
-                int64_t srow = 0;
-                if (have) {
-                    const int ccx = e.cls & 1, ccy = (e.cls >> 1) & 1, ccz = e.cls >> 2;
-                    have = occ[cbase + (int64_t(2 * pz + ccz) * n + (2 * py + ccy)) * n + (2 * px + ccx)] > 0;
-                    srow = ((int64_t(e.cls) * m + pz) * m + py) * m + px;
+                int64_t srow[TPC];
+                uint32_t nb[TPC];
+#pragma unroll
+                for (int t = 0; t < TPC; ++t) {
+                    const int px = s_tgt[t][row][0] + e.sx, py = s_tgt[t][row][1] + e.sy,
+                              pz = s_tgt[t][row][2] + e.sz;
+                    bool have = px >= 0 && py >= 0 && pz >= 0 && px < m && py < m && pz < m;
+                    srow[t] = 0;
+                    if (have) {
+                        const int ccx = e.cls & 1, ccy = (e.cls >> 1) & 1, ccz = e.cls >> 2;
+                        have = occ[cbase + (int64_t(2 * pz + ccz) * n + (2 * py + ccy)) * n + (2 * px + ccx)] > 0;
+                        srow[t] = ((int64_t(e.cls) * m + pz) * m + py) * m + px;
+                    }
+                    nb[t] = have ? 16u : 0u;
                 }
-                const uint32_t nb = have ? 16u : 0u;
                 const int np = passes_of(e, P.split);
                 for (int pass = 0; pass < np && ok; ++pass) {
-                    const uint8_t *src = ((pass == 1) ? P.Wlo : P.Whi) + P.wofs[level] + srow * P.row_bytes;
+                    const uint8_t *wb = ((pass == 1) ? P.Wlo : P.Whi) + P.wofs[level];
                     for (int kb = 0; kb < P.kb; ++kb, ++it) {
                         const int s = it % stages;
                         const uint32_t ph = (it / stages) & 1;
@@ -429,10 +439,14 @@ __global__ void __launch_bounds__(192, 1)
                             ok = false;
                             break;
                         }
-                        const uint32_t dst = smem0 + s * stage_bytes + rowdst;
-                        const uint8_t *sk = src + kb * 128;
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) cp_async16(dst + ((c ^ (row & 7)) << 4), sk + 16 * c, nb);
+                        for (int t = 0; t < TPC; ++t) {
+                            const uint32_t dst = smem0 + s * stage_bytes + t * kTileA + rowdst;
+                            const uint8_t *sk = wb + srow[t] * P.row_bytes + kb * 128;
+#pragma unroll
+                            for (int c = 0; c < 8; ++c)
+                                cp_async16(dst + ((c ^ (row & 7)) << 4), sk + 16 * c, nb[t]);
+                        }
                         cp_async_commit();
                         if (it - done >= lag) {
                             // the copies of stage `done` are complete: make them visible to the
@@ -456,30 +470,29 @@ __global__ void __launch_bounds__(192, 1)
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int q = warp % 4;
         const int trow = q * 32 + lane;  // TMEM lane = tile row
-        bool valid = ok && trow < nrow;
-        int64_t g = 0;
-        if (valid) {
-            const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
-            g = cbase + (int64_t(2 * s_tgt[trow][2] + cz) * n + (2 * s_tgt[trow][1] + cy)) * n +
-                (2 * s_tgt[trow][0] + cx);
-        }
         float sc = float(double(n) / box->H) * float(double(n) / box->H);
         if (P.wmax) sc *= P.inv_op_scale / wscale_of(P.wmax[level]);
-        float *dst = S + g * int64_t(P.nvalid);
-        double *dst64 = S64 ? S64 + g * int64_t(P.nvalid) : nullptr;  // FP64 local values, when kept
-        if (ok && !any_src) {
-            // no occupied source anywhere in the interaction list: zero local values
+        const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
+        for (int t = 0; t < TPC; ++t) {
+            const bool valid = ok && t * 128 + trow < nrow;
+            int64_t g = 0;
             if (valid)
-                for (int col = group * P.ncta; col < min(P.nvalid, (group + 1) * P.ncta); ++col) {
-                    if (dst64) dst64[col] = 0.0;
-                    else dst[col] = 0.f;
-                }
-        } else if (ok) {
-            for (int jj = 0; jj < 3; ++jj)
+                g = cbase + (int64_t(2 * s_tgt[t][trow][2] + cz) * n + (2 * s_tgt[t][trow][1] + cy)) * n +
+                    (2 * s_tgt[t][trow][0] + cx);
+            float *dst = S + g * int64_t(P.nvalid);
+            double *dst64 = S64 ? S64 + g * int64_t(P.nvalid) : nullptr;  // FP64 local values, when kept
+            if (ok && !any_src) {
+                // no occupied source anywhere in the interaction list: zero local values
+                if (valid)
+                    for (int col = group * P.ncta; col < min(P.nvalid, (group + 1) * P.ncta); ++col) {
+                        if (dst64) dst64[col] = 0.0;
+                        else dst[col] = 0.f;
+                    }
+            } else if (ok) {
                 for (int c0 = 0; c0 < P.nsub; c0 += 16) {
                     float v[16];
-                    tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t(jj * P.nsub + c0), v);
-                    const int col = group * P.ncta + jj * P.nsub + c0;
+                    tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t(t * P.nsub + c0), v);
+                    const int col = group * P.ncta + c0;
                     if (valid)
                         for (int i = 0; i < 16; ++i)
                             if (col + i < P.nvalid) {
@@ -487,6 +500,7 @@ __global__ void __launch_bounds__(192, 1)
                                 else dst[col + i] = v[i] * sc;
                             }
                 }
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -659,7 +673,7 @@ __global__ void k_mb_list(int n, int L, const int *__restrict__ flags, const int
     }
 }
 
-// segment table: {first list entry, cells, first tile}; seg[n_seg].z = tiles
+// segment table: {first list entry, cells, first CTA}; seg[n_seg].z = CTAs (per operator group)
 __global__ void k_seg_table(int L, const int *__restrict__ pos, int4 *__restrict__ seg) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int tiles = 0, si = 0;
@@ -669,7 +683,7 @@ __global__ void k_seg_table(int L, const int *__restrict__ pos, int4 *__restrict
             const int64_t s0 = slot_base(l) + c * m3;
             const int first = pos[s0], cnt = pos[s0 + m3] - first;
             seg[si] = make_int4(first, cnt, tiles, 0);
-            tiles += (cnt + 127) / 128;
+            tiles += ((cnt + 127) / 128 + TPC - 1) / TPC;  // CTAs: TPC tiles each
         }
     }
     seg[si] = make_int4(0, 0, tiles, 0);
@@ -703,23 +717,24 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     T.fp16 = (ctx->opt.m2l_split == 4 || ctx->opt.m2l_split == 5) ? 1 : 0;
     T.esz = T.tf32 ? 4 : 2;
     T.Kp = ((9 * P3 + 63) / 64) * 64;
-    // N per MMA: multiple of 16, three of them per block, 3 nsub <= 512 TMEM columns
+    // N per MMA (= operator rows per CTA): multiple of 16, one accumulator per
+    // tile, TPC x nsub <= 512 TMEM columns
     const int nv = 6 * P3;
     int best = 0, best_waste = 1 << 30;
-    for (int ns = 16; ns <= 160; ns += 16) {
-        const int g = (nv + 3 * ns - 1) / (3 * ns);
-        const int waste = g * 3 * ns - nv + g * 64;  // padding plus a per-group cost
+    for (int ns = 16; ns * TPC <= 512 && ns <= 256; ns += 16) {
+        const int g = (nv + ns - 1) / ns;
+        const int waste = g * ns - nv + g * 32;  // padding plus a per-group cost (the tiles' rows are re-read)
         if (waste < best_waste) {
             best_waste = waste;
             best = ns;
         }
     }
     T.nsub = best;
-    T.ncta = 3 * best;
+    T.ncta = best;
     T.groups = (nv + T.ncta - 1) / T.ncta;
     T.Np = T.groups * T.ncta;
     T.tmem_cols = 32;
-    while (T.tmem_cols < T.ncta) T.tmem_cols *= 2;
+    while (T.tmem_cols < TPC * T.nsub) T.tmem_cols *= 2;
     // the 316 offsets, and which of them get the residual passes
     std::vector<int> off;
     std::vector<int> lo_of;
@@ -860,8 +875,8 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
     }
     // cell slots, target list and segment table (filled on the device per pass)
     const int64_t slots = slot_base(L);
-    int64_t tiles = 0;  // upper bound: every cell holds targets
-    for (int l = 2; l < L; ++l) tiles += 8 * (((int64_t(1) << (3 * (l - 1))) + 127) / 128);
+    int64_t tiles = 0;  // CTAs per operator group, upper bound: every cell holds targets
+    for (int l = 2; l < L; ++l) tiles += 8 * ((((int64_t(1) << (3 * (l - 1))) + 127) / 128 + TPC - 1) / TPC);
     if (slots > T.slot_cap) {
         void *ps[] = {T.d_flags, T.d_pos, T.d_list};
         for (void *q : ps)
@@ -953,7 +968,7 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     prm.split = T.split;
     prm.drop_first = T.inject_drop;
     T.inject_drop = 0;
-    const int stage_bytes = 128 * 64 * 2 + T.ncta * 128;
+    const int stage_bytes = kStageA + T.ncta * 128;
     // as many stages as fit in the 227 KB a block may use (barriers and alignment take ~1.2 KB)
     int stages = std::max(2, std::min(6, (225 * 1024) / stage_bytes));
     const size_t smem = size_t(stages) * stage_bytes + 1024 + (2 * stages + 2) * 8 + 64;
