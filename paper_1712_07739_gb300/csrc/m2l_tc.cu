@@ -406,28 +406,43 @@ __global__ void __launch_bounds__(192, 1)
         {
             // ---------------- multipole rows (A): gathered by cp.async into the 128-byte
             // swizzled K-major layout (16-byte piece c of row r at (c ^ (r & 7)) * 16);
-            // sources outside the sub-grid, or empty, read as zeros
+            // sources outside the sub-grid, or empty, read as zeros.  Each thread finds
+            // the source of its own row; the copies go by 8 lanes per row (lane l moves
+            // piece l % 8 of rows 4 i + l / 8 of its warp's 32), so a warp instruction
+            // reads four whole 128-byte row pieces.
             const int lag = stages - 1;
             int it = 0, done = 0;
             bool ok = true;
-            const uint32_t rowdst = uint32_t(row) * 128u;
+            const int c = lane & 7, wrow0 = row - lane;  // this warp's first tile row
             for (int oi = 0; oi < 189 && ok; ++oi) {
                 if (!((s_active[oi / 32] >> (oi % 32)) & 1u)) continue;
                 const OffsetEntry e = c_offs[cls][oi];
-                int64_t srow[TPC];
-                uint32_t nb[TPC];
+                int64_t own[TPC];
+                uint32_t own_nb = 0;
 #pragma unroll
                 for (int t = 0; t < TPC; ++t) {
                     const int px = s_tgt[t][row][0] + e.sx, py = s_tgt[t][row][1] + e.sy,
                               pz = s_tgt[t][row][2] + e.sz;
                     bool have = px >= 0 && py >= 0 && pz >= 0 && px < m && py < m && pz < m;
-                    srow[t] = 0;
+                    own[t] = 0;
                     if (have) {
                         const int ccx = e.cls & 1, ccy = (e.cls >> 1) & 1, ccz = e.cls >> 2;
                         have = occ[cbase + (int64_t(2 * pz + ccz) * n + (2 * py + ccy)) * n + (2 * px + ccx)] > 0;
-                        srow[t] = ((int64_t(e.cls) * m + pz) * m + py) * m + px;
+                        own[t] = (((int64_t(e.cls) * m + pz) * m + py) * m + px) * P.row_bytes;
                     }
-                    nb[t] = have ? 16u : 0u;
+                    own_nb |= have ? (1u << t) : 0u;
+                }
+                int64_t srcoff[8][TPC];
+                uint32_t nbm = 0;  // bit 8 t + i: row 4 i + lane / 8 of tile t has a source
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int from = 4 * i + (lane >> 3);
+                    const uint32_t f = __shfl_sync(0xffffffffu, own_nb, from);
+#pragma unroll
+                    for (int t = 0; t < TPC; ++t) {
+                        srcoff[i][t] = __shfl_sync(0xffffffffu, own[t], from);
+                        nbm |= ((f >> t) & 1u) << (8 * t + i);
+                    }
                 }
                 const int np = passes_of(e, P.split);
                 for (int pass = 0; pass < np && ok; ++pass) {
@@ -439,14 +454,16 @@ __global__ void __launch_bounds__(192, 1)
                             ok = false;
                             break;
                         }
+                        const uint32_t sbase = smem0 + s * stage_bytes;
+                        const uint8_t *wk = wb + kb * 128 + 16 * c;
 #pragma unroll
-                        for (int t = 0; t < TPC; ++t) {
-                            const uint32_t dst = smem0 + s * stage_bytes + t * kTileA + rowdst;
-                            const uint8_t *sk = wb + srow[t] * P.row_bytes + kb * 128;
+                        for (int t = 0; t < TPC; ++t)
 #pragma unroll
-                            for (int c = 0; c < 8; ++c)
-                                cp_async16(dst + ((c ^ (row & 7)) << 4), sk + 16 * c, nb[t]);
-                        }
+                            for (int i = 0; i < 8; ++i) {
+                                const int r = wrow0 + 4 * i + (lane >> 3);
+                                cp_async16(sbase + t * kTileA + r * 128 + ((c ^ (r & 7)) << 4), wk + srcoff[i][t],
+                                           ((nbm >> (8 * t + i)) & 1u) ? 16u : 0u);
+                            }
                         cp_async_commit();
                         if (it - done >= lag) {
                             // the copies of stage `done` are complete: make them visible to the
