@@ -257,6 +257,96 @@ __device__ __forceinline__ void h_cubic_f32(float cp, float c44, float D, int Q,
     }
 }
 
+// Same rule with two circle points per step in packed FP32x2 arithmetic
+// (one instruction for the two points' products); Q even.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// a b - c d
+__device__ __forceinline__ float2 fms2(float2 a, float2 b, float2 c, float2 d) { return fma2(a, b, mul2(neg2(c), d)); }
+
+__device__ __forceinline__ void h_cubic_f32x2(float cp, float c44, float D, int Q, const float4 *__restrict__ tab2,
+                                              const float T[3], float hs[18]) {
+    const float T0 = T[0], T1 = T[1], T2 = T[2];
+    int k0 = 0;
+    if (fabsf(T1) < fabsf(T0)) k0 = 1;
+    if (fabsf(T2) < fabsf(k0 == 0 ? T0 : T1)) k0 = 2;
+    float a0 = k0 == 0 ? 1.f : 0.f, a1 = k0 == 1 ? 1.f : 0.f, a2 = k0 == 2 ? 1.f : 0.f;
+    const float dd = a0 * T0 + a1 * T1 + a2 * T2;
+    a0 -= dd * T0;
+    a1 -= dd * T1;
+    a2 -= dd * T2;
+    const float nr = rsqrtf(a0 * a0 + a1 * a1 + a2 * a2);
+    const float e10 = a0 * nr, e11 = a1 * nr, e12 = a2 * nr;
+    const float e20 = T1 * e12 - T2 * e11, e21 = T2 * e10 - T0 * e12, e22 = T0 * e11 - T1 * e10;
+    const float2 cpD = f2(cp + D), cp2 = f2(cp), c442 = f2(c44);
+    // zT products folded with their constants: s_ii = z_i (2 (cp + D) T_i), s_ij = z_i (cp T_j) + z_j (cp T_i)
+    const float2 dT0 = f2(2.f * (cp + D) * T0), dT1 = f2(2.f * (cp + D) * T1), dT2 = f2(2.f * (cp + D) * T2);
+    const float2 cT0 = f2(cp * T0), cT1 = f2(cp * T1), cT2 = f2(cp * T2);
+    float2 acc[18], msum[6];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) acc[i] = f2(0.f);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) msum[i] = f2(0.f);
+    for (int k = 0; k < Q / 2; ++k) {
+        const float4 t = tab2[k];  // (cos, sin) of points 2k and 2k + 1
+        const float2 c = make_float2(t.x, t.z), sn = make_float2(t.y, t.w);
+        const float2 z0 = fma2(c, f2(e10), mul2(sn, f2(e20)));
+        const float2 z1 = fma2(c, f2(e11), mul2(sn, f2(e21)));
+        const float2 z2 = fma2(c, f2(e12), mul2(sn, f2(e22)));
+        const float2 m00 = fma2(cpD, mul2(z0, z0), c442), m11 = fma2(cpD, mul2(z1, z1), c442),
+                     m22 = fma2(cpD, mul2(z2, z2), c442);
+        const float2 cz0 = mul2(cp2, z0), cz1 = mul2(cp2, z1);
+        const float2 m01 = mul2(cz0, z1), m02 = mul2(cz0, z2), m12 = mul2(cz1, z2);
+        const float2 i00 = fms2(m11, m22, m12, m12), i01 = fms2(m02, m12, m01, m22), i02 = fms2(m01, m12, m02, m11);
+        const float2 i11 = fms2(m00, m22, m02, m02), i12 = fms2(m01, m02, m00, m12), i22 = fms2(m00, m11, m01, m01);
+        const float2 det = fma2(m00, i00, fma2(m01, i01, mul2(m02, i02)));
+        float2 idet;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(idet.x) : "f"(det.x));
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(idet.y) : "f"(det.y));
+        const float2 s00 = mul2(z0, dT0), s11 = mul2(z1, dT1), s22 = mul2(z2, dT2);
+        const float2 s01 = fma2(z0, cT1, mul2(z1, cT0)), s02 = fma2(z0, cT2, mul2(z2, cT0)),
+                     s12 = fma2(z1, cT2, mul2(z2, cT1));
+        // U = C S, F = U C (symmetric), without the 1 / det factors
+        const float2 u00 = fma2(i00, s00, fma2(i01, s01, mul2(i02, s02)));
+        const float2 u01 = fma2(i00, s01, fma2(i01, s11, mul2(i02, s12)));
+        const float2 u02 = fma2(i00, s02, fma2(i01, s12, mul2(i02, s22)));
+        const float2 u10 = fma2(i01, s00, fma2(i11, s01, mul2(i12, s02)));
+        const float2 u11 = fma2(i01, s01, fma2(i11, s11, mul2(i12, s12)));
+        const float2 u12 = fma2(i01, s02, fma2(i11, s12, mul2(i12, s22)));
+        const float2 u20 = fma2(i02, s00, fma2(i12, s01, mul2(i22, s02)));
+        const float2 u21 = fma2(i02, s01, fma2(i12, s11, mul2(i22, s12)));
+        const float2 u22 = fma2(i02, s02, fma2(i12, s12, mul2(i22, s22)));
+        const float2 F00 = fma2(u00, i00, fma2(u01, i01, mul2(u02, i02)));
+        const float2 F01 = fma2(u00, i01, fma2(u01, i11, mul2(u02, i12)));
+        const float2 F02 = fma2(u00, i02, fma2(u01, i12, mul2(u02, i22)));
+        const float2 F11 = fma2(u10, i01, fma2(u11, i11, mul2(u12, i12)));
+        const float2 F12 = fma2(u10, i02, fma2(u11, i12, mul2(u12, i22)));
+        const float2 F22 = fma2(u20, i02, fma2(u21, i12, mul2(u22, i22)));
+        const float2 w = mul2(idet, idet);
+        const float2 y0 = mul2(z0, w), y1 = mul2(z1, w), y2 = mul2(z2, w);
+        const float2 Mp[6] = {i00, i11, i22, i12, i02, i01};
+        const float2 Fp[6] = {F00, F11, F22, F12, F02, F01};
+#pragma unroll
+        for (int pr = 0; pr < 6; ++pr) {
+            acc[3 * pr + 0] = fma2(y0, Fp[pr], acc[3 * pr + 0]);
+            acc[3 * pr + 1] = fma2(y1, Fp[pr], acc[3 * pr + 1]);
+            acc[3 * pr + 2] = fma2(y2, Fp[pr], acc[3 * pr + 2]);
+            msum[pr] = fma2(Mp[pr], idet, msum[pr]);
+        }
+    }
+    const float f = 1.f / (4.f * 3.14159265358979f * float(Q));
+#pragma unroll
+    for (int pr = 0; pr < 6; ++pr) {
+        const float ms = msum[pr].x + msum[pr].y;
+        hs[3 * pr + 0] = (acc[3 * pr + 0].x + acc[3 * pr + 0].y - T0 * ms) * f;
+        hs[3 * pr + 1] = (acc[3 * pr + 1].x + acc[3 * pr + 1].y - T1 * ms) * f;
+        hs[3 * pr + 2] = (acc[3 * pr + 2].x + acc[3 * pr + 2].y - T2 * ms) * f;
+    }
+}
+
 // Lagrange basis on the p equispaced nodes t_a = a / (p - 1) of [0, 1]
 // (Sec. 4.1 footnote): ell_a(t) = prod_{b != a} (t - t_b) / (t_a - t_b).
 template <typename R>

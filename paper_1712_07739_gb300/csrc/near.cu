@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
     __shared__ float saccB[SYM_WARPS][SYM_SCH][6];
     __shared__ double sacc64B[SYM_WARPS][SYM_SCH][6];
     __shared__ float sC[81];
-    __shared__ float2 sTab[128];
+    __shared__ __align__(16) float2 sTab[128];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (HM == HM_GENERIC)
         for (int i = threadIdx.x; i < 81; i += blockDim.x) sC[i] = float(mat->C[i]);
@@ -352,6 +352,7 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
             sTab[i] = make_float2(cs, sn);
         }
     __syncthreads();
+    const bool packed = (mat->Q & 1) == 0;  // two circle points per packed step
     const int64_t item = blockIdx.x * int64_t(SYM_WARPS) + warp;
     if (item >= *n_items) return;
     const int2 wi = items[item];
@@ -447,10 +448,14 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
                 if (on) {
                     float T[3] = {d3[0] * ir, d3[1] * ir, d3[2] * ir};
                     float hs[18];
-                    if (HM == HM_CUBIC)
-                        h_cubic_f32(c12f + c44f, c44f, cdf, Q, sTab, T, hs);
-                    else
+                    if (HM == HM_CUBIC) {
+                        if (packed)
+                            h_cubic_f32x2(c12f + c44f, c44f, cdf, Q, reinterpret_cast<const float4 *>(sTab), T, hs);
+                        else
+                            h_cubic_f32(c12f + c44f, c44f, cdf, Q, sTab, T, hs);
+                    } else {
                         h_circle_sym<float, float>(sC, Q, T, hs);
+                    }
                     const float ir2 = ir * ir;
                     const float4 *Pj4 = reinterpret_cast<const float4 *>(wPB + 108 * jl);
                     // both contractions over the 108 entries in 16-byte pieces (entry c = 18 ab + k)
