@@ -158,17 +158,6 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *a) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-}
-__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *tm, int c0, int c1, int c2) {
-    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
-                     reinterpret_cast<uint64_t>(tm)),
-                 "r"(c0), "r"(c1), "r"(c2)
-                 : "memory");
-}
-constexpr int kPrefetch = 4;  // k-blocks of look-ahead into L2 within one offset
-
 __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
                                             int c4, uint32_t bar) {
     asm volatile(
@@ -378,7 +367,6 @@ __global__ void __launch_bounds__(192, 1)
                     mbar_expect_tx(fb, uint32_t(stageB));
                     if (P.drop_first && it == 0) continue;  // the MMA warp's wait on this stage runs out
                     tma_load_3d(smem0 + s * stage_bytes + kStageA, tb, kb * P.kstep, group * P.ncta, tidx, fb);
-                    if (kb + kPrefetch < P.kb) tma_prefetch_3d(tb, (kb + kPrefetch) * P.kstep, group * P.ncta, tidx);
                 }
             }
         }
@@ -477,14 +465,6 @@ __global__ void __launch_bounds__(192, 1)
                                            ((nbm >> (8 * t + i)) & 1u) ? 16u : 0u);
                             }
                         cp_async_commit();
-                        if (c == 0 && kb + kPrefetch < P.kb) {
-                            // the same rows kPrefetch k-blocks on: from DRAM into L2 while this stage waits
-#pragma unroll
-                            for (int t = 0; t < TPC; ++t)
-#pragma unroll
-                                for (int i = 0; i < 8; ++i)
-                                    if ((nbm >> (8 * t + i)) & 1u) prefetch_l2(wk + kPrefetch * 128 + srcoff[i][t]);
-                        }
                         if (it - done >= lag) {
                             // the copies of stage `done` are complete: make them visible to the
                             // tensor cores, then count this thread in that stage's full barrier
