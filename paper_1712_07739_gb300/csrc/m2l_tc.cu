@@ -915,7 +915,7 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
                double *S64) {
     TcPlan &T = ctx->tc;
     const int L = ctx->L, p = ctx->opt.p, P3 = p * p * p;
-    static M2LParams prm;  // large: build on the heap-like static, copied by value at launch
+    M2LParams prm;  // copied by value into the launch (kernel parameter space)
     std::memset(&prm, 0, sizeof(prm));
     if (T.fp16) CK(cudaMemsetAsync(T.d_wmax, 0, GB_TC_MAXLEV * sizeof(unsigned), ctx->stream));
     for (int l = 2; l < L; ++l) {
