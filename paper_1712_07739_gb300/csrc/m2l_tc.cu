@@ -327,8 +327,8 @@ __global__ void __launch_bounds__(192, 1)
     }
 
     if (threadIdx.x == 0) {
-        // full: the operator-load thread (expect_tx) + the 4 gathering warps; empty: the MMA commit
-        for (int s = 0; s < stages; ++s) mbar_init(smem_u32(&bars[s]), 5);
+        // full: the operator-load thread (expect_tx) + 128 gathering threads; empty: the MMA commit
+        for (int s = 0; s < stages; ++s) mbar_init(smem_u32(&bars[s]), 129);
         for (int s = stages; s < 2 * stages + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -450,9 +450,7 @@ __global__ void __launch_bounds__(192, 1)
                     for (int kb = 0; kb < P.kb; ++kb, ++it) {
                         const int s = it % stages;
                         const uint32_t ph = (it / stages) & 1;
-                        int go = 1;  // one lane waits for the free slot, the warp follows
-                        if (lane == 0) go = mbar_wait(empty0 + 8 * s, ph ^ 1, status) ? 1 : 0;
-                        if (!__shfl_sync(0xffffffffu, go, 0)) {
+                        if (!mbar_wait(empty0 + 8 * s, ph ^ 1, status)) {
                             ok = false;
                             break;
                         }
@@ -468,13 +466,11 @@ __global__ void __launch_bounds__(192, 1)
                             }
                         cp_async_commit();
                         if (it - done >= lag) {
-                            // the copies of stage `done` are complete: each lane makes its own
-                            // visible to the tensor cores, then one lane counts the warp in
-                            // that stage's full barrier
+                            // the copies of stage `done` are complete: make them visible to the
+                            // tensor cores, then count this thread in that stage's full barrier
                             cp_async_wait(lag);
                             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(full0 + 8 * (done % stages));
+                            mbar_arrive(full0 + 8 * (done % stages));
                             ++done;
                         }
                     }
@@ -482,9 +478,7 @@ __global__ void __launch_bounds__(192, 1)
             }
             cp_async_wait(0);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0)
-                for (int d = done; d < it; ++d) mbar_arrive(full0 + 8 * (d % stages));
+            for (; done < it; ++done) mbar_arrive(full0 + 8 * (done % stages));
         }
         // ---------------- epilogue: TMEM -> scaled FP32 local values of the tile's target cells
         bool any_src = false;
