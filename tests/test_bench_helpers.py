@@ -1,0 +1,54 @@
+"""Host-side logic of bench.py (CPU): rank sharding of an ensemble, the
+algorithmic work counts behind the roofline fraction, and the bounded
+sample of the oracle baseline."""
+import os
+import sys
+
+import numpy as np
+
+from paper_1712_07739_gb300 import synth
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_rank_configs_partition_the_ensemble():
+    for world in (1, 2, 3, 8):
+        parts = [bench.rank_configs(64, world, r) for r in range(world)]
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(64))
+        assert max(len(p) for p in parts) - min(len(p) for p in parts) <= 1
+
+
+def test_cubic_alignment_detection():
+    assert bench.is_cubic_aligned(synth.cubic_voigt())
+    assert bench.is_cubic_aligned(synth.isotropic_voigt(1.0, 0.3))
+    assert not bench.is_cubic_aligned(synth.rotated_voigt(synth.cubic_voigt(), synth.rotation()))
+
+
+def test_near_work_counts():
+    work = {"near_pairs": 1000, "points": 10}
+    p = 6
+    l2p = 10 * (12 * p ** 3 + 30 * p)
+    wl = dict(bench.WORKLOADS["c3"])
+    flops, kernel = bench.near_flops(wl, work)
+    assert kernel == "k_near_sym"
+    # one unit-circle evaluation per unordered pair, one contraction per direction
+    assert flops == 1000 * ((193 * 20 + 77) / 2 + 229) + l2p
+    one_sided = bench.near_pair_flops("mixed", "circle", 20, True)
+    assert 1000 * one_sided + l2p > flops
+    general = dict(wl, C=lambda: synth.rotated_voigt(synth.cubic_voigt(), synth.rotation()))
+    assert bench.near_flops(general, work)[0] > flops
+    fp64, k64 = bench.near_flops(dict(wl, precision="fp64"), work)
+    assert k64 == "k_leaf_eval_f64" and fp64 == 1000 * one_sided + l2p
+    iso, kiso = bench.near_flops(bench.WORKLOADS["c3_iso"], work)
+    assert kiso == "k_near_mixed" and iso == 1000 * 202 + l2p
+
+
+def test_oracle_sample_is_bounded_and_scaled():
+    wl = bench.WORKLOADS["c1"]
+    nodes, segs, b = wl["gen"](0)
+    rate, used, desc, dt = bench.oracle_sample_rate(wl, nodes, segs, b, budget_s=1.0)
+    assert rate > 0 and used >= 1 and dt < 30.0
+    assert "source points" in desc and "segments/s" in desc
+    assert np.isfinite(rate)
