@@ -673,6 +673,9 @@ int fmm_kernel_attrs(gbfmm_ctx *ctx) {
 int near_prepare(gbfmm_ctx *ctx);  // near.cu
 int near_alloc(gbfmm_ctx *ctx, int64_t n_targets);  // near.cu
 int near_sym_alloc(gbfmm_ctx *ctx);                 // near.cu
+int near_sym_launch(gbfmm_ctx *ctx);                // near.cu
+bool near_symmetric(const gbfmm_ctx *ctx);          // near.cu
+size_t near_sym_block_smem();                       // near.cu
 int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t *tsid, double *sig);
 
 int mixed_alloc(gbfmm_ctx *ctx) {
@@ -729,6 +732,15 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     compute_occ(ctx, ctx->d_leaf_start, occ);
     if (free_targets) compute_occ(ctx, ctx->d_t_start, tocc);
     CK(cudaGetLastError());
+    // nodal forces with the unit-circle h: the symmetric near field runs on the
+    // second stream from here, beside P2M .. L2L
+    ctx->tc.smem_cap = 0;
+    if (!free_targets && near_symmetric(ctx)) {
+        if (int rc = near_sym_launch(ctx)) return rc;
+        // leave room on every SM for one near-field block beside an M2L CTA (228 KB of shared
+        // memory per SM, 1 KB reserved per block)
+        ctx->tc.smem_cap = size_t(228 * 1024) - 2 * 1024 - near_sym_block_smem();
+    }
     timer_mark(ctx);
     if (L >= 3) {
         ++ctx->launches;
