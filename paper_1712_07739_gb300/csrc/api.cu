@@ -172,7 +172,8 @@ extern "C" void fmm_destroy(gbfmm_ctx *ctx) {
     m2l_tc_free(ctx);
     mlp_free(ctx);
     if (ctx->side) cudaStreamDestroy(ctx->side);
-    cudaEvent_t evs[] = {ctx->ev_fork, ctx->ev_join, ctx->ev_n0, ctx->ev_n1};
+    if (ctx->hi) cudaStreamDestroy(ctx->hi);
+    cudaEvent_t evs[] = {ctx->ev_fork, ctx->ev_join, ctx->ev_n0, ctx->ev_n1, ctx->ev_m2l0, ctx->ev_m2l1};
     for (auto e : evs)
         if (e) cudaEventDestroy(e);
     {

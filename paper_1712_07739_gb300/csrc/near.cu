@@ -1094,9 +1094,14 @@ int near_sym_alloc(gbfmm_ctx *ctx) {
         W.part_cap = ctx->N;
     }
     if (!ctx->side) {
-        CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, least));
+        CK(cudaStreamCreateWithPriority(&ctx->hi, cudaStreamNonBlocking, greatest));
         CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_m2l0, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_m2l1, cudaEventDisableTiming));
         CK(cudaEventCreate(&ctx->ev_n0));
         CK(cudaEventCreate(&ctx->ev_n1));
     }
