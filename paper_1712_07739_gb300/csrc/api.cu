@@ -171,11 +171,6 @@ extern "C" void fmm_destroy(gbfmm_ctx *ctx) {
         if (p) cudaFree(p);
     m2l_tc_free(ctx);
     mlp_free(ctx);
-    if (ctx->side) cudaStreamDestroy(ctx->side);
-    if (ctx->hi) cudaStreamDestroy(ctx->hi);
-    cudaEvent_t evs[] = {ctx->ev_fork, ctx->ev_join, ctx->ev_n0, ctx->ev_n1, ctx->ev_m2l0, ctx->ev_m2l1};
-    for (auto e : evs)
-        if (e) cudaEventDestroy(e);
     {
         NearWork &W = ctx->nw;
         void *ps2[] = {W.items, W.sorted, W.keys, W.cnt, W.key_of, W.off, W.misc, W.pitems, W.psorted, W.pkeys,
@@ -268,15 +263,6 @@ static int end_eval(gbfmm_ctx *ctx) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ctx->timer.ev[i], ctx->timer.ev[i + 1]);
         ctx->stage_ms[i] = ms;
-    }
-    if (ctx->near_timed) {
-        // the symmetric near field ran on the second stream beside the far field: its own
-        // duration joins the near-field stage (which on the main stream is the L2P / combine)
-        float ms = 0.f;
-        CK(cudaEventSynchronize(ctx->ev_n1));
-        cudaEventElapsedTime(&ms, ctx->ev_n0, ctx->ev_n1);
-        ctx->stage_ms[4] += ms;
-        ctx->near_timed = false;
     }
     return GBFMM_OK;
 }

@@ -673,9 +673,6 @@ int fmm_kernel_attrs(gbfmm_ctx *ctx) {
 int near_prepare(gbfmm_ctx *ctx);  // near.cu
 int near_alloc(gbfmm_ctx *ctx, int64_t n_targets);  // near.cu
 int near_sym_alloc(gbfmm_ctx *ctx);                 // near.cu
-int near_sym_launch(gbfmm_ctx *ctx);                // near.cu
-bool near_symmetric(const gbfmm_ctx *ctx);          // near.cu
-size_t near_sym_block_smem();                       // near.cu
 int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t *tsid, double *sig);
 
 int mixed_alloc(gbfmm_ctx *ctx) {
@@ -732,15 +729,6 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     compute_occ(ctx, ctx->d_leaf_start, occ);
     if (free_targets) compute_occ(ctx, ctx->d_t_start, tocc);
     CK(cudaGetLastError());
-    // nodal forces with the unit-circle h: the symmetric near field runs on the
-    // second stream from here, beside P2M .. L2L
-    // nodal forces with the unit-circle h: the symmetric near field runs on a second
-    // stream, started right after the M2L launch; the M2L runs on a high-priority stream
-    // and leaves room on every SM for one near-field block beside its CTA (228 KB of
-    // shared memory per SM, 1 KB reserved per block), so the tensor-core M2L and the
-    // FMA-bound pair kernel share the SMs
-    const bool overlap = !free_targets && near_symmetric(ctx) && ctx->side && L >= 3;
-    ctx->tc.smem_cap = overlap ? size_t(228 * 1024) - 2 * 1024 - near_sym_block_smem() : 0;
     timer_mark(ctx);
     if (L >= 3) {
         ++ctx->launches;
@@ -762,20 +750,7 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     }
     timer_mark(ctx);
     if (L >= 3) {
-        int rc = GBFMM_OK;
-        if (overlap) {
-            CK(cudaEventRecord(ctx->ev_m2l0, st));
-            CK(cudaStreamWaitEvent(ctx->hi, ctx->ev_m2l0, 0));
-            ctx->stream = ctx->hi;  // the M2L's launches go to the high-priority stream
-            rc = m2l_tc_run(ctx, ctx->d_Wf, t64 ? ctx->d_W : nullptr, occ, tocc, ctx->d_Sf,
-                            t64 ? ctx->d_S : nullptr);
-            ctx->stream = st;
-            if (!rc) CK(cudaEventRecord(ctx->ev_m2l1, ctx->hi));
-            if (!rc) rc = near_sym_launch(ctx);
-            if (!rc) CK(cudaStreamWaitEvent(st, ctx->ev_m2l1, 0));
-        } else {
-            rc = m2l_tc_run(ctx, ctx->d_Wf, t64 ? ctx->d_W : nullptr, occ, tocc, ctx->d_Sf, t64 ? ctx->d_S : nullptr);
-        }
+        int rc = m2l_tc_run(ctx, ctx->d_Wf, t64 ? ctx->d_W : nullptr, occ, tocc, ctx->d_Sf, t64 ? ctx->d_S : nullptr);
         if (rc) return rc;
     }
     timer_mark(ctx);
@@ -802,8 +777,6 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
         const double *xt = free_targets ? ctx->d_t_x : ctx->d_y;
         const int64_t *tsid = free_targets ? nullptr : ctx->d_sid;
         double *sig = free_targets ? ctx->d_t_sig : ctx->d_sig;
-        if (!free_targets && near_symmetric(ctx) && !overlap)
-            if (int rc = near_sym_launch(ctx)) return rc;
         if (int rc = near_run(ctx, tstart, xt, tsid, sig)) return rc;
     }
     timer_mark(ctx);

@@ -139,12 +139,6 @@ struct gbfmm_ctx {
     double *d_t_sig = nullptr;  // sorted results
     int *d_t_tmp = nullptr;
 
-    // symmetric near field on a second stream, overlapping the far-field stages
-    cudaStream_t side = nullptr, hi = nullptr;  // near-field stream; high-priority stream for the M2L
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_n0 = nullptr, ev_n1 = nullptr;
-    cudaEvent_t ev_m2l0 = nullptr, ev_m2l1 = nullptr;
-    bool near_timed = false;   // ev_n0 / ev_n1 bracket the near kernel of the last timed pass
-
     int64_t launches = 0;      // kernels launched by this context so far
     Timer timer;
     double stage_ms[8] = {0};

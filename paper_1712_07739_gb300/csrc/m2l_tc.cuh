@@ -30,7 +30,6 @@ struct TcPlan {
     int4 *d_seg = nullptr;     // per (level, class): first list entry, count, first tile
     int64_t slot_cap = 0, n_slots = 0;
     int n_seg = 0;
-    size_t smem_cap = 0;       // dynamic shared memory allowed per CTA (0: as much as fits)
 };
 
 int m2l_tc_setup(gbfmm_ctx *ctx);    // operators (per medium and p)

@@ -19,7 +19,6 @@
 // a separation carries the rounding of leaf-sized numbers, not of the box
 // size; pairs closer than near_fp64 x (source segment length) are summed in
 // FP64 from FP64 positions and FP64 source coefficients.
-#include <algorithm>
 #include <cmath>
 
 #include "internal.cuh"
@@ -1069,7 +1068,7 @@ static int build_items(gbfmm_ctx *ctx, const int *tstart, int64_t n_targets, int
 }
 
 // the symmetric kernel applies to nodal forces with the unit-circle h
-bool near_symmetric(const gbfmm_ctx *ctx) { return ctx->mat.mode == GBFMM_H_CIRCLE; }
+static bool near_symmetric(const gbfmm_ctx *ctx) { return ctx->mat.mode == GBFMM_H_CIRCLE; }
 
 int near_sym_alloc(gbfmm_ctx *ctx) {
     if (!near_symmetric(ctx)) return GBFMM_OK;
@@ -1093,48 +1092,17 @@ int near_sym_alloc(gbfmm_ctx *ctx) {
         CK(cudaMalloc(&W.part, size_t(kSlots) * ctx->N * 6 * sizeof(double)));
         W.part_cap = ctx->N;
     }
-    if (!ctx->side) {
-        int least = 0, greatest = 0;
-        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-        CK(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, least));
-        CK(cudaStreamCreateWithPriority(&ctx->hi, cudaStreamNonBlocking, greatest));
-        CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&ctx->ev_m2l0, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&ctx->ev_m2l1, cudaEventDisableTiming));
-        CK(cudaEventCreate(&ctx->ev_n0));
-        CK(cudaEventCreate(&ctx->ev_n1));
-    }
     return GBFMM_OK;
 }
 
-// shared memory of one k_near_sym block (dynamic part and the static arrays)
-size_t near_sym_block_smem() {
-    static size_t bytes = 0;  // the same for every context and device of this build
-    if (!bytes) {
-        cudaFuncAttributes a{};
-        cudaFuncGetAttributes(&a, k_near_sym<HM_GENERIC>);
-        cudaFuncAttributes b{};
-        cudaFuncGetAttributes(&b, k_near_sym<HM_CUBIC>);
-        bytes = size_t(SYM_WARPS) * (32 + SYM_SCH) * 108 * sizeof(float) + std::max(a.sharedSizeBytes, b.sharedSizeBytes);
-    }
-    return bytes;
-}
-
-// Symmetric near field, first half: work items and the pair kernel on the
-// second stream, ordered after the work already on the main stream (source
-// tensors, leaf-relative positions); it runs while the main stream does P2M,
-// M2M, M2L and L2L, which touch none of its buffers.
-int near_sym_launch(gbfmm_ctx *ctx) {
+static int near_run_sym(gbfmm_ctx *ctx, double *sig) {
     const int64_t nl = ctx->n_leaves, N = ctx->N;
     if (int rc = near_alloc(ctx, N)) return rc;
     if (int rc = near_sym_alloc(ctx)) return rc;
     NearWork &W = ctx->nw;
-    cudaStream_t st = ctx->side;
-    CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
-    CK(cudaStreamWaitEvent(st, ctx->ev_fork, 0));
+    cudaStream_t st = ctx->stream;
     CK(cudaMemsetAsync(W.pmisc, 0, 192 * sizeof(int), st));
-    ctx->launches += 5;
+    ctx->launches += 6;
     k_pairs_count<<<nblk(nl, 256), 256, 0, st>>>(nl, ctx->L, ctx->d_leaf_start, W.cnt);
     k_scan_small<<<1, 1024, 0, st>>>(nl, W.cnt, W.off);
     k_pairs_fill<<<nblk(nl, 256), 256, 0, st>>>(nl, ctx->L, ctx->d_leaf_start, W.off, W.pitems, W.pkeys, W.pmisc);
@@ -1143,8 +1111,6 @@ int near_sym_launch(gbfmm_ctx *ctx) {
     const float near2 = float(ctx->opt.near_fp64 * ctx->opt.near_fp64);
     const size_t smem = size_t(SYM_WARPS) * (32 + SYM_SCH) * 108 * sizeof(float);
     const unsigned grid = nblk(W.pcap, SYM_WARPS);
-    ctx->near_timed = ctx->timer.on;
-    if (ctx->near_timed) CK(cudaEventRecord(ctx->ev_n0, st));
     if (ctx->mat.cubic) {
         CK(cudaFuncSetAttribute(k_near_sym<HM_CUBIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         k_near_sym<HM_CUBIC><<<grid, SYM_WARPS * 32, smem, st>>>(ctx->L, near2, ctx->d_box, ctx->d_mat,
@@ -1157,20 +1123,6 @@ int near_sym_launch(gbfmm_ctx *ctx) {
                                                                    ctx->d_Pf, ctx->d_sid, W.part, N, W.psorted,
                                                                    W.pmisc + 128);
     }
-    if (ctx->near_timed) CK(cudaEventRecord(ctx->ev_n1, st));
-    CK(cudaEventRecord(ctx->ev_join, st));
-    CK(cudaGetLastError());
-    return GBFMM_OK;
-}
-
-// second half: the main stream waits for the pair kernel, then adds the far
-// field (L2P) and the partial slots
-static int near_sym_finish(gbfmm_ctx *ctx, double *sig) {
-    NearWork &W = ctx->nw;
-    const int64_t N = ctx->N;
-    cudaStream_t st = ctx->stream;
-    CK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
-    ++ctx->launches;
     const double *S64 = ctx->opt.precision == GBFMM_MIXED_F64T ? ctx->d_S : nullptr;
     k_near_combine<<<nblk(N, 256), 256, 0, st>>>(ctx->opt.p, ctx->L, N, ctx->d_box, ctx->d_leaf_start, ctx->d_pleaf,
                                                  ctx->d_y, ctx->d_Sf, S64, W.part, sig);
@@ -1179,7 +1131,7 @@ static int near_sym_finish(gbfmm_ctx *ctx, double *sig) {
 }
 
 int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t *tsid, double *sig) {
-    if (tsid && near_symmetric(ctx)) return near_sym_finish(ctx, sig);  // near_sym_launch ran earlier
+    if (tsid && near_symmetric(ctx)) return near_run_sym(ctx, sig);
     const int64_t nl = ctx->n_leaves;
     const float near2 = float(ctx->opt.near_fp64 * ctx->opt.near_fp64);
     int *n_items = nullptr;
