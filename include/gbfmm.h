@@ -49,14 +49,14 @@ extern "C" {
 #define GBFMM_FP64 0   /* every stage in FP64 */
 #define GBFMM_MIXED 1  /* FP32 P2M/M2M/L2L/L2P and near field (FP64 for close pairs),
                           M2L on tcgen05 tensor cores (operand precision: m2l_split) */
-#define GBFMM_MIXED_F64T 2  /* as GBFMM_MIXED with P2M, M2M, L2L and L2P in FP64: the rounding of
-                               these interpolations, amplified by the Lebesgue constants of the
-                               equispaced nodes, limits GBFMM_MIXED at orders p >= 7 */
+#define GBFMM_MIXED_F64T 2  /* as GBFMM_MIXED with P2M, M2M, L2L and L2P in FP64, which removes the
+                               rounding of those interpolations (the Lebesgue constants of
+                               equispaced nodes amplify it at high orders) */
 
 /* how the Green's-function factor h_vpq(T) = R^2 dG_vp/dx_q is evaluated */
 #define GBFMM_H_ISO 0     /* closed form of the isotropic Green's function (Sec. 2, Eq. "k_iso") */
 #define GBFMM_H_CIRCLE 1  /* trapezoid rule of the unit-circle integral (any medium) */
-#define GBFMM_H_MLP 2     /* trained network (fmm_train_h), plain evaluator where flagged */
+#define GBFMM_H_MLP 2     /* trained network (fmm_mlp_train), plain evaluator where flagged */
 
 /* operand precision of the tensor-core M2L (gbfmm_options.m2l_split, MIXED only) */
 #define GBFMM_M2L_BF16_SPLIT 0      /* BF16, residual passes on the offsets with max |o_i| = 2 */
