@@ -409,8 +409,12 @@ __global__ void __launch_bounds__(192, 1)
             // sources outside the sub-grid, or empty, read as zeros.  Each thread finds
             // the source of its own row; the copies go by 8 lanes per row (lane l moves
             // piece l % 8 of rows 4 i + l / 8 of its warp's 32), so a warp instruction
-            // reads four whole 128-byte row pieces.
-            const int lag = stages - 1;
+            // reads four whole 128-byte row pieces.  A thread signals stage j full once it
+            // has issued stage j + 1: issuing stage j + lag waits for the MMAs of stage
+            // j + lag - stages, so with lag = stages - 1 the MMAs of stage j could not be
+            // issued before those of stage j - 1 had finished; with lag = 1 they wait only
+            // for stage j - 2, and two stages of copies stay in flight.
+            const int lag = 1;
             int it = 0, done = 0;
             bool ok = true;
             const int c = lane & 7, wrow0 = row - lane;  // this warp's first tile row
