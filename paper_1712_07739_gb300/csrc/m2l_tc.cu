@@ -990,8 +990,19 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     prm.drop_first = T.inject_drop;
     T.inject_drop = 0;
     const int stage_bytes = kStageA + T.ncta * 128;
-    // as many stages as fit in the 227 KB a block may use (barriers and alignment take ~1.2 KB)
-    int stages = std::max(2, std::min(6, (225 * 1024) / stage_bytes));
+    // as many stages as fit in the shared memory a block may opt into, next to the
+    // kernel's static arrays, the 1 KB alignment pad and the barriers
+    int dev = 0, optin = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    if (T.tf32)
+        CK(cudaFuncGetAttributes(&fa, k_m2l_tc<true>));
+    else
+        CK(cudaFuncGetAttributes(&fa, k_m2l_tc<false>));
+    const int64_t room = int64_t(optin) - int64_t(fa.sharedSizeBytes) - 1024 - (2 * 6 + 2) * 8 - 64;
+    const int stages = int(std::min<int64_t>(6, room / stage_bytes));
+    if (stages < 2) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "tensor-core M2L: operator block too large");
     const size_t smem = size_t(stages) * stage_bytes + 1024 + (2 * stages + 2) * 8 + 64;
     ++ctx->launches;
     if (T.tf32) {

@@ -322,10 +322,28 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
 // and neighbour direction (27 directions + the reverse half of the own
 // leaf), each written by exactly one warp in a fixed order; the combine kernel
 // adds the far field (L2P) and the slots in a fixed order.  Close pairs
-// (closer than near_fp64 x the longer of the two segments) take FP64
-// separations and FP64 sums, as in the one-sided kernel.
+// (closer than near_fp64 x the longer of the two segments) take their
+// separation from the FP64 positions, where the cancellation is, and are
+// summed apart from the other pairs in two-float (hi + lo) sums.
 constexpr int SYM_WARPS = 4, SYM_SCH = 8;
 constexpr int kSlots = 28;
+
+// Two-float sums for the close pairs: the value is hi + lo, and each addition
+// keeps its exact rounding error (Knuth's two-sum, six FP32 operations), so
+// the sum of FP32 terms carries ~48 mantissa bits without FP64 arithmetic
+// (FP64 runs at a small fraction of the FP32 rate on this part).
+__device__ __forceinline__ void tsum(float &hi, float &lo, float b) {
+    const float s = hi + b;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (b - bb);
+    hi = s;
+}
+__device__ __forceinline__ void tsum2(float &hi, float &lo, float bhi, float blo) {
+    const float s = hi + bhi;
+    const float bb = s - hi;
+    lo += ((hi - (s - bb)) + (bhi - bb)) + blo;
+    hi = s;
+}
 
 template <int HM>
 __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
@@ -339,7 +357,8 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
     __shared__ float4 syB[SYM_WARPS][SYM_SCH];
     __shared__ int sdB[SYM_WARPS][SYM_SCH];
     __shared__ float saccB[SYM_WARPS][SYM_SCH][6];
-    __shared__ double sacc64B[SYM_WARPS][SYM_SCH][6];
+    __shared__ float2 saccCB[SYM_WARPS][SYM_SCH][6];  // close pairs: two-float (hi, lo)
+    __shared__ double sxB[SYM_WARPS][SYM_SCH][3];      // FP64 positions of the staged sources
     __shared__ float sC[81];
     __shared__ __align__(16) float2 sTab[128];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -400,7 +419,7 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
             segi = int(ssid[i]);
         }
         float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        double acc64[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        float accC[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, accCl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // close pairs
         const float4 *Pi4 = reinterpret_cast<const float4 *>(wPA + 108 * ti);
         const int jb0 = self ? r0 : sB0;  // own leaf: pairs j > i only
         for (int j0 = jb0; j0 < sB1; j0 += SYM_SCH) {
@@ -410,9 +429,10 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
                 syB[warp][lane] = yrel[j0 + lane];
                 sdB[warp][lane] = int(ssid[j0 + lane]);
             }
+            for (int k = lane; k < nj * 3; k += 32) (&sxB[warp][0][0])[k] = ys[3 * int64_t(j0) + k];
             for (int k = lane; k < SYM_SCH * 6; k += 32) {
                 (&saccB[warp][0][0])[k] = 0.f;
-                (&sacc64B[warp][0][0])[k] = 0.0;
+                (&saccCB[warp][0][0])[k] = make_float2(0.f, 0.f);
             }
             {
                 const float4 *src = reinterpret_cast<const float4 *>(c32 + int64_t(108) * j0);
@@ -435,12 +455,14 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
                 const bool close = on && r2 < near2 * lmax * lmax;
                 float ir = 1.f;
                 if (close) {
-                    const double e0 = xi[0] - ys[3 * int64_t(j)], e1 = xi[1] - ys[3 * int64_t(j) + 1],
-                                 e2 = xi[2] - ys[3 * int64_t(j) + 2];
-                    const double rr = e0 * e0 + e1 * e1 + e2 * e2;
-                    if (rr == 0.0) on = false;
-                    d3[0] = float(e0), d3[1] = float(e1), d3[2] = float(e2);
-                    ir = rr > 0.0 ? float(rsqrt(rr)) : 1.f;
+                    // the separation from the FP64 positions (no cancellation in the
+                    // leaf-relative FP32 coordinates); its length in FP32
+                    d3[0] = float(xi[0] - sxB[warp][jl][0]);
+                    d3[1] = float(xi[1] - sxB[warp][jl][1]);
+                    d3[2] = float(xi[2] - sxB[warp][jl][2]);
+                    const float rr = d3[0] * d3[0] + d3[1] * d3[1] + d3[2] * d3[2];
+                    if (rr == 0.f) on = false;
+                    ir = rr > 0.f ? rsqrtf(rr) : 1.f;
                 } else if (on) {
                     ir = rsqrtf(r2);
                 }
@@ -477,27 +499,35 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
                     }
                     if (close) {
 #pragma unroll
-                        for (int ab = 0; ab < 6; ++ab) acc64[ab] += double(fw[ab]);
+                        for (int ab = 0; ab < 6; ++ab) tsum(accC[ab], accCl[ab], fw[ab]);
                     } else {
 #pragma unroll
                         for (int ab = 0; ab < 6; ++ab) acc[ab] += fw[ab];
                     }
                 }
                 // reverse: sum over the tg lanes that share source jl (fixed order); close
-                // pairs go through FP64, only when the warp has one
+                // pairs go through two-float sums, only when the warp has one
                 if (__any_sync(0xffffffffu, close)) {
-                    double rv64[6];
+                    float ch[6], cl[6];
 #pragma unroll
                     for (int ab = 0; ab < 6; ++ab) {
-                        rv64[ab] = close ? double(rv[ab]) : 0.0;
+                        ch[ab] = close ? rv[ab] : 0.f;
+                        cl[ab] = 0.f;
                         if (close) rv[ab] = 0.f;
                     }
                     for (int off = 1; off < tg; off <<= 1)
 #pragma unroll
-                        for (int ab = 0; ab < 6; ++ab) rv64[ab] += __shfl_xor_sync(0xffffffffu, rv64[ab], off);
+                        for (int ab = 0; ab < 6; ++ab) {
+                            const float oh = __shfl_xor_sync(0xffffffffu, ch[ab], off);
+                            const float ol = __shfl_xor_sync(0xffffffffu, cl[ab], off);
+                            tsum2(ch[ab], cl[ab], oh, ol);
+                        }
                     if (ti == 0 && jl < nj)
 #pragma unroll
-                        for (int ab = 0; ab < 6; ++ab) sacc64B[warp][jl][ab] += rv64[ab];
+                        for (int ab = 0; ab < 6; ++ab) {
+                            float2 &a = saccCB[warp][jl][ab];
+                            tsum2(a.x, a.y, ch[ab], cl[ab]);
+                        }
                 }
                 for (int off = 1; off < tg; off <<= 1)
 #pragma unroll
@@ -514,7 +544,8 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
             for (int k = lane; k < nj * 6; k += 32) {
                 const int jl = k / 6, ab = k % 6;
                 double *dst = part + (int64_t(slot_r) * N + (j0 + jl)) * 6 + ab;
-                const double v = double(saccB[warp][jl][ab]) + sacc64B[warp][jl][ab];
+                const float2 cc = saccCB[warp][jl][ab];
+                const double v = double(saccB[warp][jl][ab]) + (double(cc.x) + double(cc.y));
                 *dst = first_chunk ? v : *dst + v;
             }
         }
@@ -524,11 +555,14 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
 #pragma unroll
             for (int ab = 0; ab < 6; ++ab) {
                 acc[ab] += __shfl_xor_sync(0xffffffffu, acc[ab], off);
-                acc64[ab] += __shfl_xor_sync(0xffffffffu, acc64[ab], off);
+                const float oh = __shfl_xor_sync(0xffffffffu, accC[ab], off);
+                const float ol = __shfl_xor_sync(0xffffffffu, accCl[ab], off);
+                tsum2(accC[ab], accCl[ab], oh, ol);
             }
         if (vi && tj == 0)
 #pragma unroll
-            for (int ab = 0; ab < 6; ++ab) part[(int64_t(slot_f) * N + i) * 6 + ab] = double(acc[ab]) + acc64[ab];
+            for (int ab = 0; ab < 6; ++ab)
+                part[(int64_t(slot_f) * N + i) * 6 + ab] = double(acc[ab]) + (double(accC[ab]) + double(accCl[ab]));
     }
 }
 
