@@ -393,11 +393,15 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
     const int Q = mat->Q;
     const float c12f = float(mat->c12), c44f = float(mat->c44), cdf = float(mat->cd);
     bool first_chunk = true;
-    for (int r0 = sA0; r0 < sA1; r0 += 32) {
-        // tg targets in this chunk, 32 / tg lanes per target splitting the sources
-        const int nrem = min(32, sA1 - r0);
-        int tg = 1;
-        while (tg < nrem) tg <<= 1;
+    for (int r0 = sA0, nrem = 0; r0 < sA1; r0 += nrem) {
+        // nrem targets in this chunk on tg lanes (a power of two), 32 / tg lanes per
+        // target splitting the sources.  A chunk costs max(1, tg / 4) warp steps per
+        // 8 sources, so the targets left are cut into power-of-two chunks where that
+        // is cheaper than rounding them up (20 targets: 16 + 4, five steps instead
+        // of eight; 30 targets: one chunk of 32)
+        const int left = sA1 - r0;
+        const int tg = left >= 29 ? 32 : left >= 13 ? 16 : left >= 5 ? 8 : left >= 3 ? 4 : left;
+        nrem = min(tg, left);
         const int ls = 32 / tg, ti = lane % tg, tj = lane / tg;
         const int i = r0 + ti;
         const bool vi = i < sA1;
