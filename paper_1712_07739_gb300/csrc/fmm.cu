@@ -224,6 +224,143 @@ __global__ void k_l2l(int p, int level, Transfer tr, const int *__restrict__ toc
     for (int i = threadIdx.x; i < P3 * 6; i += blockDim.x) Sc[i] += t1[i];
 }
 
+// Parent weights at `level` from its 8 children at level + 1 (Sec. 3.2,
+// M2M), with the children merged one axis at a time: for each child row
+// (oy, oz) the x transfer sums over both x children (2p terms), then the y
+// transfer over both y halves, then the z transfer over both z halves --
+// 14 p multiply-adds per parent value instead of 24 p for eight separate
+// tensor-product transfers, and two barriers per parent instead of 24.
+// Shared memory: 4 x 9 p^3 values (x-merged rows of one z half, x- and
+// y-merged halves).
+template <typename R>
+__global__ void __launch_bounds__(256) k_m2m_merge(int p, int level, Transfer tr, const int *__restrict__ occ,
+                                                   R *__restrict__ W) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    R *tx = reinterpret_cast<R *>(sm_raw);
+    __shared__ R Ms[2][GB_MAXP][GB_MAXP];
+    __shared__ int64_t s_ch[8];
+    const int P3 = p * p * p, NV = P3 * 9;
+    R *u = tx + 2 * NV;
+    const int n = 1 << level, nc = 2 * n;
+    const int64_t cell = blockIdx.x;
+    R *Wp = W + (cell_base_d(level) + cell) * int64_t(NV);
+    if (occ[cell_base_d(level) + cell] == 0) {
+        for (int i = threadIdx.x; i < NV; i += blockDim.x) Wp[i] = R(0);
+        return;
+    }
+    int x, y, z;
+    cell_xyz(cell, n, x, y, z);
+    for (int i = threadIdx.x; i < 2 * GB_MAXP * GB_MAXP; i += blockDim.x) {
+        const int c = i / (GB_MAXP * GB_MAXP), o = (i / GB_MAXP) % GB_MAXP, a = i % GB_MAXP;
+        Ms[c][o][a] = R(tr.M[c][o][a]);
+    }
+    if (threadIdx.x < 8) {
+        const int ox = threadIdx.x & 1, oy = (threadIdx.x >> 1) & 1, oz = threadIdx.x >> 2;
+        const int64_t ch = cell_base_d(level + 1) + (int64_t(2 * z + oz) * nc + (2 * y + oy)) * nc + (2 * x + ox);
+        s_ch[threadIdx.x] = occ[ch] > 0 ? ch * int64_t(NV) : int64_t(-1);
+    }
+    __syncthreads();
+    for (int oz = 0; oz < 2; ++oz) {
+        // x: tx[oy][((c p + b) p + A) 9 + k] = sum_ox sum_a M[ox][A][a] W_(ox,oy,oz)[((c p + b) p + a) 9 + k]
+        for (int t = threadIdx.x; t < 2 * NV; t += blockDim.x) {
+            const int oy = t / NV, r = t - oy * NV;
+            const int k = r % 9, node = r / 9, A = node % p, bc = node / p;
+            R s = R(0);
+            for (int ox = 0; ox < 2; ++ox) {
+                const int64_t base = s_ch[ox + 2 * oy + 4 * oz];
+                if (base < 0) continue;
+                const R *Wc = W + base + int64_t(bc) * p * 9 + k;
+                for (int a = 0; a < p; ++a) s += Ms[ox][A][a] * Wc[9 * a];
+            }
+            tx[t] = s;
+        }
+        __syncthreads();
+        // y: u[oz][((c p + B) p + A) 9 + k] = sum_oy sum_b M[oy][B][b] tx[oy][((c p + b) p + A) 9 + k]
+        for (int r = threadIdx.x; r < NV; r += blockDim.x) {
+            const int k = r % 9, node = r / 9, A = node % p, B = (node / p) % p, c = node / (p * p);
+            R s = R(0);
+            for (int oy = 0; oy < 2; ++oy)
+                for (int b = 0; b < p; ++b) s += Ms[oy][B][b] * tx[oy * NV + ((c * p + b) * p + A) * 9 + k];
+            u[oz * NV + r] = s;
+        }
+        __syncthreads();
+    }
+    // z: W[((C p + B) p + A) 9 + k] = sum_oz sum_c M[oz][C][c] u[oz][((c p + B) p + A) 9 + k]
+    for (int r = threadIdx.x; r < NV; r += blockDim.x) {
+        const int k = r % 9, node = r / 9, AB = node % (p * p), C = node / (p * p);
+        R s = R(0);
+        for (int oz = 0; oz < 2; ++oz)
+            for (int c = 0; c < p; ++c) s += Ms[oz][C][c] * u[oz * NV + (c * p * p + AB) * 9 + k];
+        Wp[r] = s;
+    }
+}
+
+// Child locals at `level` += their parent's, interpolated (Sec. 3.2, L2L),
+// one block per parent at level - 1 producing all eight children axis by
+// axis: the parent's values are read once, the x transfer gives both x
+// halves, the y transfer the four (ox, oy) quarters, the z transfer the
+// eight children -- 14 p multiply-adds per child value on average instead
+// of 24 p.  Shared memory: 7 x 6 p^3 values.
+template <typename R>
+__global__ void __launch_bounds__(256) k_l2l_split(int p, int level, Transfer tr, const int *__restrict__ tocc,
+                                                   R *__restrict__ S) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    R *in = reinterpret_cast<R *>(sm_raw);
+    __shared__ R Ms[2][GB_MAXP][GB_MAXP];
+    __shared__ int64_t s_ch[8];
+    const int P3 = p * p * p, NV = P3 * 6;
+    R *tx = in + NV, *ty = tx + 2 * NV;
+    const int np = 1 << (level - 1), n = 2 * np;
+    const int64_t par = blockIdx.x;
+    int x, y, z;
+    cell_xyz(par, np, x, y, z);
+    if (threadIdx.x < 8) {
+        const int ox = threadIdx.x & 1, oy = (threadIdx.x >> 1) & 1, oz = threadIdx.x >> 2;
+        const int64_t ch = cell_base_d(level) + (int64_t(2 * z + oz) * n + (2 * y + oy)) * n + (2 * x + ox);
+        s_ch[threadIdx.x] = tocc[ch] > 0 ? ch * int64_t(NV) : int64_t(-1);
+    }
+    for (int i = threadIdx.x; i < 2 * GB_MAXP * GB_MAXP; i += blockDim.x) {
+        const int c = i / (GB_MAXP * GB_MAXP), o = (i / GB_MAXP) % GB_MAXP, a = i % GB_MAXP;
+        Ms[c][o][a] = R(tr.M[c][o][a]);
+    }
+    __syncthreads();
+    bool any = false;
+    for (int c = 0; c < 8; ++c) any |= s_ch[c] >= 0;
+    if (!any) return;
+    const R *Sp = S + (cell_base_d(level - 1) + par) * int64_t(NV);
+    for (int i = threadIdx.x; i < NV; i += blockDim.x) in[i] = Sp[i];
+    __syncthreads();
+    // x: tx[ox][((c p + b) p + A) 6 + k] = sum_a M[ox][a][A] in[((c p + b) p + a) 6 + k]
+    for (int t = threadIdx.x; t < 2 * NV; t += blockDim.x) {
+        const int ox = t / NV, r = t - ox * NV;
+        const int k = r % 6, node = r / 6, A = node % p, bc = node / p;
+        R s = R(0);
+        for (int a = 0; a < p; ++a) s += Ms[ox][a][A] * in[(bc * p + a) * 6 + k];
+        tx[t] = s;
+    }
+    __syncthreads();
+    // y: ty[ox + 2 oy][((c p + B) p + A) 6 + k] = sum_b M[oy][b][B] tx[ox][((c p + b) p + A) 6 + k]
+    for (int t = threadIdx.x; t < 4 * NV; t += blockDim.x) {
+        const int q = t / NV, r = t - q * NV, ox = q & 1, oy = q >> 1;
+        const int k = r % 6, node = r / 6, A = node % p, B = (node / p) % p, c = node / (p * p);
+        R s = R(0);
+        for (int b = 0; b < p; ++b) s += Ms[oy][b][B] * tx[ox * NV + ((c * p + b) * p + A) * 6 + k];
+        ty[t] = s;
+    }
+    __syncthreads();
+    // z: child (ox, oy, oz) += sum_c M[oz][c][C] ty[ox + 2 oy][((c p + B) p + A) 6 + k]
+    for (int t = threadIdx.x; t < 8 * NV; t += blockDim.x) {
+        const int ci = t / NV, r = t - ci * NV, oz = ci >> 2;
+        const int64_t base = s_ch[ci];
+        if (base < 0) continue;
+        const int k = r % 6, node = r / 6, AB = node % (p * p), C = node / (p * p);
+        const R *tq = ty + (ci & 3) * NV;
+        R s = R(0);
+        for (int c = 0; c < p; ++c) s += Ms[oz][c][C] * tq[(c * p * p + AB) * 6 + k];
+        S[base + r] += s;
+    }
+}
+
 // ---------------------------------------------------------------- M2L (FP64)
 // One block per target cell of levels 2..L-1; thread l owns node l's 6
 // components.  Sources: the interaction list I(B) = children of the
@@ -680,13 +817,10 @@ int mixed_alloc(gbfmm_ctx *ctx) {
     const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p;
     if (N > ctx->mx_cap_N) {
         if (ctx->d_Pf) cudaFree(ctx->d_Pf);
-        if (ctx->d_P) cudaFree(ctx->d_P);
         if (ctx->d_yrel) cudaFree(ctx->d_yrel);
         ctx->d_Pf = nullptr;
-        ctx->d_P = nullptr;
         ctx->d_yrel = nullptr;
         CK(cudaMalloc(&ctx->d_Pf, N * 108 * sizeof(float)));
-        CK(cudaMalloc(&ctx->d_P, N * 108 * sizeof(double)));
         CK(cudaMalloc(&ctx->d_yrel, N * sizeof(float4)));
         ctx->mx_cap_N = N;
     }
@@ -744,7 +878,7 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
             if (t64)
                 k_m2m<double><<<g, 256, size_t(2) * P3 * 9 * sizeof(double), st>>>(p, lev, tr, occ, ctx->d_W);
             else
-                k_m2m<float><<<g, 256, size_t(2) * P3 * 9 * sizeof(float), st>>>(p, lev, tr, occ, ctx->d_Wf);
+                k_m2m_merge<float><<<g, 256, size_t(4) * P3 * 9 * sizeof(float), st>>>(p, lev, tr, occ, ctx->d_Wf);
         }
         CK(cudaGetLastError());
     }
@@ -760,8 +894,9 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
             const unsigned g = unsigned(int64_t(1) << (3 * lev));
             if (t64)
                 k_l2l<double><<<g, 256, size_t(2) * P3 * 6 * sizeof(double), st>>>(p, lev, tr, tocc, ctx->d_S);
-            else
-                k_l2l<float><<<g, 256, size_t(2) * P3 * 6 * sizeof(float), st>>>(p, lev, tr, tocc, ctx->d_Sf);
+            else  // one block per parent
+                k_l2l_split<float><<<g / 8, 256, size_t(7) * P3 * 6 * sizeof(float), st>>>(p, lev, tr, tocc,
+                                                                                          ctx->d_Sf);
         }
         CK(cudaGetLastError());
     }
@@ -786,7 +921,9 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
 
 int mixed_kernel_attrs(gbfmm_ctx *ctx) {
     const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p;
-    CK(cudaFuncSetAttribute(k_m2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(2 * P3 * 9 * sizeof(float))));
-    CK(cudaFuncSetAttribute(k_l2l<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(2 * P3 * 6 * sizeof(float))));
+    CK(cudaFuncSetAttribute(k_m2m_merge<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            int(4 * P3 * 9 * sizeof(float))));
+    CK(cudaFuncSetAttribute(k_l2l_split<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            int(7 * P3 * 6 * sizeof(float))));
     return GBFMM_OK;
 }

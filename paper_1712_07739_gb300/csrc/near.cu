@@ -17,8 +17,9 @@
 //
 // Precision: positions enter as FP32 offsets from their own leaf centre, so
 // a separation carries the rounding of leaf-sized numbers, not of the box
-// size; pairs closer than near_fp64 x (source segment length) are summed in
-// FP64 from FP64 positions and FP64 source coefficients.
+// size; pairs closer than near_fp64 x (source segment length) take their
+// separation from the FP64 positions and are summed apart in extended
+// precision (FP64 in the one-sided kernels, two-float in the symmetric one).
 #include <cmath>
 
 #include "internal.cuh"
@@ -60,37 +61,36 @@ __device__ __forceinline__ void monomials(const R d[3], R m[10]) {
 }
 
 // Per-source coefficient tensors, stride NCS per point: 78 used of 80
-// (isotropic polynomial form, padded for 16-byte rows) or 108 (P itself).
-// Computed in FP64 from q, stored in FP64 and FP32.
+// (isotropic polynomial form, padded for 16-byte rows) or 108 (P itself),
+// for the FP32 near-field kernels: formed in FP32 from q (nine terms per
+// entry; the entries are stored in FP32 either way, and FP64 arithmetic runs
+// at a small fraction of the FP32 rate on this part).
 template <int NCS>
-__global__ void k_src_coef(int64_t N, const double *__restrict__ q, const double *__restrict__ Asym, double hc,
-                           double ha, double *__restrict__ c64, float *__restrict__ c32) {
-    __shared__ double As[6 * 9 * 18];
-    for (int i = threadIdx.x; i < 6 * 9 * 18; i += blockDim.x) As[i] = Asym[i];
+__global__ void k_src_coef(int64_t N, const double *__restrict__ q, const double *__restrict__ Asym, float hc,
+                           float ha, float *__restrict__ c32) {
+    __shared__ float As[6 * 9 * 18];
+    for (int i = threadIdx.x; i < 6 * 9 * 18; i += blockDim.x) As[i] = float(Asym[i]);
     __syncthreads();
     const int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (j >= N) return;
-    double qq[9];
-    for (int i = 0; i < 9; ++i) qq[i] = q[9 * j + i];
+    float qq[9];
+    for (int i = 0; i < 9; ++i) qq[i] = float(q[9 * j + i]);
     constexpr int PV[6] = {0, 1, 2, 1, 0, 0}, PP[6] = {0, 1, 2, 2, 2, 1};
     for (int ab = 0; ab < 6; ++ab) {
-        double P[18];
+        float P[18];
         for (int k = 0; k < 18; ++k) {
-            double s = 0.0;
-            for (int wr = 0; wr < 9; ++wr) s += As[(ab * 9 + wr) * 18 + k] * qq[wr];
+            float s = 0.f;
+            for (int wr = 0; wr < 9; ++wr) s = fmaf(As[(ab * 9 + wr) * 18 + k], qq[wr], s);
             P[k] = s;
         }
         if (NCS == 108) {
-            for (int k = 0; k < 18; ++k) {
-                c64[j * 108 + ab * 18 + k] = P[k];
-                c32[j * 108 + ab * 18 + k] = float(P[k]);
-            }
+            for (int k = 0; k < 18; ++k) c32[j * 108 + ab * 18 + k] = P[k];
         } else {
-            double lin[3] = {0, 0, 0}, cub[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            float lin[3] = {0, 0, 0}, cub[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int pr = 0; pr < 6; ++pr) {
                 const int v = PV[pr], p = PP[pr];
                 for (int qd = 0; qd < 3; ++qd) {
-                    const double w = P[3 * pr + qd];
+                    const float w = P[3 * pr + qd];
                     if (v == p) lin[qd] += -ha * hc * w;
                     if (v == qd) lin[p] += hc * w;
                     if (p == qd) lin[v] += hc * w;
@@ -98,24 +98,15 @@ __global__ void k_src_coef(int64_t N, const double *__restrict__ q, const double
                     if (a > b) { t = a; a = b; b = t; }
                     if (b > c) { t = b; b = c; c = t; }
                     if (a > b) { t = a; a = b; b = t; }
-                    cub[mono_index(a, b, c)] += -3.0 * hc * w;
+                    cub[mono_index(a, b, c)] += -3.f * hc * w;
                 }
             }
-            for (int i = 0; i < 3; ++i) {
-                c64[j * NCS + ab * 13 + i] = lin[i];
-                c32[j * NCS + ab * 13 + i] = float(lin[i]);
-            }
-            for (int i = 0; i < 10; ++i) {
-                c64[j * NCS + ab * 13 + 3 + i] = cub[i];
-                c32[j * NCS + ab * 13 + 3 + i] = float(cub[i]);
-            }
+            for (int i = 0; i < 3; ++i) c32[j * NCS + ab * 13 + i] = lin[i];
+            for (int i = 0; i < 10; ++i) c32[j * NCS + ab * 13 + 3 + i] = cub[i];
         }
     }
     if (NCS == 80)
-        for (int i = 78; i < 80; ++i) {
-            c64[j * 80 + i] = 0.0;
-            c32[j * 80 + i] = 0.f;
-        }
+        for (int i = 78; i < 80; ++i) c32[j * 80 + i] = 0.f;
 }
 
 template <typename R>
@@ -169,7 +160,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
     int p, int L, int64_t nl, float near2, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat,
     const int *__restrict__ tstart, const double *__restrict__ xt, const int64_t *__restrict__ tsid,
     const int *__restrict__ sstart, const float4 *__restrict__ yrel, const double *__restrict__ ys,
-    const float *__restrict__ c32, const double *__restrict__ c64, const int64_t *__restrict__ ssid,
+    const float *__restrict__ c32, const int64_t *__restrict__ ssid,
     const float *__restrict__ S, double *__restrict__ sig, const int2 *__restrict__ items,
     const int *__restrict__ n_items) {
     __shared__ __align__(16) float sP[WARPS][SCH * NCS];
@@ -1046,11 +1037,11 @@ int near_prepare(gbfmm_ctx *ctx) {
     const int64_t N = ctx->N;
     ++ctx->launches;
     if (near_coef_count(ctx) == 80)
-        k_src_coef<80><<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, ctx->mat.hc, ctx->mat.ha,
-                                                                ctx->d_P, ctx->d_Pf);
+        k_src_coef<80><<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, float(ctx->mat.hc),
+                                                                float(ctx->mat.ha), ctx->d_Pf);
     else
-        k_src_coef<108><<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, ctx->mat.hc, ctx->mat.ha,
-                                                                 ctx->d_P, ctx->d_Pf);
+        k_src_coef<108><<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, float(ctx->mat.hc),
+                                                                 float(ctx->mat.ha), ctx->d_Pf);
     CK(cudaGetLastError());
     return GBFMM_OK;
 }
@@ -1201,7 +1192,7 @@ int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t 
     }
 #define GB_NEAR_ARGS                                                                                           \
     ctx->opt.p, ctx->L, nl, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, ctx->d_y, \
-        ctx->d_Pf, ctx->d_P, ctx->d_sid, ctx->d_Sf, sig, items, n_items
+        ctx->d_Pf, ctx->d_sid, ctx->d_Sf, sig, items, n_items
     if (near_coef_count(ctx) == 80)
         k_near_mixed<HM_ISO, 80, 32><<<grid, WARPS * 32, 0, ctx->stream>>>(GB_NEAR_ARGS);
     else if (ctx->mat.cubic)
