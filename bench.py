@@ -91,10 +91,10 @@ def near_flops(wl, work):
 
 # DRAM bytes per target point of one k_near_sym launch (cubic rule, Q = 20), from
 # one ncu capture on the 250,000-segment slab network (dram__bytes_read.sum +
-# dram__bytes_write.sum = 7.43 GB for 1,000,000 points); valid for that kernel
+# dram__bytes_write.sum = 7.94 GB for 1,000,000 points); valid for that kernel
 # version only
-NEAR_SYM_DRAM_BYTES_PER_POINT = 7.430e9 / 1.0e6
-FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 (nominal, profiling recipe table)
+NEAR_SYM_DRAM_BYTES_PER_POINT = 7.943e9 / 1.0e6
+FP64_PEAK_TFLOPS = 1.25          # GB300 FP64, nominal
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 WORKLOADS = {
@@ -507,7 +507,7 @@ def run_ours(args, wl):
         if sym and wl.get("circle_q") == 20:
             traffic = NEAR_SYM_DRAM_BYTES_PER_POINT * work["points"]
             traffic_src = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_near_sym on the "
-                           "250k-segment slab network (7.43 GB for 1,000,000 points), scaled by points")
+                           "250k-segment slab network (7.94 GB for 1,000,000 points), scaled by points")
     else:
         flops = work["m2l_pairs"] * 2 * 54 * p ** 6
         achieved = flops / (m2l_ms / 1e3) / 1e12

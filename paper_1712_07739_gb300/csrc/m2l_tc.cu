@@ -581,43 +581,42 @@ __global__ void k_build_ops(int p, int lat_n, int Np, int Kp, const double *__re
     }
 }
 
-// W (FP32, [cell][p^3 * 9]) -> parity-split BF16 hi / lo, [class][mz][my][mx][Kp] per level
+// W (FP32, [cell][p^3 * 9]) -> parity-split BF16 hi / lo, [class][mz][my][mx][Kp] per level,
+// one block per cell at a time.  Rows of cells without segments are not written: the
+// gather never reads them (their copies are zero fills).
 template <typename E, typename TW>
 __global__ void k_pack_w(int level, int P3, int Kp, const TW *__restrict__ W, const int *__restrict__ occ,
                          const unsigned *__restrict__ wmax, E *__restrict__ hi, E *__restrict__ lo) {
     const int n = 1 << level, m = n / 2;
     const double s = wmax ? double(wscale_of(wmax[level])) : 1.0;
     const int64_t cells = int64_t(n) * n * n;
-    const int64_t total = cells * Kp;
-    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
-         idx += int64_t(gridDim.x) * blockDim.x) {
-        const int k = int(idx % Kp);
-        const int64_t lin = idx / Kp;
+    for (int64_t lin = blockIdx.x; lin < cells; lin += gridDim.x) {
+        const int64_t g = cell_base_d(level) + lin;
+        if (occ[g] <= 0) continue;
         const int x = int(lin % n), y = int((lin / n) % n), z = int(lin / (int64_t(n) * n));
         const int cls = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
-        const int64_t dst = ((((int64_t(cls) * m + z / 2) * m + y / 2) * m + x / 2) * Kp) + k;
-        const int64_t g = cell_base_d(level) + lin;
-        double v = 0.0;
-        if (k < 9 * P3 && occ[g] > 0) v = double(W[g * 9 * P3 + k]);
-        const double vs = s * v;
-        const E h = to_elem<E>(vs);
-        hi[dst] = h;
-        if (lo) lo[dst] = to_elem<E>(vs - elem_value(h));
+        const int64_t row = (((int64_t(cls) * m + z / 2) * m + y / 2) * m + x / 2) * Kp;
+        for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+            const double v = k < 9 * P3 ? double(W[g * 9 * P3 + k]) : 0.0;
+            const double vs = s * v;
+            const E h = to_elem<E>(vs);
+            hi[row + k] = h;
+            if (lo) lo[row + k] = to_elem<E>(vs - elem_value(h));
+        }
     }
 }
 
 // largest |W| over the occupied cells of one level (non-negative floats order
-// like their bit patterns)
+// like their bit patterns), one block per cell at a time
 template <typename TW>
 __global__ void k_wmax(int level, int P3, const TW *__restrict__ W, const int *__restrict__ occ,
                        unsigned *__restrict__ wmax) {
     const int64_t cells = int64_t(1) << (3 * level), base = cell_base_d(level);
-    const int64_t total = cells * 9 * P3;
     float mx = 0.f;
-    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
-         idx += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t g = base + idx / (9 * P3);
-        if (occ[g] > 0) mx = fmaxf(mx, fabsf(float(W[base * 9 * P3 + idx])));
+    for (int64_t lin = blockIdx.x; lin < cells; lin += gridDim.x) {
+        if (occ[base + lin] <= 0) continue;
+        const TW *w = W + (base + lin) * int64_t(9 * P3);
+        for (int k = threadIdx.x; k < 9 * P3; k += blockDim.x) mx = fmaxf(mx, fabsf(float(w[k])));
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(wmax + level, __float_as_uint(mx));
@@ -923,9 +922,9 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     std::memset(&prm, 0, sizeof(prm));
     if (T.fp16) CK(cudaMemsetAsync(T.d_wmax, 0, GB_TC_MAXLEV * sizeof(unsigned), ctx->stream));
     for (int l = 2; l < L; ++l) {
-        const int64_t el = (int64_t(1) << (3 * l)) * T.Kp;
+        const int64_t cells_l = int64_t(1) << (3 * l);
         void *whi = (char *)T.Whi + T.wofs[l] * T.esz, *wlo = (char *)T.Wlo + T.wofs[l] * T.esz;
-        const unsigned gb = nblk(el, 256);
+        const unsigned gb = unsigned(std::min<int64_t>(cells_l, 8 * 152));  // blocks stride over the cells
         if (T.tf32) {
             ++ctx->launches;
             if (W64)
@@ -933,8 +932,7 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
             else
                 k_pack_w<float><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, nullptr, (float *)whi, (float *)nullptr);
         } else if (T.fp16) {
-            const int64_t vals = (int64_t(1) << (3 * l)) * 9 * P3;
-            const unsigned gm = unsigned(std::min<int64_t>(nblk(vals, 256), 4 * 152));
+            const unsigned gm = gb;
             __half *lo = T.split ? (__half *)wlo : nullptr;
             ctx->launches += 2;
             if (W64) {
