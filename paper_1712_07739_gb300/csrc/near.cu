@@ -109,6 +109,27 @@ __global__ void k_src_coef(int64_t N, const double *__restrict__ q, const double
         for (int i = 78; i < 80; ++i) c32[j * 80 + i] = 0.f;
 }
 
+// The 108-entry tensors P for 64 points per block: q staged in shared memory,
+// consecutive threads compute and store consecutive entries (coalesced rows).
+constexpr int kCoefPts = 64;
+__global__ void __launch_bounds__(256) k_src_coef108(int64_t N, const double *__restrict__ q,
+                                                     const double *__restrict__ Asym, float *__restrict__ c32) {
+    __shared__ float As[6 * 9 * 18];
+    __shared__ float sq[kCoefPts][9];
+    for (int i = threadIdx.x; i < 6 * 9 * 18; i += blockDim.x) As[i] = float(Asym[i]);
+    const int64_t j0 = blockIdx.x * int64_t(kCoefPts);
+    const int np = int(min(int64_t(kCoefPts), N - j0));
+    for (int i = threadIdx.x; i < np * 9; i += blockDim.x) (&sq[0][0])[i] = float(q[9 * j0 + i]);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < np * 108; idx += blockDim.x) {
+        const int jl = idx / 108, e = idx - jl * 108, ab = e / 18, k = e - ab * 18;
+        float acc = 0.f;
+#pragma unroll
+        for (int wr = 0; wr < 9; ++wr) acc = fmaf(As[(ab * 9 + wr) * 18 + k], sq[jl][wr], acc);
+        c32[j0 * 108 + idx] = acc;
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ void pair_iso(const R d[3], R ir, const R *c, R acc[6]) {
     const R ir2 = ir * ir, ir3 = ir * ir2, ir5 = ir3 * ir2;
@@ -1040,8 +1061,7 @@ int near_prepare(gbfmm_ctx *ctx) {
         k_src_coef<80><<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, float(ctx->mat.hc),
                                                                 float(ctx->mat.ha), ctx->d_Pf);
     else
-        k_src_coef<108><<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, float(ctx->mat.hc),
-                                                                 float(ctx->mat.ha), ctx->d_Pf);
+        k_src_coef108<<<nblk(N, kCoefPts), 256, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, ctx->d_Pf);
     CK(cudaGetLastError());
     return GBFMM_OK;
 }
