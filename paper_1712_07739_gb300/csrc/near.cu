@@ -60,14 +60,13 @@ __device__ __forceinline__ void monomials(const R d[3], R m[10]) {
     (void)a12;
 }
 
-// Per-source coefficient tensors, stride NCS per point: 78 used of 80
-// (isotropic polynomial form, padded for 16-byte rows) or 108 (P itself),
-// for the FP32 near-field kernels: formed in FP32 from q (nine terms per
-// entry; the entries are stored in FP32 either way, and FP64 arithmetic runs
-// at a small fraction of the FP32 rate on this part).
-template <int NCS>
-__global__ void k_src_coef(int64_t N, const double *__restrict__ q, const double *__restrict__ Asym, float hc,
-                           float ha, float *__restrict__ c32) {
+// Per-source coefficient tensors of the isotropic polynomial form, 80 per
+// point (78 used, padded for 16-byte rows): 3 linear and 10 cubic-monomial
+// coefficients per stress component, from P = sum_wr A q formed in FP32
+// (nine terms per entry; the near field reads FP32 coefficients, and FP64
+// arithmetic runs at a small fraction of the FP32 rate on this part).
+__global__ void k_src_coef80(int64_t N, const double *__restrict__ q, const double *__restrict__ Asym, float hc,
+                             float ha, float *__restrict__ c32) {
     __shared__ float As[6 * 9 * 18];
     for (int i = threadIdx.x; i < 6 * 9 * 18; i += blockDim.x) As[i] = float(Asym[i]);
     __syncthreads();
@@ -83,30 +82,25 @@ __global__ void k_src_coef(int64_t N, const double *__restrict__ q, const double
             for (int wr = 0; wr < 9; ++wr) s = fmaf(As[(ab * 9 + wr) * 18 + k], qq[wr], s);
             P[k] = s;
         }
-        if (NCS == 108) {
-            for (int k = 0; k < 18; ++k) c32[j * 108 + ab * 18 + k] = P[k];
-        } else {
-            float lin[3] = {0, 0, 0}, cub[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            for (int pr = 0; pr < 6; ++pr) {
-                const int v = PV[pr], p = PP[pr];
-                for (int qd = 0; qd < 3; ++qd) {
-                    const float w = P[3 * pr + qd];
-                    if (v == p) lin[qd] += -ha * hc * w;
-                    if (v == qd) lin[p] += hc * w;
-                    if (p == qd) lin[v] += hc * w;
-                    int a = v, b = p, c = qd, t;
-                    if (a > b) { t = a; a = b; b = t; }
-                    if (b > c) { t = b; b = c; c = t; }
-                    if (a > b) { t = a; a = b; b = t; }
-                    cub[mono_index(a, b, c)] += -3.f * hc * w;
-                }
+        float lin[3] = {0, 0, 0}, cub[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int pr = 0; pr < 6; ++pr) {
+            const int v = PV[pr], p = PP[pr];
+            for (int qd = 0; qd < 3; ++qd) {
+                const float w = P[3 * pr + qd];
+                if (v == p) lin[qd] += -ha * hc * w;
+                if (v == qd) lin[p] += hc * w;
+                if (p == qd) lin[v] += hc * w;
+                int a = v, b = p, c = qd, t;
+                if (a > b) { t = a; a = b; b = t; }
+                if (b > c) { t = b; b = c; c = t; }
+                if (a > b) { t = a; a = b; b = t; }
+                cub[mono_index(a, b, c)] += -3.f * hc * w;
             }
-            for (int i = 0; i < 3; ++i) c32[j * NCS + ab * 13 + i] = lin[i];
-            for (int i = 0; i < 10; ++i) c32[j * NCS + ab * 13 + 3 + i] = cub[i];
         }
+        for (int i = 0; i < 3; ++i) c32[j * 80 + ab * 13 + i] = lin[i];
+        for (int i = 0; i < 10; ++i) c32[j * 80 + ab * 13 + 3 + i] = cub[i];
     }
-    if (NCS == 80)
-        for (int i = 78; i < 80; ++i) c32[j * 80 + i] = 0.f;
+    for (int i = 78; i < 80; ++i) c32[j * 80 + i] = 0.f;
 }
 
 // The 108-entry tensors P for 64 points per block: q staged in shared memory,
@@ -1058,8 +1052,8 @@ int near_prepare(gbfmm_ctx *ctx) {
     const int64_t N = ctx->N;
     ++ctx->launches;
     if (near_coef_count(ctx) == 80)
-        k_src_coef<80><<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, float(ctx->mat.hc),
-                                                                float(ctx->mat.ha), ctx->d_Pf);
+        k_src_coef80<<<nblk(N, 128), 128, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, float(ctx->mat.hc),
+                                                              float(ctx->mat.ha), ctx->d_Pf);
     else
         k_src_coef108<<<nblk(N, kCoefPts), 256, 0, ctx->stream>>>(N, ctx->d_q, ctx->d_Asym, ctx->d_Pf);
     CK(cudaGetLastError());
