@@ -128,6 +128,11 @@ WORKLOADS["c3_fp64"] = dict(
          "unit-circle h (cubic form, Q=32), p=6, 7-level octree",
     gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=32, p=6, levels=7,
     precision="fp64")
+WORKLOADS["c3q_iso_fp64"] = dict(
+    desc="250,000 segments (5,000 loops x 50 in 32 Gaussian slabs), isotropic mu=1 nu=0.3, plain FP64 path, p=6, "
+         "6-level octree (the isotropic near field is cheap, so the step shows the FP64 M2L)",
+    gen=WORKLOADS["c3q"]["gen"], C=lambda: synth.isotropic_voigt(1.0, 0.3), h_mode="iso", p=6, levels=6,
+    precision="fp64")
 WORKLOADS["c5"] = dict(
     desc="64 independent cubic networks, N_s log-uniform in [1e4, 2e5] (4,639,301 segments in all), loop "
          "densities 0.2-5x, mixed precision p=6, unit-circle Q=20, depth per network by the autotuner, evaluation "
@@ -415,7 +420,8 @@ def run_ours(args, wl):
     d_segs = torch.tensor(segs, device=dev)
     d_b = torch.tensor(b, device=dev)
     f = gb.FMM(p=wl["p"], levels=args.levels or wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
-               circle_q=wl.get("circle_q", 0), m2l_split=wl.get("m2l_split", 4))
+               circle_q=wl.get("circle_q", 0), m2l_split=wl.get("m2l_split", 4),
+               m2l_fft=None if args.m2l_fft < 0 else args.m2l_fft)
     f.set_material(wl["C"]())
     mlp_info = None
     if wl["h_mode"] == "mlp":
@@ -534,6 +540,7 @@ def run_ours(args, wl):
             "config": {"workload": args.workload, "desc": wl["desc"], "n_segs": n_segs, "levels": info["levels"],
                        "p": p, "precision": wl["precision"], "h_mode": wl["h_mode"],
                        "circle_q": wl.get("circle_q", 0), "m2l_split": wl.get("m2l_split", 4),
+                       "m2l_fft": int(f.options.m2l_fft),
                        "l2": "flushed: 256 MiB write between steps, outside the step events",
                        "step": "fmm_build_tree + fmm_eval_nodal_forces"},
             "stage_ms": {"precontract": st[:, 0].mean(), "p2m_m2m": st[:, 1].mean(), "m2l": m2l_ms,
@@ -563,6 +570,7 @@ def main():
     ap.add_argument("--p", type=int, default=0, help="override the workload's interpolation order")
     ap.add_argument("--m2l-split", type=int, default=-1, help="override the M2L operand mode (fmm options)")
     ap.add_argument("--circle-q", type=int, default=0, help="override the unit-circle points")
+    ap.add_argument("--m2l-fft", type=int, default=-1, help="FP64 path: 1 = M2L through transforms, 0 = dense")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.p:

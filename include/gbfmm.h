@@ -86,11 +86,19 @@ typedef struct {
                               on the offsets with max |o_i| = 2 */
     double mlp_min_dist;   /* GBFMM_H_MLP: near pairs closer than this many source segment
                               lengths use the plain evaluator; 0 = 8 */
+    int m2l_fft;           /* FP64: 1 = M2L through the Toeplitz structure of the operators
+                              (Sec. 4.1, Theorem 1): each offset's node-to-node map applied as
+                              a convolution, by products of discrete Fourier transforms of size
+                              (2p)^3 (54 (2p)^2 (p+1) complex multiply-adds per cell pair
+                              instead of 54 p^6; fmm_default_options); 0 = dense node-pair
+                              sums.  Falls back to the dense form while the stream is being
+                              captured into a graph. */
 } gbfmm_options;
 
 typedef struct gbfmm_ctx gbfmm_ctx;
 
-/* Fill *opt with defaults (p=4, n_gauss=4, levels=0, FP64, H_ISO). */
+/* Fill *opt with defaults (p=4, n_gauss=4, levels=0, FP64, H_ISO, m2l_split = GBFMM_M2L_FP16,
+   m2l_fft = 1). */
 void fmm_default_options(gbfmm_options *opt);
 
 /* Create a context.  opt: host, copied.  cuda_stream: a cudaStream_t or NULL.

@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
         ("p", ctypes.c_int), ("n_gauss", ctypes.c_int), ("levels", ctypes.c_int),
         ("precision", ctypes.c_int), ("h_mode", ctypes.c_int), ("circle_q", ctypes.c_int),
         ("leaf_segments", ctypes.c_int), ("near_fp64", ctypes.c_double), ("m2l_split", ctypes.c_int),
-        ("mlp_min_dist", ctypes.c_double),
+        ("mlp_min_dist", ctypes.c_double), ("m2l_fft", ctypes.c_int),
     ]
 
 
@@ -124,7 +124,7 @@ class FMM:
     """
 
     def __init__(self, p=4, n_gauss=4, levels=0, precision="fp64", h_mode="iso", circle_q=0,
-                 leaf_segments=0, near_fp64=0.0, m2l_split=4, mlp_min_dist=0.0, stream=None):
+                 leaf_segments=0, near_fp64=0.0, m2l_split=4, mlp_min_dist=0.0, m2l_fft=None, stream=None):
         import torch
 
         self._torch = torch
@@ -137,6 +137,8 @@ class FMM:
         o.circle_q, o.leaf_segments, o.near_fp64 = circle_q, leaf_segments, near_fp64
         o.m2l_split = m2l_split
         o.mlp_min_dist = mlp_min_dist
+        if m2l_fft is not None:
+            o.m2l_fft = int(m2l_fft)
         self.options = o
         if stream is None:
             stream = torch.cuda.current_stream()

@@ -120,6 +120,7 @@ extern "C" void fmm_default_options(gbfmm_options *o) {
     o->leaf_segments = 0;
     o->near_fp64 = 0.0;
     o->m2l_split = GBFMM_M2L_FP16;
+    o->m2l_fft = 1;
 }
 
 extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *stream) {
@@ -129,7 +130,7 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
         (opt->levels != 0 && (opt->levels < 3 || opt->levels > 9)) ||
         (opt->precision < GBFMM_FP64 || opt->precision > GBFMM_MIXED_F64T) || opt->h_mode < 0 || opt->h_mode > 2 ||
         opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0) || opt->m2l_split < 0 ||
-        opt->m2l_split > 5)
+        opt->m2l_split > 5 || opt->m2l_fft < 0 || opt->m2l_fft > 1)
         return GBFMM_ERR_INVALID_ARG;
     gbfmm_ctx *ctx = new gbfmm_ctx();
     ctx->opt = *opt;
@@ -170,6 +171,7 @@ extern "C" void fmm_destroy(gbfmm_ctx *ctx) {
     for (void *p : ps)
         if (p) cudaFree(p);
     m2l_tc_free(ctx);
+    m2l_fft_free(ctx);
     mlp_free(ctx);
     {
         NearWork &W = ctx->nw;

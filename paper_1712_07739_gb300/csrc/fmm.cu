@@ -732,7 +732,11 @@ int fmm_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
         CK(cudaGetLastError());
     }
     timer_mark(ctx);
-    if (L >= 3) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap));
+    if (L >= 3 && ctx->opt.m2l_fft && cap == cudaStreamCaptureStatusNone) {
+        if (int rc = m2l_fft_run(ctx, occ, tocc)) return rc;
+    } else if (L >= 3) {
         const int64_t ncell = ctx->n_cells - cell_base(2);
         const int bd = ((P3 + 31) / 32) * 32;
         ++ctx->launches;

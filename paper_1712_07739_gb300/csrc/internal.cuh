@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/gbfmm.h"
+#include "m2l_fft.cuh"
 #include "m2l_tc.cuh"
 
 #define GB_MAXP 8
@@ -89,6 +90,8 @@ struct gbfmm_ctx {
 
     // mixed-precision M2L on tensor cores
     TcPlan tc;
+    // FP64 M2L through transforms (gbfmm_options.m2l_fft)
+    FftPlan fft;
     // learned h
     MlpState mlp;
     NearWork nw;

@@ -197,6 +197,7 @@ extern "C" int fmm_set_material(gbfmm_ctx *ctx, const double *V) {
         ctx->lat_n = 0;
         ctx->tc.Thi = ctx->tc.Tlo = nullptr;
         ctx->tc.ready_ops = false;
+        ctx->fft.ready = false;
         ctx->borrowed_material = false;
     }
     if (!V) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_set_material: null stiffness");
@@ -247,6 +248,7 @@ extern "C" int fmm_set_material(gbfmm_ctx *ctx, const double *V) {
         m.ha = 3.0 - 4.0 * nu;
     }
     ctx->mat = m;
+    ctx->fft.ready = false;  // the transformed operators belong to the previous medium
     int rc = material_setup(ctx);
     if (rc) return rc;
     ctx->have_material = true;

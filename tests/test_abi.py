@@ -45,10 +45,27 @@ def test_missing_library_fails_loudly(tmp_path):
             gb._lib = gb._lib_saved
 
 
-def test_options_layout_matches_header():
+def test_options_layout_matches_header(tmp_path):
+    """The ctypes mirror of gbfmm_options has the header's size and field
+    offsets (a C program compiled against include/gbfmm.h prints them)."""
     import ctypes
+    import shutil
+    import subprocess
 
     import paper_1712_07739_gb300 as gb
 
-    # 7 ints + pad + double + int + pad + double = 56 bytes on LP64
-    assert ctypes.sizeof(gb.Options) == 56
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = [f[0] for f in gb.Options._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gbfmm.h"', "int main(void) {",
+             '  printf("%zu\\n", sizeof(gbfmm_options));']
+    lines += [f'  printf("%zu\\n", offsetof(gbfmm_options, {n}));' for n in names]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(gb.Options)
+    assert vals[1:] == [getattr(gb.Options, n).offset for n in names]

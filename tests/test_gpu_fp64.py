@@ -150,3 +150,51 @@ def test_errors_are_reported():
     nodes[1] = [0.3, 0.2, 0.1]
     f.build(_gpu(nodes), _gpu(segs), _gpu(np.ones((2, 3))))
     assert np.isfinite(f.nodal_forces().cpu().numpy()).all()
+
+
+# ---------------------------------------------------------------- M2L through transforms
+# The Toeplitz form (Sec. 4.1, Theorem 1) computes the same Algorithm 2: each
+# offset's node-to-node map is a convolution, applied through discrete
+# Fourier transforms of size (2p)^3.  It must meet the same 1e-10 bar against
+# the oracle, and agree with the dense FP64 pass to rounding.
+
+@pytest.mark.parametrize("p,L", [(2, 3), (3, 4), (6, 4)])
+def test_fft_m2l_matches_algorithm2(p, L):
+    nodes, segs, b = synth.polygon_loops(n_segs=600, n_loops=20, seed=11)
+    f = _fmm(nodes, segs, b, ISO_C, p=p, levels=L, m2l_fft=1)
+    F = f.nodal_forces().cpu().numpy()
+    assert f.device_status() == 0
+    Fo, _ = _oracle_forces(ISO, nodes, segs, b, p, L)
+    err = oracle.rel_l2(F, Fo)
+    print(f"FFT M2L p={p} L={L} vs Algorithm 2: {err:.3e}")
+    assert err <= TOL_FP64
+
+
+def test_fft_m2l_free_targets_match_algorithm2(c1):
+    nodes, segs, b = c1
+    f = _fmm(nodes, segs, b, ISO_C, p=4, levels=3, m2l_fft=1)
+    rng = np.random.default_rng(5)
+    y, q, sid = oracle.quadrature(nodes, segs, b, 4)
+    lo, hi = y.min(0), y.max(0)
+    xt = lo + (hi - lo) * rng.uniform(0.02, 0.98, (300, 3))
+    s = f.stress(_gpu(xt)).cpu().numpy()
+    so = oracle_b.lagrange_fmm(ISO, y, q, sid, p=4, L=3, xt=xt, tseg=-np.ones(len(xt), np.int64))
+    assert oracle.rel_l2(s, so) <= TOL_FP64
+
+
+@pytest.mark.parametrize("p,L", [(5, 4), (7, 4), (8, 3)])
+def test_fft_m2l_equals_dense_pass(p, L):
+    """Cubic medium (unit-circle h), nodal forces and free-target stresses:
+    the transform form and the dense node-pair sums agree to rounding."""
+    nodes, segs, b = synth.polygon_loops(n_segs=800, n_loops=25, seed=13)
+    C6 = synth.cubic_voigt()
+    kw = dict(p=p, levels=L, h_mode="circle", circle_q=32)
+    fd = _fmm(nodes, segs, b, C6, m2l_fft=0, **kw)
+    ff = _fmm(nodes, segs, b, C6, m2l_fft=1, **kw)
+    Fd, Ff = fd.nodal_forces().cpu().numpy(), ff.nodal_forces().cpu().numpy()
+    rng = np.random.default_rng(6)
+    xt = nodes.min(0) + (nodes.max(0) - nodes.min(0)) * rng.uniform(0.05, 0.95, (200, 3))
+    sd, sf = fd.stress(_gpu(xt)).cpu().numpy(), ff.stress(_gpu(xt)).cpu().numpy()
+    e_f, e_s = oracle.rel_l2(Ff, Fd), oracle.rel_l2(sf, sd)
+    print(f"FFT vs dense M2L p={p} L={L}: forces {e_f:.3e}, stresses {e_s:.3e}")
+    assert e_f <= 1e-12 and e_s <= 1e-12
