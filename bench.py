@@ -515,9 +515,15 @@ def run_ours(args, wl):
             traffic_src = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_near_sym on the "
                            "250k-segment slab network (7.94 GB for 1,000,000 points), scaled by points")
     else:
-        flops = work["m2l_pairs"] * 2 * 54 * p ** 6
+        fft = fp64 and int(f.options.m2l_fft) == 1
+        # dense: 2*54*p^6 per cell pair; through transforms: 54 complex multiply-adds
+        # (8 FLOP) at each of (2p)^2 (p+1) frequencies per cell pair
+        per_pair = 8 * 54 * (2 * p) ** 2 * (p + 1) if fft else 2 * 54 * p ** 6
+        flops = work["m2l_pairs"] * per_pair
         achieved = flops / (m2l_ms / 1e3) / 1e12
-        if fp64:
+        if fft:
+            dom, bound, src = "k_m2l_fft (FP64 M2L through transforms)", "alu", "FP64 1.25 TFLOP/s nominal (recipe)"
+        elif fp64:
             dom, bound, src = "k_m2l_f64 (M2L)", "alu", "FP64 1.25 TFLOP/s nominal (recipe)"
         else:
             dom, bound = "k_m2l_tc (M2L, tcgen05 BF16)", "tensor"
@@ -525,7 +531,7 @@ def run_ours(args, wl):
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": src,
                 "work": "algorithmic: near pairs x FLOP/pair (h once per unordered pair when h is the unit-circle "
-                        "rule) + L2P, or M2L cell pairs x 2*54*p^6"}
+                        "rule) + L2P, or M2L cell pairs x 2*54*p^6 (x 8*54*(2p)^2*(p+1) through transforms)"}
 
     if rank == 0:
         cpu = None
