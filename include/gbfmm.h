@@ -270,7 +270,7 @@ int fmm_mlp_labels(gbfmm_ctx *ctx, int64_t n, const float *dirs, float *y);
 int fmm_mlp_train(gbfmm_ctx *ctx, int64_t n, const float *dirs, int epochs, int batch, double lr,
                   uint64_t seed, float *final_loss);
 
-/* Judge the network against the plain evaluator per angular bin (5 x 256
+/* Assess the network against the plain evaluator per angular bin (5 x 256
  * bins of direction, 64 sample directions each) and record which bins the
  * near field of GBFMM_H_MLP must evaluate with the plain rule: those whose
  * largest component error exceeds bin_tol x (RMS of h).  fallback_frac

@@ -533,7 +533,7 @@ extern "C" int fmm_mlp_train(gbfmm_ctx *ctx, int64_t n, const float *dirs, int e
     return GBFMM_OK;
 }
 
-// Judge the network per angular bin against the plain evaluator: 64 directions
+// Assess the network per angular bin against the plain evaluator: 64 directions
 // per bin of the near-field kernel's binning (dominant axis face +z, +x, -x,
 // +y, -y and a 16 x 16 grid of the other two components); a bin whose largest
 // component error exceeds bin_tol x (RMS of h over all samples) is flagged

@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
     float4 *wy = sy[warp];
     int *wsd = ssd[warp];
     for (int r0 = t0; r0 < t1; r0 += 32) {
-        // tg targets this round, 32 / tg lanes per target splitting the sources
+        // tg targets in this pass, 32 / tg lanes per target splitting the sources
         const int nrem = min(32, t1 - r0);
         int tg = 1;
         while (tg < nrem) tg <<= 1;
