@@ -65,6 +65,7 @@ extern "C" {
 #define GBFMM_M2L_TF32 3            /* FP32 operands, kind::tf32 */
 #define GBFMM_M2L_FP16 4            /* FP16, multipole values scaled per level (fmm_default_options) */
 #define GBFMM_M2L_FP16_SPLIT 5      /* FP16 scaled, residual passes on the offsets with max |o_i| = 2 */
+#define GBFMM_M2L_FP16_SPLIT_ALL 6  /* FP16 scaled, residual passes on all 316 offsets */
 
 typedef struct {
     int p;                 /* Lagrange nodes per dimension, 2..8 (Sec. 4.1) */
@@ -83,7 +84,8 @@ typedef struct {
                               per-level scaling of the multipole values (a power of two from
                               each level's largest |W|) and one power-of-two scale for the
                               operators (fmm_default_options), 5 = as 4 plus residual passes
-                              on the offsets with max |o_i| = 2 */
+                              on the offsets with max |o_i| = 2, 6 = as 4 plus residual
+                              passes on all 316 offsets */
     double mlp_min_dist;   /* GBFMM_H_MLP: near pairs closer than this many source segment
                               lengths use the plain evaluator; 0 = 8 */
     int m2l_fft;           /* FP64: 1 = M2L through the Toeplitz structure of the operators
@@ -93,6 +95,11 @@ typedef struct {
                               instead of 54 p^6; fmm_default_options); 0 = dense node-pair
                               sums.  Falls back to the dense form while the stream is being
                               captured into a graph. */
+    int m2l_chunks;        /* MIXED: the tensor-core M2L sums each class's 189 offsets in this
+                              many consecutive runs, each accumulated in tensor memory from
+                              zero and added to the local values in FP32 (FP64 with
+                              GBFMM_MIXED_F64T); shorter accumulation chains, one launch per
+                              run.  0 = 1. */
 } gbfmm_options;
 
 typedef struct gbfmm_ctx gbfmm_ctx;
@@ -204,6 +211,21 @@ int fmm_device_status(gbfmm_ctx *ctx, int *status);
  * GBFMM_ERR_TIMEOUT through fmm_device_status and its outputs are invalid.
  * Nothing faults and the context stays usable.  Errors: INVALID_ARG. */
 int fmm_inject_fault(gbfmm_ctx *ctx, int kind);
+
+/* ------------------------------------------------------------------------
+ * Measurement (not part of the method): the device's fused multiply-add
+ * throughput, the denominator of the near-field and FP64-pass rooflines.
+ * ------------------------------------------------------------------------ */
+
+/* Measured peak rate in TFLOP/s (2 per multiply-add) on the current device:
+ * kind 0 = FP32 scalar FMA, 1 = FP32 packed pairs (two multiply-adds per
+ * instruction), 2 = FP64 FMA.  Every thread of 8 blocks per SM runs 8
+ * independent chains x <- x/2 + 1 (CUDA events, on cuda_stream, which may be
+ * NULL); the launch grows until it lasts ~150 ms and the best of three such
+ * launches is reported.  Each chain must end exactly at its fixed point 2
+ * (self-check).  Synchronises.  Allocates 4 bytes of device memory.
+ * Errors: INVALID_ARG, CUDA, DEGENERATE (a chain missed its fixed point). */
+int fmm_probe_fma(int kind, void *cuda_stream, double *tflops);
 
 /* ------------------------------------------------------------------------
  * Batches of independent segment networks.

@@ -1,19 +1,28 @@
-"""The Lagrange FMM by its algorithm, in plain NumPy, for tiny inputs.
+"""The Lagrange FMM by its definition, in plain NumPy, for tiny inputs.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-``lagrange_fmm`` follows Algorithm 2 of arXiv:1712.07739 step by step on a
-uniform octree with levels 0 .. L-1:
+The method (arXiv:1712.07739, Sec. 4) replaces the kernel between two
+well-separated cells by its tensor-product Lagrange interpolant on p
+equispaced nodes per axis in each cell (Sec. 4.1, Eq. "interpolant"), so the
+far-field sum at a target factors (Sec. 4.3, Eq. "far-field") into: the
+source strengths weighted by the source cell's basis functions at the
+source points (the multipole weights W of each node), the node-to-node
+kernel matrix of the cell pair (Eq. "m2l") applied to them, and the target
+cell's basis functions at the target.  On a uniform octree with levels
+0 .. L-1 (Algorithm 2) the weights of a parent follow from its children's by
+evaluating the parent's basis at the child nodes (exact: the child
+interpolant is a polynomial of the same degree), each cell receives the
+node-kernel sums of its interaction list, a child receives its parent's
+local values interpolated to its nodes, and a leaf's targets get the local
+values interpolated to them plus the direct sum of Eq. "stress3" over the
+neighbouring leaves.
 
-  (1.a) P2M  W_m  = sum_{y_j in I} L_p(ybar_m, y_j) q_j              (leaves)
-  (1.b) M2M  W_m' = sum_{J in C(I)} sum_m L_p(ybar_m', ybar_m) W_m   (up)
-  (2)   M2L  s(xbar_l) = sum_{J in I(I)} sum_m K(xbar_l - ybar_m) W_m
-  (3.a) L2L  s(xbar_l') += sum_l L_p(xbar_l', xbar_l) s(xbar_l)       (down)
-  (3.b) L2P  s(x_i) = sum_l L_p(xbar_l, x_i) s(xbar_l) + near sum over N(I)
-
-``pairwise_far_field`` is Algorithm 1 applied to every interaction-list pair
-at every level (no M2M / L2L); the two agree to rounding because same-degree
-Lagrange interpolation reproduces the parent basis exactly, which is a pin.
+``lagrange_fmm`` computes that result level by level.
+``pairwise_far_field`` evaluates Eq. "far-field" separately for every
+(target cell, interaction-list cell) pair at every level, with no
+child/parent transfers; the two agree to rounding because the transfers are
+exact, which is a pin.
 
 Conventions (readings of the paper where it is silent):
 * root cube: edge H = s (1 + 2^-10), s the largest extent of the source
@@ -121,8 +130,6 @@ def _apply_offset(mat, p, h, o, Wstack, chunk=64):
 
 def _near(mat, xt, tseg, tleaf, ys, qs, sseg, sleaf, n):
     out = np.zeros((len(xt), 6))
-    skey = sleaf[:, 0] * n * n + sleaf[:, 1] * n + sleaf[:, 2]
-    order = np.argsort(skey, kind="stable")
     for key in np.unique(tleaf[:, 0] * n * n + tleaf[:, 1] * n + tleaf[:, 2]):
         B = np.array([key // (n * n), (key // n) % n, key % n])
         ti = np.nonzero((tleaf == B).all(axis=1))[0]
@@ -133,12 +140,12 @@ def _near(mat, xt, tseg, tleaf, ys, qs, sseg, sleaf, n):
         if len(sj) == 0:
             continue
         out[ti] = direct_stress(mat, xt[ti], tseg[ti], ys[sj], qs[sj], sseg[sj])
-    del order
     return out
 
 
 def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
-    """Stress [n_t, 6] at targets by Algorithm 2 (targets default to sources)."""
+    """Stress [n_t, 6] at targets by the multilevel Lagrange FMM (Algorithm 2; targets
+    default to sources)."""
     ys = np.asarray(ys, dtype=np.float64)
     qs = np.asarray(qs, dtype=np.float64).reshape(-1, 9)
     if xt is None:
@@ -147,14 +154,14 @@ def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
     lf = L - 1
     nL = 1 << lf
     P3 = p ** 3
-    # (1.a) P2M at the leaves
+    # multipole weights of the leaves: source strengths times the leaf basis at the points
     W = {lf: np.zeros((nL, nL, nL, P3, 9))}
     sl = cell_of(ys, origin, H, lf)
     hL = H / nL
     t = (ys - (origin + sl * hL)) / hL
     Lb = basis_3d(t, p)
     np.add.at(W[lf], (sl[:, 0], sl[:, 1], sl[:, 2]), Lb[:, :, None] * qs[:, None, :])
-    # (1.b) M2M up the tree
+    # weights of the parents: the parent basis at the child nodes (upward)
     M = child_transfer(p)
     for lev in range(lf - 1, 1, -1):
         n = 1 << lev
@@ -165,7 +172,7 @@ def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
             Wp += np.einsum("Aa,Bb,Cc,xyzabcw->xyzABCw", M[c[0]], M[c[1]], M[c[2]], ch).reshape(
                 n, n, n, P3, 9)
         W[lev] = Wp
-    # (2) M2L at every level >= 2, pairs grouped by offset
+    # node-kernel sums over the interaction lists at every level >= 2, pairs grouped by offset
     S = {}
     for lev in range(2, lf + 1):
         n = 1 << lev
@@ -190,14 +197,14 @@ def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
             res = _apply_offset(mat, p, h, o, Ws)
             for (B, _), r in zip(pairs, res):
                 S[lev][B] += r
-    # (3.a) L2L down the tree
+    # local values of the children: the parent's interpolated to the child nodes (downward)
     for lev in range(3, lf + 1):
         n = 1 << (lev - 1)
         Sp = S[lev - 1].reshape(n, n, n, p, p, p, 6)
         for c in itertools.product((0, 1), repeat=3):
             add = np.einsum("Aa,Bb,Cc,xyzABCs->xyzabcs", M[c[0]], M[c[1]], M[c[2]], Sp)
             S[lev][c[0]::2, c[1]::2, c[2]::2] += add.reshape(n, n, n, P3, 6)
-    # (3.b) L2P + near field
+    # local values interpolated to the targets, plus the direct near sum
     tl = cell_of(xt, origin, H, lf)
     out = np.zeros((len(xt), 6))
     if lf >= 2:
@@ -208,9 +215,9 @@ def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
 
 
 def pairwise_far_field(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
-    """Far field of the same tree by Algorithm 1 applied to each (B, A) pair
-    with A in I(B), at each level >= 2 (anterpolate from A's points, node
-    kernel, interpolate to B's points).  Near sum included."""
+    """Far field of the same tree by Eq. "far-field" for each (B, A) pair with
+    A in I(B), at each level >= 2: the weights of A's points on A's nodes, the
+    node kernel of the pair, B's basis at B's points.  Near sum included."""
     ys = np.asarray(ys, dtype=np.float64)
     qs = np.asarray(qs, dtype=np.float64).reshape(-1, 9)
     if xt is None:
@@ -232,9 +239,9 @@ def pairwise_far_field(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
                 if len(sj) == 0:
                     continue
                 LA = basis_3d((ys[sj] - (origin + np.asarray(A) * h)) / h, p)
-                Wm = LA.T @ qs[sj]                                   # step 1
-                sl = _apply_offset(mat, p, h, o, Wm[None])[0]        # step 2
-                out[ti] += LB @ sl                                    # step 3
+                Wm = LA.T @ qs[sj]                                   # weights on A's nodes
+                sl = _apply_offset(mat, p, h, o, Wm[None])[0]        # node kernel of (B, A)
+                out[ti] += LB @ sl                                    # B's basis at the targets
     nL = 1 << lf
     out += _near(mat, xt, np.asarray(tseg), cell_of(xt, origin, H, lf), ys, qs,
                  np.asarray(sseg), cell_of(ys, origin, H, lf), nL)

@@ -29,7 +29,7 @@ EXPORTS = [
     "fmm_default_options", "fmm_create", "fmm_destroy", "fmm_last_error",
     "fmm_set_material", "fmm_build_tree", "fmm_eval_stress", "fmm_eval_nodal_forces",
     "fmm_tree_info", "fmm_set_timing", "fmm_stage_times", "fmm_launch_count", "fmm_work_counts",
-    "fmm_device_status", "fmm_inject_fault",
+    "fmm_device_status", "fmm_inject_fault", "fmm_probe_fma",
     "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
     "fmm_mlp_eval_noalloc", "fmm_mlp_calibrate",
     "fmm_batch_create", "fmm_batch_destroy", "fmm_batch_last_error", "fmm_batch_set_material", "fmm_batch_build",
@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
         ("p", ctypes.c_int), ("n_gauss", ctypes.c_int), ("levels", ctypes.c_int),
         ("precision", ctypes.c_int), ("h_mode", ctypes.c_int), ("circle_q", ctypes.c_int),
         ("leaf_segments", ctypes.c_int), ("near_fp64", ctypes.c_double), ("m2l_split", ctypes.c_int),
-        ("mlp_min_dist", ctypes.c_double), ("m2l_fft", ctypes.c_int),
+        ("mlp_min_dist", ctypes.c_double), ("m2l_fft", ctypes.c_int), ("m2l_chunks", ctypes.c_int),
     ]
 
 
@@ -81,6 +81,8 @@ def load_library(path: str = LIB_PATH):
     L.fmm_work_counts.argtypes = [vp, ctypes.POINTER(i64)]
     L.fmm_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.fmm_inject_fault.argtypes = [vp, ctypes.c_int]
+    L.fmm_probe_fma.argtypes = [ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]
+    L.fmm_probe_fma.restype = ctypes.c_int
     fp = ctypes.POINTER(ctypes.c_float)
     L.fmm_mlp_train.argtypes = [vp, i64, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, fp]
     L.fmm_mlp_get.argtypes = [vp, fp, fp]
@@ -115,6 +117,21 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
+def probe_fma(kind, stream=None):
+    """Measured FMA throughput of the current device in TFLOP/s: kind "fp32",
+    "fp32x2" (packed pairs) or "fp64" (self-checking chains, ~0.5 s)."""
+    import torch
+
+    lib = load_library()
+    k = {"fp32": 0, "fp32x2": 1, "fp64": 2}[kind]
+    st = stream if stream is not None else torch.cuda.current_stream()
+    v = ctypes.c_double()
+    rc = lib.fmm_probe_fma(k, ctypes.c_void_p(st.cuda_stream), ctypes.byref(v))
+    if rc != 0:
+        raise GbfmmError(f"fmm_probe_fma({kind}) failed ({rc})")
+    return v.value
+
+
 class FMM:
     """One Lagrange-FMM context on the current CUDA device and stream.
 
@@ -124,7 +141,8 @@ class FMM:
     """
 
     def __init__(self, p=4, n_gauss=4, levels=0, precision="fp64", h_mode="iso", circle_q=0,
-                 leaf_segments=0, near_fp64=0.0, m2l_split=4, mlp_min_dist=0.0, m2l_fft=None, stream=None):
+                 leaf_segments=0, near_fp64=0.0, m2l_split=4, mlp_min_dist=0.0, m2l_fft=None, m2l_chunks=None,
+                 stream=None):
         import torch
 
         self._torch = torch
@@ -139,6 +157,8 @@ class FMM:
         o.mlp_min_dist = mlp_min_dist
         if m2l_fft is not None:
             o.m2l_fft = int(m2l_fft)
+        if m2l_chunks is not None:
+            o.m2l_chunks = int(m2l_chunks)
         self.options = o
         if stream is None:
             stream = torch.cuda.current_stream()

@@ -62,47 +62,30 @@ static int ensure_tree_buffers(gbfmm_ctx *ctx) {
     const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p;
     const bool fp64 = ctx->opt.precision == GBFMM_FP64;
     const bool w64 = ctx->opt.precision != GBFMM_MIXED;  // FP64 multipole and local values
-    if (N > ctx->cap_N) {
-        release(ctx->d_y); release(ctx->d_q); release(ctx->d_sid); release(ctx->d_slen); release(ctx->d_pos);
-        release(ctx->d_pleaf); release(ctx->d_sig); release(ctx->d_y0); release(ctx->d_q0);
-        if (fp64) release(ctx->d_P);
-        release(ctx->d_leaf_of); release(ctx->d_perm);
-        CK(cudaMalloc(&ctx->d_y, N * 3 * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_q, N * 9 * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_sid, N * sizeof(int64_t)));
-        CK(cudaMalloc(&ctx->d_slen, N * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_pos, N * sizeof(int)));
-        CK(cudaMalloc(&ctx->d_pleaf, N * sizeof(int)));
-        CK(cudaMalloc(&ctx->d_sig, N * 6 * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_y0, N * 3 * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_q0, N * 9 * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_leaf_of, N * sizeof(int)));
-        CK(cudaMalloc(&ctx->d_perm, N * sizeof(int)));
-        if (fp64) CK(cudaMalloc(&ctx->d_P, N * 108 * sizeof(double)));
-        ctx->cap_N = N;
+    {
+        GrowBuf b[12] = {{(void **)&ctx->d_y, N * 3 * sizeof(double)},  {(void **)&ctx->d_q, N * 9 * sizeof(double)},
+                         {(void **)&ctx->d_sid, N * sizeof(int64_t)},   {(void **)&ctx->d_slen, N * sizeof(double)},
+                         {(void **)&ctx->d_pos, N * sizeof(int)},       {(void **)&ctx->d_pleaf, N * sizeof(int)},
+                         {(void **)&ctx->d_sig, N * 6 * sizeof(double)}, {(void **)&ctx->d_y0, N * 3 * sizeof(double)},
+                         {(void **)&ctx->d_q0, N * 9 * sizeof(double)}, {(void **)&ctx->d_leaf_of, N * sizeof(int)},
+                         {(void **)&ctx->d_perm, N * sizeof(int)},      {(void **)&ctx->d_P, N * 108 * sizeof(double)}};
+        if (int rc = grow_dev(ctx, ctx->cap_N, N, b, fp64 ? 12 : 11, "points")) return rc;
     }
-    if (ns > ctx->cap_segs) {
-        release(ctx->d_len0);
-        CK(cudaMalloc(&ctx->d_len0, ns * sizeof(double)));
-        ctx->cap_segs = ns;
+    if (int rc = grow_dev(ctx, ctx->cap_segs, ns, {{(void **)&ctx->d_len0, ns * sizeof(double)}}, "segments"))
+        return rc;
+    {
+        GrowBuf b[3] = {{(void **)&ctx->d_tmp_i, 2 * nc * sizeof(int)},
+                        {(void **)&ctx->d_W, nc * P3 * 9 * sizeof(double)},
+                        {(void **)&ctx->d_S, nc * P3 * 6 * sizeof(double)}};
+        if (int rc = grow_dev(ctx, ctx->cap_cells, nc, b, w64 ? 3 : 1, "cells")) return rc;
     }
-    if (nc > ctx->cap_cells) {
-        release(ctx->d_W); release(ctx->d_S); release(ctx->d_tmp_i);
-        CK(cudaMalloc(&ctx->d_tmp_i, 2 * nc * sizeof(int)));
-        if (w64) {
-            CK(cudaMalloc(&ctx->d_W, nc * P3 * 9 * sizeof(double)));
-            CK(cudaMalloc(&ctx->d_S, nc * P3 * 6 * sizeof(double)));
-        }
-        ctx->cap_cells = nc;
-    }
-    if (nl > ctx->cap_leaves) {
-        release(ctx->d_leaf_start); release(ctx->d_t_start); release(ctx->d_cnt); release(ctx->d_cursor);
-        CK(cudaMalloc(&ctx->d_leaf_start, (nl + 1) * sizeof(int)));
-        CK(cudaMalloc(&ctx->d_t_start, (nl + 1) * sizeof(int)));
-        CK(cudaMalloc(&ctx->d_cnt, nl * sizeof(int)));
-        CK(cudaMalloc(&ctx->d_cursor, nl * sizeof(int)));
-        ctx->cap_leaves = nl;
-    }
+    if (int rc = grow_dev(ctx, ctx->cap_leaves, nl,
+                          {{(void **)&ctx->d_leaf_start, (nl + 1) * sizeof(int)},
+                           {(void **)&ctx->d_t_start, (nl + 1) * sizeof(int)},
+                           {(void **)&ctx->d_cnt, nl * sizeof(int)},
+                           {(void **)&ctx->d_cursor, nl * sizeof(int)}},
+                          "leaves"))
+        return rc;
     if (!ctx->d_part) CK(cudaMalloc(&ctx->d_part, 512 * 6 * sizeof(double)));
     if (!ctx->d_bad) CK(cudaMalloc(&ctx->d_bad, sizeof(int)));
     return GBFMM_OK;
@@ -130,7 +113,8 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
         (opt->levels != 0 && (opt->levels < 3 || opt->levels > 9)) ||
         (opt->precision < GBFMM_FP64 || opt->precision > GBFMM_MIXED_F64T) || opt->h_mode < 0 || opt->h_mode > 2 ||
         opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0) || opt->m2l_split < 0 ||
-        opt->m2l_split > 5 || opt->m2l_fft < 0 || opt->m2l_fft > 1)
+        opt->m2l_split > 6 || opt->m2l_fft < 0 || opt->m2l_fft > 1 || opt->m2l_chunks < 0 ||
+        opt->m2l_chunks > 189)
         return GBFMM_ERR_INVALID_ARG;
     gbfmm_ctx *ctx = new gbfmm_ctx();
     ctx->opt = *opt;

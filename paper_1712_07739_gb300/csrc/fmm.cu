@@ -1,10 +1,10 @@
-// The Lagrange FMM pass of Algorithm 2, FP64 path:
+// The Lagrange FMM pass (Sec. 4, Algorithm 2), FP64 path:
 //   precontract  P_j[ab][k] = sum_wr Asym[ab][wr][k] q_j[wr]   (per source)
-//   (1.a) P2M    W_m = sum_{y_j in leaf} L_p(ybar_m, y_j) q_j
-//   (1.b) M2M    W_m' = sum_children sum_m L_p(ybar_m', ybar_m) W_m
-//   (2)   M2L    s(xbar_l) = sum_{A in I(B)} sum_m K(xbar_l - ybar_m) W_m
-//   (3.a) L2L    s(xbar_l') += sum_l L_p(xbar_l', xbar_l) s(xbar_l)
-//   (3.b) L2P    s(x_i) = sum_l L_p(xbar_l, x_i) s(xbar_l) + near field over N(leaf)
+//   P2M  W_m = sum_{y_j in leaf} L_p(ybar_m, y_j) q_j          (Eq. "far-field", source side)
+//   M2M  W_m' = sum_children sum_m L_p(ybar_m', ybar_m) W_m    (parent basis at the child nodes)
+//   M2L  s(xbar_l) = sum_{A in I(B)} sum_m K(xbar_l - ybar_m) W_m   (Eq. "m2l")
+//   L2L  s(xbar_l') += sum_l L_p(xbar_l', xbar_l) s(xbar_l)    (parent local values at the child nodes)
+//   L2P  s(x_i) = sum_l L_p(xbar_l, x_i) s(xbar_l) + near field over N(leaf)
 // Nodes of a cell of edge h at corner c are c + h t_a, t_a = a/(p-1)
 // (Sec. 4.1); node index m = (mz p + my) p + mx.
 #include <cmath>
@@ -819,23 +819,15 @@ int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t 
 int mixed_alloc(gbfmm_ctx *ctx) {
     const int64_t N = ctx->N, nc = ctx->n_cells;
     const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p;
-    if (N > ctx->mx_cap_N) {
-        if (ctx->d_Pf) cudaFree(ctx->d_Pf);
-        if (ctx->d_yrel) cudaFree(ctx->d_yrel);
-        ctx->d_Pf = nullptr;
-        ctx->d_yrel = nullptr;
-        CK(cudaMalloc(&ctx->d_Pf, N * 108 * sizeof(float)));
-        CK(cudaMalloc(&ctx->d_yrel, N * sizeof(float4)));
-        ctx->mx_cap_N = N;
-    }
-    if (nc > ctx->mx_cap_cells) {
-        if (ctx->d_Wf) cudaFree(ctx->d_Wf);
-        if (ctx->d_Sf) cudaFree(ctx->d_Sf);
-        ctx->d_Wf = ctx->d_Sf = nullptr;
-        CK(cudaMalloc(&ctx->d_Wf, nc * P3 * 9 * sizeof(float)));
-        CK(cudaMalloc(&ctx->d_Sf, nc * P3 * 6 * sizeof(float)));
-        ctx->mx_cap_cells = nc;
-    }
+    if (int rc = grow_dev(ctx, ctx->mx_cap_N, N,
+                          {{(void **)&ctx->d_Pf, N * 108 * sizeof(float)}, {(void **)&ctx->d_yrel, N * sizeof(float4)}},
+                          "mixed-pass points"))
+        return rc;
+    if (int rc = grow_dev(ctx, ctx->mx_cap_cells, nc,
+                          {{(void **)&ctx->d_Wf, nc * P3 * 9 * sizeof(float)},
+                           {(void **)&ctx->d_Sf, nc * P3 * 6 * sizeof(float)}},
+                          "mixed-pass cells"))
+        return rc;
     if (int rc = near_alloc(ctx, N)) return rc;
     if (int rc = near_sym_alloc(ctx)) return rc;
     if (!ctx->tc.ready_ops) {

@@ -135,7 +135,8 @@ struct gbfmm_ctx {
     int64_t mx_cap_N = 0, mx_cap_cells = 0;
 
     // free-target evaluation
-    int64_t t_cap = 0;
+    int64_t t_cap = 0;                 // targets the buffers below hold (0 after a failed allocation)
+    int64_t t_cap_leaves = 0;          // leaves the target scratch was sized for
     int *d_t_pos = nullptr;     // target -> sorted slot
     int *d_t_start = nullptr;   // [n_leaves + 1]
     double *d_t_x = nullptr;    // sorted targets
@@ -154,6 +155,22 @@ int set_err(gbfmm_ctx *c, int code, const std::string &msg);
 // of device memory: sizes, depth, options and every device pointer.  A graph
 // recorded from an evaluation stays valid while this value is unchanged.
 uint64_t layout_hash(const gbfmm_ctx *ctx);  // api.cu
+#include "grow.h"
+
+// grow_set on device memory (cudaMalloc / cudaFree); a failed allocation sets
+// the context's error and returns GBFMM_ERR_CUDA
+inline int grow_dev(gbfmm_ctx *ctx, int64_t &cap, int64_t need, const GrowBuf *bufs, int n, const char *what) {
+    const int rc = grow_set(
+        cap, need, bufs, n, [](void **p, size_t b) { return cudaMalloc(p, b) == cudaSuccess ? 0 : -1; },
+        [](void *p) { cudaFree(p); });
+    if (rc == 0) return GBFMM_OK;
+    const cudaError_t e = cudaGetLastError();  // clears the (non-sticky) allocation error
+    return set_err(ctx, GBFMM_ERR_CUDA, std::string("cudaMalloc (") + what + "): " + cudaGetErrorString(e));
+}
+inline int grow_dev(gbfmm_ctx *ctx, int64_t &cap, int64_t need, std::initializer_list<GrowBuf> bufs,
+                    const char *what) {
+    return grow_dev(ctx, cap, need, bufs.begin(), int(bufs.size()), what);
+}
 #define CK(call)                                                                   \
     do {                                                                           \
         cudaError_t e_ = (call);                                                   \

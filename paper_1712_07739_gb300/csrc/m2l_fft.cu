@@ -1,5 +1,5 @@
 // FP64 M2L through the Toeplitz structure of the operators (Sec. 4.1,
-// Theorem 1; Algorithm 2 step 2).
+// Theorem 1; the M2L stage of Algorithm 2).
 //
 // For an offset o (target cell B = source cell A + o, in cell units of the
 // level) the local value at node l of B is
@@ -257,6 +257,7 @@ int m2l_fft_run(gbfmm_ctx *ctx, const int *occ, const int *tocc) {
     cudaStream_t st = ctx->stream;
     if (L < 3) return GBFMM_OK;
     if (!F.ready || F.p != p) {
+        F.ready = false;
         if (F.Khat) cudaFree(F.Khat);
         F.Khat = nullptr;
         CK(cudaMalloc(&F.Khat, size_t(343) * 54 * NF * sizeof(double2)));
@@ -270,14 +271,10 @@ int m2l_fft_run(gbfmm_ctx *ctx, const int *occ, const int *tocc) {
         F.p = p;
     }
     const int64_t max_cells = int64_t(1) << (3 * (L - 1));
-    if (max_cells > F.cell_cap) {
-        if (F.slot) cudaFree(F.slot);
-        if (F.slot_cell) cudaFree(F.slot_cell);
-        F.slot = F.slot_cell = nullptr;
-        CK(cudaMalloc(&F.slot, max_cells * sizeof(int)));
-        CK(cudaMalloc(&F.slot_cell, max_cells * sizeof(int)));
-        F.cell_cap = max_cells;
-    }
+    if (int rc = grow_dev(ctx, F.cell_cap, max_cells,
+                          {{(void **)&F.slot, max_cells * sizeof(int)}, {(void **)&F.slot_cell, max_cells * sizeof(int)}},
+                          "M2L transform slots"))
+        return rc;
     if (!F.count) CK(cudaMalloc(&F.count, sizeof(int)));
     const size_t sm_w = size_t(N) * sizeof(double2) + size_t(p) * p * NH * sizeof(double2) +
                         size_t(p) * N * NH * sizeof(double2) + size_t(P3) * sizeof(double);
@@ -295,12 +292,9 @@ int m2l_fft_run(gbfmm_ctx *ctx, const int *occ, const int *tocc) {
         int cnt = 0;
         CK(cudaMemcpyAsync(&cnt, F.count, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (cnt > F.what_cap) {
-            if (F.What) cudaFree(F.What);
-            F.What = nullptr;
-            CK(cudaMalloc(&F.What, size_t(cnt) * 9 * NF * sizeof(double2)));
-            F.what_cap = cnt;
-        }
+        if (int rc = grow_dev(ctx, F.what_cap, cnt, {{(void **)&F.What, size_t(cnt) * 9 * NF * sizeof(double2)}},
+                              "transformed multipole values"))
+            return rc;
         if (cnt > 0) {
             ++ctx->launches;
             k_fft_w<<<unsigned(cnt), 256, sm_w, st>>>(p, lev, ctx->d_W, F.slot_cell, F.What);

@@ -1,5 +1,5 @@
 // M2L on the tcgen05 tensor cores: offset-grouped dense GEMMs (Sec. 4.1,
-// Eq. "m2l"; Algorithm 2 step 2) with FP32 accumulation in TMEM.
+// Eq. "m2l"; the M2L stage of Algorithm 2) with FP32 accumulation in TMEM.
 //
 // Formulation.  At level l the cells form a 2^l grid.  Split it into the 8
 // parity classes c = (x & 1, y & 1, z & 1); each class is an m^3 sub-grid,
@@ -80,6 +80,8 @@ struct M2LParams {
     uint32_t idesc; // tcgen05 instruction descriptor
     const unsigned *wmax;  // FP16 mode: per-level max |W| bits (the W scale), else null
     float inv_op_scale;    // FP16 mode: 1 / operator scale, else 1
+    int o_lo, o_hi;        // this launch takes the entries o_lo .. o_hi - 1 of each class's offset list
+    int accumulate;        // 0: the epilogue writes the local values, 1: it adds to them
 };
 
 // FP16 mode: power of two that brings a level's largest |W| into [2^12, 2^13)
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
 
     // active offsets: lane r of warp w checks rows 4r .. 4r + 3 of every tile
-    for (int oi = warp; oi < 189; oi += 6) {
+    for (int oi = P.o_lo + warp; oi < P.o_hi; oi += 6) {
         const OffsetEntry e = c_offs[cls][oi];
         const int ccx = e.cls & 1, ccy = (e.cls >> 1) & 1, ccz = e.cls >> 2;
         bool hit = false;
@@ -400,7 +402,8 @@ __global__ void __launch_bounds__(192, 1)
                 }
             }
         }
-        mma_commit(accb);  // fires when every MMA issued above has completed
+        // fires when every MMA issued above has completed (no MMA, no wait: see the epilogue)
+        if (s_active[0] | s_active[1] | s_active[2] | s_active[3] | s_active[4] | s_active[5]) mma_commit(accb);
     } else if (warp >= 2) {
         const int row = threadIdx.x - 64;  // 0..127: this thread's tile row
         {
@@ -487,7 +490,7 @@ __global__ void __launch_bounds__(192, 1)
         // ---------------- epilogue: TMEM -> scaled FP32 local values of the tile's target cells
         bool any_src = false;
         for (int i = 0; i < 6; ++i) any_src |= s_active[i] != 0u;
-        const bool ok = mbar_wait(accb, 0, status);
+        const bool ok = any_src ? mbar_wait(accb, 0, status) : true;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int q = warp % 4;
         const int trow = q * 32 + lane;  // TMEM lane = tile row
@@ -503,8 +506,8 @@ __global__ void __launch_bounds__(192, 1)
             float *dst = S + g * int64_t(P.nvalid);
             double *dst64 = S64 ? S64 + g * int64_t(P.nvalid) : nullptr;  // FP64 local values, when kept
             if (ok && !any_src) {
-                // no occupied source anywhere in the interaction list: zero local values
-                if (valid)
+                // no occupied source among this launch's offsets: zero local values (or nothing to add)
+                if (valid && !P.accumulate)
                     for (int col = group * P.ncta; col < min(P.nvalid, (group + 1) * P.ncta); ++col) {
                         if (dst64) dst64[col] = 0.0;
                         else dst[col] = 0.f;
@@ -517,8 +520,13 @@ __global__ void __launch_bounds__(192, 1)
                     if (valid)
                         for (int i = 0; i < 16; ++i)
                             if (col + i < P.nvalid) {
-                                if (dst64) dst64[col + i] = double(v[i]) * double(sc);
-                                else dst[col + i] = v[i] * sc;
+                                if (P.accumulate) {
+                                    if (dst64) dst64[col + i] += double(v[i]) * double(sc);
+                                    else dst[col + i] += v[i] * sc;
+                                } else {
+                                    if (dst64) dst64[col + i] = double(v[i]) * double(sc);
+                                    else dst[col + i] = v[i] * sc;
+                                }
                             }
                 }
             }
@@ -734,7 +742,7 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     const int p = ctx->opt.p, P3 = p * p * p;
     TcPlan &T = ctx->tc;
     T.tf32 = ctx->opt.m2l_split == 3 ? 1 : 0;
-    T.fp16 = (ctx->opt.m2l_split == 4 || ctx->opt.m2l_split == 5) ? 1 : 0;
+    T.fp16 = (ctx->opt.m2l_split >= 4) ? 1 : 0;
     T.esz = T.tf32 ? 4 : 2;
     T.Kp = ((9 * P3 + 63) / 64) * 64;
     // N per MMA (= operator rows per CTA): multiple of 16, one accumulator per
@@ -768,7 +776,7 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
                 off.push_back(oy);
                 off.push_back(oz);
                 const int sm = ctx->opt.m2l_split;
-                const bool split = !T.tf32 && (sm == 2 || ((sm == 0 || sm == 5) && mx == 2));
+                const bool split = !T.tf32 && (sm == 2 || sm == 6 || ((sm == 0 || sm == 5) && mx == 2));
                 lo_of.push_back(split ? n_lo++ : -1);
             }
     T.n_off = int(off.size() / 3);
@@ -885,28 +893,18 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
         T.wofs[l] = tot;
         tot += (int64_t(1) << (3 * l)) * T.Kp;
     }
-    if (tot > T.w_cap) {
-        if (T.Whi) cudaFree(T.Whi);
-        if (T.Wlo) cudaFree(T.Wlo);
-        T.Whi = T.Wlo = nullptr;
-        CK(cudaMalloc(&T.Whi, tot * T.esz));
-        CK(cudaMalloc(&T.Wlo, tot * T.esz));
-        T.w_cap = tot;
-    }
+    if (int rc = grow_dev(ctx, T.w_cap, tot, {{&T.Whi, size_t(tot) * T.esz}, {&T.Wlo, size_t(tot) * T.esz}},
+                          "packed multipole values"))
+        return rc;
     // cell slots, target list and segment table (filled on the device per pass)
     const int64_t slots = slot_base(L);
     int64_t tiles = 0;  // CTAs per operator group, upper bound: every cell holds targets
     for (int l = 2; l < L; ++l) tiles += 8 * ((((int64_t(1) << (3 * (l - 1))) + 127) / 128 + TPC - 1) / TPC);
-    if (slots > T.slot_cap) {
-        void *ps[] = {T.d_flags, T.d_pos, T.d_list};
-        for (void *q : ps)
-            if (q) cudaFree(q);
-        T.d_flags = T.d_pos = T.d_list = nullptr;
-        CK(cudaMalloc(&T.d_flags, slots * sizeof(int)));
-        CK(cudaMalloc(&T.d_pos, (slots + 1) * sizeof(int)));
-        CK(cudaMalloc(&T.d_list, slots * sizeof(int)));
-        T.slot_cap = slots;
-    }
+    if (int rc = grow_dev(ctx, T.slot_cap, slots,
+                          {{(void **)&T.d_flags, slots * sizeof(int)}, {(void **)&T.d_pos, (slots + 1) * sizeof(int)},
+                           {(void **)&T.d_list, slots * sizeof(int)}},
+                          "M2L target lists"))
+        return rc;
     if (!T.d_seg) CK(cudaMalloc(&T.d_seg, (kMaxSeg + 1) * sizeof(int4)));
     T.n_slots = slots;
     T.n_seg = 8 * (L - 2);
@@ -1002,17 +1000,27 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     const int stages = int(std::min<int64_t>(6, room / stage_bytes));
     if (stages < 2) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "tensor-core M2L: operator block too large");
     const size_t smem = size_t(stages) * stage_bytes + 1024 + (2 * stages + 2) * 8 + 64;
-    ++ctx->launches;
-    if (T.tf32) {
+    if (T.tf32)
         CK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        k_m2l_tc<true><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
-                                                             Sf, S64, T.d_status, stages, T.groups);
-    } else {
+    else
         CK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        k_m2l_tc<false><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box,
-                                                              Sf, S64, T.d_status, stages, T.groups);
+    // offset chunks: each launch accumulates a run of consecutive offsets of every class's list
+    // in tensor memory; the chunks' sums are added outside the tensor cores, in the local values
+    const int chunks = std::max(1, std::min(189, ctx->opt.m2l_chunks));
+    for (int c = 0; c < chunks; ++c) {
+        prm.o_lo = (189 * c) / chunks;
+        prm.o_hi = (189 * (c + 1)) / chunks;
+        prm.accumulate = c > 0 ? 1 : 0;
+        if (c > 0) prm.drop_first = 0;
+        ++ctx->launches;
+        if (T.tf32)
+            k_m2l_tc<true><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc,
+                                                                 ctx->d_box, Sf, S64, T.d_status, stages, T.groups);
+        else
+            k_m2l_tc<false><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc,
+                                                                  ctx->d_box, Sf, S64, T.d_status, stages, T.groups);
+        CK(cudaGetLastError());
     }
-    CK(cudaGetLastError());
     return GBFMM_OK;
 }
 

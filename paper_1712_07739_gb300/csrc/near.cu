@@ -1,4 +1,4 @@
-// Near field (Algorithm 2 step 3.b, second sum) and L2P of the mixed-
+// Near field (the direct sum over neighbouring leaves in Algorithm 2) and L2P of the mixed-
 // precision pass: one warp per target leaf.
 //
 // For a source point j the kernel contraction of Sec. 2 Eq. "stress3",
@@ -1067,23 +1067,18 @@ int near_alloc(gbfmm_ctx *ctx, int64_t n_targets) {
     const int64_t nl = ctx->n_leaves;
     const int64_t cap = nl + n_targets / 32 + 1;
     NearWork &W = ctx->nw;
-    if (cap > W.cap || nl > W.cap_leaves) {
-        void *ps[] = {W.items, W.sorted, W.keys, W.cnt, W.key_of, W.off, W.misc};
-        for (void *q : ps)
-            if (q) cudaFree(q);
-        W.items = W.sorted = nullptr;
-        W.keys = W.cnt = W.key_of = W.off = W.misc = nullptr;
-        W.cap = W.cap_leaves = 0;
-        CK(cudaMalloc(&W.items, cap * sizeof(int2)));
-        CK(cudaMalloc(&W.sorted, cap * sizeof(int2)));
-        CK(cudaMalloc(&W.keys, cap * sizeof(int)));
-        CK(cudaMalloc(&W.cnt, nl * sizeof(int)));
-        CK(cudaMalloc(&W.key_of, nl * sizeof(int)));
-        CK(cudaMalloc(&W.off, (nl + 1) * sizeof(int)));
-        CK(cudaMalloc(&W.misc, 192 * sizeof(int)));  // hist[64], cursor[64], n_items, total
-        W.cap = cap;
-        W.cap_leaves = nl;
+    if (nl > W.cap_leaves) W.cap = 0;  // the per-leaf arrays grow with the item arrays
+    const int64_t cap0 = W.cap;
+    if (int rc = grow_dev(ctx, W.cap, cap,
+                          {{(void **)&W.items, cap * sizeof(int2)}, {(void **)&W.sorted, cap * sizeof(int2)},
+                           {(void **)&W.keys, cap * sizeof(int)}, {(void **)&W.cnt, nl * sizeof(int)},
+                           {(void **)&W.key_of, nl * sizeof(int)}, {(void **)&W.off, (nl + 1) * sizeof(int)},
+                           {(void **)&W.misc, 192 * sizeof(int)}},  // hist[64], cursor[64], n_items, total
+                          "near-field work list")) {
+        W.cap_leaves = 0;
+        return rc;
     }
+    if (W.cap != cap0) W.cap_leaves = nl;
     return GBFMM_OK;
 }
 
@@ -1117,24 +1112,14 @@ int near_sym_alloc(gbfmm_ctx *ctx) {
     if (!near_symmetric(ctx)) return GBFMM_OK;
     NearWork &W = ctx->nw;
     const int64_t pcap = 14 * ctx->n_leaves;
-    if (pcap > W.pcap) {
-        void *ps[] = {W.pitems, W.psorted, W.pkeys, W.pmisc};
-        for (void *q : ps)
-            if (q) cudaFree(q);
-        W.pitems = W.psorted = nullptr;
-        W.pkeys = W.pmisc = nullptr;
-        CK(cudaMalloc(&W.pitems, pcap * sizeof(int2)));
-        CK(cudaMalloc(&W.psorted, pcap * sizeof(int2)));
-        CK(cudaMalloc(&W.pkeys, pcap * sizeof(int)));
-        CK(cudaMalloc(&W.pmisc, 192 * sizeof(int)));
-        W.pcap = pcap;
-    }
-    if (ctx->N > W.part_cap) {
-        if (W.part) cudaFree(W.part);
-        W.part = nullptr;
-        CK(cudaMalloc(&W.part, size_t(kSlots) * ctx->N * 6 * sizeof(double)));
-        W.part_cap = ctx->N;
-    }
+    if (int rc = grow_dev(ctx, W.pcap, pcap,
+                          {{(void **)&W.pitems, pcap * sizeof(int2)}, {(void **)&W.psorted, pcap * sizeof(int2)},
+                           {(void **)&W.pkeys, pcap * sizeof(int)}, {(void **)&W.pmisc, 192 * sizeof(int)}},
+                          "near-field leaf pairs"))
+        return rc;
+    if (int rc = grow_dev(ctx, W.part_cap, ctx->N,
+                          {{(void **)&W.part, size_t(kSlots) * ctx->N * 6 * sizeof(double)}}, "near-field partial sums"))
+        return rc;
     return GBFMM_OK;
 }
 

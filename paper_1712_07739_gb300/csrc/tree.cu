@@ -304,21 +304,18 @@ int tree_build(gbfmm_ctx *ctx) {
 int targets_sort(gbfmm_ctx *ctx, int64_t n_t, const double *x) {
     cudaStream_t st = ctx->stream;
     const int64_t nl = ctx->n_leaves;
-    if (n_t > ctx->t_cap) {
-        if (ctx->d_t_pos) cudaFree(ctx->d_t_pos);
-        if (ctx->d_t_x) cudaFree(ctx->d_t_x);
-        if (ctx->d_t_sig) cudaFree(ctx->d_t_sig);
-        if (ctx->d_t_tmp) cudaFree(ctx->d_t_tmp);
-        ctx->d_t_pos = nullptr;
-        ctx->d_t_x = nullptr;
-        ctx->d_t_sig = nullptr;
-        ctx->d_t_tmp = nullptr;
-        CK(cudaMalloc(&ctx->d_t_pos, n_t * sizeof(int)));
-        CK(cudaMalloc(&ctx->d_t_x, n_t * 3 * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_t_sig, n_t * 6 * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_t_tmp, (2 * n_t + 2 * nl) * sizeof(int)));
-        ctx->t_cap = n_t;
+    // the scratch holds per-target and per-leaf arrays: regrow for more targets or more leaves
+    if (nl > ctx->t_cap_leaves) ctx->t_cap = 0;
+    const int64_t t0 = ctx->t_cap;
+    if (int rc = grow_dev(ctx, ctx->t_cap, n_t,
+                          {{(void **)&ctx->d_t_pos, n_t * sizeof(int)}, {(void **)&ctx->d_t_x, n_t * 3 * sizeof(double)},
+                           {(void **)&ctx->d_t_sig, n_t * 6 * sizeof(double)},
+                           {(void **)&ctx->d_t_tmp, (2 * n_t + 2 * nl) * sizeof(int)}},
+                          "targets")) {
+        ctx->t_cap_leaves = 0;
+        return rc;
     }
+    if (ctx->t_cap != t0) ctx->t_cap_leaves = nl;
     int *leaf_of = ctx->d_t_tmp, *perm = leaf_of + n_t, *cnt = perm + n_t, *cursor = cnt + nl;
     CK(cudaMemsetAsync(cnt, 0, nl * sizeof(int), st));
     CK(cudaMemsetAsync(cursor, 0, nl * sizeof(int), st));
