@@ -73,29 +73,40 @@ def near_pair_flops(precision, h_mode, q, cubic=False):
 
 def near_flops(wl, work):
     """Algorithmic FLOP of the near field (+ L2P) of one pass and the kernel
-    that does it.  With the unit-circle h the mixed pass evaluates h once per
-    unordered pair (h is odd) and contracts it for both directions: per
+    that does it.  With the unit-circle h both passes evaluate h once per
+    unordered pair (h is odd) and contract it for both directions: per
     ordered pair half an h evaluation (cubic rule 193 Q + 77, general rule
     450 Q + 20) plus one contraction (229)."""
     p, q = wl["p"], wl.get("circle_q", 64)
     cubic = is_cubic_aligned(wl["C"]())
     l2p = work["points"] * (12 * p ** 3 + 30 * p)
+    if wl["h_mode"] == "circle":
+        # symmetric kernels (FP32 in the mixed pass, FP64 in the FP64 pass)
+        h = 193 * q + 77 if cubic else 450 * q + 20
+        name = "k_near_sym64" if wl["precision"] == "fp64" else "k_near_sym"
+        return work["near_pairs"] * (h / 2.0 + 229) + l2p, name
     if wl["precision"] == "fp64":
         return work["near_pairs"] * near_pair_flops("fp64", wl["h_mode"], q, cubic) + l2p, "k_leaf_eval_f64"
-    if wl["h_mode"] == "circle":
-        h = 193 * q + 77 if cubic else 450 * q + 20
-        return work["near_pairs"] * (h / 2.0 + 229) + l2p, "k_near_sym"
     name = "k_near_mlp" if wl["h_mode"] == "mlp" else "k_near_mixed"
     return work["near_pairs"] * near_pair_flops("mixed", wl["h_mode"], q, cubic) + l2p, name
 
 
 # DRAM bytes per target point of one k_near_sym launch (cubic rule, Q = 20), from
 # one ncu capture on the 250,000-segment slab network (dram__bytes_read.sum +
-# dram__bytes_write.sum = 7.94 GB for 1,000,000 points); valid for that kernel
-# version only
+# dram__bytes_write.sum); valid for the kernel version the capture was taken of
 NEAR_SYM_DRAM_BYTES_PER_POINT = 7.943e9 / 1.0e6
-FP64_PEAK_TFLOPS = 1.25          # GB300 FP64, nominal
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def measured_alu_peaks():
+    """FP32 and FP64 fused multiply-add throughput of this GPU, measured now by
+    the library's self-checking probe (fmm_probe_fma, ~0.5 s each): the
+    denominators of the near-field and FP64-pass rooflines."""
+    import paper_1712_07739_gb300 as gb
+
+    fp32 = max(gb.probe_fma("fp32"), gb.probe_fma("fp32x2"))
+    return {"fp32_tflops": fp32, "fp64_tflops": gb.probe_fma("fp64"),
+            "source": "fmm_probe_fma on this GPU before the timed region (FMA chains, CUDA events, best of 3), "
+                      "of measured"}
 
 WORKLOADS = {
     "c1": dict(
@@ -211,12 +222,15 @@ class ClockSampler:
 
 
 def measured_bf16_peak():
-    """Dense BF16 peak from MEASURED_PEAKS.json (burst: the kernel is timed on its own)."""
+    """Dense 16-bit tensor peak from MEASURED_PEAKS.json: the sustained figure, as
+    the M2L runs inside a step of several hundred milliseconds (FP16 and BF16
+    have the same nominal dense rate)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)["bf16_tflops"]), "MEASURED_PEAKS.json bf16_tflops (burst), of measured"
+            return (float(json.load(fh)["bf16_tflops_sustained"]),
+                    "MEASURED_PEAKS.json bf16_tflops_sustained (FP16 operands: same nominal rate), of measured")
     except (OSError, KeyError, ValueError):
-        return 1900.0, "fallback 1.9 PFLOP/s bf16 burst (profiling recipe), of fallback"
+        return 1700.0, "fallback 1.7 PFLOP/s bf16 sustained, of fallback"
 
 
 def oracle_sample_rate(wl, nodes, segs, b, budget_s, nthreads=0, seed=123):
@@ -373,8 +387,9 @@ def run_batch(args, wl):
     p = wl["p"]
     if st[4] >= st[2]:
         flops, kname = near_flops(wl, work)
+        pk = measured_alu_peaks()
         roof = {"bound": "alu", "kernel": kname + " (largest network alone)", "achieved": flops / (st[4] / 1e3) / 1e12,
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "peak_source": "152 SM x 128 lanes x 2 x 2.07 GHz"}
+                "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "peak_source": pk["source"]}
     else:
         pk, src = measured_bf16_peak()
         flops = work["m2l_pairs"] * 2 * 54 * p ** 6
@@ -386,7 +401,7 @@ def run_batch(args, wl):
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
-            "dtype": "f32/bf16", "data": "synthetic",
+            "dtype": "f32/fp16", "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "n_configs": len(nets_all),
                        "n_segs_rank0": n_segs,
                        "depths": depths, "l2": "flushed: 256 MiB write between steps, outside the step events",
@@ -421,6 +436,7 @@ def run_ours(args, wl):
     d_b = torch.tensor(b, device=dev)
     f = gb.FMM(p=wl["p"], levels=args.levels or wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
                circle_q=wl.get("circle_q", 0), m2l_split=wl.get("m2l_split", 4),
+               m2l_chunks=wl.get("m2l_chunks"), m2l_basis=wl.get("m2l_basis"),
                m2l_fft=None if args.m2l_fft < 0 else args.m2l_fft)
     f.set_material(wl["C"]())
     mlp_info = None
@@ -498,70 +514,140 @@ def run_ours(args, wl):
     d2h = h_out.numel() * 8
 
     # roofline of the dominant kernel (stage times are CUDA events around it)
+    peaks = measured_alu_peaks()
     st = np.array(stage)            # [steps, 8]: precontract, P2M+M2M, M2L, L2L, L2P+P2P, forces
-    m2l_ms, leaf_ms = st[:, 2].mean(), st[:, 4].mean()
     p = wl["p"]
-    fp64 = wl["precision"] == "fp64"
-    peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
-    traffic, traffic_src = None, None
-    if leaf_ms >= m2l_ms:
-        flops, kname = near_flops(wl, work)
-        achieved = flops / (leaf_ms / 1e3) / 1e12
-        sym = kname == "k_near_sym"
-        dom = kname + " (L2P + near-field P2P)"
-        bound, src = "alu", ("FP64 1.25 TFLOP/s nominal (recipe)" if fp64 else "152 SM x 128 lanes x 2 x 2.07 GHz")
-        if sym and wl.get("circle_q") == 20:
-            traffic = NEAR_SYM_DRAM_BYTES_PER_POINT * work["points"]
-            traffic_src = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_near_sym on the "
-                           "250k-segment slab network (7.94 GB for 1,000,000 points), scaled by points")
-    else:
-        fft = fp64 and int(f.options.m2l_fft) == 1
-        # dense: 2*54*p^6 per cell pair; through transforms: 54 complex multiply-adds
-        # (8 FLOP) at each of (2p)^2 (p+1) frequencies per cell pair
-        per_pair = 8 * 54 * (2 * p) ** 2 * (p + 1) if fft else 2 * 54 * p ** 6
-        flops = work["m2l_pairs"] * per_pair
-        achieved = flops / (m2l_ms / 1e3) / 1e12
-        if fft:
-            dom, bound, src = "k_m2l_fft (FP64 M2L through transforms)", "alu", "FP64 1.25 TFLOP/s nominal (recipe)"
-        elif fp64:
-            dom, bound, src = "k_m2l_f64 (M2L)", "alu", "FP64 1.25 TFLOP/s nominal (recipe)"
-        else:
-            dom, bound = "k_m2l_tc (M2L, tcgen05 BF16)", "tensor"
-            peak, src = measured_bf16_peak()
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": src,
-                "work": "algorithmic: near pairs x FLOP/pair (h once per unordered pair when h is the unit-circle "
-                        "rule) + L2P, or M2L cell pairs x 2*54*p^6 (x 8*54*(2p)^2*(p+1) through transforms)"}
+    roofline = roofline_of(wl, work, st[:, 2].mean(), st[:, 4].mean(), int(f.options.m2l_fft), peaks)
+    accuracy = oracle_node_error(wl, args.workload, out.cpu().numpy(), nodes, segs, b)
+    f.close()
+
+    fp64_arm = None
+    if wl.get("fp64_arm") and not args.no_fp64_arm:
+        fp64_arm = run_fp64_arm(wl, args.workload, d_nodes, d_segs, d_b, nodes, segs, b, flush, stream)
+        fp64_arm["roofline"] = roofline_of(dict(wl, precision="fp64"), work, fp64_arm["stage_ms"]["m2l"],
+                                           fp64_arm["stage_ms"]["l2p_p2p"], 1, peaks)
 
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             r, used, desc, dt = oracle_sample_rate(wl, nodes, segs, b, 20.0)
             cpu = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc}
+        fp64 = wl["precision"] == "fp64"
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32/bf16",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32/fp16",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "n_segs": n_segs, "levels": info["levels"],
                        "p": p, "precision": wl["precision"], "h_mode": wl["h_mode"],
                        "circle_q": wl.get("circle_q", 0), "m2l_split": wl.get("m2l_split", 4),
+                       "m2l_chunks": wl.get("m2l_chunks", 1), "m2l_basis": wl.get("m2l_basis", 0),
                        "m2l_fft": int(f.options.m2l_fft),
                        "l2": "flushed: 256 MiB write between steps, outside the step events",
                        "step": "fmm_build_tree + fmm_eval_nodal_forces"},
-            "stage_ms": {"precontract": st[:, 0].mean(), "p2m_m2m": st[:, 1].mean(), "m2l": m2l_ms,
-                         "l2l": st[:, 3].mean(), "l2p_p2p": leaf_ms, "forces": st[:, 5].mean()},
+            "stage_ms": {"precontract": st[:, 0].mean(), "p2m_m2m": st[:, 1].mean(), "m2l": st[:, 2].mean(),
+                         "l2l": st[:, 3].mean(), "l2p_p2p": st[:, 4].mean(), "forces": st[:, 5].mean()},
             "work": work, "wall_s": wall,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "device_status": dev_status, "clocks": clk, "roofline": roofline,
-            "cpu_baseline": cpu,
+            "peaks": peaks, "accuracy": accuracy, "cpu_baseline": cpu,
         }
+        if fp64_arm is not None:
+            res["fp64_plain"] = fp64_arm
+            res["speedup_vs_fp64_plain"] = value / fp64_arm["value"]
         if mlp_info is not None:
             res["learned"] = mlp_info
         print(json.dumps(res, default=float))
-    f.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+GOLDEN = {"c3": "c3_sampled_forces.json", "c3q": "c3q_sampled_forces.json"}
+
+
+def oracle_node_error(wl, name, F, nodes, segs, b):
+    """Relative L2 nodal-force error on the nodes whose FP64 oracle forces
+    (direct sum of Eq. stress3) are stored under tests/golden (written by the
+    scripts there, which call only the oracle); None for other workloads."""
+    fn = GOLDEN.get(name)
+    if fn is None:
+        return None
+    with open(os.path.join(ROOT, "tests", "golden", fn)) as fh:
+        gold = json.load(fh)
+    ids = np.array(gold["node_ids"])
+    if gold["n_segs"] != len(segs) or not np.allclose(nodes[ids], np.array(gold["node_xyz"]), rtol=0, atol=1e-12):
+        return None
+    Fo = np.array(gold["forces"])
+    err = float(np.linalg.norm(F[ids] - Fo) / np.linalg.norm(Fo))
+    return {"rel_l2_vs_oracle": err, "nodes": int(len(ids)), "gate": 1e-4, "meets_gate": err <= 1e-4,
+            "oracle": f"tests/golden/{fn}: FP64 direct sum, unit-circle h Q={gold.get('Q')}"}
+
+
+def roofline_of(wl, work, m2l_ms, leaf_ms, m2l_fft, peaks):
+    """Roofline of the dominant stage of a pass: near field + L2P (ALU-bound)
+    or M2L (tensor-bound on the mixed pass, FP64 ALU on the FP64 pass)."""
+    p = wl["p"]
+    fp64 = wl["precision"] == "fp64"
+    alu_peak = peaks["fp64_tflops"] if fp64 else peaks["fp32_tflops"]
+    traffic, traffic_src = None, None
+    if leaf_ms >= m2l_ms:
+        flops, kname = near_flops(wl, work)
+        achieved = flops / (leaf_ms / 1e3) / 1e12
+        dom, bound, peak, src = kname + " (L2P + near-field P2P)", "alu", alu_peak, peaks["source"]
+        if kname == "k_near_sym" and wl.get("circle_q") == 20:
+            traffic = NEAR_SYM_DRAM_BYTES_PER_POINT * work["points"]
+            traffic_src = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_near_sym on the "
+                           "250k-segment slab network, scaled by points")
+    else:
+        fft = fp64 and m2l_fft == 1
+        # dense: 2*54*p^6 per cell pair; through transforms: 54 complex multiply-adds
+        # (8 FLOP) at each of (2p)^2 (p+1) frequencies per cell pair
+        per_pair = 8 * 54 * (2 * p) ** 2 * (p + 1) if fft else 2 * 54 * p ** 6
+        flops = work["m2l_pairs"] * per_pair
+        achieved = flops / (m2l_ms / 1e3) / 1e12
+        if fp64:
+            dom = "k_m2l_fft (FP64 M2L through transforms)" if fft else "k_m2l_f64 (M2L)"
+            bound, peak, src = "alu", alu_peak, peaks["source"]
+        else:
+            dom, bound = "k_m2l_tc (M2L, tcgen05 FP16 operands)", "tensor"
+            peak, src = measured_bf16_peak()
+    return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": src,
+            "work": "algorithmic: near pairs x FLOP/pair (h once per unordered pair when h is the unit-circle "
+                    "rule) + L2P, or M2L cell pairs x 2*54*p^6 (x 8*54*(2p)^2*(p+1) through transforms)"}
+
+
+def run_fp64_arm(wl, name, d_nodes, d_segs, d_b, nodes, segs, b, flush, stream):
+    """The same step through the plain FP64 pass (the metric's comparison arm):
+    FP64 everywhere, M2L through transforms, symmetric FP64 near field with the
+    same unit-circle rule.  One untimed and one timed step (tens of seconds
+    each at a million segments)."""
+    import torch
+
+    import paper_1712_07739_gb300 as gb
+
+    f = gb.FMM(p=wl["p"], levels=wl["levels"], precision="fp64", h_mode=wl["h_mode"],
+               circle_q=wl.get("circle_q", 0), m2l_fft=1).set_material(wl["C"]())
+    out = torch.empty((len(nodes), 3), dtype=torch.float64, device=d_nodes.device)
+    f.build(d_nodes, d_segs, d_b)
+    f.nodal_forces(out=out)
+    f.set_timing(True)
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    f.build(d_nodes, d_segs, d_b)
+    f.nodal_forces(out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = f.stage_times()
+    ms = e0.elapsed_time(e1)
+    f.close()
+    return {"value": len(segs) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": 1, "warmup": 1,
+            "stage_ms": {"precontract": st[0], "p2m_m2m": st[1], "m2l": st[2], "l2l": st[3], "l2p_p2p": st[4],
+                         "forces": st[5]},
+            "accuracy": oracle_node_error(wl, name, out.cpu().numpy(), nodes, segs, b),
+            "config": "same network, p, tree and unit-circle rule; precision fp64, M2L through transforms"}
 
 
 def main():
@@ -572,11 +658,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-arm", action="store_true", help="skip the plain FP64 pass of the same step")
     ap.add_argument("--levels", type=int, default=0, help="override the workload's tree depth")
     ap.add_argument("--p", type=int, default=0, help="override the workload's interpolation order")
     ap.add_argument("--m2l-split", type=int, default=-1, help="override the M2L operand mode (fmm options)")
     ap.add_argument("--circle-q", type=int, default=0, help="override the unit-circle points")
     ap.add_argument("--m2l-fft", type=int, default=-1, help="FP64 path: 1 = M2L through transforms, 0 = dense")
+    ap.add_argument("--m2l-chunks", type=int, default=-1, help="override the M2L offset chunks (fmm options)")
+    ap.add_argument("--m2l-basis", type=int, default=-1, help="override the M2L operand basis (fmm options)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.p:
@@ -585,6 +674,10 @@ def main():
         wl["m2l_split"] = args.m2l_split
     if args.circle_q:
         wl["circle_q"] = args.circle_q
+    if args.m2l_chunks >= 0:
+        wl["m2l_chunks"] = args.m2l_chunks
+    if args.m2l_basis >= 0:
+        wl["m2l_basis"] = args.m2l_basis
     if args.impl == "reference":
         run_reference(args, wl)
     elif wl.get("batch"):

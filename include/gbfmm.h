@@ -100,6 +100,15 @@ typedef struct {
                               zero and added to the local values in FP32 (FP64 with
                               GBFMM_MIXED_F64T); shorter accumulation chains, one launch per
                               run.  0 = 1. */
+    int m2l_basis;         /* MIXED: operands of the tensor-core M2L.  0 = the node values of
+                              Eq. "m2l" (multipole values at the source cell's nodes); 1 = the
+                              Legendre moments of each source cell, sum_j P_k(y_j) q_j with
+                              Legendre polynomials of degree < p per axis, against operators
+                              T V^-1 precomputed in FP64 -- the same product in exact
+                              arithmetic, without the oscillating node values whose
+                              cancellation inside each GEMM costs precision. */
+    int m2l_split_levels;  /* MIXED, m2l_split 0, 2, 5 or 6: the residual passes apply only at
+                              the tree levels whose bit is set (bit l = level l); 0 = all. */
 } gbfmm_options;
 
 typedef struct gbfmm_ctx gbfmm_ctx;

@@ -44,6 +44,7 @@ class Options(ctypes.Structure):
         ("precision", ctypes.c_int), ("h_mode", ctypes.c_int), ("circle_q", ctypes.c_int),
         ("leaf_segments", ctypes.c_int), ("near_fp64", ctypes.c_double), ("m2l_split", ctypes.c_int),
         ("mlp_min_dist", ctypes.c_double), ("m2l_fft", ctypes.c_int), ("m2l_chunks", ctypes.c_int),
+        ("m2l_basis", ctypes.c_int), ("m2l_split_levels", ctypes.c_int),
     ]
 
 
@@ -142,7 +143,7 @@ class FMM:
 
     def __init__(self, p=4, n_gauss=4, levels=0, precision="fp64", h_mode="iso", circle_q=0,
                  leaf_segments=0, near_fp64=0.0, m2l_split=4, mlp_min_dist=0.0, m2l_fft=None, m2l_chunks=None,
-                 stream=None):
+                 m2l_basis=None, m2l_split_levels=None, stream=None):
         import torch
 
         self._torch = torch
@@ -159,6 +160,10 @@ class FMM:
             o.m2l_fft = int(m2l_fft)
         if m2l_chunks is not None:
             o.m2l_chunks = int(m2l_chunks)
+        if m2l_basis is not None:
+            o.m2l_basis = int(m2l_basis)
+        if m2l_split_levels is not None:
+            o.m2l_split_levels = int(m2l_split_levels)
         self.options = o
         if stream is None:
             stream = torch.cuda.current_stream()

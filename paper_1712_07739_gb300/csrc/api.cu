@@ -8,7 +8,9 @@
 
 int fmm_kernel_attrs(gbfmm_ctx *ctx);  // fmm.cu
 void mlp_free(gbfmm_ctx *ctx);         // mlp.cu
-int mixed_alloc(gbfmm_ctx *ctx);       // mixed.cu
+int mixed_alloc(gbfmm_ctx *ctx);       // fmm.cu
+int near_alloc(gbfmm_ctx *ctx, int64_t n_targets);  // near.cu
+int near_sym_alloc(gbfmm_ctx *ctx);                 // near.cu
 int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t);
 
 int set_err(gbfmm_ctx *c, int code, const std::string &msg) {
@@ -114,7 +116,7 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
         (opt->precision < GBFMM_FP64 || opt->precision > GBFMM_MIXED_F64T) || opt->h_mode < 0 || opt->h_mode > 2 ||
         opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0) || opt->m2l_split < 0 ||
         opt->m2l_split > 6 || opt->m2l_fft < 0 || opt->m2l_fft > 1 || opt->m2l_chunks < 0 ||
-        opt->m2l_chunks > 189)
+        opt->m2l_chunks > 189 || opt->m2l_basis < 0 || opt->m2l_basis > 1)
         return GBFMM_ERR_INVALID_ARG;
     gbfmm_ctx *ctx = new gbfmm_ctx();
     ctx->opt = *opt;
@@ -203,6 +205,11 @@ extern "C" int fmm_build_tree(gbfmm_ctx *ctx, int64_t n_nodes, const double *nod
     if (rc) return rc;
     if (ctx->opt.precision != GBFMM_FP64) {
         rc = mixed_alloc(ctx);
+        if (rc) return rc;
+    } else {
+        // work list and partial sums of the FP64 symmetric near field (unit-circle h)
+        rc = near_alloc(ctx, ctx->N);
+        if (!rc) rc = near_sym_alloc(ctx);
         if (rc) return rc;
     }
     ctx->built = true;

@@ -705,6 +705,8 @@ void timer_mark(gbfmm_ctx *ctx) {
     cudaEventRecord(ctx->timer.ev[ctx->timer.n++], ctx->stream);
 }
 
+int near_run_sym64(gbfmm_ctx *ctx, double *sig);  // near.cu
+
 // Runs the pass.  free_targets: targets are the sorted free points of
 // targets_sort (no segment exclusion), else the sorted Gauss points.
 int fmm_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
@@ -752,7 +754,10 @@ int fmm_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
         CK(cudaGetLastError());
     }
     timer_mark(ctx);
-    {
+    if (!free_targets && ctx->mat.mode == GBFMM_H_CIRCLE) {
+        // nodal forces with the unit-circle h: one h per unordered point pair (h is odd)
+        if (int rc = near_run_sym64(ctx, ctx->d_sig)) return rc;
+    } else {
         const size_t smem = (size_t(P3) * 6 + 64 * 3 + 64 * 108) * sizeof(double) + 64 * sizeof(int64_t);
         const double *xt = free_targets ? ctx->d_t_x : ctx->d_y;
         const int64_t *tsid = free_targets ? nullptr : ctx->d_sid;

@@ -347,6 +347,71 @@ __device__ __forceinline__ void h_cubic_f32x2(float cp, float c44, float D, int 
     }
 }
 
+// The cubic rule of h_cubic_f32 in any precision (the FP64 pass's symmetric
+// near field): points from a table, the adjugate C of (zz) with
+// (zz)^-1 = C / det and F = C S C / det^2, so each point costs one reciprocal.
+template <typename R>
+__device__ __forceinline__ void h_cubic_tab(R cp, R c44, R D, int Q, const R *__restrict__ tab_c,
+                                            const R *__restrict__ tab_s, const R T[3], R hs[18]) {
+    const R T0 = T[0], T1 = T[1], T2 = T[2];
+    int k0 = 0;
+    if (fabs(T1) < fabs(T0)) k0 = 1;
+    if (fabs(T2) < fabs(k0 == 0 ? T0 : T1)) k0 = 2;
+    R a0 = k0 == 0 ? R(1) : R(0), a1 = k0 == 1 ? R(1) : R(0), a2 = k0 == 2 ? R(1) : R(0);
+    const R dd = a0 * T0 + a1 * T1 + a2 * T2;
+    a0 -= dd * T0;
+    a1 -= dd * T1;
+    a2 -= dd * T2;
+    const R nr = R(1) / sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+    const R e10 = a0 * nr, e11 = a1 * nr, e12 = a2 * nr;
+    const R e20 = T1 * e12 - T2 * e11, e21 = T2 * e10 - T0 * e12, e22 = T0 * e11 - T1 * e10;
+    const R cpD = cp + D, cpD2 = R(2) * (cp + D);
+    R acc[18], msum[6];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) acc[i] = R(0);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) msum[i] = R(0);
+    for (int k = 0; k < Q; ++k) {
+        const R c = tab_c[k], sn = tab_s[k];
+        const R z0 = c * e10 + sn * e20, z1 = c * e11 + sn * e21, z2 = c * e12 + sn * e22;
+        const R m00 = cpD * z0 * z0 + c44, m11 = cpD * z1 * z1 + c44, m22 = cpD * z2 * z2 + c44;
+        const R m01 = cp * z0 * z1, m02 = cp * z0 * z2, m12 = cp * z1 * z2;
+        const R i00 = m11 * m22 - m12 * m12, i01 = m02 * m12 - m01 * m22, i02 = m01 * m12 - m02 * m11;
+        const R i11 = m00 * m22 - m02 * m02, i12 = m01 * m02 - m00 * m12, i22 = m00 * m11 - m01 * m01;
+        const R idet = R(1) / (m00 * i00 + m01 * i01 + m02 * i02);
+        const R s00 = cpD2 * z0 * T0, s11 = cpD2 * z1 * T1, s22 = cpD2 * z2 * T2;
+        const R s01 = cp * (z0 * T1 + z1 * T0), s02 = cp * (z0 * T2 + z2 * T0), s12 = cp * (z1 * T2 + z2 * T1);
+        const R u00 = i00 * s00 + i01 * s01 + i02 * s02, u01 = i00 * s01 + i01 * s11 + i02 * s12,
+                u02 = i00 * s02 + i01 * s12 + i02 * s22;
+        const R u10 = i01 * s00 + i11 * s01 + i12 * s02, u11 = i01 * s01 + i11 * s11 + i12 * s12,
+                u12 = i01 * s02 + i11 * s12 + i12 * s22;
+        const R u20 = i02 * s00 + i12 * s01 + i22 * s02, u21 = i02 * s01 + i12 * s11 + i22 * s12,
+                u22 = i02 * s02 + i12 * s12 + i22 * s22;
+        const R F00 = u00 * i00 + u01 * i01 + u02 * i02, F01 = u00 * i01 + u01 * i11 + u02 * i12,
+                F02 = u00 * i02 + u01 * i12 + u02 * i22;
+        const R F11 = u10 * i01 + u11 * i11 + u12 * i12, F12 = u10 * i02 + u11 * i12 + u12 * i22,
+                F22 = u20 * i02 + u21 * i12 + u22 * i22;
+        const R w = idet * idet;
+        const R y0 = z0 * w, y1 = z1 * w, y2 = z2 * w;
+        const R Mp[6] = {i00, i11, i22, i12, i02, i01};
+        const R Fp[6] = {F00, F11, F22, F12, F02, F01};
+#pragma unroll
+        for (int pr = 0; pr < 6; ++pr) {
+            acc[3 * pr + 0] += y0 * Fp[pr];
+            acc[3 * pr + 1] += y1 * Fp[pr];
+            acc[3 * pr + 2] += y2 * Fp[pr];
+            msum[pr] += Mp[pr] * idet;
+        }
+    }
+    const R f = R(1.0 / (4.0 * 3.14159265358979323846 * double(Q)));
+#pragma unroll
+    for (int pr = 0; pr < 6; ++pr) {
+        hs[3 * pr + 0] = (acc[3 * pr + 0] - T0 * msum[pr]) * f;
+        hs[3 * pr + 1] = (acc[3 * pr + 1] - T1 * msum[pr]) * f;
+        hs[3 * pr + 2] = (acc[3 * pr + 2] - T2 * msum[pr]) * f;
+    }
+}
+
 // Lagrange basis on the p equispaced nodes t_a = a / (p - 1) of [0, 1]
 // (Sec. 4.1 footnote): ell_a(t) = prod_{b != a} (t - t_b) / (t_a - t_b).
 template <typename R>

@@ -74,7 +74,8 @@ struct M2LParams {
     int ncta;       // operator rows per CTA (= nsub)
     int nvalid;     // 6 p^3
     int tmem_cols;  // power of two >= ncta
-    int split;      // residual passes on the near offsets
+    int split;      // residual passes on the near offsets, at the levels whose bit is set in split_levels
+    int split_levels;
     int drop_first; // failure-detection test: arm the first stage but issue no load into it
     int kstep;      // operand elements per 128-byte row: 64 (bf16, fp16) or 32 (tf32)
     uint32_t idesc; // tcgen05 instruction descriptor
@@ -257,7 +258,8 @@ __device__ __forceinline__ uint32_t morton_compact(uint32_t v) {
 // list entry, cells, first tile}; seg[n_seg].z = total tiles.
 constexpr int kMaxSeg = 8 * GB_TC_MAXLEV;
 
-// number of K-block iterations of one work item (same count on every warp)
+// number of K-block iterations of one work item (same count on every warp);
+// split: the residual passes apply at this level
 __device__ __forceinline__ int passes_of(const OffsetEntry &e, int split) { return (split && e.lo >= 0) ? 3 : 1; }
 
 template <bool TF32>
@@ -299,6 +301,7 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     if (s_level < 0 || s_stop) return;  // surplus block, or an earlier block timed out
     const int level = s_level, cls = s_cls, nrow = s_nrow;
+    const int split = P.split && ((P.split_levels >> level) & 1);
     const int m = 1 << (level - 1), n = 1 << level;
     const int64_t cbase = cell_base_d(level);
     for (int r = threadIdx.x; r < 128 * TPC; r += blockDim.x) {
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(192, 1)
         for (int oi = 0; oi < 189 && ok; ++oi) {
             if (!((s_active[oi / 32] >> (oi % 32)) & 1u)) continue;
             const OffsetEntry e = c_offs[cls][oi];
-            const int np = passes_of(e, P.split);
+            const int np = passes_of(e, split);
             for (int pass = 0; pass < np && ok; ++pass) {
                 const CUtensorMap *tb = (pass == 2) ? &P.tmTlo : &P.tmT;
                 const int tidx = (pass == 2) ? e.lo : e.top;
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(192, 1)
         for (int oi = 0; oi < 189 && ok; ++oi) {
             if (!((s_active[oi / 32] >> (oi % 32)) & 1u)) continue;
             const OffsetEntry e = c_offs[cls][oi];
-            const int np = passes_of(e, P.split);
+            const int np = passes_of(e, split);
             for (int pass = 0; pass < np && ok; ++pass) {
                 for (int kb = 0; kb < P.kb; ++kb, ++it) {
                     const int s = it % stages;
@@ -451,7 +454,7 @@ __global__ void __launch_bounds__(192, 1)
                         nbm |= ((f >> t) & 1u) << (8 * t + i);
                     }
                 }
-                const int np = passes_of(e, P.split);
+                const int np = passes_of(e, split);
                 for (int pass = 0; pass < np && ok; ++pass) {
                     const uint8_t *wb = ((pass == 1) ? P.Wlo : P.Whi) + P.wofs[level];
                     for (int kb = 0; kb < P.kb; ++kb, ++it) {
@@ -586,6 +589,124 @@ __global__ void k_build_ops(int p, int lat_n, int Np, int Kp, const double *__re
         Thi[idx] = hi;
         const int li = lo_of[o];
         if (li >= 0 && Tlo) Tlo[(int64_t(li) * Np + nn) * Kp + k] = to_elem<E>(v - elem_value(hi));
+    }
+}
+
+// ---------------------------------------------------------------- Legendre-moment operands
+// With gbfmm_options.m2l_basis = 1 the GEMM runs on the Legendre moments of
+// each source cell instead of its node values: W'_k = sum_m P_k(ybar_m) W_m
+// with P_k(t) = P_k1(2 t_1 - 1) P_k2(2 t_2 - 1) P_k3(2 t_3 - 1) (degrees
+// k_i < p), which, since the node values come from Lagrange interpolation
+// of degree p - 1, equals sum_j P_k(y_j) q_j over the cell's sources, and
+// the operators become T' = T V^-1 (V = V1 x V1 x V1, V1[n][a] = P_n(2 t_a - 1)),
+// so T' W' = T W exactly.  The moments are bounded by sum |q| and the rows of
+// T' decay with the degree (Legendre coefficients of a smooth kernel), so the
+// products summed in one GEMM do not cancel the way the oscillating node
+// values of equispaced interpolation do, and 16-bit operands and FP32
+// accumulation lose far less.  Every transform is separable: three passes
+// of a p x p matrix along the node axes.
+// Basis matrices, passed by value (they depend on p, which differs between contexts)
+struct BasisMats {
+    double V[GB_MAXP * GB_MAXP];   // V1[n][a]
+    double Ct[GB_MAXP * GB_MAXP];  // (V1^-1)^T[n][a]
+    float Vf[GB_MAXP * GB_MAXP];   // V1 in FP32 (moments of the FP32 pass)
+};
+
+// out[.., n, ..] = sum_a M[n][a] in[.., a, ..] along one node axis of a [p^3][9] block,
+// summed in the precision R of the values
+template <typename R, typename MT>
+__device__ __forceinline__ void axis_pass(int p, int axis, const MT *M, const R *__restrict__ in, R *__restrict__ out) {
+    const int P3 = p * p * p, stride = axis == 0 ? 1 : (axis == 1 ? p : p * p);
+    for (int e = threadIdx.x; e < 9 * P3; e += blockDim.x) {
+        const int m = e / 9, wr = e - 9 * m;
+        const int n = (m / stride) % p, base = m - n * stride;
+        R acc = R(0);
+        for (int a = 0; a < p; ++a) acc += R(M[n * p + a]) * in[(base + a * stride) * 9 + wr];
+        out[e] = acc;
+    }
+}
+
+// Modal operator rows T'[o][n][k'] (FP64 arithmetic).  mode 0: largest |T'| into
+// *absmax (the FP16 scale); mode 1: write hi (and lo for split offsets).
+template <typename E>
+__global__ void k_build_ops_modal(int p, int lat_n, int Np, int Kp, const double *__restrict__ Klat,
+                                  const int *__restrict__ off_xyz, const int *__restrict__ lo_of, double scale,
+                                  const __grid_constant__ BasisMats B, int mode, unsigned long long *__restrict__ absmax,
+                                  E *__restrict__ Thi, E *__restrict__ Tlo) {
+    extern __shared__ double sm_modal[];
+    const int P3 = p * p * p, R0 = (lat_n - 1) / 2;
+    const int o = blockIdx.x / Np, nn = blockIdx.x % Np;
+    double *a = sm_modal, *b = sm_modal + 9 * P3;
+    const int64_t row = (int64_t(o) * Np + nn) * Kp;
+    const int li = lo_of[o];
+    if (nn >= 6 * P3) {  // padding rows
+        if (mode == 1)
+            for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+                Thi[row + k] = to_elem<E>(0.0);
+                if (li >= 0 && Tlo) Tlo[(int64_t(li) * Np + nn) * Kp + k] = to_elem<E>(0.0);
+            }
+        return;
+    }
+    const int l = nn / 6, ab = nn % 6;
+    const int ox = off_xyz[3 * o], oy = off_xyz[3 * o + 1], oz = off_xyz[3 * o + 2];
+    for (int e = threadIdx.x; e < 9 * P3; e += blockDim.x) {
+        const int mm = e / 9, wr = e % 9;
+        const int Dx = ox * (p - 1) + (l % p) - (mm % p) + R0;
+        const int Dy = oy * (p - 1) + ((l / p) % p) - ((mm / p) % p) + R0;
+        const int Dz = oz * (p - 1) + (l / (p * p)) - (mm / (p * p)) + R0;
+        a[e] = Klat[((int64_t(Dz) * lat_n + Dy) * lat_n + Dx) * 54 + ab * 9 + wr];
+    }
+    __syncthreads();
+    axis_pass<double, double>(p, 0, B.Ct, a, b);
+    __syncthreads();
+    axis_pass<double, double>(p, 1, B.Ct, b, a);
+    __syncthreads();
+    axis_pass<double, double>(p, 2, B.Ct, a, b);
+    __syncthreads();
+    if (mode == 0) {
+        double mx = 0.0;
+        for (int e = threadIdx.x; e < 9 * P3; e += blockDim.x) mx = fmax(mx, fabs(b[e]));
+        for (int s = 16; s > 0; s >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+        if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(absmax, (unsigned long long)__double_as_longlong(mx));
+        return;
+    }
+    for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+        const double v = k < 9 * P3 ? scale * b[k] : 0.0;
+        const E hi = to_elem<E>(v);
+        Thi[row + k] = hi;
+        if (li >= 0 && Tlo) Tlo[(int64_t(li) * Np + nn) * Kp + k] = to_elem<E>(v - elem_value(hi));
+    }
+}
+
+// Node values -> Legendre moments, in place, for the occupied cells of one level
+template <typename TW>
+__global__ void k_w_modal(int level, int p, const __grid_constant__ BasisMats B, TW *__restrict__ W,
+                          const int *__restrict__ occ) {
+    extern __shared__ __align__(16) unsigned char sm_wm[];
+    const int P3 = p * p * p;
+    TW *a = reinterpret_cast<TW *>(sm_wm), *b = a + 9 * P3;
+    const int64_t cells = int64_t(1) << (3 * level), base = cell_base_d(level);
+    for (int64_t lin = blockIdx.x; lin < cells; lin += gridDim.x) {
+        if (occ[base + lin] <= 0) continue;
+        TW *w = W + (base + lin) * int64_t(9 * P3);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 9 * P3; e += blockDim.x) a[e] = w[e];
+        __syncthreads();
+        if constexpr (sizeof(TW) == 8) {
+            axis_pass<TW, double>(p, 0, B.V, a, b);
+            __syncthreads();
+            axis_pass<TW, double>(p, 1, B.V, b, a);
+            __syncthreads();
+            axis_pass<TW, double>(p, 2, B.V, a, b);
+        } else {
+            axis_pass<TW, float>(p, 0, B.Vf, a, b);
+            __syncthreads();
+            axis_pass<TW, float>(p, 1, B.Vf, b, a);
+            __syncthreads();
+            axis_pass<TW, float>(p, 2, B.Vf, a, b);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 9 * P3; e += blockDim.x) w[e] = b[e];
     }
 }
 
@@ -737,6 +858,57 @@ inline unsigned nblk(int64_t n, int b) { return unsigned(std::min<int64_t>((n + 
 
 }  // namespace
 
+// V1[n][a] = P_n(2 t_a - 1) on the p equispaced nodes t_a = a / (p - 1), and the
+// transpose of its inverse (Gauss-Jordan with partial pivoting, FP64)
+static bool basis_matrices(int p, double *V, double *Ct) {
+    for (int a = 0; a < p; ++a) {
+        const double x = 2.0 * a / (p - 1) - 1.0;
+        double pm = 1.0, pc = x;
+        for (int n = 0; n < p; ++n) {
+            const double v = n == 0 ? 1.0 : (n == 1 ? x : 0.0);
+            if (n <= 1) {
+                V[n * p + a] = v;
+                continue;
+            }
+            const double nx = ((2.0 * n - 1.0) * x * pc - (n - 1.0) * pm) / n;
+            pm = pc;
+            pc = nx;
+            V[n * p + a] = nx;
+        }
+    }
+    double A[GB_MAXP][2 * GB_MAXP];
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < 2 * p; ++j) A[i][j] = j < p ? V[i * p + j] : (j - p == i ? 1.0 : 0.0);
+    for (int c = 0; c < p; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < p; ++r)
+            if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+        if (std::fabs(A[piv][c]) < 1e-300) return false;
+        for (int j = 0; j < 2 * p; ++j) std::swap(A[c][j], A[piv][j]);
+        const double d = A[c][c];
+        for (int j = 0; j < 2 * p; ++j) A[c][j] /= d;
+        for (int r = 0; r < p; ++r)
+            if (r != c) {
+                const double f = A[r][c];
+                for (int j = 0; j < 2 * p; ++j) A[r][j] -= f * A[c][j];
+            }
+    }
+    for (int n = 0; n < p; ++n)
+        for (int a = 0; a < p; ++a) Ct[n * p + a] = A[a][p + n];  // (V1^-1)[a][n]
+    return true;
+}
+
+static BasisMats basis_of(const TcPlan &T, int p) {
+    BasisMats B;
+    std::memset(&B, 0, sizeof(B));
+    for (int i = 0; i < p * p; ++i) {
+        B.V[i] = T.basisV[i];
+        B.Ct[i] = T.basisCt[i];
+        B.Vf[i] = float(T.basisV[i]);
+    }
+    return B;
+}
+
 // Offsets, their parity-class lists and the operator tables.
 int m2l_tc_setup(gbfmm_ctx *ctx) {
     const int p = ctx->opt.p, P3 = p * p * p;
@@ -823,7 +995,40 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     CK(cudaMalloc(&T.Tlo, std::max<size_t>(lo_elems, 1) * T.esz));
     T.split = n_lo > 0 ? 1 : 0;
     T.op_scale = 1.0;
-    if (T.fp16) {
+    T.modal = ctx->opt.m2l_basis == 1 ? 1 : 0;
+    if (T.modal && !basis_matrices(p, T.basisV, T.basisCt))
+        return set_err(ctx, GBFMM_ERR_INVALID_ARG, "m2l setup: singular Legendre basis matrix");
+    const size_t sm_modal = size_t(2) * 9 * P3 * sizeof(double);
+    if (T.modal) {
+        CK(cudaFuncSetAttribute(k_build_ops_modal<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_modal)));
+        CK(cudaFuncSetAttribute(k_build_ops_modal<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_modal)));
+        CK(cudaFuncSetAttribute(k_build_ops_modal<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(sm_modal)));
+        CK(cudaFuncSetAttribute(k_w_modal<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_modal)));
+        CK(cudaFuncSetAttribute(k_w_modal<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_modal / 2)));
+    }
+    const BasisMats B = basis_of(T, p);
+    if (T.fp16 && T.modal) {
+        // one power of two for all operators from the largest modal entry
+        unsigned long long *d_mx = nullptr, mx_bits = 0;
+        CK(cudaMalloc(&d_mx, sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(d_mx, 0, sizeof(unsigned long long), ctx->stream));
+        ++ctx->launches;
+        k_build_ops_modal<__half><<<unsigned(T.n_off * T.Np), 256, sm_modal, ctx->stream>>>(
+            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, 1.0, B, 0, d_mx, (__half *)nullptr, (__half *)nullptr);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&mx_bits, d_mx, sizeof(mx_bits), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        cudaFree(d_mx);
+        double mx = 0.0;
+        std::memcpy(&mx, &mx_bits, sizeof(mx));
+        if (mx > 0.0) {
+            int e = 0;
+            std::frexp(mx, &e);
+            T.op_scale = std::ldexp(1.0, 14 - e);
+        }
+        if (!T.d_wmax) CK(cudaMalloc(&T.d_wmax, GB_TC_MAXLEV * sizeof(unsigned)));
+    } else if (T.fp16) {
         // one power of two for all operators: the largest lattice value maps below 2^14
         unsigned long long *d_mx = nullptr, mx_bits = 0;
         CK(cudaMalloc(&d_mx, sizeof(unsigned long long)));
@@ -846,7 +1051,21 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
         if (!T.d_wmax) CK(cudaMalloc(&T.d_wmax, GB_TC_MAXLEV * sizeof(unsigned)));
     }
     ++ctx->launches;
-    if (T.tf32)
+    if (T.modal) {
+        const unsigned g = unsigned(T.n_off * T.Np);
+        if (T.tf32)
+            k_build_ops_modal<float><<<g, 256, sm_modal, ctx->stream>>>(p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off,
+                                                                        d_lo, 1.0, B, 1, nullptr, (float *)T.Thi,
+                                                                        (float *)nullptr);
+        else if (T.fp16)
+            k_build_ops_modal<__half><<<g, 256, sm_modal, ctx->stream>>>(p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off,
+                                                                         d_lo, T.op_scale, B, 1, nullptr,
+                                                                         (__half *)T.Thi, (__half *)T.Tlo);
+        else
+            k_build_ops_modal<__nv_bfloat16><<<g, 256, sm_modal, ctx->stream>>>(
+                p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, 1.0, B, 1, nullptr, (__nv_bfloat16 *)T.Thi,
+                (__nv_bfloat16 *)T.Tlo);
+    } else if (T.tf32)
         k_build_ops<float><<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(
             p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, T.n_off, 1.0, (float *)T.Thi, (float *)nullptr);
     else if (T.fp16)
@@ -919,10 +1138,23 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     M2LParams prm;  // copied by value into the launch (kernel parameter space)
     std::memset(&prm, 0, sizeof(prm));
     if (T.fp16) CK(cudaMemsetAsync(T.d_wmax, 0, GB_TC_MAXLEV * sizeof(unsigned), ctx->stream));
+    const BasisMats B = basis_of(T, p);
+    const int split_levels = ctx->opt.m2l_split_levels ? ctx->opt.m2l_split_levels : ~0;
     for (int l = 2; l < L; ++l) {
+        const bool split_l = T.split && ((split_levels >> l) & 1);  // residual W only where it is read
         const int64_t cells_l = int64_t(1) << (3 * l);
         void *whi = (char *)T.Whi + T.wofs[l] * T.esz, *wlo = (char *)T.Wlo + T.wofs[l] * T.esz;
         const unsigned gb = unsigned(std::min<int64_t>(cells_l, 8 * 152));  // blocks stride over the cells
+        if (T.modal) {
+            // node values -> Legendre moments (in place: nothing reads these W after the M2L)
+            ++ctx->launches;
+            if (W64)
+                k_w_modal<double><<<gb, 256, size_t(2) * 9 * P3 * sizeof(double), ctx->stream>>>(
+                    l, p, B, const_cast<double *>(W64), occ);
+            else
+                k_w_modal<float><<<gb, 256, size_t(2) * 9 * P3 * sizeof(float), ctx->stream>>>(
+                    l, p, B, const_cast<float *>(Wf), occ);
+        }
         if (T.tf32) {
             ++ctx->launches;
             if (W64)
@@ -931,7 +1163,7 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
                 k_pack_w<float><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, nullptr, (float *)whi, (float *)nullptr);
         } else if (T.fp16) {
             const unsigned gm = gb;
-            __half *lo = T.split ? (__half *)wlo : nullptr;
+            __half *lo = split_l ? (__half *)wlo : nullptr;
             ctx->launches += 2;
             if (W64) {
                 k_wmax<<<gm, 256, 0, ctx->stream>>>(l, P3, W64, occ, T.d_wmax);
@@ -941,7 +1173,7 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
                 k_pack_w<__half><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, T.d_wmax, (__half *)whi, lo);
             }
         } else {
-            __nv_bfloat16 *lo = T.split ? (__nv_bfloat16 *)wlo : nullptr;
+            __nv_bfloat16 *lo = split_l ? (__nv_bfloat16 *)wlo : nullptr;
             ++ctx->launches;
             if (W64)
                 k_pack_w<__nv_bfloat16><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, W64, occ, nullptr,
@@ -983,6 +1215,7 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     prm.nvalid = 6 * P3;
     prm.tmem_cols = T.tmem_cols;
     prm.split = T.split;
+    prm.split_levels = split_levels;
     prm.drop_first = T.inject_drop;
     T.inject_drop = 0;
     const int stage_bytes = kStageA + T.ncta * 128;

@@ -17,6 +17,8 @@ struct TcPlan {
     int fp16 = 0;              // FP16 operands: operators x op_scale, multipole values x a power of
                                // two per level chosen from the level's largest |W|
     double op_scale = 1.0;     // power of two applied to the FP16 operators
+    int modal = 0;             // operands are the source cells' Legendre moments (gbfmm_options.m2l_basis)
+    double basisV[64] = {0}, basisCt[64] = {0};  // V1[n][a] = P_n(2 t_a - 1) and (V1^-1)^T
     unsigned *d_wmax = nullptr;  // per level: bits of max |W| over occupied cells (FP16 mode)
     int esz = 2;               // operand element size in bytes
     void *Thi = nullptr, *Tlo = nullptr;  // operators [n_off][Np][Kp] (bf16, or fp32 when tf32)

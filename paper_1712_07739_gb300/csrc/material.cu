@@ -149,7 +149,7 @@ int material_setup(gbfmm_ctx *ctx) {
 int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
     if (!src->have_material) return set_err(ctx, GBFMM_ERR_NO_MATERIAL, "share_material: source has no material");
     if (ctx->opt.p != src->opt.p || ctx->opt.precision != src->opt.precision || ctx->opt.h_mode != src->opt.h_mode ||
-        ctx->opt.m2l_split != src->opt.m2l_split)
+        ctx->opt.m2l_split != src->opt.m2l_split || ctx->opt.m2l_basis != src->opt.m2l_basis)
         return set_err(ctx, GBFMM_ERR_INVALID_ARG, "share_material: options differ");
     ctx->mat = src->mat;
     std::memcpy(ctx->Asym, src->Asym, sizeof(ctx->Asym));
@@ -173,6 +173,9 @@ int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
     T.tf32 = S.tf32;
     T.fp16 = S.fp16;
     T.op_scale = S.op_scale;
+    T.modal = S.modal;
+    std::memcpy(T.basisV, S.basisV, sizeof(T.basisV));
+    std::memcpy(T.basisCt, S.basisCt, sizeof(T.basisCt));
     T.esz = S.esz;
     T.Thi = S.Thi;
     T.Tlo = S.Tlo;

@@ -576,6 +576,141 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
     }
 }
 
+// FP64 form of the symmetric near field for the FP64 pass: the same leaf-pair
+// work items, target chunks and partial slots as k_near_sym, with FP64
+// positions, source tensors (P of k_precontract<double>), h and sums.  The
+// cubic rule takes its circle points from a shared table; the general
+// medium uses h_circle_sym.  FP64 arithmetic is the bound, so two warps per
+// block and the full 108-entry tensors staged as doubles suffice.
+constexpr int S64_WARPS = 2, S64_SCH = 8;
+
+template <int HM>
+__global__ void __launch_bounds__(S64_WARPS * 32) k_near_sym64(
+    int L, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat, const int *__restrict__ sstart,
+    const double *__restrict__ ys, const double *__restrict__ P64, const int64_t *__restrict__ ssid,
+    double *__restrict__ part, int64_t N, const int2 *__restrict__ items, const int *__restrict__ n_items) {
+    extern __shared__ __align__(16) double sm_s64[];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    double *wPA = sm_s64 + warp * (32 * 108 + S64_SCH * 108);  // [32][108]: the chunk's target tensors
+    double *wPB = wPA + 32 * 108;                               // [SCH][108]: staged sources
+    __shared__ double sxB[S64_WARPS][S64_SCH][3];
+    __shared__ int64_t sdB[S64_WARPS][S64_SCH];
+    __shared__ double saccB[S64_WARPS][S64_SCH][6];
+    __shared__ double sC[81];
+    __shared__ double sTc[256], sTs[256];
+    if (HM == HM_GENERIC)
+        for (int i = threadIdx.x; i < 81; i += blockDim.x) sC[i] = mat->C[i];
+    if (HM == HM_CUBIC)
+        for (int i = threadIdx.x; i < mat->Q && i < 256; i += blockDim.x) sincospi(double(i) / double(mat->Q), &sTs[i], &sTc[i]);
+    __syncthreads();
+    const int64_t item = blockIdx.x * int64_t(S64_WARPS) + warp;
+    if (item >= *n_items) return;
+    const int2 wi = items[item];
+    const int64_t Aleaf = wi.x;
+    const int d = wi.y;
+    const int nlv = 1 << (L - 1);
+    int ax, ay, az;
+    cell_xyz3(Aleaf, nlv, ax, ay, az);
+    const int nb = 13 + d;
+    const int ox = nb % 3 - 1, oy = (nb / 3) % 3 - 1, oz = nb / 9 - 1;
+    const int64_t Bleaf = (int64_t(az + oz) * nlv + (ay + oy)) * nlv + (ax + ox);
+    const bool self = d == 0;
+    const int sA0 = sstart[Aleaf], sA1 = sstart[Aleaf + 1];
+    const int sB0 = sstart[Bleaf], sB1 = sstart[Bleaf + 1];
+    const int slot_f = nb, slot_r = self ? 27 : 26 - nb;
+    const int Q = mat->Q;
+    const double cp = mat->c12 + mat->c44, c44 = mat->c44, cd = mat->cd;
+    bool first_chunk = true;
+    for (int r0 = sA0, nrem = 0; r0 < sA1; r0 += nrem) {
+        const int left = sA1 - r0;
+        const int tg = left >= 29 ? 32 : left >= 13 ? 16 : left >= 5 ? 8 : left >= 3 ? 4 : left;
+        nrem = min(tg, left);
+        const int ls = 32 / tg, ti = lane % tg, tj = lane / tg;
+        const int i = r0 + ti;
+        const bool vi = i < sA1;
+        __syncwarp();
+        {
+            const double2 *src = reinterpret_cast<const double2 *>(P64 + int64_t(108) * r0);
+            double2 *dst = reinterpret_cast<double2 *>(wPA);
+            for (int k = lane; k < nrem * 54; k += 32) dst[k] = __ldg(src + k);
+        }
+        __syncwarp();
+        double xi[3] = {0.0, 0.0, 0.0};
+        int64_t segi = -2;
+        if (vi) {
+            xi[0] = ys[3 * int64_t(i)], xi[1] = ys[3 * int64_t(i) + 1], xi[2] = ys[3 * int64_t(i) + 2];
+            segi = ssid[i];
+        }
+        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        const double *Pi = wPA + 108 * ti;
+        const int jb0 = self ? r0 : sB0;
+        for (int j0 = jb0; j0 < sB1; j0 += S64_SCH) {
+            const int nj = min(S64_SCH, sB1 - j0);
+            __syncwarp();
+            if (lane < nj) sdB[warp][lane] = ssid[j0 + lane];
+            for (int k = lane; k < nj * 3; k += 32) (&sxB[warp][0][0])[k] = ys[3 * int64_t(j0) + k];
+            for (int k = lane; k < S64_SCH * 6; k += 32) (&saccB[warp][0][0])[k] = 0.0;
+            {
+                const double2 *src = reinterpret_cast<const double2 *>(P64 + int64_t(108) * j0);
+                double2 *dst = reinterpret_cast<double2 *>(wPB);
+                for (int k = lane; k < nj * 54; k += 32) dst[k] = __ldg(src + k);
+            }
+            __syncwarp();
+            for (int jj = 0; jj < nj; jj += ls) {
+                const int jl = jj + tj;
+                const int j = j0 + jl;
+                const bool on = vi && jl < nj && (!self || j > i) && sdB[warp][jl] != segi;
+                double fw[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, rv[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                if (on) {
+                    const double d3[3] = {xi[0] - sxB[warp][jl][0], xi[1] - sxB[warp][jl][1], xi[2] - sxB[warp][jl][2]};
+                    const double r2 = d3[0] * d3[0] + d3[1] * d3[1] + d3[2] * d3[2];
+                    if (r2 > 0.0) {
+                        const double ir = rsqrt(r2);
+                        const double T[3] = {d3[0] * ir, d3[1] * ir, d3[2] * ir};
+                        double hs[18];
+                        if (HM == HM_CUBIC)
+                            h_cubic_tab<double>(cp, c44, cd, Q, sTc, sTs, T, hs);
+                        else
+                            h_circle_sym<double, double>(sC, Q, T, hs);
+                        const double *Pj = wPB + 108 * jl;
+#pragma unroll
+                        for (int c = 0; c < 108; ++c) {
+                            fw[c / 18] = fma(Pj[c], hs[c % 18], fw[c / 18]);
+                            rv[c / 18] = fma(Pi[c], hs[c % 18], rv[c / 18]);
+                        }
+                        const double ir2 = ir * ir;
+#pragma unroll
+                        for (int ab = 0; ab < 6; ++ab) {
+                            acc[ab] += fw[ab] * ir2;
+                            rv[ab] *= -ir2;
+                        }
+                    }
+                }
+                for (int off = 1; off < tg; off <<= 1)
+#pragma unroll
+                    for (int ab = 0; ab < 6; ++ab) rv[ab] += __shfl_xor_sync(0xffffffffu, rv[ab], off);
+                if (ti == 0 && jl < nj)
+#pragma unroll
+                    for (int ab = 0; ab < 6; ++ab) saccB[warp][jl][ab] += rv[ab];
+            }
+            __syncwarp();
+            for (int k = lane; k < nj * 6; k += 32) {
+                const int jl = k / 6, ab = k % 6;
+                double *dst = part + (int64_t(slot_r) * N + (j0 + jl)) * 6 + ab;
+                const double v = saccB[warp][jl][ab];
+                *dst = first_chunk ? v : *dst + v;
+            }
+        }
+        first_chunk = false;
+        for (int off = tg; off < 32; off <<= 1)
+#pragma unroll
+            for (int ab = 0; ab < 6; ++ab) acc[ab] += __shfl_xor_sync(0xffffffffu, acc[ab], off);
+        if (vi && tj == 0)
+#pragma unroll
+            for (int ab = 0; ab < 6; ++ab) part[(int64_t(slot_f) * N + i) * 6 + ab] = acc[ab];
+    }
+}
+
 // far field (L2P) plus the partial slots, in a fixed order
 __global__ void k_near_combine(int p, int L, int64_t N, const TreeBox *__restrict__ box,
                                const int *__restrict__ sstart, const int *__restrict__ pleaf,
@@ -1123,19 +1258,57 @@ int near_sym_alloc(gbfmm_ctx *ctx) {
     return GBFMM_OK;
 }
 
-static int near_run_sym(gbfmm_ctx *ctx, double *sig) {
+// leaf-pair work items of the symmetric near fields, heaviest first (count, scan, fill, order)
+static int build_pair_items(gbfmm_ctx *ctx) {
     const int64_t nl = ctx->n_leaves, N = ctx->N;
     if (int rc = near_alloc(ctx, N)) return rc;
     if (int rc = near_sym_alloc(ctx)) return rc;
     NearWork &W = ctx->nw;
     cudaStream_t st = ctx->stream;
     CK(cudaMemsetAsync(W.pmisc, 0, 192 * sizeof(int), st));
-    ctx->launches += 6;
+    ctx->launches += 4;
     k_pairs_count<<<nblk(nl, 256), 256, 0, st>>>(nl, ctx->L, ctx->d_leaf_start, W.cnt);
     k_scan_small<<<1, 1024, 0, st>>>(nl, W.cnt, W.off);
     k_pairs_fill<<<nblk(nl, 256), 256, 0, st>>>(nl, ctx->L, ctx->d_leaf_start, W.off, W.pitems, W.pkeys, W.pmisc);
     k_items_order<<<nblk(W.pcap, 256) < 1024 ? nblk(W.pcap, 256) : 1024, 256, 0, st>>>(
         int(W.pcap), W.off + nl, W.pitems, W.pkeys, W.pmisc, W.pmisc + 64, W.psorted, W.pmisc + 128);
+    CK(cudaGetLastError());
+    return GBFMM_OK;
+}
+
+// FP64 pass, nodal forces with the unit-circle h: symmetric near field in FP64, then
+// L2P from the FP64 local values and the partial slots (k_near_combine)
+int near_run_sym64(gbfmm_ctx *ctx, double *sig) {
+    if (int rc = build_pair_items(ctx)) return rc;
+    const int64_t N = ctx->N;
+    NearWork &W = ctx->nw;
+    cudaStream_t st = ctx->stream;
+    const size_t smem = size_t(S64_WARPS) * (32 + S64_SCH) * 108 * sizeof(double);
+    const unsigned grid = nblk(W.pcap, S64_WARPS);
+    ctx->launches += 2;
+    if (ctx->mat.cubic) {
+        CK(cudaFuncSetAttribute(k_near_sym64<HM_CUBIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_near_sym64<HM_CUBIC><<<grid, S64_WARPS * 32, smem, st>>>(ctx->L, ctx->d_box, ctx->d_mat, ctx->d_leaf_start,
+                                                                   ctx->d_y, ctx->d_P, ctx->d_sid, W.part, N,
+                                                                   W.psorted, W.pmisc + 128);
+    } else {
+        CK(cudaFuncSetAttribute(k_near_sym64<HM_GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_near_sym64<HM_GENERIC><<<grid, S64_WARPS * 32, smem, st>>>(ctx->L, ctx->d_box, ctx->d_mat,
+                                                                     ctx->d_leaf_start, ctx->d_y, ctx->d_P, ctx->d_sid,
+                                                                     W.part, N, W.psorted, W.pmisc + 128);
+    }
+    k_near_combine<<<nblk(N, 256), 256, 0, st>>>(ctx->opt.p, ctx->L, N, ctx->d_box, ctx->d_leaf_start, ctx->d_pleaf,
+                                                 ctx->d_y, nullptr, ctx->d_S, W.part, sig);
+    CK(cudaGetLastError());
+    return GBFMM_OK;
+}
+
+static int near_run_sym(gbfmm_ctx *ctx, double *sig) {
+    if (int rc = build_pair_items(ctx)) return rc;
+    const int64_t N = ctx->N;
+    NearWork &W = ctx->nw;
+    cudaStream_t st = ctx->stream;
+    ctx->launches += 2;
     const float near2 = float(ctx->opt.near_fp64 * ctx->opt.near_fp64);
     const size_t smem = size_t(SYM_WARPS) * (32 + SYM_SCH) * 108 * sizeof(float);
     const unsigned grid = nblk(W.pcap, SYM_WARPS);

@@ -40,7 +40,9 @@ def test_near_work_counts():
     general = dict(wl, C=lambda: synth.rotated_voigt(synth.cubic_voigt(), synth.rotation()))
     assert bench.near_flops(general, work)[0] > flops
     fp64, k64 = bench.near_flops(dict(wl, precision="fp64"), work)
-    assert k64 == "k_leaf_eval_f64" and fp64 == 1000 * one_sided + l2p
+    assert k64 == "k_near_sym64" and fp64 == flops  # the FP64 pass's symmetric kernel does the same work
+    fiso, kfiso = bench.near_flops(dict(bench.WORKLOADS["c3_iso"], precision="fp64"), work)
+    assert kfiso == "k_leaf_eval_f64" and fiso == 1000 * 341 + l2p
     iso, kiso = bench.near_flops(bench.WORKLOADS["c3_iso"], work)
     assert kiso == "k_near_mixed" and iso == 1000 * 202 + l2p
 
