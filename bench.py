@@ -115,29 +115,35 @@ WORKLOADS = {
         gen=lambda seed: synth.hexagon_loops(seed=seed), C=lambda: synth.isotropic_voigt(1.0, 0.3),
         h_mode="iso", p=4, levels=3, precision="fp64"),
 }
+# The mixed pass's M2L operands in every mixed workload below: FP16 Legendre moments of
+# the source cells, residual (hi + lo) passes on the leading block of low-order moments,
+# the offsets summed in 7 runs (the library defaults, spelled out).
+MIXED_M2L = dict(m2l_split=6, m2l_basis=1, m2l_chunks=7, m2l_split_kblocks=1)
 WORKLOADS["c3"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs, sigma 0.02), cubic C11=1.684 C12=1.214 "
-         "C44=0.754, order p=6, mixed precision (FP16 tensor-core M2L with per-level scaling, FP32 near field with "
-         "FP64 close pairs), unit-circle h (cubic form, Q=20 points on the half circle), 7-level octree",
+         "C44=0.754, order p=7, 7-level octree, mixed precision (tensor-core M2L on FP16 Legendre moments with "
+         "residual passes on the low-order moments, FP32 near field with FP64 separations for close pairs), "
+         "unit-circle h (cubic form, Q=20 points on the half circle); the same step through the plain FP64 pass "
+         "is timed in the same run",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
-    h_mode="circle", circle_q=20, p=6, levels=7, precision="mixed")
+    h_mode="circle", circle_q=20, p=7, levels=7, precision="mixed", fp64_arm=True, **MIXED_M2L)
 WORKLOADS["c3_iso"] = dict(
-    desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs), isotropic mu=1 nu=0.3, p=6, mixed precision",
+    desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs), isotropic mu=1 nu=0.3, p=7, mixed precision",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.isotropic_voigt(1.0, 0.3),
-    h_mode="iso", p=6, levels=7, precision="mixed")
+    h_mode="iso", p=7, levels=7, precision="mixed", **MIXED_M2L)
 WORKLOADS["c3q"] = dict(
-    desc="profiling case: 250,000 segments (5,000 loops x 50 in 32 Gaussian slabs), cubic, p=6, mixed, 6-level octree",
+    desc="profiling case: 250,000 segments (5,000 loops x 50 in 32 Gaussian slabs), cubic, p=7, mixed, 6-level octree",
     gen=lambda seed: synth.slab_loops(n_loops=5000, seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
-    h_mode="circle", circle_q=20, p=6, levels=6, precision="mixed")
+    h_mode="circle", circle_q=20, p=7, levels=6, precision="mixed", **MIXED_M2L)
 WORKLOADS["c3_mlp"] = dict(
     desc="c3 network with the learned angular factor in the near field (pairs beyond 8 segment lengths in bins "
          "the plain evaluator accepted at 2e-2 x RMS(h)), plain cubic rule elsewhere",
-    gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="mlp", circle_q=20, p=6, levels=7,
-    precision="mixed", mlp=dict(n_dirs=2_000_000, epochs=12, batch=8192, lr=3e-3, bin_tol=2e-2))
+    gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="mlp", circle_q=20, p=7, levels=7,
+    precision="mixed", mlp=dict(n_dirs=2_000_000, epochs=12, batch=8192, lr=3e-3, bin_tol=2e-2), **MIXED_M2L)
 WORKLOADS["c3_fp64"] = dict(
-    desc="the 1,000,000-segment cubic slab network of c3 through the plain FP64 path: FP64 M2L, FP64 near field, "
-         "unit-circle h (cubic form, Q=32), p=6, 7-level octree",
-    gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=32, p=6, levels=7,
+    desc="the 1,000,000-segment cubic slab network of c3 through the plain FP64 path: FP64 M2L through transforms, "
+         "symmetric FP64 near field, unit-circle h (cubic form, Q=20), p=7, 7-level octree",
+    gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=20, p=7, levels=7,
     precision="fp64")
 WORKLOADS["c3q_iso_fp64"] = dict(
     desc="250,000 segments (5,000 loops x 50 in 32 Gaussian slabs), isotropic mu=1 nu=0.3, plain FP64 path, p=6, "
@@ -146,10 +152,10 @@ WORKLOADS["c3q_iso_fp64"] = dict(
     precision="fp64")
 WORKLOADS["c5"] = dict(
     desc="64 independent cubic networks, N_s log-uniform in [1e4, 2e5] (4,639,301 segments in all), loop "
-         "densities 0.2-5x, mixed precision p=6, unit-circle Q=20, depth per network by the autotuner, evaluation "
-         "of all 64 recorded in one CUDA graph",
+         "densities 0.2-5x, mixed precision p=7 (M2L operands as c3), unit-circle Q=20, depth per network by "
+         "the autotuner, evaluation of all 64 recorded in one CUDA graph",
     batch=True, gen_batch=lambda seed: synth.ensemble(seed=4 + 1000 * seed), C=lambda: synth.cubic_voigt(),
-    h_mode="circle", circle_q=20, p=6, levels=0, precision="mixed")
+    h_mode="circle", circle_q=20, p=7, levels=0, precision="mixed", **MIXED_M2L)
 DEFAULT_WORKLOAD = "c3"
 
 
@@ -321,7 +327,7 @@ def run_batch(args, wl):
     n_segs = sum(len(s) for _, s, _ in nets)
     dn = [(torch.tensor(n, device=dev), torch.tensor(s, device=dev), torch.tensor(b, device=dev)) for n, s, b in nets]
     bt = gb.Batch(len(nets), p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
-                  circle_q=wl.get("circle_q", 0)).set_material(wl["C"]())
+                  circle_q=wl.get("circle_q", 0), **m2l_options(wl)).set_material(wl["C"]())
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
@@ -376,7 +382,7 @@ def run_batch(args, wl):
     # roofline of the dominant kernel on the largest network, measured alone
     big = int(np.argmax([len(s) for _, s, _ in nets]))
     f = gb.FMM(p=wl["p"], levels=depths[big], precision=wl["precision"], h_mode=wl["h_mode"],
-               circle_q=wl.get("circle_q", 0)).set_material(wl["C"]())
+               circle_q=wl.get("circle_q", 0), **m2l_options(wl)).set_material(wl["C"]())
     f.build(*dn[big])
     out = torch.empty((len(nets[big][0]), 3), dtype=torch.float64, device=dev)
     f.nodal_forces(out=out)
@@ -435,9 +441,8 @@ def run_ours(args, wl):
     d_segs = torch.tensor(segs, device=dev)
     d_b = torch.tensor(b, device=dev)
     f = gb.FMM(p=wl["p"], levels=args.levels or wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
-               circle_q=wl.get("circle_q", 0), m2l_split=wl.get("m2l_split", 4),
-               m2l_chunks=wl.get("m2l_chunks"), m2l_basis=wl.get("m2l_basis"),
-               m2l_fft=None if args.m2l_fft < 0 else args.m2l_fft)
+               circle_q=wl.get("circle_q", 0), m2l_fft=None if args.m2l_fft < 0 else args.m2l_fft,
+               **m2l_options(wl))
     f.set_material(wl["C"]())
     mlp_info = None
     if wl["h_mode"] == "mlp":
@@ -540,9 +545,9 @@ def run_ours(args, wl):
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "n_segs": n_segs, "levels": info["levels"],
                        "p": p, "precision": wl["precision"], "h_mode": wl["h_mode"],
-                       "circle_q": wl.get("circle_q", 0), "m2l_split": wl.get("m2l_split", 4),
-                       "m2l_chunks": wl.get("m2l_chunks", 1), "m2l_basis": wl.get("m2l_basis", 0),
-                       "m2l_fft": int(f.options.m2l_fft),
+                       "circle_q": wl.get("circle_q", 0), "m2l_split": int(f.options.m2l_split),
+                       "m2l_chunks": int(f.options.m2l_chunks), "m2l_basis": int(f.options.m2l_basis),
+                       "m2l_split_kblocks": int(f.options.m2l_split_kblocks), "m2l_fft": int(f.options.m2l_fft),
                        "l2": "flushed: 256 MiB write between steps, outside the step events",
                        "step": "fmm_build_tree + fmm_eval_nodal_forces"},
             "stage_ms": {"precontract": st[:, 0].mean(), "p2m_m2m": st[:, 1].mean(), "m2l": st[:, 2].mean(),
@@ -562,7 +567,12 @@ def run_ours(args, wl):
         torch.distributed.destroy_process_group()
 
 
-GOLDEN = {"c3": "c3_sampled_forces.json", "c3q": "c3q_sampled_forces.json"}
+GOLDEN = {"c3": "c3_sampled_forces.json", "c3q": "c3q_sampled_forces.json", "c3_fp64": "c3_sampled_forces.json"}
+
+
+def m2l_options(wl):
+    """The tensor-core M2L operand options a workload names (library defaults otherwise)."""
+    return {k: wl[k] for k in ("m2l_split", "m2l_basis", "m2l_chunks", "m2l_split_kblocks") if k in wl}
 
 
 def oracle_node_error(wl, name, F, nodes, segs, b):
@@ -666,6 +676,7 @@ def main():
     ap.add_argument("--m2l-fft", type=int, default=-1, help="FP64 path: 1 = M2L through transforms, 0 = dense")
     ap.add_argument("--m2l-chunks", type=int, default=-1, help="override the M2L offset chunks (fmm options)")
     ap.add_argument("--m2l-basis", type=int, default=-1, help="override the M2L operand basis (fmm options)")
+    ap.add_argument("--m2l-split-kblocks", type=int, default=-1, help="override the residual K blocks (fmm options)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.p:
@@ -678,6 +689,8 @@ def main():
         wl["m2l_chunks"] = args.m2l_chunks
     if args.m2l_basis >= 0:
         wl["m2l_basis"] = args.m2l_basis
+    if args.m2l_split_kblocks >= 0:
+        wl["m2l_split_kblocks"] = args.m2l_split_kblocks
     if args.impl == "reference":
         run_reference(args, wl)
     elif wl.get("batch"):

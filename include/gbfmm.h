@@ -63,9 +63,10 @@ extern "C" {
 #define GBFMM_M2L_BF16 1            /* BF16 only */
 #define GBFMM_M2L_BF16_SPLIT_ALL 2  /* BF16, residual passes on all 316 offsets */
 #define GBFMM_M2L_TF32 3            /* FP32 operands, kind::tf32 */
-#define GBFMM_M2L_FP16 4            /* FP16, multipole values scaled per level (fmm_default_options) */
+#define GBFMM_M2L_FP16 4            /* FP16, multipole values scaled per level */
 #define GBFMM_M2L_FP16_SPLIT 5      /* FP16 scaled, residual passes on the offsets with max |o_i| = 2 */
-#define GBFMM_M2L_FP16_SPLIT_ALL 6  /* FP16 scaled, residual passes on all 316 offsets */
+#define GBFMM_M2L_FP16_SPLIT_ALL 6  /* FP16 scaled, residual passes on all 316 offsets (fmm_default_options,
+                                       over the leading K block: m2l_split_kblocks = 1) */
 
 typedef struct {
     int p;                 /* Lagrange nodes per dimension, 2..8 (Sec. 4.1) */
@@ -83,9 +84,9 @@ typedef struct {
                               all 316 offsets, 3 = TF32 (FP32 operands), 4 = FP16 with
                               per-level scaling of the multipole values (a power of two from
                               each level's largest |W|) and one power-of-two scale for the
-                              operators (fmm_default_options), 5 = as 4 plus residual passes
+                              operators, 5 = as 4 plus residual passes
                               on the offsets with max |o_i| = 2, 6 = as 4 plus residual
-                              passes on all 316 offsets */
+                              passes on all 316 offsets (fmm_default_options) */
     double mlp_min_dist;   /* GBFMM_H_MLP: near pairs closer than this many source segment
                               lengths use the plain evaluator; 0 = 8 */
     int m2l_fft;           /* FP64: 1 = M2L through the Toeplitz structure of the operators
@@ -99,22 +100,31 @@ typedef struct {
                               many consecutive runs, each accumulated in tensor memory from
                               zero and added to the local values in FP32 (FP64 with
                               GBFMM_MIXED_F64T); shorter accumulation chains, one launch per
-                              run.  0 = 1. */
+                              run.  0 = 1; fmm_default_options: 7. */
     int m2l_basis;         /* MIXED: operands of the tensor-core M2L.  0 = the node values of
                               Eq. "m2l" (multipole values at the source cell's nodes); 1 = the
                               Legendre moments of each source cell, sum_j P_k(y_j) q_j with
                               Legendre polynomials of degree < p per axis, against operators
                               T V^-1 precomputed in FP64 -- the same product in exact
                               arithmetic, without the oscillating node values whose
-                              cancellation inside each GEMM costs precision. */
+                              cancellation inside each GEMM costs precision
+                              (fmm_default_options). */
     int m2l_split_levels;  /* MIXED, m2l_split 0, 2, 5 or 6: the residual passes apply only at
                               the tree levels whose bit is set (bit l = level l); 0 = all. */
+    int m2l_split_kblocks; /* MIXED, with residual passes: they cover only this many leading
+                              K blocks of 64 operand columns (0 = all).  With m2l_basis = 1
+                              the columns are ordered by the moments' total degree, so the
+                              leading blocks hold the low-order moments, which carry most of
+                              every product and hence most of its rounding error
+                              (fmm_default_options: 1). */
 } gbfmm_options;
 
 typedef struct gbfmm_ctx gbfmm_ctx;
 
-/* Fill *opt with defaults (p=4, n_gauss=4, levels=0, FP64, H_ISO, m2l_split = GBFMM_M2L_FP16,
-   m2l_fft = 1). */
+/* Fill *opt with defaults (p=4, n_gauss=4, levels=0, FP64, H_ISO, m2l_fft = 1; for the mixed
+   pass: m2l_split = GBFMM_M2L_FP16_SPLIT_ALL with m2l_split_kblocks = 1, m2l_basis = 1,
+   m2l_chunks = 7 -- FP16 Legendre-moment operands, residual passes on the leading block of
+   low-order moments, offsets summed in 7 runs). */
 void fmm_default_options(gbfmm_options *opt);
 
 /* Create a context.  opt: host, copied.  cuda_stream: a cudaStream_t or NULL.

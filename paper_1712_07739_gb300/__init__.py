@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
         ("precision", ctypes.c_int), ("h_mode", ctypes.c_int), ("circle_q", ctypes.c_int),
         ("leaf_segments", ctypes.c_int), ("near_fp64", ctypes.c_double), ("m2l_split", ctypes.c_int),
         ("mlp_min_dist", ctypes.c_double), ("m2l_fft", ctypes.c_int), ("m2l_chunks", ctypes.c_int),
-        ("m2l_basis", ctypes.c_int), ("m2l_split_levels", ctypes.c_int),
+        ("m2l_basis", ctypes.c_int), ("m2l_split_levels", ctypes.c_int), ("m2l_split_kblocks", ctypes.c_int),
     ]
 
 
@@ -142,8 +142,8 @@ class FMM:
     """
 
     def __init__(self, p=4, n_gauss=4, levels=0, precision="fp64", h_mode="iso", circle_q=0,
-                 leaf_segments=0, near_fp64=0.0, m2l_split=4, mlp_min_dist=0.0, m2l_fft=None, m2l_chunks=None,
-                 m2l_basis=None, m2l_split_levels=None, stream=None):
+                 leaf_segments=0, near_fp64=0.0, m2l_split=None, mlp_min_dist=0.0, m2l_fft=None, m2l_chunks=None,
+                 m2l_basis=None, m2l_split_levels=None, m2l_split_kblocks=None, stream=None):
         import torch
 
         self._torch = torch
@@ -154,7 +154,8 @@ class FMM:
         o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
         o.h_mode = _HMODE[h_mode] if isinstance(h_mode, str) else int(h_mode)
         o.circle_q, o.leaf_segments, o.near_fp64 = circle_q, leaf_segments, near_fp64
-        o.m2l_split = m2l_split
+        if m2l_split is not None:
+            o.m2l_split = int(m2l_split)
         o.mlp_min_dist = mlp_min_dist
         if m2l_fft is not None:
             o.m2l_fft = int(m2l_fft)
@@ -164,6 +165,8 @@ class FMM:
             o.m2l_basis = int(m2l_basis)
         if m2l_split_levels is not None:
             o.m2l_split_levels = int(m2l_split_levels)
+        if m2l_split_kblocks is not None:
+            o.m2l_split_kblocks = int(m2l_split_kblocks)
         self.options = o
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -334,7 +337,8 @@ class Batch:
     autotuned depth per network with levels=0, graph-recorded evaluation)."""
 
     def __init__(self, n_configs, p=6, n_gauss=4, levels=0, precision="mixed", h_mode="circle", circle_q=0,
-                 leaf_segments=0, near_fp64=0.0, m2l_split=4, stream=None):
+                 leaf_segments=0, near_fp64=0.0, m2l_split=None, m2l_basis=None, m2l_chunks=None,
+                 m2l_split_levels=None, m2l_split_kblocks=None, stream=None):
         import torch
 
         self._torch = torch
@@ -344,7 +348,11 @@ class Batch:
         o.p, o.n_gauss, o.levels = p, n_gauss, levels
         o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
         o.h_mode = _HMODE[h_mode] if isinstance(h_mode, str) else int(h_mode)
-        o.circle_q, o.leaf_segments, o.near_fp64, o.m2l_split = circle_q, leaf_segments, near_fp64, m2l_split
+        o.circle_q, o.leaf_segments, o.near_fp64 = circle_q, leaf_segments, near_fp64
+        for name, v in (("m2l_split", m2l_split), ("m2l_basis", m2l_basis), ("m2l_chunks", m2l_chunks), ("m2l_split_levels", m2l_split_levels),
+                        ("m2l_split_kblocks", m2l_split_kblocks)):
+            if v is not None:
+                setattr(o, name, int(v))
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -104,8 +104,11 @@ extern "C" void fmm_default_options(gbfmm_options *o) {
     o->circle_q = 0;
     o->leaf_segments = 0;
     o->near_fp64 = 0.0;
-    o->m2l_split = GBFMM_M2L_FP16;
+    o->m2l_split = GBFMM_M2L_FP16_SPLIT_ALL;
     o->m2l_fft = 1;
+    o->m2l_chunks = 7;
+    o->m2l_basis = 1;
+    o->m2l_split_kblocks = 1;
 }
 
 extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *stream) {
@@ -116,7 +119,8 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
         (opt->precision < GBFMM_FP64 || opt->precision > GBFMM_MIXED_F64T) || opt->h_mode < 0 || opt->h_mode > 2 ||
         opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0) || opt->m2l_split < 0 ||
         opt->m2l_split > 6 || opt->m2l_fft < 0 || opt->m2l_fft > 1 || opt->m2l_chunks < 0 ||
-        opt->m2l_chunks > 189 || opt->m2l_basis < 0 || opt->m2l_basis > 1)
+        opt->m2l_chunks > 189 || opt->m2l_basis < 0 || opt->m2l_basis > 1 ||
+        opt->m2l_split_kblocks < 0)
         return GBFMM_ERR_INVALID_ARG;
     gbfmm_ctx *ctx = new gbfmm_ctx();
     ctx->opt = *opt;

@@ -70,6 +70,7 @@ struct M2LParams {
     CUtensorMap tmT;                  // T hi: (Kp, Np, 316)
     CUtensorMap tmTlo;                // T residual: (Kp, Np, n_lo)
     int kb;         // K blocks of 64
+    int kb_res;     // K blocks the residual passes cover (the leading ones)
     int nsub;       // N per MMA (multiple of 16, <= 256)
     int ncta;       // operator rows per CTA (= nsub)
     int nvalid;     // 6 p^3
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(192, 1)
             for (int pass = 0; pass < np && ok; ++pass) {
                 const CUtensorMap *tb = (pass == 2) ? &P.tmTlo : &P.tmT;
                 const int tidx = (pass == 2) ? e.lo : e.top;
-                for (int kb = 0; kb < P.kb; ++kb, ++it) {
+                for (int kb = 0; kb < (pass == 0 ? P.kb : P.kb_res); ++kb, ++it) {
                     const int s = it % stages;
                     const uint32_t ph = (it / stages) & 1;
                     if (!mbar_wait(empty0 + 8 * s, ph ^ 1, status)) {
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(192, 1)
             const OffsetEntry e = c_offs[cls][oi];
             const int np = passes_of(e, split);
             for (int pass = 0; pass < np && ok; ++pass) {
-                for (int kb = 0; kb < P.kb; ++kb, ++it) {
+                for (int kb = 0; kb < (pass == 0 ? P.kb : P.kb_res); ++kb, ++it) {
                     const int s = it % stages;
                     const uint32_t ph = (it / stages) & 1;
                     if (!mbar_wait(full0 + 8 * s, ph, status)) {
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(192, 1)
                 const int np = passes_of(e, split);
                 for (int pass = 0; pass < np && ok; ++pass) {
                     const uint8_t *wb = ((pass == 1) ? P.Wlo : P.Whi) + P.wofs[level];
-                    for (int kb = 0; kb < P.kb; ++kb, ++it) {
+                    for (int kb = 0; kb < (pass == 0 ? P.kb : P.kb_res); ++kb, ++it) {
                         const int s = it % stages;
                         const uint32_t ph = (it / stages) & 1;
                         if (!mbar_wait(empty0 + 8 * s, ph ^ 1, status)) {
@@ -610,6 +611,7 @@ struct BasisMats {
     double V[GB_MAXP * GB_MAXP];   // V1[n][a]
     double Ct[GB_MAXP * GB_MAXP];  // (V1^-1)^T[n][a]
     float Vf[GB_MAXP * GB_MAXP];   // V1 in FP32 (moments of the FP32 pass)
+    short pos[GB_MAXP * GB_MAXP * GB_MAXP];  // K position of moment (kz p + ky) p + kx: by total degree
 };
 
 // out[.., n, ..] = sum_a M[n][a] in[.., a, ..] along one node axis of a [p^3][9] block,
@@ -670,11 +672,13 @@ __global__ void k_build_ops_modal(int p, int lat_n, int Np, int Kp, const double
         if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(absmax, (unsigned long long)__double_as_longlong(mx));
         return;
     }
+    // column of moment kk, component wr: 9 pos[kk] + wr (moments ordered by total degree)
     for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+        const int e = k < 9 * P3 ? 9 * B.pos[k / 9] + k % 9 : k;
         const double v = k < 9 * P3 ? scale * b[k] : 0.0;
         const E hi = to_elem<E>(v);
-        Thi[row + k] = hi;
-        if (li >= 0 && Tlo) Tlo[(int64_t(li) * Np + nn) * Kp + k] = to_elem<E>(v - elem_value(hi));
+        Thi[row + e] = hi;
+        if (li >= 0 && Tlo) Tlo[(int64_t(li) * Np + nn) * Kp + e] = to_elem<E>(v - elem_value(hi));
     }
 }
 
@@ -706,7 +710,7 @@ __global__ void k_w_modal(int level, int p, const __grid_constant__ BasisMats B,
             axis_pass<TW, float>(p, 2, B.Vf, a, b);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < 9 * P3; e += blockDim.x) w[e] = b[e];
+        for (int e = threadIdx.x; e < 9 * P3; e += blockDim.x) w[9 * B.pos[e / 9] + e % 9] = b[e];
     }
 }
 
@@ -906,6 +910,12 @@ static BasisMats basis_of(const TcPlan &T, int p) {
         B.Ct[i] = T.basisCt[i];
         B.Vf[i] = float(T.basisV[i]);
     }
+    // moments ordered by total degree kx + ky + kz (then by index): the leading K
+    // blocks hold the low-order moments, which carry most of each product
+    int next = 0;
+    for (int deg = 0; deg <= 3 * (p - 1); ++deg)
+        for (int kk = 0; kk < p * p * p; ++kk)
+            if (kk % p + (kk / p) % p + kk / (p * p) == deg) B.pos[kk] = short(next++);
     return B;
 }
 
@@ -1207,6 +1217,7 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     }
     prm.kstep = 128 / T.esz;
     prm.kb = T.Kp / prm.kstep;
+    prm.kb_res = ctx->opt.m2l_split_kblocks > 0 ? std::min(prm.kb, ctx->opt.m2l_split_kblocks) : prm.kb;
     prm.idesc = idesc_of(128, T.nsub, T.tf32, T.fp16);
     prm.wmax = T.fp16 ? T.d_wmax : nullptr;
     prm.inv_op_scale = float(1.0 / T.op_scale);

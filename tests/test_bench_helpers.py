@@ -28,9 +28,9 @@ def test_cubic_alignment_detection():
 
 def test_near_work_counts():
     work = {"near_pairs": 1000, "points": 10}
-    p = 6
-    l2p = 10 * (12 * p ** 3 + 30 * p)
     wl = dict(bench.WORKLOADS["c3"])
+    p = wl["p"]
+    l2p = 10 * (12 * p ** 3 + 30 * p)
     flops, kernel = bench.near_flops(wl, work)
     assert kernel == "k_near_sym"
     # one unit-circle evaluation per unordered pair, one contraction per direction

@@ -1,11 +1,13 @@
 """Parity at the full 1M-segment size, in the launch configuration bench.py
-times (mixed precision, p = 6, 7-level octree, cubic unit-circle rule with
-Q = 20, FP16 tensor-core M2L), on nodes the oracle computed one by one: the
-direct Mura sum of Eq. "stress3" against all 4M source points (oracle
-Q = 32, ~2e-10 in h), stored in tests/golden/c3_sampled_forces.json by
-tests/golden/make_c3_sampled_forces.py.  The mixed pass is also compared
-with the plain FP64 pass at the same order on a quarter-size network, which
-separates the precision error from the interpolation error of order p.
+times (mixed precision, p = 7, 7-level octree, cubic unit-circle rule with
+Q = 20, tensor-core M2L on FP16 Legendre moments with residual passes on the
+low-order moments), on nodes the oracle computed one by one: the direct Mura
+sum of Eq. "stress3" against all 4M source points (oracle Q = 32, ~2e-10 in
+h), stored in tests/golden/c3_sampled_forces.json by
+tests/golden/make_c3_sampled_forces.py.  The 1e-4 bar of the method's
+accuracy target applies to the bench configuration.  On a quarter-size
+network the same configuration and the FP64 pass are held against stored
+direct-sum forces too.
 """
 import json
 import os
@@ -47,10 +49,11 @@ def c3_case():
 
 
 def _forces(nodes, segs, b, wl, **over):
+    import bench
     import paper_1712_07739_gb300 as gb
 
     kw = dict(p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
-              circle_q=wl["circle_q"], m2l_split=wl.get("m2l_split", 4))
+              circle_q=wl["circle_q"], **bench.m2l_options(wl))
     kw.update(over)
     f = gb.FMM(**kw).set_material(wl["C"]())
     f.build(torch.tensor(nodes, device="cuda"), torch.tensor(segs, device="cuda"), torch.tensor(b, device="cuda"))
@@ -61,16 +64,12 @@ def _forces(nodes, segs, b, wl, **over):
 
 
 @pytest.mark.parametrize("label,over,tol", [
-    pytest.param("bench configuration", {}, 3e-4, id="bench"),
-    pytest.param("BF16, residual passes on the nearest offsets", {"m2l_split": 0}, 3e-4, id="bf16split"),
-    pytest.param("p=7", {"p": 7}, 3e-4, id="p7"),
-    pytest.param("p=7, FP16 with residual passes on the nearest offsets", {"p": 7, "m2l_split": 5}, 3e-4,
-                 id="p7split"),
-    pytest.param("p=8, FP16 with residual passes on the nearest offsets", {"p": 8, "m2l_split": 5}, 3e-4,
-                 id="p8split"),
-    pytest.param("p=7, FP64 interpolation stages", {"p": 7, "precision": "mixed_f64t"}, 3e-4, id="p7f64t"),
-    pytest.param("p=8, FP64 interpolation stages, FP16 with residual passes on the nearest offsets",
-                 {"p": 8, "precision": "mixed_f64t", "m2l_split": 5}, 3e-4, id="p8f64t"),
+    pytest.param("bench configuration", {}, 1e-4, id="bench"),
+    pytest.param("p=8", {"p": 8}, 1e-4, id="p8"),
+    pytest.param("p=7, FP64 interpolation stages", {"precision": "mixed_f64t"}, 1e-4, id="p7f64t"),
+    # order 6 is not enough for the slab walls: its interpolation error alone (the FP64 pass
+    # at p = 6) is ~1.6e-4 against the direct sum, which is why the bench runs p = 7
+    pytest.param("p=6", {"p": 6}, 3e-4, id="p6"),
 ])
 def test_full_size_sampled_nodes_match_direct_sum(c3_case, label, over, tol):
     nodes, segs, b, wl, ids, Fo = c3_case
@@ -83,16 +82,13 @@ def test_full_size_sampled_nodes_match_direct_sum(c3_case, label, over, tol):
     assert err < tol
 
 
-def test_mixed_matches_fp64_pass_at_same_order():
-    """250,000 segments of the slab walls (6 levels): the mixed pass against
-    the plain FP64 pass at p = 6 over all nodes -- the precision error alone,
-    which must stay under 1e-4."""
-    wl = _bench_workload("c3q")
-    nodes, segs, b = wl["gen"](0)
-    Fm = _forces(nodes, segs, b, wl)
-    Fd = _forces(nodes, segs, b, wl, precision="fp64", circle_q=32)
-    err = oracle.rel_l2(Fm, Fd)
-    print(f"250k segments, mixed vs FP64 pass, p=6: rel L2 {err:.3e}")
+def test_full_size_fp64_pass_matches_direct_sum(c3_case):
+    """The plain FP64 pass at the bench's order and tree (the comparison arm
+    bench.py times), against the same stored nodes."""
+    nodes, segs, b, wl, ids, Fo = c3_case
+    F = _forces(nodes, segs, b, wl, precision="fp64")
+    err = np.linalg.norm(F[ids] - Fo) / np.linalg.norm(Fo)
+    print(f"1M segments, FP64 pass p={wl['p']}: vs direct sum {err:.3e}")
     assert err < 1e-4
 
 
@@ -120,11 +116,12 @@ def test_full_size_repeatable_and_linear_in_b():
 GOLDEN_Q = os.path.join(ROOT, "tests", "golden", "c3q_sampled_forces.json")
 
 
-@pytest.mark.parametrize("p,prec", [(6, "mixed"), (8, "mixed"), (8, "mixed_f64t")])
+@pytest.mark.parametrize("p,prec", [(7, "mixed"), (8, "mixed"), (8, "mixed_f64t")])
 def test_quarter_size_error_budget(p, prec):
     """250,000-segment slab network, 32 nodes against the direct sum (stored
-    by tests/golden/make_c3q_sampled_forces.py): the FP64 pass measures the
-    interpolation error of order p, the mixed pass adds the precision error."""
+    by tests/golden/make_c3q_sampled_forces.py): the FP64 pass shows the
+    interpolation error of order p, the mixed pass adds the rounding error;
+    both meet 1e-4 against the oracle."""
     wl = _bench_workload("c3q")
     nodes, segs, b = wl["gen"](0)
     with open(GOLDEN_Q) as fh:
@@ -137,7 +134,5 @@ def test_quarter_size_error_budget(p, prec):
     Fm = _forces(nodes, segs, b, wl, p=p, precision=prec)
     e_d = np.linalg.norm(Fd[ids] - Fo) / np.linalg.norm(Fo)
     e_m = np.linalg.norm(Fm[ids] - Fo) / np.linalg.norm(Fo)
-    e_md = oracle.rel_l2(Fm, Fd)
-    print(f"250k segments, p={p}, {prec}: FP64 pass vs direct sum {e_d:.3e}, {prec} vs direct sum {e_m:.3e}, "
-          f"{prec} vs FP64 pass (all nodes) {e_md:.3e}")
-    assert e_d < 1e-3 and e_m < 1e-3
+    print(f"250k segments, p={p}, {prec}: FP64 pass vs direct sum {e_d:.3e}, {prec} vs direct sum {e_m:.3e}")
+    assert e_d < 1e-4 and e_m < 1e-4

@@ -60,18 +60,6 @@ def test_mixed_orders_depths(p, L):
     assert err <= TOL_MIXED
 
 
-@pytest.mark.parametrize("split", [0, 1, 2, 3, 4, 5])
-def test_mixed_equals_fp64_gpu_pass_closely(split):
-    """Slab-clustered network (the dense-wall structure of the 1M-segment
-    workload, scaled down) at p = 6: every split setting meets 1e-4 on forces."""
-    nodes, segs, b = synth.slab_loops(n_loops=300, segs_per_loop=20, n_slabs=6, seed=22)
-    _, Fm = _run(nodes, segs, b, ISO_C, p=6, levels=5, precision="mixed", m2l_split=split)
-    _, Fd = _run(nodes, segs, b, ISO_C, p=6, levels=5, precision="fp64")
-    err = oracle.rel_l2(Fm, Fd)
-    print(f"mixed split={split} vs fp64 GPU:", err)
-    assert err <= TOL_MIXED
-
-
 def test_mixed_rotated_crystal_general_rule():
     """A cubic crystal turned off the x, y, z axes: the near field takes the
     general unit-circle rule (all 81 stiffness entries), evaluated once per
@@ -106,14 +94,16 @@ def test_mixed_cubic_circle():
     assert err <= TOL_MIXED
 
 
-@pytest.mark.parametrize("split,tol", [(2, TOL_MIXED), (0, 1e-3), (4, 1e-3)])
-def test_mixed_free_targets(split, tol):
-    """Free points see mostly far field, so the BF16 rounding of the
-    offsets without residual passes shows; splitting all offsets meets 1e-4."""
+@pytest.mark.parametrize("m2l", [dict(m2l_split=2, m2l_basis=0, m2l_split_kblocks=0, m2l_chunks=1),
+                                 dict(m2l_split=6, m2l_basis=0, m2l_split_kblocks=0, m2l_chunks=7), {}])
+def test_mixed_free_targets(m2l):
+    """Free points see mostly far field, where the M2L operands' rounding
+    shows: residual passes on every offset (node values), or the default
+    Legendre-moment operands, meet 1e-4 against Algorithm 2."""
     nodes, segs, b = synth.polygon_loops(n_segs=800, n_loops=25, seed=24)
     import paper_1712_07739_gb300 as gb
 
-    f = gb.FMM(p=4, levels=4, precision="mixed", m2l_split=split).set_material(ISO_C)
+    f = gb.FMM(p=4, levels=4, precision="mixed", **m2l).set_material(ISO_C)
     f.build(_gpu(nodes), _gpu(segs), _gpu(b))
     y, q, sid = oracle.quadrature(nodes, segs, b, 4)
     rng = np.random.default_rng(9)
@@ -123,8 +113,8 @@ def test_mixed_free_targets(split, tol):
     assert f.device_status() == 0
     so = oracle_b.lagrange_fmm(ISO, y, q, sid, p=4, L=4, xt=xt, tseg=-np.ones(len(xt), np.int64))
     err = oracle.rel_l2(s, so)
-    print(f"mixed free targets split={split}:", err)
-    assert err <= tol
+    print(f"mixed free targets {m2l}:", err)
+    assert err <= TOL_MIXED
 
 
 def test_bounded_wait_reports_timeout_and_context_recovers():
@@ -146,14 +136,20 @@ def test_bounded_wait_reports_timeout_and_context_recovers():
     assert np.allclose(again, good, rtol=0, atol=1e-12 * np.abs(good).max())
 
 
-@pytest.mark.parametrize("q,tol", [(16, 3e-5), (20, 5e-6)])
-def test_mixed_cubic_quadrature_points(q, tol):
-    """Fewer points of the unit-circle rule (spectral convergence: 2.7e-5 at
-    Q=16, 1.5e-6 at Q=20 in h) change the nodal forces by less than that."""
-    nodes, segs, b = synth.slab_loops(n_loops=300, segs_per_loop=20, n_slabs=6, seed=26)
+@pytest.fixture(scope="module")
+def cubic_slabs_oracle():
+    nodes, segs, b = synth.slab_loops(n_loops=40, segs_per_loop=20, n_slabs=3, seed=26)
     C6 = synth.cubic_voigt()
-    _, Fq = _run(nodes, segs, b, C6, p=5, levels=5, precision="mixed", h_mode="circle", circle_q=q)
-    _, Fr = _run(nodes, segs, b, C6, p=5, levels=5, precision="mixed", h_mode="circle", circle_q=64)
-    err = oracle.rel_l2(Fq, Fr)
-    print(f"circle Q={q} vs Q=64: {err:.3e}")
-    assert err <= tol
+    return nodes, segs, b, C6, _oracle_forces(oracle.Material.aniso(C6, Q=64), nodes, segs, b, 5, 4)
+
+
+@pytest.mark.parametrize("q", [16, 20, 32])
+def test_mixed_cubic_quadrature_points(cubic_slabs_oracle, q):
+    """Points of the unit-circle rule in the near field (spectral convergence:
+    2.7e-5 at Q = 16, 1.5e-6 at Q = 20 in h): the mixed pass with Q points
+    against Algorithm 2 with Q = 64 meets 1e-4 from Q = 16 on."""
+    nodes, segs, b, C6, Fo = cubic_slabs_oracle
+    _, F = _run(nodes, segs, b, C6, p=5, levels=4, precision="mixed", h_mode="circle", circle_q=q)
+    err = oracle.rel_l2(F, Fo)
+    print(f"circle Q={q} vs Algorithm 2 (Q=64): {err:.3e}")
+    assert err <= TOL_MIXED

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import oracle_b
 from oracle import mlp_ref
 from paper_1712_07739_gb300 import synth
 
@@ -105,31 +106,34 @@ def test_training_reduces_error():
     assert np.array_equal(h2, -h)
 
 
-def test_network_in_near_field_vs_plain():
+def test_network_in_near_field_vs_algorithm2():
     """Mixed pass with the learned h in the near field (pairs beyond
     mlp_min_dist segment lengths, bins the plain evaluator accepted) against
-    the same pass with the plain evaluator everywhere."""
+    the oracle's Lagrange FMM (Algorithm 2) on the same tree: the network's
+    error in h (~1 % RMS, BF16) shows as ~1e-3 in the forces."""
     import paper_1712_07739_gb300 as gb
 
-    nodes, segs, b = synth.slab_loops(n_loops=200, segs_per_loop=20, n_slabs=4, seed=33)
+    nodes, segs, b = synth.slab_loops(n_loops=40, segs_per_loop=20, n_slabs=3, seed=33)
     dn, ds, db = (torch.tensor(a, device="cuda") for a in (nodes, segs, b))
-    plain = gb.FMM(p=4, levels=5, precision="mixed", h_mode="circle", circle_q=32).set_material(CUB)
-    plain.build(dn, ds, db)
-    Fp = plain.nodal_forces().cpu().numpy()
-    f = gb.FMM(p=4, levels=5, precision="mixed", h_mode="mlp", circle_q=32, mlp_min_dist=8.0).set_material(CUB)
+    y, q, sid = oracle.quadrature(nodes, segs, b, 4)
+    Fo = oracle.nodal_forces(nodes, segs, b,
+                             oracle_b.lagrange_fmm(oracle.Material.aniso(CUB, Q=32), y, q, sid, p=4, L=4), 4)
+    f = gb.FMM(p=4, levels=4, precision="mixed", h_mode="mlp", circle_q=32, mlp_min_dist=8.0).set_material(CUB)
     f.mlp_train(torch.tensor(synth.directions(400_000, seed=34), device="cuda"), epochs=20, batch=4096, lr=3e-3,
                 seed=2)
     frac = f.mlp_calibrate(2e-2)
     f.build(dn, ds, db)
     Fm = f.nodal_forces().cpu().numpy()
-    err = np.linalg.norm(Fm - Fp) / np.linalg.norm(Fp)
-    print(f"network near field vs plain: rel L2 {err:.3e}, bins on the plain rule {frac:.3f}")
+    err = oracle.rel_l2(Fm, Fo)
+    print(f"network near field vs Algorithm 2: rel L2 {err:.3e}, bins on the plain rule {frac:.3f}")
     assert np.isfinite(Fm).all()
     assert err < 1e-2
-    # with every bin on the plain rule the two passes agree to rounding
+    # with every bin on the plain rule the pass meets the mixed-precision bar
     f.mlp_calibrate(1e-12)
     Fa = f.nodal_forces().cpu().numpy()
-    assert np.linalg.norm(Fa - Fp) / np.linalg.norm(Fp) < 1e-6
+    err_plain = oracle.rel_l2(Fa, Fo)
+    print(f"every bin on the plain rule vs Algorithm 2: {err_plain:.3e}")
+    assert err_plain < 1e-4
 
 
 def _near_ms(f, dn, ds, db, reps=3):
@@ -148,14 +152,25 @@ def test_network_gain_rotated_crystal():
     """What the trained network gains: in a cubic crystal whose axes are not
     along x, y, z the plain evaluator is the general unit-circle rule (zz and
     zT from all 81 stiffness entries at Q = 32 points per pair); the network
-    costs the same whatever the medium.  Same network, same pass: near-field
-    time with the network (pairs beyond mlp_min_dist segment lengths, bins the
-    plain evaluator accepted) against the plain evaluator everywhere, and the
-    force difference it costs."""
+    costs the same whatever the medium.  Same pass with the network (pairs
+    beyond mlp_min_dist segment lengths, bins the plain evaluator accepted)
+    against the plain evaluator everywhere: the network's near field must be
+    faster, and both are measured against the oracle's direct-sum forces at
+    16 stored nodes (tests/golden/rotated100k_sampled_forces.json)."""
+    import json
+    import os
+
     import paper_1712_07739_gb300 as gb
 
     C = synth.rotated_voigt(CUB, synth.rotation())
     nodes, segs, b = synth.slab_loops(n_loops=2000, segs_per_loop=50, n_slabs=8, seed=35)
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "rotated100k_sampled_forces.json")) as fh:
+        gold = json.load(fh)
+    assert gold["n_segs"] == len(segs) and gold["checks"]["sum_segs"] == int(segs.sum())
+    ids = np.array(gold["node_ids"])
+    assert np.allclose(nodes[ids], np.array(gold["node_xyz"]), rtol=0, atol=1e-12)
+    Fo = np.array(gold["forces"])
     dn, ds, db = (torch.tensor(a, device="cuda") for a in (nodes, segs, b))
     kw = dict(p=5, levels=5, precision="mixed", circle_q=32)
     plain = gb.FMM(h_mode="circle", **kw).set_material(C)
@@ -165,8 +180,11 @@ def test_network_gain_rotated_crystal():
                 seed=3)
     frac = f.mlp_calibrate(5e-2)
     t_mlp, Fm = _near_ms(f, dn, ds, db)
-    err = np.linalg.norm(Fm - Fp) / np.linalg.norm(Fp)
+    e_plain = np.linalg.norm(Fp[ids] - Fo) / np.linalg.norm(Fo)
+    e_mlp = np.linalg.norm(Fm[ids] - Fo) / np.linalg.norm(Fo)
     print(f"rotated cubic crystal, 100k segments: near field plain {t_plain:.1f} ms, network {t_mlp:.1f} ms "
-          f"(gain {t_plain / t_mlp:.2f}x), bins on the plain rule {frac:.3f}, force difference {err:.2e}")
+          f"(gain {t_plain / t_mlp:.2f}x), bins on the plain rule {frac:.3f}; vs direct sum: plain {e_plain:.2e}, "
+          f"network {e_mlp:.2e}")
     assert np.isfinite(Fm).all()
-    assert err < 2e-2
+    assert t_plain / t_mlp > 1.0
+    assert e_mlp < 2e-2

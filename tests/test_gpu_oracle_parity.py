@@ -1,0 +1,218 @@
+"""GPU passes against the FP64 oracle on the same seeded inputs.
+
+Every assertion here has the oracle on its right-hand side: forces stored by
+the scripts under tests/golden (which call only oracle/ and synth), or
+computed here by the oracle on networks small enough to take seconds.
+
+* The 6,000-segment slab network (isotropic, p = 6, 5 levels): every M2L
+  operand mode of the mixed pass against the oracle's Lagrange FMM at the
+  same order and tree (Algorithm 2: the difference is rounding alone, bar
+  1e-4), the FP64 pass at 1e-10, and the mixed pass against the direct sum.
+* Close pairs from different loops: twins of one loop displaced by 1e-3 to 1
+  segment lengths along its glide-plane normal (nearly coincident, parallel
+  segments) and a copy tilted by 1e-2 rad (nearly parallel, crossing): the
+  pairs that take FP64 separations and two-float sums in the mixed near
+  field, against the direct sum of Eq. "stress3" at 1e-4 per twin.
+* Three networks of the 64-network ensemble (batched pass with autotuned
+  depths) against stored direct-sum forces at sampled nodes.
+* Free target points (stress, mostly far field) against Algorithm 2 at 1e-4.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import oracle_b
+from paper_1712_07739_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ISO_C = synth.isotropic_voigt(1.0, 0.3)
+CUB_C = synth.cubic_voigt()
+TOL_MIXED = 1e-4
+# the library's default M2L operands (FP16 Legendre moments, residual passes on the
+# leading block of low-order moments, offsets summed in 7 runs)
+DEFAULT_M2L = {}
+# the node-value operand modes, spelled out
+NODAL = dict(m2l_basis=0, m2l_split_kblocks=0, m2l_chunks=1)
+
+
+def _gpu(a):
+    return torch.tensor(np.asarray(a), device="cuda")
+
+
+def _forces(nodes, segs, b, C, **kw):
+    import paper_1712_07739_gb300 as gb
+
+    f = gb.FMM(**kw).set_material(C)
+    f.build(_gpu(nodes), _gpu(segs), _gpu(b))
+    F = f.nodal_forces().cpu().numpy()
+    assert f.device_status() == 0
+    f.close()
+    return F
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def slab6k():
+    with open(os.path.join(ROOT, "tests", "golden", "slab6k_algorithm2_forces.json")) as fh:
+        gold = json.load(fh)
+    nodes, segs, b = synth.slab_loops(n_loops=300, segs_per_loop=20, n_slabs=6, seed=22)
+    assert gold["n_segs"] == len(segs) and gold["checks"]["sum_segs"] == int(segs.sum())
+    ids = np.array(gold["node_ids"])
+    assert np.allclose(nodes[ids], np.array(gold["node_xyz"]), rtol=0, atol=1e-12)
+    return nodes, segs, b, ids, np.array(gold["forces_algorithm2"]), np.array(gold["forces_direct"])
+
+
+@pytest.mark.parametrize("m2l", [
+    pytest.param(DEFAULT_M2L, id="default"),
+    pytest.param(dict(NODAL, m2l_split=4), id="fp16"),
+    pytest.param(dict(m2l_split=4, m2l_basis=1, m2l_chunks=1), id="fp16-legendre"),
+    pytest.param(dict(m2l_split=4, m2l_basis=1, m2l_chunks=7), id="fp16-legendre-chunks7"),
+    pytest.param(dict(m2l_split=6, m2l_basis=1, m2l_split_kblocks=2, m2l_chunks=3), id="fp16-legendre-res2-chunks3"),
+    pytest.param(dict(NODAL, m2l_split=5, m2l_chunks=7), id="fp16-split-near-chunks7"),
+    pytest.param(dict(NODAL, m2l_split=6, m2l_chunks=27), id="fp16-split-all-chunks27"),
+    pytest.param(dict(NODAL, m2l_split=0), id="bf16-split-near"),
+    pytest.param(dict(NODAL, m2l_split=1), id="bf16"),
+    pytest.param(dict(NODAL, m2l_split=2), id="bf16-split-all"),
+    pytest.param(dict(NODAL, m2l_split=3), id="tf32"),
+    pytest.param(dict(m2l_split=3, m2l_basis=1, m2l_chunks=7), id="tf32-legendre"),
+])
+def test_slab6k_mixed_matches_stored_algorithm2(slab6k, m2l):
+    nodes, segs, b, ids, F2, _ = slab6k
+    F = _forces(nodes, segs, b, ISO_C, p=6, levels=5, precision="mixed", **m2l)
+    err = _rel(F[ids], F2)
+    print(f"slab 6k mixed {m2l} vs Algorithm 2 (400 nodes): {err:.3e}")
+    assert err <= TOL_MIXED
+
+
+def test_slab6k_fp64_matches_stored_algorithm2(slab6k):
+    nodes, segs, b, ids, F2, Fd = slab6k
+    F = _forces(nodes, segs, b, ISO_C, p=6, levels=5, precision="fp64")
+    err = _rel(F[ids], F2)
+    print(f"slab 6k FP64 pass vs Algorithm 2: {err:.3e}; vs direct sum {_rel(F[ids], Fd):.3e}")
+    assert err <= 1e-10
+
+
+def test_slab6k_mixed_vs_direct_sum(slab6k):
+    """The whole approximation (interpolation of order 6 plus rounding)."""
+    nodes, segs, b, ids, F2, Fd = slab6k
+    F = _forces(nodes, segs, b, ISO_C, p=6, levels=5, precision="mixed", **DEFAULT_M2L)
+    err = _rel(F[ids], Fd)
+    print(f"slab 6k mixed vs direct sum: {err:.3e} (Algorithm 2 vs direct sum {_rel(F2, Fd):.3e})")
+    assert err <= TOL_MIXED
+
+
+def close_pair_network(seed=41):
+    """Ten polygonal loops plus five copies of loop 0: four displaced along its
+    glide-plane normal by 1e-3, 1e-2, 1e-1 and 1 mean segment lengths, one
+    tilted by 1e-2 rad about an in-plane axis and displaced by 0.05 lengths.
+    Each copy has its own Burgers vector of the 1/2<111> family.  Returns the
+    network, the loop size and the node range of every copy."""
+    nodes, segs, b = synth.polygon_loops(n_segs=400, n_loops=10, seg_range=(30, 50), r_range=(0.02, 0.06),
+                                         box=0.3, seed=seed)
+    m0 = int(np.argmax(segs[:, 1] == 0)) + 1  # loop 0 closes back to node 0
+    loop = nodes[:m0]
+    lseg = float(np.mean(np.linalg.norm(np.roll(loop, -1, 0) - loop, axis=1)))
+    c = loop.mean(0)
+    nrm = np.cross(loop[1] - c, loop[2] - c)
+    nrm /= np.linalg.norm(nrm)
+    u = (loop[0] - c) / np.linalg.norm(loop[0] - c)
+    v = np.cross(nrm, u)
+    th = 1e-2
+    K = np.array([[0, -v[2], v[1]], [v[2], 0, -v[0]], [-v[1], v[0], 0]])
+    Rm = np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
+    copies = [loop + d * lseg * nrm for d in (1e-3, 1e-2, 1e-1, 1.0)]
+    copies.append((loop - c) @ Rm.T + c + 0.05 * lseg * nrm)
+    rng = np.random.default_rng(seed)
+    ns, ss, bs, ranges = [nodes], [segs], [b], []
+    base = len(nodes)
+    for cp in copies:
+        idx = base + np.arange(m0)
+        ns.append(cp)
+        ss.append(np.stack([idx, np.roll(idx, -1)], 1))
+        bd = synth._B111[rng.integers(4)] / np.sqrt(3.0) * 1e-3
+        bs.append(np.repeat(bd[None], m0, 0))
+        ranges.append((base, base + m0))
+        base += m0
+    return np.concatenate(ns), np.concatenate(ss).astype(np.int64), np.concatenate(bs), m0, ranges
+
+
+def test_close_pairs_of_different_loops_match_direct_sum():
+    nodes, segs, b, m0, ranges = close_pair_network()
+    F = _forces(nodes, segs, b, CUB_C, p=6, levels=4, precision="mixed", h_mode="circle", circle_q=20,
+                **DEFAULT_M2L)
+    Fo, _ = oracle.network_forces(oracle.Material.aniso(CUB_C, Q=32), nodes, segs, b)
+    err = _rel(F, Fo)
+    print(f"close pairs: all nodes {err:.3e}")
+    assert err <= TOL_MIXED
+    groups = [(0, m0)] + ranges
+    for (lo, hi), name in zip(groups, ["loop 0", "1e-3 l", "1e-2 l", "1e-1 l", "1 l", "tilted"]):
+        e = _rel(F[lo:hi], Fo[lo:hi])
+        print(f"  {name}: {e:.3e} (|F| max {np.abs(Fo[lo:hi]).max():.3e})")
+        assert e <= TOL_MIXED, name
+
+
+@pytest.fixture(scope="module")
+def c5_gold():
+    with open(os.path.join(ROOT, "tests", "golden", "c5_sampled_forces.json")) as fh:
+        return json.load(fh)
+
+
+def test_ensemble_networks_match_stored_direct_sum(c5_gold):
+    """Three networks of the 64-network cubic ensemble through the batched
+    pass in the ensemble workload's configuration (bench.py c5), against
+    direct-sum forces at 8 nodes each."""
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_1712_07739_gb300 as gb
+
+    wl = bench.WORKLOADS["c5"]
+    nets_all = wl["gen_batch"](0)
+    picks = c5_gold["networks"]
+    nets = [nets_all[g["index"]] for g in picks]
+    bt = gb.Batch(len(nets), p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
+                  circle_q=wl["circle_q"], m2l_split=wl.get("m2l_split", 4), m2l_basis=wl.get("m2l_basis"),
+                  m2l_chunks=wl.get("m2l_chunks")).set_material(wl["C"]())
+    for k, (n, s, b) in enumerate(nets):
+        bt.build(k, _gpu(n), _gpu(s), _gpu(b))
+    F = [x.cpu().numpy() for x in bt.nodal_forces()]
+    for k, g in enumerate(picks):
+        n, s, b = nets[k]
+        assert g["n_segs"] == len(s) and g["checks"]["sum_segs"] == int(s.sum())
+        ids = np.array(g["node_ids"])
+        assert np.allclose(n[ids], np.array(g["node_xyz"]), rtol=0, atol=1e-12)
+        err = _rel(F[k][ids], np.array(g["forces"]))
+        print(f"ensemble network {g['index']} ({len(s)} segments, {bt.info(k)['levels']} levels): {err:.3e}")
+        assert err <= TOL_MIXED
+    bt.close()
+
+
+def test_free_targets_default_operands_match_algorithm2():
+    """Free points see mostly far field, where the M2L operands' rounding
+    shows; the default operands meet 1e-4 against Algorithm 2."""
+    import paper_1712_07739_gb300 as gb
+
+    nodes, segs, b = synth.polygon_loops(n_segs=800, n_loops=25, seed=24)
+    f = gb.FMM(p=4, levels=4, precision="mixed", **DEFAULT_M2L).set_material(ISO_C)
+    f.build(_gpu(nodes), _gpu(segs), _gpu(b))
+    y, q, sid = oracle.quadrature(nodes, segs, b, 4)
+    rng = np.random.default_rng(9)
+    lo, hi = y.min(0), y.max(0)
+    xt = lo + (hi - lo) * rng.uniform(0.02, 0.98, (400, 3))
+    s = f.stress(_gpu(xt)).cpu().numpy()
+    assert f.device_status() == 0
+    so = oracle_b.lagrange_fmm(oracle.Material.iso(1.0, 0.3), y, q, sid, p=4, L=4, xt=xt,
+                               tseg=-np.ones(len(xt), np.int64))
+    err = oracle.rel_l2(s, so)
+    print(f"free targets, default operands, vs Algorithm 2: {err:.3e}")
+    assert err <= TOL_MIXED
