@@ -566,7 +566,7 @@ __device__ __forceinline__ double elem_value(__nv_bfloat16 x) { return double(__
 __device__ __forceinline__ double elem_value(float x) { return double(x); }
 
 template <typename E>
-__global__ void k_build_ops(int p, int lat_n, int Np, int Kp, const double *__restrict__ Klat,
+__global__ void k_build_ops(int p, int lat_n, int Np, int Kp, int Kp_lo, const double *__restrict__ Klat,
                             const int *__restrict__ off_xyz, const int *__restrict__ lo_of, int n_off,
                             double scale, E *__restrict__ Thi, E *__restrict__ Tlo) {
     const int64_t total = int64_t(n_off) * Np * Kp;
@@ -589,7 +589,7 @@ __global__ void k_build_ops(int p, int lat_n, int Np, int Kp, const double *__re
         const E hi = to_elem<E>(v);
         Thi[idx] = hi;
         const int li = lo_of[o];
-        if (li >= 0 && Tlo) Tlo[(int64_t(li) * Np + nn) * Kp + k] = to_elem<E>(v - elem_value(hi));
+        if (li >= 0 && Tlo && k < Kp_lo) Tlo[(int64_t(li) * Np + nn) * Kp_lo + k] = to_elem<E>(v - elem_value(hi));
     }
 }
 
@@ -631,7 +631,7 @@ __device__ __forceinline__ void axis_pass(int p, int axis, const MT *M, const R 
 // Modal operator rows T'[o][n][k'] (FP64 arithmetic).  mode 0: largest |T'| into
 // *absmax (the FP16 scale); mode 1: write hi (and lo for split offsets).
 template <typename E>
-__global__ void k_build_ops_modal(int p, int lat_n, int Np, int Kp, const double *__restrict__ Klat,
+__global__ void k_build_ops_modal(int p, int lat_n, int Np, int Kp, int Kp_lo, const double *__restrict__ Klat,
                                   const int *__restrict__ off_xyz, const int *__restrict__ lo_of, double scale,
                                   const __grid_constant__ BasisMats B, int mode, unsigned long long *__restrict__ absmax,
                                   E *__restrict__ Thi, E *__restrict__ Tlo) {
@@ -645,7 +645,7 @@ __global__ void k_build_ops_modal(int p, int lat_n, int Np, int Kp, const double
         if (mode == 1)
             for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
                 Thi[row + k] = to_elem<E>(0.0);
-                if (li >= 0 && Tlo) Tlo[(int64_t(li) * Np + nn) * Kp + k] = to_elem<E>(0.0);
+                if (li >= 0 && Tlo && k < Kp_lo) Tlo[(int64_t(li) * Np + nn) * Kp_lo + k] = to_elem<E>(0.0);
             }
         return;
     }
@@ -678,7 +678,7 @@ __global__ void k_build_ops_modal(int p, int lat_n, int Np, int Kp, const double
         const double v = k < 9 * P3 ? scale * b[k] : 0.0;
         const E hi = to_elem<E>(v);
         Thi[row + e] = hi;
-        if (li >= 0 && Tlo) Tlo[(int64_t(li) * Np + nn) * Kp + e] = to_elem<E>(v - elem_value(hi));
+        if (li >= 0 && Tlo && e < Kp_lo) Tlo[(int64_t(li) * Np + nn) * Kp_lo + e] = to_elem<E>(v - elem_value(hi));
     }
 }
 
@@ -997,7 +997,10 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     CK(cudaMalloc(&d_lo, lo_of.size() * sizeof(int)));
     CK(cudaMemcpy(d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_lo, lo_of.data(), lo_of.size() * sizeof(int), cudaMemcpyHostToDevice));
-    const size_t hi_elems = size_t(T.n_off) * T.Np * T.Kp, lo_elems = size_t(T.n_lo) * T.Np * T.Kp;
+    // the residual passes read the leading m2l_split_kblocks blocks of K only
+    const int kstep = 128 / T.esz;
+    T.Kp_lo = ctx->opt.m2l_split_kblocks > 0 ? std::min(T.Kp, ctx->opt.m2l_split_kblocks * kstep) : T.Kp;
+    const size_t hi_elems = size_t(T.n_off) * T.Np * T.Kp, lo_elems = size_t(T.n_lo) * T.Np * T.Kp_lo;
     if (T.Thi) cudaFree(T.Thi);
     if (T.Tlo) cudaFree(T.Tlo);
     T.Thi = T.Tlo = nullptr;
@@ -1025,7 +1028,7 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
         CK(cudaMemsetAsync(d_mx, 0, sizeof(unsigned long long), ctx->stream));
         ++ctx->launches;
         k_build_ops_modal<__half><<<unsigned(T.n_off * T.Np), 256, sm_modal, ctx->stream>>>(
-            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, 1.0, B, 0, d_mx, (__half *)nullptr, (__half *)nullptr);
+            p, ctx->lat_n, T.Np, T.Kp, T.Kp_lo, ctx->d_Klat, d_off, d_lo, 1.0, B, 0, d_mx, (__half *)nullptr, (__half *)nullptr);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&mx_bits, d_mx, sizeof(mx_bits), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
@@ -1064,27 +1067,27 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     if (T.modal) {
         const unsigned g = unsigned(T.n_off * T.Np);
         if (T.tf32)
-            k_build_ops_modal<float><<<g, 256, sm_modal, ctx->stream>>>(p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off,
+            k_build_ops_modal<float><<<g, 256, sm_modal, ctx->stream>>>(p, ctx->lat_n, T.Np, T.Kp, T.Kp_lo, ctx->d_Klat, d_off,
                                                                         d_lo, 1.0, B, 1, nullptr, (float *)T.Thi,
                                                                         (float *)nullptr);
         else if (T.fp16)
-            k_build_ops_modal<__half><<<g, 256, sm_modal, ctx->stream>>>(p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off,
+            k_build_ops_modal<__half><<<g, 256, sm_modal, ctx->stream>>>(p, ctx->lat_n, T.Np, T.Kp, T.Kp_lo, ctx->d_Klat, d_off,
                                                                          d_lo, T.op_scale, B, 1, nullptr,
                                                                          (__half *)T.Thi, (__half *)T.Tlo);
         else
             k_build_ops_modal<__nv_bfloat16><<<g, 256, sm_modal, ctx->stream>>>(
-                p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, 1.0, B, 1, nullptr, (__nv_bfloat16 *)T.Thi,
+                p, ctx->lat_n, T.Np, T.Kp, T.Kp_lo, ctx->d_Klat, d_off, d_lo, 1.0, B, 1, nullptr, (__nv_bfloat16 *)T.Thi,
                 (__nv_bfloat16 *)T.Tlo);
     } else if (T.tf32)
         k_build_ops<float><<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(
-            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, T.n_off, 1.0, (float *)T.Thi, (float *)nullptr);
+            p, ctx->lat_n, T.Np, T.Kp, T.Kp_lo, ctx->d_Klat, d_off, d_lo, T.n_off, 1.0, (float *)T.Thi, (float *)nullptr);
     else if (T.fp16)
         k_build_ops<__half><<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(
-            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, T.n_off, T.op_scale, (__half *)T.Thi,
+            p, ctx->lat_n, T.Np, T.Kp, T.Kp_lo, ctx->d_Klat, d_off, d_lo, T.n_off, T.op_scale, (__half *)T.Thi,
             (__half *)T.Tlo);
     else
         k_build_ops<__nv_bfloat16><<<nblk(int64_t(hi_elems), 256), 256, 0, ctx->stream>>>(
-            p, ctx->lat_n, T.Np, T.Kp, ctx->d_Klat, d_off, d_lo, T.n_off, 1.0, (__nv_bfloat16 *)T.Thi,
+            p, ctx->lat_n, T.Np, T.Kp, T.Kp_lo, ctx->d_Klat, d_off, d_lo, T.n_off, 1.0, (__nv_bfloat16 *)T.Thi,
             (__nv_bfloat16 *)T.Tlo);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1211,8 +1214,9 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
         const cuuint32_t boxd[3] = {cuuint32_t(128 / T.esz), cuuint32_t(T.nsub), 1};
         int rc = encode(ctx, &prm.tmT, T.Thi, 3, dims, strides, boxd, T);
         if (rc) return rc;
-        const cuuint64_t dl[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(std::max(T.n_lo, 1))};
-        rc = encode(ctx, &prm.tmTlo, T.Tlo, 3, dl, strides, boxd, T);
+        const cuuint64_t dl[3] = {cuuint64_t(T.Kp_lo), cuuint64_t(T.Np), cuuint64_t(std::max(T.n_lo, 1))};
+        const cuuint64_t sl[2] = {cuuint64_t(T.Kp_lo) * T.esz, cuuint64_t(T.Kp_lo) * T.esz * T.Np};
+        rc = encode(ctx, &prm.tmTlo, T.Tlo, 3, dl, sl, boxd, T);
         if (rc) return rc;
     }
     prm.kstep = 128 / T.esz;

@@ -10,6 +10,7 @@ struct gbfmm_ctx;
 struct TcPlan {
     bool ready_ops = false;
     int Kp = 0, Np = 0;        // padded K (9 p^3 -> multiple of 64) and N (6 p^3 -> groups x 3 nsub)
+    int Kp_lo = 0;             // K columns of the residual operators (the leading blocks the residual passes read)
     int nsub = 0, ncta = 0, groups = 0, tmem_cols = 0;
     int n_off = 0, n_lo = 0;   // operators and residual operators
     int split = 1;             // residual passes on offsets with max |o_i| = 2

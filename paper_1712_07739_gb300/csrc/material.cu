@@ -149,7 +149,8 @@ int material_setup(gbfmm_ctx *ctx) {
 int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
     if (!src->have_material) return set_err(ctx, GBFMM_ERR_NO_MATERIAL, "share_material: source has no material");
     if (ctx->opt.p != src->opt.p || ctx->opt.precision != src->opt.precision || ctx->opt.h_mode != src->opt.h_mode ||
-        ctx->opt.m2l_split != src->opt.m2l_split || ctx->opt.m2l_basis != src->opt.m2l_basis)
+        ctx->opt.m2l_split != src->opt.m2l_split || ctx->opt.m2l_basis != src->opt.m2l_basis ||
+        ctx->opt.m2l_split_kblocks != src->opt.m2l_split_kblocks)
         return set_err(ctx, GBFMM_ERR_INVALID_ARG, "share_material: options differ");
     ctx->mat = src->mat;
     std::memcpy(ctx->Asym, src->Asym, sizeof(ctx->Asym));
@@ -162,6 +163,7 @@ int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
     const TcPlan &S = src->tc;
     T.ready_ops = S.ready_ops;
     T.Kp = S.Kp;
+    T.Kp_lo = S.Kp_lo;
     T.Np = S.Np;
     T.nsub = S.nsub;
     T.ncta = S.ncta;

@@ -108,9 +108,9 @@ def test_training_reduces_error():
 
 def test_network_in_near_field_vs_algorithm2():
     """Mixed pass with the learned h in the near field (pairs beyond
-    mlp_min_dist segment lengths, bins the plain evaluator accepted) against
-    the oracle's Lagrange FMM (Algorithm 2) on the same tree: the network's
-    error in h (~1 % RMS, BF16) shows as ~1e-3 in the forces."""
+    mlp_min_dist segment lengths, bins the plain evaluator accepted at
+    5e-2 x RMS(h)) against the oracle's Lagrange FMM (Algorithm 2) on the same
+    tree: the network's error in h (~1 % RMS, BF16) shows in the forces."""
     import paper_1712_07739_gb300 as gb
 
     nodes, segs, b = synth.slab_loops(n_loops=40, segs_per_loop=20, n_slabs=3, seed=33)
@@ -121,11 +121,12 @@ def test_network_in_near_field_vs_algorithm2():
     f = gb.FMM(p=4, levels=4, precision="mixed", h_mode="mlp", circle_q=32, mlp_min_dist=8.0).set_material(CUB)
     f.mlp_train(torch.tensor(synth.directions(400_000, seed=34), device="cuda"), epochs=20, batch=4096, lr=3e-3,
                 seed=2)
-    frac = f.mlp_calibrate(2e-2)
+    frac = f.mlp_calibrate(5e-2)
     f.build(dn, ds, db)
     Fm = f.nodal_forces().cpu().numpy()
     err = oracle.rel_l2(Fm, Fo)
     print(f"network near field vs Algorithm 2: rel L2 {err:.3e}, bins on the plain rule {frac:.3f}")
+    assert frac < 1.0  # the network serves part of the pairs
     assert np.isfinite(Fm).all()
     assert err < 1e-2
     # with every bin on the plain rule the pass meets the mixed-precision bar
