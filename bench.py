@@ -95,6 +95,10 @@ def near_flops(wl, work):
 # one ncu capture on the 250,000-segment slab network (dram__bytes_read.sum +
 # dram__bytes_write.sum); valid for the kernel version the capture was taken of
 NEAR_SYM_DRAM_BYTES_PER_POINT = 7.943e9 / 1.0e6
+# DRAM bytes per occupied M2L cell pair of k_m2l_tc at p = 7 (default operands),
+# from one ncu capture of one of the 7 offset launches on the 250,000-segment
+# slab network: 7 x 13.43 GB / 2,010,436 pairs
+M2L_TC_P7_DRAM_BYTES_PER_PAIR = 7 * 13.43e9 / 2010436
 
 
 def measured_alu_peaks():
@@ -123,10 +127,10 @@ WORKLOADS["c3"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs, sigma 0.02), cubic C11=1.684 C12=1.214 "
          "C44=0.754, order p=7, 7-level octree, mixed precision (tensor-core M2L on FP16 Legendre moments with "
          "residual passes on the low-order moments, FP32 near field with FP64 separations for close pairs), "
-         "unit-circle h (cubic form, Q=20 points on the half circle); the same step through the plain FP64 pass "
+         "unit-circle h (cubic form, Q=16 points on the half circle); the same step through the plain FP64 pass "
          "is timed in the same run",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
-    h_mode="circle", circle_q=20, p=7, levels=7, precision="mixed", fp64_arm=True, **MIXED_M2L)
+    h_mode="circle", circle_q=16, p=7, levels=7, precision="mixed", fp64_arm=True, **MIXED_M2L)
 WORKLOADS["c3_iso"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs), isotropic mu=1 nu=0.3, p=7, mixed precision",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.isotropic_voigt(1.0, 0.3),
@@ -621,6 +625,10 @@ def roofline_of(wl, work, m2l_ms, leaf_ms, m2l_fft, peaks):
         else:
             dom, bound = "k_m2l_tc (M2L, tcgen05 FP16 operands)", "tensor"
             peak, src = measured_bf16_peak()
+            if p == 7 and wl.get("m2l_basis") == 1:
+                traffic = M2L_TC_P7_DRAM_BYTES_PER_PAIR * work["m2l_pairs"]
+                traffic_src = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_m2l_tc (p=7, "
+                               "default operands) on the 250k-segment slab network, scaled by occupied cell pairs")
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": src,
             "work": "algorithmic: near pairs x FLOP/pair (h once per unordered pair when h is the unit-circle "

@@ -34,8 +34,9 @@ def test_near_work_counts():
     flops, kernel = bench.near_flops(wl, work)
     assert kernel == "k_near_sym"
     # one unit-circle evaluation per unordered pair, one contraction per direction
-    assert flops == 1000 * ((193 * 20 + 77) / 2 + 229) + l2p
-    one_sided = bench.near_pair_flops("mixed", "circle", 20, True)
+    q = wl["circle_q"]
+    assert flops == 1000 * ((193 * q + 77) / 2 + 229) + l2p
+    one_sided = bench.near_pair_flops("mixed", "circle", q, True)
     assert 1000 * one_sided + l2p > flops
     general = dict(wl, C=lambda: synth.rotated_voigt(synth.cubic_voigt(), synth.rotation()))
     assert bench.near_flops(general, work)[0] > flops
