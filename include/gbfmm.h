@@ -224,6 +224,11 @@ int fmm_work_counts(gbfmm_ctx *ctx, int64_t *counts);
  * stream, reads the word into *status (host) and clears it. */
 int fmm_device_status(gbfmm_ctx *ctx, int *status);
 
+/* ------------------------------------------------------------------------
+ * Testing only: failure injection (not part of the method; no production
+ * caller needs it).
+ * ------------------------------------------------------------------------ */
+
 /* Failure-detection test hook.  kind = 1: the next tensor-core M2L
  * (GBFMM_MIXED) arms its first pipeline stage without loading it, so the
  * consumer's bounded wait runs out (about 10 s); the pass then reports
