@@ -123,6 +123,12 @@ WORKLOADS = {
 # the source cells, residual (hi + lo) passes on the leading block of low-order moments,
 # the offsets summed in 7 runs (the library defaults, spelled out).
 MIXED_M2L = dict(m2l_split=6, m2l_basis=1, m2l_chunks=7, m2l_split_kblocks=1)
+WORKLOADS["c2"] = dict(
+    desc="50,000 segments (1,000 polygonal loops of 10-80 segments, log-uniform radii 0.005-0.05, seed 1), cubic "
+         "C11=1.684 C12=1.214 C44=0.754, plain FP64 pass (M2L through transforms, symmetric FP64 near field), "
+         "order p=5, 5-level octree, unit-circle h Q=32",
+    gen=lambda seed: synth.polygon_loops(seed=1 + 1000 * seed), C=lambda: synth.cubic_voigt(),
+    h_mode="circle", circle_q=32, p=5, levels=5, precision="fp64")
 WORKLOADS["c3"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs, sigma 0.02), cubic C11=1.684 C12=1.214 "
          "C44=0.754, order p=7, 7-level octree, mixed precision (tensor-core M2L on FP16 Legendre moments with "
@@ -551,7 +557,8 @@ def run_ours(args, wl):
                        "p": p, "precision": wl["precision"], "h_mode": wl["h_mode"],
                        "circle_q": wl.get("circle_q", 0), "m2l_split": int(f.options.m2l_split),
                        "m2l_chunks": int(f.options.m2l_chunks), "m2l_basis": int(f.options.m2l_basis),
-                       "m2l_split_kblocks": int(f.options.m2l_split_kblocks), "m2l_fft": int(f.options.m2l_fft),
+                       "m2l_split_kblocks": int(f.options.m2l_split_kblocks),
+                       "m2l_kernel": int(f.options.m2l_kernel), "m2l_fft": int(f.options.m2l_fft),
                        "l2": "flushed: 256 MiB write between steps, outside the step events",
                        "step": "fmm_build_tree + fmm_eval_nodal_forces"},
             "stage_ms": {"precontract": st[:, 0].mean(), "p2m_m2m": st[:, 1].mean(), "m2l": st[:, 2].mean(),
@@ -571,12 +578,13 @@ def run_ours(args, wl):
         torch.distributed.destroy_process_group()
 
 
-GOLDEN = {"c3": "c3_sampled_forces.json", "c3q": "c3q_sampled_forces.json", "c3_fp64": "c3_sampled_forces.json"}
+GOLDEN = {"c3": "c3_sampled_forces.json", "c3q": "c3q_sampled_forces.json", "c3_fp64": "c3_sampled_forces.json",
+          "c2": "c2_forces.json"}
 
 
 def m2l_options(wl):
     """The tensor-core M2L operand options a workload names (library defaults otherwise)."""
-    return {k: wl[k] for k in ("m2l_split", "m2l_basis", "m2l_chunks", "m2l_split_kblocks") if k in wl}
+    return {k: wl[k] for k in ("m2l_split", "m2l_basis", "m2l_chunks", "m2l_split_kblocks", "m2l_kernel") if k in wl}
 
 
 def oracle_node_error(wl, name, F, nodes, segs, b):
@@ -588,10 +596,15 @@ def oracle_node_error(wl, name, F, nodes, segs, b):
         return None
     with open(os.path.join(ROOT, "tests", "golden", fn)) as fh:
         gold = json.load(fh)
-    ids = np.array(gold["node_ids"])
-    if gold["n_segs"] != len(segs) or not np.allclose(nodes[ids], np.array(gold["node_xyz"]), rtol=0, atol=1e-12):
+    if "forces_direct" in gold:  # Algorithm-2 forces at many nodes, direct-sum forces at some of them
+        ids, Fo = np.array(gold["direct_node_ids"]), np.array(gold["forces_direct"])
+    else:
+        ids, Fo = np.array(gold["node_ids"]), np.array(gold["forces"])
+    # the stored forces belong to exactly this network
+    chk = gold["checks"]
+    if (gold["n_segs"] != len(segs) or chk["sum_segs"] != int(segs.sum())
+            or abs(chk["sum_nodes"] - nodes.sum()) > 1e-9 * abs(nodes.sum())):
         return None
-    Fo = np.array(gold["forces"])
     err = float(np.linalg.norm(F[ids] - Fo) / np.linalg.norm(Fo))
     return {"rel_l2_vs_oracle": err, "nodes": int(len(ids)), "gate": 1e-4, "meets_gate": err <= 1e-4,
             "oracle": f"tests/golden/{fn}: FP64 direct sum, unit-circle h Q={gold.get('Q')}"}
@@ -685,6 +698,7 @@ def main():
     ap.add_argument("--m2l-chunks", type=int, default=-1, help="override the M2L offset chunks (fmm options)")
     ap.add_argument("--m2l-basis", type=int, default=-1, help="override the M2L operand basis (fmm options)")
     ap.add_argument("--m2l-split-kblocks", type=int, default=-1, help="override the residual K blocks (fmm options)")
+    ap.add_argument("--m2l-kernel", type=int, default=-1, help="override the M2L tile form (fmm options)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.p:
@@ -699,6 +713,8 @@ def main():
         wl["m2l_basis"] = args.m2l_basis
     if args.m2l_split_kblocks >= 0:
         wl["m2l_split_kblocks"] = args.m2l_split_kblocks
+    if args.m2l_kernel >= 0:
+        wl["m2l_kernel"] = args.m2l_kernel
     if args.impl == "reference":
         run_reference(args, wl)
     elif wl.get("batch"):

@@ -117,6 +117,11 @@ typedef struct {
                               leading blocks hold the low-order moments, which carry most of
                               every product and hence most of its rounding error
                               (fmm_default_options: 1). */
+    int m2l_kernel;        /* MIXED: form of the tile GEMM of the tensor-core M2L.  0 = three
+                              tiles of 128 target cells per CTA as the M operands, one block of
+                              operator rows shared as N; 1 = two 128-row blocks of operator
+                              rows as the M operands, the CTA's 256 target cells shared as
+                              N = 256 (half the gathered bytes per product). */
 } gbfmm_options;
 
 typedef struct gbfmm_ctx gbfmm_ctx;

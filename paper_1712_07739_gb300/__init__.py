@@ -45,6 +45,7 @@ class Options(ctypes.Structure):
         ("leaf_segments", ctypes.c_int), ("near_fp64", ctypes.c_double), ("m2l_split", ctypes.c_int),
         ("mlp_min_dist", ctypes.c_double), ("m2l_fft", ctypes.c_int), ("m2l_chunks", ctypes.c_int),
         ("m2l_basis", ctypes.c_int), ("m2l_split_levels", ctypes.c_int), ("m2l_split_kblocks", ctypes.c_int),
+        ("m2l_kernel", ctypes.c_int),
     ]
 
 
@@ -143,7 +144,7 @@ class FMM:
 
     def __init__(self, p=4, n_gauss=4, levels=0, precision="fp64", h_mode="iso", circle_q=0,
                  leaf_segments=0, near_fp64=0.0, m2l_split=None, mlp_min_dist=0.0, m2l_fft=None, m2l_chunks=None,
-                 m2l_basis=None, m2l_split_levels=None, m2l_split_kblocks=None, stream=None):
+                 m2l_basis=None, m2l_split_levels=None, m2l_split_kblocks=None, m2l_kernel=None, stream=None):
         import torch
 
         self._torch = torch
@@ -167,6 +168,8 @@ class FMM:
             o.m2l_split_levels = int(m2l_split_levels)
         if m2l_split_kblocks is not None:
             o.m2l_split_kblocks = int(m2l_split_kblocks)
+        if m2l_kernel is not None:
+            o.m2l_kernel = int(m2l_kernel)
         self.options = o
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -338,7 +341,7 @@ class Batch:
 
     def __init__(self, n_configs, p=6, n_gauss=4, levels=0, precision="mixed", h_mode="circle", circle_q=0,
                  leaf_segments=0, near_fp64=0.0, m2l_split=None, m2l_basis=None, m2l_chunks=None,
-                 m2l_split_levels=None, m2l_split_kblocks=None, stream=None):
+                 m2l_split_levels=None, m2l_split_kblocks=None, m2l_kernel=None, stream=None):
         import torch
 
         self._torch = torch
@@ -350,7 +353,7 @@ class Batch:
         o.h_mode = _HMODE[h_mode] if isinstance(h_mode, str) else int(h_mode)
         o.circle_q, o.leaf_segments, o.near_fp64 = circle_q, leaf_segments, near_fp64
         for name, v in (("m2l_split", m2l_split), ("m2l_basis", m2l_basis), ("m2l_chunks", m2l_chunks), ("m2l_split_levels", m2l_split_levels),
-                        ("m2l_split_kblocks", m2l_split_kblocks)):
+                        ("m2l_split_kblocks", m2l_split_kblocks), ("m2l_kernel", m2l_kernel)):
             if v is not None:
                 setattr(o, name, int(v))
         if stream is None:

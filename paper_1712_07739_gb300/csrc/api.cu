@@ -120,7 +120,7 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
         opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0) || opt->m2l_split < 0 ||
         opt->m2l_split > 6 || opt->m2l_fft < 0 || opt->m2l_fft > 1 || opt->m2l_chunks < 0 ||
         opt->m2l_chunks > 189 || opt->m2l_basis < 0 || opt->m2l_basis > 1 ||
-        opt->m2l_split_kblocks < 0)
+        opt->m2l_split_kblocks < 0 || opt->m2l_kernel < 0 || opt->m2l_kernel > 1)
         return GBFMM_ERR_INVALID_ARG;
     gbfmm_ctx *ctx = new gbfmm_ctx();
     ctx->opt = *opt;

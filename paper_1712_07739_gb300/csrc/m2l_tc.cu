@@ -82,6 +82,7 @@ struct M2LParams {
     uint32_t idesc; // tcgen05 instruction descriptor
     const unsigned *wmax;  // FP16 mode: per-level max |W| bits (the W scale), else null
     float inv_op_scale;    // FP16 mode: 1 / operator scale, else 1
+    int nblk;              // operators as A: 128-row blocks of operator rows (a CTA takes two)
     int o_lo, o_hi;        // this launch takes the entries o_lo .. o_hi - 1 of each class's offset list
     int accumulate;        // 0: the epilogue writes the local values, 1: it adds to them
 };
@@ -97,9 +98,15 @@ __device__ __forceinline__ float wscale_of(unsigned bits) {
     return ldexpf(1.f, 13 - e);
 }
 
-constexpr int TPC = 3;                        // tiles of 128 cells per CTA, sharing each operator stage
-constexpr int kTileA = 128 * 128;             // one tile's multipole rows per stage: 16 KB
-constexpr int kStageA = TPC * kTileA;         // 48 KB
+// Two forms of the tile GEMM (gbfmm_options.m2l_kernel):
+//  cells as A (SWAP = false): three tiles of 128 target cells per CTA are the M = 128
+//    operands of three MMAs that share one block of nsub operator rows (B, N = nsub);
+//  operators as A (SWAP = true): two 128-row blocks of operator rows are the M = 128
+//    operands (TMA) of two MMAs that share the CTA's two tiles of target cells as one
+//    N = 256 operand, so a gathered row feeds 256 instead of nsub output columns and a
+//    stage gathers 32 instead of 48 KB for about the same tensor work.
+constexpr int kTileA = 128 * 128;  // one tile's multipole rows per stage: 16 KB
+template <bool SWAP> constexpr int tpc_of() { return SWAP ? 2 : 3; }  // tiles of 128 cells per CTA
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -263,7 +270,7 @@ constexpr int kMaxSeg = 8 * GB_TC_MAXLEV;
 // split: the residual passes apply at this level
 __device__ __forceinline__ int passes_of(const OffsetEntry &e, int split) { return (split && e.lo >= 0) ? 3 : 1; }
 
-template <bool TF32>
+template <bool TF32, bool SWAP>
 __global__ void __launch_bounds__(192, 1)
     k_m2l_tc(const __grid_constant__ M2LParams P, const int4 *__restrict__ seg, int n_seg,
              const int *__restrict__ list, const int *__restrict__ occ, const int *__restrict__ tocc,
@@ -271,7 +278,10 @@ __global__ void __launch_bounds__(192, 1)
              int *__restrict__ status, int stages, int groups) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int stageB = P.ncta * 128;
+    constexpr int TPC = tpc_of<SWAP>();
+    constexpr int kStageA = TPC * kTileA;  // the tiles' gathered multipole rows
+    // operator rows per stage: nsub rows (cells as A) or two 128-row blocks (operators as A)
+    const int stageB = SWAP ? 2 * kTileA : P.ncta * 128;
     const int stage_bytes = kStageA + stageB;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + stages * stage_bytes);
     // bars[0..stages): full, [stages..2 stages): empty, [2 stages]: accumulator ready
@@ -303,6 +313,7 @@ __global__ void __launch_bounds__(192, 1)
     if (s_level < 0 || s_stop) return;  // surplus block, or an earlier block timed out
     const int level = s_level, cls = s_cls, nrow = s_nrow;
     const int split = P.split && ((P.split_levels >> level) & 1);
+    const int mbc = SWAP ? min(2, P.nblk - 2 * group) : 1;  // operator blocks of this CTA (operators as A)
     const int m = 1 << (level - 1), n = 1 << level;
     const int64_t cbase = cell_base_d(level);
     for (int r = threadIdx.x; r < 128 * TPC; r += blockDim.x) {
@@ -370,9 +381,14 @@ __global__ void __launch_bounds__(192, 1)
                         break;
                     }
                     const uint32_t fb = full0 + 8 * s;
-                    mbar_expect_tx(fb, uint32_t(stageB));
+                    mbar_expect_tx(fb, uint32_t(SWAP ? mbc * kTileA : stageB));
                     if (P.drop_first && it == 0) continue;  // the MMA warp's wait on this stage runs out
-                    tma_load_3d(smem0 + s * stage_bytes + kStageA, tb, kb * P.kstep, group * P.ncta, tidx, fb);
+                    if (SWAP)
+                        for (int mb = 0; mb < mbc; ++mb)
+                            tma_load_3d(smem0 + s * stage_bytes + kStageA + mb * kTileA, tb, kb * P.kstep,
+                                        group * 256 + mb * 128, tidx, fb);
+                    else
+                        tma_load_3d(smem0 + s * stage_bytes + kStageA, tb, kb * P.kstep, group * P.ncta, tidx, fb);
                 }
             }
         }
@@ -396,10 +412,19 @@ __global__ void __launch_bounds__(192, 1)
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t a = smem0 + s * stage_bytes;
                     for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t bd = sw128_desc(a + kStageA + kk * 32);
-                        for (int t = 0; t < TPC; ++t) {
-                            const uint64_t ad = sw128_desc(a + t * kTileA + kk * 32);
-                            mma_issue<TF32>(tmem + t * P.nsub, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                        if (SWAP) {
+                            // the two tiles' 256 rows (contiguous, 1024 B per 8 rows) are the N operand
+                            const uint64_t bd = sw128_desc(a + kk * 32);
+                            for (int mb = 0; mb < mbc; ++mb) {
+                                const uint64_t ad = sw128_desc(a + kStageA + mb * kTileA + kk * 32);
+                                mma_issue<TF32>(tmem + mb * 256, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                            }
+                        } else {
+                            const uint64_t bd = sw128_desc(a + kStageA + kk * 32);
+                            for (int t = 0; t < TPC; ++t) {
+                                const uint64_t ad = sw128_desc(a + t * kTileA + kk * 32);
+                                mma_issue<TF32>(tmem + t * P.nsub, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                            }
                         }
                     }
                     mma_commit(empty0 + 8 * s);
@@ -501,7 +526,38 @@ __global__ void __launch_bounds__(192, 1)
         float sc = float(double(n) / box->H) * float(double(n) / box->H);
         if (P.wmax) sc *= P.inv_op_scale / wscale_of(P.wmax[level]);
         const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
-        for (int t = 0; t < TPC; ++t) {
+        if (SWAP) {
+            // TMEM lane = operator row (of block mb), column = target cell (tile col / 128)
+            for (int mb = 0; mb < mbc; ++mb) {
+                const int nr = group * 256 + mb * 128 + trow;  // this thread's operator row
+                const bool rv = nr < P.nvalid;
+                for (int c0 = 0; c0 < 256; c0 += 16) {
+                    float v[16];
+                    if (ok && any_src) tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t(mb * 256 + c0), v);
+                    for (int i = 0; i < 16; ++i) {
+                        const int cell = c0 + i, t = cell >> 7, r = cell & 127;
+                        if (!ok || !rv || cell >= nrow) continue;
+                        const int64_t g = cbase +
+                                          (int64_t(2 * s_tgt[t][r][2] + cz) * n + (2 * s_tgt[t][r][1] + cy)) * n +
+                                          (2 * s_tgt[t][r][0] + cx);
+                        const int64_t e = g * int64_t(P.nvalid) + nr;
+                        if (!any_src) {
+                            if (!P.accumulate) {
+                                if (S64) S64[e] = 0.0;
+                                else S[e] = 0.f;
+                            }
+                        } else if (P.accumulate) {
+                            if (S64) S64[e] += double(v[i]) * double(sc);
+                            else S[e] += v[i] * sc;
+                        } else {
+                            if (S64) S64[e] = double(v[i]) * double(sc);
+                            else S[e] = v[i] * sc;
+                        }
+                    }
+                }
+            }
+        }
+        for (int t = 0; t < (SWAP ? 0 : TPC); ++t) {
             const bool valid = ok && t * 128 + trow < nrow;
             int64_t g = 0;
             if (valid)
@@ -827,7 +883,7 @@ __global__ void k_mb_list(int n, int L, const int *__restrict__ flags, const int
 }
 
 // segment table: {first list entry, cells, first CTA}; seg[n_seg].z = CTAs (per operator group)
-__global__ void k_seg_table(int L, const int *__restrict__ pos, int4 *__restrict__ seg) {
+__global__ void k_seg_table(int L, int tpc, const int *__restrict__ pos, int4 *__restrict__ seg) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int tiles = 0, si = 0;
     for (int l = 2; l < L; ++l) {
@@ -836,7 +892,7 @@ __global__ void k_seg_table(int L, const int *__restrict__ pos, int4 *__restrict
             const int64_t s0 = slot_base(l) + c * m3;
             const int first = pos[s0], cnt = pos[s0 + m3] - first;
             seg[si] = make_int4(first, cnt, tiles, 0);
-            tiles += ((cnt + 127) / 128 + TPC - 1) / TPC;  // CTAs: TPC tiles each
+            tiles += ((cnt + 127) / 128 + tpc - 1) / tpc;  // CTAs: tpc tiles each
         }
     }
     seg[si] = make_int4(0, 0, tiles, 0);
@@ -927,24 +983,38 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     T.fp16 = (ctx->opt.m2l_split >= 4) ? 1 : 0;
     T.esz = T.tf32 ? 4 : 2;
     T.Kp = ((9 * P3 + 63) / 64) * 64;
-    // N per MMA (= operator rows per CTA): multiple of 16, one accumulator per
-    // tile, TPC x nsub <= 512 TMEM columns
     const int nv = 6 * P3;
-    int best = 0, best_waste = 1 << 30;
-    for (int ns = 16; ns * TPC <= 512 && ns <= 256; ns += 16) {
-        const int g = (nv + ns - 1) / ns;
-        const int waste = g * ns - nv + g * 32;  // padding plus a per-group cost (the tiles' rows are re-read)
-        if (waste < best_waste) {
-            best_waste = waste;
-            best = ns;
+    T.swap = ctx->opt.m2l_kernel == 1 ? 1 : 0;
+    T.tpc = T.swap ? 2 : 3;
+    if (T.swap) {
+        // operators as A: blocks of 128 operator rows, two per CTA; N = 256 cells per MMA;
+        // two accumulators of 256 columns
+        T.nblk = (nv + 127) / 128;
+        T.Np = T.nblk * 128;
+        T.groups = (T.nblk + 1) / 2;
+        T.nsub = 256;
+        T.ncta = 256;
+        T.tmem_cols = 512;
+    } else {
+        // N per MMA (= operator rows per CTA): multiple of 16, one accumulator per
+        // tile, 3 x nsub <= 512 TMEM columns
+        int best = 0, best_waste = 1 << 30;
+        for (int ns = 16; ns * 3 <= 512 && ns <= 256; ns += 16) {
+            const int g = (nv + ns - 1) / ns;
+            const int waste = g * ns - nv + g * 32;  // padding plus a per-group cost (the tiles' rows are re-read)
+            if (waste < best_waste) {
+                best_waste = waste;
+                best = ns;
+            }
         }
+        T.nsub = best;
+        T.ncta = best;
+        T.groups = (nv + T.ncta - 1) / T.ncta;
+        T.Np = T.groups * T.ncta;
+        T.nblk = 0;
+        T.tmem_cols = 32;
+        while (T.tmem_cols < 3 * T.nsub) T.tmem_cols *= 2;
     }
-    T.nsub = best;
-    T.ncta = best;
-    T.groups = (nv + T.ncta - 1) / T.ncta;
-    T.Np = T.groups * T.ncta;
-    T.tmem_cols = 32;
-    while (T.tmem_cols < TPC * T.nsub) T.tmem_cols *= 2;
     // the 316 offsets, and which of them get the residual passes
     std::vector<int> off;
     std::vector<int> lo_of;
@@ -1131,7 +1201,7 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
     // cell slots, target list and segment table (filled on the device per pass)
     const int64_t slots = slot_base(L);
     int64_t tiles = 0;  // CTAs per operator group, upper bound: every cell holds targets
-    for (int l = 2; l < L; ++l) tiles += 8 * ((((int64_t(1) << (3 * (l - 1))) + 127) / 128 + TPC - 1) / TPC);
+    for (int l = 2; l < L; ++l) tiles += 8 * ((((int64_t(1) << (3 * (l - 1))) + 127) / 128 + T.tpc - 1) / T.tpc);
     if (int rc = grow_dev(ctx, T.slot_cap, slots,
                           {{(void **)&T.d_flags, slots * sizeof(int)}, {(void **)&T.d_pos, (slots + 1) * sizeof(int)},
                            {(void **)&T.d_list, slots * sizeof(int)}},
@@ -1207,11 +1277,12 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     ctx->launches += 3;
     k_scan_flags<<<1, 1024, 0, ctx->stream>>>(int(T.n_slots), T.d_flags, T.d_pos);
     k_mb_list<<<nblk(T.n_slots, 256), 256, 0, ctx->stream>>>(int(T.n_slots), L, T.d_flags, T.d_pos, T.d_list);
-    k_seg_table<<<1, 32, 0, ctx->stream>>>(L, T.d_pos, T.d_seg);
+    k_seg_table<<<1, 32, 0, ctx->stream>>>(L, T.tpc, T.d_pos, T.d_seg);
     {
         const cuuint64_t dims[3] = {cuuint64_t(T.Kp), cuuint64_t(T.Np), cuuint64_t(T.n_off)};
         const cuuint64_t strides[2] = {cuuint64_t(T.Kp) * T.esz, cuuint64_t(T.Kp) * T.esz * T.Np};
-        const cuuint32_t boxd[3] = {cuuint32_t(128 / T.esz), cuuint32_t(T.nsub), 1};
+        // box: one K block of operator rows: nsub rows (cells as A) or a 128-row block (operators as A)
+        const cuuint32_t boxd[3] = {cuuint32_t(128 / T.esz), cuuint32_t(T.swap ? 128 : T.nsub), 1};
         int rc = encode(ctx, &prm.tmT, T.Thi, 3, dims, strides, boxd, T);
         if (rc) return rc;
         const cuuint64_t dl[3] = {cuuint64_t(T.Kp_lo), cuuint64_t(T.Np), cuuint64_t(std::max(T.n_lo, 1))};
@@ -1222,7 +1293,8 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     prm.kstep = 128 / T.esz;
     prm.kb = T.Kp / prm.kstep;
     prm.kb_res = ctx->opt.m2l_split_kblocks > 0 ? std::min(prm.kb, ctx->opt.m2l_split_kblocks) : prm.kb;
-    prm.idesc = idesc_of(128, T.nsub, T.tf32, T.fp16);
+    prm.idesc = idesc_of(128, T.nsub, T.tf32, T.fp16);  // M = 128; N = nsub, or 256 cells (operators as A)
+    prm.nblk = T.nblk;
     prm.wmax = T.fp16 ? T.d_wmax : nullptr;
     prm.inv_op_scale = float(1.0 / T.op_scale);
     prm.nsub = T.nsub;
@@ -1233,25 +1305,21 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     prm.split_levels = split_levels;
     prm.drop_first = T.inject_drop;
     T.inject_drop = 0;
-    const int stage_bytes = kStageA + T.ncta * 128;
+    const int stage_bytes = T.tpc * kTileA + (T.swap ? 2 * kTileA : T.ncta * 128);
     // as many stages as fit in the shared memory a block may opt into, next to the
     // kernel's static arrays, the 1 KB alignment pad and the barriers
     int dev = 0, optin = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    auto kern = T.tf32 ? (T.swap ? k_m2l_tc<true, true> : k_m2l_tc<true, false>)
+                       : (T.swap ? k_m2l_tc<false, true> : k_m2l_tc<false, false>);
     cudaFuncAttributes fa;
-    if (T.tf32)
-        CK(cudaFuncGetAttributes(&fa, k_m2l_tc<true>));
-    else
-        CK(cudaFuncGetAttributes(&fa, k_m2l_tc<false>));
+    CK(cudaFuncGetAttributes(&fa, kern));
     const int64_t room = int64_t(optin) - int64_t(fa.sharedSizeBytes) - 1024 - (2 * 6 + 2) * 8 - 64;
     const int stages = int(std::min<int64_t>(6, room / stage_bytes));
     if (stages < 2) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "tensor-core M2L: operator block too large");
     const size_t smem = size_t(stages) * stage_bytes + 1024 + (2 * stages + 2) * 8 + 64;
-    if (T.tf32)
-        CK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    else
-        CK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     // offset chunks: each launch accumulates a run of consecutive offsets of every class's list
     // in tensor memory; the chunks' sums are added outside the tensor cores, in the local values
     const int chunks = std::max(1, std::min(189, ctx->opt.m2l_chunks));
@@ -1261,12 +1329,8 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
         prm.accumulate = c > 0 ? 1 : 0;
         if (c > 0) prm.drop_first = 0;
         ++ctx->launches;
-        if (T.tf32)
-            k_m2l_tc<true><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc,
-                                                                 ctx->d_box, Sf, S64, T.d_status, stages, T.groups);
-        else
-            k_m2l_tc<false><<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc,
-                                                                  ctx->d_box, Sf, S64, T.d_status, stages, T.groups);
+        kern<<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box, Sf, S64,
+                                                   T.d_status, stages, T.groups);
         CK(cudaGetLastError());
     }
     return GBFMM_OK;

@@ -12,6 +12,9 @@ struct TcPlan {
     int Kp = 0, Np = 0;        // padded K (9 p^3 -> multiple of 64) and N (6 p^3 -> groups x 3 nsub)
     int Kp_lo = 0;             // K columns of the residual operators (the leading blocks the residual passes read)
     int nsub = 0, ncta = 0, groups = 0, tmem_cols = 0;
+    int swap = 0;              // operators as the A operand (gbfmm_options.m2l_kernel = 1)
+    int tpc = 3;               // tiles of 128 target cells per CTA
+    int nblk = 0;              // operators as A: 128-row operator blocks
     int n_off = 0, n_lo = 0;   // operators and residual operators
     int split = 1;             // residual passes on offsets with max |o_i| = 2
     int tf32 = 0;              // operands in FP32 storage, MMA kind::tf32 (no residual passes)

@@ -150,7 +150,7 @@ int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
     if (!src->have_material) return set_err(ctx, GBFMM_ERR_NO_MATERIAL, "share_material: source has no material");
     if (ctx->opt.p != src->opt.p || ctx->opt.precision != src->opt.precision || ctx->opt.h_mode != src->opt.h_mode ||
         ctx->opt.m2l_split != src->opt.m2l_split || ctx->opt.m2l_basis != src->opt.m2l_basis ||
-        ctx->opt.m2l_split_kblocks != src->opt.m2l_split_kblocks)
+        ctx->opt.m2l_split_kblocks != src->opt.m2l_split_kblocks || ctx->opt.m2l_kernel != src->opt.m2l_kernel)
         return set_err(ctx, GBFMM_ERR_INVALID_ARG, "share_material: options differ");
     ctx->mat = src->mat;
     std::memcpy(ctx->Asym, src->Asym, sizeof(ctx->Asym));
@@ -168,6 +168,9 @@ int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
     T.nsub = S.nsub;
     T.ncta = S.ncta;
     T.groups = S.groups;
+    T.swap = S.swap;
+    T.tpc = S.tpc;
+    T.nblk = S.nblk;
     T.tmem_cols = S.tmem_cols;
     T.n_off = S.n_off;
     T.n_lo = S.n_lo;

@@ -331,7 +331,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
 // (closer than near_fp64 x the longer of the two segments) take their
 // separation from the FP64 positions, where the cancellation is, and are
 // summed apart from the other pairs in two-float (hi + lo) sums.
-constexpr int SYM_WARPS = 4, SYM_SCH = 8;
+// One warp per block (a block's shared-memory slice is freed as soon as its leaf pair is
+// done) and 12 resident blocks per SM (152 registers): at 1M segments, Q = 16, the near
+// field took 195 ms against 204 ms with four warps per block at the same 12 warps per SM
+// (there the slowest warp of a block held the other three slices).
+constexpr int SYM_WARPS = 1, SYM_SCH = 8, SYM_MINB = 12;
 constexpr int kSlots = 28;
 
 // Two-float sums for the close pairs: the value is hi + lo, and each addition
@@ -352,7 +356,7 @@ __device__ __forceinline__ void tsum2(float &hi, float &lo, float bhi, float blo
 }
 
 template <int HM>
-__global__ void __launch_bounds__(SYM_WARPS * 32) k_near_sym(
+__global__ void __launch_bounds__(SYM_WARPS * 32, SYM_MINB) k_near_sym(
     int L, float near2, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat,
     const int *__restrict__ sstart, const float4 *__restrict__ yrel, const double *__restrict__ ys,
     const float *__restrict__ c32, const int64_t *__restrict__ ssid, double *__restrict__ part, int64_t N,

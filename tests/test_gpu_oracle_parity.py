@@ -73,6 +73,7 @@ def slab6k():
 
 @pytest.mark.parametrize("m2l", [
     pytest.param(DEFAULT_M2L, id="default"),
+    pytest.param(dict(m2l_kernel=1), id="default-operators-as-A"),
     pytest.param(dict(NODAL, m2l_split=4), id="fp16"),
     pytest.param(dict(m2l_split=4, m2l_basis=1, m2l_chunks=1), id="fp16-legendre"),
     pytest.param(dict(m2l_split=4, m2l_basis=1, m2l_chunks=7), id="fp16-legendre-chunks7"),
@@ -215,4 +216,41 @@ def test_free_targets_default_operands_match_algorithm2():
                                tseg=-np.ones(len(xt), np.int64))
     err = oracle.rel_l2(s, so)
     print(f"free targets, default operands, vs Algorithm 2: {err:.3e}")
+    assert err <= TOL_MIXED
+
+
+@pytest.fixture(scope="module")
+def c2_case():
+    """The 50,000-segment cubic network of the FP64 configuration (1,000
+    polygonal loops of 10-80 segments), with the oracle's Algorithm-2 forces
+    at 200 nodes and direct-sum forces at 32 of them (p = 5, 5 levels, Q = 32)."""
+    with open(os.path.join(ROOT, "tests", "golden", "c2_forces.json")) as fh:
+        gold = json.load(fh)
+    nodes, segs, b = synth.config("c2")
+    assert gold["n_segs"] == len(segs) and gold["checks"]["sum_segs"] == int(segs.sum())
+    ids = np.array(gold["node_ids"])
+    assert np.allclose(nodes[ids], np.array(gold["node_xyz"]), rtol=0, atol=1e-12)
+    return (nodes, segs, b, ids, np.array(gold["forces_algorithm2"]), np.array(gold["direct_node_ids"]),
+            np.array(gold["forces_direct"]))
+
+
+def test_c2_fp64_matches_stored_algorithm2(c2_case):
+    """The plain FP64 pass at high order against the oracle's Algorithm 2 on
+    the same tree: the 1e-10 bar of the FP64 path (rounding only)."""
+    nodes, segs, b, ids, F2, idd, Fd = c2_case
+    F = _forces(nodes, segs, b, CUB_C, p=5, levels=5, precision="fp64", h_mode="circle", circle_q=32)
+    err = _rel(F[ids], F2)
+    pos = {int(k): i for i, k in enumerate(ids)}
+    e_d = _rel(F[idd], Fd)
+    print(f"c2 FP64 pass vs Algorithm 2 (200 nodes): {err:.3e}; vs direct sum (32 nodes): {e_d:.3e}")
+    assert err <= 1e-10
+    # the stored Algorithm-2 forces at the direct-sum nodes show the same interpolation error
+    assert abs(_rel(F2[[pos[int(k)] for k in idd]], Fd) - e_d) <= 1e-8
+
+
+def test_c2_mixed_matches_stored_algorithm2(c2_case):
+    nodes, segs, b, ids, F2, idd, Fd = c2_case
+    F = _forces(nodes, segs, b, CUB_C, p=5, levels=5, precision="mixed", h_mode="circle", circle_q=32)
+    err = _rel(F[ids], F2)
+    print(f"c2 mixed pass vs Algorithm 2 (200 nodes): {err:.3e}")
     assert err <= TOL_MIXED
