@@ -267,7 +267,10 @@ int fmm_probe_fma(int kind, void *cuda_stream, double *tflops);
  * measured once by timing a pass of the first network built, and the depth
  * with the smallest predicted time among L0-1..L0+1 (L0 from N_s /
  * leaf_segments) is kept; the slot keeps it for later builds while its N_s
- * stays within 10 %.  fmm_batch_eval_nodal_forces records the passes of
+ * stays within 10 %.  Created with m2l_kernel = 2, the same calibration also
+ * times both tile forms of the tensor-core M2L (gbfmm_options.m2l_kernel) on
+ * that network and keeps the faster for every slot.
+ * fmm_batch_eval_nodal_forces records the passes of
  * all slots into one CUDA graph (spread over up to 8 internal streams and
  * joined back onto the batch's stream) on its first call after a build, and
  * replays it afterwards.
@@ -290,9 +293,34 @@ int fmm_batch_build(gbfmm_batch *batch, int k, int64_t n_nodes, const double *no
  * pointers ([n_nodes_k][3] double each, overwritten).  Asynchronous on the
  * batch's stream.  Errors: NOT_BUILT, CUDA. */
 int fmm_batch_eval_nodal_forces(gbfmm_batch *batch, double *const *f_nodes);
-/* Slot k's tree depth, the total kernel launches of all slots, and the
- * autotuner's cost constants (seconds per near pair, per cell); any output
- * may be NULL. */
+/* One step of every slot as one CUDA graph: each slot's tree is rebuilt from
+ * the arrays given at its last fmm_batch_build (the caller may have changed
+ * their contents, e.g. moved the nodes, but not their sizes or addresses) and
+ * its nodal forces evaluated into f_nodes[k] (host array of n_configs device
+ * pointers).  The graph is recorded on the first call (and again after a
+ * build that changes a slot's depth, sizes or buffers) and replayed after;
+ * nothing synchronises the host.  The recorded builds skip the host-side
+ * checks of fmm_batch_build: fmm_batch_status reports what they found.
+ * Every slot must have been built once with fmm_batch_build.
+ * Errors: NOT_BUILT, CUDA. */
+int fmm_batch_step(gbfmm_batch *batch, double *const *f_nodes);
+
+/* Checks of the last builds and passes of every slot (synchronises): *status
+ * is GBFMM_OK, or for the first slot *slot with a problem GBFMM_ERR_DEGENERATE
+ * (a zero-length or non-finite segment), GBFMM_ERR_INVALID_ARG (non-finite
+ * node coordinates) or GBFMM_ERR_TIMEOUT (a bounded wait of the M2L gave up;
+ * cleared by the read).  slot, status: host. */
+int fmm_batch_status(gbfmm_batch *batch, int *slot, int *status);
+
+/* Tile form of the tensor-core M2L the slots use, and when the autotuner chose
+ * it (batch created with m2l_kernel = 2) the M2L stage time of each form on
+ * the calibration network in milliseconds (-1 when not measured).  Any output
+ * may be NULL; m2l_ms: host, 2 doubles. */
+int fmm_batch_tuning(const gbfmm_batch *batch, int *m2l_kernel, double *m2l_ms);
+
+/* Slot k's tree depth, the total kernel launches of all slots (direct
+ * launches plus the kernel nodes of every graph replay), and the autotuner's
+ * cost constants (seconds per near pair, per cell); any output may be NULL. */
 int fmm_batch_info(const gbfmm_batch *batch, int k, int *levels, int64_t *launches, double *c_near, double *c_far);
 
 /* ------------------------------------------------------------------------

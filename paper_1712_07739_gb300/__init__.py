@@ -33,7 +33,7 @@ EXPORTS = [
     "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
     "fmm_mlp_eval_noalloc", "fmm_mlp_calibrate",
     "fmm_batch_create", "fmm_batch_destroy", "fmm_batch_last_error", "fmm_batch_set_material", "fmm_batch_build",
-    "fmm_batch_eval_nodal_forces", "fmm_batch_info",
+    "fmm_batch_eval_nodal_forces", "fmm_batch_info", "fmm_batch_step", "fmm_batch_status", "fmm_batch_tuning",
 ]
 MLP_PARAMS = 37664
 
@@ -104,8 +104,11 @@ def load_library(path: str = LIB_PATH):
     L.fmm_batch_eval_nodal_forces.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
     L.fmm_batch_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64),
                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.fmm_batch_step.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
+    L.fmm_batch_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.fmm_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     for name in ("fmm_batch_create", "fmm_batch_set_material", "fmm_batch_build", "fmm_batch_eval_nodal_forces",
-                 "fmm_batch_info"):
+                 "fmm_batch_info", "fmm_batch_step", "fmm_batch_status", "fmm_batch_tuning"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("fmm_mlp_calibrate", "fmm_mlp_eval_noalloc", "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
                  "fmm_inject_fault", "fmm_device_status", "fmm_launch_count", "fmm_work_counts", "fmm_create", "fmm_set_material", "fmm_build_tree", "fmm_eval_stress",
@@ -402,11 +405,38 @@ class Batch:
                                               _ptr(segs), _ptr(burgers)), "fmm_batch_build")
         return self
 
+    def nodes(self, k):
+        """Network k's node array as the library reads it (the tensor given to
+        build, or its float64 copy): move nodes in place, then call step()."""
+        return self._keep[k][0]
+
     def nodal_forces(self):
         """Evaluate every network; returns the list of [n_nodes_k, 3] tensors (reused between calls)."""
         arr = (ctypes.c_void_p * self.n)(*[o.data_ptr() for o in self._out])
         self._check(self._lib.fmm_batch_eval_nodal_forces(self._h, arr), "fmm_batch_eval_nodal_forces")
         return self._out
+
+    def step(self):
+        """Rebuild every network from its current node positions and evaluate all
+        of them as one graph replay (the inputs' sizes and addresses must be the
+        ones of the last build); returns the list of force tensors."""
+        arr = (ctypes.c_void_p * self.n)(*[o.data_ptr() for o in self._out])
+        self._check(self._lib.fmm_batch_step(self._h, arr), "fmm_batch_step")
+        return self._out
+
+    def status(self):
+        """(slot, code) of the first network whose last build or pass reported a
+        problem, or (-1, 0) (synchronises)."""
+        k, c = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.fmm_batch_status(self._h, ctypes.byref(k), ctypes.byref(c)), "fmm_batch_status")
+        return k.value, c.value
+
+    def tuning(self):
+        """M2L tile form in use and, when the autotuner chose it, each form's M2L
+        time on the calibration network (ms)."""
+        form, ms = ctypes.c_int(), (ctypes.c_double * 2)()
+        self._check(self._lib.fmm_batch_tuning(self._h, ctypes.byref(form), ms), "fmm_batch_tuning")
+        return {"m2l_kernel": form.value, "m2l_ms": [ms[0], ms[1]]}
 
     def info(self, k):
         lv, la = ctypes.c_int(), ctypes.c_int64()

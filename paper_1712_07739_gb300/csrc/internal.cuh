@@ -185,7 +185,7 @@ __host__ __device__ inline int64_t cell_base_d(int l) { return ((int64_t(1) << (
 
 // stages (implemented in the .cu files)
 int material_setup(gbfmm_ctx *ctx);                 // material.cu
-int tree_build(gbfmm_ctx *ctx);                     // tree.cu
+int tree_build(gbfmm_ctx *ctx, bool validate = true);  // tree.cu; validate: read back the checks (synchronises)
 int fmm_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t);  // fmm.cu
 int forces_from_stress(gbfmm_ctx *ctx, double *f_nodes, double *f_seg, double *sigma_pts);
 int targets_sort(gbfmm_ctx *ctx, int64_t n_t, const double *x);

@@ -252,7 +252,7 @@ inline unsigned nblk(int64_t n, int b) { return unsigned((n + b - 1) / b); }
 
 }  // namespace
 
-int tree_build(gbfmm_ctx *ctx) {
+int tree_build(gbfmm_ctx *ctx, bool validate) {
     cudaStream_t st = ctx->stream;
     const int ng = ctx->opt.n_gauss;
     const int64_t N = ctx->N;
@@ -290,6 +290,9 @@ int tree_build(gbfmm_ctx *ctx) {
     k_gather_points<<<nblk(N, 256), 256, 0, st>>>(N, ng, perm, y0, q0, len0, leaf_of, ctx->d_y, ctx->d_q,
                                                   ctx->d_sid, ctx->d_slen, ctx->d_pos, ctx->d_pleaf);
     CK(cudaGetLastError());
+    // without validation (a build recorded into a graph) the flag stays on the device:
+    // fmm_batch_status reads it with the root box
+    if (!validate) return GBFMM_OK;
     int hbad = 0;
     CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     TreeBox hb{};

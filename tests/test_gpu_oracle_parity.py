@@ -169,7 +169,8 @@ def c5_gold():
 
 def test_ensemble_networks_match_stored_direct_sum(c5_gold):
     """Three networks of the 64-network cubic ensemble through the batched
-    pass in the ensemble workload's configuration (bench.py c5), against
+    step in the ensemble workload's configuration (bench.py c5: autotuned
+    depth and M2L tile form, builds and passes replayed as one graph), against
     direct-sum forces at 8 nodes each."""
     import sys
 
@@ -182,11 +183,13 @@ def test_ensemble_networks_match_stored_direct_sum(c5_gold):
     picks = c5_gold["networks"]
     nets = [nets_all[g["index"]] for g in picks]
     bt = gb.Batch(len(nets), p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
-                  circle_q=wl["circle_q"], m2l_split=wl.get("m2l_split", 4), m2l_basis=wl.get("m2l_basis"),
-                  m2l_chunks=wl.get("m2l_chunks")).set_material(wl["C"]())
+                  circle_q=wl["circle_q"], **bench.m2l_options(wl)).set_material(wl["C"]())
     for k, (n, s, b) in enumerate(nets):
         bt.build(k, _gpu(n), _gpu(s), _gpu(b))
-    F = [x.cpu().numpy() for x in bt.nodal_forces()]
+    bt.step()
+    F = [x.cpu().numpy() for x in bt.step()]
+    assert bt.status() == (-1, 0)
+    print("M2L tile form", bt.tuning())
     for k, g in enumerate(picks):
         n, s, b = nets[k]
         assert g["n_segs"] == len(s) and g["checks"]["sum_segs"] == int(s.sum())
