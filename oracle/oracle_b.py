@@ -18,6 +18,13 @@ local values interpolated to its nodes, and a leaf's targets get the local
 values interpolated to them plus the direct sum of Eq. "stress3" over the
 neighbouring leaves.
 
+The Chebyshev FMM the paper compares against (Sec. 3, the kernel-independent
+method of Fong and Darve it implements) is the same algorithm on Chebyshev
+nodes with the M2L compressed by the singular value decomposition: the node
+set is a parameter here (``nodes``), and ``m2l_svd_bases`` gives the two
+orthonormal bases of the compression, which ``lagrange_fmm`` applies when
+given them.
+
 ``lagrange_fmm`` computes that result level by level.
 ``pairwise_far_field`` evaluates Eq. "far-field" separately for every
 (target cell, interaction-list cell) pair at every level, with no
@@ -29,7 +36,18 @@ Conventions (readings of the paper where it is silent):
   points (1 if they coincide), centred on their bounding box; a point goes to
   cell floor((y - origin) * (2^l / H)), clamped to [0, 2^l - 1];
 * nodes: p equispaced nodes per dimension including the cell faces,
-  t_a = a / (p - 1), a = 0..p-1 (Section 4.1);
+  t_a = a / (p - 1), a = 0..p-1 (Section 4.1); Chebyshev nodes are the
+  zeros of the Chebyshev polynomial T_p mapped to [0, 1] (first kind),
+  t_a = (1 - cos((2a + 1) pi / (2p))) / 2, in increasing order;
+* SVD compression (Sec. 3, Eq. "mem_cheb"; the paper gives the compression
+  ratio, not the construction, which is the cited black-box FMM's): with
+  T_o the node-kernel matrix of offset o on a unit cell (rows (target node,
+  stress component), columns (source node, strength component)), the target
+  basis U holds the leading left singular vectors of [T_1 ... T_316] side by
+  side and the source basis R the leading right singular vectors of the 316
+  stacked; a vector is kept while its singular value exceeds tol times the
+  largest.  The compressed M2L applies U (U^T T_o R) R^T in place of T_o;
+  the kernel's homogeneity makes the bases one for all levels;
 * basis: "owner cell's basis at node l, evaluated at the point" for all of
   P2M, M2M, L2L and L2P (the argument order of L_p is inconsistent between
   Algorithms 1 and 2);
@@ -62,9 +80,18 @@ def cell_of(y, origin, H, level):
     return np.clip(idx, 0, n - 1)
 
 
-def basis_1d(t, p):
-    """ell_a(t) = prod_{b != a} (t - t_b) / (t_a - t_b), t_a = a/(p-1)."""
-    nodes = np.arange(p) / (p - 1)
+def node_positions(p, nodes="equispaced"):
+    """The p interpolation nodes of a unit cell, in [0, 1], increasing."""
+    if nodes == "equispaced":
+        return np.arange(p) / (p - 1)
+    if nodes == "chebyshev":
+        return 0.5 * (1.0 - np.cos((2 * np.arange(p) + 1) * np.pi / (2 * p)))
+    raise ValueError(nodes)
+
+
+def basis_1d(t, p, nodes="equispaced"):
+    """ell_a(t) = prod_{b != a} (t - t_b) / (t_a - t_b) on the node set's t_a."""
+    nodes = node_positions(p, nodes)
     t = np.asarray(t, dtype=np.float64)
     out = np.ones(t.shape + (p,))
     for a in range(p):
@@ -74,17 +101,17 @@ def basis_1d(t, p):
     return out
 
 
-def basis_3d(t, p):
+def basis_3d(t, p, nodes="equispaced"):
     """L_p(xbar_l, x) for local coordinates t [n, 3] -> [n, p^3], l = (a, b, c)
     flattened with a (x) slowest."""
-    bx, by, bz = basis_1d(t[:, 0], p), basis_1d(t[:, 1], p), basis_1d(t[:, 2], p)
+    bx, by, bz = basis_1d(t[:, 0], p, nodes), basis_1d(t[:, 1], p, nodes), basis_1d(t[:, 2], p, nodes)
     return np.einsum("na,nb,nc->nabc", bx, by, bz).reshape(len(t), p ** 3)
 
 
-def child_transfer(p):
+def child_transfer(p, nodes="equispaced"):
     """M[c][a', a] = ell_a'((c + t_a) / 2): parent basis a' at child node a."""
-    nodes = np.arange(p) / (p - 1)
-    return [basis_1d((c + nodes) / 2.0, p).T for c in (0, 1)]
+    t = node_positions(p, nodes)
+    return [basis_1d((c + t) / 2.0, p, nodes).T for c in (0, 1)]
 
 
 def interaction_offsets(cell):
@@ -102,11 +129,11 @@ def interaction_offsets(cell):
     return out
 
 
-def _node_kernels(mat, p, h, o, rows=None):
+def _node_kernels(mat, p, h, o, rows=None, nodes="equispaced"):
     """T_o[l, :, m, :] = K(xbar_l - ybar_m) for one offset o, with the node
     difference (o + (t_l - t_m)) h; returns [len(rows), 6, p^3, 9] for the
     requested target-node rows l (all rows by default)."""
-    t = np.arange(p) / (p - 1)
+    t = node_positions(p, nodes)
     g = np.array(list(itertools.product(t, t, t)))  # [p^3, 3], x slowest
     if rows is None:
         rows = np.arange(len(g))
@@ -116,16 +143,47 @@ def _node_kernels(mat, p, h, o, rows=None):
     return np.ascontiguousarray(K.transpose(0, 2, 1, 3))
 
 
-def _apply_offset(mat, p, h, o, Wstack, chunk=64):
+def _apply_offset(mat, p, h, o, Wstack, chunk=64, nodes="equispaced"):
     """sum_m K(xbar_l - ybar_m) W_m for a stack of source weights [n, p^3, 9]
     -> [n, p^3, 6], building the node kernel a block of rows at a time."""
     P3 = p ** 3
     out = np.zeros((Wstack.shape[0], P3, 6))
     for r0 in range(0, P3, chunk):
         rows = np.arange(r0, min(P3, r0 + chunk))
-        T = _node_kernels(mat, p, h, o, rows)
+        T = _node_kernels(mat, p, h, o, rows, nodes)
         out[:, rows, :] = np.einsum("lamw,nmw->nla", T, Wstack)
     return out
+
+
+def m2l_offsets():
+    """The 316 offsets o = B - A over all interaction lists: o in [-3, 3]^3 with
+    max |o_i| >= 2 (the 7^3 - 3^3 of Sec. 3's count of pre-computed operators)."""
+    return [o for o in itertools.product(range(-3, 4), repeat=3) if max(abs(x) for x in o) >= 2]
+
+
+def m2l_svd_bases(mat, p, nodes="equispaced", tol=None, ranks=None):
+    """Bases of the SVD-compressed M2L on a unit cell (module header): U [6 p^3, r1]
+    and R [9 p^3, r2] with orthonormal columns, and the singular values of the
+    side-by-side (target side) and stacked (source side) operator matrices, in
+    decreasing order.  Their squares are the eigenvalues of the Gram matrices
+    sum_o T_o T_o^T and sum_o T_o^T T_o, whose eigenvectors are the singular
+    vectors.  The ranks come from ``tol`` (relative to the largest singular
+    value) or are given as ``ranks`` = (r1, r2)."""
+    P3 = p ** 3
+    Gt = np.zeros((6 * P3, 6 * P3))
+    Gs = np.zeros((9 * P3, 9 * P3))
+    for o in m2l_offsets():
+        T = _node_kernels(mat, p, 1.0, o, nodes=nodes).reshape(6 * P3, 9 * P3)
+        Gt += T @ T.T
+        Gs += T.T @ T
+    lt, Ut = np.linalg.eigh(Gt)
+    ls, Us = np.linalg.eigh(Gs)
+    st, Ut = np.sqrt(np.maximum(lt[::-1], 0.0)), Ut[:, ::-1]
+    ss, Us = np.sqrt(np.maximum(ls[::-1], 0.0)), Us[:, ::-1]
+    if ranks is None:
+        ranks = (int((st > tol * st[0]).sum()), int((ss > tol * ss[0]).sum()))
+    r1, r2 = ranks
+    return np.ascontiguousarray(Ut[:, :r1]), np.ascontiguousarray(Us[:, :r2]), st, ss
 
 
 def _near(mat, xt, tseg, tleaf, ys, qs, sseg, sleaf, n):
@@ -143,9 +201,11 @@ def _near(mat, xt, tseg, tleaf, ys, qs, sseg, sleaf, n):
     return out
 
 
-def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
+def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None, nodes="equispaced", svd=None):
     """Stress [n_t, 6] at targets by the multilevel Lagrange FMM (Algorithm 2; targets
-    default to sources)."""
+    default to sources), on the given node set; with svd = (U, R) from
+    ``m2l_svd_bases`` the M2L is the compressed one: every source cell's weights
+    are projected onto R's columns and every cell's M2L sum onto U's."""
     ys = np.asarray(ys, dtype=np.float64)
     qs = np.asarray(qs, dtype=np.float64).reshape(-1, 9)
     if xt is None:
@@ -159,10 +219,10 @@ def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
     sl = cell_of(ys, origin, H, lf)
     hL = H / nL
     t = (ys - (origin + sl * hL)) / hL
-    Lb = basis_3d(t, p)
+    Lb = basis_3d(t, p, nodes)
     np.add.at(W[lf], (sl[:, 0], sl[:, 1], sl[:, 2]), Lb[:, :, None] * qs[:, None, :])
     # weights of the parents: the parent basis at the child nodes (upward)
-    M = child_transfer(p)
+    M = child_transfer(p, nodes)
     for lev in range(lf - 1, 1, -1):
         n = 1 << lev
         Wp = np.zeros((n, n, n, P3, 9))
@@ -194,9 +254,15 @@ def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
                     groups.setdefault(o, []).append((B, A))
         for o, pairs in groups.items():
             Ws = np.stack([W[lev][A] for _, A in pairs])
-            res = _apply_offset(mat, p, h, o, Ws)
+            if svd is not None:  # R R^T W: the source weights seen through the compression
+                R = svd[1]
+                Ws = ((Ws.reshape(len(pairs), 9 * P3) @ R) @ R.T).reshape(len(pairs), P3, 9)
+            res = _apply_offset(mat, p, h, o, Ws, nodes=nodes)
             for (B, _), r in zip(pairs, res):
                 S[lev][B] += r
+        if svd is not None:  # U U^T of each cell's M2L sum
+            U = svd[0]
+            S[lev] = ((S[lev].reshape(-1, 6 * P3) @ U) @ U.T).reshape(S[lev].shape)
     # local values of the children: the parent's interpolated to the child nodes (downward)
     for lev in range(3, lf + 1):
         n = 1 << (lev - 1)
@@ -209,12 +275,12 @@ def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
     out = np.zeros((len(xt), 6))
     if lf >= 2:
         tt = (xt - (origin + tl * hL)) / hL
-        out += np.einsum("nl,nls->ns", basis_3d(tt, p), S[lf][tl[:, 0], tl[:, 1], tl[:, 2]])
+        out += np.einsum("nl,nls->ns", basis_3d(tt, p, nodes), S[lf][tl[:, 0], tl[:, 1], tl[:, 2]])
     out += _near(mat, xt, np.asarray(tseg), tl, ys, qs, np.asarray(sseg), sl, nL)
     return out
 
 
-def pairwise_far_field(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
+def pairwise_far_field(mat, ys, qs, sseg, p, L, xt=None, tseg=None, nodes="equispaced"):
     """Far field of the same tree by Eq. "far-field" for each (B, A) pair with
     A in I(B), at each level >= 2: the weights of A's points on A's nodes, the
     node kernel of the pair, B's basis at B's points.  Near sum included."""
@@ -232,15 +298,15 @@ def pairwise_far_field(mat, ys, qs, sseg, p, L, xt=None, tseg=None):
         tc = cell_of(xt, origin, H, lev)
         for B in {tuple(r) for r in tc}:
             ti = np.nonzero((tc == B).all(axis=1))[0]
-            LB = basis_3d((xt[ti] - (origin + np.asarray(B) * h)) / h, p)
+            LB = basis_3d((xt[ti] - (origin + np.asarray(B) * h)) / h, p, nodes)
             for o in interaction_offsets(B):
                 A = tuple(B[d] - o[d] for d in range(3))
                 sj = np.nonzero((sc == A).all(axis=1))[0]
                 if len(sj) == 0:
                     continue
-                LA = basis_3d((ys[sj] - (origin + np.asarray(A) * h)) / h, p)
+                LA = basis_3d((ys[sj] - (origin + np.asarray(A) * h)) / h, p, nodes)
                 Wm = LA.T @ qs[sj]                                   # weights on A's nodes
-                sl = _apply_offset(mat, p, h, o, Wm[None])[0]        # node kernel of (B, A)
+                sl = _apply_offset(mat, p, h, o, Wm[None], nodes=nodes)[0]  # node kernel of (B, A)
                 out[ti] += LB @ sl                                    # B's basis at the targets
     nL = 1 << lf
     out += _near(mat, xt, np.asarray(tseg), cell_of(xt, origin, H, lf), ys, qs,
