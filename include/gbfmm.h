@@ -261,15 +261,15 @@ int fmm_probe_fma(int kind, void *cuda_stream, double *tflops);
  *
  * A batch holds one network per slot; all slots share the medium's tables
  * (kernel lattice and M2L operators, which do not depend on the network).
- * With opt.levels == 0 each slot's tree depth is chosen by an autotuner: a
- * pass is modelled as c_near x (near point pairs) + c_far x (cells of levels
- * >= 2) (the near/far cost balance of App. B), the two constants are
- * measured once by timing a pass of the first network built, and the depth
- * with the smallest predicted time among L0-1..L0+1 (L0 from N_s /
- * leaf_segments) is kept; the slot keeps it for later builds while its N_s
- * stays within 10 %.  Created with m2l_kernel = 2, the same calibration also
- * times both tile forms of the tensor-core M2L (gbfmm_options.m2l_kernel) on
- * that network and keeps the faster for every slot.
+ * With opt.levels == 0 each slot's tree depth is chosen by an autotuner
+ * (the near/far cost balance of App. B): one pass of the network is timed at
+ * each candidate depth from L0 - 1 up (L0 from N_s / leaf_segments), deeper
+ * while the time keeps falling, and the fastest depth is kept; the slot keeps
+ * it for later builds while its N_s stays within 10 %.  The first network
+ * built also gives two informational constants (c_near, c_far: seconds per
+ * near pair and per cell of levels >= 2 at L0).  Created with m2l_kernel = 2,
+ * that first network also times both tile forms of the tensor-core M2L
+ * (gbfmm_options.m2l_kernel) and the faster is kept for every slot.
  * fmm_batch_eval_nodal_forces records the passes of
  * all slots into one CUDA graph (spread over up to 8 internal streams and
  * joined back onto the batch's stream) on its first call after a build, and
@@ -319,8 +319,9 @@ int fmm_batch_status(gbfmm_batch *batch, int *slot, int *status);
 int fmm_batch_tuning(const gbfmm_batch *batch, int *m2l_kernel, double *m2l_ms);
 
 /* Slot k's tree depth, the total kernel launches of all slots (direct
- * launches plus the kernel nodes of every graph replay), and the autotuner's
- * cost constants (seconds per near pair, per cell); any output may be NULL. */
+ * launches plus the kernel nodes of every graph replay), and the cost
+ * constants measured on the first network (seconds per near pair, per cell);
+ * any output may be NULL. */
 int fmm_batch_info(const gbfmm_batch *batch, int k, int *levels, int64_t *launches, double *c_near, double *c_far);
 
 /* ------------------------------------------------------------------------

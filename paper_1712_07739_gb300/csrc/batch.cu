@@ -4,12 +4,13 @@
 // depends only on the medium and the order p (the kernel lattice and the M2L
 // operator tables, Sec. 4.1: the operators do not depend on the
 // configuration), so the tables exist once.  Each network gets its own tree
-// depth from an autotuner that follows the cost model of App. B with
-// constants measured on this GPU: a pass costs c_near x (near point pairs) +
-// c_far x (cells of levels >= 2), and the depth that minimises it is taken
-// among the candidates around N_s / leaf_segments.  The evaluation of all
-// networks is recorded once into a CUDA graph (fanned out over a few
-// streams) and replayed; a rebuild invalidates it.
+// depth from an autotuner that settles the near/far balance of App. B by
+// measurement: the candidates from N_s / leaf_segments down by one level and
+// up while the time falls are each timed on the network, and the fastest is
+// kept (a fixed cost per cell does not hold: the tensor-core M2L's tiles fill
+// up with depth).  The evaluation of all networks, or every network's tree
+// build and evaluation, is recorded once into a CUDA graph (fanned out over
+// a few streams) and replayed; a rebuild invalidates it.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -40,7 +41,7 @@ struct gbfmm_batch {
     int64_t replayed = 0;  // kernels run by graph replays (the contexts count only direct launches)
     bool auto_kernel = false;  // the autotuner picks the M2L tile form (m2l_kernel = 2 at creation)
     double m2l_ms_form[2] = {-1.0, -1.0};  // M2L stage times of the two forms on the calibration network (ms)
-    double c_near = 0.0, c_far = 0.0;  // seconds per near pair / per cell (autotuner)
+    double c_near = 0.0, c_far = 0.0;  // seconds per near pair / per cell, first network at L0 (reported)
     std::vector<int> tuned_L;          // depth chosen per slot, reused while N_s stays within 10 %
     std::vector<int64_t> tuned_ns;
     std::string err;
@@ -215,6 +216,28 @@ static int tune_form(gbfmm_batch *b, gbfmm_ctx *c, int64_t n_nodes, double ms0, 
     return GBFMM_OK;
 }
 
+// Elapsed time of one pass of slot context c at its current build (milliseconds)
+static int time_pass(gbfmm_batch *b, gbfmm_ctx *c, int64_t n_nodes, double *ms) {
+    double *f = nullptr;
+    if (cudaMalloc(&f, n_nodes * 3 * sizeof(double)) != cudaSuccess)
+        return berr(b, GBFMM_ERR_CUDA, "fmm_batch_build: calibration buffer");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+    int rc = fmm_eval_nodal_forces(c, f, nullptr, nullptr);
+    cudaEventRecord(e1, c->stream);
+    float t = 0.f;
+    if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        rc = GBFMM_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(f);
+    if (rc) return berr(b, rc, rc == GBFMM_ERR_CUDA ? std::string("fmm_batch_build: timed pass") : fmm_last_error(c));
+    *ms = double(t);
+    return GBFMM_OK;
+}
+
 // cells of levels 2 .. L-1 (the M2L work of the dense tensor-core pass)
 static double far_cells(int L) {
     double s = 0.0;
@@ -274,18 +297,22 @@ extern "C" int fmm_batch_build(gbfmm_batch *b, int k, int64_t n_nodes, const dou
         if (b->auto_kernel && b->m2l_ms_form[0] < 0.0 && (rc = tune_form(b, c, n_nodes, t[2], build_at)))
             return rc;
     }
+    // every candidate depth timed on this network (one pass each): the near field and
+    // the M2L trade against each other, and the M2L's cost per cell falls steeply with
+    // depth while its tiles fill up, which no per-cell constant captures.  Deeper
+    // candidates are tried while the time keeps falling.
     int best = L0;
     double best_t = 1e300;
-    for (int L = std::max(3, L0 - 1); L <= std::min(8, L0 + 1); ++L) {
+    for (int L = std::max(3, L0 - 1); L <= 8; ++L) {
         int rc = build_at(L);
         if (rc) return berr(b, rc, fmm_last_error(c));
-        int64_t w[4];
-        rc = work_counts(c, w);
-        if (rc) return berr(b, rc, fmm_last_error(c));
-        const double pred = b->c_near * double(w[0]) + b->c_far * far_cells(L);
-        if (pred < best_t) {
-            best_t = pred;
+        double ms = 0.0;
+        if ((rc = time_pass(b, c, n_nodes, &ms))) return rc;
+        if (ms < best_t) {
+            best_t = ms;
             best = L;
+        } else if (L > L0) {
+            break;
         }
     }
     if (c->L != best) {
