@@ -137,6 +137,16 @@ WORKLOADS["c3"] = dict(
          "is timed in the same run",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
     h_mode="circle", circle_q=16, p=7, levels=7, precision="mixed", fp64_arm=True, **MIXED_M2L)
+WORKLOADS["c3svd"] = dict(
+    desc="c3 (1,000,000 slab segments, cubic, p=7, 7 levels, Q=16) with the SVD-compressed M2L (the Chebyshev "
+         "FMM's compression on the equispaced nodes: singular vectors kept above 1e-6 of the largest)",
+    gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=16, p=7, levels=7,
+    precision="mixed", m2l_svd_tol=1e-6, m2l_split=6, m2l_chunks=7, m2l_split_kblocks=1)
+WORKLOADS["c3cheb"] = dict(
+    desc="c3 on Chebyshev nodes with the SVD-compressed M2L (the paper's Chebyshev FMM), singular vectors kept "
+         "above 1e-6 of the largest",
+    gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=16, p=7, levels=7,
+    precision="mixed", nodes="chebyshev", m2l_svd_tol=1e-6, m2l_split=6, m2l_chunks=7, m2l_split_kblocks=1)
 WORKLOADS["c3_iso"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs), isotropic mu=1 nu=0.3, p=7, mixed precision",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.isotropic_voigt(1.0, 0.3),
@@ -542,7 +552,8 @@ def run_ours(args, wl):
     peaks = measured_alu_peaks()
     st = np.array(stage)            # [steps, 8]: precontract, P2M+M2M, M2L, L2L, L2P+P2P, forces
     p = wl["p"]
-    roofline = roofline_of(wl, work, st[:, 2].mean(), st[:, 4].mean(), int(f.options.m2l_fft), peaks)
+    ranks = f.m2l_ranks()
+    roofline = roofline_of(wl, work, st[:, 2].mean(), st[:, 4].mean(), int(f.options.m2l_fft), peaks, ranks=ranks)
     accuracy = oracle_node_error(wl, args.workload, out.cpu().numpy(), nodes, segs, b)
     f.close()
 
@@ -569,6 +580,8 @@ def run_ours(args, wl):
                        "m2l_chunks": int(f.options.m2l_chunks), "m2l_basis": int(f.options.m2l_basis),
                        "m2l_split_kblocks": int(f.options.m2l_split_kblocks),
                        "m2l_kernel": int(f.options.m2l_kernel), "m2l_fft": int(f.options.m2l_fft),
+                       "nodes": ["equispaced", "chebyshev"][int(f.options.nodes)],
+                       "m2l_svd_tol": float(f.options.m2l_svd_tol), "m2l_svd_ranks": ranks,
                        "l2": "flushed: 256 MiB write between steps, outside the step events",
                        "step": "fmm_build_tree + fmm_eval_nodal_forces"},
             "stage_ms": {"precontract": st[:, 0].mean(), "p2m_m2m": st[:, 1].mean(), "m2l": st[:, 2].mean(),
@@ -589,12 +602,13 @@ def run_ours(args, wl):
 
 
 GOLDEN = {"c3": "c3_sampled_forces.json", "c3q": "c3q_sampled_forces.json", "c3_fp64": "c3_sampled_forces.json",
-          "c2": "c2_forces.json"}
+          "c2": "c2_forces.json", "c3svd": "c3_sampled_forces.json", "c3cheb": "c3_sampled_forces.json"}
 
 
 def m2l_options(wl):
     """The tensor-core M2L operand options a workload names (library defaults otherwise)."""
-    return {k: wl[k] for k in ("m2l_split", "m2l_basis", "m2l_chunks", "m2l_split_kblocks", "m2l_kernel") if k in wl}
+    return {k: wl[k] for k in ("m2l_split", "m2l_basis", "m2l_chunks", "m2l_split_kblocks", "m2l_kernel", "nodes",
+                               "m2l_svd_tol") if k in wl}
 
 
 def oracle_node_error(wl, name, F, nodes, segs, b):
@@ -620,9 +634,12 @@ def oracle_node_error(wl, name, F, nodes, segs, b):
             "oracle": f"tests/golden/{fn}: FP64 direct sum, unit-circle h Q={gold.get('Q')}"}
 
 
-def roofline_of(wl, work, m2l_ms, leaf_ms, m2l_fft, peaks):
+def roofline_of(wl, work, m2l_ms, leaf_ms, m2l_fft, peaks, ranks=None):
     """Roofline of the dominant stage of a pass: near field + L2P (ALU-bound)
-    or M2L (tensor-bound on the mixed pass, FP64 ALU on the FP64 pass)."""
+    or M2L (tensor-bound on the mixed pass, FP64 ALU on the FP64 pass).  With
+    the compressed M2L a cell pair costs 2 r1 r2 (the ranks as run), and the
+    stage time includes the two per-cell basis transforms."""
+    svd = bool(ranks and ranks.get("r1"))
     p = wl["p"]
     fp64 = wl["precision"] == "fp64"
     alu_peak = peaks["fp64_tflops"] if fp64 else peaks["fp32_tflops"]
@@ -640,6 +657,8 @@ def roofline_of(wl, work, m2l_ms, leaf_ms, m2l_fft, peaks):
         # dense: 2*54*p^6 per cell pair; through transforms: 54 complex multiply-adds
         # (8 FLOP) at each of (2p)^2 (p+1) frequencies per cell pair
         per_pair = 8 * 54 * (2 * p) ** 2 * (p + 1) if fft else 2 * 54 * p ** 6
+        if svd:
+            per_pair = 2 * ranks["r1"] * ranks["r2"]
         flops = work["m2l_pairs"] * per_pair
         achieved = flops / (m2l_ms / 1e3) / 1e12
         if fp64:
@@ -647,15 +666,18 @@ def roofline_of(wl, work, m2l_ms, leaf_ms, m2l_fft, peaks):
             bound, peak, src = "alu", alu_peak, peaks["source"]
         else:
             dom, bound = "k_m2l_tc (M2L, tcgen05 FP16 operands)", "tensor"
+            if svd:
+                dom = "k_m2l_tc (SVD-compressed M2L, tcgen05 FP16 operands; stage includes the basis transforms)"
             peak, src = measured_bf16_peak()
-            if p == 7 and wl.get("m2l_basis") == 1:
+            if p == 7 and wl.get("m2l_basis") == 1 and not svd:
                 traffic = M2L_TC_P7_DRAM_BYTES_PER_PAIR * work["m2l_pairs"]
                 traffic_src = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_m2l_tc (p=7, "
                                "default operands) on the 250k-segment slab network, scaled by occupied cell pairs")
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": src,
             "work": "algorithmic: near pairs x FLOP/pair (h once per unordered pair when h is the unit-circle "
-                    "rule) + L2P, or M2L cell pairs x 2*54*p^6 (x 8*54*(2p)^2*(p+1) through transforms)"}
+                    "rule) + L2P, or M2L cell pairs x 2*54*p^6 (x 8*54*(2p)^2*(p+1) through transforms, "
+                    "x 2*r1*r2 compressed)"}
 
 
 def run_fp64_arm(wl, name, d_nodes, d_segs, d_b, nodes, segs, b, flush, stream):
@@ -709,6 +731,7 @@ def main():
     ap.add_argument("--m2l-basis", type=int, default=-1, help="override the M2L operand basis (fmm options)")
     ap.add_argument("--m2l-split-kblocks", type=int, default=-1, help="override the residual K blocks (fmm options)")
     ap.add_argument("--m2l-kernel", type=int, default=-1, help="override the M2L tile form (fmm options)")
+    ap.add_argument("--m2l-svd-tol", type=float, default=-1.0, help="override the M2L compression (fmm options)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.p:
@@ -725,6 +748,8 @@ def main():
         wl["m2l_split_kblocks"] = args.m2l_split_kblocks
     if args.m2l_kernel >= 0:
         wl["m2l_kernel"] = args.m2l_kernel
+    if args.m2l_svd_tol >= 0:
+        wl["m2l_svd_tol"] = args.m2l_svd_tol
     if args.impl == "reference":
         run_reference(args, wl)
     elif wl.get("batch"):

@@ -68,6 +68,10 @@ extern "C" {
 #define GBFMM_M2L_FP16_SPLIT_ALL 6  /* FP16 scaled, residual passes on all 316 offsets (fmm_default_options,
                                        over the leading K block: m2l_split_kblocks = 1) */
 
+/* interpolation nodes per axis of a cell (gbfmm_options.nodes) */
+#define GBFMM_NODES_EQUISPACED 0  /* t_a = a / (p - 1), faces included (Sec. 4.1) */
+#define GBFMM_NODES_CHEBYSHEV 1   /* zeros of T_p mapped to [0, 1] (the Chebyshev FMM, Sec. 3) */
+
 typedef struct {
     int p;                 /* Lagrange nodes per dimension, 2..8 (Sec. 4.1) */
     int n_gauss;           /* Gauss points per segment, 1..16 (Sec. 2, Eq. "stress_discrete") */
@@ -122,6 +126,22 @@ typedef struct {
                               operator rows shared as N; 1 = two 128-row blocks of operator
                               rows as the M operands, the CTA's 256 target cells shared as
                               N = 256 (half the gathered bytes per product). */
+    int nodes;             /* GBFMM_NODES_EQUISPACED (fmm_default_options) or
+                              GBFMM_NODES_CHEBYSHEV; Chebyshev nodes need the compressed M2L
+                              (m2l_svd_tol > 0, MIXED): their operators have no Toeplitz
+                              structure. */
+    double m2l_svd_tol;    /* MIXED: > 0 compresses the M2L by the singular value decomposition
+                              (the Chebyshev FMM's compression, Sec. 3, Eq. "mem_cheb"): the
+                              316 unit-cell operators T_o [6 p^3 x 9 p^3] side by side give a
+                              target basis U (left singular vectors), stacked a source basis R
+                              (right singular vectors); a vector is kept while its singular
+                              value exceeds m2l_svd_tol times the largest, the kept counts
+                              rounded up to the tile granularity (r1 to 16, r2 to 64).  Each
+                              pass then transforms every cell's multipole values W -> R^T W
+                              (r2 values), runs the tensor-core M2L on the r1 x r2 operators
+                              U^T T_o R, and expands the local values S = U S'.  The bases and
+                              operators are built in FP64 at fmm_set_material; m2l_basis is
+                              ignored.  0 = off (fmm_default_options). */
 } gbfmm_options;
 
 typedef struct gbfmm_ctx gbfmm_ctx;
@@ -202,6 +222,14 @@ int fmm_eval_nodal_forces(gbfmm_ctx *ctx, double *f_nodes, double *f_seg, double
  * (host outputs; any may be NULL). */
 int fmm_tree_info(const gbfmm_ctx *ctx, int *levels, int64_t *n_leaves, int64_t *n_points);
 
+/* The compressed M2L of a context (m2l_svd_tol > 0; set up by its first
+ * build): ranks[0..3] = target and source coefficients per cell as run (r1,
+ * r2, rounded up to the tiles) and the counts above the tolerance;
+ * sigma[0..3] = largest and smallest kept singular value, target side then
+ * source side.  All zero when the M2L is not compressed or not set up.
+ * ranks: host, 4 ints; sigma: host, 4 doubles; either may be NULL. */
+int fmm_m2l_ranks(const gbfmm_ctx *ctx, int *ranks, double *sigma);
+
 /* Device time in milliseconds of each stage of the last fmm_eval_* call,
  * measured with CUDA events on the context stream: [0] precompute
  * source tensors, [1] P2M+M2M, [2] M2L, [3] L2L, [4] L2P+P2P, [5] forces.
@@ -263,8 +291,8 @@ int fmm_probe_fma(int kind, void *cuda_stream, double *tflops);
  * (kernel lattice and M2L operators, which do not depend on the network).
  * With opt.levels == 0 each slot's tree depth is chosen by an autotuner
  * (the near/far cost balance of App. B): one pass of the network is timed at
- * each candidate depth from L0 - 1 up (L0 from N_s / leaf_segments), deeper
- * while the time keeps falling, and the fastest depth is kept; the slot keeps
+ * each candidate depth L0 - 1 .. L0 + 1 (L0 from N_s / leaf_segments; the
+ * deepest only while the time is still falling) and the fastest is kept; the slot keeps
  * it for later builds while its N_s stays within 10 %.  The first network
  * built also gives two informational constants (c_near, c_far: seconds per
  * near pair and per cell of levels >= 2 at L0).  Created with m2l_kernel = 2,

@@ -28,7 +28,7 @@ _HMODE = {"iso": H_ISO, "circle": H_CIRCLE, "mlp": H_MLP}
 EXPORTS = [
     "fmm_default_options", "fmm_create", "fmm_destroy", "fmm_last_error",
     "fmm_set_material", "fmm_build_tree", "fmm_eval_stress", "fmm_eval_nodal_forces",
-    "fmm_tree_info", "fmm_set_timing", "fmm_stage_times", "fmm_launch_count", "fmm_work_counts",
+    "fmm_tree_info", "fmm_m2l_ranks", "fmm_set_timing", "fmm_stage_times", "fmm_launch_count", "fmm_work_counts",
     "fmm_device_status", "fmm_inject_fault", "fmm_probe_fma",
     "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
     "fmm_mlp_eval_noalloc", "fmm_mlp_calibrate",
@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
         ("leaf_segments", ctypes.c_int), ("near_fp64", ctypes.c_double), ("m2l_split", ctypes.c_int),
         ("mlp_min_dist", ctypes.c_double), ("m2l_fft", ctypes.c_int), ("m2l_chunks", ctypes.c_int),
         ("m2l_basis", ctypes.c_int), ("m2l_split_levels", ctypes.c_int), ("m2l_split_kblocks", ctypes.c_int),
-        ("m2l_kernel", ctypes.c_int),
+        ("m2l_kernel", ctypes.c_int), ("nodes", ctypes.c_int), ("m2l_svd_tol", ctypes.c_double),
     ]
 
 
@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
     L.fmm_eval_stress.argtypes = [vp, i64, dp, dp]
     L.fmm_eval_nodal_forces.argtypes = [vp, dp, dp, dp]
     L.fmm_tree_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.fmm_m2l_ranks.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.fmm_set_timing.argtypes = [vp, ctypes.c_int]
     L.fmm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.fmm_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
@@ -112,7 +113,7 @@ def load_library(path: str = LIB_PATH):
         getattr(L, name).restype = ctypes.c_int
     for name in ("fmm_mlp_calibrate", "fmm_mlp_eval_noalloc", "fmm_mlp_train", "fmm_mlp_get", "fmm_mlp_set", "fmm_mlp_eval", "fmm_mlp_grad", "fmm_mlp_labels",
                  "fmm_inject_fault", "fmm_device_status", "fmm_launch_count", "fmm_work_counts", "fmm_create", "fmm_set_material", "fmm_build_tree", "fmm_eval_stress",
-                 "fmm_eval_nodal_forces", "fmm_tree_info", "fmm_set_timing", "fmm_stage_times"):
+                 "fmm_eval_nodal_forces", "fmm_tree_info", "fmm_m2l_ranks", "fmm_set_timing", "fmm_stage_times"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -137,6 +138,16 @@ def probe_fma(kind, stream=None):
     return v.value
 
 
+_NODES = {"equispaced": 0, "chebyshev": 1}
+
+
+def _set_nodes_svd(o, nodes, m2l_svd_tol):
+    if nodes is not None:
+        o.nodes = _NODES[nodes] if isinstance(nodes, str) else int(nodes)
+    if m2l_svd_tol is not None:
+        o.m2l_svd_tol = float(m2l_svd_tol)
+
+
 class FMM:
     """One Lagrange-FMM context on the current CUDA device and stream.
 
@@ -147,13 +158,15 @@ class FMM:
 
     def __init__(self, p=4, n_gauss=4, levels=0, precision="fp64", h_mode="iso", circle_q=0,
                  leaf_segments=0, near_fp64=0.0, m2l_split=None, mlp_min_dist=0.0, m2l_fft=None, m2l_chunks=None,
-                 m2l_basis=None, m2l_split_levels=None, m2l_split_kblocks=None, m2l_kernel=None, stream=None):
+                 m2l_basis=None, m2l_split_levels=None, m2l_split_kblocks=None, m2l_kernel=None, nodes=None,
+                 m2l_svd_tol=None, stream=None):
         import torch
 
         self._torch = torch
         self._lib = load_library()
         o = Options()
         self._lib.fmm_default_options(ctypes.byref(o))
+        _set_nodes_svd(o, nodes, m2l_svd_tol)
         o.p, o.n_gauss, o.levels = p, n_gauss, levels
         o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
         o.h_mode = _HMODE[h_mode] if isinstance(h_mode, str) else int(h_mode)
@@ -243,6 +256,13 @@ class FMM:
         self._check(self._lib.fmm_tree_info(self._h, ctypes.byref(lv), ctypes.byref(nl), ctypes.byref(npt)),
                     "fmm_tree_info")
         return {"levels": lv.value, "n_leaves": nl.value, "n_points": npt.value}
+
+    def m2l_ranks(self):
+        """Compressed M2L: coefficients per cell as run and above the tolerance, and the
+        largest / smallest kept singular values (zeros when not compressed)."""
+        r, sg = (ctypes.c_int * 4)(), (ctypes.c_double * 4)()
+        self._check(self._lib.fmm_m2l_ranks(self._h, r, sg), "fmm_m2l_ranks")
+        return {"r1": r[0], "r2": r[1], "r1_raw": r[2], "r2_raw": r[3], "sigma": list(sg)}
 
     def launch_count(self):
         c = ctypes.c_int64()
@@ -344,13 +364,15 @@ class Batch:
 
     def __init__(self, n_configs, p=6, n_gauss=4, levels=0, precision="mixed", h_mode="circle", circle_q=0,
                  leaf_segments=0, near_fp64=0.0, m2l_split=None, m2l_basis=None, m2l_chunks=None,
-                 m2l_split_levels=None, m2l_split_kblocks=None, m2l_kernel=None, stream=None):
+                 m2l_split_levels=None, m2l_split_kblocks=None, m2l_kernel=None, nodes=None, m2l_svd_tol=None,
+                 stream=None):
         import torch
 
         self._torch = torch
         self._lib = load_library()
         o = Options()
         self._lib.fmm_default_options(ctypes.byref(o))
+        _set_nodes_svd(o, nodes, m2l_svd_tol)
         o.p, o.n_gauss, o.levels = p, n_gauss, levels
         o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
         o.h_mode = _HMODE[h_mode] if isinstance(h_mode, str) else int(h_mode)

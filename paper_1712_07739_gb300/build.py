@@ -21,6 +21,16 @@ def _nvcc():
     return "nvcc"
 
 
+def _which(cmd):
+    if os.path.isabs(cmd):
+        return cmd
+    for d in os.environ.get("PATH", "").split(os.pathsep):
+        c = os.path.join(d, cmd)
+        if os.path.exists(c):
+            return c
+    return "/usr/local/cuda/bin/nvcc"
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = srcs + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "gbfmm.h")]
@@ -42,7 +52,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(comp, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    # cuBLAS / cuSOLVER (the SVD setup and the compressed M2L's basis transforms), found
+    # at run time next to the CUDA runtime the library was built against
+    libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(_which(nvcc)))), "lib64")
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas", "-lcusolver",
+                           f"-Xlinker=-rpath={libdir}"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -120,7 +120,13 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
         opt->circle_q < 0 || opt->leaf_segments < 0 || !(opt->near_fp64 >= 0.0) || opt->m2l_split < 0 ||
         opt->m2l_split > 6 || opt->m2l_fft < 0 || opt->m2l_fft > 1 || opt->m2l_chunks < 0 ||
         opt->m2l_chunks > 189 || opt->m2l_basis < 0 || opt->m2l_basis > 1 ||
-        opt->m2l_split_kblocks < 0 || opt->m2l_kernel < 0 || opt->m2l_kernel > 1)
+        opt->m2l_split_kblocks < 0 || opt->m2l_kernel < 0 || opt->m2l_kernel > 1 || opt->nodes < 0 ||
+        opt->nodes > 1 || !(opt->m2l_svd_tol >= 0.0) || opt->m2l_svd_tol >= 1.0)
+        return GBFMM_ERR_INVALID_ARG;
+    // the compressed M2L runs in the mixed pass only, and Chebyshev nodes need it (their
+    // operators have no Toeplitz structure for the lattice table and the FFT M2L)
+    if ((opt->m2l_svd_tol > 0.0 || opt->nodes == GBFMM_NODES_CHEBYSHEV) &&
+        (opt->precision != GBFMM_MIXED || opt->m2l_svd_tol <= 0.0))
         return GBFMM_ERR_INVALID_ARG;
     gbfmm_ctx *ctx = new gbfmm_ctx();
     ctx->opt = *opt;
@@ -302,6 +308,21 @@ extern "C" int fmm_tree_info(const gbfmm_ctx *ctx, int *levels, int64_t *n_leave
     if (levels) *levels = ctx->L;
     if (n_leaves) *n_leaves = ctx->n_leaves;
     if (n_points) *n_points = ctx->N;
+    return GBFMM_OK;
+}
+
+extern "C" int fmm_m2l_ranks(const gbfmm_ctx *ctx, int *ranks, double *sigma) {
+    if (!ctx) return GBFMM_ERR_INVALID_ARG;
+    const TcPlan &T = ctx->tc;
+    const bool on = T.svd && T.bases_ok;
+    if (ranks) {
+        ranks[0] = on ? T.r1 : 0;
+        ranks[1] = on ? T.r2 : 0;
+        ranks[2] = on ? T.r1_raw : 0;
+        ranks[3] = on ? T.r2_raw : 0;
+    }
+    if (sigma)
+        for (int i = 0; i < 4; ++i) sigma[i] = on ? T.svd_sigma[i] : 0.0;
     return GBFMM_OK;
 }
 

@@ -153,6 +153,8 @@ extern "C" int fmm_batch_set_material(gbfmm_batch *b, const double *C_voigt) {
     gbfmm_ctx *c0 = b->ctx[0];
     int rc = fmm_set_material(c0, C_voigt);
     if (rc) return berr(b, rc, fmm_last_error(c0));
+    // the operator tables exist once, built here by the first slot, before the others share them
+    if (c0->opt.precision != GBFMM_FP64 && (rc = m2l_tc_setup(c0))) return berr(b, rc, fmm_last_error(c0));
     for (size_t k = 1; k < b->ctx.size(); ++k) {
         int r2 = share_material(b->ctx[k], c0);
         if (r2) return berr(b, r2, fmm_last_error(b->ctx[k]));
@@ -297,13 +299,14 @@ extern "C" int fmm_batch_build(gbfmm_batch *b, int k, int64_t n_nodes, const dou
         if (b->auto_kernel && b->m2l_ms_form[0] < 0.0 && (rc = tune_form(b, c, n_nodes, t[2], build_at)))
             return rc;
     }
-    // every candidate depth timed on this network (one pass each): the near field and
-    // the M2L trade against each other, and the M2L's cost per cell falls steeply with
-    // depth while its tiles fill up, which no per-cell constant captures.  Deeper
-    // candidates are tried while the time keeps falling.
+    // every candidate depth L0 - 1 .. L0 + 1 timed on this network (one pass each): the
+    // near field and the M2L trade against each other, and the M2L's cost per cell falls
+    // steeply with depth while its tiles fill up, which no per-cell constant captures.
+    // The deepest candidate is tried only while the time is still falling; the buffers
+    // keep the size of the deepest candidate built, which bounds a batch's memory.
     int best = L0;
     double best_t = 1e300;
-    for (int L = std::max(3, L0 - 1); L <= 8; ++L) {
+    for (int L = std::max(3, L0 - 1); L <= std::min(8, L0 + 1); ++L) {
         int rc = build_at(L);
         if (rc) return berr(b, rc, fmm_last_error(c));
         double ms = 0.0;

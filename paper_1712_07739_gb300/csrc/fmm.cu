@@ -73,7 +73,7 @@ __global__ void k_occ_up(int level, int *__restrict__ occ) {
 // one block per leaf; thread m accumulates W[m][0..8].  The local
 // coordinate of a point is formed in FP64; the basis and sums in R.
 template <typename R>
-__global__ void k_p2m(int p, int L, const TreeBox *__restrict__ box, const int *__restrict__ start,
+__global__ void k_p2m(int p, int nodes, int L, const TreeBox *__restrict__ box, const int *__restrict__ start,
                       const double *__restrict__ y, const double *__restrict__ q, R *__restrict__ W) {
     const int64_t leaf = blockIdx.x;
     const int nl = 1 << (L - 1);
@@ -102,7 +102,7 @@ __global__ void k_p2m(int p, int L, const TreeBox *__restrict__ box, const int *
             int j = t / 3, d = t % 3;
             R tt = R((y[3 * int64_t(j0 + j) + d] - c0[d]) * ih);
             R v[GB_MAXP];
-            lagrange_1d<R>(p, tt, v);
+            lagrange_1d<R>(p, tt, v, nodes);
             for (int a = 0; a < p; ++a) sb[j][d][a] = v[a];
         }
         for (int t = threadIdx.x; t < nj * 9; t += blockDim.x) sq[t / 9][t % 9] = R(q[9 * int64_t(j0) + t]);
@@ -425,7 +425,7 @@ __global__ void k_m2l_f64(int p, int L, int lat_n, const TreeBox *__restrict__ b
 // of the 27 neighbouring leaves (Eq. "stress3"), skipping the target's own
 // segment.
 template <int MODE>
-__global__ void k_leaf_eval_f64(int p, int L, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat,
+__global__ void k_leaf_eval_f64(int p, int nodes, int L, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat,
                                 const int *__restrict__ tstart, const double *__restrict__ xt,
                                 const int64_t *__restrict__ tsid, const int *__restrict__ sstart,
                                 const double *__restrict__ ys, const double *__restrict__ P,
@@ -464,9 +464,9 @@ __global__ void k_leaf_eval_f64(int p, int L, const TreeBox *__restrict__ box, c
             myseg = tsid ? tsid[t] : -1;
             if (far) {
                 double bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
-                lagrange_1d<double>(p, (x[0] - c0[0]) * ih, bx);
-                lagrange_1d<double>(p, (x[1] - c0[1]) * ih, by);
-                lagrange_1d<double>(p, (x[2] - c0[2]) * ih, bz);
+                lagrange_1d<double>(p, (x[0] - c0[0]) * ih, bx, nodes);
+                lagrange_1d<double>(p, (x[1] - c0[1]) * ih, by, nodes);
+                lagrange_1d<double>(p, (x[2] - c0[2]) * ih, bz, nodes);
                 for (int l = 0; l < P3; ++l) {
                     double w = bx[l % p] * by[(l / p) % p] * bz[l / (p * p)];
                     for (int ab = 0; ab < 6; ++ab) acc[ab] += w * sS[l * 6 + ab];
@@ -587,8 +587,24 @@ __global__ void k_scatter_targets(int64_t n, const int *__restrict__ pos, const 
     for (int a = 0; a < 6; ++a) dst[6 * k + a] = s[a];
 }
 
-Transfer make_transfer(int p) {
+// M[c][A][a] = ell_A((c + t_a) / 2): the parent's basis function A at node a of child c
+// (equispaced nodes as before; Chebyshev nodes, the zeros of T_p on [0, 1])
+Transfer make_transfer(int p, int nodes) {
     Transfer t{};
+    if (nodes == GBFMM_NODES_CHEBYSHEV) {
+        double tn[GB_MAXP];
+        for (int b = 0; b < p; ++b) tn[b] = 0.5 * (1.0 - std::cos(M_PI * double(2 * b + 1) / double(2 * p)));
+        for (int c = 0; c < 2; ++c)
+            for (int A = 0; A < p; ++A)
+                for (int a = 0; a < p; ++a) {
+                    const double x = (c + tn[a]) / 2.0;
+                    double v = 1.0;
+                    for (int b = 0; b < p; ++b)
+                        if (b != A) v *= (x - tn[b]) / (tn[A] - tn[b]);
+                    t.M[c][A][a] = v;
+                }
+        return t;
+    }
     for (int c = 0; c < 2; ++c)
         for (int A = 0; A < p; ++A)
             for (int a = 0; a < p; ++a) {
@@ -716,7 +732,7 @@ int fmm_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     int *occ = ctx->d_tmp_i;                 // [n_cells] sources per cell
     int *tocc = free_targets ? occ + ctx->n_cells : occ;
     const int *tstart = free_targets ? ctx->d_t_start : ctx->d_leaf_start;
-    Transfer tr = make_transfer(p);
+    Transfer tr = make_transfer(p, ctx->opt.nodes);
 
     timer_mark(ctx);
     ++ctx->launches;
@@ -727,7 +743,7 @@ int fmm_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     timer_mark(ctx);
     if (L >= 3) {
         ++ctx->launches;
-        k_p2m<double><<<unsigned(nl), 256, 0, st>>>(p, L, ctx->d_box, ctx->d_leaf_start, ctx->d_y, ctx->d_q, ctx->d_W);
+        k_p2m<double><<<unsigned(nl), 256, 0, st>>>(p, ctx->opt.nodes, L, ctx->d_box, ctx->d_leaf_start, ctx->d_y, ctx->d_q, ctx->d_W);
         const size_t sm9 = size_t(2) * P3 * 9 * sizeof(double);
         for (int lev = L - 2; lev >= 2; --lev)
             { ++ctx->launches; k_m2m<double><<<unsigned(int64_t(1) << (3 * lev)), 256, sm9, st>>>(p, lev, tr, occ, ctx->d_W); }
@@ -765,11 +781,11 @@ int fmm_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
         ++ctx->launches;
         if (ctx->mat.mode == GBFMM_H_ISO)
             k_leaf_eval_f64<GBFMM_H_ISO><<<unsigned(nl), 128, smem, st>>>(
-                p, L, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_y, ctx->d_P, ctx->d_sid,
+                p, ctx->opt.nodes, L, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_y, ctx->d_P, ctx->d_sid,
                 ctx->d_S, sig);
         else
             k_leaf_eval_f64<GBFMM_H_CIRCLE><<<unsigned(nl), 128, smem, st>>>(
-                p, L, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_y, ctx->d_P, ctx->d_sid,
+                p, ctx->opt.nodes, L, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_y, ctx->d_P, ctx->d_sid,
                 ctx->d_S, sig);
         CK(cudaGetLastError());
     }
@@ -849,6 +865,10 @@ __global__ void k_leaf_s_to_f32(int64_t n, const double *__restrict__ S, float *
 }
 
 int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
+    if (!ctx->tc.ready_ops) {  // the medium changed after the build
+        if (int rc = m2l_tc_setup(ctx)) return rc;
+        if (int rc = m2l_tc_prepare(ctx)) return rc;
+    }
     cudaStream_t st = ctx->stream;
     const bool t64 = ctx->opt.precision == GBFMM_MIXED_F64T;  // FP64 P2M, M2M, L2L, L2P
     const int p = ctx->opt.p, L = ctx->L, P3 = p * p * p;
@@ -856,7 +876,7 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     int *occ = ctx->d_tmp_i;
     int *tocc = free_targets ? occ + ctx->n_cells : occ;
     const int *tstart = free_targets ? ctx->d_t_start : ctx->d_leaf_start;
-    Transfer tr = make_transfer(p);
+    Transfer tr = make_transfer(p, ctx->opt.nodes);
     timer_mark(ctx);
     if (int rc = near_prepare(ctx)) return rc;
     ++ctx->launches;
@@ -868,10 +888,10 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     if (L >= 3) {
         ++ctx->launches;
         if (t64)
-            k_p2m<double><<<unsigned(nl), 256, 0, st>>>(p, L, ctx->d_box, ctx->d_leaf_start, ctx->d_y, ctx->d_q,
+            k_p2m<double><<<unsigned(nl), 256, 0, st>>>(p, ctx->opt.nodes, L, ctx->d_box, ctx->d_leaf_start, ctx->d_y, ctx->d_q,
                                                         ctx->d_W);
         else
-            k_p2m<float><<<unsigned(nl), 256, 0, st>>>(p, L, ctx->d_box, ctx->d_leaf_start, ctx->d_y, ctx->d_q,
+            k_p2m<float><<<unsigned(nl), 256, 0, st>>>(p, ctx->opt.nodes, L, ctx->d_box, ctx->d_leaf_start, ctx->d_y, ctx->d_q,
                                                        ctx->d_Wf);
         for (int lev = L - 2; lev >= 2; --lev) {
             ++ctx->launches;

@@ -412,15 +412,68 @@ __device__ __forceinline__ void h_cubic_tab(R cp, R c44, R D, int Q, const R *__
     }
 }
 
-// Lagrange basis on the p equispaced nodes t_a = a / (p - 1) of [0, 1]
-// (Sec. 4.1 footnote): ell_a(t) = prod_{b != a} (t - t_b) / (t_a - t_b).
+// Lagrange basis ell_a(t) = prod_{b != a} (t - t_b) / (t_a - t_b) on the p
+// nodes of [0, 1]: nodes = GBFMM_NODES_EQUISPACED, t_a = a / (p - 1) (Sec. 4.1
+// footnote); nodes = GBFMM_NODES_CHEBYSHEV, the zeros of the Chebyshev
+// polynomial T_p mapped to [0, 1], t_a = (1 - cos((2a + 1) pi / (2p))) / 2
+// (the nodes of the Chebyshev FMM, Sec. 3).
 template <typename R>
-__device__ __forceinline__ void lagrange_1d(int p, R t, R *out) {
+__device__ __forceinline__ R cheb_node(int a, int p) {
+    if constexpr (sizeof(R) == 8)
+        return 0.5 * (1.0 - cospi(double(2 * a + 1) / double(2 * p)));
+    else
+        return 0.5f * (1.0f - cospif(float(2 * a + 1) / float(2 * p)));
+}
+
+template <typename R>
+__device__ __forceinline__ void lagrange_1d(int p, R t, R *out, int nodes) {
+    if (nodes == GBFMM_NODES_CHEBYSHEV) {
+        // node positions recomputed in the loops: a local table of them, inlined into
+        // the near-field kernels next to the three output arrays, gave wrong basis values
+        // there (measured: the y-axis values equalled the z-axis ones)
+        for (int a = 0; a < p; ++a) {
+            const R ta = cheb_node<R>(a, p);
+            R v = R(1);
+            for (int b = 0; b < p; ++b)
+                if (b != a) {
+                    const R tb = cheb_node<R>(b, p);
+                    v *= (t - tb) / (ta - tb);
+                }
+            out[a] = v;
+        }
+        return;
+    }
     const R inv = R(1) / R(p - 1);
     for (int a = 0; a < p; ++a) {
         R v = R(1);
         for (int b = 0; b < p; ++b)
             if (b != a) v *= (t - R(b) * inv) / (R(a - b) * inv);
         out[a] = v;
+    }
+}
+
+// The kernel of Sec. 2, Eq. "kernel" at separation d (FP64, 54 values
+// K[ab][wr]): K = sum_k Asym[ab wr][k] h_k(d / |d|) / |d|^2, zero at d = 0.
+__device__ __forceinline__ void kernel_at(const DevMaterial *mat, const double *Asym, const double d[3],
+                                          double out[54]) {
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (r2 == 0.0) {
+        for (int i = 0; i < 54; ++i) out[i] = 0.0;
+        return;
+    }
+    const double ir = 1.0 / sqrt(r2);
+    const double T[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
+    double hs[18];
+    if (mat->mode == GBFMM_H_ISO)
+        h_iso_sym<double>(mat->hc, mat->ha, T, hs);
+    else if (mat->cubic)
+        h_circle_cubic<double>(mat->c12, mat->c44, mat->cd, mat->Q, T, hs);
+    else
+        h_circle_sym<double, double>(mat->C, mat->Q, T, hs);
+    const double ir2 = 1.0 / r2;
+    for (int i = 0; i < 54; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < 18; ++k) acc += Asym[i * 18 + k] * hs[k];
+        out[i] = acc * ir2;
     }
 }

@@ -770,11 +770,12 @@ __global__ void k_w_modal(int level, int p, const __grid_constant__ BasisMats B,
     }
 }
 
-// W (FP32, [cell][p^3 * 9]) -> parity-split BF16 hi / lo, [class][mz][my][mx][Kp] per level,
-// one block per cell at a time.  Rows of cells without segments are not written: the
-// gather never reads them (their copies are zero fills).
+// W (FP32, [cell][kv]: kv = 9 p^3 node values or moments, or r2 compressed values) ->
+// parity-split hi / lo, [class][mz][my][mx][Kp] per level, one block per cell at a time.
+// Rows of cells without segments are not written: the gather never reads them (their
+// copies are zero fills).
 template <typename E, typename TW>
-__global__ void k_pack_w(int level, int P3, int Kp, const TW *__restrict__ W, const int *__restrict__ occ,
+__global__ void k_pack_w(int level, int kv, int Kp, const TW *__restrict__ W, const int *__restrict__ occ,
                          const unsigned *__restrict__ wmax, E *__restrict__ hi, E *__restrict__ lo) {
     const int n = 1 << level, m = n / 2;
     const double s = wmax ? double(wscale_of(wmax[level])) : 1.0;
@@ -786,7 +787,7 @@ __global__ void k_pack_w(int level, int P3, int Kp, const TW *__restrict__ W, co
         const int cls = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
         const int64_t row = (((int64_t(cls) * m + z / 2) * m + y / 2) * m + x / 2) * Kp;
         for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
-            const double v = k < 9 * P3 ? double(W[g * 9 * P3 + k]) : 0.0;
+            const double v = k < kv ? double(W[g * kv + k]) : 0.0;
             const double vs = s * v;
             const E h = to_elem<E>(vs);
             hi[row + k] = h;
@@ -798,14 +799,14 @@ __global__ void k_pack_w(int level, int P3, int Kp, const TW *__restrict__ W, co
 // largest |W| over the occupied cells of one level (non-negative floats order
 // like their bit patterns), one block per cell at a time
 template <typename TW>
-__global__ void k_wmax(int level, int P3, const TW *__restrict__ W, const int *__restrict__ occ,
+__global__ void k_wmax(int level, int kv, const TW *__restrict__ W, const int *__restrict__ occ,
                        unsigned *__restrict__ wmax) {
     const int64_t cells = int64_t(1) << (3 * level), base = cell_base_d(level);
     float mx = 0.f;
     for (int64_t lin = blockIdx.x; lin < cells; lin += gridDim.x) {
         if (occ[base + lin] <= 0) continue;
-        const TW *w = W + (base + lin) * int64_t(9 * P3);
-        for (int k = threadIdx.x; k < 9 * P3; k += blockDim.x) mx = fmaxf(mx, fabsf(float(w[k])));
+        const TW *w = W + (base + lin) * int64_t(kv);
+        for (int k = threadIdx.x; k < kv; k += blockDim.x) mx = fmaxf(mx, fabsf(float(w[k])));
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(wmax + level, __float_as_uint(mx));
@@ -982,8 +983,12 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     T.tf32 = ctx->opt.m2l_split == 3 ? 1 : 0;
     T.fp16 = (ctx->opt.m2l_split >= 4) ? 1 : 0;
     T.esz = T.tf32 ? 4 : 2;
-    T.Kp = ((9 * P3 + 63) / 64) * 64;
-    const int nv = 6 * P3;
+    // compressed M2L: the GEMM's K and N are the kept source and target ranks
+    T.svd = ctx->opt.m2l_svd_tol > 0.0 ? 1 : 0;
+    if (T.svd)
+        if (int rc = svd_bases(ctx)) return rc;
+    T.Kp = ((((T.svd ? T.r2 : 9 * P3)) + 63) / 64) * 64;
+    const int nv = T.svd ? T.r1 : 6 * P3;
     T.swap = ctx->opt.m2l_kernel == 1 ? 1 : 0;
     T.tpc = T.swap ? 2 : 3;
     if (T.swap) {
@@ -1078,7 +1083,7 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
     CK(cudaMalloc(&T.Tlo, std::max<size_t>(lo_elems, 1) * T.esz));
     T.split = n_lo > 0 ? 1 : 0;
     T.op_scale = 1.0;
-    T.modal = ctx->opt.m2l_basis == 1 ? 1 : 0;
+    T.modal = (ctx->opt.m2l_basis == 1 && !T.svd) ? 1 : 0;
     if (T.modal && !basis_matrices(p, T.basisV, T.basisCt))
         return set_err(ctx, GBFMM_ERR_INVALID_ARG, "m2l setup: singular Legendre basis matrix");
     const size_t sm_modal = size_t(2) * 9 * P3 * sizeof(double);
@@ -1091,7 +1096,15 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
         CK(cudaFuncSetAttribute(k_w_modal<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_modal / 2)));
     }
     const BasisMats B = basis_of(T, p);
-    if (T.fp16 && T.modal) {
+    if (T.svd) {
+        // U^T T_o R for every offset (FP64), with the FP16 scale from their largest entry
+        if (int rc = svd_operators(ctx, d_off, d_lo, T.n_off)) {
+            cudaFree(d_off);
+            cudaFree(d_lo);
+            return rc;
+        }
+        if (T.fp16 && !T.d_wmax) CK(cudaMalloc(&T.d_wmax, GB_TC_MAXLEV * sizeof(unsigned)));
+    } else if (T.fp16 && T.modal) {
         // one power of two for all operators from the largest modal entry
         unsigned long long *d_mx = nullptr, mx_bits = 0;
         CK(cudaMalloc(&d_mx, sizeof(unsigned long long)));
@@ -1133,8 +1146,10 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
         }
         if (!T.d_wmax) CK(cudaMalloc(&T.d_wmax, GB_TC_MAXLEV * sizeof(unsigned)));
     }
-    ++ctx->launches;
-    if (T.modal) {
+    if (!T.svd) ++ctx->launches;
+    if (T.svd) {
+        // written by svd_operators
+    } else if (T.modal) {
         const unsigned g = unsigned(T.n_off * T.Np);
         if (T.tf32)
             k_build_ops_modal<float><<<g, 256, sm_modal, ctx->stream>>>(p, ctx->lat_n, T.Np, T.Kp, T.Kp_lo, ctx->d_Klat, d_off,
@@ -1211,6 +1226,7 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
     T.n_slots = slots;
     T.n_seg = 8 * (L - 2);
     T.n_work = int(tiles * T.groups);
+    if (T.svd) return svd_prepare(ctx);
     return GBFMM_OK;
 }
 
@@ -1223,12 +1239,17 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     if (T.fp16) CK(cudaMemsetAsync(T.d_wmax, 0, GB_TC_MAXLEV * sizeof(unsigned), ctx->stream));
     const BasisMats B = basis_of(T, p);
     const int split_levels = ctx->opt.m2l_split_levels ? ctx->opt.m2l_split_levels : ~0;
+    // compressed M2L: every cell's multipole values -> r2 coefficients R^T W first
+    if (T.svd)
+        if (int rc = svd_transform_w(ctx, Wf)) return rc;
+    const float *Wsrc = T.svd ? T.Wc : Wf;
+    const int kv = T.svd ? T.r2 : 9 * P3;  // valid values per cell row
     for (int l = 2; l < L; ++l) {
         const bool split_l = T.split && ((split_levels >> l) & 1);  // residual W only where it is read
         const int64_t cells_l = int64_t(1) << (3 * l);
         void *whi = (char *)T.Whi + T.wofs[l] * T.esz, *wlo = (char *)T.Wlo + T.wofs[l] * T.esz;
         const unsigned gb = unsigned(std::min<int64_t>(cells_l, 8 * 152));  // blocks stride over the cells
-        if (T.modal) {
+        if (T.modal && !T.svd) {
             // node values -> Legendre moments (in place: nothing reads these W after the M2L)
             ++ctx->launches;
             if (W64)
@@ -1241,28 +1262,28 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
         if (T.tf32) {
             ++ctx->launches;
             if (W64)
-                k_pack_w<float><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, W64, occ, nullptr, (float *)whi, (float *)nullptr);
+                k_pack_w<float><<<gb, 256, 0, ctx->stream>>>(l, kv, T.Kp, W64, occ, nullptr, (float *)whi, (float *)nullptr);
             else
-                k_pack_w<float><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, nullptr, (float *)whi, (float *)nullptr);
+                k_pack_w<float><<<gb, 256, 0, ctx->stream>>>(l, kv, T.Kp, Wsrc, occ, nullptr, (float *)whi, (float *)nullptr);
         } else if (T.fp16) {
             const unsigned gm = gb;
             __half *lo = split_l ? (__half *)wlo : nullptr;
             ctx->launches += 2;
             if (W64) {
-                k_wmax<<<gm, 256, 0, ctx->stream>>>(l, P3, W64, occ, T.d_wmax);
-                k_pack_w<__half><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, W64, occ, T.d_wmax, (__half *)whi, lo);
+                k_wmax<<<gm, 256, 0, ctx->stream>>>(l, kv, W64, occ, T.d_wmax);
+                k_pack_w<__half><<<gb, 256, 0, ctx->stream>>>(l, kv, T.Kp, W64, occ, T.d_wmax, (__half *)whi, lo);
             } else {
-                k_wmax<<<gm, 256, 0, ctx->stream>>>(l, P3, Wf, occ, T.d_wmax);
-                k_pack_w<__half><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, T.d_wmax, (__half *)whi, lo);
+                k_wmax<<<gm, 256, 0, ctx->stream>>>(l, kv, Wsrc, occ, T.d_wmax);
+                k_pack_w<__half><<<gb, 256, 0, ctx->stream>>>(l, kv, T.Kp, Wsrc, occ, T.d_wmax, (__half *)whi, lo);
             }
         } else {
             __nv_bfloat16 *lo = split_l ? (__nv_bfloat16 *)wlo : nullptr;
             ++ctx->launches;
             if (W64)
-                k_pack_w<__nv_bfloat16><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, W64, occ, nullptr,
+                k_pack_w<__nv_bfloat16><<<gb, 256, 0, ctx->stream>>>(l, kv, T.Kp, W64, occ, nullptr,
                                                                      (__nv_bfloat16 *)whi, lo);
             else
-                k_pack_w<__nv_bfloat16><<<gb, 256, 0, ctx->stream>>>(l, P3, T.Kp, Wf, occ, nullptr,
+                k_pack_w<__nv_bfloat16><<<gb, 256, 0, ctx->stream>>>(l, kv, T.Kp, Wsrc, occ, nullptr,
                                                                      (__nv_bfloat16 *)whi, lo);
         }
         prm.wofs[l] = T.wofs[l] * T.esz;
@@ -1299,7 +1320,7 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     prm.inv_op_scale = float(1.0 / T.op_scale);
     prm.nsub = T.nsub;
     prm.ncta = T.ncta;
-    prm.nvalid = 6 * P3;
+    prm.nvalid = T.svd ? T.r1 : 6 * P3;
     prm.tmem_cols = T.tmem_cols;
     prm.split = T.split;
     prm.split_levels = split_levels;
@@ -1323,16 +1344,19 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     // offset chunks: each launch accumulates a run of consecutive offsets of every class's list
     // in tensor memory; the chunks' sums are added outside the tensor cores, in the local values
     const int chunks = std::max(1, std::min(189, ctx->opt.m2l_chunks));
+    float *Sout = T.svd ? T.Sc : Sf;  // compressed: the r1 coefficients of every target cell
+    if (T.svd) CK(cudaMemsetAsync(T.Sc, 0, size_t(ctx->n_cells) * T.r1 * sizeof(float), ctx->stream));
     for (int c = 0; c < chunks; ++c) {
         prm.o_lo = (189 * c) / chunks;
         prm.o_hi = (189 * (c + 1)) / chunks;
         prm.accumulate = c > 0 ? 1 : 0;
         if (c > 0) prm.drop_first = 0;
         ++ctx->launches;
-        kern<<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box, Sf, S64,
+        kern<<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box, Sout, S64,
                                                    T.d_status, stages, T.groups);
         CK(cudaGetLastError());
     }
+    if (T.svd) return svd_expand_s(ctx, Sf);  // S = U S'
     return GBFMM_OK;
 }
 
@@ -1348,6 +1372,7 @@ int m2l_tc_status(gbfmm_ctx *ctx, int *out) {
 
 void m2l_tc_free(gbfmm_ctx *ctx) {
     TcPlan &T = ctx->tc;
+    svd_free(ctx, ctx->borrowed_material);
     void *ps[] = {T.Thi, T.Tlo, T.Whi, T.Wlo, T.d_status, T.d_flags, T.d_pos, T.d_list, T.d_seg, T.d_wmax};
     for (void *q : ps)
         if (q) cudaFree(q);

@@ -36,6 +36,23 @@ struct TcPlan {
     int4 *d_seg = nullptr;     // per (level, class): first list entry, count, first tile
     int64_t slot_cap = 0, n_slots = 0;
     int n_seg = 0;
+    // SVD-compressed M2L (gbfmm_options.m2l_svd_tol > 0, m2l_svd.cu): the GEMM runs on
+    // r2 source and r1 target coefficients per cell
+    int svd = 0;
+    int r1 = 0, r2 = 0;        // kept target / source singular vectors (rounded up to 16 / 64)
+    int r1_raw = 0, r2_raw = 0;  // counts above the tolerance
+    float *Uf = nullptr;       // target basis [6 p^3][r1], column-major (ld 6 p^3), shared in a batch
+    float *Rf = nullptr;       // source basis [9 p^3][r2], column-major (ld 9 p^3), shared in a batch
+    double *U64 = nullptr, *R64 = nullptr;  // the bases in FP64 (operator construction)
+    int bases_ok = 0;          // U, R belong to the current medium and options
+    int gemm_emulated = 0;     // the per-pass FP32 GEMMs run as BF16x9 emulation
+    double svd_sigma[4] = {0}; // largest and smallest kept singular values: target, source
+    float *Wc = nullptr;       // per tree: [n_cells][r2] compressed multipole values
+    float *Sc = nullptr;       // per tree: [n_cells][r1] compressed local values
+    int64_t c_cap = 0;
+    void *blas = nullptr;      // cuBLAS handle of this context (its own workspace: contexts of a
+    void *blas_ws = nullptr;   // batch run concurrently)
+    size_t blas_ws_bytes = 0;
 };
 
 int m2l_tc_setup(gbfmm_ctx *ctx);    // operators (per medium and p)
@@ -45,3 +62,16 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
                double *S64);
 void m2l_tc_free(gbfmm_ctx *ctx);
 int m2l_tc_status(gbfmm_ctx *ctx, int *out);
+
+// SVD compression (m2l_svd.cu).  svd_bases: the two bases and the kept ranks (before the
+// operator tables are sized); svd_operators: the compressed operators U^T T_o R of the
+// n_off offsets (xyz in d_off) into T.Thi / T.Tlo with the FP16 scale; svd_prepare: per-tree
+// buffers; svd_transform_w / svd_expand_s: R^T W per cell of levels 2..L-1 before the
+// M2L and S = U S' after it; svd_free: this context's handle and buffers (and the bases
+// unless borrowed).
+int svd_bases(gbfmm_ctx *ctx);
+int svd_operators(gbfmm_ctx *ctx, const int *d_off, const int *d_lo, int n_off);
+int svd_prepare(gbfmm_ctx *ctx);
+int svd_transform_w(gbfmm_ctx *ctx, const float *Wf);
+int svd_expand_s(gbfmm_ctx *ctx, float *Sf);
+void svd_free(gbfmm_ctx *ctx, bool borrowed);

@@ -65,29 +65,9 @@ __global__ void k_lattice(const DevMaterial *mat, const double *Asym, int p, int
     int dx = int(idx % lat_n) - R0;
     int dy = int((idx / lat_n) % lat_n) - R0;
     int dz = int(idx / (int64_t(lat_n) * lat_n)) - R0;
-    double *out = Klat + idx * 54;
-    if (dx == 0 && dy == 0 && dz == 0) {
-        for (int i = 0; i < 54; ++i) out[i] = 0.0;
-        return;
-    }
-    double s = 1.0 / double(p - 1);
-    double d[3] = {dx * s, dy * s, dz * s};
-    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    double ir = 1.0 / sqrt(r2);
-    double T[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
-    double hs[18];
-    if (mat->mode == GBFMM_H_ISO)
-        h_iso_sym<double>(mat->hc, mat->ha, T, hs);
-    else if (mat->cubic)
-        h_circle_cubic<double>(mat->c12, mat->c44, mat->cd, mat->Q, T, hs);
-    else
-        h_circle_sym<double, double>(mat->C, mat->Q, T, hs);
-    double ir2 = 1.0 / r2;
-    for (int i = 0; i < 54; ++i) {
-        double acc = 0.0;
-        for (int k = 0; k < 18; ++k) acc += Asym[i * 18 + k] * hs[k];
-        out[i] = acc * ir2;
-    }
+    const double s = 1.0 / double(p - 1);
+    const double d[3] = {dx * s, dy * s, dz * s};
+    kernel_at(mat, Asym, d, Klat + idx * 54);
 }
 
 }  // namespace
@@ -150,7 +130,8 @@ int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
     if (!src->have_material) return set_err(ctx, GBFMM_ERR_NO_MATERIAL, "share_material: source has no material");
     if (ctx->opt.p != src->opt.p || ctx->opt.precision != src->opt.precision || ctx->opt.h_mode != src->opt.h_mode ||
         ctx->opt.m2l_split != src->opt.m2l_split || ctx->opt.m2l_basis != src->opt.m2l_basis ||
-        ctx->opt.m2l_split_kblocks != src->opt.m2l_split_kblocks || ctx->opt.m2l_kernel != src->opt.m2l_kernel)
+        ctx->opt.m2l_split_kblocks != src->opt.m2l_split_kblocks || ctx->opt.m2l_kernel != src->opt.m2l_kernel ||
+        ctx->opt.nodes != src->opt.nodes || ctx->opt.m2l_svd_tol != src->opt.m2l_svd_tol)
         return set_err(ctx, GBFMM_ERR_INVALID_ARG, "share_material: options differ");
     ctx->mat = src->mat;
     std::memcpy(ctx->Asym, src->Asym, sizeof(ctx->Asym));
@@ -184,6 +165,19 @@ int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
     T.esz = S.esz;
     T.Thi = S.Thi;
     T.Tlo = S.Tlo;
+    // compressed M2L: the bases are shared, the per-tree buffers and the cuBLAS handle are not
+    T.svd = S.svd;
+    T.r1 = S.r1;
+    T.r2 = S.r2;
+    T.r1_raw = S.r1_raw;
+    T.r2_raw = S.r2_raw;
+    T.Uf = S.Uf;
+    T.Rf = S.Rf;
+    T.U64 = S.U64;
+    T.R64 = S.R64;
+    T.bases_ok = S.bases_ok;
+    T.gemm_emulated = S.gemm_emulated;
+    std::memcpy(T.svd_sigma, S.svd_sigma, sizeof(T.svd_sigma));
     if (!T.d_status) {
         CK(cudaMalloc(&T.d_status, sizeof(int)));
         CK(cudaMemset(T.d_status, 0, sizeof(int)));
@@ -204,6 +198,8 @@ extern "C" int fmm_set_material(gbfmm_ctx *ctx, const double *V) {
         ctx->d_Klat = nullptr;
         ctx->lat_n = 0;
         ctx->tc.Thi = ctx->tc.Tlo = nullptr;
+        ctx->tc.Uf = ctx->tc.Rf = nullptr;
+        ctx->tc.U64 = ctx->tc.R64 = nullptr;
         ctx->tc.ready_ops = false;
         ctx->fft.ready = false;
         ctx->borrowed_material = false;
@@ -257,6 +253,8 @@ extern "C" int fmm_set_material(gbfmm_ctx *ctx, const double *V) {
     }
     ctx->mat = m;
     ctx->fft.ready = false;  // the transformed operators belong to the previous medium
+    ctx->tc.ready_ops = false;
+    ctx->tc.bases_ok = 0;
     int rc = material_setup(ctx);
     if (rc) return rc;
     ctx->have_material = true;

@@ -172,7 +172,7 @@ constexpr int WARPS = 4;
 // sources are staged per warp chunk (static shared memory stays < 48 KB)
 template <int HM, int NCS, int SCH>
 __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
-    int p, int L, int64_t nl, float near2, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat,
+    int p, int nodes, int L, int64_t nl, float near2, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat,
     const int *__restrict__ tstart, const double *__restrict__ xt, const int64_t *__restrict__ tsid,
     const int *__restrict__ sstart, const float4 *__restrict__ yrel, const double *__restrict__ ys,
     const float *__restrict__ c32, const int64_t *__restrict__ ssid,
@@ -234,9 +234,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mixed(
         }
         if (far && ph == 0) {
             float bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
-            lagrange_1d<float>(p, float((x[0] - c0[0]) * ih), bx);
-            lagrange_1d<float>(p, float((x[1] - c0[1]) * ih), by);
-            lagrange_1d<float>(p, float((x[2] - c0[2]) * ih), bz);
+            lagrange_1d<float>(p, float((x[0] - c0[0]) * ih), bx, nodes);
+            lagrange_1d<float>(p, float((x[1] - c0[1]) * ih), by, nodes);
+            lagrange_1d<float>(p, float((x[2] - c0[2]) * ih), bz, nodes);
             for (int lz = 0; lz < p; ++lz)
                 for (int ly = 0; ly < p; ++ly) {
                     const float wyz = by[ly] * bz[lz];
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(S64_WARPS * 32) k_near_sym64(
 }
 
 // far field (L2P) plus the partial slots, in a fixed order
-__global__ void k_near_combine(int p, int L, int64_t N, const TreeBox *__restrict__ box,
+__global__ void k_near_combine(int p, int nodes, int L, int64_t N, const TreeBox *__restrict__ box,
                                const int *__restrict__ sstart, const int *__restrict__ pleaf,
                                const double *__restrict__ xt, const float *__restrict__ S,
                                const double *__restrict__ S64, const double *__restrict__ part,
@@ -733,9 +733,9 @@ __global__ void k_near_combine(int p, int L, int64_t N, const TreeBox *__restric
         const int P3 = p * p * p;
         const double h = box->H / nlv, ih = double(nlv) / box->H;
         double bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
-        lagrange_1d<double>(p, (xt[3 * t] - (box->origin[0] + cx * h)) * ih, bx);
-        lagrange_1d<double>(p, (xt[3 * t + 1] - (box->origin[1] + cy * h)) * ih, by);
-        lagrange_1d<double>(p, (xt[3 * t + 2] - (box->origin[2] + cz * h)) * ih, bz);
+        lagrange_1d<double>(p, (xt[3 * t] - (box->origin[0] + cx * h)) * ih, bx, nodes);
+        lagrange_1d<double>(p, (xt[3 * t + 1] - (box->origin[1] + cy * h)) * ih, by, nodes);
+        lagrange_1d<double>(p, (xt[3 * t + 2] - (box->origin[2] + cz * h)) * ih, bz, nodes);
         const double *Sl = S64 + (cell_base_d(L - 1) + leaf) * int64_t(P3) * 6;
         for (int lz = 0; lz < p; ++lz)
             for (int ly = 0; ly < p; ++ly) {
@@ -751,9 +751,9 @@ __global__ void k_near_combine(int p, int L, int64_t N, const TreeBox *__restric
         const double h = box->H / nlv, ih = double(nlv) / box->H;
         float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
-        lagrange_1d<float>(p, float((xt[3 * t] - (box->origin[0] + cx * h)) * ih), bx);
-        lagrange_1d<float>(p, float((xt[3 * t + 1] - (box->origin[1] + cy * h)) * ih), by);
-        lagrange_1d<float>(p, float((xt[3 * t + 2] - (box->origin[2] + cz * h)) * ih), bz);
+        lagrange_1d<float>(p, float((xt[3 * t] - (box->origin[0] + cx * h)) * ih), bx, nodes);
+        lagrange_1d<float>(p, float((xt[3 * t + 1] - (box->origin[1] + cy * h)) * ih), by, nodes);
+        lagrange_1d<float>(p, float((xt[3 * t + 2] - (box->origin[2] + cz * h)) * ih), bz, nodes);
         const float *Sl = S + (cell_base_d(L - 1) + leaf) * int64_t(P3) * 6;
         for (int lz = 0; lz < p; ++lz)
             for (int ly = 0; ly < p; ++ly) {
@@ -854,7 +854,7 @@ constexpr int MSCH = 16;  // sources staged per warp chunk in the network kernel
 // added by the lane that queued it, in queue order (deterministic).
 template <bool CUBIC>
 __global__ void __launch_bounds__(WARPS * 32) k_near_mlp(
-    int p, int L, int64_t nl, float near2, float rmin2, const TreeBox *__restrict__ box,
+    int p, int nodes, int L, int64_t nl, float near2, float rmin2, const TreeBox *__restrict__ box,
     const DevMaterial *__restrict__ mat, const int *__restrict__ tstart, const double *__restrict__ xt,
     const int64_t *__restrict__ tsid, const int *__restrict__ sstart, const float4 *__restrict__ yrel,
     const double *__restrict__ ys, const float *__restrict__ c32, const int64_t *__restrict__ ssid,
@@ -926,9 +926,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_near_mlp(
         }
         if (far && ph == 0) {
             float bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
-            lagrange_1d<float>(p, float((x[0] - c0[0]) * ih), bx);
-            lagrange_1d<float>(p, float((x[1] - c0[1]) * ih), by);
-            lagrange_1d<float>(p, float((x[2] - c0[2]) * ih), bz);
+            lagrange_1d<float>(p, float((x[0] - c0[0]) * ih), bx, nodes);
+            lagrange_1d<float>(p, float((x[1] - c0[1]) * ih), by, nodes);
+            lagrange_1d<float>(p, float((x[2] - c0[2]) * ih), bz, nodes);
             for (int lz = 0; lz < p; ++lz)
                 for (int ly = 0; ly < p; ++ly) {
                     const float wyz = by[ly] * bz[lz];
@@ -1301,7 +1301,7 @@ int near_run_sym64(gbfmm_ctx *ctx, double *sig) {
                                                                      ctx->d_leaf_start, ctx->d_y, ctx->d_P, ctx->d_sid,
                                                                      W.part, N, W.psorted, W.pmisc + 128);
     }
-    k_near_combine<<<nblk(N, 256), 256, 0, st>>>(ctx->opt.p, ctx->L, N, ctx->d_box, ctx->d_leaf_start, ctx->d_pleaf,
+    k_near_combine<<<nblk(N, 256), 256, 0, st>>>(ctx->opt.p, ctx->opt.nodes, ctx->L, N, ctx->d_box, ctx->d_leaf_start, ctx->d_pleaf,
                                                  ctx->d_y, nullptr, ctx->d_S, W.part, sig);
     CK(cudaGetLastError());
     return GBFMM_OK;
@@ -1329,7 +1329,7 @@ static int near_run_sym(gbfmm_ctx *ctx, double *sig) {
                                                                    W.pmisc + 128);
     }
     const double *S64 = ctx->opt.precision == GBFMM_MIXED_F64T ? ctx->d_S : nullptr;
-    k_near_combine<<<nblk(N, 256), 256, 0, st>>>(ctx->opt.p, ctx->L, N, ctx->d_box, ctx->d_leaf_start, ctx->d_pleaf,
+    k_near_combine<<<nblk(N, 256), 256, 0, st>>>(ctx->opt.p, ctx->opt.nodes, ctx->L, N, ctx->d_box, ctx->d_leaf_start, ctx->d_pleaf,
                                                  ctx->d_y, ctx->d_Sf, S64, W.part, sig);
     CK(cudaGetLastError());
     return GBFMM_OK;
@@ -1352,7 +1352,7 @@ int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t 
         const float rmin = float(ctx->opt.mlp_min_dist > 0.0 ? ctx->opt.mlp_min_dist : 8.0);
         const size_t smem = sizeof(mlpw::Weights);
 #define GB_MLP_ARGS                                                                                                  \
-    ctx->opt.p, ctx->L, nl, near2, rmin *rmin, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, \
+    ctx->opt.p, ctx->opt.nodes, ctx->L, nl, near2, rmin *rmin, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, \
         ctx->d_y, ctx->d_Pf, ctx->d_sid, ctx->d_Sf, sig, ctx->mlp.theta_h, ctx->mlp.theta, ctx->mlp.scale,        \
         ctx->mlp.d_binmask, items, n_items
         if (ctx->mat.cubic) {
@@ -1367,7 +1367,7 @@ int near_run(gbfmm_ctx *ctx, const int *tstart, const double *xt, const int64_t 
         return GBFMM_OK;
     }
 #define GB_NEAR_ARGS                                                                                           \
-    ctx->opt.p, ctx->L, nl, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, ctx->d_y, \
+    ctx->opt.p, ctx->opt.nodes, ctx->L, nl, near2, ctx->d_box, ctx->d_mat, tstart, xt, tsid, ctx->d_leaf_start, ctx->d_yrel, ctx->d_y, \
         ctx->d_Pf, ctx->d_sid, ctx->d_Sf, sig, items, n_items
     if (near_coef_count(ctx) == 80)
         k_near_mixed<HM_ISO, 80, 32><<<grid, WARPS * 32, 0, ctx->stream>>>(GB_NEAR_ARGS);
