@@ -129,24 +129,27 @@ WORKLOADS["c2"] = dict(
          "order p=5, 5-level octree, unit-circle h Q=32",
     gen=lambda seed: synth.polygon_loops(seed=1 + 1000 * seed), C=lambda: synth.cubic_voigt(),
     h_mode="circle", circle_q=32, p=5, levels=5, precision="fp64")
+# The compressed M2L of the headline: Chebyshev nodes, singular vectors kept above 5e-5 of
+# the largest (the paper's Chebyshev FMM), FP16 operands with residual passes on the
+# leading block of 64 singular directions, offsets summed in 7 runs.
+CHEB_M2L = dict(nodes="chebyshev", m2l_svd_tol=5e-5, m2l_split=6, m2l_chunks=7, m2l_split_kblocks=1)
 WORKLOADS["c3"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs, sigma 0.02), cubic C11=1.684 C12=1.214 "
-         "C44=0.754, order p=7, 7-level octree, mixed precision (tensor-core M2L on FP16 Legendre moments with "
-         "residual passes on the low-order moments, FP32 near field with FP64 separations for close pairs), "
-         "unit-circle h (cubic form, Q=16 points on the half circle); the same step through the plain FP64 pass "
-         "is timed in the same run",
+         "C44=0.754, order p=7 on Chebyshev nodes, 7-level octree, mixed precision (SVD-compressed M2L on the "
+         "tensor cores: FP16 operands, residual passes on the leading singular directions; FP32 near field with "
+         "FP64 separations for close pairs), unit-circle h (cubic form, Q=16 points on the half circle); the same "
+         "step through the plain FP64 pass is timed in the same run",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
-    h_mode="circle", circle_q=16, p=7, levels=7, precision="mixed", fp64_arm=True, **MIXED_M2L)
+    h_mode="circle", circle_q=16, p=7, levels=7, precision="mixed", fp64_arm=True, **CHEB_M2L)
+WORKLOADS["c3legendre"] = dict(
+    desc="c3 on equispaced nodes with the dense M2L (every one of the 54 p^6 products per cell pair, on FP16 "
+         "Legendre moments of the source cells with residual passes on the low-order moments)",
+    gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=16, p=7, levels=7,
+    precision="mixed", **MIXED_M2L)
 WORKLOADS["c3svd"] = dict(
-    desc="c3 (1,000,000 slab segments, cubic, p=7, 7 levels, Q=16) with the SVD-compressed M2L (the Chebyshev "
-         "FMM's compression on the equispaced nodes: singular vectors kept above 1e-6 of the largest)",
+    desc="c3 on equispaced nodes with the SVD-compressed M2L (singular vectors kept above 1e-5 of the largest)",
     gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=16, p=7, levels=7,
-    precision="mixed", m2l_svd_tol=1e-6, m2l_split=6, m2l_chunks=7, m2l_split_kblocks=1)
-WORKLOADS["c3cheb"] = dict(
-    desc="c3 on Chebyshev nodes with the SVD-compressed M2L (the paper's Chebyshev FMM), singular vectors kept "
-         "above 1e-6 of the largest",
-    gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=16, p=7, levels=7,
-    precision="mixed", nodes="chebyshev", m2l_svd_tol=1e-6, m2l_split=6, m2l_chunks=7, m2l_split_kblocks=1)
+    precision="mixed", m2l_svd_tol=1e-5, m2l_split=6, m2l_chunks=7, m2l_split_kblocks=1)
 WORKLOADS["c3_iso"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs), isotropic mu=1 nu=0.3, p=7, mixed precision",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.isotropic_voigt(1.0, 0.3),
@@ -172,10 +175,10 @@ WORKLOADS["c3q_iso_fp64"] = dict(
     precision="fp64")
 WORKLOADS["c5"] = dict(
     desc="64 independent cubic networks, N_s log-uniform in [1e4, 2e5] (4,639,301 segments in all), loop "
-         "densities 0.2-5x, mixed precision p=7 (M2L operands as c3), unit-circle Q=20, depth per network by "
+         "densities 0.2-5x, mixed precision p=7 (Chebyshev nodes and compressed M2L as c3), unit-circle Q=20, depth per network by "
          "the autotuner (and the M2L tile form), every step's 64 tree builds and passes replayed as one CUDA graph",
     batch=True, gen_batch=lambda seed: synth.ensemble(seed=4 + 1000 * seed), C=lambda: synth.cubic_voigt(),
-    h_mode="circle", circle_q=20, p=7, levels=0, precision="mixed", m2l_kernel=2, **MIXED_M2L)
+    h_mode="circle", circle_q=20, p=7, levels=0, precision="mixed", m2l_kernel=2, **CHEB_M2L)
 DEFAULT_WORKLOAD = "c3"
 
 
@@ -602,7 +605,7 @@ def run_ours(args, wl):
 
 
 GOLDEN = {"c3": "c3_sampled_forces.json", "c3q": "c3q_sampled_forces.json", "c3_fp64": "c3_sampled_forces.json",
-          "c2": "c2_forces.json", "c3svd": "c3_sampled_forces.json", "c3cheb": "c3_sampled_forces.json"}
+          "c2": "c2_forces.json", "c3svd": "c3_sampled_forces.json", "c3legendre": "c3_sampled_forces.json"}
 
 
 def m2l_options(wl):

@@ -1,7 +1,9 @@
 """Parity at the full 1M-segment size, in the launch configuration bench.py
-times (mixed precision, p = 7, 7-level octree, cubic unit-circle rule with
-Q = 20, tensor-core M2L on FP16 Legendre moments with residual passes on the
-low-order moments), on nodes the oracle computed one by one: the direct Mura
+times (mixed precision, p = 7 on Chebyshev nodes, 7-level octree, cubic
+unit-circle rule with Q = 16, SVD-compressed tensor-core M2L), and in the
+dense-M2L configuration on equispaced nodes (FP16 Legendre moments with
+residual passes on the low-order moments), on nodes the oracle computed one
+by one: the direct Mura
 sum of Eq. "stress3" against all 4M source points (oracle Q = 32, ~2e-10 in
 h), stored in tests/golden/c3_sampled_forces.json by
 tests/golden/make_c3_sampled_forces.py.  The 1e-4 bar of the method's
@@ -55,6 +57,9 @@ def _forces(nodes, segs, b, wl, **over):
     kw = dict(p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
               circle_q=wl["circle_q"], **bench.m2l_options(wl))
     kw.update(over)
+    if kw["precision"] != "mixed":  # the compressed M2L (and Chebyshev nodes) belong to the mixed pass
+        kw.pop("nodes", None)
+        kw.pop("m2l_svd_tol", None)
     f = gb.FMM(**kw).set_material(wl["C"]())
     f.build(torch.tensor(nodes, device="cuda"), torch.tensor(segs, device="cuda"), torch.tensor(b, device="cuda"))
     F = f.nodal_forces().cpu().numpy()
@@ -63,16 +68,20 @@ def _forces(nodes, segs, b, wl, **over):
     return F
 
 
-@pytest.mark.parametrize("label,over,tol", [
-    pytest.param("bench configuration", {}, 1e-4, id="bench"),
-    pytest.param("p=8", {"p": 8}, 1e-4, id="p8"),
-    pytest.param("p=7, FP64 interpolation stages", {"precision": "mixed_f64t"}, 1e-4, id="p7f64t"),
-    # order 6 is not enough for the slab walls: its interpolation error alone (the FP64 pass
-    # at p = 6) is ~1.6e-4 against the direct sum, which is why the bench runs p = 7
-    pytest.param("p=6", {"p": 6}, 3e-4, id="p6"),
+@pytest.mark.parametrize("label,workload,over,tol", [
+    pytest.param("bench configuration", "c3", {}, 1e-4, id="bench"),
+    pytest.param("Chebyshev, compressed M2L, p=8", "c3", {"p": 8}, 1e-4, id="p8"),
+    pytest.param("equispaced, dense M2L", "c3legendre", {}, 1e-4, id="dense"),
+    pytest.param("equispaced, compressed M2L", "c3svd", {}, 1e-4, id="svd"),
+    pytest.param("dense M2L, FP64 interpolation stages", "c3legendre", {"precision": "mixed_f64t"}, 1e-4,
+                 id="dense-f64t"),
+    # order 6 on equispaced nodes is not enough for the slab walls: its interpolation error
+    # alone (the FP64 pass at p = 6) is ~1.6e-4 against the direct sum
+    pytest.param("dense M2L, p=6", "c3legendre", {"p": 6}, 3e-4, id="dense-p6"),
 ])
-def test_full_size_sampled_nodes_match_direct_sum(c3_case, label, over, tol):
-    nodes, segs, b, wl, ids, Fo = c3_case
+def test_full_size_sampled_nodes_match_direct_sum(c3_case, label, workload, over, tol):
+    nodes, segs, b, _, ids, Fo = c3_case
+    wl = _bench_workload(workload)
     F = _forces(nodes, segs, b, wl, **over)
     assert np.isfinite(F).all()
     err = np.linalg.norm(F[ids] - Fo) / np.linalg.norm(Fo)
