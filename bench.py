@@ -91,14 +91,11 @@ def near_flops(wl, work):
     return work["near_pairs"] * near_pair_flops("mixed", wl["h_mode"], q, cubic) + l2p, name
 
 
-# DRAM bytes per target point of one k_near_sym launch (cubic rule, Q = 20), from
+# DRAM bytes per target point of one k_near_sym launch (cubic rule, Q = 16), from
 # one ncu capture on the 250,000-segment slab network (dram__bytes_read.sum +
-# dram__bytes_write.sum); valid for the kernel version the capture was taken of
-NEAR_SYM_DRAM_BYTES_PER_POINT = 7.943e9 / 1.0e6
-# DRAM bytes per occupied M2L cell pair of k_m2l_tc at p = 7 (default operands),
-# from one ncu capture of one of the 7 offset launches on the 250,000-segment
-# slab network: 7 x 13.43 GB / 2,010,436 pairs
-M2L_TC_P7_DRAM_BYTES_PER_PAIR = 7 * 13.43e9 / 2010436
+# dram__bytes_write.sum = 6.530 + 1.344 GB for 1,000,000 points); valid for the
+# kernel version the capture was taken of
+NEAR_SYM_DRAM_BYTES_PER_POINT = (6.530216e9 + 1.343735e9) / 1.0e6
 
 
 def measured_alu_peaks():
@@ -158,6 +155,11 @@ WORKLOADS["c3q"] = dict(
     desc="profiling case: 250,000 segments (5,000 loops x 50 in 32 Gaussian slabs), cubic, p=7, mixed, 6-level octree",
     gen=lambda seed: synth.slab_loops(n_loops=5000, seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
     h_mode="circle", circle_q=20, p=7, levels=6, precision="mixed", **MIXED_M2L)
+WORKLOADS["c3q_cheb"] = dict(
+    desc="profiling case of the headline's kernels: 250,000 segments (5,000 loops x 50 in 32 Gaussian slabs), "
+         "cubic, p=7 on Chebyshev nodes with the compressed M2L as c3, unit-circle Q=16, 6-level octree",
+    gen=WORKLOADS["c3q"]["gen"], C=lambda: synth.cubic_voigt(), h_mode="circle", circle_q=16, p=7, levels=6,
+    precision="mixed", **CHEB_M2L)
 WORKLOADS["c3_mlp"] = dict(
     desc="c3 network with the learned angular factor in the near field (pairs beyond 8 segment lengths in bins "
          "the plain evaluator accepted at 2e-2 x RMS(h)), plain cubic rule elsewhere",
@@ -180,6 +182,16 @@ WORKLOADS["c5"] = dict(
     batch=True, gen_batch=lambda seed: synth.ensemble(seed=4 + 1000 * seed), C=lambda: synth.cubic_voigt(),
     h_mode="circle", circle_q=20, p=7, levels=0, precision="mixed", m2l_kernel=2, **CHEB_M2L)
 DEFAULT_WORKLOAD = "c3"
+
+
+def profile_region(args, start):
+    """With --profile-region, the timed steps alone are a profiler range
+    (ncu --profile-from-start off captures only them, not the medium setup)."""
+    if getattr(args, "profile_region", False):
+        import torch
+
+        rt = torch.cuda.cudart()
+        (rt.cudaProfilerStart if start else rt.cudaProfilerStop)()
 
 
 def rank_configs(n_configs, world, rank):
@@ -378,12 +390,14 @@ def run_batch(args, wl):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    profile_region(args, True)
     for i in range(args.steps):
         flush.zero_()
         evs[i][0].record(stream)
         step()
         evs[i][1].record(stream)
     torch.cuda.synchronize()
+    profile_region(args, False)
     clk = clocks.stop()
     launches = bt.info(0)["launches"] - l0
     t_ms = sum(a.elapsed_time(b_) for a, b_ in evs)
@@ -507,6 +521,7 @@ def run_ours(args, wl):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    profile_region(args, True)
     t0 = time.perf_counter()
     for i in range(args.steps):
         flush.zero_()
@@ -515,6 +530,7 @@ def run_ours(args, wl):
         evs[i][1].record(stream)
         stage.append(f.stage_times())
     torch.cuda.synchronize()
+    profile_region(args, False)
     wall = time.perf_counter() - t0
     if world > 1:
         torch.distributed.barrier()
@@ -651,7 +667,7 @@ def roofline_of(wl, work, m2l_ms, leaf_ms, m2l_fft, peaks, ranks=None):
         flops, kname = near_flops(wl, work)
         achieved = flops / (leaf_ms / 1e3) / 1e12
         dom, bound, peak, src = kname + " (L2P + near-field P2P)", "alu", alu_peak, peaks["source"]
-        if kname == "k_near_sym" and wl.get("circle_q") == 20:
+        if kname == "k_near_sym" and wl.get("circle_q") == 16:
             traffic = NEAR_SYM_DRAM_BYTES_PER_POINT * work["points"]
             traffic_src = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_near_sym on the "
                            "250k-segment slab network, scaled by points")
@@ -672,10 +688,6 @@ def roofline_of(wl, work, m2l_ms, leaf_ms, m2l_fft, peaks, ranks=None):
             if svd:
                 dom = "k_m2l_tc (SVD-compressed M2L, tcgen05 FP16 operands; stage includes the basis transforms)"
             peak, src = measured_bf16_peak()
-            if p == 7 and wl.get("m2l_basis") == 1 and not svd:
-                traffic = M2L_TC_P7_DRAM_BYTES_PER_PAIR * work["m2l_pairs"]
-                traffic_src = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_m2l_tc (p=7, "
-                               "default operands) on the 250k-segment slab network, scaled by occupied cell pairs")
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": src,
             "work": "algorithmic: near pairs x FLOP/pair (h once per unordered pair when h is the unit-circle "
@@ -725,6 +737,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the plain FP64 pass of the same step")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="mark the timed steps as the profiler range (for ncu --profile-from-start off)")
     ap.add_argument("--levels", type=int, default=0, help="override the workload's tree depth")
     ap.add_argument("--p", type=int, default=0, help="override the workload's interpolation order")
     ap.add_argument("--m2l-split", type=int, default=-1, help="override the M2L operand mode (fmm options)")
