@@ -128,8 +128,8 @@ WORKLOADS["c2"] = dict(
     h_mode="circle", circle_q=32, p=5, levels=5, precision="fp64")
 # The compressed M2L of the headline: Chebyshev nodes, singular vectors kept above 5e-5 of
 # the largest (the paper's Chebyshev FMM), FP16 operands with residual passes on the
-# leading block of 64 singular directions, offsets summed in 7 runs.
-CHEB_M2L = dict(nodes="chebyshev", m2l_svd_tol=5e-5, m2l_split=6, m2l_chunks=7, m2l_split_kblocks=1)
+# leading block of 64 singular directions, offsets summed in 3 runs.
+CHEB_M2L = dict(nodes="chebyshev", m2l_svd_tol=5e-5, m2l_split=6, m2l_chunks=3, m2l_split_kblocks=1)
 WORKLOADS["c3"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs, sigma 0.02), cubic C11=1.684 C12=1.214 "
          "C44=0.754, order p=7 on Chebyshev nodes, 7-level octree, mixed precision (SVD-compressed M2L on the "

@@ -147,6 +147,41 @@ __global__ void k_ops_convert(int64_t total, int Np, int Kp, int Kp_lo, const do
     }
 }
 
+inline int pad8(int n) { return (n + 7) / 8 * 8; }
+
+// largest |x| over n values into *bits (non-negative floats order like their bit patterns)
+__global__ void k_absmax_f32(int64_t n, const float *__restrict__ x, unsigned *__restrict__ bits) {
+    float mx = 0.f;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        mx = fmaxf(mx, fabsf(x[i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(bits, __float_as_uint(mx));
+}
+
+// rows vectors of n FP32 values (contiguous) -> FP16 hi + lo, stride ldx (zero padded), all
+// scaled by the power of two s that maps the largest |value| just below 2^14:
+// hi = fp16(s x), lo = fp16(s x - hi).  *alpha (if given) = 1 / (s sbasis), the factor that
+// undoes both scales of a product with a basis split the same way.
+__global__ void k_split_f16(int64_t rows, int n, int ldx, const float *__restrict__ src,
+                            const unsigned *__restrict__ bits, float sbasis, __half *__restrict__ hi,
+                            __half *__restrict__ lo, float *__restrict__ alpha) {
+    const float mx = __uint_as_float(*bits);
+    int e = 0;
+    frexpf(mx, &e);
+    const float s = mx > 0.f ? ldexpf(1.f, 14 - e) : 1.f;
+    if (alpha && blockIdx.x == 0 && threadIdx.x == 0) *alpha = 1.f / (s * sbasis);
+    const int64_t total = rows * ldx;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = idx / ldx;
+        const int k = int(idx - r * ldx);
+        const float v = k < n ? src[r * n + k] * s : 0.f;
+        const __half h = __float2half_rn(v);
+        hi[idx] = h;
+        lo[idx] = __float2half_rn(v - __half2float(h));
+    }
+}
+
 // the 316 offsets o in [-3, 3]^3 with max |o_i| >= 2
 std::vector<int> all_offsets() {
     std::vector<int> off;
@@ -292,7 +327,40 @@ int svd_bases(gbfmm_ctx *ctx) {
         k_take_cols<<<nblk(int64_t(nt) * T.r1, 256), 256, 0, st>>>(nt, T.r1, Gt, T.U64, T.Uf);
         k_take_cols<<<nblk(int64_t(ns) * T.r2, 256), 256, 0, st>>>(ns, T.r2, Gs, T.R64, T.Rf);
         CK(cudaGetLastError());
+        // FP16 hi + lo of both bases for the per-pass transforms, columns padded to 8 rows
+        void *olds[4] = {T.Uh, T.Ul, T.Rh, T.Rl};
+        for (void *q : olds)
+            if (q) cudaFree(q);
+        T.Uh = T.Ul = T.Rh = T.Rl = nullptr;
+        const size_t nu = size_t(pad8(nt)) * T.r1, nr = size_t(pad8(ns)) * T.r2;
+        CK(cudaMalloc(&T.Uh, nu * sizeof(__half)));
+        CK(cudaMalloc(&T.Ul, nu * sizeof(__half)));
+        CK(cudaMalloc(&T.Rh, nr * sizeof(__half)));
+        CK(cudaMalloc(&T.Rl, nr * sizeof(__half)));
+        unsigned *d_b = nullptr;
+        CK(cudaMalloc(&d_b, 2 * sizeof(unsigned)));
+        CK(cudaMemsetAsync(d_b, 0, 2 * sizeof(unsigned), st));
+        ctx->launches += 4;
+        k_absmax_f32<<<256, 256, 0, st>>>(int64_t(nt) * T.r1, T.Uf, d_b);
+        k_absmax_f32<<<256, 256, 0, st>>>(int64_t(ns) * T.r2, T.Rf, d_b + 1);
+        k_split_f16<<<nblk(int64_t(nu), 256), 256, 0, st>>>(T.r1, nt, pad8(nt), T.Uf, d_b, 1.f, (__half *)T.Uh,
+                                                             (__half *)T.Ul, nullptr);
+        k_split_f16<<<nblk(int64_t(nr), 256), 256, 0, st>>>(T.r2, ns, pad8(ns), T.Rf, d_b + 1, 1.f, (__half *)T.Rh,
+                                                             (__half *)T.Rl, nullptr);
+        CK(cudaGetLastError());
+        unsigned hb[2] = {0, 0};
+        CK(cudaMemcpyAsync(hb, d_b, sizeof(hb), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        cudaFree(d_b);
+        auto scale_of = [](unsigned b) {
+            float mx;
+            std::memcpy(&mx, &b, sizeof(mx));
+            int e = 0;
+            std::frexp(mx, &e);
+            return mx > 0.f ? std::ldexp(1.f, 14 - e) : 1.f;
+        };
+        T.sU = scale_of(hb[0]);
+        T.sR = scale_of(hb[1]);
         return GBFMM_OK;
     };
     rc = run();
@@ -380,74 +448,115 @@ int svd_operators(gbfmm_ctx *ctx, const int *d_off, const int *d_lo, int n_off) 
 
 int svd_prepare(gbfmm_ctx *ctx) {
     TcPlan &T = ctx->tc;
+    const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p;
     const int64_t per = std::max(T.r1, T.r2);
     if (int rc = grow_dev(ctx, T.c_cap, ctx->n_cells * per,
                           {{(void **)&T.Wc, size_t(ctx->n_cells) * per * sizeof(float)},
                            {(void **)&T.Sc, size_t(ctx->n_cells) * per * sizeof(float)}},
                           "compressed M2L values"))
         return rc;
-    if (int rc = ensure_blas(ctx)) return rc;
-    if (!T.gemm_emulated) {
-        // does this cuBLAS run FP32 GEMMs as BF16x9 emulation on this device?  A small
-        // product on the (allocated) buffers settles it once, outside any graph capture
-        const float one = 1.f, zero = 0.f;
-        const cublasStatus_t s =
-            cublasGemmEx((cublasHandle_t)T.blas, CUBLAS_OP_N, CUBLAS_OP_N, 16, 16, 16, &one, T.Wc, CUDA_R_32F, 16,
-                         T.Wc, CUDA_R_32F, 16, &zero, T.Sc, CUDA_R_32F, 16, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-                         CUBLAS_GEMM_DEFAULT);
-        T.gemm_emulated = s == CUBLAS_STATUS_SUCCESS ? 1 : -1;
-        CK(cudaStreamSynchronize(ctx->stream));
+    // one level's transform input split into FP16 hi + lo (the deepest level is the largest)
+    const int64_t xrow = std::max<int64_t>(pad8(9 * P3), T.r1);
+    const int64_t need = (int64_t(1) << (3 * (ctx->L - 1))) * xrow;
+    if (int rc = grow_dev(ctx, T.x_cap, need,
+                          {{&T.Xh, size_t(need) * sizeof(__half)}, {&T.Xl, size_t(need) * sizeof(__half)}},
+                          "compressed M2L transform operands"))
+        return rc;
+    if (!T.d_scal) CK(cudaMalloc(&T.d_scal, (2 + 2 * GB_TC_MAXLEV) * sizeof(float)));
+    if (!T.d_bits) CK(cudaMalloc(&T.d_bits, 2 * GB_TC_MAXLEV * sizeof(unsigned)));
+    const float consts[2] = {0.f, 1.f};
+    CK(cudaMemcpyAsync(T.d_scal, consts, sizeof(consts), cudaMemcpyHostToDevice, ctx->stream));
+    return ensure_blas(ctx);
+}
+
+// Y (m x rows, ld ldy, FP32) = alpha (Ah^T|Ah) (Xh + Xl) + Al (Xh): the product of an FP16-split
+// basis and an FP16-split operand on the tensor cores with FP32 accumulation, hi*hi + hi*lo + lo*hi
+// (the lo*lo term is below FP32 rounding); alpha, 0 and 1 are device scalars
+static int split_gemm(gbfmm_ctx *ctx, cublasOperation_t opA, int m, int64_t rows, int k, const void *Ah,
+                      const void *Al, int lda, int ldx, const float *alpha, float *Y, int ldy) {
+    TcPlan &T = ctx->tc;
+    cublasHandle_t h = (cublasHandle_t)T.blas;
+    const float *zero = T.d_scal, *one = T.d_scal + 1;
+    const void *A[3] = {Ah, Ah, Al}, *X[3] = {T.Xh, T.Xl, T.Xh};
+    BL(cublasSetPointerMode(h, CUBLAS_POINTER_MODE_DEVICE));
+    for (int t = 0; t < 3; ++t) {
+        const cublasStatus_t st = cublasGemmEx(h, opA, CUBLAS_OP_N, m, int(rows), k, alpha, A[t], CUDA_R_16F, lda, X[t],
+                                               CUDA_R_16F, ldx, t ? one : zero, Y, CUDA_R_32F, ldy, CUBLAS_COMPUTE_32F,
+                                               CUBLAS_GEMM_DEFAULT);
+        if (st != CUBLAS_STATUS_SUCCESS) {
+            cublasSetPointerMode(h, CUBLAS_POINTER_MODE_HOST);
+            return set_err(ctx, GBFMM_ERR_CUDA, "cuBLAS FP16 transform GEMM: " + std::to_string(int(st)));
+        }
     }
+    BL(cublasSetPointerMode(h, CUBLAS_POINTER_MODE_HOST));
     return GBFMM_OK;
 }
 
-static cublasComputeType_t f32_compute(const TcPlan &T) {
-    return T.gemm_emulated > 0 ? CUBLAS_COMPUTE_32F_EMULATED_16BFX9 : CUBLAS_COMPUTE_32F;
+// One level's rows [rows][n] of src (FP32) into the FP16 split with its own power-of-two scale
+static int split_level(gbfmm_ctx *ctx, const float *src, int64_t rows, int n, int ldx, int slot, float sbasis) {
+    TcPlan &T = ctx->tc;
+    cudaStream_t st = ctx->stream;
+    const int64_t cnt = rows * n;
+    const unsigned g = unsigned(std::min<int64_t>(nblk(cnt, 256), 8 * 152));
+    CK(cudaMemsetAsync(T.d_bits + slot, 0, sizeof(unsigned), st));
+    ctx->launches += 2;
+    k_absmax_f32<<<g, 256, 0, st>>>(cnt, src, T.d_bits + slot);
+    k_split_f16<<<unsigned(std::min<int64_t>(nblk(rows * ldx, 256), 16 * 152)), 256, 0, st>>>(
+        rows, n, ldx, src, T.d_bits + slot, sbasis, (__half *)T.Xh, (__half *)T.Xl, T.d_scal + 2 + slot);
+    CK(cudaGetLastError());
+    return GBFMM_OK;
 }
 
 int svd_transform_w(gbfmm_ctx *ctx, const float *Wf) {
     TcPlan &T = ctx->tc;
-    const int L = ctx->L, P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p, ns = 9 * P3;
-    const int64_t base = cell_base(2), rows = cell_base(L) - base;
-    if (rows <= 0) return GBFMM_OK;
+    const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p, ns = 9 * P3, lds = pad8(ns);
     if (int rc = ensure_blas(ctx)) return rc;
-    const float one = 1.f, zero = 0.f;
-    // W'^T (r2 x cells) = R^T (r2 x 9 p^3) W^T (9 p^3 x cells): every cell of levels 2 .. L-1
-    BL(cublasGemmEx((cublasHandle_t)T.blas, CUBLAS_OP_T, CUBLAS_OP_N, T.r2, int(rows), ns, &one, T.Rf, CUDA_R_32F,
-                    ns, Wf + base * ns, CUDA_R_32F, ns, &zero, T.Wc + base * T.r2, CUDA_R_32F, T.r2, f32_compute(T),
-                    CUBLAS_GEMM_DEFAULT));
+    // W'^T (r2 x cells) = R^T (r2 x 9 p^3) W^T (9 p^3 x cells), level by level (each its own scale)
+    for (int l = 2; l < ctx->L; ++l) {
+        const int64_t row0 = cell_base(l), rows = int64_t(1) << (3 * l);
+        if (int rc = split_level(ctx, Wf + row0 * ns, rows, ns, lds, l, T.sR)) return rc;
+        if (int rc = split_gemm(ctx, CUBLAS_OP_T, T.r2, rows, lds, T.Rh, T.Rl, lds, lds, T.d_scal + 2 + l,
+                                T.Wc + row0 * T.r2, T.r2))
+            return rc;
+    }
     return GBFMM_OK;
 }
 
 int svd_expand_s(gbfmm_ctx *ctx, float *Sf) {
     TcPlan &T = ctx->tc;
-    const int L = ctx->L, P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p, nt = 6 * P3;
-    const int64_t base = cell_base(2), rows = cell_base(L) - base;
-    if (rows <= 0) return GBFMM_OK;
+    const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p, nt = 6 * P3;
     if (int rc = ensure_blas(ctx)) return rc;
-    const float one = 1.f, zero = 0.f;
-    // S^T (6 p^3 x cells) = U (6 p^3 x r1) S'^T (r1 x cells)
-    BL(cublasGemmEx((cublasHandle_t)T.blas, CUBLAS_OP_N, CUBLAS_OP_N, nt, int(rows), T.r1, &one, T.Uf, CUDA_R_32F,
-                    nt, T.Sc + base * T.r1, CUDA_R_32F, T.r1, &zero, Sf + base * nt, CUDA_R_32F, nt, f32_compute(T),
-                    CUBLAS_GEMM_DEFAULT));
+    // S^T (6 p^3 x cells) = U (6 p^3 x r1) S'^T (r1 x cells), level by level
+    for (int l = 2; l < ctx->L; ++l) {
+        const int64_t row0 = cell_base(l), rows = int64_t(1) << (3 * l);
+        if (int rc = split_level(ctx, T.Sc + row0 * T.r1, rows, T.r1, T.r1, GB_TC_MAXLEV + l, T.sU)) return rc;
+        if (int rc = split_gemm(ctx, CUBLAS_OP_N, nt, rows, T.r1, T.Uh, T.Ul, pad8(nt), T.r1,
+                                T.d_scal + 2 + GB_TC_MAXLEV + l, Sf + row0 * nt, nt))
+            return rc;
+    }
     return GBFMM_OK;
 }
 
 void svd_free(gbfmm_ctx *ctx, bool borrowed) {
     TcPlan &T = ctx->tc;
     if (T.blas) cublasDestroy((cublasHandle_t)T.blas);
-    void *mine[] = {T.Wc, T.Sc, T.blas_ws};
+    void *mine[] = {T.Wc, T.Sc, T.blas_ws, T.Xh, T.Xl, T.d_scal, T.d_bits};
     for (void *q : mine)
         if (q) cudaFree(q);
     if (!borrowed) {
-        void *tabs[] = {T.Uf, T.Rf, T.U64, T.R64};
+        void *tabs[] = {T.Uf, T.Rf, T.U64, T.R64, T.Uh, T.Ul, T.Rh, T.Rl};
         for (void *q : tabs)
             if (q) cudaFree(q);
     }
     T.blas = T.blas_ws = nullptr;
     T.Wc = T.Sc = nullptr;
+    T.Xh = T.Xl = nullptr;
+    T.d_scal = nullptr;
+    T.d_bits = nullptr;
     T.Uf = T.Rf = nullptr;
     T.U64 = T.R64 = nullptr;
+    T.Uh = T.Ul = T.Rh = T.Rl = nullptr;
     T.c_cap = 0;
+    T.x_cap = 0;
     T.bases_ok = 0;
 }

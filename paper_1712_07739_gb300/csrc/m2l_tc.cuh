@@ -44,8 +44,14 @@ struct TcPlan {
     float *Uf = nullptr;       // target basis [6 p^3][r1], column-major (ld 6 p^3), shared in a batch
     float *Rf = nullptr;       // source basis [9 p^3][r2], column-major (ld 9 p^3), shared in a batch
     double *U64 = nullptr, *R64 = nullptr;  // the bases in FP64 (operator construction)
+    void *Uh = nullptr, *Ul = nullptr;  // U split into FP16 hi + lo (x sU), [6 p^3 padded to 8][r1], shared
+    void *Rh = nullptr, *Rl = nullptr;  // R split likewise, [9 p^3 padded to 8][r2], shared
+    float sU = 1.f, sR = 1.f;  // the bases' power-of-two scales
     int bases_ok = 0;          // U, R belong to the current medium and options
-    int gemm_emulated = 0;     // the per-pass FP32 GEMMs run as BF16x9 emulation
+    void *Xh = nullptr, *Xl = nullptr;  // per tree: one level's transform input split into FP16 hi + lo
+    int64_t x_cap = 0;
+    float *d_scal = nullptr;   // per tree: 0, 1 and the per-level GEMM scale factors (device scalars)
+    unsigned *d_bits = nullptr;  // per tree: per-level largest |value| bits of the transform inputs
     double svd_sigma[4] = {0}; // largest and smallest kept singular values: target, source
     float *Wc = nullptr;       // per tree: [n_cells][r2] compressed multipole values
     float *Sc = nullptr;       // per tree: [n_cells][r1] compressed local values

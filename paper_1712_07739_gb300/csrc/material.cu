@@ -176,7 +176,12 @@ int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
     T.U64 = S.U64;
     T.R64 = S.R64;
     T.bases_ok = S.bases_ok;
-    T.gemm_emulated = S.gemm_emulated;
+    T.Uh = S.Uh;
+    T.Ul = S.Ul;
+    T.Rh = S.Rh;
+    T.Rl = S.Rl;
+    T.sU = S.sU;
+    T.sR = S.sR;
     std::memcpy(T.svd_sigma, S.svd_sigma, sizeof(T.svd_sigma));
     if (!T.d_status) {
         CK(cudaMalloc(&T.d_status, sizeof(int)));
@@ -200,6 +205,7 @@ extern "C" int fmm_set_material(gbfmm_ctx *ctx, const double *V) {
         ctx->tc.Thi = ctx->tc.Tlo = nullptr;
         ctx->tc.Uf = ctx->tc.Rf = nullptr;
         ctx->tc.U64 = ctx->tc.R64 = nullptr;
+        ctx->tc.Uh = ctx->tc.Ul = ctx->tc.Rh = ctx->tc.Rl = nullptr;
         ctx->tc.ready_ops = false;
         ctx->fft.ready = false;
         ctx->borrowed_material = false;
