@@ -18,9 +18,11 @@
 // every level.
 //
 // The setup is FP64 dense linear algebra done by library routines (cuBLAS
-// DSYRK and DGEMM, cuSOLVER's symmetric eigensolver); the per-pass
-// transforms are plain FP32 GEMMs (cuBLAS, FP32 accuracy from the BF16x9
-// emulation on the tensor cores where available).
+// DSYRK and DGEMM, cuSOLVER's symmetric eigensolver).  The per-pass
+// transforms are plain dense GEMMs with FP32 results, run by cuBLAS on the
+// tensor cores as three FP16 products of hi + lo splits of both factors
+// (hi*hi + hi*lo + lo*hi, FP32 accumulation; each level's operand scaled by
+// its own power of two).
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 #include <cuda_bf16.h>
