@@ -201,6 +201,37 @@ def _near(mat, xt, tseg, tleaf, ys, qs, sseg, sleaf, n):
     return out
 
 
+def _m2l_level(mat, p, H, lev, W, src_occ, tgt_occ, nodes, svd):
+    """Node-kernel sums of one level's interaction lists (Algorithm 2, M2L), pairs
+    grouped by offset: S[B] = sum over A in I(B) of T_(B - A) W[A] for the target
+    cells tgt_occ and the source cells src_occ (boolean grids); with svd the
+    compressed M2L (sources projected onto R, each cell's sum onto U)."""
+    n = 1 << lev
+    h = H / n
+    P3 = p ** 3
+    S = np.zeros((n, n, n, P3, 6))
+    groups = {}
+    for B in itertools.product(range(n), repeat=3):
+        if not tgt_occ[B]:
+            continue  # no target below B: its local values are never used
+        for o in interaction_offsets(B):
+            A = tuple(B[d] - o[d] for d in range(3))
+            if all(0 <= A[d] < n for d in range(3)) and src_occ[A]:
+                groups.setdefault(o, []).append((B, A))
+    for o, pairs in groups.items():
+        Ws = np.stack([W[A] for _, A in pairs])
+        if svd is not None:  # R R^T W: the source weights seen through the compression
+            R = svd[1]
+            Ws = ((Ws.reshape(len(pairs), 9 * P3) @ R) @ R.T).reshape(len(pairs), P3, 9)
+        res = _apply_offset(mat, p, h, o, Ws, nodes=nodes)
+        for (B, _), r in zip(pairs, res):
+            S[B] += r
+    if svd is not None:  # U U^T of each cell's M2L sum
+        U = svd[0]
+        S = ((S.reshape(-1, 6 * P3) @ U) @ U.T).reshape(S.shape)
+    return S
+
+
 def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None, nodes="equispaced", svd=None):
     """Stress [n_t, 6] at targets by the multilevel Lagrange FMM (Algorithm 2; targets
     default to sources), on the given node set; with svd = (U, R) from
@@ -211,6 +242,22 @@ def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None, nodes="equispaced"
     if xt is None:
         xt, tseg = ys, sseg
     origin, H = root_box(ys)
+    S, sl, tl = _far_levels(mat, ys, qs, p, L, xt, origin, H, nodes, svd)
+    lf = L - 1
+    nL = 1 << lf
+    hL = H / nL
+    out = np.zeros((len(xt), 6))
+    if lf >= 2:
+        tt = (xt - (origin + tl * hL)) / hL
+        out += np.einsum("nl,nls->ns", basis_3d(tt, p, nodes), S[lf][tl[:, 0], tl[:, 1], tl[:, 2]])
+    out += _near(mat, xt, np.asarray(tseg), tl, ys, qs, np.asarray(sseg), sl, nL)
+    return out
+
+
+def _far_levels(mat, ys, qs, p, L, xt, origin, H, nodes, svd):
+    """P2M at the leaves, M2M up, M2L at every level >= 2 and L2L down (Algorithm 2):
+    the local values S[level] of every cell, and the leaf cell of each source
+    and target."""
     lf = L - 1
     nL = 1 << lf
     P3 = p ** 3
@@ -232,37 +279,17 @@ def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None, nodes="equispaced"
             Wp += np.einsum("Aa,Bb,Cc,xyzabcw->xyzABCw", M[c[0]], M[c[1]], M[c[2]], ch).reshape(
                 n, n, n, P3, 9)
         W[lev] = Wp
-    # node-kernel sums over the interaction lists at every level >= 2, pairs grouped by offset
+    # node-kernel sums over the interaction lists at every level >= 2
     S = {}
     for lev in range(2, lf + 1):
         n = 1 << lev
-        h = H / n
-        S[lev] = np.zeros((n, n, n, P3, 6))
         occ = np.zeros((n, n, n), dtype=bool)
         c = cell_of(ys, origin, H, lev)
         occ[c[:, 0], c[:, 1], c[:, 2]] = True
         tocc = np.zeros((n, n, n), dtype=bool)
         c = cell_of(xt, origin, H, lev)
         tocc[c[:, 0], c[:, 1], c[:, 2]] = True
-        groups = {}
-        for B in itertools.product(range(n), repeat=3):
-            if not tocc[B]:
-                continue  # no target below B: its local values are never used
-            for o in interaction_offsets(B):
-                A = tuple(B[d] - o[d] for d in range(3))
-                if all(0 <= A[d] < n for d in range(3)) and occ[A]:
-                    groups.setdefault(o, []).append((B, A))
-        for o, pairs in groups.items():
-            Ws = np.stack([W[lev][A] for _, A in pairs])
-            if svd is not None:  # R R^T W: the source weights seen through the compression
-                R = svd[1]
-                Ws = ((Ws.reshape(len(pairs), 9 * P3) @ R) @ R.T).reshape(len(pairs), P3, 9)
-            res = _apply_offset(mat, p, h, o, Ws, nodes=nodes)
-            for (B, _), r in zip(pairs, res):
-                S[lev][B] += r
-        if svd is not None:  # U U^T of each cell's M2L sum
-            U = svd[0]
-            S[lev] = ((S[lev].reshape(-1, 6 * P3) @ U) @ U.T).reshape(S[lev].shape)
+        S[lev] = _m2l_level(mat, p, H, lev, W[lev], occ, tocc, nodes, svd)
     # local values of the children: the parent's interpolated to the child nodes (downward)
     for lev in range(3, lf + 1):
         n = 1 << (lev - 1)
@@ -270,13 +297,71 @@ def lagrange_fmm(mat, ys, qs, sseg, p, L, xt=None, tseg=None, nodes="equispaced"
         for c in itertools.product((0, 1), repeat=3):
             add = np.einsum("Aa,Bb,Cc,xyzABCs->xyzabcs", M[c[0]], M[c[1]], M[c[2]], Sp)
             S[lev][c[0]::2, c[1]::2, c[2]::2] += add.reshape(n, n, n, P3, 6)
-    # local values interpolated to the targets, plus the direct near sum
-    tl = cell_of(xt, origin, H, lf)
-    out = np.zeros((len(xt), 6))
+    return S, sl, cell_of(xt, origin, H, lf)
+
+
+def adaptive_fmm(mat, ys, qs, sseg, p, L, refine, nodes="equispaced", svd=None):
+    """Stress [n, 6] at the source points by the Lagrange FMM on an adaptive tree:
+    the uniform tree of Algorithm 2 (leaves at level L - 1) in which every leaf
+    holding more than ``refine`` points is split once more.  Two adjacent split
+    leaves interact through their children: adjacent children by the direct sum
+    of Eq. "stress3", the others by an M2L at level L (the children's interaction
+    lists, restricted to children of split leaves); every other pair of adjacent
+    leaves by the direct sum as in Algorithm 2.  The points of a split leaf take
+    the local values of their child: the parent's interpolated to it plus the
+    level-L M2L sum.  With every occupied leaf split this is Algorithm 2 on L + 1
+    levels."""
+    ys = np.asarray(ys, dtype=np.float64)
+    qs = np.asarray(qs, dtype=np.float64).reshape(-1, 9)
+    sseg = np.asarray(sseg)
+    origin, H = root_box(ys)
+    S, sl, _ = _far_levels(mat, ys, qs, p, L, ys, origin, H, nodes, svd)
+    lf = L - 1
+    nL, nF = 1 << lf, 2 << lf
+    hL, hF = H / nL, H / nF
+    P3 = p ** 3
+    cnt = np.zeros((nL, nL, nL), dtype=np.int64)
+    np.add.at(cnt, (sl[:, 0], sl[:, 1], sl[:, 2]), 1)
+    split = cnt > refine
+    in_split = split[sl[:, 0], sl[:, 1], sl[:, 2]]
+    sf = cell_of(ys, origin, H, lf + 1)
+    # children of split leaves: multipole weights, M2L among themselves at level L, L2L from the parent
+    idx = np.nonzero(in_split)[0]
+    Wf = np.zeros((nF, nF, nF, P3, 9))
+    tf = (ys[idx] - (origin + sf[idx] * hF)) / hF
+    np.add.at(Wf, (sf[idx, 0], sf[idx, 1], sf[idx, 2]), basis_3d(tf, p, nodes)[:, :, None] * qs[idx][:, None, :])
+    focc = np.zeros((nF, nF, nF), dtype=bool)
+    focc[sf[idx, 0], sf[idx, 1], sf[idx, 2]] = True
+    Sf = _m2l_level(mat, p, H, lf + 1, Wf, focc, focc, nodes, svd)
     if lf >= 2:
-        tt = (xt - (origin + tl * hL)) / hL
-        out += np.einsum("nl,nls->ns", basis_3d(tt, p, nodes), S[lf][tl[:, 0], tl[:, 1], tl[:, 2]])
-    out += _near(mat, xt, np.asarray(tseg), tl, ys, qs, np.asarray(sseg), sl, nL)
+        M = child_transfer(p, nodes)
+        Sp = S[lf].reshape(nL, nL, nL, p, p, p, 6)
+        for c in itertools.product((0, 1), repeat=3):
+            add = np.einsum("Aa,Bb,Cc,xyzABCs->xyzabcs", M[c[0]], M[c[1]], M[c[2]], Sp)
+            Sf[c[0]::2, c[1]::2, c[2]::2] += add.reshape(nL, nL, nL, P3, 6)
+    # far field at the points: the leaf's local values, or the child's for points of split leaves
+    out = np.zeros((len(ys), 6))
+    co = np.nonzero(~in_split)[0]
+    if lf >= 2 and len(co):
+        tt = (ys[co] - (origin + sl[co] * hL)) / hL
+        out[co] += np.einsum("nl,nls->ns", basis_3d(tt, p, nodes), S[lf][sl[co, 0], sl[co, 1], sl[co, 2]])
+    if len(idx):
+        out[idx] += np.einsum("nl,nls->ns", basis_3d(tf, p, nodes), Sf[sf[idx, 0], sf[idx, 1], sf[idx, 2]])
+    # near field: adjacent leaves, except non-adjacent children of two different split leaves
+    for key in np.unique(sl[:, 0] * nL * nL + sl[:, 1] * nL + sl[:, 2]):
+        B = np.array([key // (nL * nL), (key // nL) % nL, key % nL])
+        ti = np.nonzero((sl == B).all(axis=1))[0]
+        near = ((sl >= B - 1) & (sl <= B + 1)).all(axis=1)
+        if not split[tuple(B)]:
+            sj = np.nonzero(near)[0]
+            out[ti] += direct_stress(mat, ys[ti], sseg[ti], ys[sj], qs[sj], sseg[sj])
+            continue
+        other_split = near & in_split & ~(sl == B).all(axis=1)
+        for fc in np.unique(sf[ti], axis=0):
+            tc = ti[(sf[ti] == fc).all(axis=1)]
+            keep = near & ~(other_split & (np.abs(sf - fc).max(axis=1) >= 2))
+            sj = np.nonzero(keep)[0]
+            out[tc] += direct_stress(mat, ys[tc], sseg[tc], ys[sj], qs[sj], sseg[sj])
     return out
 
 
