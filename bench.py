@@ -138,6 +138,12 @@ WORKLOADS["c3"] = dict(
          "step through the plain FP64 pass is timed in the same run",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
     h_mode="circle", circle_q=16, p=7, levels=7, precision="mixed", fp64_arm=True, **CHEB_M2L)
+WORKLOADS["c3a"] = dict(
+    desc="c3 on an adaptive octree: the 7-level tree with every leaf holding more than 48 Gauss points split "
+         "once more (children of two split leaves that are not adjacent interact by an M2L one level down, "
+         "adjacent ones directly)",
+    gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=16, p=7, levels=7,
+    precision="mixed", refine_points=48, **CHEB_M2L)
 WORKLOADS["c3legendre"] = dict(
     desc="c3 on equispaced nodes with the dense M2L (every one of the 54 p^6 products per cell pair, on FP16 "
          "Legendre moments of the source cells with residual passes on the low-order moments)",
@@ -601,6 +607,7 @@ def run_ours(args, wl):
                        "m2l_kernel": int(f.options.m2l_kernel), "m2l_fft": int(f.options.m2l_fft),
                        "nodes": ["equispaced", "chebyshev"][int(f.options.nodes)],
                        "m2l_svd_tol": float(f.options.m2l_svd_tol), "m2l_svd_ranks": ranks,
+                       "refine_points": int(f.options.refine_points),
                        "l2": "flushed: 256 MiB write between steps, outside the step events",
                        "step": "fmm_build_tree + fmm_eval_nodal_forces"},
             "stage_ms": {"precontract": st[:, 0].mean(), "p2m_m2m": st[:, 1].mean(), "m2l": st[:, 2].mean(),
@@ -621,13 +628,14 @@ def run_ours(args, wl):
 
 
 GOLDEN = {"c3": "c3_sampled_forces.json", "c3q": "c3q_sampled_forces.json", "c3_fp64": "c3_sampled_forces.json",
-          "c2": "c2_forces.json", "c3svd": "c3_sampled_forces.json", "c3legendre": "c3_sampled_forces.json"}
+          "c2": "c2_forces.json", "c3svd": "c3_sampled_forces.json", "c3legendre": "c3_sampled_forces.json",
+          "c3a": "c3_sampled_forces.json"}
 
 
 def m2l_options(wl):
     """The tensor-core M2L operand options a workload names (library defaults otherwise)."""
     return {k: wl[k] for k in ("m2l_split", "m2l_basis", "m2l_chunks", "m2l_split_kblocks", "m2l_kernel", "nodes",
-                               "m2l_svd_tol") if k in wl}
+                               "m2l_svd_tol", "refine_points") if k in wl}
 
 
 def oracle_node_error(wl, name, F, nodes, segs, b):
@@ -749,6 +757,8 @@ def main():
     ap.add_argument("--m2l-split-kblocks", type=int, default=-1, help="override the residual K blocks (fmm options)")
     ap.add_argument("--m2l-kernel", type=int, default=-1, help="override the M2L tile form (fmm options)")
     ap.add_argument("--m2l-svd-tol", type=float, default=-1.0, help="override the M2L compression (fmm options)")
+    ap.add_argument("--refine-points", type=int, default=-1,
+                    help="override the adaptive tree's split threshold (0: uniform tree; fmm options)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.p:
@@ -767,6 +777,8 @@ def main():
         wl["m2l_kernel"] = args.m2l_kernel
     if args.m2l_svd_tol >= 0:
         wl["m2l_svd_tol"] = args.m2l_svd_tol
+    if args.refine_points >= 0:
+        wl["refine_points"] = args.refine_points
     if args.impl == "reference":
         run_reference(args, wl)
     elif wl.get("batch"):

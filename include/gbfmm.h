@@ -142,6 +142,14 @@ typedef struct {
                               U^T T_o R, and expands the local values S = U S'.  The bases and
                               operators are built in FP64 at fmm_set_material; m2l_basis is
                               ignored.  0 = off (fmm_default_options). */
+    int refine_points;     /* MIXED with the compressed M2L and the unit-circle h: > 0 makes
+                              the tree adaptive -- every leaf holding more than this many Gauss
+                              points is split once more (one level below the leaves).  Two
+                              adjacent split leaves interact through their children: adjacent
+                              children directly, the others by an M2L one level down; all
+                              other adjacent leaves directly; points of split leaves take their
+                              child's local values.  Nodal forces only (fmm_eval_stress keeps
+                              the uniform tree).  0 = off (fmm_default_options). */
 } gbfmm_options;
 
 typedef struct gbfmm_ctx gbfmm_ctx;
@@ -245,9 +253,11 @@ int fmm_launch_count(const gbfmm_ctx *ctx, int64_t *count);
 /* Work of one pass over the built tree, for roofline accounting
  * (host output, 4 int64): [0] near-field point pairs evaluated by the
  * self-evaluation of fmm_eval_nodal_forces (target x source point pairs in
- * neighbouring leaves, own-segment pairs excluded), [1] M2L cell pairs
- * (target cell, interaction-list cell) with both non-empty, [2] occupied
- * leaves, [3] Gauss points.  Launches two small kernels and synchronises.
+ * neighbouring leaves, own-segment pairs excluded; with refine_points > 0,
+ * pairs between non-adjacent children of two split leaves excluded too),
+ * [1] M2L cell pairs (target cell, interaction-list cell) with both
+ * non-empty, the split leaves' children included, [2] occupied leaves,
+ * [3] Gauss points.  Launches a few small kernels and synchronises.
  * Errors: NOT_BUILT, CUDA. */
 int fmm_work_counts(gbfmm_ctx *ctx, int64_t *counts);
 

@@ -52,6 +52,19 @@ static void free_tree(gbfmm_ctx *ctx) {
     release(ctx->d_part);
     release(ctx->d_bad);
     release(ctx->d_yrel);
+    {
+        auto &RF = ctx->rf;
+        release(RF.child_of);
+        release(RF.pfine);
+        release(RF.ref_start);
+        release(RF.ref_leaf);
+        release(RF.child_start);
+        release(RF.W7);
+        release(RF.S7);
+        release(RF.Wc7);
+        release(RF.Sc7);
+        RF.cap_N = RF.cap_leaves = RF.cap_ref = RF.cap_cells = 0;
+    }
     ctx->mx_cap_N = ctx->mx_cap_cells = 0;
     ctx->cap_N = ctx->cap_segs = ctx->cap_cells = ctx->cap_leaves = 0;
     ctx->built = false;
@@ -76,7 +89,10 @@ static int ensure_tree_buffers(gbfmm_ctx *ctx) {
     if (int rc = grow_dev(ctx, ctx->cap_segs, ns, {{(void **)&ctx->d_len0, ns * sizeof(double)}}, "segments"))
         return rc;
     {
-        GrowBuf b[3] = {{(void **)&ctx->d_tmp_i, 2 * nc * sizeof(int)},
+        // occupancy scratch: sources and targets per cell (with the adaptive tree, sources of
+        // one more level: the children of split leaves)
+        const int64_t n_occ = 2 * (ctx->rf.on ? cell_base(ctx->L + 1) : nc);
+        GrowBuf b[3] = {{(void **)&ctx->d_tmp_i, n_occ * sizeof(int)},
                         {(void **)&ctx->d_W, nc * P3 * 9 * sizeof(double)},
                         {(void **)&ctx->d_S, nc * P3 * 6 * sizeof(double)}};
         if (int rc = grow_dev(ctx, ctx->cap_cells, nc, b, w64 ? 3 : 1, "cells")) return rc;
@@ -90,6 +106,24 @@ static int ensure_tree_buffers(gbfmm_ctx *ctx) {
         return rc;
     if (!ctx->d_part) CK(cudaMalloc(&ctx->d_part, 512 * 6 * sizeof(double)));
     if (!ctx->d_bad) CK(cudaMalloc(&ctx->d_bad, sizeof(int)));
+    if (ctx->rf.on) {
+        // adaptive tree: split leaves hold more than refine_points points each, so there are
+        // at most N / (refine_points + 1) of them
+        auto &RF = ctx->rf;
+        const int64_t cap_ref = N / (ctx->opt.refine_points + 1) + 1;
+        if (int rc = grow_dev(ctx, RF.cap_N, N,
+                              {{(void **)&RF.child_of, size_t(N)}, {(void **)&RF.pfine, N * sizeof(int)}},
+                              "adaptive-tree points"))
+            return rc;
+        if (int rc = grow_dev(ctx, RF.cap_leaves, nl, {{(void **)&RF.ref_start, (nl + 1) * sizeof(int)}},
+                              "adaptive-tree leaves"))
+            return rc;
+        if (int rc = grow_dev(ctx, RF.cap_ref, cap_ref,
+                              {{(void **)&RF.ref_leaf, cap_ref * sizeof(int)},
+                               {(void **)&RF.child_start, 9 * cap_ref * sizeof(int)}},
+                              "adaptive-tree split leaves"))
+            return rc;
+    }
     return GBFMM_OK;
 }
 
@@ -128,8 +162,14 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
     if ((opt->m2l_svd_tol > 0.0 || opt->nodes == GBFMM_NODES_CHEBYSHEV) &&
         (opt->precision != GBFMM_MIXED || opt->m2l_svd_tol <= 0.0))
         return GBFMM_ERR_INVALID_ARG;
+    // the adaptive tree runs its extra level through the compressed M2L and its near
+    // field through the symmetric kernel of the unit-circle h
+    if (opt->refine_points < 0 ||
+        (opt->refine_points > 0 && (opt->m2l_svd_tol <= 0.0 || opt->h_mode != GBFMM_H_CIRCLE)))
+        return GBFMM_ERR_INVALID_ARG;
     gbfmm_ctx *ctx = new gbfmm_ctx();
     ctx->opt = *opt;
+    ctx->rf.on = opt->refine_points > 0 ? 1 : 0;
     if (ctx->opt.near_fp64 == 0.0) ctx->opt.near_fp64 = 2.0;
     if (ctx->opt.leaf_segments == 0) ctx->opt.leaf_segments = 32;
     ctx->stream = (cudaStream_t)stream;
@@ -198,6 +238,8 @@ extern "C" int fmm_build_tree(gbfmm_ctx *ctx, int64_t n_nodes, const double *nod
         return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_build_tree: empty network or null pointer");
     const int64_t N = n_segs * ctx->opt.n_gauss;
     if (N >= (int64_t(1) << 31)) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_build_tree: too many points");
+    if (ctx->rf.on && N >= (int64_t(1) << 28))
+        return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_build_tree: adaptive tree limited to 2^28 points");
     ctx->built = false;
     ctx->n_nodes = n_nodes;
     ctx->n_segs = n_segs;
@@ -207,6 +249,8 @@ extern "C" int fmm_build_tree(gbfmm_ctx *ctx, int64_t n_nodes, const double *nod
     ctx->burgers = burgers;
     ctx->L = choose_levels(ctx, n_segs);
     const int L = ctx->L;
+    if (ctx->rf.on && L + 1 > GB_TC_MAXLEV)
+        return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_build_tree: adaptive tree needs levels <= 7");
     ctx->n_leaves = int64_t(1) << (3 * (L - 1));
     ctx->n_cells = cell_base(L);
     int rc = ensure_tree_buffers(ctx);
@@ -243,11 +287,15 @@ uint64_t layout_hash(const gbfmm_ctx *c) {
                           c->tc.d_flags, c->tc.d_pos, c->tc.d_list, c->tc.d_seg, c->tc.d_wmax, c->mlp.theta, c->mlp.theta_h,
                           c->mlp.scale, c->mlp.d_binmask, c->nw.items, c->nw.sorted, c->nw.keys, c->nw.cnt,
                           c->nw.key_of, c->nw.off, c->nw.misc, c->nw.pitems, c->nw.psorted,
-                          c->nw.pkeys, c->nw.pmisc, c->nw.part};
+                          c->nw.pkeys, c->nw.pmisc, c->nw.part, c->tc.Uh, c->tc.Ul, c->tc.Rh, c->tc.Rl,
+                          c->tc.Xh, c->tc.Xl, c->tc.d_scal, c->tc.d_bits, c->tc.Wc, c->tc.Sc, c->tc.blas_ws,
+                          c->rf.child_of, c->rf.ref_start, c->rf.ref_leaf, c->rf.child_start, c->rf.pfine,
+                          c->rf.W7, c->rf.S7, c->rf.Wc7, c->rf.Sc7};
     mix(ptrs, sizeof(ptrs));
     v(c->mat.mode), v(c->mat.Q), v(c->mat.cubic), v(c->tc.n_work), v(c->tc.split), v(c->tc.tf32);
     mix(c->tc.wofs, sizeof(c->tc.wofs));
     v(c->tc.n_slots), v(c->tc.n_seg), v(c->nw.cap), v(c->nw.cap_leaves), v(c->mlp.trained);
+    v(c->tc.r1), v(c->tc.r2), v(c->rf.cap_ref), v(c->rf.n_ref_host), v(c->tc.blas);
     return h;
 }
 

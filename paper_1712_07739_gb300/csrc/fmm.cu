@@ -73,6 +73,10 @@ __global__ void k_occ_up(int level, int *__restrict__ occ) {
 // one block per leaf; thread m accumulates W[m][0..8].  The local
 // coordinate of a point is formed in FP64; the basis and sums in R.
 template <typename R>
+__device__ void p2m_range(int p, int nodes, int b, int e, const double c0[3], double ih, const double *__restrict__ y,
+                          const double *__restrict__ q, R *__restrict__ Wc);
+
+template <typename R>
 __global__ void k_p2m(int p, int nodes, int L, const TreeBox *__restrict__ box, const int *__restrict__ start,
                       const double *__restrict__ y, const double *__restrict__ q, R *__restrict__ W) {
     const int64_t leaf = blockIdx.x;
@@ -89,6 +93,43 @@ __global__ void k_p2m(int p, int nodes, int L, const TreeBox *__restrict__ box, 
     const double h = box->H / nl;
     const double ih = double(nl) / box->H;
     const double c0[3] = {box->origin[0] + cx * h, box->origin[1] + cy * h, box->origin[2] + cz * h};
+    p2m_range<R>(p, nodes, b, e, c0, ih, y, q, Wc);
+}
+
+// adaptive tree: P2M of the children of split leaves, one block per child cell 8 r + c
+// (compact rows; empty and absent children get zeros)
+template <typename R>
+__global__ void k_p2m_fine(int p, int nodes, int L, const TreeBox *__restrict__ box, const int *__restrict__ n_ref,
+                           const int *__restrict__ ref_leaf, const int *__restrict__ child_start,
+                           const double *__restrict__ y, const double *__restrict__ q, R *__restrict__ W7) {
+    const int64_t f = blockIdx.x;
+    const int r = int(f >> 3), c = int(f & 7);
+    const int P3 = p * p * p;
+    R *Wc = W7 + f * int64_t(P3) * 9;
+    int b = 0, e = 0;
+    if (r < *n_ref) {
+        b = child_start[9 * r + c];
+        e = child_start[9 * r + c + 1];
+    }
+    if (b == e) {
+        for (int i = threadIdx.x; i < P3 * 9; i += blockDim.x) Wc[i] = R(0);
+        return;
+    }
+    const int nl = 1 << (L - 1);
+    int cx, cy, cz;
+    cell_xyz(ref_leaf[r], nl, cx, cy, cz);
+    const double h = box->H / (2 * nl);
+    const double ih = double(2 * nl) / box->H;
+    const double c0[3] = {box->origin[0] + (2 * cx + (c & 1)) * h, box->origin[1] + (2 * cy + ((c >> 1) & 1)) * h,
+                          box->origin[2] + (2 * cz + (c >> 2)) * h};
+    p2m_range<R>(p, nodes, b, e, c0, ih, y, q, Wc);
+}
+
+// W[m][wr] = sum over the points b..e of L_m(local position) q_wr (Sec. 4.3, P2M)
+template <typename R>
+__device__ void p2m_range(int p, int nodes, int b, int e, const double c0[3], double ih, const double *__restrict__ y,
+                          const double *__restrict__ q, R *__restrict__ Wc) {
+    const int P3 = p * p * p;
     constexpr int CH = 64;
     __shared__ R sb[CH][3][GB_MAXP];
     __shared__ R sq[CH][9];
@@ -222,6 +263,43 @@ __global__ void k_l2l(int p, int level, Transfer tr, const int *__restrict__ toc
     transfer3<6, R>(p, tr.M[x & 1], tr.M[y & 1], tr.M[z & 1], false, in, t1);
     R *Sc = S + (cell_base_d(level) + cell) * int64_t(P3) * 6;
     for (int i = threadIdx.x; i < P3 * 6; i += blockDim.x) Sc[i] += t1[i];
+}
+
+// adaptive tree: occupancy of the children of split leaves at level L (one below the
+// leaves), into occL (the level's part of the occupancy array, zeroed before)
+__global__ void k_fine_occ(int64_t n_fine, int L, const int *__restrict__ n_ref, const int *__restrict__ ref_leaf,
+                           const int *__restrict__ child_start, int *__restrict__ occL) {
+    const int64_t f = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (f >= n_fine) return;
+    const int r = int(f >> 3), c = int(f & 7);
+    if (r >= *n_ref) return;
+    const int cnt = child_start[9 * r + c + 1] - child_start[9 * r + c];
+    if (cnt == 0) return;
+    const int nl = 1 << (L - 1), nf = 2 * nl;
+    int x, y, z;
+    cell_xyz(ref_leaf[r], nl, x, y, z);
+    const int64_t lin = (int64_t(2 * z + (c >> 2)) * nf + (2 * y + ((c >> 1) & 1))) * nf + (2 * x + (c & 1));
+    occL[lin] = cnt;
+}
+
+// adaptive tree: children's local values += their split parent's, interpolated (L2L),
+// one block per child cell 8 r + c that holds points
+template <typename R>
+__global__ void k_l2l_fine(int p, int L, Transfer tr, const int *__restrict__ n_ref, const int *__restrict__ ref_leaf,
+                           const int *__restrict__ child_start, const R *__restrict__ S, R *__restrict__ S7) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    R *in = reinterpret_cast<R *>(sm_raw);
+    const int64_t f = blockIdx.x;
+    const int r = int(f >> 3), c = int(f & 7);
+    if (r >= *n_ref || child_start[9 * r + c + 1] == child_start[9 * r + c]) return;
+    const int P3 = p * p * p;
+    R *t1 = in + P3 * 6;
+    const R *Sp = S + (cell_base_d(L - 1) + ref_leaf[r]) * int64_t(P3) * 6;
+    for (int i = threadIdx.x; i < P3 * 6; i += blockDim.x) in[i] = Sp[i];
+    __syncthreads();
+    transfer3<6, R>(p, tr.M[c & 1], tr.M[(c >> 1) & 1], tr.M[c >> 2], false, in, t1);
+    R *out = S7 + f * int64_t(P3) * 6;
+    for (int i = threadIdx.x; i < P3 * 6; i += blockDim.x) out[i] += t1[i];
 }
 
 // Parent weights at `level` from its 8 children at level + 1 (Sec. 3.2,
@@ -634,38 +712,60 @@ void compute_occ(gbfmm_ctx *ctx, const int *start, int *occ) {
 namespace {
 // near pairs per target point: sources in the 27 neighbour leaves minus the
 // points of its own segment that lie there
+// (adaptive tree: a point of a split leaf meets, in another split leaf, the points of the
+// children adjacent to its own child only)
+__device__ inline bool fine_adjacent(int ox, int oy, int oz, int ca, int cb) {
+    return abs(2 * ox + (cb & 1) - (ca & 1)) <= 1 && abs(2 * oy + ((cb >> 1) & 1) - ((ca >> 1) & 1)) <= 1 &&
+           abs(2 * oz + (cb >> 2) - (ca >> 2)) <= 1;
+}
 __global__ void k_count_near(int64_t N, int L, int n_g, const int *__restrict__ start, const int *__restrict__ pleaf,
                              const int64_t *__restrict__ sid, const int *__restrict__ pos,
-                             unsigned long long *__restrict__ out) {
+                             const int *__restrict__ ref_start, const int *__restrict__ child_start,
+                             const int *__restrict__ pfine, unsigned long long *__restrict__ out) {
     int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     unsigned long long c = 0;
     if (i < N) {
         const int nl = 1 << (L - 1);
         int bx, by, bz;
-        cell_xyz(pleaf[i], nl, bx, by, bz);
+        const int Bl = pleaf[i];
+        cell_xyz(Bl, nl, bx, by, bz);
+        const int fi = pfine ? pfine[i] : -1;
         for (int nb = 0; nb < 27; ++nb) {
             int ax = bx + nb % 3 - 1, ay = by + (nb / 3) % 3 - 1, az = bz + nb / 9 - 1;
             if (ax < 0 || ay < 0 || az < 0 || ax >= nl || ay >= nl || az >= nl) continue;
             int64_t A = (int64_t(az) * nl + ay) * nl + ax;
-            c += start[A + 1] - start[A];
+            if (fi >= 0 && A != Bl && ref_start[A + 1] > ref_start[A]) {
+                const int rA = ref_start[A];
+                for (int cb = 0; cb < 8; ++cb)
+                    if (fine_adjacent(ax - bx, ay - by, az - bz, fi & 7, cb))
+                        c += child_start[9 * rA + cb + 1] - child_start[9 * rA + cb];
+            } else {
+                c += start[A + 1] - start[A];
+            }
         }
         const int64_t s = sid[i];
         for (int g = 0; g < n_g; ++g) {
+            const int j = pos[s * n_g + g];
             int ox, oy, oz;
-            cell_xyz(pleaf[pos[s * n_g + g]], nl, ox, oy, oz);
-            if (abs(ox - bx) <= 1 && abs(oy - by) <= 1 && abs(oz - bz) <= 1) --c;
+            cell_xyz(pleaf[j], nl, ox, oy, oz);
+            if (abs(ox - bx) > 1 || abs(oy - by) > 1 || abs(oz - bz) > 1) continue;
+            const int fj = pfine ? pfine[j] : -1;
+            if (fi >= 0 && fj >= 0 && pleaf[j] != Bl && !fine_adjacent(ox - bx, oy - by, oz - bz, fi & 7, fj & 7))
+                continue;  // not a near pair of the adaptive tree
+            --c;
         }
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
-__global__ void k_count_m2l(int L, const int *__restrict__ occ, unsigned long long *__restrict__ out) {
+// levels 2 .. Lm - 1 (Lm = L + 1 adds the adaptive tree's children)
+__global__ void k_count_m2l(int L, int Lm, const int *__restrict__ occ, unsigned long long *__restrict__ out) {
     int64_t g = cell_base_d(2) + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     unsigned long long c = 0, leaves = 0;
-    if (g < cell_base_d(L)) {
+    if (g < cell_base_d(Lm)) {
         int lev = 2;
-        while (lev + 1 < L && g >= cell_base_d(lev + 1)) ++lev;
+        while (lev + 1 < Lm && g >= cell_base_d(lev + 1)) ++lev;
         const int n = 1 << lev;
         int bx, by, bz;
         cell_xyz(g - cell_base_d(lev), n, bx, by, bz);
@@ -699,12 +799,24 @@ int work_counts(gbfmm_ctx *ctx, int64_t *res) {
     CK(cudaMallocAsync(&d, 4 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), st));
     int *occ = ctx->d_tmp_i;
+    const int L = ctx->L;
     compute_occ(ctx, ctx->d_leaf_start, occ);
+    const auto &RF = ctx->rf;
+    const bool fine = RF.on && L >= 3 && RF.fine_rows() > 0;
+    if (fine) {  // the children of split leaves at level L
+        const int64_t n_fine = RF.fine_rows();
+        CK(cudaMemsetAsync(occ + cell_base(L), 0, (cell_base(L + 1) - cell_base(L)) * sizeof(int), st));
+        ++ctx->launches;
+        k_fine_occ<<<nblk(n_fine, 256), 256, 0, st>>>(n_fine, L, RF.ref_start + ctx->n_leaves, RF.ref_leaf,
+                                                      RF.child_start, occ + cell_base(L));
+    }
     ++ctx->launches;
-    k_count_near<<<nblk(ctx->N, 256), 256, 0, st>>>(ctx->N, ctx->L, ctx->opt.n_gauss, ctx->d_leaf_start,
-                                                     ctx->d_pleaf, ctx->d_sid, ctx->d_pos, d);
+    k_count_near<<<nblk(ctx->N, 256), 256, 0, st>>>(ctx->N, L, ctx->opt.n_gauss, ctx->d_leaf_start, ctx->d_pleaf,
+                                                     ctx->d_sid, ctx->d_pos, fine ? RF.ref_start : nullptr,
+                                                     RF.child_start, fine ? RF.pfine : nullptr, d);
     ++ctx->launches;
-    k_count_m2l<<<nblk(ctx->n_cells - cell_base(2), 256), 256, 0, st>>>(ctx->L, occ, d);
+    const int Lm = fine ? L + 1 : L;
+    k_count_m2l<<<nblk(cell_base(Lm) - cell_base(2), 256), 256, 0, st>>>(L, Lm, occ, d);
     unsigned long long h[4];
     CK(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
     CK(cudaFreeAsync(d, st));
@@ -877,6 +989,12 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
     int *tocc = free_targets ? occ + ctx->n_cells : occ;
     const int *tstart = free_targets ? ctx->d_t_start : ctx->d_leaf_start;
     Transfer tr = make_transfer(p, ctx->opt.nodes);
+    // adaptive tree: the children of split leaves take part in nodal-force passes (free
+    // targets keep the uniform tree, whose near field covers whole leaves)
+    auto &RF = ctx->rf;
+    const int64_t n_fine = RF.fine_rows();
+    const bool fine = RF.on && !free_targets && L >= 3 && n_fine > 0;
+    const int *n_ref = RF.ref_start ? RF.ref_start + nl : nullptr;
     timer_mark(ctx);
     if (int rc = near_prepare(ctx)) return rc;
     ++ctx->launches;
@@ -901,11 +1019,21 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
             else
                 k_m2m_merge<float><<<g, 256, size_t(4) * P3 * 9 * sizeof(float), st>>>(p, lev, tr, occ, ctx->d_Wf);
         }
+        if (fine) {
+            // the children of split leaves: multipole values and their occupancy at level L
+            ctx->launches += 2;
+            k_p2m_fine<float><<<unsigned(n_fine), 256, 0, st>>>(p, ctx->opt.nodes, L, ctx->d_box, n_ref, RF.ref_leaf,
+                                                                RF.child_start, ctx->d_y, ctx->d_q, RF.W7);
+            CK(cudaMemsetAsync(occ + cell_base(L), 0, (cell_base(L + 1) - cell_base(L)) * sizeof(int), st));
+            k_fine_occ<<<nblk(n_fine, 256), 256, 0, st>>>(n_fine, L, n_ref, RF.ref_leaf, RF.child_start,
+                                                          occ + cell_base(L));
+        }
         CK(cudaGetLastError());
     }
     timer_mark(ctx);
     if (L >= 3) {
-        int rc = m2l_tc_run(ctx, ctx->d_Wf, t64 ? ctx->d_W : nullptr, occ, tocc, ctx->d_Sf, t64 ? ctx->d_S : nullptr);
+        int rc = m2l_tc_run(ctx, ctx->d_Wf, t64 ? ctx->d_W : nullptr, occ, tocc, ctx->d_Sf, t64 ? ctx->d_S : nullptr,
+                            fine);
         if (rc) return rc;
     }
     timer_mark(ctx);
@@ -919,6 +1047,13 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
                 k_l2l_split<float><<<g / 8, 256, size_t(7) * P3 * 6 * sizeof(float), st>>>(p, lev, tr, tocc,
                                                                                           ctx->d_Sf);
         }
+        CK(cudaGetLastError());
+    }
+    if (fine) {
+        // the children's local values (the level-L M2L, written by m2l_tc_run) += the parent's
+        ++ctx->launches;
+        k_l2l_fine<float><<<unsigned(n_fine), 256, size_t(2) * P3 * 6 * sizeof(float), st>>>(
+            p, L, tr, n_ref, RF.ref_leaf, RF.child_start, ctx->d_Sf, RF.S7);
         CK(cudaGetLastError());
     }
     if (t64 && L >= 3) {
@@ -946,5 +1081,7 @@ int mixed_kernel_attrs(gbfmm_ctx *ctx) {
                             int(4 * P3 * 9 * sizeof(float))));
     CK(cudaFuncSetAttribute(k_l2l_split<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             int(7 * P3 * 6 * sizeof(float))));
+    CK(cudaFuncSetAttribute(k_l2l_fine<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            int(2 * P3 * 6 * sizeof(float))));
     return GBFMM_OK;
 }

@@ -123,6 +123,28 @@ struct gbfmm_ctx {
     const double *burgers = nullptr;
     const double *node_xyz = nullptr;
 
+    // adaptive tree (gbfmm_options.refine_points > 0): every leaf holding more points is
+    // split once more; sizes are bounded by N / (refine_points + 1) split leaves, so the
+    // build needs no host read-back
+    struct Refine {
+        int on = 0;
+        int64_t cap_ref = 0;                   // split leaves the buffers hold
+        int64_t n_ref_host = -1;               // split leaves of the last validated build (-1: not read)
+        int64_t cap_N = 0, cap_leaves = 0, cap_cells = 0;
+        unsigned char *child_of = nullptr;     // [N] original order: child (0..7) of the point's leaf
+        int *ref_start = nullptr;              // [n_leaves + 1] scan of the split flags: leaf -> split index
+        int *ref_leaf = nullptr;               // [cap_ref] split index -> leaf
+        int *child_start = nullptr;            // [cap_ref][9] sorted-point ranges of the children
+        int *pfine = nullptr;                  // [N] sorted point -> child cell 8 r + c, or -1
+        float *W7 = nullptr;                   // [8 cap_ref][9 p^3] children's multipole values
+        float *S7 = nullptr;                   // [8 cap_ref][6 p^3] children's local values
+        float *Wc7 = nullptr;                  // [8 cap_ref][r2] compressed multipole values
+        float *Sc7 = nullptr;                  // [8 cap_ref][r1] compressed local values
+        // child cells the fine-level launches cover: the split leaves a validated build read
+        // back, else the capacity (kernels skip the rows past the device count)
+        int64_t fine_rows() const { return 8 * (n_ref_host >= 0 ? n_ref_host : cap_ref); }
+    } rf;
+
     // per-eval buffers
     double *d_P = nullptr;     // [N][108] precontracted source tensors (FP64)
     float *d_Pf = nullptr;     // [N][108] FP32 copy for the mixed path

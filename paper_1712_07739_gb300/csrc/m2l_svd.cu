@@ -450,16 +450,28 @@ int svd_operators(gbfmm_ctx *ctx, const int *d_off, const int *d_lo, int n_off) 
 
 int svd_prepare(gbfmm_ctx *ctx) {
     TcPlan &T = ctx->tc;
+    auto &RF = ctx->rf;
     const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p;
     const int64_t per = std::max(T.r1, T.r2);
-    if (int rc = grow_dev(ctx, T.c_cap, ctx->n_cells * per,
-                          {{(void **)&T.Wc, size_t(ctx->n_cells) * per * sizeof(float)},
-                           {(void **)&T.Sc, size_t(ctx->n_cells) * per * sizeof(float)}},
+    // global rows of every M2L level (one more with the adaptive tree's children)
+    const int64_t rows = cell_base(ctx->L + (RF.on ? 1 : 0));
+    if (int rc = grow_dev(ctx, T.c_cap, rows * per,
+                          {{(void **)&T.Wc, size_t(rows) * per * sizeof(float)},
+                           {(void **)&T.Sc, size_t(rows) * per * sizeof(float)}},
                           "compressed M2L values"))
         return rc;
-    // one level's transform input split into FP16 hi + lo (the deepest level is the largest)
+    const int64_t n_fine = RF.on ? 8 * RF.cap_ref : 0;
+    if (RF.on)
+        if (int rc = grow_dev(ctx, RF.cap_cells, n_fine * (15 * P3 + T.r1 + T.r2),
+                              {{(void **)&RF.W7, size_t(n_fine) * 9 * P3 * sizeof(float)},
+                               {(void **)&RF.S7, size_t(n_fine) * 6 * P3 * sizeof(float)},
+                               {(void **)&RF.Wc7, size_t(n_fine) * T.r2 * sizeof(float)},
+                               {(void **)&RF.Sc7, size_t(n_fine) * T.r1 * sizeof(float)}},
+                              "adaptive-tree children"))
+            return rc;
+    // one level's transform input split into FP16 hi + lo (the deepest level, or the children)
     const int64_t xrow = std::max<int64_t>(pad8(9 * P3), T.r1);
-    const int64_t need = (int64_t(1) << (3 * (ctx->L - 1))) * xrow;
+    const int64_t need = std::max<int64_t>(int64_t(1) << (3 * (ctx->L - 1)), n_fine) * xrow;
     if (int rc = grow_dev(ctx, T.x_cap, need,
                           {{&T.Xh, size_t(need) * sizeof(__half)}, {&T.Xl, size_t(need) * sizeof(__half)}},
                           "compressed M2L transform operands"))
@@ -509,8 +521,36 @@ static int split_level(gbfmm_ctx *ctx, const float *src, int64_t rows, int n, in
     return GBFMM_OK;
 }
 
-int svd_transform_w(gbfmm_ctx *ctx, const float *Wf) {
+// adaptive tree: rows of the children's compact arrays [8 r + c][rowlen] to and from the
+// global rows of level L (gather: children without points, which the M2L did not write,
+// and unused capacity read zeros)
+__global__ void k_fine_rows(int64_t n_fine, int L, const int *__restrict__ n_ref, const int *__restrict__ ref_leaf,
+                            const int *__restrict__ child_start, int rowlen, float *__restrict__ compact,
+                            float *__restrict__ global, int gather) {
+    const int nl = 1 << (L - 1), nf = 2 * nl;
+    const int nr = *n_ref;
+    const int64_t total = n_fine * rowlen;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t f = idx / rowlen;
+        const int k = int(idx - f * rowlen), r = int(f >> 3), c = int(f & 7);
+        if (r >= nr || child_start[9 * r + c + 1] == child_start[9 * r + c]) {
+            if (gather) compact[idx] = 0.f;
+            continue;
+        }
+        const int leaf = ref_leaf[r];
+        const int x = leaf % nl, y = (leaf / nl) % nl, z = leaf / (nl * nl);
+        const int64_t lin = (int64_t(2 * z + (c >> 2)) * nf + (2 * y + ((c >> 1) & 1))) * nf + (2 * x + (c & 1));
+        if (gather)
+            compact[idx] = global[lin * rowlen + k];
+        else
+            global[lin * rowlen + k] = compact[idx];
+    }
+}
+
+int svd_transform_w(gbfmm_ctx *ctx, const float *Wf, bool fine) {
     TcPlan &T = ctx->tc;
+    auto &RF = ctx->rf;
     const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p, ns = 9 * P3, lds = pad8(ns);
     if (int rc = ensure_blas(ctx)) return rc;
     // W'^T (r2 x cells) = R^T (r2 x 9 p^3) W^T (9 p^3 x cells), level by level (each its own scale)
@@ -521,11 +561,25 @@ int svd_transform_w(gbfmm_ctx *ctx, const float *Wf) {
                                 T.Wc + row0 * T.r2, T.r2))
             return rc;
     }
+    if (fine) {
+        // the children of split leaves, compact, then into the global rows of level L
+        const int l = ctx->L;
+        const int64_t n_fine = RF.fine_rows();
+        if (int rc = split_level(ctx, RF.W7, n_fine, ns, lds, l, T.sR)) return rc;
+        if (int rc = split_gemm(ctx, CUBLAS_OP_T, T.r2, n_fine, lds, T.Rh, T.Rl, lds, lds, T.d_scal + 2 + l, RF.Wc7,
+                                T.r2))
+            return rc;
+        ++ctx->launches;
+        k_fine_rows<<<unsigned(std::min<int64_t>(nblk(n_fine * T.r2, 256), 16 * 152)), 256, 0, ctx->stream>>>(
+            n_fine, l, RF.ref_start + ctx->n_leaves, RF.ref_leaf, RF.child_start, T.r2, RF.Wc7, T.Wc + cell_base(l) * T.r2, 0);
+        CK(cudaGetLastError());
+    }
     return GBFMM_OK;
 }
 
-int svd_expand_s(gbfmm_ctx *ctx, float *Sf) {
+int svd_expand_s(gbfmm_ctx *ctx, float *Sf, bool fine) {
     TcPlan &T = ctx->tc;
+    auto &RF = ctx->rf;
     const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p, nt = 6 * P3;
     if (int rc = ensure_blas(ctx)) return rc;
     // S^T (6 p^3 x cells) = U (6 p^3 x r1) S'^T (r1 x cells), level by level
@@ -534,6 +588,19 @@ int svd_expand_s(gbfmm_ctx *ctx, float *Sf) {
         if (int rc = split_level(ctx, T.Sc + row0 * T.r1, rows, T.r1, T.r1, GB_TC_MAXLEV + l, T.sU)) return rc;
         if (int rc = split_gemm(ctx, CUBLAS_OP_N, nt, rows, T.r1, T.Uh, T.Ul, pad8(nt), T.r1,
                                 T.d_scal + 2 + GB_TC_MAXLEV + l, Sf + row0 * nt, nt))
+            return rc;
+    }
+    if (fine) {
+        // the children's compressed local values gathered from level L, expanded into S7
+        const int l = ctx->L;
+        const int64_t n_fine = RF.fine_rows();
+        ++ctx->launches;
+        k_fine_rows<<<unsigned(std::min<int64_t>(nblk(n_fine * T.r1, 256), 16 * 152)), 256, 0, ctx->stream>>>(
+            n_fine, l, RF.ref_start + ctx->n_leaves, RF.ref_leaf, RF.child_start, T.r1, RF.Sc7, T.Sc + cell_base(l) * T.r1, 1);
+        CK(cudaGetLastError());
+        if (int rc = split_level(ctx, RF.Sc7, n_fine, T.r1, T.r1, GB_TC_MAXLEV + l, T.sU)) return rc;
+        if (int rc = split_gemm(ctx, CUBLAS_OP_N, nt, n_fine, T.r1, T.Uh, T.Ul, pad8(nt), T.r1,
+                                T.d_scal + 2 + GB_TC_MAXLEV + l, RF.S7, nt))
             return rc;
     }
     return GBFMM_OK;

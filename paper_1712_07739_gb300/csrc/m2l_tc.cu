@@ -1203,7 +1203,7 @@ static int encode(gbfmm_ctx *ctx, CUtensorMap *tm, void *base, int rank, const c
 // Per-tree buffers: packed W (hi / lo), tensor maps, work list.
 int m2l_tc_prepare(gbfmm_ctx *ctx) {
     TcPlan &T = ctx->tc;
-    const int L = ctx->L;
+    const int L = ctx->L + (ctx->rf.on ? 1 : 0);  // the adaptive tree's children: one more M2L level
     if (L - 1 >= GB_TC_MAXLEV) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "tensor-core M2L: too many levels");
     int64_t tot = 0;
     for (int l = 2; l < L; ++l) {
@@ -1231,9 +1231,11 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
 }
 
 int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *occ, const int *tocc, float *Sf,
-               double *S64) {
+               double *S64, bool fine) {
     TcPlan &T = ctx->tc;
-    const int L = ctx->L, p = ctx->opt.p, P3 = p * p * p;
+    // with the adaptive tree's children the M2L runs one level deeper (level ctx->L: the
+    // children of split leaves, their compressed values gathered and scattered by svd_*)
+    const int L = ctx->L + (fine ? 1 : 0), p = ctx->opt.p, P3 = p * p * p;
     M2LParams prm;  // copied by value into the launch (kernel parameter space)
     std::memset(&prm, 0, sizeof(prm));
     if (T.fp16) CK(cudaMemsetAsync(T.d_wmax, 0, GB_TC_MAXLEV * sizeof(unsigned), ctx->stream));
@@ -1241,7 +1243,7 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
     const int split_levels = ctx->opt.m2l_split_levels ? ctx->opt.m2l_split_levels : ~0;
     // compressed M2L: every cell's multipole values -> r2 coefficients R^T W first
     if (T.svd)
-        if (int rc = svd_transform_w(ctx, Wf)) return rc;
+        if (int rc = svd_transform_w(ctx, Wf, fine)) return rc;
     const float *Wsrc = T.svd ? T.Wc : Wf;
     const int kv = T.svd ? T.r2 : 9 * P3;  // valid values per cell row
     for (int l = 2; l < L; ++l) {
@@ -1295,6 +1297,9 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
         ++ctx->launches;
         k_mb_flags<<<nblk(int64_t(1) << (3 * l), 256), 256, 0, ctx->stream>>>(l, tocc, T.d_flags);
     }
+    if (ctx->rf.on && !fine)  // the slots of the children's level hold no targets in this pass
+        CK(cudaMemsetAsync(T.d_flags + slot_base(L), 0, (slot_base(L + 1) - slot_base(L)) * sizeof(int),
+                           ctx->stream));
     ctx->launches += 3;
     k_scan_flags<<<1, 1024, 0, ctx->stream>>>(int(T.n_slots), T.d_flags, T.d_pos);
     k_mb_list<<<nblk(T.n_slots, 256), 256, 0, ctx->stream>>>(int(T.n_slots), L, T.d_flags, T.d_pos, T.d_list);
@@ -1352,11 +1357,11 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
         prm.accumulate = c > 0 ? 1 : 0;
         if (c > 0) prm.drop_first = 0;
         ++ctx->launches;
-        kern<<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, T.n_seg, T.d_list, occ, tocc, ctx->d_box, Sout, S64,
-                                                   T.d_status, stages, T.groups);
+        kern<<<T.n_work, 192, smem, ctx->stream>>>(prm, T.d_seg, 8 * (L - 2), T.d_list, occ, tocc, ctx->d_box, Sout,
+                                                   S64, T.d_status, stages, T.groups);
         CK(cudaGetLastError());
     }
-    if (T.svd) return svd_expand_s(ctx, Sf);  // S = U S'
+    if (T.svd) return svd_expand_s(ctx, Sf, fine);  // S = U S'
     return GBFMM_OK;
 }
 

@@ -65,7 +65,7 @@ int m2l_tc_setup(gbfmm_ctx *ctx);    // operators (per medium and p)
 int m2l_tc_prepare(gbfmm_ctx *ctx);  // per tree
 // W64 / S64 non-null: FP64 multipole values in, FP64 local values out (GBFMM_MIXED_F64T)
 int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *occ, const int *tocc, float *Sf,
-               double *S64);
+               double *S64, bool fine = false);
 void m2l_tc_free(gbfmm_ctx *ctx);
 int m2l_tc_status(gbfmm_ctx *ctx, int *out);
 
@@ -78,6 +78,6 @@ int m2l_tc_status(gbfmm_ctx *ctx, int *out);
 int svd_bases(gbfmm_ctx *ctx);
 int svd_operators(gbfmm_ctx *ctx, const int *d_off, const int *d_lo, int n_off);
 int svd_prepare(gbfmm_ctx *ctx);
-int svd_transform_w(gbfmm_ctx *ctx, const float *Wf);
-int svd_expand_s(gbfmm_ctx *ctx, float *Sf);
+int svd_transform_w(gbfmm_ctx *ctx, const float *Wf, bool fine);
+int svd_expand_s(gbfmm_ctx *ctx, float *Sf, bool fine);
 void svd_free(gbfmm_ctx *ctx, bool borrowed);

@@ -360,7 +360,8 @@ __global__ void __launch_bounds__(SYM_WARPS * 32, SYM_MINB) k_near_sym(
     int L, float near2, const TreeBox *__restrict__ box, const DevMaterial *__restrict__ mat,
     const int *__restrict__ sstart, const float4 *__restrict__ yrel, const double *__restrict__ ys,
     const float *__restrict__ c32, const int64_t *__restrict__ ssid, double *__restrict__ part, int64_t N,
-    const int2 *__restrict__ items, const int *__restrict__ n_items) {
+    const int2 *__restrict__ items, const int *__restrict__ n_items, const int *__restrict__ ref_start,
+    const int *__restrict__ child_start) {
     extern __shared__ __align__(16) float sm_sym[];
     float *wPA = sm_sym + (threadIdx.x / 32) * (32 * 108 + SYM_SCH * 108);  // [32][108]: lanes' own tensors
     float *wPB = wPA + 32 * 108;                                            // [SCH][108] staged sources
@@ -403,18 +404,35 @@ __global__ void __launch_bounds__(SYM_WARPS * 32, SYM_MINB) k_near_sym(
     const int Q = mat->Q;
     const float c12f = float(mat->c12), c44f = float(mat->c44), cdf = float(mat->cd);
     bool first_chunk = true;
-    for (int r0 = sA0, nrem = 0; r0 < sA1; r0 += nrem) {
+    // adaptive tree: two different split leaves interact through their adjacent children
+    // only (the others through the M2L one level down): the targets go child by child and
+    // each target child meets the children of B adjacent to it
+    int rA = -1, rB = -1;
+    if (ref_start && !self) {
+        if (ref_start[Aleaf + 1] > ref_start[Aleaf]) rA = ref_start[Aleaf];
+        if (ref_start[Bleaf + 1] > ref_start[Bleaf]) rB = ref_start[Bleaf];
+    }
+    const bool fine = rA >= 0 && rB >= 0;
+    if (fine) {
+        // B's reverse slots then collect several target children: they start from zero
+        for (int k = lane; k < (sB1 - sB0) * 6; k += 32)
+            part[(int64_t(slot_r) * N + sB0 + k / 6) * 6 + k % 6] = 0.0;
+        __syncwarp();
+    }
+    for (int ts = 0; ts < (fine ? 8 : 1); ++ts) {
+    const int tA0 = fine ? child_start[9 * rA + ts] : sA0, tA1 = fine ? child_start[9 * rA + ts + 1] : sA1;
+    for (int r0 = tA0, nrem = 0; r0 < tA1; r0 += nrem) {
         // nrem targets in this chunk on tg lanes (a power of two), 32 / tg lanes per
         // target splitting the sources.  A chunk costs max(1, tg / 4) warp steps per
         // 8 sources, so the targets left are cut into power-of-two chunks where that
         // is cheaper than rounding them up (20 targets: 16 + 4, five steps instead
         // of eight; 30 targets: one chunk of 32)
-        const int left = sA1 - r0;
+        const int left = tA1 - r0;
         const int tg = left >= 29 ? 32 : left >= 13 ? 16 : left >= 5 ? 8 : left >= 3 ? 4 : left;
         nrem = min(tg, left);
         const int ls = 32 / tg, ti = lane % tg, tj = lane / tg;
         const int i = r0 + ti;
-        const bool vi = i < sA1;
+        const bool vi = i < tA1;
         // stage the lanes' own source tensors, one 432-byte row per target: the
         // 16-byte reads of 8 consecutive rows fall in 8 different bank quads
         __syncwarp();
@@ -435,9 +453,18 @@ __global__ void __launch_bounds__(SYM_WARPS * 32, SYM_MINB) k_near_sym(
         float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float accC[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, accCl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // close pairs
         const float4 *Pi4 = reinterpret_cast<const float4 *>(wPA + 108 * ti);
-        const int jb0 = self ? r0 : sB0;  // own leaf: pairs j > i only
-        for (int j0 = jb0; j0 < sB1; j0 += SYM_SCH) {
-            const int nj = min(SYM_SCH, sB1 - j0);
+        for (int ss = 0; ss < (fine ? 8 : 1); ++ss) {
+        int jb0 = self ? r0 : sB0, jb1 = sB1;  // own leaf: pairs j > i only
+        if (fine) {
+            // B's child ss against A's child ts: adjacent at the children's level?
+            const int dx = 2 * ox + (ss & 1) - (ts & 1), dy = 2 * oy + ((ss >> 1) & 1) - ((ts >> 1) & 1),
+                      dz = 2 * oz + (ss >> 2) - (ts >> 2);
+            if (abs(dx) > 1 || abs(dy) > 1 || abs(dz) > 1) continue;
+            jb0 = child_start[9 * rB + ss];
+            jb1 = child_start[9 * rB + ss + 1];
+        }
+        for (int j0 = jb0; j0 < jb1; j0 += SYM_SCH) {
+            const int nj = min(SYM_SCH, jb1 - j0);
             __syncwarp();
             if (lane < nj) {
                 syB[warp][lane] = yrel[j0 + lane];
@@ -560,8 +587,9 @@ __global__ void __launch_bounds__(SYM_WARPS * 32, SYM_MINB) k_near_sym(
                 double *dst = part + (int64_t(slot_r) * N + (j0 + jl)) * 6 + ab;
                 const float2 cc = saccCB[warp][jl][ab];
                 const double v = double(saccB[warp][jl][ab]) + (double(cc.x) + double(cc.y));
-                *dst = first_chunk ? v : *dst + v;
+                *dst = (first_chunk && !fine) ? v : *dst + v;
             }
+        }
         }
         first_chunk = false;
         // forward: sum over the lanes that share target i (fixed order)
@@ -577,6 +605,7 @@ __global__ void __launch_bounds__(SYM_WARPS * 32, SYM_MINB) k_near_sym(
 #pragma unroll
             for (int ab = 0; ab < 6; ++ab)
                 part[(int64_t(slot_f) * N + i) * 6 + ab] = double(acc[ab]) + (double(accC[ab]) + double(accCl[ab]));
+    }
     }
 }
 
@@ -720,7 +749,8 @@ __global__ void k_near_combine(int p, int nodes, int L, int64_t N, const TreeBox
                                const int *__restrict__ sstart, const int *__restrict__ pleaf,
                                const double *__restrict__ xt, const float *__restrict__ S,
                                const double *__restrict__ S64, const double *__restrict__ part,
-                               double *__restrict__ sig) {
+                               double *__restrict__ sig, const int *__restrict__ pfine,
+                               const float *__restrict__ S7) {
     const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (t >= N) return;
     const int nlv = 1 << (L - 1);
@@ -748,13 +778,24 @@ __global__ void k_near_combine(int p, int nodes, int L, int64_t N, const TreeBox
             }
     } else if (L >= 3) {
         const int P3 = p * p * p;
-        const double h = box->H / nlv, ih = double(nlv) / box->H;
+        double h = box->H / nlv, ih = double(nlv) / box->H;
+        double c0[3] = {box->origin[0] + cx * h, box->origin[1] + cy * h, box->origin[2] + cz * h};
+        const float *Sl = S + (cell_base_d(L - 1) + leaf) * int64_t(P3) * 6;
+        const int f = pfine ? pfine[t] : -1;
+        if (f >= 0) {
+            // a point of a split leaf: its child's local values and cell (adaptive tree)
+            h *= 0.5;
+            ih *= 2.0;
+            c0[0] += (f & 1) * h;
+            c0[1] += ((f >> 1) & 1) * h;
+            c0[2] += ((f >> 2) & 1) * h;
+            Sl = S7 + int64_t(f) * P3 * 6;
+        }
         float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float bx[GB_MAXP], by[GB_MAXP], bz[GB_MAXP];
-        lagrange_1d<float>(p, float((xt[3 * t] - (box->origin[0] + cx * h)) * ih), bx, nodes);
-        lagrange_1d<float>(p, float((xt[3 * t + 1] - (box->origin[1] + cy * h)) * ih), by, nodes);
-        lagrange_1d<float>(p, float((xt[3 * t + 2] - (box->origin[2] + cz * h)) * ih), bz, nodes);
-        const float *Sl = S + (cell_base_d(L - 1) + leaf) * int64_t(P3) * 6;
+        lagrange_1d<float>(p, float((xt[3 * t] - c0[0]) * ih), bx, nodes);
+        lagrange_1d<float>(p, float((xt[3 * t + 1] - c0[1]) * ih), by, nodes);
+        lagrange_1d<float>(p, float((xt[3 * t + 2] - c0[2]) * ih), bz, nodes);
         for (int lz = 0; lz < p; ++lz)
             for (int ly = 0; ly < p; ++ly) {
                 const float wyz = by[ly] * bz[lz];
@@ -1302,13 +1343,15 @@ int near_run_sym64(gbfmm_ctx *ctx, double *sig) {
                                                                      W.part, N, W.psorted, W.pmisc + 128);
     }
     k_near_combine<<<nblk(N, 256), 256, 0, st>>>(ctx->opt.p, ctx->opt.nodes, ctx->L, N, ctx->d_box, ctx->d_leaf_start, ctx->d_pleaf,
-                                                 ctx->d_y, nullptr, ctx->d_S, W.part, sig);
+                                                 ctx->d_y, nullptr, ctx->d_S, W.part, sig, nullptr, nullptr);
     CK(cudaGetLastError());
     return GBFMM_OK;
 }
 
 static int near_run_sym(gbfmm_ctx *ctx, double *sig) {
     if (int rc = build_pair_items(ctx)) return rc;
+    // adaptive tree (nodal forces): split leaves, their children's ranges and local values
+    const int *ref_start = ctx->rf.on && ctx->L >= 3 ? ctx->rf.ref_start : nullptr;
     const int64_t N = ctx->N;
     NearWork &W = ctx->nw;
     cudaStream_t st = ctx->stream;
@@ -1320,17 +1363,19 @@ static int near_run_sym(gbfmm_ctx *ctx, double *sig) {
         CK(cudaFuncSetAttribute(k_near_sym<HM_CUBIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         k_near_sym<HM_CUBIC><<<grid, SYM_WARPS * 32, smem, st>>>(ctx->L, near2, ctx->d_box, ctx->d_mat,
                                                                  ctx->d_leaf_start, ctx->d_yrel, ctx->d_y, ctx->d_Pf,
-                                                                 ctx->d_sid, W.part, N, W.psorted, W.pmisc + 128);
+                                                                 ctx->d_sid, W.part, N, W.psorted, W.pmisc + 128,
+                                                                 ref_start, ctx->rf.child_start);
     } else {
         CK(cudaFuncSetAttribute(k_near_sym<HM_GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         k_near_sym<HM_GENERIC><<<grid, SYM_WARPS * 32, smem, st>>>(ctx->L, near2, ctx->d_box, ctx->d_mat,
                                                                    ctx->d_leaf_start, ctx->d_yrel, ctx->d_y,
                                                                    ctx->d_Pf, ctx->d_sid, W.part, N, W.psorted,
-                                                                   W.pmisc + 128);
+                                                                   W.pmisc + 128, ref_start, ctx->rf.child_start);
     }
     const double *S64 = ctx->opt.precision == GBFMM_MIXED_F64T ? ctx->d_S : nullptr;
     k_near_combine<<<nblk(N, 256), 256, 0, st>>>(ctx->opt.p, ctx->opt.nodes, ctx->L, N, ctx->d_box, ctx->d_leaf_start, ctx->d_pleaf,
-                                                 ctx->d_y, ctx->d_Sf, S64, W.part, sig);
+                                                 ctx->d_y, ctx->d_Sf, S64, W.part, sig,
+                                                 ref_start ? ctx->rf.pfine : nullptr, ctx->rf.S7);
     CK(cudaGetLastError());
     return GBFMM_OK;
 }

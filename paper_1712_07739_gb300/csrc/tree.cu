@@ -100,7 +100,7 @@ __device__ __forceinline__ int leaf_coord(double v, double o, double f, int n) {
 }
 
 __global__ void k_leaf_count(int64_t n, const double *__restrict__ y, const TreeBox *__restrict__ box, int L,
-                             int *__restrict__ leaf_of, int *__restrict__ cnt) {
+                             int *__restrict__ leaf_of, int *__restrict__ cnt, unsigned char *__restrict__ child_of) {
     int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
     int nl = 1 << (L - 1);
@@ -110,6 +110,13 @@ __global__ void k_leaf_count(int64_t n, const double *__restrict__ y, const Tree
     int cz = leaf_coord(y[3 * i + 2], box->origin[2], f, nl);
     int leaf = (cz * nl + cy) * nl + cx;
     leaf_of[i] = leaf;
+    if (child_of) {
+        // the point's cell one level below the leaves, as a child (bit d: upper half along axis d)
+        const int fx = leaf_coord(y[3 * i], box->origin[0], 2.0 * f, 2 * nl);
+        const int fy = leaf_coord(y[3 * i + 1], box->origin[1], 2.0 * f, 2 * nl);
+        const int fz = leaf_coord(y[3 * i + 2], box->origin[2], 2.0 * f, 2 * nl);
+        child_of[i] = (unsigned char)((fx & 1) | ((fy & 1) << 1) | ((fz & 1) << 2));
+    }
     atomicAdd(&cnt[leaf], 1);
 }
 
@@ -149,15 +156,22 @@ __global__ void k_scatter(int64_t n, const int *__restrict__ leaf_of, const int 
 }
 
 // restore original order inside each leaf: one block per leaf, bitonic
-// sort in shared memory (leaves above 8192 points: one-thread insertion sort)
-__global__ void k_leaf_sort(int64_t n_leaves, const int *__restrict__ start, int *__restrict__ perm) {
+// sort in shared memory (leaves above 8192 points: one-thread insertion sort).
+// With child_of (adaptive tree) the points of a leaf holding more than refine points
+// are ordered by child first (key child * 2^28 + original index; N < 2^28).
+__global__ void k_leaf_sort(int64_t n_leaves, const int *__restrict__ start, int *__restrict__ perm,
+                            const unsigned char *__restrict__ child_of, int refine) {
     constexpr int CAP = 8192;
+    constexpr int MASK = (1 << 28) - 1;
     __shared__ int v[CAP];
     const int64_t l = blockIdx.x;
     const int b = start[l], e = start[l + 1], n = e - b;
     if (n <= 1) return;
+    const bool by_child = child_of && n > refine;
+    auto key = [&](int x) { return by_child ? (int(child_of[x]) << 28) | x : x; };
     if (n > CAP) {
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
+            for (int i = b; i < e; ++i) perm[i] = key(perm[i]);
             for (int i = b + 1; i < e; ++i) {
                 const int x = perm[i];
                 int j = i - 1;
@@ -167,11 +181,14 @@ __global__ void k_leaf_sort(int64_t n_leaves, const int *__restrict__ start, int
                 }
                 perm[j + 1] = x;
             }
+            if (by_child)
+                for (int i = b; i < e; ++i) perm[i] &= MASK;
+        }
         return;
     }
     int m = 1;
     while (m < n) m <<= 1;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = i < n ? perm[b + i] : 0x7fffffff;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = i < n ? key(perm[b + i]) : 0x7fffffff;
     __syncthreads();
     for (int k = 2; k <= m; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -188,18 +205,47 @@ __global__ void k_leaf_sort(int64_t n_leaves, const int *__restrict__ start, int
             }
             __syncthreads();
         }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) perm[b + i] = v[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) perm[b + i] = by_child ? (v[i] & MASK) : v[i];
+}
+
+// adaptive tree: split flag of every leaf (more than refine points)
+__global__ void k_ref_flags(int64_t nl, const int *__restrict__ start, int refine, int *__restrict__ flags) {
+    const int64_t l = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (l < nl) flags[l] = (start[l + 1] - start[l]) > refine ? 1 : 0;
+}
+
+// adaptive tree: for every split leaf (index r from the scan of the flags) its leaf
+// and the sorted-point ranges of its 8 children (the points are ordered by child)
+__global__ void k_ref_children(int64_t nl, const int *__restrict__ start, const int *__restrict__ ref_start,
+                               const int *__restrict__ perm, const unsigned char *__restrict__ child_of,
+                               int *__restrict__ ref_leaf, int *__restrict__ child_start) {
+    const int64_t l = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (l >= nl || ref_start[l + 1] == ref_start[l]) return;
+    const int r = ref_start[l];
+    ref_leaf[r] = int(l);
+    const int b = start[l], e = start[l + 1];
+    int i = b;
+    for (int c = 0; c < 8; ++c) {
+        child_start[9 * r + c] = i;
+        while (i < e && int(child_of[perm[i]]) == c) ++i;
+    }
+    child_start[9 * r + 8] = e;
 }
 
 __global__ void k_gather_points(int64_t n, int n_g, const int *__restrict__ perm, const double *__restrict__ y0,
                                 const double *__restrict__ q0, const double *__restrict__ len0,
                                 const int *__restrict__ leaf_of, double *__restrict__ y, double *__restrict__ q,
                                 int64_t *__restrict__ sid, double *__restrict__ slen, int *__restrict__ pos,
-                                int *__restrict__ pleaf) {
+                                int *__restrict__ pleaf, const unsigned char *__restrict__ child_of,
+                                const int *__restrict__ ref_start, int *__restrict__ pfine) {
     int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
     int k = perm[i];
     pleaf[i] = leaf_of[k];
+    if (pfine) {
+        const int lf = leaf_of[k];
+        pfine[i] = ref_start[lf + 1] > ref_start[lf] ? 8 * ref_start[lf] + int(child_of[k]) : -1;
+    }
     for (int d = 0; d < 3; ++d) y[3 * i + d] = y0[3 * int64_t(k) + d];
     for (int d = 0; d < 9; ++d) q[9 * i + d] = q0[9 * int64_t(k) + d];
     sid[i] = k / n_g;
@@ -279,25 +325,41 @@ int tree_build(gbfmm_ctx *ctx, bool validate) {
     CK(cudaMemsetAsync(cnt, 0, nl * sizeof(int), st));
     CK(cudaMemsetAsync(cursor, 0, nl * sizeof(int), st));
     ++ctx->launches;
-    k_leaf_count<<<nblk(N, 256), 256, 0, st>>>(N, y0, ctx->d_box, ctx->L, leaf_of, cnt);
+    auto &RF = ctx->rf;
+    const bool refine = RF.on != 0;
+    k_leaf_count<<<nblk(N, 256), 256, 0, st>>>(N, y0, ctx->d_box, ctx->L, leaf_of, cnt, refine ? RF.child_of : nullptr);
     ++ctx->launches;
     k_scan<<<1, 1024, 0, st>>>(nl, cnt, ctx->d_leaf_start);
     ++ctx->launches;
     k_scatter<<<nblk(N, 256), 256, 0, st>>>(N, leaf_of, ctx->d_leaf_start, cursor, perm);
     ++ctx->launches;
-    k_leaf_sort<<<unsigned(nl), 128, 0, st>>>(nl, ctx->d_leaf_start, perm);
+    k_leaf_sort<<<unsigned(nl), 128, 0, st>>>(nl, ctx->d_leaf_start, perm, refine ? RF.child_of : nullptr,
+                                               ctx->opt.refine_points);
+    RF.n_ref_host = -1;
+    if (refine) {
+        // split leaves: flags, their scan (leaf -> split index), each split leaf's child ranges
+        ctx->launches += 3;
+        k_ref_flags<<<nblk(nl, 256), 256, 0, st>>>(nl, ctx->d_leaf_start, ctx->opt.refine_points, cursor);
+        k_scan<<<1, 1024, 0, st>>>(nl, cursor, RF.ref_start);
+        k_ref_children<<<nblk(nl, 128), 128, 0, st>>>(nl, ctx->d_leaf_start, RF.ref_start, perm, RF.child_of,
+                                                      RF.ref_leaf, RF.child_start);
+    }
     ++ctx->launches;
     k_gather_points<<<nblk(N, 256), 256, 0, st>>>(N, ng, perm, y0, q0, len0, leaf_of, ctx->d_y, ctx->d_q,
-                                                  ctx->d_sid, ctx->d_slen, ctx->d_pos, ctx->d_pleaf);
+                                                  ctx->d_sid, ctx->d_slen, ctx->d_pos, ctx->d_pleaf,
+                                                  refine ? RF.child_of : nullptr, RF.ref_start,
+                                                  refine ? RF.pfine : nullptr);
     CK(cudaGetLastError());
     // without validation (a build recorded into a graph) the flag stays on the device:
     // fmm_batch_status reads it with the root box
     if (!validate) return GBFMM_OK;
-    int hbad = 0;
+    int hbad = 0, href = 0;
     CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     TreeBox hb{};
     CK(cudaMemcpyAsync(&hb, ctx->d_box, sizeof(TreeBox), cudaMemcpyDeviceToHost, st));
+    if (refine) CK(cudaMemcpyAsync(&href, RF.ref_start + nl, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (refine) RF.n_ref_host = href;
     if (hbad) return set_err(ctx, GBFMM_ERR_DEGENERATE, "fmm_build_tree: zero-length or non-finite segment");
     if (!std::isfinite(hb.H)) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "fmm_build_tree: non-finite node coordinates");
     return GBFMM_OK;
@@ -323,13 +385,13 @@ int targets_sort(gbfmm_ctx *ctx, int64_t n_t, const double *x) {
     CK(cudaMemsetAsync(cnt, 0, nl * sizeof(int), st));
     CK(cudaMemsetAsync(cursor, 0, nl * sizeof(int), st));
     ++ctx->launches;
-    k_leaf_count<<<nblk(n_t, 256), 256, 0, st>>>(n_t, x, ctx->d_box, ctx->L, leaf_of, cnt);
+    k_leaf_count<<<nblk(n_t, 256), 256, 0, st>>>(n_t, x, ctx->d_box, ctx->L, leaf_of, cnt, nullptr);
     ++ctx->launches;
     k_scan<<<1, 1024, 0, st>>>(nl, cnt, ctx->d_t_start);
     ++ctx->launches;
     k_scatter<<<nblk(n_t, 256), 256, 0, st>>>(n_t, leaf_of, ctx->d_t_start, cursor, perm);
     ++ctx->launches;
-    k_leaf_sort<<<unsigned(nl), 128, 0, st>>>(nl, ctx->d_t_start, perm);
+    k_leaf_sort<<<unsigned(nl), 128, 0, st>>>(nl, ctx->d_t_start, perm, nullptr, 0);
     ++ctx->launches;
     k_gather_targets<<<nblk(n_t, 256), 256, 0, st>>>(n_t, perm, x, ctx->d_t_x, ctx->d_t_pos);
     CK(cudaGetLastError());
