@@ -139,11 +139,11 @@ WORKLOADS["c3"] = dict(
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
     h_mode="circle", circle_q=16, p=7, levels=7, precision="mixed", fp64_arm=True, **CHEB_M2L)
 WORKLOADS["c3a"] = dict(
-    desc="c3 on an adaptive octree: the 7-level tree with every leaf holding more than 48 Gauss points split "
+    desc="c3 on an adaptive octree: the 7-level tree with every leaf holding more than 128 Gauss points split "
          "once more (children of two split leaves that are not adjacent interact by an M2L one level down, "
          "adjacent ones directly)",
     gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=16, p=7, levels=7,
-    precision="mixed", refine_points=48, **CHEB_M2L)
+    precision="mixed", refine_points=128, **CHEB_M2L)
 WORKLOADS["c3legendre"] = dict(
     desc="c3 on equispaced nodes with the dense M2L (every one of the 54 p^6 products per cell pair, on FP16 "
          "Legendre moments of the source cells with residual passes on the low-order moments)",

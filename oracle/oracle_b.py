@@ -25,6 +25,11 @@ set is a parameter here (``nodes``), and ``m2l_svd_bases`` gives the two
 orthonormal bases of the compression, which ``lagrange_fmm`` applies when
 given them.
 
+The symmetry reduction the paper points to (Sec. 6): for a medium with the
+cube's symmetries (isotropic, or cubic with axes along x, y, z) every one of
+the 316 operators is a signed permutation of rows and columns of one of 16
+(``cube_group``, ``offset_orbits``, ``symmetric_operator``).
+
 ``lagrange_fmm`` computes that result level by level.
 ``pairwise_far_field`` evaluates Eq. "far-field" separately for every
 (target cell, interaction-list cell) pair at every level, with no
@@ -159,6 +164,77 @@ def m2l_offsets():
     """The 316 offsets o = B - A over all interaction lists: o in [-3, 3]^3 with
     max |o_i| >= 2 (the 7^3 - 3^3 of Sec. 3's count of pre-computed operators)."""
     return [o for o in itertools.product(range(-3, 4), repeat=3) if max(abs(x) for x in o) >= 2]
+
+
+def cube_group():
+    """The 48 orthogonal maps of a cube onto itself (Sec. 6: the symmetries of
+    space the operator count 316 -> 16 relies on): the signed permutation
+    matrices g, g[i, pi(i)] = s_i, 24 of them proper (det +1)."""
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            g = np.zeros((3, 3), dtype=np.int64)
+            for i in range(3):
+                g[i, perm[i]] = signs[i]
+            out.append(g)
+    return out
+
+
+def offset_orbits():
+    """The 316 offsets grouped into orbits of ``cube_group``: a list of
+    (rep, members), members = [(o, g)] with o = g rep for every offset of the
+    orbit, rep the member with non-negative components in decreasing order."""
+    G = cube_group()
+    seen, out = set(), []
+    for o in m2l_offsets():
+        rep = tuple(sorted((abs(x) for x in o), reverse=True))
+        if rep in seen:
+            continue
+        seen.add(rep)
+        members = {}
+        for g in G:
+            img = tuple(int(x) for x in g @ np.array(rep))
+            members.setdefault(img, g)  # one map per image
+        out.append((rep, sorted(members.items())))
+    return out
+
+
+def symmetric_operator(mat, p, o, g, rep, nodes="equispaced"):
+    """T_o [p^3, 6, p^3, 9] (layout of ``_node_kernels``) built from the
+    operator of its orbit's representative, o = g rep.
+
+    For a medium with C_ijkl invariant under g the kernel obeys
+    K(g d)_{ab,wr} = det(g) g_ai g_bj g_wk g_rl K(d)_{ij,kl} (the factor det(g)
+    comes from the permutation symbol in the kernel of Sec. 2, a pseudo-tensor).
+    The cell maps onto itself by x -> g (x - c) + c about its centre c, which
+    takes node l (positions t_l) to the node l' with l'_i = l_pi(i) where
+    s_i = +1 and p - 1 - l_pi(i) where s_i = -1 (the node sets are symmetric
+    under t -> 1 - t); node differences then map by g, so
+    T_o[l', ab, m', wr] = det(g) s_a s_b s_w s_r T_rep[l, pi(a)pi(b), m, pi(w)pi(r)]."""
+    g = np.asarray(g)
+    assert tuple(int(x) for x in g @ np.array(rep)) == tuple(o)
+    P3 = p ** 3
+    T = _node_kernels(mat, p, 1.0, rep, nodes=nodes)  # [l, ab, m, wr]
+    perm = [int(np.nonzero(g[i])[0][0]) for i in range(3)]
+    sgn = [int(g[i, perm[i]]) for i in range(3)]
+    det = int(round(np.linalg.det(g)))
+    # node map l -> l' (index (lx p + ly) p + lz, x slowest)
+    idx = np.array(list(itertools.product(range(p), repeat=3)))
+    img = np.empty_like(idx)
+    for i in range(3):
+        col = idx[:, perm[i]]
+        img[:, i] = col if sgn[i] > 0 else p - 1 - col
+    lmap = (img[:, 0] * p + img[:, 1]) * p + img[:, 2]
+    voigt = {(0, 0): 0, (1, 1): 1, (2, 2): 2, (1, 2): 3, (2, 1): 3, (0, 2): 4, (2, 0): 4, (0, 1): 5, (1, 0): 5}
+    pairs = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    out = np.zeros((P3, 6, P3, 9))
+    for ab, (a, b) in enumerate(pairs):
+        src_ab = voigt[(perm[a], perm[b])]
+        for w in range(3):
+            for r in range(3):
+                s = det * sgn[a] * sgn[b] * sgn[w] * sgn[r]
+                out[np.ix_(lmap, [ab], lmap, [3 * w + r])] = s * T[:, [src_ab], :, :][:, :, :, [3 * perm[w] + perm[r]]]
+    return out
 
 
 def m2l_svd_bases(mat, p, nodes="equispaced", tol=None, ranks=None):

@@ -111,10 +111,12 @@ def _unique_blocks(p):
 def test_printed_values_reproduced():
     """Every value in tests/golden/paper_printed_values.txt follows from the
     oracle: operator counts from its interaction lists, unique blocks counted
-    on its node-kernel matrices, memory from Eq. "mem_unif" with those."""
+    on its node-kernel matrices, memory from Eq. "mem_unif" with those, the
+    operators left by the cube's symmetries from its orbits of offsets."""
     n_ops, n_comp = _oracle_counts()
     rows = _printed_values()
-    assert len(rows) == 6
+    assert len(rows) == 8
+    n_orbits = len(ob.offset_orbits())
     for q, arg, val, unit, tol, where in rows:
         if q == "lagrange_m2l_memory_fp64":
             p = int(arg.split("=")[1])
@@ -125,6 +127,10 @@ def test_printed_values_reproduced():
             got = n_ops
         elif q == "toeplitz_unique_blocks":
             got = _unique_blocks(int(arg.split("=")[1]))
+        elif q == "unique_operators_by_symmetry":
+            got = n_orbits
+        elif q == "symmetry_memory_ratio":
+            got = n_ops / n_orbits
         else:
             raise AssertionError(q)
         assert abs(got - val) <= tol, (q, arg, got, val, where)
