@@ -150,6 +150,14 @@ typedef struct {
                               other adjacent leaves directly; points of split leaves take their
                               child's local values.  Nodal forces only (fmm_eval_stress keeps
                               the uniform tree).  0 = off (fmm_default_options). */
+    int m2l_symmetry;      /* FP64 with m2l_fft = 1: 1 = keep the transformed operators of 16
+                              offsets only (Sec. 6: the cube's symmetries of space and kernel
+                              map every one of the 316 operators to a signed permutation of
+                              rows and columns of one of 16; the table shrinks 316/16 times) and
+                              apply each offset's from its representative's at permuted
+                              frequencies.  Needs a medium with those symmetries (isotropic, or
+                              cubic with axes along x, y, z): fmm_eval_* returns INVALID_ARG
+                              for any other.  0 = off (fmm_default_options). */
 } gbfmm_options;
 
 typedef struct gbfmm_ctx gbfmm_ctx;

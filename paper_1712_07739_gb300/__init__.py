@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
         ("mlp_min_dist", ctypes.c_double), ("m2l_fft", ctypes.c_int), ("m2l_chunks", ctypes.c_int),
         ("m2l_basis", ctypes.c_int), ("m2l_split_levels", ctypes.c_int), ("m2l_split_kblocks", ctypes.c_int),
         ("m2l_kernel", ctypes.c_int), ("nodes", ctypes.c_int), ("m2l_svd_tol", ctypes.c_double),
-        ("refine_points", ctypes.c_int),
+        ("refine_points", ctypes.c_int), ("m2l_symmetry", ctypes.c_int),
     ]
 
 
@@ -162,7 +162,7 @@ class FMM:
     def __init__(self, p=4, n_gauss=4, levels=0, precision="fp64", h_mode="iso", circle_q=0,
                  leaf_segments=0, near_fp64=0.0, m2l_split=None, mlp_min_dist=0.0, m2l_fft=None, m2l_chunks=None,
                  m2l_basis=None, m2l_split_levels=None, m2l_split_kblocks=None, m2l_kernel=None, nodes=None,
-                 m2l_svd_tol=None, refine_points=None, stream=None):
+                 m2l_svd_tol=None, refine_points=None, m2l_symmetry=None, stream=None):
         import torch
 
         self._torch = torch
@@ -170,6 +170,8 @@ class FMM:
         o = Options()
         self._lib.fmm_default_options(ctypes.byref(o))
         _set_nodes_svd(o, nodes, m2l_svd_tol, refine_points)
+        if m2l_symmetry is not None:
+            o.m2l_symmetry = int(m2l_symmetry)
         o.p, o.n_gauss, o.levels = p, n_gauss, levels
         o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
         o.h_mode = _HMODE[h_mode] if isinstance(h_mode, str) else int(h_mode)

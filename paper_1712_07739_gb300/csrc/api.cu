@@ -167,6 +167,10 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
     if (opt->refine_points < 0 ||
         (opt->refine_points > 0 && (opt->m2l_svd_tol <= 0.0 || opt->h_mode != GBFMM_H_CIRCLE)))
         return GBFMM_ERR_INVALID_ARG;
+    // the symmetry-reduced operator table belongs to the FP64 M2L through transforms
+    if (opt->m2l_symmetry < 0 || opt->m2l_symmetry > 1 ||
+        (opt->m2l_symmetry == 1 && (opt->precision != GBFMM_FP64 || opt->m2l_fft != 1)))
+        return GBFMM_ERR_INVALID_ARG;
     gbfmm_ctx *ctx = new gbfmm_ctx();
     ctx->opt = *opt;
     ctx->rf.on = opt->refine_points > 0 ? 1 : 0;

@@ -22,6 +22,19 @@
 // (three stress components per sweep, thread per frequency) and transforms
 // it back.  Every transform is a separable pass per axis over a shared
 // table of the N roots of unity.
+//
+// Symmetry reduction (gbfmm_options.m2l_symmetry; Sec. 6): in a medium
+// invariant under a signed permutation g of the axes (g_{i pi(i)} = s_i) the
+// kernel obeys K(g d) = det(g) rho(g) K(d), rho(g) acting on the stress pair
+// ab and the strength pair wr as (rho K)[ab][wr] = s_a s_b s_w s_r
+// K[pi(a) pi(b)][pi(w) pi(r)] (det(g): the permutation symbol of the kernel).
+// Every offset o is g rep for one of 16 representatives (components sorted,
+// non-negative), node differences map by g, so the transforms obey
+//     K^_o[f] = det(g) rho(g) K^_rep[g^T f],   (g^T f)_j = s_i f_i, pi(i) = j,
+// frequencies mod N; where (g^T f)_x > p the half spectrum holds the
+// conjugate at -(g^T f).  The table keeps the 16 representatives (316/16 times
+// smaller) and k_m2l_fft reads each offset's entries from its
+// representative's at the permuted frequency, with permuted, signed components.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -119,17 +132,24 @@ __device__ void inv3(int N, int NH, int p, const double2 *Sh, double2 *B1, doubl
     __syncthreads();
 }
 
+// the 16 representatives' offset indices (symmetry-reduced table)
+struct RepList {
+    int oi[16];
+};
+
 // Transformed kernel components of every offset o with max |o_i| >= 2:
-// block (oi, comp), oi = ((oz + 3) 7 + (oy + 3)) 7 + (ox + 3).
+// block (table slot, comp); slot = oi = ((oz + 3) 7 + (oy + 3)) 7 + (ox + 3), or
+// with reps the slot's representative.
 __global__ void __launch_bounds__(256) k_fft_ops(int p, int lat_n, const double *__restrict__ Klat,
-                                                 double2 *__restrict__ Khat) {
+                                                 double2 *__restrict__ Khat, int use_reps, RepList reps) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int N = 2 * p, NH = p + 1, NF = N * N * NH;
     double2 *tw = reinterpret_cast<double2 *>(sm_raw);
     double2 *A1 = tw + N;
     double2 *A2 = A1 + N * N * NH;
     double *a = reinterpret_cast<double *>(A2 + N * N * NH);
-    const int oi = blockIdx.x / 54, comp = blockIdx.x % 54;
+    const int slot = blockIdx.x / 54, comp = blockIdx.x % 54;
+    const int oi = use_reps ? reps.oi[slot] : slot;
     const int ox = oi % 7 - 3, oy = (oi / 7) % 7 - 3, oz = oi / 49 - 3;
     if (max(abs(ox), max(abs(oy), abs(oz))) < 2) return;
     const int R0 = (lat_n - 1) / 2;
@@ -145,7 +165,7 @@ __global__ void __launch_bounds__(256) k_fft_ops(int p, int lat_n, const double 
         a[t] = v;
     }
     __syncthreads();
-    fwd3(N, NH, N, a, A1, A2, tw, Khat + (int64_t(oi) * 54 + comp) * NF);
+    fwd3(N, NH, N, a, A1, A2, tw, Khat + (int64_t(slot) * 54 + comp) * NF);
 }
 
 // Slots of the occupied cells of one level
@@ -181,11 +201,14 @@ __global__ void __launch_bounds__(256) k_fft_w(int p, int lev, const double *__r
     }
 }
 
-// One block per cell of the level: S for the cells with targets
+// One block per cell of the level: S for the cells with targets (SYM: Khat holds the 16
+// representatives, osym and gmap map each offset onto one)
+template <bool SYM>
 __global__ void __launch_bounds__(256) k_m2l_fft(int p, int lev, const TreeBox *__restrict__ box,
                                                  const int *__restrict__ tocc, const int *__restrict__ slot,
                                                  const double2 *__restrict__ Khat, const double2 *__restrict__ What,
-                                                 double *__restrict__ S) {
+                                                 double *__restrict__ S, const int *__restrict__ osym,
+                                                 const unsigned char *__restrict__ gmap) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int N = 2 * p, NH = p + 1, NF = N * N * NH, P3 = p * p * p;
     double2 *tw = reinterpret_cast<double2 *>(sm_raw);
@@ -194,12 +217,15 @@ __global__ void __launch_bounds__(256) k_m2l_fft(int p, int lev, const TreeBox *
     double2 *B2 = B1 + p * N * NH;    // [p][p][NH]
     double *sout = reinterpret_cast<double *>(B2 + p * p * NH);  // [p^3]
     __shared__ int s_src[216], s_oi[216];
+    __shared__ unsigned char s_gmap[SYM ? 48 * 60 : 4];
     const int n = 1 << lev;
     const int64_t g = cell_base_d(lev) + blockIdx.x;
     if (tocc[g] == 0) return;
     int bx, by, bz;
     cell_xyz_f(blockIdx.x, n, bx, by, bz);
     load_twiddles(N, tw);
+    if (SYM)
+        for (int t = threadIdx.x; t < 48 * 60; t += blockDim.x) s_gmap[t] = gmap[t];
     // interaction list in a fixed order: children of the parent's 27 neighbours
     // that are not neighbours of B and hold sources
     for (int c = threadIdx.x; c < 216; c += blockDim.x) {
@@ -212,6 +238,7 @@ __global__ void __launch_bounds__(256) k_m2l_fft(int p, int lev, const TreeBox *
             if (max(abs(ox), max(abs(oy), abs(oz))) >= 2) {
                 src = slot[(int64_t(az) * n + ay) * n + ax];
                 oi = ((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3);
+                if (SYM) oi = osym[oi];  // representative | map << 8
             }
         }
         s_src[c] = src;
@@ -231,11 +258,38 @@ __global__ void __launch_bounds__(256) k_m2l_fft(int p, int lev, const TreeBox *
                 double2 w[9];
 #pragma unroll
                 for (int wr = 0; wr < 9; ++wr) w[wr] = wv[int64_t(wr) * NF];
-                const double2 *kv = Khat + (int64_t(s_oi[c]) * 54 + 27 * grp) * NF + f;
+                if (SYM) {
+                    // the representative's entries at g^T f, components permuted and signed
+                    const int code = s_oi[c];
+                    const unsigned char *gm = s_gmap + (code >> 8) * 60;
+                    const int fv[3] = {f % NH, (f / NH) % N, f / (NH * N)};
+                    int f2[3];
 #pragma unroll
-                for (int k = 0; k < 3; ++k)
+                    for (int j = 0; j < 3; ++j) {
+                        const int a = gm[54 + j], v = fv[a & 3];
+                        f2[j] = (a & 4) ? (v ? N - v : 0) : v;
+                    }
+                    const bool cj = f2[0] > p;  // stored as the conjugate at -(g^T f)
+                    if (cj)
 #pragma unroll
-                    for (int wr = 0; wr < 9; ++wr) cmac(acc[k], kv[int64_t(k * 9 + wr) * NF], w[wr]);
+                        for (int j = 0; j < 3; ++j) f2[j] = f2[j] ? N - f2[j] : 0;
+                    const double2 *kb = Khat + int64_t(code & 255) * 54 * NF + (f2[2] * N + f2[1]) * NH + f2[0];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+#pragma unroll
+                        for (int wr = 0; wr < 9; ++wr) {
+                            const int cc = gm[27 * grp + 9 * k + wr];
+                            const double2 v = kb[int64_t(cc & 63) * NF];
+                            const bool neg = (cc & 64) != 0;
+                            cmac(acc[k], make_double2(neg ? -v.x : v.x, (neg != cj) ? -v.y : v.y), w[wr]);
+                        }
+                } else {
+                    const double2 *kv = Khat + (int64_t(s_oi[c]) * 54 + 27 * grp) * NF + f;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+#pragma unroll
+                        for (int wr = 0; wr < 9; ++wr) cmac(acc[k], kv[int64_t(k * 9 + wr) * NF], w[wr]);
+                }
             }
             for (int k = 0; k < 3; ++k) Sh[k * NF + f] = acc[k];
         }
@@ -248,6 +302,92 @@ __global__ void __launch_bounds__(256) k_m2l_fft(int p, int lev, const TreeBox *
     }
 }
 
+// The cube's 48 signed axis permutations, map gi = 8 (permutation index) + sign bits
+// (bit i: s_i = -1), permutations in lexicographic order; g_{i pi(i)} = s_i.
+struct CubeMap {
+    int pi[3], s[3], det;
+};
+CubeMap cube_map(int gi) {
+    static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    static const int parity[6] = {1, -1, -1, 1, 1, -1};
+    CubeMap m{};
+    const int pk = gi / 8, sb = gi % 8;
+    m.det = parity[pk];
+    for (int i = 0; i < 3; ++i) {
+        m.pi[i] = perms[pk][i];
+        m.s[i] = (sb >> i) & 1 ? -1 : 1;
+        m.det *= m.s[i];
+    }
+    return m;
+}
+
+int voigt_of(int a, int b) {
+    if (a == b) return a;
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo == 1 ? 3 : (hi == 2 ? 4 : 5);  // (1,2) yz, (0,2) xz, (0,1) xy
+}
+
+// C_ijkl (index ((i 3 + j) 3 + k) 3 + l) unchanged by all 48 maps?
+bool cube_invariant(const double *C) {
+    double mx = 0.0;
+    for (int i = 0; i < 81; ++i) mx = std::max(mx, std::fabs(C[i]));
+    for (int gi = 0; gi < 48; ++gi) {
+        const CubeMap m = cube_map(gi);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) {
+                        const double c = m.s[i] * m.s[j] * m.s[k] * m.s[l] *
+                                         C[((m.pi[i] * 3 + m.pi[j]) * 3 + m.pi[k]) * 3 + m.pi[l]];
+                        if (std::fabs(c - C[((i * 3 + j) * 3 + k) * 3 + l]) > 1e-12 * mx) return false;
+                    }
+    }
+    return true;
+}
+
+// Representatives (r0 >= r1 >= r2 >= 0, r0 in {2, 3}) in a fixed order, each offset's
+// representative and map (o = g rep), and per map its component and frequency-axis tables
+void sym_tables(RepList &reps, int osym[343], unsigned char gmap[48 * 60]) {
+    int rep_key[16], nr = 0;
+    for (int r0 = 2; r0 <= 3; ++r0)
+        for (int r1 = 0; r1 <= r0; ++r1)
+            for (int r2 = 0; r2 <= r1; ++r2) {
+                rep_key[nr] = (r0 * 4 + r1) * 4 + r2;
+                reps.oi[nr++] = ((r2 + 3) * 7 + (r1 + 3)) * 7 + (r0 + 3);  // (x, y, z) = (r0, r1, r2)
+            }
+    for (int oi = 0; oi < 343; ++oi) {
+        const int o[3] = {oi % 7 - 3, (oi / 7) % 7 - 3, oi / 49 - 3};
+        int a[3] = {std::abs(o[0]), std::abs(o[1]), std::abs(o[2])};
+        std::sort(a, a + 3);
+        osym[oi] = -1;
+        if (a[2] < 2) continue;
+        const int r[3] = {a[2], a[1], a[0]}, key = (r[0] * 4 + r[1]) * 4 + r[2];
+        const int ri = int(std::find(rep_key, rep_key + 16, key) - rep_key);
+        for (int gi = 0; gi < 48 && osym[oi] < 0; ++gi) {
+            const CubeMap m = cube_map(gi);
+            bool ok = true;
+            for (int i = 0; i < 3; ++i) ok = ok && o[i] == m.s[i] * r[m.pi[i]];
+            if (ok) osym[oi] = ri | (gi << 8);
+        }
+    }
+    static const int va[6] = {0, 1, 2, 1, 0, 0}, vb[6] = {0, 1, 2, 2, 2, 1};
+    for (int gi = 0; gi < 48; ++gi) {
+        const CubeMap m = cube_map(gi);
+        unsigned char *gm = gmap + gi * 60;
+        for (int ab = 0; ab < 6; ++ab)
+            for (int w = 0; w < 3; ++w)
+                for (int r = 0; r < 3; ++r) {
+                    const int a = va[ab], b = vb[ab];
+                    const int src = voigt_of(m.pi[a], m.pi[b]) * 9 + m.pi[w] * 3 + m.pi[r];
+                    const int sg = m.det * m.s[a] * m.s[b] * m.s[w] * m.s[r];
+                    gm[ab * 9 + w * 3 + r] = (unsigned char)(src | (sg < 0 ? 64 : 0));
+                }
+        // frequency axis j of the representative's frame: (g^T f)_j = s_i f_i with pi(i) = j
+        for (int i = 0; i < 3; ++i) gm[54 + m.pi[i]] = (unsigned char)(i | (m.s[i] < 0 ? 4 : 0));
+        for (int t = 57; t < 60; ++t) gm[t] = 0;
+    }
+}
+
 }  // namespace
 
 int m2l_fft_run(gbfmm_ctx *ctx, const int *occ, const int *tocc) {
@@ -256,19 +396,38 @@ int m2l_fft_run(gbfmm_ctx *ctx, const int *occ, const int *tocc) {
     const int N = 2 * p, NH = p + 1, NF = N * N * NH, P3 = p * p * p;
     cudaStream_t st = ctx->stream;
     if (L < 3) return GBFMM_OK;
-    if (!F.ready || F.p != p) {
+    const bool sym = ctx->opt.m2l_symmetry == 1;
+    RepList reps{};
+    if (!F.ready || F.p != p || F.sym != sym) {
         F.ready = false;
         if (F.Khat) cudaFree(F.Khat);
         F.Khat = nullptr;
-        CK(cudaMalloc(&F.Khat, size_t(343) * 54 * NF * sizeof(double2)));
+        int n_tab = 343;
+        if (sym) {
+            if (!cube_invariant(ctx->mat.C))
+                return set_err(ctx, GBFMM_ERR_INVALID_ARG,
+                               "m2l_symmetry: the medium lacks the cube's symmetries (isotropic, or cubic with "
+                               "axes along x, y, z)");
+            int osym[343];
+            unsigned char gmap[48 * 60];
+            sym_tables(reps, osym, gmap);
+            if (!F.d_osym) CK(cudaMalloc(&F.d_osym, sizeof(osym)));
+            if (!F.d_gmap) CK(cudaMalloc(&F.d_gmap, sizeof(gmap)));
+            CK(cudaMemcpyAsync(F.d_osym, osym, sizeof(osym), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(F.d_gmap, gmap, sizeof(gmap), cudaMemcpyHostToDevice, st));
+            CK(cudaStreamSynchronize(st));  // the host tables are locals
+            n_tab = 16;
+        }
+        CK(cudaMalloc(&F.Khat, size_t(n_tab) * 54 * NF * sizeof(double2)));
         const size_t sm = size_t(N) * sizeof(double2) + 2 * size_t(N) * N * NH * sizeof(double2) +
                           size_t(N) * N * N * sizeof(double);
         CK(cudaFuncSetAttribute(k_fft_ops, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
         ++ctx->launches;
-        k_fft_ops<<<343 * 54, 256, sm, st>>>(p, ctx->lat_n, ctx->d_Klat, F.Khat);
+        k_fft_ops<<<unsigned(n_tab * 54), 256, sm, st>>>(p, ctx->lat_n, ctx->d_Klat, F.Khat, sym ? 1 : 0, reps);
         CK(cudaGetLastError());
         F.ready = true;
         F.p = p;
+        F.sym = sym;
     }
     const int64_t max_cells = int64_t(1) << (3 * (L - 1));
     if (int rc = grow_dev(ctx, F.cell_cap, max_cells,
@@ -282,7 +441,8 @@ int m2l_fft_run(gbfmm_ctx *ctx, const int *occ, const int *tocc) {
                         size_t(p) * N * NH * sizeof(double2) + size_t(p) * p * NH * sizeof(double2) +
                         size_t(P3) * sizeof(double);
     CK(cudaFuncSetAttribute(k_fft_w, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_w)));
-    CK(cudaFuncSetAttribute(k_m2l_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_a)));
+    auto kern = sym ? k_m2l_fft<true> : k_m2l_fft<false>;
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_a)));
     for (int lev = 2; lev < L; ++lev) {
         const int64_t cells = int64_t(1) << (3 * lev);
         CK(cudaMemsetAsync(F.count, 0, sizeof(int), st));
@@ -301,7 +461,8 @@ int m2l_fft_run(gbfmm_ctx *ctx, const int *occ, const int *tocc) {
             CK(cudaGetLastError());
         }
         ++ctx->launches;
-        k_m2l_fft<<<unsigned(cells), 256, sm_a, st>>>(p, lev, ctx->d_box, tocc, F.slot, F.Khat, F.What, ctx->d_S);
+        kern<<<unsigned(cells), 256, sm_a, st>>>(p, lev, ctx->d_box, tocc, F.slot, F.Khat, F.What, ctx->d_S,
+                                                 F.d_osym, F.d_gmap);
         CK(cudaGetLastError());
     }
     return GBFMM_OK;
@@ -309,7 +470,7 @@ int m2l_fft_run(gbfmm_ctx *ctx, const int *occ, const int *tocc) {
 
 void m2l_fft_free(gbfmm_ctx *ctx) {
     FftPlan &F = ctx->fft;
-    void *ps[] = {F.Khat, F.What, F.slot, F.slot_cell, F.count};
+    void *ps[] = {F.Khat, F.What, F.slot, F.slot_cell, F.count, F.d_osym, F.d_gmap};
     for (void *q : ps)
         if (q) cudaFree(q);
     F = FftPlan{};

@@ -10,7 +10,12 @@ struct gbfmm_ctx;
 struct FftPlan {
     bool ready = false;            // Khat holds the transformed operators of the current medium and p
     int p = 0;
-    double2 *Khat = nullptr;       // [343 offsets][54][NF]: offsets with max |o_i| >= 2 filled
+    bool sym = false;              // Khat holds the 16 representatives of the cube's symmetry orbits
+    double2 *Khat = nullptr;       // [343 offsets][54][NF]: offsets with max |o_i| >= 2 filled;
+                                   // with sym [16 representatives][54][NF]
+    int *d_osym = nullptr;         // sym: [343] representative | map << 8 of each offset
+    unsigned char *d_gmap = nullptr;  // sym: [48][60] per map: 54 source components (bit 6: negate),
+                                      // then per frequency axis its source axis and sign (bit 2)
     double2 *What = nullptr;       // [slots][9][NF]: transformed multipole values of one level
     int64_t what_cap = 0;          // slots
     int *slot = nullptr;           // [cells of one level]: slot of each occupied cell, else -1
