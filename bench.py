@@ -122,10 +122,10 @@ WORKLOADS = {
 MIXED_M2L = dict(m2l_split=6, m2l_basis=1, m2l_chunks=7, m2l_split_kblocks=1)
 WORKLOADS["c2"] = dict(
     desc="50,000 segments (1,000 polygonal loops of 10-80 segments, log-uniform radii 0.005-0.05, seed 1), cubic "
-         "C11=1.684 C12=1.214 C44=0.754, plain FP64 pass (M2L through transforms, symmetric FP64 near field), "
-         "order p=5, 5-level octree, unit-circle h Q=32",
+         "C11=1.684 C12=1.214 C44=0.754, plain FP64 pass (M2L through transforms on the table of the 16 "
+         "symmetry-orbit representatives, symmetric FP64 near field), order p=5, 5-level octree, unit-circle h Q=32",
     gen=lambda seed: synth.polygon_loops(seed=1 + 1000 * seed), C=lambda: synth.cubic_voigt(),
-    h_mode="circle", circle_q=32, p=5, levels=5, precision="fp64")
+    h_mode="circle", circle_q=32, p=5, levels=5, precision="fp64", m2l_symmetry=1)
 # The compressed M2L of the headline: Chebyshev nodes, singular vectors kept above 5e-5 of
 # the largest (the paper's Chebyshev FMM), FP16 operands with residual passes on the
 # leading block of 64 singular directions, offsets summed in 3 runs.
@@ -608,6 +608,7 @@ def run_ours(args, wl):
                        "nodes": ["equispaced", "chebyshev"][int(f.options.nodes)],
                        "m2l_svd_tol": float(f.options.m2l_svd_tol), "m2l_svd_ranks": ranks,
                        "refine_points": int(f.options.refine_points),
+                       "m2l_symmetry": int(f.options.m2l_symmetry),
                        "l2": "flushed: 256 MiB write between steps, outside the step events",
                        "step": "fmm_build_tree + fmm_eval_nodal_forces"},
             "stage_ms": {"precontract": st[:, 0].mean(), "p2m_m2m": st[:, 1].mean(), "m2l": st[:, 2].mean(),
@@ -635,7 +636,7 @@ GOLDEN = {"c3": "c3_sampled_forces.json", "c3q": "c3q_sampled_forces.json", "c3_
 def m2l_options(wl):
     """The tensor-core M2L operand options a workload names (library defaults otherwise)."""
     return {k: wl[k] for k in ("m2l_split", "m2l_basis", "m2l_chunks", "m2l_split_kblocks", "m2l_kernel", "nodes",
-                               "m2l_svd_tol", "refine_points") if k in wl}
+                               "m2l_svd_tol", "refine_points", "m2l_symmetry") if k in wl}
 
 
 def oracle_node_error(wl, name, F, nodes, segs, b):
@@ -713,7 +714,7 @@ def run_fp64_arm(wl, name, d_nodes, d_segs, d_b, nodes, segs, b, flush, stream):
     import paper_1712_07739_gb300 as gb
 
     f = gb.FMM(p=wl["p"], levels=wl["levels"], precision="fp64", h_mode=wl["h_mode"],
-               circle_q=wl.get("circle_q", 0), m2l_fft=1).set_material(wl["C"]())
+               circle_q=wl.get("circle_q", 0), m2l_fft=1, m2l_symmetry=1).set_material(wl["C"]())
     out = torch.empty((len(nodes), 3), dtype=torch.float64, device=d_nodes.device)
     f.build(d_nodes, d_segs, d_b)
     f.nodal_forces(out=out)
@@ -733,7 +734,8 @@ def run_fp64_arm(wl, name, d_nodes, d_segs, d_b, nodes, segs, b, flush, stream):
             "stage_ms": {"precontract": st[0], "p2m_m2m": st[1], "m2l": st[2], "l2l": st[3], "l2p_p2p": st[4],
                          "forces": st[5]},
             "accuracy": oracle_node_error(wl, name, out.cpu().numpy(), nodes, segs, b),
-            "config": "same network, p, tree and unit-circle rule; precision fp64, M2L through transforms"}
+            "config": "same network, p, tree and unit-circle rule; precision fp64, M2L through transforms on "
+                      "the 16 symmetry-orbit representatives' table"}
 
 
 def main():
@@ -757,6 +759,8 @@ def main():
     ap.add_argument("--m2l-split-kblocks", type=int, default=-1, help="override the residual K blocks (fmm options)")
     ap.add_argument("--m2l-kernel", type=int, default=-1, help="override the M2L tile form (fmm options)")
     ap.add_argument("--m2l-svd-tol", type=float, default=-1.0, help="override the M2L compression (fmm options)")
+    ap.add_argument("--m2l-symmetry", type=int, default=-1,
+                    help="override the FP64 M2L table: 1 = 16 symmetry-orbit representatives, 0 = all 316")
     ap.add_argument("--refine-points", type=int, default=-1,
                     help="override the adaptive tree's split threshold (0: uniform tree; fmm options)")
     args = ap.parse_args()
@@ -779,6 +783,8 @@ def main():
         wl["m2l_svd_tol"] = args.m2l_svd_tol
     if args.refine_points >= 0:
         wl["refine_points"] = args.refine_points
+    if args.m2l_symmetry >= 0:
+        wl["m2l_symmetry"] = args.m2l_symmetry
     if args.impl == "reference":
         run_reference(args, wl)
     elif wl.get("batch"):

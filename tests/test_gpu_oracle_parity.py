@@ -237,15 +237,19 @@ def c2_case():
             np.array(gold["forces_direct"]))
 
 
-def test_c2_fp64_matches_stored_algorithm2(c2_case):
+@pytest.mark.parametrize("sym", [0, 1])
+def test_c2_fp64_matches_stored_algorithm2(c2_case, sym):
     """The plain FP64 pass at high order against the oracle's Algorithm 2 on
-    the same tree: the 1e-10 bar of the FP64 path (rounding only)."""
+    the same tree: the 1e-10 bar of the FP64 path (rounding only), with the
+    full operator table and with the 16 symmetry-orbit representatives."""
     nodes, segs, b, ids, F2, idd, Fd = c2_case
-    F = _forces(nodes, segs, b, CUB_C, p=5, levels=5, precision="fp64", h_mode="circle", circle_q=32)
+    F = _forces(nodes, segs, b, CUB_C, p=5, levels=5, precision="fp64", h_mode="circle", circle_q=32,
+                m2l_symmetry=sym)
     err = _rel(F[ids], F2)
     pos = {int(k): i for i, k in enumerate(ids)}
     e_d = _rel(F[idd], Fd)
-    print(f"c2 FP64 pass vs Algorithm 2 (200 nodes): {err:.3e}; vs direct sum (32 nodes): {e_d:.3e}")
+    print(f"c2 FP64 pass (symmetry table {sym}) vs Algorithm 2 (200 nodes): {err:.3e}; "
+          f"vs direct sum (32 nodes): {e_d:.3e}")
     assert err <= 1e-10
     # the stored Algorithm-2 forces at the direct-sum nodes show the same interpolation error
     assert abs(_rel(F2[[pos[int(k)] for k in idd]], Fd) - e_d) <= 1e-8
