@@ -93,9 +93,9 @@ def near_flops(wl, work):
 
 # DRAM bytes per target point of one k_near_sym launch (cubic rule, Q = 16), from
 # one ncu capture on the 250,000-segment slab network (dram__bytes_read.sum +
-# dram__bytes_write.sum = 6.530 + 1.344 GB for 1,000,000 points); valid for the
+# dram__bytes_write.sum = 6.494 + 1.347 GB for 1,000,000 points); valid for the
 # kernel version the capture was taken of
-NEAR_SYM_DRAM_BYTES_PER_POINT = (6.530216e9 + 1.343735e9) / 1.0e6
+NEAR_SYM_DRAM_BYTES_PER_POINT = (6.493849e9 + 1.346746e9) / 1.0e6
 
 
 def measured_alu_peaks():
@@ -122,10 +122,10 @@ WORKLOADS = {
 MIXED_M2L = dict(m2l_split=6, m2l_basis=1, m2l_chunks=7, m2l_split_kblocks=1)
 WORKLOADS["c2"] = dict(
     desc="50,000 segments (1,000 polygonal loops of 10-80 segments, log-uniform radii 0.005-0.05, seed 1), cubic "
-         "C11=1.684 C12=1.214 C44=0.754, plain FP64 pass (M2L through transforms on the table of the 16 "
-         "symmetry-orbit representatives, symmetric FP64 near field), order p=5, 5-level octree, unit-circle h Q=32",
+         "C11=1.684 C12=1.214 C44=0.754, plain FP64 pass (M2L through transforms, symmetric FP64 near field), "
+         "order p=5, 5-level octree, unit-circle h Q=32",
     gen=lambda seed: synth.polygon_loops(seed=1 + 1000 * seed), C=lambda: synth.cubic_voigt(),
-    h_mode="circle", circle_q=32, p=5, levels=5, precision="fp64", m2l_symmetry=1)
+    h_mode="circle", circle_q=32, p=5, levels=5, precision="fp64")
 # The compressed M2L of the headline: Chebyshev nodes, singular vectors kept above 5e-5 of
 # the largest (the paper's Chebyshev FMM), FP16 operands with residual passes on the
 # leading block of 64 singular directions, offsets summed in 3 runs.
@@ -714,7 +714,7 @@ def run_fp64_arm(wl, name, d_nodes, d_segs, d_b, nodes, segs, b, flush, stream):
     import paper_1712_07739_gb300 as gb
 
     f = gb.FMM(p=wl["p"], levels=wl["levels"], precision="fp64", h_mode=wl["h_mode"],
-               circle_q=wl.get("circle_q", 0), m2l_fft=1, m2l_symmetry=1).set_material(wl["C"]())
+               circle_q=wl.get("circle_q", 0), m2l_fft=1).set_material(wl["C"]())
     out = torch.empty((len(nodes), 3), dtype=torch.float64, device=d_nodes.device)
     f.build(d_nodes, d_segs, d_b)
     f.nodal_forces(out=out)
@@ -734,8 +734,7 @@ def run_fp64_arm(wl, name, d_nodes, d_segs, d_b, nodes, segs, b, flush, stream):
             "stage_ms": {"precontract": st[0], "p2m_m2m": st[1], "m2l": st[2], "l2l": st[3], "l2p_p2p": st[4],
                          "forces": st[5]},
             "accuracy": oracle_node_error(wl, name, out.cpu().numpy(), nodes, segs, b),
-            "config": "same network, p, tree and unit-circle rule; precision fp64, M2L through transforms on "
-                      "the 16 symmetry-orbit representatives' table"}
+            "config": "same network, p, tree and unit-circle rule; precision fp64, M2L through transforms"}
 
 
 def main():
