@@ -132,18 +132,18 @@ WORKLOADS["c2"] = dict(
 CHEB_M2L = dict(nodes="chebyshev", m2l_svd_tol=5e-5, m2l_split=6, m2l_chunks=3, m2l_split_kblocks=1)
 WORKLOADS["c3"] = dict(
     desc="1,000,000 segments (20,000 loops x 50 in 32 Gaussian slabs, sigma 0.02), cubic C11=1.684 C12=1.214 "
-         "C44=0.754, order p=7 on Chebyshev nodes, 7-level octree, mixed precision (SVD-compressed M2L on the "
-         "tensor cores: FP16 operands, residual passes on the leading singular directions; FP32 near field with "
-         "FP64 separations for close pairs), unit-circle h (cubic form, Q=16 points on the half circle); the same "
-         "step through the plain FP64 pass is timed in the same run",
+         "C44=0.754, order p=7 on Chebyshev nodes, adaptive octree: 7 levels with every leaf holding more than 128 "
+         "Gauss points split once more (children of two split leaves that are not adjacent interact by an M2L one "
+         "level down, adjacent ones directly), mixed precision (SVD-compressed M2L on the tensor cores: FP16 "
+         "operands, residual passes on the leading singular directions; FP32 near field with FP64 separations for "
+         "close pairs), unit-circle h (cubic form, Q=16 points on the half circle); the same step through the "
+         "plain FP64 pass (uniform 7-level tree) is timed in the same run",
     gen=lambda seed: synth.slab_loops(seed=2 + 1000 * seed), C=lambda: synth.cubic_voigt(),
-    h_mode="circle", circle_q=16, p=7, levels=7, precision="mixed", fp64_arm=True, **CHEB_M2L)
-WORKLOADS["c3a"] = dict(
-    desc="c3 on an adaptive octree: the 7-level tree with every leaf holding more than 128 Gauss points split "
-         "once more (children of two split leaves that are not adjacent interact by an M2L one level down, "
-         "adjacent ones directly)",
+    h_mode="circle", circle_q=16, p=7, levels=7, precision="mixed", refine_points=128, fp64_arm=True, **CHEB_M2L)
+WORKLOADS["c3u"] = dict(
+    desc="c3 on the uniform 7-level octree (no leaf split)",
     gen=WORKLOADS["c3"]["gen"], C=WORKLOADS["c3"]["C"], h_mode="circle", circle_q=16, p=7, levels=7,
-    precision="mixed", refine_points=128, **CHEB_M2L)
+    precision="mixed", **CHEB_M2L)
 WORKLOADS["c3legendre"] = dict(
     desc="c3 on equispaced nodes with the dense M2L (every one of the 54 p^6 products per cell pair, on FP16 "
          "Legendre moments of the source cells with residual passes on the low-order moments)",
@@ -630,7 +630,7 @@ def run_ours(args, wl):
 
 GOLDEN = {"c3": "c3_sampled_forces.json", "c3q": "c3q_sampled_forces.json", "c3_fp64": "c3_sampled_forces.json",
           "c2": "c2_forces.json", "c3svd": "c3_sampled_forces.json", "c3legendre": "c3_sampled_forces.json",
-          "c3a": "c3_sampled_forces.json"}
+          "c3u": "c3_sampled_forces.json"}
 
 
 def m2l_options(wl):

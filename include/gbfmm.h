@@ -142,14 +142,18 @@ typedef struct {
                               U^T T_o R, and expands the local values S = U S'.  The bases and
                               operators are built in FP64 at fmm_set_material; m2l_basis is
                               ignored.  0 = off (fmm_default_options). */
-    int refine_points;     /* MIXED with the compressed M2L and the unit-circle h: > 0 makes
+    int refine_points;     /* MIXED with the compressed M2L on FP16 operands (m2l_split 4, 5
+                              or 6) and the unit-circle h: > 0 makes
                               the tree adaptive -- every leaf holding more than this many Gauss
                               points is split once more (one level below the leaves).  Two
                               adjacent split leaves interact through their children: adjacent
                               children directly, the others by an M2L one level down; all
                               other adjacent leaves directly; points of split leaves take their
-                              child's local values.  Nodal forces only (fmm_eval_stress keeps
-                              the uniform tree).  0 = off (fmm_default_options). */
+                              child's local values.  The children's M2L runs one GEMM per
+                              offset over the occupied pairs (cuBLAS) and reads the pair counts
+                              back, so the pass synchronises once.  Nodal forces only
+                              (fmm_eval_stress keeps the uniform tree).  0 = off
+                              (fmm_default_options). */
     int m2l_symmetry;      /* FP64 with m2l_fft = 1: 1 = keep the transformed operators of 16
                               offsets only (Sec. 6: the cube's symmetries of space and kernel
                               map every one of the 316 operators to a signed permutation of

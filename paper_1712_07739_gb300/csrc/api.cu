@@ -165,7 +165,8 @@ extern "C" int fmm_create(gbfmm_ctx **out, const gbfmm_options *opt, void *strea
     // the adaptive tree runs its extra level through the compressed M2L and its near
     // field through the symmetric kernel of the unit-circle h
     if (opt->refine_points < 0 ||
-        (opt->refine_points > 0 && (opt->m2l_svd_tol <= 0.0 || opt->h_mode != GBFMM_H_CIRCLE)))
+        (opt->refine_points > 0 && (opt->m2l_svd_tol <= 0.0 || opt->h_mode != GBFMM_H_CIRCLE ||
+                                    opt->m2l_split < GBFMM_M2L_FP16)))
         return GBFMM_ERR_INVALID_ARG;
     // the symmetry-reduced operator table belongs to the FP64 M2L through transforms
     if (opt->m2l_symmetry < 0 || opt->m2l_symmetry > 1 ||
@@ -294,7 +295,8 @@ uint64_t layout_hash(const gbfmm_ctx *c) {
                           c->nw.pkeys, c->nw.pmisc, c->nw.part, c->tc.Uh, c->tc.Ul, c->tc.Rh, c->tc.Rl,
                           c->tc.Xh, c->tc.Xl, c->tc.d_scal, c->tc.d_bits, c->tc.Wc, c->tc.Sc, c->tc.blas_ws,
                           c->rf.child_of, c->rf.ref_start, c->rf.ref_leaf, c->rf.child_start, c->rf.pfine,
-                          c->rf.W7, c->rf.S7, c->rf.Wc7, c->rf.Sc7};
+                          c->rf.W7, c->rf.S7, c->rf.Wc7, c->rf.Sc7, c->tc.d_pcnt, c->tc.d_pairs, c->tc.Gh,
+                          c->tc.Gl, c->tc.Yf};
     mix(ptrs, sizeof(ptrs));
     v(c->mat.mode), v(c->mat.Q), v(c->mat.cubic), v(c->tc.n_work), v(c->tc.split), v(c->tc.tf32);
     mix(c->tc.wofs, sizeof(c->tc.wofs));

@@ -1020,13 +1020,10 @@ int mixed_pass(gbfmm_ctx *ctx, bool free_targets, int64_t n_t) {
                 k_m2m_merge<float><<<g, 256, size_t(4) * P3 * 9 * sizeof(float), st>>>(p, lev, tr, occ, ctx->d_Wf);
         }
         if (fine) {
-            // the children of split leaves: multipole values and their occupancy at level L
-            ctx->launches += 2;
+            // the children of split leaves: their multipole values
+            ++ctx->launches;
             k_p2m_fine<float><<<unsigned(n_fine), 256, 0, st>>>(p, ctx->opt.nodes, L, ctx->d_box, n_ref, RF.ref_leaf,
                                                                 RF.child_start, ctx->d_y, ctx->d_q, RF.W7);
-            CK(cudaMemsetAsync(occ + cell_base(L), 0, (cell_base(L + 1) - cell_base(L)) * sizeof(int), st));
-            k_fine_occ<<<nblk(n_fine, 256), 256, 0, st>>>(n_fine, L, n_ref, RF.ref_leaf, RF.child_start,
-                                                          occ + cell_base(L));
         }
         CK(cudaGetLastError());
     }

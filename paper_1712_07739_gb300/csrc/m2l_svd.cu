@@ -448,13 +448,202 @@ int svd_operators(gbfmm_ctx *ctx, const int *d_off, const int *d_lo, int n_off) 
     return rc;
 }
 
+// per-tree scale slots: the W transforms of levels 0..MAXLEV-1, the S transforms of the same
+// levels, and the children's compressed multipole values of the adaptive tree
+constexpr int kFineSlot = 2 * GB_TC_MAXLEV;
+constexpr int kScaleSlots = 2 * GB_TC_MAXLEV + 1;
+
+static int split_level(gbfmm_ctx *ctx, const float *src, int64_t rows, int n, int ldx, int slot, float sbasis);
+
+// adaptive tree: the (target child, source child) pairs of the children's M2L, grouped by
+// operator.  The children of a split leaf meet the children of the split leaves around it
+// that are not adjacent to them at the children's level (the interaction list one level
+// below the leaves, restricted to children of split leaves; offset = target - source).
+// pass 0 counts the pairs of every operator, pass 1 writes them from the scanned counts.
+__global__ void k_fine_pairs(int pass, int64_t n_fine, int L, const int *__restrict__ n_ref,
+                             const int *__restrict__ ref_leaf, const int *__restrict__ ref_start,
+                             const int *__restrict__ child_start, const int *__restrict__ op_of,
+                             int *__restrict__ cnt, const int *__restrict__ first, int *__restrict__ cur,
+                             int2 *__restrict__ pairs) {
+    const int64_t f = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (f >= n_fine) return;
+    const int r = int(f >> 3), c = int(f & 7);
+    if (r >= *n_ref || child_start[9 * r + c + 1] == child_start[9 * r + c]) return;
+    const int nl = 1 << (L - 1);
+    const int A = ref_leaf[r];
+    const int ax = A % nl, ay = (A / nl) % nl, az = A / (nl * nl);
+    const int tx = 2 * ax + (c & 1), ty = 2 * ay + ((c >> 1) & 1), tz = 2 * az + (c >> 2);
+    for (int nb = 0; nb < 27; ++nb) {
+        if (nb == 13) continue;  // siblings are adjacent to each other
+        const int bx = ax + nb % 3 - 1, by = ay + (nb / 3) % 3 - 1, bz = az + nb / 9 - 1;
+        if (bx < 0 || by < 0 || bz < 0 || bx >= nl || by >= nl || bz >= nl) continue;
+        const int B = (bz * nl + by) * nl + bx;
+        if (ref_start[B + 1] == ref_start[B]) continue;
+        const int rB = ref_start[B];
+        for (int c2 = 0; c2 < 8; ++c2) {
+            if (child_start[9 * rB + c2 + 1] == child_start[9 * rB + c2]) continue;
+            const int ox = tx - (2 * bx + (c2 & 1)), oy = ty - (2 * by + ((c2 >> 1) & 1)),
+                      oz = tz - (2 * bz + (c2 >> 2));
+            if (max(abs(ox), max(abs(oy), abs(oz))) < 2) continue;
+            const int i = op_of[((oz + 3) * 7 + (oy + 3)) * 7 + (ox + 3)];
+            if (pass == 0)
+                atomicAdd(&cnt[i], 1);
+            else
+                pairs[first[i] + atomicAdd(&cur[i], 1)] = make_int2(int(f), 8 * rB + c2);
+        }
+    }
+}
+
+// the source rows of pairs [p0, p0 + n): FP16 hi (Kp values) and lo (the leading Kp_lo)
+__global__ void k_fine_gather(int64_t n, const int2 *__restrict__ pairs, int Kp, int Kp_lo,
+                              const __half *__restrict__ Xh, const __half *__restrict__ Xl, __half *__restrict__ Gh,
+                              __half *__restrict__ Gl) {
+    const int64_t total = n * (Kp + Kp_lo);
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t row = idx / (Kp + Kp_lo);
+        const int k = int(idx - row * (Kp + Kp_lo));
+        const int64_t src = pairs[row].y;
+        if (k < Kp)
+            Gh[row * Kp + k] = Xh[src * Kp + k];
+        else
+            Gl[row * Kp_lo + (k - Kp)] = Xl[src * Kp + (k - Kp)];
+    }
+}
+
+// target children's compressed local values += the products of one operator's pairs, times
+// the level factor (2^L / H)^2 of the children's cells (each target once per operator)
+__global__ void k_fine_scatter(int64_t n, const int2 *__restrict__ pairs, const float *__restrict__ Y, int Np,
+                               int r1, int L, const TreeBox *__restrict__ box, float *__restrict__ Sc7) {
+    const double nh = double(1 << L) / box->H;
+    const float lvl = float(nh * nh);
+    const int64_t total = n * r1;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t row = idx / r1;
+        const int k = int(idx - row * r1);
+        Sc7[int64_t(pairs[row].x) * r1 + k] += Y[row * Np + k] * lvl;
+    }
+}
+
+// The children's M2L of the adaptive tree (Algorithm 2's M2L one level below the leaves,
+// between children of split leaves): their compressed multipole values split into FP16
+// hi + lo with their own power of two, then per operator C_o the gathered source rows of its
+// pairs as one GEMM (hi x hi over all of K, the residual products on the leading Kp_lo
+// columns as in the tensor-core kernel), added to the target children's compressed local
+// values operator by operator (a fixed order).  Reads the pair counts back to size the GEMMs.
+int fine_m2l(gbfmm_ctx *ctx) {
+    TcPlan &T = ctx->tc;
+    auto &RF = ctx->rf;
+    cudaStream_t st = ctx->stream;
+    const int L = ctx->L, n_op = T.n_off;
+    const int64_t n_fine = RF.fine_rows();
+    if (!T.fp16 || n_op != 316)
+        return set_err(ctx, GBFMM_ERR_INVALID_ARG, "adaptive tree: the children's M2L needs FP16 operands");
+    if (n_fine == 0) return GBFMM_OK;
+    const int *n_ref = RF.ref_start + ctx->n_leaves;
+    if (!T.d_pcnt) {
+        CK(cudaMalloc(&T.d_pcnt, (343 + 316 + 317 + 316) * sizeof(int)));
+        int op_of[343];
+        for (int oi = 0, i = 0; oi < 343; ++oi) {
+            const int ox = oi % 7 - 3, oy = (oi / 7) % 7 - 3, oz = oi / 49 - 3;
+            op_of[oi] = std::max(std::abs(ox), std::max(std::abs(oy), std::abs(oz))) >= 2 ? i++ : -1;
+        }
+        CK(cudaMemcpy(T.d_pcnt, op_of, sizeof(op_of), cudaMemcpyHostToDevice));
+    }
+    int *op_of = T.d_pcnt, *cnt = T.d_pcnt + 343, *first = cnt + 316, *cur = first + 317;
+    CK(cudaMemsetAsync(cnt, 0, 316 * sizeof(int), st));
+    CK(cudaMemsetAsync(cur, 0, 316 * sizeof(int), st));
+    CK(cudaMemsetAsync(RF.Sc7, 0, size_t(n_fine) * T.r1 * sizeof(float), st));
+    ++ctx->launches;
+    k_fine_pairs<<<nblk(n_fine, 128), 128, 0, st>>>(0, n_fine, L, n_ref, RF.ref_leaf, RF.ref_start, RF.child_start,
+                                                    op_of, cnt, nullptr, nullptr, nullptr);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(T.h_pcnt, cnt, 316 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    T.h_pfirst[0] = 0;
+    int64_t biggest = 0;
+    for (int i = 0; i < 316; ++i) {
+        T.h_pfirst[i + 1] = T.h_pfirst[i] + T.h_pcnt[i];
+        biggest = std::max<int64_t>(biggest, T.h_pcnt[i]);
+    }
+    const int64_t total = T.h_pfirst[316];
+    if (total == 0) return GBFMM_OK;
+    if (int rc = grow_dev(ctx, T.pair_cap, total, {{(void **)&T.d_pairs, size_t(total) * sizeof(int2)}},
+                          "adaptive-tree M2L pairs"))
+        return rc;
+    CK(cudaMemcpyAsync(first, T.h_pfirst, 317 * sizeof(int), cudaMemcpyHostToDevice, st));
+    ++ctx->launches;
+    k_fine_pairs<<<nblk(n_fine, 128), 128, 0, st>>>(1, n_fine, L, n_ref, RF.ref_leaf, RF.ref_start, RF.child_start,
+                                                    op_of, nullptr, first, cur, T.d_pairs);
+    CK(cudaGetLastError());
+    // the children's values in FP16 (operator scale folded into alpha)
+    const int Kp = T.Kp, Kp_lo = T.Kp_lo, Np = T.Np;
+    if (int rc = split_level(ctx, RF.Wc7, n_fine, T.r2, Kp, kFineSlot, float(T.op_scale))) return rc;
+    // runs of consecutive operators of at most `run` pairs (at least the largest operator's)
+    const int64_t run = std::max<int64_t>(biggest, int64_t(1) << 19);
+    if (int rc = grow_dev(ctx, T.g_cap, run,
+                          {{&T.Gh, size_t(run) * Kp * sizeof(__half)},
+                           {&T.Gl, size_t(run) * std::max(Kp_lo, 1) * sizeof(__half)},
+                           {(void **)&T.Yf, size_t(run) * Np * sizeof(float)}},
+                          "adaptive-tree M2L operands"))
+        return rc;
+    cublasHandle_t h = (cublasHandle_t)T.blas;
+    const float *alpha = T.d_scal + 2 + kFineSlot, *zero = T.d_scal, *one = T.d_scal + 1;
+    const __half *Thi = static_cast<const __half *>(T.Thi), *Tlo = static_cast<const __half *>(T.Tlo);
+    __half *Gh = static_cast<__half *>(T.Gh), *Gl = static_cast<__half *>(T.Gl);
+    BL(cublasSetPointerMode(h, CUBLAS_POINTER_MODE_DEVICE));
+    auto gemm = [&](int k, const __half *A, int lda, const __half *B, int ldb, const float *beta, float *C,
+                    int n) -> int {
+        const cublasStatus_t e = cublasGemmEx(h, CUBLAS_OP_T, CUBLAS_OP_N, Np, n, k, alpha, A, CUDA_R_16F, lda, B,
+                                              CUDA_R_16F, ldb, beta, C, CUDA_R_32F, Np, CUBLAS_COMPUTE_32F,
+                                              CUBLAS_GEMM_DEFAULT);
+        if (e == CUBLAS_STATUS_SUCCESS) return GBFMM_OK;
+        cublasSetPointerMode(h, CUBLAS_POINTER_MODE_HOST);
+        return set_err(ctx, GBFMM_ERR_CUDA, "cuBLAS adaptive-tree M2L GEMM: " + std::to_string(int(e)));
+    };
+    for (int i0 = 0; i0 < 316;) {
+        int i1 = i0;
+        while (i1 < 316 && T.h_pfirst[i1 + 1] - T.h_pfirst[i0] <= run) ++i1;
+        const int64_t p0 = T.h_pfirst[i0], np = T.h_pfirst[i1] - p0;
+        if (np > 0) {
+            ++ctx->launches;
+            k_fine_gather<<<unsigned(std::min<int64_t>(nblk(np * (Kp + Kp_lo), 256), 16 * 152)), 256, 0, st>>>(
+                np, T.d_pairs + p0, Kp, Kp_lo, static_cast<const __half *>(T.Xh), static_cast<const __half *>(T.Xl),
+                Gh, Gl);
+            CK(cudaGetLastError());
+        }
+        for (int i = i0; i < i1; ++i) {
+            const int n = T.h_pcnt[i];
+            if (n == 0) continue;
+            const int64_t row = T.h_pfirst[i] - p0;
+            float *Y = T.Yf + row * Np;
+            // Y^T (Np x n) = C_o (Np x Kp, row-major) W'^T (Kp x n)
+            if (int rc = gemm(Kp, Thi + size_t(i) * Np * Kp, Kp, Gh + row * Kp, Kp, zero, Y, n)) return rc;
+            if (T.lo_host[i] >= 0 && Kp_lo > 0) {
+                if (int rc = gemm(Kp_lo, Tlo + size_t(T.lo_host[i]) * Np * Kp_lo, Kp_lo, Gh + row * Kp, Kp, one, Y, n))
+                    return rc;
+                if (int rc = gemm(Kp_lo, Thi + size_t(i) * Np * Kp, Kp, Gl + row * Kp_lo, Kp_lo, one, Y, n))
+                    return rc;
+            }
+            ++ctx->launches;
+            k_fine_scatter<<<unsigned(std::min<int64_t>(nblk(int64_t(n) * T.r1, 256), 8 * 152)), 256, 0, st>>>(
+                n, T.d_pairs + T.h_pfirst[i], Y, Np, T.r1, L, ctx->d_box, RF.Sc7);
+            CK(cudaGetLastError());
+        }
+        i0 = i1;
+    }
+    BL(cublasSetPointerMode(h, CUBLAS_POINTER_MODE_HOST));
+    return GBFMM_OK;
+}
+
 int svd_prepare(gbfmm_ctx *ctx) {
     TcPlan &T = ctx->tc;
     auto &RF = ctx->rf;
     const int P3 = ctx->opt.p * ctx->opt.p * ctx->opt.p;
     const int64_t per = std::max(T.r1, T.r2);
-    // global rows of every M2L level (one more with the adaptive tree's children)
-    const int64_t rows = cell_base(ctx->L + (RF.on ? 1 : 0));
+    // rows of every M2L level (the adaptive tree's children keep compact arrays)
+    const int64_t rows = cell_base(ctx->L);
     if (int rc = grow_dev(ctx, T.c_cap, rows * per,
                           {{(void **)&T.Wc, size_t(rows) * per * sizeof(float)},
                            {(void **)&T.Sc, size_t(rows) * per * sizeof(float)}},
@@ -476,8 +665,8 @@ int svd_prepare(gbfmm_ctx *ctx) {
                           {{&T.Xh, size_t(need) * sizeof(__half)}, {&T.Xl, size_t(need) * sizeof(__half)}},
                           "compressed M2L transform operands"))
         return rc;
-    if (!T.d_scal) CK(cudaMalloc(&T.d_scal, (2 + 2 * GB_TC_MAXLEV) * sizeof(float)));
-    if (!T.d_bits) CK(cudaMalloc(&T.d_bits, 2 * GB_TC_MAXLEV * sizeof(unsigned)));
+    if (!T.d_scal) CK(cudaMalloc(&T.d_scal, (2 + kScaleSlots) * sizeof(float)));
+    if (!T.d_bits) CK(cudaMalloc(&T.d_bits, kScaleSlots * sizeof(unsigned)));
     const float consts[2] = {0.f, 1.f};
     CK(cudaMemcpyAsync(T.d_scal, consts, sizeof(consts), cudaMemcpyHostToDevice, ctx->stream));
     return ensure_blas(ctx);
@@ -521,33 +710,6 @@ static int split_level(gbfmm_ctx *ctx, const float *src, int64_t rows, int n, in
     return GBFMM_OK;
 }
 
-// adaptive tree: rows of the children's compact arrays [8 r + c][rowlen] to and from the
-// global rows of level L (gather: children without points, which the M2L did not write,
-// and unused capacity read zeros)
-__global__ void k_fine_rows(int64_t n_fine, int L, const int *__restrict__ n_ref, const int *__restrict__ ref_leaf,
-                            const int *__restrict__ child_start, int rowlen, float *__restrict__ compact,
-                            float *__restrict__ global, int gather) {
-    const int nl = 1 << (L - 1), nf = 2 * nl;
-    const int nr = *n_ref;
-    const int64_t total = n_fine * rowlen;
-    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
-         idx += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t f = idx / rowlen;
-        const int k = int(idx - f * rowlen), r = int(f >> 3), c = int(f & 7);
-        if (r >= nr || child_start[9 * r + c + 1] == child_start[9 * r + c]) {
-            if (gather) compact[idx] = 0.f;
-            continue;
-        }
-        const int leaf = ref_leaf[r];
-        const int x = leaf % nl, y = (leaf / nl) % nl, z = leaf / (nl * nl);
-        const int64_t lin = (int64_t(2 * z + (c >> 2)) * nf + (2 * y + ((c >> 1) & 1))) * nf + (2 * x + (c & 1));
-        if (gather)
-            compact[idx] = global[lin * rowlen + k];
-        else
-            global[lin * rowlen + k] = compact[idx];
-    }
-}
-
 int svd_transform_w(gbfmm_ctx *ctx, const float *Wf, bool fine) {
     TcPlan &T = ctx->tc;
     auto &RF = ctx->rf;
@@ -569,10 +731,6 @@ int svd_transform_w(gbfmm_ctx *ctx, const float *Wf, bool fine) {
         if (int rc = split_gemm(ctx, CUBLAS_OP_T, T.r2, n_fine, lds, T.Rh, T.Rl, lds, lds, T.d_scal + 2 + l, RF.Wc7,
                                 T.r2))
             return rc;
-        ++ctx->launches;
-        k_fine_rows<<<unsigned(std::min<int64_t>(nblk(n_fine * T.r2, 256), 16 * 152)), 256, 0, ctx->stream>>>(
-            n_fine, l, RF.ref_start + ctx->n_leaves, RF.ref_leaf, RF.child_start, T.r2, RF.Wc7, T.Wc + cell_base(l) * T.r2, 0);
-        CK(cudaGetLastError());
     }
     return GBFMM_OK;
 }
@@ -591,13 +749,9 @@ int svd_expand_s(gbfmm_ctx *ctx, float *Sf, bool fine) {
             return rc;
     }
     if (fine) {
-        // the children's compressed local values gathered from level L, expanded into S7
+        // the children's compressed local values (fine_m2l), expanded into S7
         const int l = ctx->L;
         const int64_t n_fine = RF.fine_rows();
-        ++ctx->launches;
-        k_fine_rows<<<unsigned(std::min<int64_t>(nblk(n_fine * T.r1, 256), 16 * 152)), 256, 0, ctx->stream>>>(
-            n_fine, l, RF.ref_start + ctx->n_leaves, RF.ref_leaf, RF.child_start, T.r1, RF.Sc7, T.Sc + cell_base(l) * T.r1, 1);
-        CK(cudaGetLastError());
         if (int rc = split_level(ctx, RF.Sc7, n_fine, T.r1, T.r1, GB_TC_MAXLEV + l, T.sU)) return rc;
         if (int rc = split_gemm(ctx, CUBLAS_OP_N, nt, n_fine, T.r1, T.Uh, T.Ul, pad8(nt), T.r1,
                                 T.d_scal + 2 + GB_TC_MAXLEV + l, RF.S7, nt))
@@ -609,7 +763,7 @@ int svd_expand_s(gbfmm_ctx *ctx, float *Sf, bool fine) {
 void svd_free(gbfmm_ctx *ctx, bool borrowed) {
     TcPlan &T = ctx->tc;
     if (T.blas) cublasDestroy((cublasHandle_t)T.blas);
-    void *mine[] = {T.Wc, T.Sc, T.blas_ws, T.Xh, T.Xl, T.d_scal, T.d_bits};
+    void *mine[] = {T.Wc, T.Sc, T.blas_ws, T.Xh, T.Xl, T.d_scal, T.d_bits, T.d_pcnt, T.d_pairs, T.Gh, T.Gl, T.Yf};
     for (void *q : mine)
         if (q) cudaFree(q);
     if (!borrowed) {
@@ -627,5 +781,10 @@ void svd_free(gbfmm_ctx *ctx, bool borrowed) {
     T.Uh = T.Ul = T.Rh = T.Rl = nullptr;
     T.c_cap = 0;
     T.x_cap = 0;
+    T.d_pcnt = nullptr;
+    T.d_pairs = nullptr;
+    T.Gh = T.Gl = nullptr;
+    T.Yf = nullptr;
+    T.pair_cap = T.g_cap = 0;
     T.bases_ok = 0;
 }

@@ -1038,6 +1038,7 @@ int m2l_tc_setup(gbfmm_ctx *ctx) {
             }
     T.n_off = int(off.size() / 3);
     T.n_lo = n_lo;
+    for (int i = 0; i < T.n_off && i < 320; ++i) T.lo_host[i] = short(lo_of[i]);
     OffsetEntry ent[8][189];
     for (int c = 0; c < 8; ++c) {
         const int cc[3] = {c & 1, (c >> 1) & 1, c >> 2};
@@ -1203,7 +1204,7 @@ static int encode(gbfmm_ctx *ctx, CUtensorMap *tm, void *base, int rank, const c
 // Per-tree buffers: packed W (hi / lo), tensor maps, work list.
 int m2l_tc_prepare(gbfmm_ctx *ctx) {
     TcPlan &T = ctx->tc;
-    const int L = ctx->L + (ctx->rf.on ? 1 : 0);  // the adaptive tree's children: one more M2L level
+    const int L = ctx->L;
     if (L - 1 >= GB_TC_MAXLEV) return set_err(ctx, GBFMM_ERR_INVALID_ARG, "tensor-core M2L: too many levels");
     int64_t tot = 0;
     for (int l = 2; l < L; ++l) {
@@ -1233,9 +1234,9 @@ int m2l_tc_prepare(gbfmm_ctx *ctx) {
 int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *occ, const int *tocc, float *Sf,
                double *S64, bool fine) {
     TcPlan &T = ctx->tc;
-    // with the adaptive tree's children the M2L runs one level deeper (level ctx->L: the
-    // children of split leaves, their compressed values gathered and scattered by svd_*)
-    const int L = ctx->L + (fine ? 1 : 0), p = ctx->opt.p, P3 = p * p * p;
+    // fine: the adaptive tree's children (level ctx->L) take part through fine_m2l, after the
+    // tensor-core M2L of levels 2 .. L-1
+    const int L = ctx->L, p = ctx->opt.p, P3 = p * p * p;
     M2LParams prm;  // copied by value into the launch (kernel parameter space)
     std::memset(&prm, 0, sizeof(prm));
     if (T.fp16) CK(cudaMemsetAsync(T.d_wmax, 0, GB_TC_MAXLEV * sizeof(unsigned), ctx->stream));
@@ -1297,9 +1298,6 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
         ++ctx->launches;
         k_mb_flags<<<nblk(int64_t(1) << (3 * l), 256), 256, 0, ctx->stream>>>(l, tocc, T.d_flags);
     }
-    if (ctx->rf.on && !fine)  // the slots of the children's level hold no targets in this pass
-        CK(cudaMemsetAsync(T.d_flags + slot_base(L), 0, (slot_base(L + 1) - slot_base(L)) * sizeof(int),
-                           ctx->stream));
     ctx->launches += 3;
     k_scan_flags<<<1, 1024, 0, ctx->stream>>>(int(T.n_slots), T.d_flags, T.d_pos);
     k_mb_list<<<nblk(T.n_slots, 256), 256, 0, ctx->stream>>>(int(T.n_slots), L, T.d_flags, T.d_pos, T.d_list);
@@ -1361,7 +1359,11 @@ int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *oc
                                                    S64, T.d_status, stages, T.groups);
         CK(cudaGetLastError());
     }
-    if (T.svd) return svd_expand_s(ctx, Sf, fine);  // S = U S'
+    if (T.svd) {
+        if (fine)
+            if (int rc = fine_m2l(ctx)) return rc;
+        return svd_expand_s(ctx, Sf, fine);  // S = U S'
+    }
     return GBFMM_OK;
 }
 

@@ -59,6 +59,16 @@ struct TcPlan {
     void *blas = nullptr;      // cuBLAS handle of this context (its own workspace: contexts of a
     void *blas_ws = nullptr;   // batch run concurrently)
     size_t blas_ws_bytes = 0;
+    short lo_host[320] = {0};  // per operator (offset order of the table): its residual operator or -1
+    // adaptive tree: the children's M2L over the occupied (target, source) pairs, one GEMM per
+    // offset (m2l_svd.cu, fine_m2l)
+    int *d_pcnt = nullptr;     // [343 offset slot -> operator][316 counts][317 firsts][316 cursors]
+    int2 *d_pairs = nullptr;   // (target child, source child), grouped by operator
+    int64_t pair_cap = 0;
+    void *Gh = nullptr, *Gl = nullptr;  // gathered source rows of a run of offsets, FP16 hi / lo
+    float *Yf = nullptr;       // their products [pairs][Np]
+    int64_t g_cap = 0;
+    int h_pcnt[316] = {0}, h_pfirst[317] = {0};  // host copies of the counts and their scan
 };
 
 int m2l_tc_setup(gbfmm_ctx *ctx);    // operators (per medium and p)
@@ -78,6 +88,7 @@ int m2l_tc_status(gbfmm_ctx *ctx, int *out);
 int svd_bases(gbfmm_ctx *ctx);
 int svd_operators(gbfmm_ctx *ctx, const int *d_off, const int *d_lo, int n_off);
 int svd_prepare(gbfmm_ctx *ctx);
+int fine_m2l(gbfmm_ctx *ctx);  // adaptive tree: children's M2L into their compressed local values
 int svd_transform_w(gbfmm_ctx *ctx, const float *Wf, bool fine);
 int svd_expand_s(gbfmm_ctx *ctx, float *Sf, bool fine);
 void svd_free(gbfmm_ctx *ctx, bool borrowed);

@@ -159,6 +159,7 @@ int share_material(gbfmm_ctx *ctx, const gbfmm_ctx *src) {
     T.tf32 = S.tf32;
     T.fp16 = S.fp16;
     T.op_scale = S.op_scale;
+    std::memcpy(T.lo_host, S.lo_host, sizeof(T.lo_host));
     T.modal = S.modal;
     std::memcpy(T.basisV, S.basisV, sizeof(T.basisV));
     std::memcpy(T.basisCt, S.basisCt, sizeof(T.basisCt));

@@ -137,19 +137,19 @@ def test_refine_needs_compressed_circle_pass():
 
 
 def test_fullsize_adaptive_against_direct_sum():
-    """The 1M-segment slab network of the bench (p = 7 on Chebyshev nodes, 7
-    levels, unit-circle Q = 16, cubic, compressed M2L) with its leaves above
-    the bench's refinement threshold split, against the stored direct-sum
-    forces at 32 nodes."""
+    """The 1M-segment slab network of the bench's headline (p = 7 on
+    Chebyshev nodes, 7 levels with the leaves above the refinement threshold
+    split, unit-circle Q = 16, cubic, compressed M2L), against the stored
+    direct-sum forces at 32 nodes."""
     import sys
 
     sys.path.insert(0, ROOT)
     import bench
     import paper_1712_07739_gb300 as gb
 
-    wl = bench.WORKLOADS["c3a"]
+    wl = bench.WORKLOADS["c3"]
     nodes, segs, b = wl["gen"](0)
-    with open(os.path.join(ROOT, "tests", "golden", bench.GOLDEN["c3a"])) as fh:
+    with open(os.path.join(ROOT, "tests", "golden", bench.GOLDEN["c3"])) as fh:
         gold = json.load(fh)
     ids = np.array(gold["node_ids"])
     f = gb.FMM(p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],

@@ -57,9 +57,10 @@ def _forces(nodes, segs, b, wl, **over):
     kw = dict(p=wl["p"], levels=wl["levels"], precision=wl["precision"], h_mode=wl["h_mode"],
               circle_q=wl["circle_q"], **bench.m2l_options(wl))
     kw.update(over)
-    if kw["precision"] != "mixed":  # the compressed M2L (and Chebyshev nodes) belong to the mixed pass
+    if kw["precision"] != "mixed":  # the compressed M2L, Chebyshev nodes and the adaptive tree belong to the mixed pass
         kw.pop("nodes", None)
         kw.pop("m2l_svd_tol", None)
+        kw.pop("refine_points", None)
     f = gb.FMM(**kw).set_material(wl["C"]())
     f.build(torch.tensor(nodes, device="cuda"), torch.tensor(segs, device="cuda"), torch.tensor(b, device="cuda"))
     F = f.nodal_forces().cpu().numpy()
@@ -69,7 +70,8 @@ def _forces(nodes, segs, b, wl, **over):
 
 
 @pytest.mark.parametrize("label,workload,over,tol", [
-    pytest.param("bench configuration", "c3", {}, 1e-4, id="bench"),
+    pytest.param("bench configuration (adaptive tree)", "c3", {}, 1e-4, id="bench"),
+    pytest.param("uniform 7-level tree", "c3u", {}, 1e-4, id="uniform"),
     pytest.param("Chebyshev, compressed M2L, p=8", "c3", {"p": 8}, 1e-4, id="p8"),
     pytest.param("equispaced, dense M2L", "c3legendre", {}, 1e-4, id="dense"),
     pytest.param("equispaced, compressed M2L", "c3svd", {}, 1e-4, id="svd"),
