@@ -96,6 +96,9 @@ def near_flops(wl, work):
 # dram__bytes_write.sum = 6.494 + 1.347 GB for 1,000,000 points); valid for the
 # kernel version the capture was taken of
 NEAR_SYM_DRAM_BYTES_PER_POINT = (6.493849e9 + 1.346746e9) / 1.0e6
+# the same two counters for the headline's launch itself (1M segments, adaptive tree at
+# threshold 128; a one-pass capture of the full-size run); None until captured
+NEAR_SYM_ADAPTIVE_1M_DRAM_BYTES = None
 
 
 def measured_alu_peaks():
@@ -676,10 +679,15 @@ def roofline_of(wl, work, m2l_ms, leaf_ms, m2l_fft, peaks, ranks=None):
         flops, kname = near_flops(wl, work)
         achieved = flops / (leaf_ms / 1e3) / 1e12
         dom, bound, peak, src = kname + " (L2P + near-field P2P)", "alu", alu_peak, peaks["source"]
-        if kname == "k_near_sym" and wl.get("circle_q") == 16:
+        if kname == "k_near_sym" and wl.get("circle_q") == 16 and not wl.get("refine_points"):
             traffic = NEAR_SYM_DRAM_BYTES_PER_POINT * work["points"]
             traffic_src = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_near_sym on the "
                            "250k-segment slab network, scaled by points")
+        elif (kname == "k_near_sym" and wl.get("refine_points") == 128 and work["points"] == 4_000_000
+              and NEAR_SYM_ADAPTIVE_1M_DRAM_BYTES):
+            traffic = NEAR_SYM_ADAPTIVE_1M_DRAM_BYTES
+            traffic_src = ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this launch "
+                           "(1M-segment network, adaptive tree at threshold 128)")
     else:
         fft = fp64 and m2l_fft == 1
         # dense: 2*54*p^6 per cell pair; through transforms: 54 complex multiply-adds
