@@ -97,8 +97,8 @@ def near_flops(wl, work):
 # kernel version the capture was taken of
 NEAR_SYM_DRAM_BYTES_PER_POINT = (6.493849e9 + 1.346746e9) / 1.0e6
 # the same two counters for the headline's launch itself (1M segments, adaptive tree at
-# threshold 128; a one-pass capture of the full-size run); None until captured
-NEAR_SYM_ADAPTIVE_1M_DRAM_BYTES = None
+# threshold 128; a one-pass capture of the full-size run)
+NEAR_SYM_ADAPTIVE_1M_DRAM_BYTES = 21815144704 + 4425026816
 
 
 def measured_alu_peaks():
