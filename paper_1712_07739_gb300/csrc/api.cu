@@ -89,8 +89,8 @@ static int ensure_tree_buffers(gbfmm_ctx *ctx) {
     if (int rc = grow_dev(ctx, ctx->cap_segs, ns, {{(void **)&ctx->d_len0, ns * sizeof(double)}}, "segments"))
         return rc;
     {
-        // occupancy scratch: sources and targets per cell (with the adaptive tree, sources of
-        // one more level: the children of split leaves)
+        // occupancy scratch: sources and targets per cell (with the adaptive tree, one more
+        // level for the children of split leaves, which fmm_work_counts counts)
         const int64_t n_occ = 2 * (ctx->rf.on ? cell_base(ctx->L + 1) : nc);
         GrowBuf b[3] = {{(void **)&ctx->d_tmp_i, n_occ * sizeof(int)},
                         {(void **)&ctx->d_W, nc * P3 * 9 * sizeof(double)},

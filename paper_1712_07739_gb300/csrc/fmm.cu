@@ -266,7 +266,8 @@ __global__ void k_l2l(int p, int level, Transfer tr, const int *__restrict__ toc
 }
 
 // adaptive tree: occupancy of the children of split leaves at level L (one below the
-// leaves), into occL (the level's part of the occupancy array, zeroed before)
+// leaves), into occL (the level's part of the occupancy array, zeroed before); the work
+// counts read it to count the children's M2L pairs
 __global__ void k_fine_occ(int64_t n_fine, int L, const int *__restrict__ n_ref, const int *__restrict__ ref_leaf,
                            const int *__restrict__ child_start, int *__restrict__ occL) {
     const int64_t f = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;

@@ -724,7 +724,7 @@ int svd_transform_w(gbfmm_ctx *ctx, const float *Wf, bool fine) {
             return rc;
     }
     if (fine) {
-        // the children of split leaves, compact, then into the global rows of level L
+        // the children of split leaves, in their compact rows (fine_m2l reads them there)
         const int l = ctx->L;
         const int64_t n_fine = RF.fine_rows();
         if (int rc = split_level(ctx, RF.W7, n_fine, ns, lds, l, T.sR)) return rc;

@@ -73,7 +73,9 @@ struct TcPlan {
 
 int m2l_tc_setup(gbfmm_ctx *ctx);    // operators (per medium and p)
 int m2l_tc_prepare(gbfmm_ctx *ctx);  // per tree
-// W64 / S64 non-null: FP64 multipole values in, FP64 local values out (GBFMM_MIXED_F64T)
+// W64 / S64 non-null: FP64 multipole values in, FP64 local values out (GBFMM_MIXED_F64T);
+// fine: the adaptive tree's children take part (compressed M2L: transforms of their values,
+// fine_m2l over their pairs, expansion into their local values)
 int m2l_tc_run(gbfmm_ctx *ctx, const float *Wf, const double *W64, const int *occ, const int *tocc, float *Sf,
                double *S64, bool fine = false);
 void m2l_tc_free(gbfmm_ctx *ctx);
