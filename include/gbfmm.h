@@ -98,8 +98,10 @@ typedef struct {
                               a convolution, by products of discrete Fourier transforms of size
                               (2p)^3 (54 (2p)^2 (p+1) complex multiply-adds per cell pair
                               instead of 54 p^6; fmm_default_options); 0 = dense node-pair
-                              sums.  Falls back to the dense form while the stream is being
-                              captured into a graph. */
+                              sums.  The transform form reads each level's count of occupied
+                              cells back to the host, so an FP64 evaluation synchronises the
+                              stream once per level; it falls back to the dense form while the
+                              stream is being captured into a graph. */
     int m2l_chunks;        /* MIXED: the tensor-core M2L sums each class's 189 offsets in this
                               many consecutive runs, each accumulated in tensor memory from
                               zero and added to the local values in FP32 (FP64 with
