@@ -214,10 +214,11 @@ int ensure_blas(gbfmm_ctx *ctx) {
         T.blas_ws_bytes = size_t(64) << 20;
         CK(cudaMalloc(&T.blas_ws, T.blas_ws_bytes));
         BL(cublasSetWorkspace(h, T.blas_ws, T.blas_ws_bytes));
-        // per-pass transforms: FP32 GEMMs emulated on the tensor cores where cuBLAS can
-        BL(cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_EAGER));
     }
     BL(cublasSetStream((cublasHandle_t)T.blas, ctx->stream));
+    // host scalars unless a caller switches to device scalars for its own calls (and back),
+    // also after a call that returned early
+    BL(cublasSetPointerMode((cublasHandle_t)T.blas, CUBLAS_POINTER_MODE_HOST));
     return GBFMM_OK;
 }
 
@@ -535,6 +536,7 @@ __global__ void k_fine_scatter(int64_t n, const int2 *__restrict__ pairs, const 
 int fine_m2l(gbfmm_ctx *ctx) {
     TcPlan &T = ctx->tc;
     auto &RF = ctx->rf;
+    if (int rc = ensure_blas(ctx)) return rc;
     cudaStream_t st = ctx->stream;
     const int L = ctx->L, n_op = T.n_off;
     const int64_t n_fine = RF.fine_rows();
