@@ -5,6 +5,7 @@ import os
 import sys
 
 import numpy as np
+import pytest
 
 from paper_1712_07739_gb300 import synth
 
@@ -55,3 +56,21 @@ def test_oracle_sample_is_bounded_and_scaled():
     assert rate > 0 and used >= 1 and dt < 30.0
     assert "source points" in desc and "segments/s" in desc
     assert np.isfinite(rate)
+
+
+def test_roofline_traffic_belongs_to_its_capture():
+    """The near field's DRAM traffic is reported only for a launch a capture
+    describes: the uniform tree (250k capture, scaled by points) or the 1M
+    headline on the adaptive tree (its own capture); anything else is null."""
+    peaks = {"fp64_tflops": 1.0, "fp32_tflops": 80.0, "source": "test"}
+    work = {"near_pairs": 3_627_757_324, "m2l_pairs": 18_013_294, "points": 4_000_000}
+    head = dict(bench.WORKLOADS["c3"])
+    assert head["refine_points"] == 128
+    r = bench.roofline_of(head, work, 75.0, 170.0, 1, peaks, ranks={"r1": 832, "r2": 960})
+    assert r["bound"] == "alu" and r["traffic"] == bench.NEAR_SYM_ADAPTIVE_1M_DRAM_BYTES
+    uni = dict(bench.WORKLOADS["c3u"])
+    r = bench.roofline_of(uni, work, 64.0, 190.0, 1, peaks, ranks={"r1": 832, "r2": 960})
+    assert r["traffic"] == pytest.approx(bench.NEAR_SYM_DRAM_BYTES_PER_POINT * 4_000_000)
+    other = dict(head, refine_points=64)
+    r = bench.roofline_of(other, work, 75.0, 170.0, 1, peaks, ranks={"r1": 832, "r2": 960})
+    assert r["traffic"] is None
